@@ -1,0 +1,773 @@
+"""CPU CKKS oracle -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow RNS-CKKS written from the MCKKS description (Sec. 2.2, Fig. 1 of
+the paper) and the readings listed under "Readings" in the design notes.  Only
+``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
+import this module.  It shares no code with the CUDA library: both sides follow
+the same written specification independently.
+
+Representation
+--------------
+* Ring R_Q = Z_Q[X]/(X^N+1), Q = q_0 ... q_{L-1} (Sec. 2.2); special primes
+  p_0 .. p_{K-1} for hybrid key switching.
+* A polynomial is a uint64 array ``[limbs, N]`` of residues, limb i modulo the
+  i-th prime of its basis.  Ciphertext components are kept in the NTT
+  (evaluation) representation: slot j of a limb holds a(psi^(2 brv(j)+1)).
+* A ciphertext is (c0, c1) with c0 + c1*s = Delta*m + e (Fig. 1 items 5-6).
+
+Every modular product goes through ``ckks_ref.c`` (``(u128)a*b % q``).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "libckks_ref.so")
+_lib = None
+
+U64P = np.ctypeslib.ndpointer(dtype=np.uint64, flags="C_CONTIGUOUS")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle's C primitives with gcc (plain -O2, OpenMP over rows)."""
+    src = os.path.join(_HERE, "ckks_ref.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        os.makedirs(os.path.dirname(_SO), exist_ok=True)
+        tmp = _SO + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-o", tmp, src])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_SO)
+        c_int, u64 = ctypes.c_int, ctypes.c_uint64
+        L.ref_powmod.restype = u64
+        L.ref_powmod.argtypes = [u64, u64, u64]
+        L.ref_ntt_direct.argtypes = [U64P, U64P, c_int, u64, u64]
+        L.ref_ntt_forward_rows.argtypes = [U64P, c_int, c_int, U64P, U64P]
+        L.ref_ntt_inverse_rows.argtypes = [U64P, c_int, c_int, U64P, U64P]
+        L.ref_negacyclic_schoolbook.argtypes = [U64P, U64P, U64P, c_int, u64]
+        for name in ("ref_rows_add", "ref_rows_sub", "ref_rows_mul"):
+            getattr(L, name).argtypes = [U64P, U64P, U64P, c_int, c_int, U64P]
+        L.ref_rows_neg.argtypes = [U64P, U64P, c_int, c_int, U64P]
+        L.ref_rows_mul_scalar.argtypes = [U64P, U64P, U64P, c_int, c_int, U64P]
+        L.ref_rows_add_scalar.argtypes = [U64P, U64P, U64P, c_int, c_int, U64P]
+        L.ref_rows_reduce.argtypes = [U64P, U64P, c_int, c_int, U64P]
+        L.ref_automorphism_ntt.argtypes = [U64P, U64P, c_int, c_int, u64]
+        L.ref_automorphism_coef.argtypes = [U64P, U64P, c_int, c_int, u64, U64P]
+        L.ref_basis_convert.argtypes = [U64P, U64P, c_int, c_int, U64P, U64P, c_int, U64P, U64P]
+        _lib = L
+    return _lib
+
+
+def _u64(xs) -> np.ndarray:
+    return np.ascontiguousarray(np.array([int(x) for x in xs], dtype=np.uint64))
+
+
+# ----------------------------------------------------------------------------
+# Number theory (primes and roots; readings R13)
+# ----------------------------------------------------------------------------
+
+def is_prime(n: int) -> bool:
+    """Deterministic Miller-Rabin for n < 2^64 (the first 12 prime bases)."""
+    if n < 2:
+        return False
+    small = (2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37)
+    for p in small:
+        if n % p == 0:
+            return n == p
+    d, s = n - 1, 0
+    while d % 2 == 0:
+        d //= 2
+        s += 1
+    for a in small:
+        x = pow(a, d, n)
+        if x in (1, n - 1):
+            continue
+        for _ in range(s - 1):
+            x = x * x % n
+            if x == n - 1:
+                break
+        else:
+            return False
+    return True
+
+
+def find_primes(log_n: int, bits: list[int]) -> list[int]:
+    """For each requested size b, in order: the largest prime q < 2^b with
+    q = 1 (mod 2N) not already chosen."""
+    two_n = 2 << log_n
+    chosen: list[int] = []
+    for b in bits:
+        c = (1 << b) - two_n + 1
+        while not is_prime(c) or c in chosen:
+            c -= two_n
+            if c <= two_n:
+                raise ValueError("no prime of %d bits for N=2^%d" % (b, log_n))
+        chosen.append(c)
+    return chosen
+
+
+def find_psi(q: int, n: int) -> int:
+    """psi = x^((q-1)/2N) for the smallest x >= 2 such that psi^N = -1 (mod q),
+    i.e. psi is a primitive 2N-th root of unity."""
+    e = (q - 1) // (2 * n)
+    x = 2
+    while True:
+        psi = pow(x, e, q)
+        if pow(psi, n, q) == q - 1:
+            return psi
+        x += 1
+
+
+def brv(x: int, bits: int) -> int:
+    return int(format(x, "0%db" % bits)[::-1], 2) if bits else 0
+
+
+def galois_element(k: int, n: int) -> int:
+    """Rotation R(m, k) (left by k slots, Sec. 3.2) is X -> X^(5^k mod 2N)."""
+    return pow(5, k % (n // 2), 2 * n)
+
+
+# ----------------------------------------------------------------------------
+# Randomness: SplitMix64 (Steele, Lea, Flood 2014), one stream per purpose
+# ----------------------------------------------------------------------------
+
+GAMMA = 0x9E3779B97F4A7C15
+M64 = (1 << 64) - 1
+
+PURPOSE_SK, PURPOSE_PK_A, PURPOSE_PK_E = 1, 2, 3
+PURPOSE_KEY_A, PURPOSE_KEY_E = 4, 5
+PURPOSE_ENC_V, PURPOSE_ENC_E0, PURPOSE_ENC_E1 = 6, 7, 8
+PURPOSE_SMUDGE = 9
+
+
+def mix64(z: int) -> int:
+    z &= M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def _mix64_np(z: np.ndarray) -> np.ndarray:
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        return z ^ (z >> np.uint64(31))
+
+
+class Stream:
+    """Counter-based SplitMix64 stream for (seed, purpose, a, b):
+    state_0 = seed XOR mix64(key + GAMMA), key = purpose<<56 | a<<32 | b;
+    draw i returns mix64(state_0 + (i+1)*GAMMA)."""
+
+    def __init__(self, seed: int, purpose: int, a: int = 0, b: int = 0):
+        key = ((purpose & 0xFF) << 56) | ((a & 0xFFFFFF) << 32) | (b & 0xFFFFFFFF)
+        self.state = (seed ^ mix64((key + GAMMA) & M64)) & M64
+        self.count = 0
+
+    def draws(self, n: int) -> np.ndarray:
+        idx = np.arange(self.count + 1, self.count + 1 + n, dtype=np.uint64)
+        with np.errstate(over="ignore"):
+            st = np.uint64(self.state) + idx * np.uint64(GAMMA)
+        self.count += n
+        return _mix64_np(st)
+
+
+def sample_uniform(stream: Stream, q: int, n: int) -> np.ndarray:
+    """Uniform residues mod q by rejection on bitlen(q)-bit draws (low bits)."""
+    mask = np.uint64((1 << q.bit_length()) - 1)
+    out = np.empty(0, dtype=np.uint64)
+    while out.size < n:
+        r = stream.draws(n - out.size) & mask
+        ok = r < np.uint64(q)
+        # draws past the n-th acceptance must not be consumed
+        acc = np.flatnonzero(ok)
+        need = n - out.size
+        if acc.size >= need:
+            last = acc[need - 1]
+            stream.count -= (r.size - 1 - last)
+            out = np.concatenate([out, r[acc[:need]]])
+        else:
+            out = np.concatenate([out, r[ok]])
+    return out
+
+
+def sample_ternary(stream: Stream, n: int) -> np.ndarray:
+    """Coefficients in {-1, 0, 1}: draw % 3 mapped 0->0, 1->1, 2->-1."""
+    r = (stream.draws(n) % np.uint64(3)).astype(np.int64)
+    r[r == 2] = -1
+    return r
+
+
+def gaussian_thresholds(sigma: float) -> tuple[int, list[int]]:
+    """CDT table of the discrete Gaussian of parameter sigma on [-B, B],
+    B = floor(6 sigma): T_k = floor(2^63 * cum_k / total), weights
+    exp(-k^2 / (2 sigma^2)) summed in increasing k."""
+    bound = int(math.floor(6.0 * sigma))
+    two_s2 = 2.0 * sigma * sigma
+    w = [math.exp(-float(k * k) / two_s2) for k in range(-bound, bound + 1)]
+    total = 0.0
+    for x in w:
+        total += x
+    cum = 0.0
+    th = []
+    for x in w:
+        cum += x
+        th.append(int(math.floor((cum / total) * 9223372036854775808.0)))
+    return bound, th
+
+
+def sample_gaussian(stream: Stream, n: int, sigma: float) -> np.ndarray:
+    """value = (smallest k with (draw >> 1) < T_k) - B, clamped to B."""
+    bound, th = gaussian_thresholds(sigma)
+    r = stream.draws(n) >> np.uint64(1)
+    idx = np.searchsorted(np.array(th, dtype=np.uint64), r, side="right")
+    idx = np.minimum(idx, 2 * bound)
+    return idx.astype(np.int64) - bound
+
+
+# ----------------------------------------------------------------------------
+# Context
+# ----------------------------------------------------------------------------
+
+class Context:
+    """Parameters: ring degree 2^log_n, Q primes of the given sizes (q_0
+    first), special primes, default scale 2^log2_scale, error width sigma."""
+
+    def __init__(self, log_n: int, q_bits, p_bits, log2_scale: float, sigma: float = 3.2):
+        self.log_n = log_n
+        self.N = 1 << log_n
+        self.S = self.N // 2
+        primes = find_primes(log_n, list(q_bits) + list(p_bits))
+        self.q = primes[: len(q_bits)]
+        self.p = primes[len(q_bits):]
+        self.n_q, self.K = len(self.q), len(self.p)
+        self.dnum = -(-self.n_q // self.K)
+        self.scale = 2.0 ** log2_scale
+        self.sigma = sigma
+        self.psi = {x: find_psi(x, self.N) for x in primes}
+        self.P = math.prod(self.p)
+
+    # -- row helpers ---------------------------------------------------------
+    def ntt(self, a: np.ndarray, primes) -> np.ndarray:
+        out = np.ascontiguousarray(a, dtype=np.uint64).copy()
+        rows = out.reshape(-1, self.N)
+        lib().ref_ntt_forward_rows(rows, rows.shape[0], self.log_n, _u64(primes), _u64(self.psi[x] for x in primes))
+        return out
+
+    def intt(self, a: np.ndarray, primes) -> np.ndarray:
+        out = np.ascontiguousarray(a, dtype=np.uint64).copy()
+        rows = out.reshape(-1, self.N)
+        lib().ref_ntt_inverse_rows(rows, rows.shape[0], self.log_n, _u64(primes), _u64(self.psi[x] for x in primes))
+        return out
+
+    def _binop(self, fn, a, b, primes):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        b = np.ascontiguousarray(b, dtype=np.uint64)
+        out = np.empty_like(a)
+        getattr(lib(), fn)(out, a, b, len(primes), self.N, _u64(primes))
+        return out
+
+    def add(self, a, b, primes):
+        return self._binop("ref_rows_add", a, b, primes)
+
+    def sub(self, a, b, primes):
+        return self._binop("ref_rows_sub", a, b, primes)
+
+    def mul(self, a, b, primes):
+        return self._binop("ref_rows_mul", a, b, primes)
+
+    def neg(self, a, primes):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        out = np.empty_like(a)
+        lib().ref_rows_neg(out, a, len(primes), self.N, _u64(primes))
+        return out
+
+    def mul_scalar(self, a, scalars, primes):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        out = np.empty_like(a)
+        lib().ref_rows_mul_scalar(out, a, _u64(scalars), len(primes), self.N, _u64(primes))
+        return out
+
+    def add_scalar(self, a, scalars, primes):
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        out = np.empty_like(a)
+        lib().ref_rows_add_scalar(out, a, _u64(scalars), len(primes), self.N, _u64(primes))
+        return out
+
+    def automorphism(self, a, g: int) -> np.ndarray:
+        a = np.ascontiguousarray(a, dtype=np.uint64)
+        out = np.empty_like(a)
+        lib().ref_automorphism_ntt(out, a, a.size // self.N, self.log_n, g)
+        return out
+
+    def signed_to_rows(self, v: np.ndarray, primes) -> np.ndarray:
+        """Integer coefficients (int64 or Python ints) -> residues per prime."""
+        out = np.empty((len(primes), self.N), dtype=np.uint64)
+        v = np.asarray(v)
+        for i, t in enumerate(primes):
+            if v.dtype == object:
+                out[i] = np.array([int(x) % t for x in v], dtype=np.uint64)
+            else:  # every prime here is below 2^62, so int64 arithmetic is exact
+                out[i] = np.mod(v.astype(np.int64), np.int64(t)).astype(np.uint64)
+        return out
+
+    def basis_convert(self, x: np.ndarray, src, dst) -> np.ndarray:
+        """Fast basis conversion (no correction): residues of one integer
+        modulo `src` -> residues modulo `dst` (coefficient representation)."""
+        Qs = math.prod(src)
+        qhat = [Qs // t for t in src]
+        qhat_inv = [pow(qh % t, -1, t) for qh, t in zip(qhat, src)]
+        qhat_mod = [qh % d for qh in qhat for d in dst]
+        out = np.empty((len(dst), self.N), dtype=np.uint64)
+        lib().ref_basis_convert(out, np.ascontiguousarray(x, dtype=np.uint64), self.N, len(src), _u64(src),
+                                _u64(qhat_inv), len(dst), _u64(dst), _u64(qhat_mod))
+        return out
+
+
+# ----------------------------------------------------------------------------
+# Encoding (canonical embedding; readings R14)
+# ----------------------------------------------------------------------------
+
+def round_half_away(x: np.ndarray) -> np.ndarray:
+    return np.sign(x) * np.floor(np.abs(x) + 0.5)
+
+
+def slot_exponents(n: int) -> np.ndarray:
+    """e_j = 5^j mod 2N: slot j is the value at zeta^(e_j), zeta = exp(i pi/N)."""
+    s = n // 2
+    e = np.empty(s, dtype=np.int64)
+    v = 1
+    for j in range(s):
+        e[j] = v
+        v = v * 5 % (2 * n)
+    return e
+
+
+def encode_real(n: int, z, scale: float) -> np.ndarray:
+    """Slots -> signed integer coefficients:
+    m_i = (2/N) Re(sum_j z_j zeta^(-i e_j)), c_i = round(scale * m_i).
+    The sum is taken with a length-2N FFT of the scattered slots."""
+    s = n // 2
+    zz = np.zeros(s, dtype=np.complex128)
+    z = np.asarray(z)
+    zz[: z.size] = z
+    e = slot_exponents(n)
+    big = np.zeros(2 * n, dtype=np.complex128)
+    big[e] = zz
+    big[(2 * n - e) % (2 * n)] = np.conj(zz)
+    m = np.fft.fft(big)[:n].real / n
+    c = round_half_away(m * scale)
+    if np.max(np.abs(c)) >= 2.0 ** 62:
+        raise OverflowError("encoded coefficient exceeds 2^62")
+    return c.astype(np.int64)
+
+
+def encode_direct(n: int, z, scale: float) -> np.ndarray:
+    """Same map as encode_real, as the O(N^2) sum of the definition (pins)."""
+    s = n // 2
+    zz = np.zeros(s, dtype=np.complex128)
+    zz[: np.asarray(z).size] = z
+    e = slot_exponents(n)
+    i = np.arange(n)
+    ang = np.pi * np.outer(i, e) / n
+    m = (2.0 / n) * (np.cos(ang) @ zz.real + np.sin(ang) @ zz.imag)
+    return round_half_away(m * scale).astype(np.int64)
+
+
+def decode(n: int, coeffs: np.ndarray, scale: float) -> np.ndarray:
+    """Centered integer coefficients -> complex slots: z_j = sum_i c_i zeta^(i e_j) / scale."""
+    e = slot_exponents(n)
+    big = np.zeros(2 * n, dtype=np.complex128)
+    big[:n] = np.asarray(coeffs, dtype=np.float64)
+    y = np.fft.ifft(big) * (2 * n)
+    return y[e] / scale
+
+
+# ----------------------------------------------------------------------------
+# Keys, encryption, decryption (Fig. 1 items 1-6; readings R15, R16)
+# ----------------------------------------------------------------------------
+
+@dataclass
+class SwitchKey:
+    b: np.ndarray  # [dnum, n_q + K, N] NTT form over q_0..q_{L-1}, p_0..p_{K-1}
+    a: np.ndarray
+
+
+@dataclass
+class KeySet:
+    seed: int
+    s_parts: list           # per-party ternary secrets (signed int64 coefficients)
+    s: np.ndarray           # sum of the shares (signed)
+    s_ntt: np.ndarray       # [n_q + K, N]
+    s_parts_ntt: list       # per party, [n_q + K, N]
+    pk_b: np.ndarray        # [n_q, N]
+    pk_a: np.ndarray
+    relin: SwitchKey | None = None
+    rot: dict = field(default_factory=dict)  # galois element -> SwitchKey
+
+
+@dataclass
+class Ciphertext:
+    c: np.ndarray   # [2, limbs, N] NTT form over q_0..q_{limbs-1}
+    scale: float
+
+    @property
+    def limbs(self) -> int:
+        return self.c.shape[1]
+
+    def copy(self) -> "Ciphertext":
+        return Ciphertext(self.c.copy(), self.scale)
+
+
+def all_primes(ctx: Context):
+    return ctx.q + ctx.p
+
+
+def gen_switch_key(ctx: Context, ks: KeySet, key_id: int, sp_ntt: np.ndarray) -> SwitchKey:
+    """swk_j = (-a_j s + e_j + P * [1 on digit j's primes] * s', a_j) over PQ
+    (reading R11: the gadget factor P*Qhat_j*[Qhat_j^-1]_{Q_j} is P modulo the
+    primes of digit j and 0 modulo every other prime)."""
+    prim = all_primes(ctx)
+    rows = len(prim)
+    B = np.empty((ctx.dnum, rows, ctx.N), dtype=np.uint64)
+    A = np.empty((ctx.dnum, rows, ctx.N), dtype=np.uint64)
+    for j in range(ctx.dnum):
+        st = Stream(ks.seed, PURPOSE_KEY_A, key_id, j)
+        a = np.stack([sample_uniform(st, t, ctx.N) for t in prim])
+        e = sample_gaussian(Stream(ks.seed, PURPOSE_KEY_E, key_id, j), ctx.N, ctx.sigma)
+        e_ntt = ctx.ntt(ctx.signed_to_rows(e, prim), prim)
+        b = ctx.sub(e_ntt, ctx.mul(a, ks.s_ntt, prim), prim)
+        lo, hi = j * ctx.K, min((j + 1) * ctx.K, ctx.n_q)
+        sub_p = prim[lo:hi]
+        gad = ctx.mul_scalar(sp_ntt[lo:hi], [ctx.P % t for t in sub_p], sub_p)
+        b[lo:hi] = ctx.add(b[lo:hi], gad, sub_p)
+        B[j], A[j] = b, a
+    return SwitchKey(B, A)
+
+
+def keygen(ctx: Context, n_parties: int, seed: int, rot_steps=(), relin: bool = True) -> KeySet:
+    """SecKeyGen for every party, s = sum of shares (reading R16), then the
+    collective public key, the relinearisation key (s' = s^2) and one Galois
+    key per rotation step (s' = sigma_g(s))."""
+    prim = all_primes(ctx)
+    parts = [sample_ternary(Stream(seed, PURPOSE_SK, party, 0), ctx.N) for party in range(n_parties)]
+    s = np.sum(parts, axis=0).astype(np.int64)
+    s_ntt = ctx.ntt(ctx.signed_to_rows(s, prim), prim)
+    parts_ntt = [ctx.ntt(ctx.signed_to_rows(x, prim), prim) for x in parts]
+    st = Stream(seed, PURPOSE_PK_A, 0, 0)
+    a = np.stack([sample_uniform(st, t, ctx.N) for t in ctx.q])
+    e = sample_gaussian(Stream(seed, PURPOSE_PK_E, 0, 0), ctx.N, ctx.sigma)
+    e_ntt = ctx.ntt(ctx.signed_to_rows(e, ctx.q), ctx.q)
+    b = ctx.sub(e_ntt, ctx.mul(a, s_ntt[: ctx.n_q], ctx.q), ctx.q)
+    ks = KeySet(seed, parts, s, s_ntt, parts_ntt, b, a)
+    if relin:
+        ks.relin = gen_switch_key(ctx, ks, 0, ctx.mul(s_ntt, s_ntt, prim))
+    for k in rot_steps:
+        add_rotation_key(ctx, ks, k)
+    return ks
+
+
+def add_rotation_key(ctx: Context, ks: KeySet, k: int) -> None:
+    g = galois_element(k, ctx.N)
+    if g != 1 and g not in ks.rot:
+        ks.rot[g] = gen_switch_key(ctx, ks, g, ctx.automorphism(ks.s_ntt, g))
+
+
+def encrypt_coeffs(ctx: Context, ks: KeySet, m: np.ndarray, scale: float, limbs: int, seed: int,
+                   tag: int = 0, index: int = 0) -> Ciphertext:
+    """Enc(pk, m) = (v*pk_b + e0 + m, v*pk_a + e1) over the first `limbs`
+    primes; m are signed integer coefficients (an encoded plaintext)."""
+    prim = ctx.q[:limbs]
+    v = sample_ternary(Stream(seed, PURPOSE_ENC_V, tag, index), ctx.N)
+    e0 = sample_gaussian(Stream(seed, PURPOSE_ENC_E0, tag, index), ctx.N, ctx.sigma)
+    e1 = sample_gaussian(Stream(seed, PURPOSE_ENC_E1, tag, index), ctx.N, ctx.sigma)
+    vn = ctx.ntt(ctx.signed_to_rows(v, prim), prim)
+    e0n = ctx.ntt(ctx.signed_to_rows(e0, prim), prim)
+    e1n = ctx.ntt(ctx.signed_to_rows(e1, prim), prim)
+    mn = ctx.ntt(ctx.signed_to_rows(m, prim), prim)
+    c0 = ctx.add(ctx.add(ctx.mul(vn, ks.pk_b[:limbs], prim), e0n, prim), mn, prim)
+    c1 = ctx.add(ctx.mul(vn, ks.pk_a[:limbs], prim), e1n, prim)
+    return Ciphertext(np.stack([c0, c1]), float(scale))
+
+
+def encrypt(ctx: Context, ks: KeySet, slots, seed: int, limbs: int | None = None, scale: float | None = None,
+            tag: int = 0, index: int = 0) -> Ciphertext:
+    scale = ctx.scale if scale is None else scale
+    limbs = ctx.n_q if limbs is None else limbs
+    return encrypt_coeffs(ctx, ks, encode_real(ctx.N, slots, scale), scale, limbs, seed, tag, index)
+
+
+def centered(x: np.ndarray, q: int) -> np.ndarray:
+    x = x.astype(object)
+    return np.array([int(v) - q if int(v) > q // 2 else int(v) for v in x], dtype=object)
+
+
+def decrypt_poly(ctx: Context, ks: KeySet, ct: Ciphertext, smudge_sigma: float = 0.0, smudge_seed: int = 0):
+    """Collective DDec restricted to q_0 (the plaintext is far below q_0/2):
+    c0 + sum_i c1*s_i, each party adding its share; returns the centered
+    integer coefficients (int64)."""
+    q0 = [ctx.q[0]]
+    acc = ct.c[0, :1].copy()
+    for i, sp in enumerate(ks.s_parts_ntt):
+        share = ctx.mul(ct.c[1, :1], sp[:1], q0)
+        if smudge_sigma > 0:
+            e = sample_gaussian(Stream(smudge_seed, PURPOSE_SMUDGE, i, 0), ctx.N, smudge_sigma)
+            share = ctx.add(share, ctx.ntt(ctx.signed_to_rows(e, q0), q0), q0)
+        acc = ctx.add(acc, share, q0)
+    coef = ctx.intt(acc, q0)[0].astype(np.int64)
+    q = ctx.q[0]
+    coef = np.where(coef > q // 2, coef - q, coef)  # q < 2^63 so int64 is safe
+    return coef
+
+
+def decrypt(ctx: Context, ks: KeySet, ct: Ciphertext, n: int | None = None) -> np.ndarray:
+    z = decode(ctx.N, decrypt_poly(ctx, ks, ct), ct.scale).real
+    return z if n is None else z[:n]
+
+
+def decrypt_crt(ctx: Context, ks: KeySet, ct: Ciphertext) -> list:
+    """Full-modulus decryption with CRT reconstruction in Python integers
+    (pins only): centered c0 + c1*s mod q_0...q_{limbs-1}."""
+    prim = ctx.q[: ct.limbs]
+    x = ctx.add(ct.c[0], ctx.mul(ct.c[1], ks.s_ntt[: ct.limbs], prim), prim)
+    coef = ctx.intt(x, prim)
+    Q = math.prod(prim)
+    out = []
+    for i in range(ctx.N):
+        v = 0
+        for t, qi in enumerate(prim):
+            qh = Q // qi
+            v += int(coef[t, i]) * qh * pow(qh, -1, qi)
+        v %= Q
+        out.append(v - Q if v > Q // 2 else v)
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Homomorphic evaluation (Fig. 1 items 7-12; readings R6, R10, R11, R12)
+# ----------------------------------------------------------------------------
+
+class ScaleError(ValueError):
+    pass
+
+
+class Evaluator:
+    """Server-side evaluation on NTT-form ciphertexts.  `counts` records the
+    operations in the units of Table I (Add, Mul_pt, Rot, Mul_ct) plus the
+    key switches, rescales and hoisted rotations actually performed."""
+
+    SCALE_TOL = 2.0 ** -20
+
+    def __init__(self, ctx: Context, ks: KeySet):
+        self.ctx, self.ks = ctx, ks
+        self.counts: dict[str, int] = {}
+
+    def _count(self, name: str, n: int = 1) -> None:
+        self.counts[name] = self.counts.get(name, 0) + n
+
+    def _prim(self, limbs: int):
+        return self.ctx.q[:limbs]
+
+    def _check(self, a: Ciphertext, b: Ciphertext) -> None:
+        if a.limbs != b.limbs:
+            raise ValueError("level mismatch: %d vs %d limbs" % (a.limbs, b.limbs))
+        if abs(a.scale / b.scale - 1.0) > self.SCALE_TOL:
+            raise ScaleError("scale mismatch: %r vs %r" % (a.scale, b.scale))
+
+    # -- additive ---------------------------------------------------------------
+    def add(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
+        self._check(a, b)
+        self._count("Add")
+        pr = self._prim(a.limbs)
+        return Ciphertext(np.stack([self.ctx.add(a.c[i], b.c[i], pr) for i in range(a.c.shape[0])]), a.scale)
+
+    def sub(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
+        self._check(a, b)
+        self._count("Add")
+        pr = self._prim(a.limbs)
+        return Ciphertext(np.stack([self.ctx.sub(a.c[i], b.c[i], pr) for i in range(a.c.shape[0])]), a.scale)
+
+    def add_const(self, ct: Ciphertext, value: float) -> Ciphertext:
+        """Adds the constant polynomial round(value * scale) (every NTT slot of c0)."""
+        c = int(round_half_away(np.array([value * ct.scale]))[0])
+        pr = self._prim(ct.limbs)
+        out = ct.c.copy()
+        out[0] = self.ctx.add_scalar(ct.c[0], [c % t for t in pr], pr)
+        return Ciphertext(out, ct.scale)
+
+    # -- multiplicative -----------------------------------------------------------
+    def mul_plain(self, ct: Ciphertext, pt_ntt: np.ndarray, pt_scale: float) -> Ciphertext:
+        """Mul_pt with an NTT-form plaintext of at least ct.limbs limbs."""
+        self._count("Mul_pt")
+        pr = self._prim(ct.limbs)
+        pt = pt_ntt[: ct.limbs]
+        return Ciphertext(np.stack([self.ctx.mul(ct.c[i], pt, pr) for i in range(2)]), ct.scale * pt_scale)
+
+    def mul_int(self, ct: Ciphertext, c: int, new_scale: float | None = None) -> Ciphertext:
+        """Multiplication by an integer constant (no level consumed)."""
+        pr = self._prim(ct.limbs)
+        sc = [c % t for t in pr]
+        out = np.stack([self.ctx.mul_scalar(ct.c[i], sc, pr) for i in range(ct.c.shape[0])])
+        return Ciphertext(out, ct.scale if new_scale is None else new_scale)
+
+    def tensor(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
+        """(a0,a1) x (b0,b1) -> (a0b0, a0b1 + a1b0, a1b1), decrypting under (1, s, s^2)."""
+        if a.limbs != b.limbs:
+            raise ValueError("level mismatch")
+        self._count("Mul_ct")
+        pr = self._prim(a.limbs)
+        m = self.ctx.mul
+        d0 = m(a.c[0], b.c[0], pr)
+        d1 = self.ctx.add(m(a.c[0], b.c[1], pr), m(a.c[1], b.c[0], pr), pr)
+        d2 = m(a.c[1], b.c[1], pr)
+        return Ciphertext(np.stack([d0, d1, d2]), a.scale * b.scale)
+
+    def relinearize(self, d: Ciphertext) -> Ciphertext:
+        ks0, ks1 = self.keyswitch(d.c[2], self.ks.relin, d.limbs)
+        pr = self._prim(d.limbs)
+        return Ciphertext(np.stack([self.ctx.add(d.c[0], ks0, pr), self.ctx.add(d.c[1], ks1, pr)]), d.scale)
+
+    def mul_relin(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
+        return self.relinearize(self.tensor(a, b))
+
+    # -- levels -----------------------------------------------------------------
+    def drop(self, ct: Ciphertext, limbs: int) -> Ciphertext:
+        """Discard the top primes (exact; the scale is unchanged)."""
+        if limbs > ct.limbs or limbs < 1:
+            raise ValueError("bad drop")
+        return Ciphertext(ct.c[:, :limbs].copy(), ct.scale)
+
+    def rescale(self, ct: Ciphertext) -> Ciphertext:
+        """RS: c' = round(c / q_top) limb-wise (reading R12): with
+        x = [c]_{q_top} + floor(q_top/2) taken in [0, q_top), the remainder
+        r = x - floor(q_top/2) is removed from every lower limb before the
+        multiplication by q_top^-1."""
+        if ct.limbs < 2:
+            raise ValueError("no level left to rescale")
+        self._count("Rescale")
+        ctx = self.ctx
+        top = ct.limbs - 1
+        qt = ctx.q[top]
+        half = (qt - 1) // 2
+        lower = ctx.q[:top]
+        out = np.empty((ct.c.shape[0], top, ctx.N), dtype=np.uint64)
+        for comp in range(ct.c.shape[0]):
+            x = ctx.intt(ct.c[comp, top:top + 1], [qt])[0]
+            x = (x + np.uint64(half)) % np.uint64(qt)
+            r = np.empty((top, ctx.N), dtype=np.uint64)
+            for i, qi in enumerate(lower):
+                r[i] = (x % np.uint64(qi) + np.uint64(qi) - np.uint64(half % qi)) % np.uint64(qi)
+            r = ctx.ntt(r, lower)
+            diff = ctx.sub(ct.c[comp, :top], r, lower)
+            out[comp] = ctx.mul_scalar(diff, [pow(qt, -1, qi) for qi in lower], lower)
+        return Ciphertext(out, ct.scale / float(qt))
+
+    # -- hybrid key switching ---------------------------------------------------------
+    def modup(self, d: np.ndarray, limbs: int) -> list:
+        """ModUp: for every digit j (K consecutive primes of Q_l), the digit's
+        residues are extended by fast basis conversion to all other primes of
+        Q_l and to the special primes.  Returns NTT-form arrays over
+        q_0..q_{limbs-1}, p_0..p_{K-1}; on the digit's own primes the input is
+        copied unchanged."""
+        ctx = self.ctx
+        self._count("ModUp")
+        coef = ctx.intt(d, ctx.q[:limbs])
+        ext = ctx.q[:limbs] + ctx.p
+        digits = []
+        for j in range(-(-limbs // ctx.K)):
+            lo, hi = j * ctx.K, min((j + 1) * ctx.K, limbs)
+            src = ctx.q[lo:hi]
+            tgt_idx = [i for i in range(len(ext)) if not lo <= i < hi]
+            tgt = [ext[i] for i in tgt_idx]
+            conv = ctx.ntt(ctx.basis_convert(coef[lo:hi], src, tgt), tgt)
+            D = np.empty((len(ext), ctx.N), dtype=np.uint64)
+            D[lo:hi] = d[lo:hi]
+            D[tgt_idx] = conv
+            digits.append(D)
+        return digits
+
+    def key_rows(self, limbs: int):
+        return list(range(limbs)) + list(range(self.ctx.n_q, self.ctx.n_q + self.ctx.K))
+
+    def inner_product(self, digits: list, key: SwitchKey, limbs: int, galois: int | None = None):
+        """sum_j sigma_g(D_j) * swk_j over Q_l and P (both key halves)."""
+        ctx = self.ctx
+        ext = ctx.q[:limbs] + ctx.p
+        rows = self.key_rows(limbs)
+        acc0 = np.zeros((len(ext), ctx.N), dtype=np.uint64)
+        acc1 = np.zeros_like(acc0)
+        for j, D in enumerate(digits):
+            Dg = ctx.automorphism(D, galois) if galois is not None else D
+            acc0 = ctx.add(acc0, ctx.mul(Dg, key.b[j][rows], ext), ext)
+            acc1 = ctx.add(acc1, ctx.mul(Dg, key.a[j][rows], ext), ext)
+        return acc0, acc1
+
+    def moddown(self, x: np.ndarray, limbs: int) -> np.ndarray:
+        """ModDown: (x - Conv_{P->Q_l}([x]_P)) * P^-1 (reading R11)."""
+        ctx = self.ctx
+        qs = ctx.q[:limbs]
+        xp = ctx.intt(x[limbs:], ctx.p)
+        conv = ctx.ntt(ctx.basis_convert(xp, ctx.p, qs), qs)
+        return ctx.mul_scalar(ctx.sub(x[:limbs], conv, qs), [pow(ctx.P % t, -1, t) for t in qs], qs)
+
+    def keyswitch(self, d: np.ndarray, key: SwitchKey, limbs: int):
+        self._count("KeySwitch")
+        digits = self.modup(d, limbs)
+        a0, a1 = self.inner_product(digits, key, limbs)
+        return self.moddown(a0, limbs), self.moddown(a1, limbs)
+
+    def _rot_key(self, k: int):
+        g = galois_element(k, self.ctx.N)
+        if g == 1:
+            return g, None
+        if g not in self.ks.rot:
+            add_rotation_key(self.ctx, self.ks, k)
+        return g, self.ks.rot[g]
+
+    def rotate(self, ct: Ciphertext, k: int) -> Ciphertext:
+        """Rot(ct, k) realising R(m, k) (left rotation by k slots; reading R1):
+        the automorphism is applied to (c0, c1), then sigma_g(c1) is switched
+        from sigma_g(s) back to s."""
+        g, key = self._rot_key(k)
+        if key is None:
+            return ct.copy()
+        self._count("Rot")
+        pr = self._prim(ct.limbs)
+        c0 = self.ctx.automorphism(ct.c[0], g)
+        c1 = self.ctx.automorphism(ct.c[1], g)
+        ks0, ks1 = self.keyswitch(c1, key, ct.limbs)
+        return Ciphertext(np.stack([self.ctx.add(c0, ks0, pr), ks1]), ct.scale)
+
+    def rotate_hoisted(self, ct: Ciphertext, steps) -> list:
+        """Several rotations of one ciphertext sharing a single ModUp of c1
+        (reading R10): Rot_k = (sigma_g(c0) + MD(<sigma_g(D), swk_g>_0),
+        MD(<sigma_g(D), swk_g>_1))."""
+        steps = list(steps)
+        pr = self._prim(ct.limbs)
+        need = [k for k in steps if galois_element(k, self.ctx.N) != 1]
+        digits = self.modup(ct.c[1], ct.limbs) if need else None
+        out = []
+        for k in steps:
+            g, key = self._rot_key(k)
+            if key is None:
+                out.append(ct.copy())
+                continue
+            self._count("Rot")
+            self._count("RotHoisted")
+            a0, a1 = self.inner_product(digits, key, ct.limbs, galois=g)
+            ks0, ks1 = self.moddown(a0, ct.limbs), self.moddown(a1, ct.limbs)
+            c0 = self.ctx.automorphism(ct.c[0], g)
+            out.append(Ciphertext(np.stack([self.ctx.add(c0, ks0, pr), ks1]), ct.scale))
+        return out

@@ -1,0 +1,536 @@
+"""Oracle for the paper's packed matrix product and composite sign -- TEST
+INFRASTRUCTURE ONLY (see oracle/ckks.py for the rules on who may import it).
+
+Sec. 3 (packed h x h matrix product with O(h) rotations), App. B (baby-step /
+giant-step and the multiplexer trick), App. C (transpose), App. E (parallel
+matrices, iota_beta) and Sec. 4 (composite polynomial g_d^(k), Alg. 5), each
+written from the paper's formulas.  Vectors here are "logical" slot vectors of
+length n = h^2; `expand` maps them to the S = beta*h^2 CKKS slots (App. E).
+"""
+from __future__ import annotations
+
+import math
+from fractions import Fraction
+
+import numpy as np
+
+from . import ckks as C
+
+# ----------------------------------------------------------------------------
+# Vectors, rotations, encodings (Sec. 3.2, 3.4, App. E)
+# ----------------------------------------------------------------------------
+
+
+def R(m: np.ndarray, k: int) -> np.ndarray:
+    """R(m, k) = (m_k, ..., m_{n-1}, m_0, ..., m_{k-1})  (Sec. 3.2)."""
+    return np.roll(m, -k)
+
+
+def iota_inv(A: np.ndarray) -> np.ndarray:
+    """Row-major matrix -> vector, a_{h*i+j} = A_{i,j} (Sec. 3.4)."""
+    return np.asarray(A).reshape(-1)
+
+
+def pack(mats, h: int, beta: int) -> np.ndarray:
+    """iota_beta^-1: slot beta*(h*i+j)+k holds (A_k)_{i,j}; missing matrices are zero (App. E)."""
+    out = np.zeros(beta * h * h)
+    for k, A in enumerate(mats):
+        out[k::beta] = iota_inv(A)
+    return out
+
+
+def unpack(slots: np.ndarray, h: int, beta: int) -> list:
+    return [np.asarray(slots[k: beta * h * h: beta]).reshape(h, h) for k in range(beta)]
+
+
+def expand(u: np.ndarray, beta: int) -> np.ndarray:
+    """A logical mask over n = h^2 positions acting on every packed matrix: u'[beta*t + j] = u[t]."""
+    return np.repeat(u, beta)
+
+
+def baby_steps(h: int) -> int:
+    """b = 2^ceil(log2(h)/2) (reading R3: the power-of-two split also covers h = 32, 128)."""
+    return 1 << math.ceil(math.log2(h) / 2) if h > 1 else 1
+
+
+# ----------------------------------------------------------------------------
+# Permutations and their diagonal vectors (Sec. 3.3, 3.5, Eqs. (1), (5)-(16))
+# ----------------------------------------------------------------------------
+
+
+def mu(A):
+    h = A.shape[0]
+    return np.array([[A[i, (i + j) % h] for j in range(h)] for i in range(h)])
+
+
+def zeta(A):
+    h = A.shape[0]
+    return np.array([[A[(i + j) % h, j] for j in range(h)] for i in range(h)])
+
+
+def phi(A, k=1):
+    h = A.shape[0]
+    return np.array([[A[i, (j + k) % h] for j in range(h)] for i in range(h)])
+
+
+def pi_(A, k=1):
+    h = A.shape[0]
+    return np.array([[A[(i + k) % h, j] for j in range(h)] for i in range(h)])
+
+
+def perm_matrix(h: int, kind: str, k: int = 0) -> np.ndarray:
+    """Matrix representations U^mu, U^zeta (Eqs. 5-6), V^k, P^k (Eqs. 7-8) and
+    the transpose U^T (App. C) as 0/1 matrices on R^(h^2)."""
+    n = h * h
+    U = np.zeros((n, n), dtype=np.int64)
+    for i in range(h):
+        for j in range(h):
+            if kind == "mu":
+                t = h * i + (i + j) % h
+            elif kind == "zeta":
+                t = h * ((i + j) % h) + j
+            elif kind == "V":
+                t = h * i + (j + k) % h
+            elif kind == "P":
+                t = h * ((i + k) % h) + j
+            elif kind == "T":
+                t = h * j + i
+            else:
+                raise ValueError(kind)
+            U[h * i + j, t] = 1
+    return U
+
+
+def diagonal(U: np.ndarray, k: int) -> np.ndarray:
+    """k-th diagonal vector u_k = (U_{0,k}, U_{1,k+1}, ..., U_{n-1,k-1}) (Sec. 3.2)."""
+    n = U.shape[0]
+    return np.array([U[t, (t + k) % n] for t in range(n)])
+
+
+def diag_mu(h: int, k: int) -> np.ndarray:
+    """u^mu_k, -h < k < h, from the two case formulas of Step 1-1 (Sec. 3.6)."""
+    t = np.arange(h * h)
+    if k >= 0:
+        return ((t - h * k >= 0) & (t - h * k < h - k)).astype(np.int64)
+    return ((t - (h + k) * h >= -k) & (t - (h + k) * h < h)).astype(np.int64)
+
+
+def diag_zeta(h: int, k: int) -> np.ndarray:
+    """u^zeta_{h*k}, 0 <= k < h: nonzero exactly at the (k + h*i)-th entries (Step 1-2)."""
+    t = np.arange(h * h)
+    return (t % h == k).astype(np.int64)
+
+
+def diag_v(h: int, k: int) -> np.ndarray:
+    """v_k, 1 <= k < h: 1 iff [t]_h < h - k (Step 2)."""
+    t = np.arange(h * h)
+    return ((t % h) < h - k).astype(np.int64)
+
+
+def diag_v_neg(h: int, k: int) -> np.ndarray:
+    """v_{k-h}: 1 iff h - k <= [t]_h < h (Step 2)."""
+    t = np.arange(h * h)
+    return ((t % h) >= h - k).astype(np.int64)
+
+
+def diag_transpose(h: int, s: int) -> np.ndarray:
+    """Diagonal (h-1)*s of U^T, -h < s < h (App. C, reading R4: the printed
+    case i < 0 is wrong; the mask is 1 at t = (h+1)*i + s for
+    max(0,-s) <= i < h - max(0,s))."""
+    t = np.arange(h * h)
+    i = (t - s) // (h + 1)
+    ok = ((t - s) % (h + 1) == 0) & (i >= max(0, -s)) & (i < h - max(0, s))
+    return ok.astype(np.int64)
+
+
+# ----------------------------------------------------------------------------
+# Matrix-product plan: which masks, at which level and scale (readings R2, R3, R7, R9)
+# ----------------------------------------------------------------------------
+
+
+def matmul_variant(limbs: int) -> str:
+    """Alg. 3 needs 3 rescales (masks of Step 1, the Step 2 mask, the ct x ct
+    product); with exactly 2 levels above q_0 the depth-2 rearrangement runs."""
+    if limbs >= 4:
+        return "alg3"
+    if limbs == 3:
+        return "depth2"
+    raise ValueError("HE-MatMult needs at least 3 limbs, got %d" % limbs)
+
+
+def plan_masks(h: int, limbs: int):
+    """Ordered list of (kind, index, logical mask vector, limbs of the
+    ciphertext it multiplies) for one product:
+      mu   : l = -h+1..h-1, vector R(u^mu_l, -b*floor(l/b))            at `limbs`
+      zeta : l = 0..h-1, R(u^zeta_{hl}, -h*b*floor(l/b)) for Alg. 3,
+             u^zeta_{hl} unrotated for the depth-2 variant              at `limbs`
+      v    : k = 1..h-1, R(v_k, -k)                                      at `limbs`-1 (Alg. 3 only)
+    A mask multiplying a ciphertext of l limbs is encoded at scale q_{l-1}."""
+    variant = matmul_variant(limbs)
+    b = baby_steps(h)
+    out = []
+    for l in range(-h + 1, h):
+        out.append(("mu", l, R(diag_mu(h, l), -b * (l // b)), limbs))
+    for l in range(h):
+        if variant == "alg3":
+            out.append(("zeta", l, R(diag_zeta(h, l), -h * b * (l // b)), limbs))
+        else:
+            out.append(("zeta", l, diag_zeta(h, l), limbs))
+    if variant == "alg3":
+        for k in range(1, h):
+            out.append(("v", k, R(diag_v(h, k), -k), limbs - 1))
+    return out
+
+
+def matmul_rotation_steps(h: int, beta: int, limbs: int) -> list:
+    """Every rotation amount one product uses, reduced mod S = beta*h^2
+    (rotations are cyclic on the slots), sorted, without 0."""
+    variant = matmul_variant(limbs)
+    b = baby_steps(h)
+    s = set()
+    for l in range(-h + 1, h):
+        s.add(beta * (l % b))
+        s.add(beta * b * (l // b))
+    if variant == "alg3":
+        for l in range(h):
+            s.add(beta * h * (l % b))
+            s.add(beta * h * b * (l // b))
+        for k in range(1, h):
+            s.update({beta * k, beta * (k - h), beta * h * k})
+    else:
+        for l in range(1, h):
+            s.add(beta * h * l)
+        for k in range(1, h):
+            s.update({beta * k, beta * (k - h), beta * h * k})
+    n_slots = beta * h * h
+    return sorted({k % n_slots for k in s} - {0})
+
+
+class MaskProvider:
+    """Encodes plan masks with the oracle encoder (scale q_{l-1} at l limbs);
+    `coeffs` exposes the signed integer coefficients so a test can hand the
+    very same plaintexts to another implementation."""
+
+    def __init__(self, ctx: C.Context, h: int, limbs: int):
+        self.ctx, self.h, self.limbs = ctx, h, limbs
+        self.beta = ctx.S // (h * h)
+        self.entries = plan_masks(h, limbs)
+        self.index = {(kind, k): i for i, (kind, k, _, _) in enumerate(self.entries)}
+        self._coeffs: dict = {}
+
+    def coeffs(self, i: int) -> np.ndarray:
+        if i not in self._coeffs:
+            kind, k, vec, lm = self.entries[i]
+            self._coeffs[i] = C.encode_real(self.ctx.N, expand(vec, self.beta), float(self.ctx.q[lm - 1]))
+        return self._coeffs[i]
+
+    def plaintext(self, kind: str, k: int):
+        i = self.index[(kind, k)]
+        lm = self.entries[i][3]
+        prim = self.ctx.q[:lm]
+        pt = self.ctx.ntt(self.ctx.signed_to_rows(self.coeffs(i), prim), prim)
+        return pt, float(self.ctx.q[lm - 1])
+
+
+# ----------------------------------------------------------------------------
+# Alg. 2 with baby-step/giant-step (App. B), Alg. 3 and the depth-2 variant
+# ----------------------------------------------------------------------------
+
+
+def lintrans_bsgs(ev: C.Evaluator, ct: C.Ciphertext, ls, stride: int, masks: MaskProvider, kind: str):
+    """HE-LinTrans over diagonals stride*l, l in `ls` (Alg. 2), split as
+    l = b*i + j (App. B): sum_i Rot( sum_j Mul_pt(Rot(ct, stride*j), R(u_l, -stride*b*i)), stride*b*i ).
+    Baby rotations share one ModUp; the result is NOT rescaled."""
+    b = baby_steps(masks.h)
+    beta = masks.beta
+    groups: dict = {}
+    for l in ls:
+        groups.setdefault(l // b, []).append((l % b, l))
+    js = sorted({j for g in groups.values() for j, _ in g})
+    babies = dict(zip(js, ev.rotate_hoisted(ct, [beta * stride * j for j in js])))
+    acc = None
+    for i in sorted(groups):
+        inner = None
+        for j, l in groups[i]:
+            pt, sc = masks.plaintext(kind, l)
+            term = ev.mul_plain(babies[j], pt, sc)
+            inner = term if inner is None else ev.add(inner, term)
+        if i != 0:
+            inner = ev.rotate(inner, beta * stride * b * i)
+        acc = inner if acc is None else ev.add(acc, inner)
+    return acc
+
+
+def matmul(ev: C.Evaluator, A: C.Ciphertext, B: C.Ciphertext, h: int, masks: MaskProvider | None = None):
+    """HE-MatMult of beta = S/h^2 packed pairs (Alg. 3 / App. E)."""
+    if A.limbs != B.limbs:
+        raise ValueError("A and B must be at the same level")
+    masks = masks or MaskProvider(ev.ctx, h, A.limbs)
+    if matmul_variant(A.limbs) == "alg3":
+        return _matmul_alg3(ev, A, B, h, masks)
+    return _matmul_depth2(ev, A, B, h, masks)
+
+
+def _matmul_alg3(ev, A, B, h, masks):
+    beta = masks.beta
+    # Step 1-1 / 1-2: A0 = U^mu a, B0 = U^zeta b
+    A0 = ev.rescale(lintrans_bsgs(ev, A, range(-h + 1, h), 1, masks, "mu"))
+    B0 = ev.rescale(lintrans_bsgs(ev, B, range(h), h, masks, "zeta"))
+    # Step 2 with the multiplexer trick (App. B): with M_k = Mul_pt(A0, R(v_k,-k)),
+    # A^(k) = Rot(M_k, k) + Rot(q*A0 - M_k, k-h); q*A0 is A0 at the mask scale.
+    qt = ev.ctx.q[A0.limbs - 1]
+    A0s = ev.mul_int(A0, qt, new_scale=A0.scale * float(qt))
+    Ak = [ev.drop(A0, A0.limbs - 1)]
+    for k in range(1, h):
+        pt, sc = masks.plaintext("v", k)
+        M = ev.mul_plain(A0, pt, sc)
+        Nk = ev.sub(A0s, M)
+        Ak.append(ev.rescale(ev.add(ev.rotate(M, beta * k), ev.rotate(Nk, beta * (k - h)))))
+    # B^(k) = Rot(B0, h*k): all rotations of one ciphertext, hoisted
+    B0d = ev.drop(B0, B0.limbs - 1)
+    Bk = [B0d] + ev.rotate_hoisted(B0d, [beta * h * k for k in range(1, h)])
+    # Step 3: sum_k A^(k) (x) B^(k), one relinearisation and one rescale (reading R10)
+    acc = ev.tensor(Ak[0], Bk[0])
+    for k in range(1, h):
+        acc = ev.add(acc, ev.tensor(Ak[k], Bk[k]))
+    return ev.rescale(ev.relinearize(acc))
+
+
+def _matmul_depth2(ev, A, B, h, masks):
+    """Reading R9: with T_l = u^zeta_{hl} . R(b, hl) and S_m = sum_{l<m} T_l,
+    v_k . R(B0, hk) = R(S_{h-k}, hk) and v_{k-h} . R(B0, hk) = R(B0 - S_{h-k}, hk),
+    so A.B = A0.B0 + sum_{k>=1} R(A0,k).R(S_{h-k},hk) + R(A0,k-h).R(B0-S_{h-k},hk)
+    needs one level for the masks and one for the ct x ct products."""
+    beta = masks.beta
+    A0 = ev.rescale(lintrans_bsgs(ev, A, range(-h + 1, h), 1, masks, "mu"))
+    Rb = [B] + ev.rotate_hoisted(B, [beta * h * l for l in range(1, h)])
+    T = []
+    for l in range(h):
+        pt, sc = masks.plaintext("zeta", l)
+        T.append(ev.mul_plain(Rb[l], pt, sc))
+    prefix = [None, T[0]]          # prefix[m] = S_m
+    for l in range(1, h):
+        prefix.append(ev.add(prefix[-1], T[l]))
+    Bfull = prefix[h]
+    B0 = ev.rescale(Bfull)
+    RA = ev.rotate_hoisted(A0, [beta * k for k in range(1, h)] + [beta * (k - h) for k in range(1, h)])
+    acc = ev.tensor(A0, B0)
+    for k in range(1, h):
+        X = ev.rescale(prefix[h - k])
+        Y = ev.rescale(ev.sub(Bfull, prefix[h - k]))
+        acc = ev.add(acc, ev.tensor(RA[k - 1], ev.rotate(X, beta * h * k)))
+        acc = ev.add(acc, ev.tensor(RA[h - 1 + k - 1], ev.rotate(Y, beta * h * k)))
+    return ev.rescale(ev.relinearize(acc))
+
+
+# ----------------------------------------------------------------------------
+# FP64 slot-space model of the same schedules (no encryption; pins Eq. (2))
+# ----------------------------------------------------------------------------
+
+
+def slot_matmul(a: np.ndarray, b: np.ndarray, h: int, beta: int = 1, variant: str = "alg3") -> np.ndarray:
+    """Runs the masks and rotations of `matmul` on plain slot vectors."""
+    n = beta * h * h
+    Rb_ = lambda v, k: np.roll(v, -(beta * k) % n)
+    bb = baby_steps(h)
+    A0 = np.zeros(n)
+    for l in range(-h + 1, h):
+        i, j = l // bb, l % bb
+        A0 += Rb_(expand(R(diag_mu(h, l), -bb * i), beta) * Rb_(a, j), bb * i)
+    if variant == "alg3":
+        B0 = np.zeros(n)
+        for l in range(h):
+            i, j = l // bb, l % bb
+            B0 += Rb_(expand(R(diag_zeta(h, l), -h * bb * i), beta) * Rb_(b, h * j), h * bb * i)
+        out = A0 * B0
+        for k in range(1, h):
+            M = A0 * expand(R(diag_v(h, k), -k), beta)
+            Ak = Rb_(M, k) + Rb_(A0 - M, k - h)
+            out += Ak * Rb_(B0, h * k)
+        return out
+    T = [expand(diag_zeta(h, l), beta) * Rb_(b, h * l) for l in range(h)]
+    Sm = np.cumsum(np.vstack([np.zeros(n)] + T), axis=0)
+    out = A0 * Sm[h]
+    for k in range(1, h):
+        out += Rb_(A0, k) * Rb_(Sm[h - k], h * k) + Rb_(A0, k - h) * Rb_(Sm[h] - Sm[h - k], h * k)
+    return out
+
+
+def slot_transpose(a: np.ndarray, h: int, beta: int = 1) -> np.ndarray:
+    n = beta * h * h
+    out = np.zeros(n)
+    for s in range(-h + 1, h):
+        out += expand(diag_transpose(h, s), beta) * np.roll(a, -(beta * (h - 1) * s) % n)
+    return out
+
+
+def transpose(ev: C.Evaluator, ct: C.Ciphertext, h: int):
+    """App. C: U^T a = sum_s t_{(h-1)s} . R(a, (h-1)s), 2h-1 diagonals, with
+    the baby-step/giant-step split on s; masks encoded here at scale q_{l-1}."""
+    ctx = ev.ctx
+    beta = ctx.S // (h * h)
+    b = baby_steps(h)
+    sc = float(ctx.q[ct.limbs - 1])
+    prim = ctx.q[: ct.limbs]
+
+    class _M:
+        pass
+
+    m = _M()
+    m.h, m.beta = h, beta
+
+    def plaintext(kind, s):
+        vec = R(diag_transpose(h, s), -(h - 1) * b * (s // b))
+        c = C.encode_real(ctx.N, expand(vec, beta), sc)
+        return ctx.ntt(ctx.signed_to_rows(c, prim), prim), sc
+
+    m.plaintext = plaintext
+    return ev.rescale(lintrans_bsgs(ev, ct, range(-h + 1, h), h - 1, m, "T"))
+
+
+# ----------------------------------------------------------------------------
+# Sec. 4: g_d, p_d, composite sign, AppMax / ReLU (Alg. 5; readings R8, R17)
+# ----------------------------------------------------------------------------
+
+
+def g_coeffs(d: int) -> list:
+    """Coefficients (Fractions) of m^1, m^3, ..., m^(2d+1) in
+    g_d(m) = sum_{i=0}^{d} 4^-i C(2i,i) m (1-m^2)^i."""
+    c = [Fraction(0)] * (d + 1)
+    for i in range(d + 1):
+        w = Fraction(math.comb(2 * i, i), 4 ** i)
+        for j in range(i + 1):  # (1-m^2)^i = sum_j C(i,j) (-m^2)^j
+            c[j] += w * math.comb(i, j) * (-1) ** j
+    return c
+
+
+def g_int_coeffs(d: int) -> list:
+    """The same coefficients as integers n_j with g_d = sum_j n_j m^(2j+1) / 2^(2d-1)."""
+    den = 2 ** (2 * d - 1)
+    out = []
+    for f in g_coeffs(d):
+        v = f * den
+        assert v.denominator == 1
+        out.append(int(v))
+    return out
+
+
+def p_d(d: int) -> Fraction:
+    """p_d = (2d+1)/4^d * C(2d, d) (Lemma 3.1)."""
+    return Fraction(2 * d + 1, 4 ** d) * math.comb(2 * d, d)
+
+
+def g_eval(d: int, m):
+    """FP64 g_d(m) with the integer coefficients (Horner in m^2)."""
+    n = g_int_coeffs(d)
+    y = np.asarray(m, dtype=np.float64) ** 2
+    acc = np.zeros_like(y) + n[-1]
+    for c in reversed(n[:-1]):
+        acc = acc * y + c
+    return np.asarray(m) * acc / 2.0 ** (2 * d - 1)
+
+
+def g_iter(d: int, k: int, m):
+    for _ in range(k):
+        m = g_eval(d, m)
+    return m
+
+
+def _rha(x: float) -> int:
+    return int(C.round_half_away(np.array([x]))[0])
+
+
+def level_adjust(ev: C.Evaluator, ct: C.Ciphertext, target: int, c_real: float, target_scale: float):
+    """Brings ct to `target` limbs at scale `target_scale`, multiplying its
+    message by c_real: drop to target+1 limbs, multiply by the integer
+    C = round(c_real * target_scale * q_target / scale), rescale by q_target.
+    The result's scale is declared to be target_scale (the integer rounding
+    of C changes the message by a relative 2^-(bits of C))."""
+    if ct.limbs <= target:
+        raise ValueError("cannot raise the level")
+    x = ev.drop(ct, target + 1) if ct.limbs > target + 1 else ct
+    qt = ev.ctx.q[target]
+    c = _rha(c_real * target_scale * float(qt) / ct.scale)
+    ev._count("Mul_const")
+    y = ev.rescale(ev.mul_int(x, c))
+    y.scale = target_scale
+    return y
+
+
+def _square_rs(ev, a, b):
+    return ev.rescale(ev.relinearize(ev.tensor(a, b)))
+
+
+def eval_g(ev: C.Evaluator, x: C.Ciphertext, d: int) -> C.Ciphertext:
+    """One application of g_d on a ciphertext (reading R8): y^j = powers of
+    y = x^2 by squaring (even j) or y^(j-1)*y (odd j), the linear combination
+    P(y) = sum_j n_j y^j with integer n_j at the deepest level, then x*P(y)
+    with the 2^-(2d-1) folded into the level adjustment of x.  Ciphertexts of
+    equal level carry equal scales because every product is of two operands of
+    one level and scale."""
+    n = g_int_coeffs(d)
+    y = {1: _square_rs(ev, x, x)}
+    for j in range(2, d + 1):
+        if j % 2 == 0:
+            y[j] = _square_rs(ev, y[j // 2], y[j // 2])
+        else:
+            a = y[j - 1]
+            y1 = level_adjust(ev, y[1], a.limbs, 1.0, a.scale) if y[1].limbs > a.limbs else y[1]
+            y[j] = _square_rs(ev, a, y1)
+    lp = min(v.limbs for v in y.values())
+    sp = next(v.scale for v in y.values() if v.limbs == lp)
+    terms = []
+    for j in range(1, d + 1):
+        if y[j].limbs > lp:
+            terms.append(level_adjust(ev, y[j], lp, float(n[j]), sp))
+        else:
+            terms.append(ev.mul_int(y[j], n[j]))
+    P = terms[0]
+    for t in terms[1:]:
+        P = ev.add(P, t)
+    P = ev.add_const(P, float(n[0]))
+    xa = level_adjust(ev, x, lp, 1.0 / 2 ** (2 * d - 1), sp)
+    return _square_rs(ev, xa, P)
+
+
+def g_depth(d: int) -> int:
+    """Levels one application of eval_g consumes."""
+    lev = {1: 1}
+    for j in range(2, d + 1):
+        lev[j] = (lev[j // 2] + 1) if j % 2 == 0 else max(lev[j - 1], lev[1]) + 1
+    return max(lev.values()) + 1
+
+
+def refresh(ev: C.Evaluator, ct: C.Ciphertext, seed: int, counter: int, index: int = 0) -> C.Ciphertext:
+    """Host simulation of DBootstrap (Fig. 1 item 14, reading R17): collective
+    decryption to integer coefficients, rescaling of those integers to the
+    default scale, re-encryption at the top level."""
+    ctx = ev.ctx
+    poly = C.decrypt_poly(ctx, ev.ks, ct)
+    ratio = ctx.scale / ct.scale
+    m = C.round_half_away(poly.astype(np.float64) * ratio).astype(np.int64)
+    ev._count("Refresh")
+    return C.encrypt_coeffs(ctx, ev.ks, m, ctx.scale, ctx.n_q, seed, tag=1 + counter, index=index)
+
+
+def sign_approx(ev: C.Evaluator, x: C.Ciphertext, d: int, k: int, relu: bool = False,
+                refresh_seed: int | None = None, index: int = 0) -> C.Ciphertext:
+    """g_d^(k)(x) (Sec. 4.2) or ReLU(x) = x (1 + g_d^(k)(x)) / 2 (Sec. 4.4).
+    Before a composition whose depth (plus the final ReLU product) no longer
+    fits, the ciphertext is refreshed if a refresh seed is given."""
+    dg = g_depth(d)
+    m = x
+    refreshes = 0
+    for it in range(k):
+        need = dg + (1 if (relu and it == k - 1) else 0)
+        if m.limbs - 1 < need:
+            if refresh_seed is None:
+                raise ValueError("levels exhausted")
+            m = refresh(ev, m, refresh_seed, refreshes, index)
+            refreshes += 1
+        m = eval_g(ev, m, d)
+    if not relu:
+        return m
+    s1 = ev.add_const(m, 1.0)
+    xa = level_adjust(ev, x, m.limbs, 0.5, m.scale)
+    return _square_rs(ev, xa, s1)

@@ -1,0 +1,146 @@
+"""Pins of the oracle's CKKS layer: encoding against the canonical-embedding
+definition, encryption round trips within the noise bound, homomorphic ops
+against plaintext arithmetic, rescale against exact integer rounding."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ckks as C
+
+
+def test_splitmix64_published_first_outputs():
+    # SplitMix64 started from state 0 (Steele, Lea & Flood; Vigna's reference code)
+    st, outs = 0, []
+    for _ in range(3):
+        st = (st + C.GAMMA) & C.M64
+        outs.append(C.mix64(st))
+    assert outs == [0xE220A8397B1DCDAF, 0x6E789E6AA1B965F4, 0x06C45D188009454F]
+    s = C.Stream(5, 1, 2, 3)
+    a = s.draws(4)
+    s2 = C.Stream(5, 1, 2, 3)
+    b = np.concatenate([s2.draws(1), s2.draws(3)])
+    assert np.array_equal(a, b)
+
+
+def test_samplers():
+    n = 1 << 16
+    t = C.sample_ternary(C.Stream(1, C.PURPOSE_SK), n)
+    assert set(np.unique(t)) == {-1, 0, 1}
+    assert all(abs(np.mean(t == v) - 1 / 3) < 0.01 for v in (-1, 0, 1))
+    g = C.sample_gaussian(C.Stream(1, C.PURPOSE_PK_E), n, 3.2)
+    assert abs(np.std(g) - 3.2) < 0.05 and abs(np.mean(g)) < 0.05 and np.abs(g).max() <= 19
+    q = (1 << 45) - 12345
+    u = C.sample_uniform(C.Stream(2, C.PURPOSE_KEY_A), q, n)
+    assert u.max() < q and abs(np.mean(u.astype(np.float64)) / q - 0.5) < 0.01
+    # rejection consumes exactly the draws up to the last accepted one
+    s = C.Stream(3, C.PURPOSE_KEY_A)
+    C.sample_uniform(s, 11, 100)
+    raw = C.Stream(3, C.PURPOSE_KEY_A).draws(s.count) & np.uint64(15)
+    assert int((raw < 11).sum()) == 100 and int(raw[-1]) < 11
+
+
+@pytest.mark.parametrize("log_n", [5, 8])
+def test_encoding_matches_definition(log_n):
+    n = 1 << log_n
+    rng = np.random.default_rng(log_n)
+    z = rng.uniform(-1, 1, n // 2)
+    a = C.encode_real(n, z, 2.0 ** 30)
+    b = C.encode_direct(n, z, 2.0 ** 30)
+    assert np.abs(a - b).max() <= 1
+    # evaluating the integer polynomial at zeta^(5^j) (numpy polyval) gives back the slots
+    zeta = np.exp(1j * np.pi / n)
+    for j in range(n // 2):
+        x = zeta ** pow(5, j, 2 * n)
+        v = np.polyval(a[::-1].astype(np.float64), x) / 2.0 ** 30
+        assert abs(v - z[j]) < 2 ** -20
+    dec = C.decode(n, a, 2.0 ** 30).real
+    assert np.abs(dec - z).max() < 2 ** -20
+
+
+def test_encode_decode_precision_at_2_40():
+    n = 1 << 12
+    z = np.random.default_rng(0).uniform(-1, 1, n // 2)
+    assert np.abs(C.decode(n, C.encode_real(n, z, 2.0 ** 40), 2.0 ** 40).real - z).max() < 2 ** -30
+
+
+@pytest.fixture(scope="module")
+def small():
+    ctx = C.Context(10, [60, 40, 40, 40], [60, 60], 40)
+    ks = C.keygen(ctx, 3, 7, rot_steps=[1, 5, -3])
+    return ctx, ks
+
+
+def test_encrypt_decrypt_roundtrip_within_noise_bound(small):
+    ctx, ks = small
+    z = np.random.default_rng(1).uniform(-1, 1, ctx.S)
+    ct = C.encrypt(ctx, ks, z, seed=3)
+    # fresh noise v*e + e0 + e1*s: |coeff| <~ 6 sigma (1 + 2 n_parties sqrt(N)); slots add sqrt(N)
+    bound = 6 * ctx.sigma * (1 + 2 * 3 * math.sqrt(ctx.N)) * math.sqrt(ctx.N) / ctx.scale
+    assert np.abs(C.decrypt(ctx, ks, ct) - z).max() < bound
+    # the q_0-only decryption equals the full CRT decryption (the plaintext is far below q_0/2)
+    full = C.decrypt_crt(ctx, ks, ct)
+    assert [int(v) for v in C.decrypt_poly(ctx, ks, ct)] == full
+
+
+def test_homomorphic_ops(small):
+    ctx, ks = small
+    rng = np.random.default_rng(2)
+    z, w = rng.uniform(-1, 1, ctx.S), rng.uniform(-1, 1, ctx.S)
+    a, b = C.encrypt(ctx, ks, z, 4), C.encrypt(ctx, ks, w, 5)
+    ev = C.Evaluator(ctx, ks)
+    tol = 2 ** -20
+    assert np.abs(C.decrypt(ctx, ks, ev.add(a, b)) - (z + w)).max() < tol
+    assert np.abs(C.decrypt(ctx, ks, ev.sub(a, b)) - (z - w)).max() < tol
+    m = ev.rescale(ev.mul_relin(a, b))
+    assert m.limbs == 3 and np.abs(C.decrypt(ctx, ks, m) - z * w).max() < tol
+    for k in (1, 5, -3):
+        r = ev.rotate(a, k)
+        assert np.abs(C.decrypt(ctx, ks, r) - np.roll(z, -k)).max() < tol
+    hs = ev.rotate_hoisted(a, [1, 5, -3, 0])
+    for k, r in zip([1, 5, -3, 0], hs):
+        assert np.abs(C.decrypt(ctx, ks, r) - np.roll(z, -k)).max() < tol
+    pt = C.encode_real(ctx.N, w, float(ctx.q[3]))
+    ptn = ctx.ntt(ctx.signed_to_rows(pt, ctx.q), ctx.q)
+    mp = ev.rescale(ev.mul_plain(a, ptn, float(ctx.q[3])))
+    assert mp.scale == ctx.scale and np.abs(C.decrypt(ctx, ks, mp) - z * w).max() < tol
+    assert np.abs(C.decrypt(ctx, ks, ev.add_const(a, 0.25)) - (z + 0.25)).max() < tol
+    assert np.abs(C.decrypt(ctx, ks, ev.mul_int(a, -3)) - (-3 * z)).max() < tol
+
+
+def test_rescale_is_exact_rounded_division(small):
+    ctx, ks = small
+    ev = C.Evaluator(ctx, ks)
+    ct = C.encrypt(ctx, ks, np.ones(4), 9)
+    out = ev.rescale(ct)
+    Q, Qp = math.prod(ctx.q), math.prod(ctx.q[:3])
+    qt = ctx.q[3]
+    for comp in range(2):
+        X = ctx.intt(ct.c[comp], ctx.q)
+        Y = ctx.intt(out.c[comp], ctx.q[:3])
+        for c in range(0, ctx.N, 37):
+            x = sum(int(X[r, c]) * (Q // t) * pow(Q // t, -1, t) for r, t in enumerate(ctx.q)) % Q
+            y = sum(int(Y[r, c]) * (Qp // t) * pow(Qp // t, -1, t) for r, t in enumerate(ctx.q[:3])) % Qp
+            assert y == ((x + qt // 2) // qt) % Qp
+    assert out.scale == ct.scale / qt
+
+
+def test_keyswitch_decrypts_to_product_with_target_key(small):
+    ctx, ks = small
+    ev = C.Evaluator(ctx, ks)
+    rng = np.random.default_rng(4)
+    limbs = 4
+    d = np.stack([rng.integers(0, q, ctx.N, dtype=np.uint64) for q in ctx.q])
+    k0, k1 = ev.keyswitch(d, ks.relin, limbs)
+    s2 = ctx.mul(ks.s_ntt[:limbs], ks.s_ntt[:limbs], ctx.q)
+    lhs = ctx.add(k0, ctx.mul(k1, ks.s_ntt[:limbs], ctx.q), ctx.q)
+    rhs = ctx.mul(d, s2, ctx.q)
+    diff = ctx.intt(ctx.sub(lhs, rhs, ctx.q), ctx.q)
+    # the key-switching error is small: dnum * N * sigma * q_max / P plus the ModDown rounding
+    bound = ctx.dnum * ctx.N * 20 * max(ctx.q) // ctx.P + ctx.N * 4
+    for r, q in enumerate(ctx.q):
+        err = [int(v) if int(v) <= q // 2 else int(v) - q for v in diff[r]]
+        assert max(abs(e) for e in err) < bound
+        if r:  # one small integer polynomial, seen identically modulo every prime
+            assert err == err0
+        err0 = err
