@@ -1,0 +1,209 @@
+/*
+ * hx -- GB300-native RNS-CKKS evaluation for the Hercules packed matrix
+ * product and composite-polynomial sign/ReLU (arXiv 2207.04620).
+ *
+ * C ABI.  Plain pointers and sizes only.  All handles are opaque and owned
+ * by the library; free them with the matching *_destroy.  Functions return
+ * HX_OK (0) or a negative hx_status; on error no output handle is produced
+ * (*out stays NULL) and hx_last_error() describes the failure (thread-local
+ * string, valid until the next call on the same thread).
+ *
+ * Streams: a `void* stream` argument is a cudaStream_t (NULL = legacy default
+ * stream).  Device work is enqueued on it; results held in handles are valid
+ * once that stream has completed.  Host buffers passed in are borrowed for the
+ * duration of the call only.
+ *
+ * Ciphertexts live in device memory, limb-major: component c, limb l,
+ * coefficient slot j at word (c*limbs + l)*N + j, every limb in the NTT
+ * (evaluation) representation: slot j of limb l holds a(psi_l^(2 brv(j)+1))
+ * mod q_l.  Limb l of a ciphertext with `limbs` limbs is modulo q_l; the
+ * special primes p_k follow the Q primes in every prime list.
+ *
+ * Paper references: Fig. 1 (the MCKKS API, Sec. 2.2) defines SecKeyGen,
+ * DKeyGen, Ecd/Dcd, Enc, DDec, Add, Sub, Mul_pt, Mul_ct, Rot, RS; Alg. 2/3,
+ * Eqs. (5)-(16), App. B and App. E define the packed h x h product; Sec. 4
+ * and Alg. 5 define g_d, its k-fold composition and ReLU.
+ */
+#ifndef HX_H
+#define HX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int hx_status;
+#define HX_OK 0
+#define HX_EINVAL (-1)   /* bad argument, shape or parameter */
+#define HX_ENOMEM (-2)   /* device allocation failed or HBM budget exceeded */
+#define HX_ELEVEL (-3)   /* not enough levels (limbs) left for the operation */
+#define HX_ESCALE (-4)   /* operands' scales or levels do not match */
+#define HX_EKEY (-5)     /* a needed rotation or relinearisation key is missing */
+#define HX_ETIMEOUT (-6) /* a bounded device wait gave up */
+#define HX_ECUDA (-7)    /* a CUDA runtime call failed */
+#define HX_EPARTY (-8)   /* a party's share is missing in a collective step */
+
+#define HX_MAX_Q 60
+#define HX_MAX_P 6
+
+typedef struct hx_context hx_context;
+typedef struct hx_keyset hx_keyset;
+typedef struct hx_ct hx_ct;
+typedef struct hx_matmul_plan hx_matmul_plan;
+
+/* Parameters (Sec. 2.2: R_Q = Z_Q[X]/(X^N+1), Q = q_0...q_{L-1}).
+ * log_n in [10, 17]; n_q Q primes of q_bits[i] bits (q_0 first), n_p special
+ * primes of p_bits[k] bits (hybrid key switching, digits of n_p primes);
+ * every size in [20, 61].  Primes: for each size in this order, the largest
+ * prime below 2^bits that is 1 mod 2N and not yet chosen.  Default encoding
+ * scale 2^log2_scale; error sampler width sigma (discrete Gaussian on
+ * [-floor(6 sigma), floor(6 sigma)]). */
+typedef struct hx_params {
+    int log_n;
+    int n_q;
+    int q_bits[HX_MAX_Q];
+    int n_p;
+    int p_bits[HX_MAX_P];
+    double log2_scale;
+    double sigma;
+} hx_params;
+
+const char *hx_last_error(void);
+
+/* ---- context -------------------------------------------------------------- */
+/* Builds primes, roots, NTT twiddles and RNS conversion tables on the current
+ * CUDA device.  Returns HX_EINVAL for unsupported parameters. */
+hx_status hx_context_create(const hx_params *p, hx_context **out);
+void hx_context_destroy(hx_context *ctx);
+/* Writes the n_q + n_p primes (Q then P) to out[0..cap); returns the count or
+ * a negative status. */
+int hx_context_primes(const hx_context *ctx, uint64_t *out, int cap);
+/* ring degree N */
+int hx_context_n(const hx_context *ctx);
+
+/* ---- keys (Fig. 1 items 1-2; host-side toy-scale multiparty) -------------- */
+/* SecKeyGen for n_parties simulated parties (ternary shares), DKeyGen of the
+ * collective public key for s = sum of shares, the relinearisation key and
+ * one Galois key per entry of rot_steps (rotation by k slots to the left,
+ * i.e. R(m, k) of Sec. 3.2; k is taken mod N/2).  Randomness: SplitMix64
+ * streams derived from `seed`.  Evaluation keys are uploaded to HBM. */
+hx_status hx_keygen(hx_context *ctx, int n_parties, uint64_t seed, const int32_t *rot_steps, size_t n_steps,
+                    hx_keyset **out);
+/* Adds Galois keys for more rotation steps (no-op for present ones). */
+hx_status hx_keyset_add_rotations(hx_context *ctx, hx_keyset *ks, const int32_t *rot_steps, size_t n_steps);
+/* Exports a switching key (galois = 0: relinearisation key) in the library's
+ * canonical layout [dnum][2 (b, a)][n_q + n_p][N] (NTT form, standard
+ * residues) into host memory; returns words written or a negative status. */
+int64_t hx_keyset_export_switch_key(const hx_keyset *ks, uint64_t galois, uint64_t *host, size_t cap);
+/* Exports the public key [2 (b, a)][n_q][N]. */
+int64_t hx_keyset_export_public_key(const hx_keyset *ks, uint64_t *host, size_t cap);
+void hx_keyset_destroy(hx_keyset *ks);
+
+/* ---- encoding / encryption / decryption (Fig. 1 items 3-6) ---------------- */
+/* Ecd: n <= N/2 real slots -> N signed integer coefficients at `scale`
+ * (canonical embedding, slot j at zeta^(5^j), rounding half away from zero). */
+hx_status hx_encode(const hx_context *ctx, const double *slots, size_t n, double scale, int64_t *coeffs);
+/* Enc(pk, Ecd(slots)) at `limbs` limbs (0 = all Q primes), default scale. */
+hx_status hx_encrypt(hx_context *ctx, const hx_keyset *ks, const double *slots, size_t n, int limbs, uint64_t seed,
+                     hx_ct **out);
+/* Enc(pk, m) for N signed integer coefficients m at `scale`; tag/index select
+ * the SplitMix64 streams of the encryption randomness. */
+hx_status hx_encrypt_coeffs(hx_context *ctx, const hx_keyset *ks, const int64_t *coeffs, double scale, int limbs,
+                            uint64_t seed, uint32_t tag, uint32_t index, hx_ct **out);
+/* DDec: every simulated party's share c1*s_i is computed on the device, the
+ * shares are summed with c0 on the host modulo q_0 and decoded (Dcd).  Writes
+ * min(n, N/2) real slots. */
+hx_status hx_decrypt(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, double *slots, size_t n);
+/* The same collective decryption stopped before decoding: N centered integer
+ * coefficients of c0 + c1*s mod q_0. */
+hx_status hx_decrypt_coeffs(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, int64_t *coeffs);
+
+/* ---- ciphertext handles ---------------------------------------------------- */
+/* Import residues [comps][limbs][N] (NTT form) from host memory. */
+hx_status hx_ct_import(hx_context *ctx, const uint64_t *host, int comps, int limbs, double scale, hx_ct **out);
+/* Export residues [comps][limbs][N]; returns words written or a negative status. */
+int64_t hx_ct_export(const hx_ct *ct, uint64_t *host, size_t cap);
+hx_status hx_ct_info(const hx_ct *ct, int *comps, int *limbs, double *scale);
+void hx_ct_destroy(hx_ct *ct);
+
+/* ---- single operations on handles (Fig. 1 items 7-12) ----------------------- */
+/* Add/Sub need equal limbs and scales within a relative 2^-20 (else
+ * HX_ESCALE); the output scale is a's. */
+hx_status hx_add(hx_context *ctx, const hx_ct *a, const hx_ct *b, hx_ct **out, void *stream);
+hx_status hx_sub(hx_context *ctx, const hx_ct *a, const hx_ct *b, hx_ct **out, void *stream);
+/* Mul_pt with the plaintext of N signed coefficients pt encoded at pt_scale. */
+hx_status hx_mul_plain(hx_context *ctx, const hx_ct *a, const int64_t *pt, double pt_scale, hx_ct **out,
+                       void *stream);
+/* multiplication by an integer constant; new_scale <= 0 keeps the scale */
+hx_status hx_mul_int(hx_context *ctx, const hx_ct *a, int64_t c, double new_scale, hx_ct **out, void *stream);
+/* adds the constant round(value * scale) to every slot */
+hx_status hx_add_const(hx_context *ctx, const hx_ct *a, double value, hx_ct **out, void *stream);
+/* Mul_ct without relinearisation: 3 components (d0, d1, d2). */
+hx_status hx_tensor(hx_context *ctx, const hx_ct *a, const hx_ct *b, hx_ct **out, void *stream);
+/* 3 components -> 2 by hybrid key switching of d2 with the relinearisation key. */
+hx_status hx_relinearize(hx_context *ctx, const hx_keyset *ks, const hx_ct *d, hx_ct **out, void *stream);
+/* RS: divide by the top prime with rounding to nearest and drop it. */
+hx_status hx_rescale(hx_context *ctx, const hx_ct *a, hx_ct **out, void *stream);
+/* discard the top limbs down to `limbs` (exact) */
+hx_status hx_drop(hx_context *ctx, const hx_ct *a, int limbs, hx_ct **out, void *stream);
+/* Rot(a, k): slots move left by k (R(m, k)); HX_EKEY without the Galois key. */
+hx_status hx_rotate(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, int32_t k, hx_ct **out, void *stream);
+/* n rotations of one ciphertext sharing a single ModUp of c1 (hoisting). */
+hx_status hx_rotate_hoisted(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, const int32_t *steps, int n,
+                            hx_ct **outs, void *stream);
+
+/* ---- raw kernels on caller device buffers (for parity tests and benches) --- */
+/* In-place forward (inverse != 0: inverse) negacyclic NTT of n_polys
+ * polynomials laid out [n_polys][limbs][N] in device memory; limb l is taken
+ * modulo prime index prime_idx[l] (host array; index into Q then P). */
+hx_status hx_ntt(hx_context *ctx, uint64_t *dev, int n_polys, int limbs, const int32_t *prime_idx, int inverse,
+                 void *stream);
+
+/* ---- HE-MatMult (Alg. 3 with App. B and App. E) ----------------------------- */
+/* A plan fixes h (a power of two, h*h <= N/2, beta = (N/2)/h^2 products per
+ * ciphertext pair) and the input level.  limbs >= 4 runs Alg. 3; limbs == 3
+ * runs the depth-2 rearrangement; fewer returns HX_ELEVEL.  Its diagonal
+ * masks are encoded by the library; hx_matmul_plan_set_mask replaces mask i
+ * (in the plan's documented order: mu diagonals l = -h+1..h-1, zeta diagonals
+ * l = 0..h-1, then for Alg. 3 the v_k masks k = 1..h-1) by N signed integer
+ * coefficients. */
+hx_status hx_matmul_plan_create(hx_context *ctx, int h, int limbs, hx_matmul_plan **out);
+int hx_matmul_plan_num_masks(const hx_matmul_plan *plan);
+hx_status hx_matmul_plan_set_mask(hx_context *ctx, hx_matmul_plan *plan, int i, const int64_t *coeffs);
+void hx_matmul_plan_destroy(hx_matmul_plan *plan);
+/* Rotation steps (mod N/2, sorted, no 0) a product of this shape uses;
+ * returns the count (writes at most cap) or a negative status. */
+int hx_matmul_rotation_steps(const hx_context *ctx, int h, int limbs, int32_t *out, int cap);
+/* One product: out = A x B for each of the beta packed pairs. */
+hx_status hx_matmul(hx_context *ctx, const hx_keyset *ks, const hx_ct *A, const hx_ct *B, int h, hx_ct **out,
+                    void *stream);
+/* `count` independent products through one batched schedule (every kernel
+ * launch covers the whole batch; key reads are shared).  plan may be NULL
+ * (library masks for the inputs' level). */
+hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *A,
+                          const hx_ct *const *B, int h, size_t count, hx_ct **out, void *stream);
+
+/* ---- sign / ReLU (Sec. 4, Alg. 5) ------------------------------------------ */
+/* g_d^(k)(x) (relu = 0) or ReLU(x) = x (1 + g_d^(k)(x)) / 2 (relu = 1), d in
+ * [1, 4].  When the next composition no longer fits in the remaining levels,
+ * the ciphertext is refreshed by a host-simulated DBootstrap (collective
+ * decryption and re-encryption at the top level, randomness from
+ * refresh_seed) if allow_refresh != 0, else HX_ELEVEL. */
+hx_status hx_sign_approx(hx_context *ctx, const hx_keyset *ks, const hx_ct *x, int d, int k, int relu,
+                         int allow_refresh, uint64_t refresh_seed, hx_ct **out, void *stream);
+hx_status hx_sign_approx_batch(hx_context *ctx, const hx_keyset *ks, const hx_ct *const *x, size_t count, int d,
+                               int k, int relu, int allow_refresh, uint64_t refresh_seed, hx_ct **out, void *stream);
+
+/* ---- counters -------------------------------------------------------------- */
+/* Operation counters since the last reset, in this order: Add, Mul_pt,
+ * Rot (full), Rot (hoisted), Mul_ct, KeySwitch, ModUp, Rescale, Refresh,
+ * kernel launches.  Returns the number of counters. */
+int hx_counters(const hx_context *ctx, uint64_t *out, int cap);
+void hx_counters_reset(hx_context *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,501 @@
+// extern "C" entry points of include/hx.h: argument checks, handle management
+// and error translation around the runtime.
+#include <cstring>
+#include <new>
+#include <stdexcept>
+
+#include "runtime.h"
+
+using namespace hx;
+
+namespace {
+
+thread_local std::string g_err;
+
+#define HX_TRY try {
+#define HX_END                                                                                                     \
+    }                                                                                                              \
+    catch (const hx::Error &e)                                                                                     \
+    {                                                                                                              \
+        g_err = e.msg;                                                                                             \
+        return e.code;                                                                                             \
+    }                                                                                                              \
+    catch (const std::bad_alloc &)                                                                                 \
+    {                                                                                                              \
+        g_err = "host allocation failed";                                                                          \
+        return HX_ENOMEM;                                                                                          \
+    }                                                                                                              \
+    catch (const std::exception &e)                                                                                \
+    {                                                                                                              \
+        g_err = e.what();                                                                                          \
+        return HX_EINVAL;                                                                                          \
+    }
+
+cudaStream_t S(void *s) { return reinterpret_cast<cudaStream_t>(s); }
+
+hx_ct *wrap(hx_context *ctx, const Cts &c)
+{
+    hx_ct *h = new hx_ct;
+    h->ctx = ctx;
+    h->c = c;
+    return h;
+}
+
+void need(bool c, const char *msg)
+{
+    if (!c) throw hx::Error{HX_EINVAL, msg};
+}
+
+} // namespace
+
+namespace hx {
+void set_error(const std::string &msg) { g_err = msg; }
+} // namespace hx
+
+extern "C" {
+
+const char *hx_last_error(void) { return g_err.c_str(); }
+
+hx_status hx_context_create(const hx_params *p, hx_context **out)
+{
+    HX_TRY
+    need(p && out, "null argument");
+    *out = nullptr;
+    std::unique_ptr<hx_context> c(new hx_context);
+    build_context(*c, *p);
+    *out = c.release();
+    return HX_OK;
+    HX_END
+}
+
+void hx_context_destroy(hx_context *ctx)
+{
+    if (!ctx) return;
+    destroy_context(*ctx);
+    delete ctx;
+}
+
+int hx_context_primes(const hx_context *ctx, uint64_t *out, int cap)
+{
+    if (!ctx || (!out && cap > 0)) return HX_EINVAL;
+    for (int i = 0; i < ctx->n_all && i < cap; i++) out[i] = ctx->primes[i];
+    return ctx->n_all;
+}
+
+int hx_context_n(const hx_context *ctx) { return ctx ? ctx->N : HX_EINVAL; }
+
+hx_status hx_keygen(hx_context *ctx, int n_parties, uint64_t seed, const int32_t *rot_steps, size_t n_steps,
+                    hx_keyset **out)
+{
+    HX_TRY
+    need(ctx && out && (rot_steps || n_steps == 0), "null argument");
+    *out = nullptr;
+    std::unique_ptr<hx_keyset> ks(new hx_keyset);
+    keygen(*ctx, *ks, n_parties, seed, nullptr);
+    std::vector<int64_t> st(rot_steps, rot_steps + n_steps);
+    add_rotation_keys(*ctx, *ks, st, nullptr);
+    *out = ks.release();
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_keyset_add_rotations(hx_context *ctx, hx_keyset *ks, const int32_t *rot_steps, size_t n_steps)
+{
+    HX_TRY
+    need(ctx && ks && (rot_steps || n_steps == 0), "null argument");
+    std::vector<int64_t> st(rot_steps, rot_steps + n_steps);
+    add_rotation_keys(*ctx, *ks, st, nullptr);
+    return HX_OK;
+    HX_END
+}
+
+int64_t hx_keyset_export_switch_key(const hx_keyset *ks, uint64_t galois, uint64_t *host, size_t cap)
+{
+    HX_TRY
+    need(ks && host, "null argument");
+    const hx_context &c = *ks->ctx;
+    const SwitchKey *k = nullptr;
+    if (galois == 0)
+        k = &ks->relin;
+    else {
+        auto it = ks->rot.find(galois);
+        if (it == ks->rot.end()) throw hx::Error{HX_EKEY, "no key for this Galois element"};
+        k = &it->second;
+    }
+    const size_t words = (size_t)c.dnum * 2 * c.n_all * c.N;
+    need(cap >= words, "buffer too small");
+    HX_CUDA(cudaDeviceSynchronize());
+    HX_CUDA(cudaMemcpy(host, k->buf->p, words * 8, cudaMemcpyDeviceToHost));
+    // Montgomery form -> standard residues: x * 2^-64 mod q
+    for (size_t r = 0; r < (size_t)c.dnum * 2 * c.n_all; r++) {
+        const uint64_t q = c.primes[r % c.n_all];
+        const uint64_t rinv = hinv((uint64_t)(((u128)1 << 64) % q), q);
+        for (int j = 0; j < c.N; j++) host[r * c.N + j] = hmul(host[r * c.N + j], rinv, q);
+    }
+    return (int64_t)words;
+    HX_END
+}
+
+int64_t hx_keyset_export_public_key(const hx_keyset *ks, uint64_t *host, size_t cap)
+{
+    HX_TRY
+    need(ks && host, "null argument");
+    const size_t words = (size_t)2 * ks->ctx->n_q * ks->ctx->N;
+    need(cap >= words, "buffer too small");
+    HX_CUDA(cudaDeviceSynchronize());
+    HX_CUDA(cudaMemcpy(host, ks->pk->p, words * 8, cudaMemcpyDeviceToHost));
+    return (int64_t)words;
+    HX_END
+}
+
+void hx_keyset_destroy(hx_keyset *ks)
+{
+    if (!ks) return;
+    cudaDeviceSynchronize();
+    delete ks;
+}
+
+hx_status hx_encode(const hx_context *ctx, const double *slots, size_t n, double scale, int64_t *coeffs)
+{
+    HX_TRY
+    need(ctx && (slots || n == 0) && coeffs, "null argument");
+    need(n <= (size_t)ctx->N / 2 && scale > 0, "too many slots or bad scale");
+    ctx->enc->encode(slots, n, scale, coeffs);
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_encrypt(hx_context *ctx, const hx_keyset *ks, const double *slots, size_t n, int limbs, uint64_t seed,
+                     hx_ct **out)
+{
+    HX_TRY
+    need(ctx && ks && (slots || n == 0) && out, "null argument");
+    *out = nullptr;
+    need(n <= (size_t)ctx->N / 2, "too many slots");
+    std::vector<int64_t> m(ctx->N);
+    ctx->enc->encode(slots, n, ctx->scale, m.data());
+    Cts c = encrypt_coeffs(*ctx, *ks, m.data(), ctx->scale, limbs ? limbs : ctx->n_q, seed, 0, 0, nullptr);
+    HX_CUDA(cudaStreamSynchronize(nullptr));
+    *out = wrap(ctx, c);
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_encrypt_coeffs(hx_context *ctx, const hx_keyset *ks, const int64_t *coeffs, double scale, int limbs,
+                            uint64_t seed, uint32_t tag, uint32_t index, hx_ct **out)
+{
+    HX_TRY
+    need(ctx && ks && coeffs && out, "null argument");
+    *out = nullptr;
+    Cts c = encrypt_coeffs(*ctx, *ks, coeffs, scale, limbs ? limbs : ctx->n_q, seed, tag, index, nullptr);
+    HX_CUDA(cudaStreamSynchronize(nullptr));
+    *out = wrap(ctx, c);
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_decrypt_coeffs(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, int64_t *coeffs)
+{
+    HX_TRY
+    need(ctx && ks && ct && coeffs, "null argument");
+    HX_CUDA(cudaDeviceSynchronize());
+    std::vector<int64_t> v = decrypt_coeffs(*ctx, *ks, ct->c, nullptr);
+    memcpy(coeffs, v.data(), sizeof(int64_t) * ctx->N);
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_decrypt(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, double *slots, size_t n)
+{
+    HX_TRY
+    need(ctx && ks && ct && (slots || n == 0), "null argument");
+    HX_CUDA(cudaDeviceSynchronize());
+    std::vector<int64_t> v = decrypt_coeffs(*ctx, *ks, ct->c, nullptr);
+    ctx->enc->decode(v.data(), ct->c.scale, slots, std::min(n, (size_t)ctx->N / 2));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_ct_import(hx_context *ctx, const uint64_t *host, int comps, int limbs, double scale, hx_ct **out)
+{
+    HX_TRY
+    need(ctx && host && out, "null argument");
+    *out = nullptr;
+    need(comps >= 2 && comps <= 3 && limbs >= 1 && limbs <= ctx->n_q && scale > 0, "bad ciphertext shape");
+    Eval ev(*ctx, nullptr);
+    Cts c = ev.alloc(1, comps, limbs);
+    c.scale = scale;
+    HX_CUDA(cudaMemcpy(c.d, host, sizeof(uint64_t) * comps * limbs * ctx->N, cudaMemcpyHostToDevice));
+    *out = wrap(ctx, c);
+    return HX_OK;
+    HX_END
+}
+
+int64_t hx_ct_export(const hx_ct *ct, uint64_t *host, size_t cap)
+{
+    HX_TRY
+    need(ct && host, "null argument");
+    const Cts &c = ct->c;
+    const size_t N = ct->ctx->N, words = (size_t)c.comps * c.limbs * N;
+    need(cap >= words, "buffer too small");
+    HX_CUDA(cudaDeviceSynchronize());
+    for (int k = 0; k < c.comps; k++)
+        HX_CUDA(cudaMemcpy(host + (size_t)k * c.limbs * N, c.d + k * c.cstride(N), sizeof(uint64_t) * c.limbs * N,
+                           cudaMemcpyDeviceToHost));
+    return (int64_t)words;
+    HX_END
+}
+
+hx_status hx_ct_info(const hx_ct *ct, int *comps, int *limbs, double *scale)
+{
+    if (!ct) return HX_EINVAL;
+    if (comps) *comps = ct->c.comps;
+    if (limbs) *limbs = ct->c.limbs;
+    if (scale) *scale = ct->c.scale;
+    return HX_OK;
+}
+
+void hx_ct_destroy(hx_ct *ct) { delete ct; }
+
+#define ONE_IN(a) need(ctx && (a) && out, "null argument"); *out = nullptr; Eval ev(*ctx, S(stream));
+
+hx_status hx_add(hx_context *ctx, const hx_ct *a, const hx_ct *b, hx_ct **out, void *stream)
+{
+    HX_TRY
+    ONE_IN(a && b)
+    *out = wrap(ctx, ev.add(a->c, b->c, false));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_sub(hx_context *ctx, const hx_ct *a, const hx_ct *b, hx_ct **out, void *stream)
+{
+    HX_TRY
+    ONE_IN(a && b)
+    *out = wrap(ctx, ev.add(a->c, b->c, true));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_mul_plain(hx_context *ctx, const hx_ct *a, const int64_t *pt, double pt_scale, hx_ct **out,
+                       void *stream)
+{
+    HX_TRY
+    ONE_IN(a && pt)
+    DevBuf p((size_t)a->c.limbs * ctx->N, S(stream));
+    upload_plaintext(*ctx, S(stream), pt, a->c.limbs, p.p);
+    *out = wrap(ctx, ev.mul_plain(a->c, p.p, pt_scale));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_mul_int(hx_context *ctx, const hx_ct *a, int64_t c, double new_scale, hx_ct **out, void *stream)
+{
+    HX_TRY
+    ONE_IN(a)
+    *out = wrap(ctx, ev.mul_int(a->c, c, new_scale));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_add_const(hx_context *ctx, const hx_ct *a, double value, hx_ct **out, void *stream)
+{
+    HX_TRY
+    ONE_IN(a)
+    *out = wrap(ctx, ev.add_const(a->c, value));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_tensor(hx_context *ctx, const hx_ct *a, const hx_ct *b, hx_ct **out, void *stream)
+{
+    HX_TRY
+    ONE_IN(a && b)
+    *out = wrap(ctx, ev.tensor(a->c, b->c));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_relinearize(hx_context *ctx, const hx_keyset *ks, const hx_ct *d, hx_ct **out, void *stream)
+{
+    HX_TRY
+    ONE_IN(ks && d)
+    *out = wrap(ctx, ev.relinearize(d->c, ks->relin));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_rescale(hx_context *ctx, const hx_ct *a, hx_ct **out, void *stream)
+{
+    HX_TRY
+    ONE_IN(a)
+    *out = wrap(ctx, ev.rescale(a->c));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_drop(hx_context *ctx, const hx_ct *a, int limbs, hx_ct **out, void *stream)
+{
+    HX_TRY
+    ONE_IN(a)
+    need(limbs >= 1 && limbs <= a->c.limbs, "bad level");
+    Cts c = ev.copy(ev.drop(a->c, limbs));
+    *out = wrap(ctx, c);
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_rotate(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, int32_t k, hx_ct **out, void *stream)
+{
+    HX_TRY
+    ONE_IN(ks && a)
+    *out = wrap(ctx, ev.rotate(a->c, k, *ks));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_rotate_hoisted(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, const int32_t *steps, int n,
+                            hx_ct **outs, void *stream)
+{
+    HX_TRY
+    need(ctx && ks && a && steps && outs && n >= 0, "null argument");
+    for (int i = 0; i < n; i++) outs[i] = nullptr;
+    Eval ev(*ctx, S(stream));
+    std::vector<int64_t> st(steps, steps + n);
+    std::vector<Cts> r = ev.rotate_hoisted(a->c, st, *ks);
+    for (int i = 0; i < n; i++) outs[i] = wrap(ctx, r[i]);
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_ntt(hx_context *ctx, uint64_t *dev, int n_polys, int limbs, const int32_t *prime_idx, int inverse,
+                 void *stream)
+{
+    HX_TRY
+    need(ctx && dev && prime_idx && n_polys >= 0 && limbs >= 1, "null argument");
+    need(limbs <= MAX_NTT_ROWS && n_polys < 65536, "too many rows");
+    std::vector<int> off(limbs), pr(limbs);
+    for (int l = 0; l < limbs; l++) {
+        need(prime_idx[l] >= 0 && prime_idx[l] < ctx->n_all, "bad prime index");
+        off[l] = l;
+        pr[l] = prime_idx[l];
+    }
+    Eval ev(*ctx, S(stream));
+    ev.ntt_inplace(dev, (size_t)limbs * ctx->N, n_polys, off, pr, inverse != 0);
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_matmul_plan_create(hx_context *ctx, int h, int limbs, hx_matmul_plan **out)
+{
+    HX_TRY
+    need(ctx && out, "null argument");
+    *out = nullptr;
+    *out = make_plan(*ctx, h, limbs, nullptr);
+    return HX_OK;
+    HX_END
+}
+
+int hx_matmul_plan_num_masks(const hx_matmul_plan *plan) { return plan ? (int)plan->masks.size() : HX_EINVAL; }
+
+hx_status hx_matmul_plan_set_mask(hx_context *ctx, hx_matmul_plan *plan, int i, const int64_t *coeffs)
+{
+    HX_TRY
+    need(ctx && plan && coeffs && i >= 0 && i < (int)plan->masks.size(), "bad mask index");
+    auto &m = plan->masks[i];
+    upload_plaintext(*ctx, nullptr, coeffs, m.limbs, m.pt->p);
+    return HX_OK;
+    HX_END
+}
+
+void hx_matmul_plan_destroy(hx_matmul_plan *plan)
+{
+    if (!plan) return;
+    cudaDeviceSynchronize();
+    delete plan;
+}
+
+int hx_matmul_rotation_steps(const hx_context *ctx, int h, int limbs, int32_t *out, int cap)
+{
+    if (!ctx || h < 2 || (h & (h - 1)) || h * h > ctx->N / 2 || limbs < 3) return HX_EINVAL;
+    std::vector<int64_t> st = plan_rotation_steps(h, ctx->N / 2 / (h * h), limbs);
+    for (int i = 0; i < (int)st.size() && i < cap; i++) out[i] = (int32_t)st[i];
+    return (int)st.size();
+}
+
+static const hx_matmul_plan *cached_plan(hx_context *ctx, int h, int limbs)
+{
+    auto key = std::make_pair(h, limbs);
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) return it->second;
+    hx_matmul_plan *p = make_plan(*ctx, h, limbs, nullptr);
+    ctx->plans[key] = p;
+    return p;
+}
+
+hx_status hx_matmul(hx_context *ctx, const hx_keyset *ks, const hx_ct *A, const hx_ct *B, int h, hx_ct **out,
+                    void *stream)
+{
+    HX_TRY
+    need(ctx && ks && A && B && out, "null argument");
+    *out = nullptr;
+    const hx_matmul_plan *p = cached_plan(ctx, h, A->c.limbs);
+    *out = wrap(ctx, matmul_batch(*ctx, *ks, *p, A->c, B->c, S(stream)));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *A,
+                          const hx_ct *const *B, int h, size_t count, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(ctx && ks && A && B && out && count >= 1, "null argument");
+    for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    need(count < 4096, "batch too large");
+    Cts a = gather(*ctx, A, count, S(stream));
+    Cts b = gather(*ctx, B, count, S(stream));
+    const hx_matmul_plan *p = plan ? plan : cached_plan(ctx, h, a.limbs);
+    need(p->h == h, "plan built for another h");
+    Cts r = matmul_batch(*ctx, *ks, *p, a, b, S(stream));
+    scatter(*ctx, r, out, S(stream));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_sign_approx(hx_context *ctx, const hx_keyset *ks, const hx_ct *x, int d, int k, int relu,
+                         int allow_refresh, uint64_t refresh_seed, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(ctx && ks && x && out, "null argument");
+    *out = nullptr;
+    *out = wrap(ctx, sign_batch(*ctx, *ks, x->c, d, k, relu != 0, allow_refresh != 0, refresh_seed, S(stream)));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_sign_approx_batch(hx_context *ctx, const hx_keyset *ks, const hx_ct *const *x, size_t count, int d,
+                               int k, int relu, int allow_refresh, uint64_t refresh_seed, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(ctx && ks && x && out && count >= 1 && count < 4096, "bad argument");
+    for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    Cts a = gather(*ctx, x, count, S(stream));
+    Cts r = sign_batch(*ctx, *ks, a, d, k, relu != 0, allow_refresh != 0, refresh_seed, S(stream));
+    scatter(*ctx, r, out, S(stream));
+    return HX_OK;
+    HX_END
+}
+
+int hx_counters(const hx_context *ctx, uint64_t *out, int cap)
+{
+    if (!ctx) return HX_EINVAL;
+    for (int i = 0; i < C_NUM && i < cap; i++) out[i] = ctx->counters[i];
+    return C_NUM;
+}
+
+void hx_counters_reset(hx_context *ctx)
+{
+    if (ctx) memset(ctx->counters, 0, sizeof(ctx->counters));
+}
+
+} // extern "C"

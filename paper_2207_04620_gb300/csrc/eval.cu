@@ -1,0 +1,299 @@
+// Batched homomorphic evaluation (Fig. 1 items 7-12).  Every operation acts on
+// a batch of B ciphertexts with one launch per kernel; hybrid key switching is
+// ModUp (iNTT, fast basis conversion per digit, NTT) -> key inner product ->
+// ModDown (iNTT of the special limbs, conversion P -> Q_l, NTT, subtract and
+// multiply by P^-1).
+#include <cmath>
+
+#include "runtime.h"
+
+namespace hx {
+
+Cts Eval::alloc(int B, int comps, int limbs)
+{
+    Cts c;
+    c.B = B;
+    c.comps = comps;
+    c.limbs = limbs;
+    c.cap = limbs;
+    c.buf = std::make_shared<DevBuf>((size_t)B * comps * limbs * ctx.N, s);
+    c.d = c.buf->p;
+    return c;
+}
+
+void Eval::check_same(const Cts &a, const Cts &b)
+{
+    HX_CHECK(a.B == b.B, HX_EINVAL, "batch sizes differ");
+    HX_CHECK(a.limbs == b.limbs, HX_ESCALE, "level mismatch");
+    HX_CHECK(std::fabs(a.scale / b.scale - 1.0) <= std::ldexp(1.0, -20), HX_ESCALE, "scale mismatch");
+}
+
+Cts Eval::add(const Cts &a, const Cts &b, bool sub)
+{
+    check_same(a, b);
+    HX_CHECK(a.comps == b.comps, HX_EINVAL, "component count mismatch");
+    Cts o = alloc(a.B, a.comps, a.limbs);
+    o.scale = a.scale;
+    launch_add(lc(), o.view(ctx.N), a.view(ctx.N), b.view(ctx.N), a.B, a.comps, a.limbs, sub);
+    ctx.counters[C_ADD] += a.B;
+    return o;
+}
+
+void Eval::add_inplace(Cts &a, const Cts &b)
+{
+    check_same(a, b);
+    launch_add(lc(), a.view(ctx.N), a.view(ctx.N), b.view(ctx.N), a.B, a.comps, a.limbs, false);
+    ctx.counters[C_ADD] += a.B;
+}
+
+Cts Eval::mul_plain(const Cts &a, const uint64_t *pt, double pt_scale)
+{
+    HX_CHECK(a.comps == 2, HX_EINVAL, "Mul_pt needs a 2-component ciphertext");
+    Cts o = alloc(a.B, 2, a.limbs);
+    o.scale = a.scale * pt_scale;
+    launch_mul_plain(lc(), o.view(ctx.N), a.view(ctx.N), pt, a.B, a.limbs);
+    ctx.counters[C_MULPT] += a.B;
+    return o;
+}
+
+Scalars scalars_for(const hx_context &ctx, int limbs, int64_t c)
+{
+    Scalars sc;
+    for (int l = 0; l < limbs; l++) {
+        const uint64_t q = ctx.primes[l];
+        uint64_t v = c >= 0 ? (uint64_t)c % q : (q - ((uint64_t)(-(c + 1)) + 1) % q) % q;
+        sc.v[l] = v;
+        sc.sh[l] = shoup_companion(v, q);
+    }
+    return sc;
+}
+
+Cts Eval::mul_int(const Cts &a, int64_t c, double new_scale)
+{
+    Cts o = alloc(a.B, a.comps, a.limbs);
+    o.scale = new_scale > 0 ? new_scale : a.scale;
+    launch_mul_scalar(lc(), o.view(ctx.N), a.view(ctx.N), scalars_for(ctx, a.limbs, c), a.B, a.comps, a.limbs);
+    return o;
+}
+
+Cts Eval::add_const(const Cts &a, double value)
+{
+    const double r = round_half_away(value * a.scale);
+    HX_CHECK(std::fabs(r) < 9.2e18, HX_EINVAL, "constant too large");
+    Cts o = alloc(a.B, 2, a.limbs);
+    o.scale = a.scale;
+    launch_add_scalar_c0(lc(), o.view(ctx.N), a.view(ctx.N), scalars_for(ctx, a.limbs, (int64_t)r), a.B, a.limbs);
+    return o;
+}
+
+Cts Eval::tensor(const Cts &a, const Cts &b)
+{
+    HX_CHECK(a.B == b.B && a.limbs == b.limbs && a.comps == 2 && b.comps == 2, HX_ESCALE, "tensor operands differ");
+    Cts o = alloc(a.B, 3, a.limbs);
+    o.scale = a.scale * b.scale;
+    launch_tensor(lc(), o.view(ctx.N), a.view(ctx.N), b.view(ctx.N), a.B, a.limbs, false);
+    ctx.counters[C_MULCT] += a.B;
+    return o;
+}
+
+void Eval::tensor_acc(Cts &acc, const Cts &a, const Cts &b)
+{
+    HX_CHECK(a.B == b.B && a.limbs == b.limbs && acc.limbs == a.limbs && acc.comps == 3, HX_ESCALE,
+             "tensor operands differ");
+    HX_CHECK(std::fabs(acc.scale / (a.scale * b.scale) - 1.0) <= std::ldexp(1.0, -20), HX_ESCALE, "scale mismatch");
+    launch_tensor(lc(), acc.view(ctx.N), a.view(ctx.N), b.view(ctx.N), a.B, a.limbs, true);
+    ctx.counters[C_MULCT] += a.B;
+    ctx.counters[C_ADD] += a.B;
+}
+
+Cts Eval::drop(const Cts &a, int limbs)
+{
+    HX_CHECK(limbs >= 1 && limbs <= a.limbs, HX_EINVAL, "bad level drop");
+    Cts o = a;
+    o.limbs = limbs;
+    return o;
+}
+
+Cts Eval::copy(const Cts &a)
+{
+    Cts o = alloc(a.B, a.comps, a.limbs);
+    o.scale = a.scale;
+    launch_copy(lc(), o.view(ctx.N), a.view(ctx.N), a.B, a.comps, a.limbs);
+    return o;
+}
+
+void Eval::ntt_inplace(uint64_t *p, size_t gstride, int groups, const std::vector<int> &off,
+                       const std::vector<int> &prime, bool inverse)
+{
+    ntt_oop(p, gstride, p, gstride, groups, off, off, prime, inverse);
+}
+
+void Eval::ntt_oop(const uint64_t *src, size_t sgs, uint64_t *dst, size_t dgs, int groups,
+                   const std::vector<int> &src_off, const std::vector<int> &dst_off, const std::vector<int> &prime,
+                   bool inverse)
+{
+    if (prime.empty() || groups == 0) return;
+    NttRows *r = new NttRows;
+    std::unique_ptr<NttRows> guard(r);
+    r->src = src;
+    r->dst = dst;
+    r->src_gs = sgs;
+    r->dst_gs = dgs;
+    r->n_groups = groups;
+    HX_CHECK(prime.size() <= (size_t)MAX_NTT_ROWS, HX_EINVAL, "too many NTT rows");
+    r->n_rows = (int)prime.size();
+    for (size_t i = 0; i < prime.size(); i++) {
+        r->src_off[i] = (int16_t)src_off[i];
+        r->dst_off[i] = (int16_t)dst_off[i];
+        r->prime[i] = (int16_t)prime[i];
+    }
+    launch_ntt(lc(), *r, inverse);
+}
+
+static std::vector<int> iota_vec(int a, int n)
+{
+    std::vector<int> v(n);
+    for (int i = 0; i < n; i++) v[i] = a + i;
+    return v;
+}
+
+BufPtr Eval::modup(const View &d, int B, int limbs)
+{
+    const int N = ctx.N, K = ctx.K, ext = limbs + K, nd = (limbs + K - 1) / K;
+    DevBuf coef((size_t)B * limbs * N, s);
+    ntt_oop(d.p, d.bstride, coef.p, (size_t)limbs * N, B, iota_vec(0, limbs), iota_vec(0, limbs), iota_vec(0, limbs),
+            true);
+    BufPtr D = std::make_shared<DevBuf>((size_t)B * nd * ext * N, s);
+    launch_basis_convert(lc(), ctx.t.modup + (size_t)limbs * ctx.dnum, ext, View{D->p, (size_t)nd * ext * N, 0},
+                         View{coef.p, (size_t)limbs * N, 0}, B, nd, (size_t)ext * N, 0);
+    std::vector<int> off, pr;
+    for (int j = 0; j < nd; j++) {
+        const int lo = j * K, hi = std::min((j + 1) * K, limbs);
+        for (int r = 0; r < ext; r++) {
+            if (r >= lo && r < hi) continue;
+            off.push_back(j * ext + r);
+            pr.push_back(r < limbs ? r : ctx.n_q + (r - limbs));
+        }
+    }
+    ntt_inplace(D->p, (size_t)nd * ext * N, B, off, pr, false);
+    ctx.counters[C_MODUP] += B;
+    return D;
+}
+
+Cts Eval::ks_finish(const BufPtr &D, const View &dnt, int B, int limbs, const SwitchKey &key, uint64_t g,
+                    const View &add, int add_mask, uint64_t add_g)
+{
+    const int N = ctx.N, K = ctx.K, ext = limbs + K, nd = (limbs + K - 1) / K;
+    DevBuf acc((size_t)B * 2 * ext * N, s);
+    View accv{acc.p, (size_t)2 * ext * N, (size_t)ext * N};
+    launch_key_ip(lc(), accv, D->p, dnt.p, dnt.bstride, key.buf->p, ctx.n_all, ctx.n_q, K, limbs, nd, g, B);
+    // ModDown of both components
+    ntt_inplace(acc.p, (size_t)ext * N, 2 * B, iota_vec(limbs, K), iota_vec(ctx.n_q, K), true);
+    DevBuf conv((size_t)B * 2 * limbs * N, s);
+    launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), limbs,
+                         View{conv.p, (size_t)limbs * N, 0}, View{acc.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0);
+    ntt_inplace(conv.p, (size_t)limbs * N, 2 * B, iota_vec(0, limbs), iota_vec(0, limbs), false);
+    Cts o = alloc(B, 2, limbs);
+    launch_moddown_final(lc(), o.view(N), accv, View{conv.p, (size_t)2 * limbs * N, (size_t)limbs * N},
+                         ctx.t.moddown + limbs, B, limbs, add, add_mask, add_g);
+    ctx.counters[C_KS] += B;
+    return o;
+}
+
+Cts Eval::relinearize(const Cts &d, const SwitchKey &rk)
+{
+    HX_CHECK(d.comps == 3, HX_EINVAL, "relinearisation needs 3 components");
+    HX_CHECK(rk.buf, HX_EKEY, "no relinearisation key");
+    const size_t N = ctx.N;
+    View d2{d.d + 2 * d.cstride(N), d.bstride(N), d.cstride(N)};
+    BufPtr D = modup(d2, d.B, d.limbs);
+    Cts o = ks_finish(D, d2, d.B, d.limbs, rk, 1, d.view(N), 3, 1);
+    o.scale = d.scale;
+    return o;
+}
+
+const SwitchKey &Eval::rot_key(const hx_keyset &ks, uint64_t g)
+{
+    auto it = ks.rot.find(g);
+    HX_CHECK(it != ks.rot.end(), HX_EKEY, "missing Galois key for element " + std::to_string(g));
+    return it->second;
+}
+
+Cts Eval::rotate(const Cts &a, int64_t k, const hx_keyset &ks)
+{
+    const uint64_t g = galois_for_step(k, ctx.log_n);
+    if (g == 1) return copy(a);
+    const SwitchKey &key = rot_key(ks, g);
+    const size_t N = ctx.N;
+    Cts t = alloc(a.B, 1, a.limbs);
+    View c1{a.d + a.cstride(N), a.bstride(N), a.cstride(N)};
+    launch_automorphism(lc(), t.view(N), c1, g, a.B, 1, a.limbs);
+    BufPtr D = modup(t.view(N), a.B, a.limbs);
+    Cts o = ks_finish(D, t.view(N), a.B, a.limbs, key, 1, a.view(N), 1, g);
+    o.scale = a.scale;
+    ctx.counters[C_ROT] += a.B;
+    return o;
+}
+
+BufPtr Eval::hoist(const Cts &a)
+{
+    const size_t N = ctx.N;
+    View c1{a.d + a.cstride(N), a.bstride(N), a.cstride(N)};
+    return modup(c1, a.B, a.limbs);
+}
+
+Cts Eval::rotate_hoisted_one(const Cts &a, const BufPtr &D, int64_t k, const hx_keyset &keys)
+{
+    const size_t N = ctx.N;
+    const uint64_t g = galois_for_step(k, ctx.log_n);
+    if (g == 1) return copy(a);
+    const SwitchKey &key = rot_key(keys, g);
+    View c1{a.d + a.cstride(N), a.bstride(N), a.cstride(N)};
+    Cts o = ks_finish(D, c1, a.B, a.limbs, key, g, a.view(N), 1, g);
+    o.scale = a.scale;
+    ctx.counters[C_ROT] += a.B;
+    ctx.counters[C_ROT_HOIST] += a.B;
+    return o;
+}
+
+std::vector<Cts> Eval::rotate_hoisted(const Cts &a, const std::vector<int64_t> &ks, const hx_keyset &keys)
+{
+    BufPtr D;
+    std::vector<Cts> out;
+    for (int64_t k : ks) {
+        if (!D && galois_for_step(k, ctx.log_n) != 1) D = hoist(a);
+        out.push_back(rotate_hoisted_one(a, D, k, keys));
+    }
+    return out;
+}
+
+Cts Eval::rescale(const Cts &a)
+{
+    HX_CHECK(a.limbs >= 2, HX_ELEVEL, "no level left to rescale");
+    const int N = ctx.N, top = a.limbs - 1, comps = a.comps, B = a.B;
+    DevBuf xtop((size_t)B * comps * N, s);
+    ntt_oop(a.d, a.cstride(N), xtop.p, (size_t)N, B * comps, {top}, {0}, {top}, true);
+    DevBuf r((size_t)B * comps * top * N, s);
+    View rv{r.p, (size_t)comps * top * N, (size_t)top * N};
+    const RescaleTable *tab = ctx.t.rescale + a.limbs;
+    launch_rescale_prep(lc(), rv, View{xtop.p, (size_t)comps * N, (size_t)N}, tab, B, comps, top);
+    ntt_inplace(r.p, (size_t)top * N, B * comps, iota_vec(0, top), iota_vec(0, top), false);
+    Cts o = alloc(B, comps, top);
+    launch_rescale_final(lc(), o.view(N), a.view(N), rv, tab, B, comps, top);
+    o.scale = a.scale / (double)ctx.primes[top];
+    ctx.counters[C_RESCALE] += B;
+    return o;
+}
+
+void upload_plaintext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst)
+{
+    Eval ev(ctx, s);
+    DevBuf tmp((size_t)ctx.N, s);
+    HX_CUDA(cudaMemcpyAsync(tmp.p, coeffs, sizeof(int64_t) * ctx.N, cudaMemcpyHostToDevice, s));
+    launch_signed_to_rows(ev.lc(), dst, reinterpret_cast<const int64_t *>(tmp.p), limbs, 1, ctx.N, ctx.d_prime_ids);
+    ev.ntt_inplace(dst, 0, 1, iota_vec(0, limbs), iota_vec(0, limbs), false);
+    launch_to_mont(ev.lc(), dst, limbs, ctx.d_prime_ids);
+    HX_CUDA(cudaStreamSynchronize(s));  // the pageable source must outlive the copy
+}
+
+} // namespace hx

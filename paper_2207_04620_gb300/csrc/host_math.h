@@ -1,0 +1,69 @@
+// Host-side number theory, randomness and encoding for the hx runtime.
+#pragma once
+#include <complex>
+#include <cstdint>
+#include <vector>
+
+namespace hx {
+
+typedef unsigned __int128 u128;
+
+inline uint64_t hmul(uint64_t a, uint64_t b, uint64_t q) { return (uint64_t)((u128)a * b % q); }
+uint64_t hpow(uint64_t a, uint64_t e, uint64_t q);
+uint64_t hinv(uint64_t a, uint64_t q);  // q prime
+bool is_prime_u64(uint64_t n);
+// For each size b (in order): largest prime < 2^b, = 1 mod 2N, not yet chosen.
+std::vector<uint64_t> choose_primes(int log_n, const std::vector<int> &bits);
+// psi = x^((q-1)/2N) for the smallest x >= 2 with psi^N = -1 mod q.
+uint64_t find_psi(uint64_t q, int log_n);
+uint64_t shoup_companion(uint64_t w, uint64_t q);  // floor(w * 2^64 / q)
+uint64_t galois_for_step(int64_t k, int log_n);    // 5^(k mod N/2) mod 2N
+
+// SplitMix64 (Steele, Lea & Flood 2014) as a counter-based stream keyed by
+// (seed, purpose, a, b): state0 = seed ^ mix64(key + gamma), draw i returns
+// mix64(state0 + (i+1)*gamma), key = purpose<<56 | a<<32 | b.
+enum Purpose : uint64_t {
+    P_SK = 1, P_PK_A = 2, P_PK_E = 3, P_KEY_A = 4, P_KEY_E = 5, P_ENC_V = 6, P_ENC_E0 = 7, P_ENC_E1 = 8, P_SMUDGE = 9
+};
+uint64_t mix64(uint64_t z);
+struct Stream {
+    uint64_t state;
+    Stream(uint64_t seed, uint64_t purpose, uint64_t a, uint64_t b);
+    uint64_t next()
+    {
+        state += 0x9E3779B97F4A7C15ull;
+        return mix64(state);
+    }
+};
+// uniform mod q: rejection on bitlen(q) low bits
+void sample_uniform(Stream &s, uint64_t q, uint64_t *out, int n);
+// {-1,0,1}: draw % 3 with 0->0, 1->1, 2->-1
+void sample_ternary(Stream &s, int64_t *out, int n);
+// discrete Gaussian by cumulative table on [-B, B], B = floor(6 sigma)
+struct GaussianCdt {
+    int bound;
+    std::vector<uint64_t> th;
+    explicit GaussianCdt(double sigma);
+    int64_t draw(Stream &s) const;
+};
+
+// round half away from zero, evaluated as sign(x) * floor(|x| + 0.5)
+double round_half_away(double x);
+
+// Canonical-embedding encoder/decoder (slot j at zeta^(5^j), zeta = e^(i pi/N))
+// built on a radix-2 complex FFT of length 2N.
+struct Encoder {
+    int log_n, n;
+    std::vector<int64_t> e;  // 5^j mod 2N
+    std::vector<std::complex<double>> roots;  // e^(-2 pi i k / 2N)
+    explicit Encoder(int log_n);
+    // m_i = (2/N) Re(sum_j z_j zeta^(-i e_j)),  coeffs = round(scale * m)
+    void encode(const double *slots, size_t count, double scale, int64_t *coeffs) const;
+    // z_j = sum_i c_i zeta^(i e_j) / scale (real part)
+    void decode(const int64_t *coeffs, double scale, double *slots, size_t count) const;
+
+  private:
+    void fft(std::vector<std::complex<double>> &a, bool inverse) const;
+};
+
+} // namespace hx

@@ -1,0 +1,138 @@
+// Internal structures shared by the host runtime and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/hx.h"
+#include "modarith.cuh"
+
+namespace hx {
+
+constexpr int MAXP = HX_MAX_Q + HX_MAX_P;
+constexpr int MAXK = HX_MAX_P;
+constexpr int MAX_NTT_ROWS = 1024;
+
+// Fast basis conversion table (Han-Ki hybrid key switching, no correction):
+// out_t = sum_i [x_i * qhat_i^-1]_{q_i} * (qhat_i mod t)  (mod t)
+struct ConvTable {
+    int n_src, n_dst;
+    int src_row[MAXK];        // rows of the source buffer
+    int src_prime[MAXK];      // prime indices (Q then P)
+    int dst_row[MAXP];        // rows of the destination buffer
+    int dst_prime[MAXP];
+    uint64_t inv[MAXK], inv_sh[MAXK];   // [qhat_i^-1]_{q_i} with Shoup companion
+    uint64_t mont[MAXK][MAXP];          // (qhat_i mod t) * 2^64 mod t (Montgomery form)
+};
+
+struct ModDownTable {
+    ConvTable conv;                      // P -> Q_l
+    uint64_t pinv[MAXP], pinv_sh[MAXP];  // P^-1 mod q_i, Shoup
+};
+
+struct RescaleTable {
+    uint64_t half;                                   // floor(q_top / 2)
+    uint64_t qinv[MAXP], qinv_sh[MAXP];              // q_top^-1 mod q_i
+    uint64_t half_mod[MAXP];                         // half mod q_i
+};
+
+// Rows of a batched NTT: for group g in [0,n_groups) and row r in
+// [0,n_rows), the source row is src + g*src_gs + src_off[r]*N and the
+// destination row dst + g*dst_gs + dst_off[r]*N (equal for in-place use),
+// taken modulo prime index prime[r].
+struct NttRows {
+    const uint64_t *src;
+    uint64_t *dst;
+    size_t src_gs, dst_gs;
+    int n_groups;
+    int n_rows;
+    int16_t src_off[MAX_NTT_ROWS];
+    int16_t dst_off[MAX_NTT_ROWS];
+    int16_t prime[MAX_NTT_ROWS];
+};
+
+struct Scalars {
+    uint64_t v[MAXP], sh[MAXP];
+};
+
+// A batch of polynomials with `comps` components of `limbs` rows each:
+// word (b, c, l, j) at p + b*bstride + c*cstride + l*N + j.
+struct View {
+    uint64_t *p;
+    size_t bstride, cstride;
+};
+
+struct DeviceTables {
+    PrimeConst *primes = nullptr;   // [n_all]
+    ulonglong2 *tw_fwd = nullptr;   // [n_all][N] (psi^brv(k), Shoup)
+    ulonglong2 *tw_inv = nullptr;   // [n_all][N] (psi^-brv(k), Shoup)
+    ConvTable *modup = nullptr;     // [(n_q+1) * dnum] by (limbs, digit)
+    ModDownTable *moddown = nullptr;// [n_q+1] by limbs
+    RescaleTable *rescale = nullptr;// [n_q+1] by limbs
+};
+
+// ---- kernel launchers (kernels.cu) ----------------------------------------------
+struct LaunchCtx {
+    int log_n, N;
+    const DeviceTables *t;
+    cudaStream_t stream;
+    uint64_t *launches;
+};
+
+void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse);
+void launch_add(const LaunchCtx &c, View out, View a, View b, int B, int comps, int limbs, bool sub);
+void launch_copy(const LaunchCtx &c, View out, View a, int B, int comps, int limbs);
+void launch_mul_plain(const LaunchCtx &c, View out, View a, const uint64_t *pt_mont, int B, int limbs);
+void launch_mul_scalar(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int comps, int limbs);
+void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int limbs);
+void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate);
+void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int B, int comps, int limbs);
+void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int n_dst_rows_max, View out, View in,
+                          int B, int groups, size_t group_stride_out, size_t group_stride_in);
+void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
+                   const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B);
+// out_c = (acc_c - conv_c) * P^-1, plus add_c[galois(j)] for the components set in add_mask
+void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
+                          int limbs, View add, int add_mask, uint64_t add_galois);
+void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps,
+                         int top);
+void launch_rescale_final(const LaunchCtx &c, View out, View in, View r, const RescaleTable *tab, int B,
+                          int comps, int top);
+void launch_keygen_b(const LaunchCtx &c, uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s,
+                     const uint64_t *sp, const uint64_t *gadget_mask, int rows, const int *prime_of_row_dev,
+                     bool to_mont);
+void launch_encrypt_combine(const LaunchCtx &c, uint64_t *ct, const uint64_t *v, const uint64_t *e0,
+                            const uint64_t *e1, const uint64_t *m, const uint64_t *pk, int n_q, int limbs);
+void launch_signed_to_rows(const LaunchCtx &c, uint64_t *out, const int64_t *in, int rows, int n_in_polys,
+                           size_t in_stride, const int *prime_dev);
+void launch_to_mont(const LaunchCtx &c, uint64_t *p, int rows, const int *prime_dev);
+
+// ---- error handling -------------------------------------------------------------
+void set_error(const std::string &msg);
+struct Error {
+    hx_status code;
+    std::string msg;
+};
+#define HX_CUDA(call)                                                                                      \
+    do {                                                                                                   \
+        cudaError_t e_ = (call);                                                                           \
+        if (e_ != cudaSuccess)                                                                             \
+            throw ::hx::Error{HX_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)};              \
+    } while (0)
+#define HX_CHECK(cond, code, msg)                                                                          \
+    do {                                                                                                   \
+        if (!(cond)) throw ::hx::Error{code, msg};                                                         \
+    } while (0)
+
+} // namespace hx
+
+namespace hx {
+// rows r of out/a/b modulo prime r: out = a * b
+void launch_mul_rows(const LaunchCtx &c, uint64_t *out, const uint64_t *a, const uint64_t *b, int rows);
+// out[b][0] = c0 limb 0, out[b][1+p] = c1 limb 0 * share_p (NTT form, prime 0)
+void launch_ddec_shares(const LaunchCtx &c, uint64_t *out, View ct, const uint64_t *shares, int n_parties, int B);
+} // namespace hx

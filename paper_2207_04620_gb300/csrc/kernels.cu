@@ -1,0 +1,716 @@
+// Device kernels of the RNS-CKKS hot path and their launchers.
+//
+// NTT: negacyclic transform of one limb = Cooley-Tukey (forward, natural ->
+// bit-reversed order, psi powers merged into the twiddles) and
+// Gentleman-Sande (inverse), split into a column phase (the first log2(N1)
+// stages: N1 rows of stride N2) and a row phase (the remaining stages on N2
+// contiguous words), each staged through shared memory.  Every global word is
+// read and written once per phase with 128-byte coalesced row segments.
+#include <cstdio>
+
+#include "internal.h"
+
+namespace hx {
+
+namespace {
+
+__device__ __forceinline__ int brv_bits(unsigned x, int bits) { return (int)(__brev(x) >> (32 - bits)); }
+
+// index of the NTT slot that the automorphism X -> X^g brings to slot j:
+// 2brv(j')+1 = (2brv(j)+1)*g mod 2N
+__device__ __forceinline__ int galois_src(int j, uint64_t g, int log_n)
+{
+    const uint64_t two_n_mask = (2ull << log_n) - 1;
+    uint64_t e = ((2ull * (uint64_t)brv_bits(j, log_n) + 1) * g) & two_n_mask;
+    return brv_bits((unsigned)((e - 1) >> 1), log_n);
+}
+
+// ---- NTT ----------------------------------------------------------------------
+
+template <int LOGM, int COLS, bool INV>
+__global__ void __launch_bounds__(((1 << LOGM) * COLS) / 8)
+k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
+           const ulonglong2 *__restrict__ tw_all, int log_n)
+{
+    constexpr int M = 1 << LOGM, E = M * COLS, T = E / 8;
+    extern __shared__ uint64_t sh[];
+    const int N = 1 << log_n, N2 = N >> LOGM;
+    const int row = blockIdx.y, g = blockIdx.z;
+    const int pr = R.prime[row];
+    const size_t doff = (size_t)g * R.dst_gs + (size_t)R.dst_off[row] * N;
+    const size_t soff = (size_t)g * R.src_gs + (size_t)R.src_off[row] * N;
+    const uint64_t *src = INV ? R.dst + doff : R.src + soff;  // first phase of the forward transform
+    uint64_t *dst = R.dst + doff;
+    const PrimeConst P = primes[pr];
+    const uint64_t q = P.q, two_q = 2 * q;
+    const ulonglong2 *tw = tw_all + (size_t)pr * N;
+    const int c0 = blockIdx.x * COLS;
+    for (int i = threadIdx.x; i < E; i += T) {
+        const int r = i / COLS, c = i % COLS;
+        sh[i] = src[(size_t)r * N2 + c0 + c];
+    }
+    __syncthreads();
+    if (!INV) {
+#pragma unroll 1
+        for (int s = 0; s < LOGM; s++) {
+            const int lt = LOGM - 1 - s;  // t = 2^lt rows
+#pragma unroll
+            for (int it = 0; it < E / 2 / T; it++) {
+                const int b = threadIdx.x + it * T;
+                const int c = b % COLS, bf = b / COLS;
+                const int grp = bf >> lt, k = bf & ((1 << lt) - 1);
+                const int r0 = (grp << (lt + 1)) + k;
+                const ulonglong2 w = tw[(1 << s) + grp];
+                uint64_t x = sh[r0 * COLS + c];
+                const uint64_t y = sh[(r0 + (1 << lt)) * COLS + c];
+                if (x >= two_q) x -= two_q;
+                const uint64_t t = shoup_lazy(y, w.x, w.y, q);
+                sh[r0 * COLS + c] = x + t;
+                sh[(r0 + (1 << lt)) * COLS + c] = x - t + two_q;
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < E; i += T) {
+            const int r = i / COLS, c = i % COLS;
+            dst[(size_t)r * N2 + c0 + c] = sh[i];
+        }
+    } else {
+#pragma unroll 1
+        for (int s = LOGM - 1; s >= 0; s--) {
+            const int lt = LOGM - 1 - s;
+#pragma unroll
+            for (int it = 0; it < E / 2 / T; it++) {
+                const int b = threadIdx.x + it * T;
+                const int c = b % COLS, bf = b / COLS;
+                const int grp = bf >> lt, k = bf & ((1 << lt) - 1);
+                const int r0 = (grp << (lt + 1)) + k;
+                const ulonglong2 w = tw[(1 << s) + grp];
+                const uint64_t x = sh[r0 * COLS + c];
+                const uint64_t y = sh[(r0 + (1 << lt)) * COLS + c];
+                uint64_t u = x + y;
+                if (u >= two_q) u -= two_q;
+                sh[r0 * COLS + c] = u;
+                sh[(r0 + (1 << lt)) * COLS + c] = shoup_lazy(x - y + two_q, w.x, w.y, q);
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < E; i += T) {
+            const int r = i / COLS, c = i % COLS;
+            dst[(size_t)r * N2 + c0 + c] = shoup(sh[i], P.n_inv, P.n_inv_sh, q);
+        }
+    }
+}
+
+template <int LOGM, int ROWS, bool INV>
+__global__ void __launch_bounds__(((1 << LOGM) * ROWS) / 8)
+k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
+           const ulonglong2 *__restrict__ tw_all, int log_n)
+{
+    constexpr int M = 1 << LOGM, E = M * ROWS, T = E / 8;
+    extern __shared__ uint64_t sh[];
+    const int N = 1 << log_n;
+    const int logm1 = log_n - LOGM;  // stages done by the column phase
+    const int row = blockIdx.y, g = blockIdx.z;
+    const int pr = R.prime[row];
+    const size_t doff = (size_t)g * R.dst_gs + (size_t)R.dst_off[row] * N;
+    const size_t soff = (size_t)g * R.src_gs + (size_t)R.src_off[row] * N;
+    const uint64_t *src = INV ? R.src + soff : R.dst + doff;  // first phase of the inverse transform
+    uint64_t *dst = R.dst + doff;
+    const PrimeConst P = primes[pr];
+    const uint64_t q = P.q, two_q = 2 * q;
+    const ulonglong2 *tw = tw_all + (size_t)pr * N;
+    const int r_base = blockIdx.x * ROWS;  // first block of M words
+    const size_t base = (size_t)r_base * M;
+    for (int i = threadIdx.x; i < E; i += T) sh[i] = src[base + i];
+    __syncthreads();
+    if (!INV) {
+#pragma unroll 1
+        for (int s = 0; s < LOGM; s++) {
+            const int lt = LOGM - 1 - s;
+            const int m = 1 << (logm1 + s);
+#pragma unroll
+            for (int it = 0; it < E / 2 / T; it++) {
+                const int b = threadIdx.x + it * T;
+                const int rr = b / (M / 2), bf = b % (M / 2);
+                const int grp = bf >> lt, k = bf & ((1 << lt) - 1);
+                const int c0 = rr * M + (grp << (lt + 1)) + k;
+                const ulonglong2 w = tw[m + ((r_base + rr) << s) + grp];
+                uint64_t x = sh[c0];
+                const uint64_t y = sh[c0 + (1 << lt)];
+                if (x >= two_q) x -= two_q;
+                const uint64_t t = shoup_lazy(y, w.x, w.y, q);
+                sh[c0] = x + t;
+                sh[c0 + (1 << lt)] = x - t + two_q;
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < E; i += T) {
+            uint64_t v = sh[i];
+            if (v >= two_q) v -= two_q;
+            if (v >= q) v -= q;
+            dst[base + i] = v;
+        }
+    } else {
+#pragma unroll 1
+        for (int s = LOGM - 1; s >= 0; s--) {
+            const int lt = LOGM - 1 - s;
+            const int m = 1 << (logm1 + s);
+#pragma unroll
+            for (int it = 0; it < E / 2 / T; it++) {
+                const int b = threadIdx.x + it * T;
+                const int rr = b / (M / 2), bf = b % (M / 2);
+                const int grp = bf >> lt, k = bf & ((1 << lt) - 1);
+                const int c0 = rr * M + (grp << (lt + 1)) + k;
+                const ulonglong2 w = tw[m + ((r_base + rr) << s) + grp];
+                const uint64_t x = sh[c0];
+                const uint64_t y = sh[c0 + (1 << lt)];
+                uint64_t u = x + y;
+                if (u >= two_q) u -= two_q;
+                sh[c0] = u;
+                sh[c0 + (1 << lt)] = shoup_lazy(x - y + two_q, w.x, w.y, q);
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < E; i += T) dst[base + i] = sh[i];
+    }
+}
+
+template <int LOGM, bool INV>
+void ntt_cols(const LaunchCtx &c, const NttRows &rows)
+{
+    constexpr int M = 1 << LOGM;
+    constexpr int COLS = (M >= 256) ? 16 : 2048 / M;
+    constexpr int E = M * COLS;
+    const int N2 = c.N >> LOGM;
+    dim3 grid(N2 / COLS, rows.n_rows, rows.n_groups);
+    const size_t smem = (size_t)E * 8;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_ntt_cols<LOGM, COLS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_ntt_cols<LOGM, COLS, INV><<<grid, E / 8, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
+                                                                 c.log_n);
+}
+
+template <int LOGM, bool INV>
+void ntt_rows(const LaunchCtx &c, const NttRows &rows)
+{
+    constexpr int M = 1 << LOGM;
+    constexpr int ROWS = (M >= 256) ? 16 : 2048 / M;
+    constexpr int E = M * ROWS;
+    const int N1 = c.N >> LOGM;
+    dim3 grid(N1 / ROWS, rows.n_rows, rows.n_groups);
+    const size_t smem = (size_t)E * 8;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_ntt_rows<LOGM, ROWS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
+    k_ntt_rows<LOGM, ROWS, INV><<<grid, E / 8, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
+                                                                 c.log_n);
+}
+
+template <bool INV>
+void ntt_cols_dispatch(const LaunchCtx &c, const NttRows &r, int logm)
+{
+    switch (logm) {
+    case 5: ntt_cols<5, INV>(c, r); break;
+    case 6: ntt_cols<6, INV>(c, r); break;
+    case 7: ntt_cols<7, INV>(c, r); break;
+    case 8: ntt_cols<8, INV>(c, r); break;
+    default: throw Error{HX_EINVAL, "unsupported NTT size"};
+    }
+}
+
+template <bool INV>
+void ntt_rows_dispatch(const LaunchCtx &c, const NttRows &r, int logm)
+{
+    switch (logm) {
+    case 5: ntt_rows<5, INV>(c, r); break;
+    case 6: ntt_rows<6, INV>(c, r); break;
+    case 7: ntt_rows<7, INV>(c, r); break;
+    case 8: ntt_rows<8, INV>(c, r); break;
+    case 9: ntt_rows<9, INV>(c, r); break;
+    default: throw Error{HX_EINVAL, "unsupported NTT size"};
+    }
+}
+
+// ---- elementwise ----------------------------------------------------------------
+// grid: x over pairs of coefficients, y = limb, z = b*comps + comp
+
+__global__ void k_add(View out, View a, View b, const PrimeConst *__restrict__ primes, int comps, int n, bool sub)
+{
+    const int l = blockIdx.y, bc = blockIdx.z, bi = bc / comps, ci = bc % comps;
+    const uint64_t q = primes[l].q;
+    const size_t oo = bi * out.bstride + ci * out.cstride + (size_t)l * n;
+    const size_t oa = bi * a.bstride + ci * a.cstride + (size_t)l * n;
+    const size_t ob = bi * b.bstride + ci * b.cstride + (size_t)l * n;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(a.p + oa + j);
+        const ulonglong2 y = *reinterpret_cast<const ulonglong2 *>(b.p + ob + j);
+        ulonglong2 r;
+        r.x = sub ? submod(x.x, y.x, q) : addmod(x.x, y.x, q);
+        r.y = sub ? submod(x.y, y.y, q) : addmod(x.y, y.y, q);
+        *reinterpret_cast<ulonglong2 *>(out.p + oo + j) = r;
+    }
+}
+
+__global__ void k_copy(View out, View a, int comps, int n)
+{
+    const int l = blockIdx.y, bc = blockIdx.z, bi = bc / comps, ci = bc % comps;
+    const size_t oo = bi * out.bstride + ci * out.cstride + (size_t)l * n;
+    const size_t oa = bi * a.bstride + ci * a.cstride + (size_t)l * n;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2)
+        *reinterpret_cast<ulonglong2 *>(out.p + oo + j) = *reinterpret_cast<const ulonglong2 *>(a.p + oa + j);
+}
+
+// out_c = a_c * pt  with pt in Montgomery form (pt * 2^64 mod q): one reduction
+__global__ void k_mul_plain(View out, View a, const uint64_t *__restrict__ pt, const PrimeConst *__restrict__ primes,
+                            int n)
+{
+    const int l = blockIdx.y, bc = blockIdx.z, bi = bc / 2, ci = bc % 2;
+    const PrimeConst P = primes[l];
+    const size_t oo = bi * out.bstride + ci * out.cstride + (size_t)l * n;
+    const size_t oa = bi * a.bstride + ci * a.cstride + (size_t)l * n;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(a.p + oa + j);
+        const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(pt + (size_t)l * n + j);
+        ulonglong2 r;
+        r.x = mont128(__umul64hi(x.x, w.x), x.x * w.x, P);
+        r.y = mont128(__umul64hi(x.y, w.y), x.y * w.y, P);
+        *reinterpret_cast<ulonglong2 *>(out.p + oo + j) = r;
+    }
+}
+
+// out = a * s_l (Shoup constant per limb)
+__global__ void k_mul_scalar(View out, View a, const __grid_constant__ Scalars sc, const PrimeConst *__restrict__ primes,
+                             int comps, int n)
+{
+    const int l = blockIdx.y, bc = blockIdx.z, bi = bc / comps, ci = bc % comps;
+    const uint64_t q = primes[l].q, w = sc.v[l], wsh = sc.sh[l];
+    const size_t oo = bi * out.bstride + ci * out.cstride + (size_t)l * n;
+    const size_t oa = bi * a.bstride + ci * a.cstride + (size_t)l * n;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(a.p + oa + j);
+        ulonglong2 r;
+        r.x = shoup(x.x, w, wsh, q);
+        r.y = shoup(x.y, w, wsh, q);
+        *reinterpret_cast<ulonglong2 *>(out.p + oo + j) = r;
+    }
+}
+
+// out = a with s_l added to every slot of c0 (a constant polynomial in NTT form)
+__global__ void k_add_scalar_c0(View out, View a, const __grid_constant__ Scalars sc,
+                                const PrimeConst *__restrict__ primes, int n)
+{
+    const int l = blockIdx.y, bc = blockIdx.z, bi = bc / 2, ci = bc % 2;
+    const uint64_t q = primes[l].q, s = ci == 0 ? sc.v[l] : 0;
+    const size_t oo = bi * out.bstride + ci * out.cstride + (size_t)l * n;
+    const size_t oa = bi * a.bstride + ci * a.cstride + (size_t)l * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        out.p[oo + j] = addmod(a.p[oa + j], s, q);
+}
+
+// (a0,a1) x (b0,b1) -> (a0b0, a0b1+a1b0, a1b1), optionally added to out
+__global__ void k_tensor(View out, View a, View b, const PrimeConst *__restrict__ primes, int n, bool acc)
+{
+    const int l = blockIdx.y, bi = blockIdx.z;
+    const PrimeConst P = primes[l];
+    const size_t la = bi * a.bstride + (size_t)l * n, lb = bi * b.bstride + (size_t)l * n;
+    const size_t lo = bi * out.bstride + (size_t)l * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const uint64_t a0 = a.p[la + j], a1 = a.p[la + a.cstride + j];
+        const uint64_t b0 = b.p[lb + j], b1 = b.p[lb + b.cstride + j];
+        Acc128 d1;
+        d1.mac(a0, b1);
+        d1.mac(a1, b0);
+        uint64_t r0 = mont128(__umul64hi(a0, b0), a0 * b0, P);
+        uint64_t r1 = mont128(d1.hi, d1.lo, P);
+        uint64_t r2 = mont128(__umul64hi(a1, b1), a1 * b1, P);
+        r0 = shoup(r0, P.r_mod, P.r_mod_sh, P.q);
+        r1 = shoup(r1, P.r_mod, P.r_mod_sh, P.q);
+        r2 = shoup(r2, P.r_mod, P.r_mod_sh, P.q);
+        if (acc) {
+            r0 = addmod(r0, out.p[lo + j], P.q);
+            r1 = addmod(r1, out.p[lo + out.cstride + j], P.q);
+            r2 = addmod(r2, out.p[lo + 2 * out.cstride + j], P.q);
+        }
+        out.p[lo + j] = r0;
+        out.p[lo + out.cstride + j] = r1;
+        out.p[lo + 2 * out.cstride + j] = r2;
+    }
+}
+
+__global__ void k_automorphism(View out, View in, uint64_t g, int comps, int log_n)
+{
+    const int n = 1 << log_n;
+    const int l = blockIdx.y, bc = blockIdx.z, bi = bc / comps, ci = bc % comps;
+    const size_t oo = bi * out.bstride + ci * out.cstride + (size_t)l * n;
+    const size_t oi = bi * in.bstride + ci * in.cstride + (size_t)l * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        out.p[oo + j] = in.p[oi + galois_src(j, g, log_n)];
+}
+
+// Fast basis conversion; grid: x over coefficients, z = b * groups + grp
+__global__ void k_basis_convert(const ConvTable *__restrict__ tabs, View out, View in, const PrimeConst *__restrict__ primes,
+                                int groups, size_t gstride_out, size_t gstride_in, int n)
+{
+    const int bz = blockIdx.z, bi = bz / groups, gi = bz % groups;
+    const ConvTable &T = tabs[gi];
+    __shared__ uint64_t smont[MAXK * MAXP];
+    __shared__ uint64_t sq[MAXP], sbar[MAXP], smneg[MAXP];
+    const int ns = T.n_src, nd = T.n_dst;
+    for (int i = threadIdx.x; i < ns * nd; i += blockDim.x) smont[i] = T.mont[i / nd][i % nd];
+    for (int d = threadIdx.x; d < nd; d += blockDim.x) {
+        const PrimeConst P = primes[T.dst_prime[d]];
+        sq[d] = P.q;
+        sbar[d] = P.bar;
+        smneg[d] = P.mneg;
+    }
+    __syncthreads();
+    const uint64_t *src = in.p + bi * in.bstride + gi * gstride_in;
+    uint64_t *dst = out.p + bi * out.bstride + gi * gstride_out;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        uint64_t y[MAXK];
+#pragma unroll
+        for (int i = 0; i < MAXK; i++) {
+            if (i < ns) {
+                const uint64_t qi = primes[T.src_prime[i]].q;
+                y[i] = shoup(src[(size_t)T.src_row[i] * n + j], T.inv[i], T.inv_sh[i], qi);
+            }
+        }
+        for (int d = 0; d < nd; d++) {
+            Acc128 acc;
+#pragma unroll
+            for (int i = 0; i < MAXK; i++)
+                if (i < ns) acc.mac(y[i], smont[i * nd + d]);
+            const uint64_t q = sq[d];
+            const uint64_t r = csub(csub(acc.hi - __umul64hi(acc.hi, sbar[d]) * q, q) + mont64(acc.lo, q, smneg[d]), q);
+            dst[(size_t)T.dst_row[d] * n + j] = r;
+        }
+    }
+}
+
+// Key inner product of hybrid key switching: for ext row t (Q_l then P),
+// acc_h[t] = sum_j src_j[t][galois(n)] * key[j][h][row(t)][n], where src_j is
+// the NTT-form input itself on digit j's own rows and the ModUp output D_j
+// elsewhere.  Keys are in Montgomery form, so one reduction gives the sum.
+__global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt, size_t dnt_bstride,
+                         const uint64_t *__restrict__ key, const PrimeConst *__restrict__ primes, int n_all, int n_q,
+                         int K, int limbs, int ndig, uint64_t g, int log_n)
+{
+    const int n = 1 << log_n;
+    const int t = blockIdx.y, bi = blockIdx.z;
+    const int ext = limbs + K;
+    const int pr = t < limbs ? t : n_q + (t - limbs);
+    const PrimeConst P = primes[pr];
+    const size_t dig_stride = (size_t)ext * n;
+    const uint64_t *Db = D + (size_t)bi * ndig * dig_stride;
+    const uint64_t *db = dnt + bi * dnt_bstride;
+    const int own_digit = t < limbs ? t / K : -1;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int js = g == 1 ? j : galois_src(j, g, log_n);
+        Acc128 a0, a1;
+        for (int d = 0; d < ndig; d++) {
+            const uint64_t x = (d == own_digit) ? db[(size_t)t * n + js] : Db[d * dig_stride + (size_t)t * n + js];
+            const uint64_t *kd = key + (size_t)d * 2 * n_all * n + (size_t)pr * n + j;
+            a0.mac(x, kd[0]);
+            a1.mac(x, kd[(size_t)n_all * n]);
+        }
+        acc.p[bi * acc.bstride + (size_t)t * n + j] = mont128(a0.hi, a0.lo, P);
+        acc.p[bi * acc.bstride + acc.cstride + (size_t)t * n + j] = mont128(a1.hi, a1.lo, P);
+    }
+}
+
+// out_c[t] = (acc_c[t] - conv_c[t]) * P^-1 (+ add_c[t][galois(j)] for the components in add_mask)
+__global__ void k_moddown_final(View out, View acc, View conv, const ModDownTable *__restrict__ tab,
+                                const PrimeConst *__restrict__ primes, View add, int add_mask, uint64_t g, int log_n)
+{
+    const int n = 1 << log_n;
+    const int t = blockIdx.y, bc = blockIdx.z, bi = bc / 2, ci = bc % 2;
+    const uint64_t q = primes[t].q, w = tab->pinv[t], wsh = tab->pinv_sh[t];
+    const uint64_t *a = acc.p + bi * acc.bstride + ci * acc.cstride + (size_t)t * n;
+    const uint64_t *cv = conv.p + bi * conv.bstride + ci * conv.cstride + (size_t)t * n;
+    uint64_t *o = out.p + bi * out.bstride + ci * out.cstride + (size_t)t * n;
+    const bool has = (add_mask >> ci) & 1;
+    const uint64_t *ap = has ? add.p + bi * add.bstride + ci * add.cstride + (size_t)t * n : nullptr;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        uint64_t r = shoup(submod(a[j], cv[j], q), w, wsh, q);
+        if (has) r = addmod(r, ap[g == 1 ? j : galois_src(j, g, log_n)], q);
+        o[j] = r;
+    }
+}
+
+// r_i = ([x + floor(q_t/2)]_{q_t} mod q_i - floor(q_t/2) mod q_i) for the lower limbs
+__global__ void k_rescale_prep(View r, View xtop, const RescaleTable *__restrict__ tab,
+                               const PrimeConst *__restrict__ primes, int comps, int top, int n)
+{
+    const int i = blockIdx.y, bc = blockIdx.z, bi = bc / comps, ci = bc % comps;
+    const uint64_t qt = primes[top].q, half = tab->half;
+    const PrimeConst Pi = primes[i];
+    const uint64_t hm = tab->half_mod[i];
+    const uint64_t *x = xtop.p + bi * xtop.bstride + ci * xtop.cstride;
+    uint64_t *o = r.p + bi * r.bstride + ci * r.cstride + (size_t)i * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const uint64_t v = csub(x[j] + half, qt);
+        o[j] = submod(reduce64(v, Pi.q, Pi.bar), hm, Pi.q);
+    }
+}
+
+__global__ void k_rescale_final(View out, View in, View r, const RescaleTable *__restrict__ tab,
+                                const PrimeConst *__restrict__ primes, int comps, int n)
+{
+    const int i = blockIdx.y, bc = blockIdx.z, bi = bc / comps, ci = bc % comps;
+    const uint64_t q = primes[i].q, w = tab->qinv[i], wsh = tab->qinv_sh[i];
+    const uint64_t *a = in.p + bi * in.bstride + ci * in.cstride + (size_t)i * n;
+    const uint64_t *rr = r.p + bi * r.bstride + ci * r.cstride + (size_t)i * n;
+    uint64_t *o = out.p + bi * out.bstride + ci * out.cstride + (size_t)i * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        o[j] = shoup(submod(a[j], rr[j], q), w, wsh, q);
+}
+
+// b = e - a*s + gad_r * s'  (all NTT form, row r modulo prime r); optionally
+// b and a are left in Montgomery form for the key inner product.
+__global__ void k_keygen_b(uint64_t *b, uint64_t *a, const uint64_t *e, const uint64_t *s, const uint64_t *sp,
+                           const uint64_t *gad, const PrimeConst *__restrict__ primes, int n, bool to_mont)
+{
+    const int r = blockIdx.y;
+    const PrimeConst P = primes[r];
+    const uint64_t gr = gad ? gad[r] : 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const size_t k = (size_t)r * n + j;
+        uint64_t v = submod(e[k], mulmod(a[k], s[k], P), P.q);
+        if (gr) v = addmod(v, mulmod(gr, sp[k], P), P.q);
+        if (to_mont) {
+            v = shoup(v, P.r_mod, P.r_mod_sh, P.q);
+            a[k] = shoup(a[k], P.r_mod, P.r_mod_sh, P.q);
+        }
+        b[k] = v;
+    }
+}
+
+// c0 = v*pk_b + e0 + m, c1 = v*pk_a + e1 on the first `limbs` primes
+__global__ void k_encrypt_combine(uint64_t *ct, const uint64_t *v, const uint64_t *e0, const uint64_t *e1,
+                                  const uint64_t *m, const uint64_t *pk, const PrimeConst *__restrict__ primes,
+                                  int n_q, int limbs, int n)
+{
+    const int l = blockIdx.y;
+    const PrimeConst P = primes[l];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const size_t k = (size_t)l * n + j;
+        const uint64_t vb = mulmod(v[k], pk[k], P);
+        const uint64_t va = mulmod(v[k], pk[(size_t)n_q * n + k], P);
+        ct[k] = addmod(addmod(vb, e0[k], P.q), m[k], P.q);
+        ct[(size_t)limbs * n + k] = addmod(va, e1[k], P.q);
+    }
+}
+
+// signed coefficients -> residues: out[p][r][j] = in[p][j] mod q_{prime[r]}
+__global__ void k_signed_to_rows(uint64_t *out, const int64_t *in, int rows, size_t in_stride, const int *prime,
+                                 const PrimeConst *__restrict__ primes, int n)
+{
+    const int r = blockIdx.y, p = blockIdx.z;
+    const uint64_t q = primes[prime[r]].q;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int64_t v = in[p * in_stride + j];
+        const uint64_t m = v >= 0 ? (uint64_t)v % q : (q - ((uint64_t)(-v) % q)) % q;
+        out[((size_t)p * rows + r) * n + j] = m;
+    }
+}
+
+__global__ void k_to_mont(uint64_t *p, const int *prime, const PrimeConst *__restrict__ primes, int n)
+{
+    const int r = blockIdx.y;
+    const PrimeConst P = primes[prime[r]];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const size_t k = (size_t)r * n + j;
+        p[k] = shoup(p[k], P.r_mod, P.r_mod_sh, P.q);
+    }
+}
+
+__global__ void k_mul_rows(uint64_t *out, const uint64_t *a, const uint64_t *b, const PrimeConst *__restrict__ primes,
+                           int n)
+{
+    const int r = blockIdx.y;
+    const PrimeConst P = primes[r];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const size_t k = (size_t)r * n + j;
+        out[k] = mulmod(a[k], b[k], P);
+    }
+}
+
+__global__ void k_ddec_shares(uint64_t *out, View ct, const uint64_t *shares, const PrimeConst *__restrict__ primes,
+                              int np, int n)
+{
+    const int p = blockIdx.y, bi = blockIdx.z;
+    const PrimeConst P = primes[0];
+    const uint64_t *c0 = ct.p + bi * ct.bstride;
+    const uint64_t *c1 = c0 + ct.cstride;
+    uint64_t *o = out + ((size_t)bi * (np + 1) + p) * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+        o[j] = p == 0 ? c0[j] : mulmod(c1[j], shares[(size_t)(p - 1) * n + j], P);
+}
+
+inline int ew_blocks(int n, int per_thread) { return (n / per_thread + 255) / 256; }
+
+inline void post(const LaunchCtx &c, int k = 1)
+{
+    if (c.launches) *c.launches += k;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) throw Error{HX_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e)};
+}
+
+} // namespace
+
+void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse)
+{
+    if (rows.n_rows <= 0 || rows.n_groups <= 0) return;
+    HX_CHECK(rows.n_rows <= MAX_NTT_ROWS && rows.n_groups < 65536, HX_EINVAL, "NTT batch too large");
+    const int logm1 = c.log_n / 2, logm2 = c.log_n - logm1;
+    if (!inverse) {
+        ntt_cols_dispatch<false>(c, rows, logm1);
+        ntt_rows_dispatch<false>(c, rows, logm2);
+    } else {
+        ntt_rows_dispatch<true>(c, rows, logm2);
+        ntt_cols_dispatch<true>(c, rows, logm1);
+    }
+    post(c, 2);
+}
+
+void launch_add(const LaunchCtx &c, View out, View a, View b, int B, int comps, int limbs, bool sub)
+{
+    dim3 grid(ew_blocks(c.N, 2), limbs, B * comps);
+    k_add<<<grid, 256, 0, c.stream>>>(out, a, b, c.t->primes, comps, c.N, sub);
+    post(c);
+}
+
+void launch_copy(const LaunchCtx &c, View out, View a, int B, int comps, int limbs)
+{
+    dim3 grid(ew_blocks(c.N, 2), limbs, B * comps);
+    k_copy<<<grid, 256, 0, c.stream>>>(out, a, comps, c.N);
+    post(c);
+}
+
+void launch_mul_plain(const LaunchCtx &c, View out, View a, const uint64_t *pt, int B, int limbs)
+{
+    dim3 grid(ew_blocks(c.N, 2), limbs, B * 2);
+    k_mul_plain<<<grid, 256, 0, c.stream>>>(out, a, pt, c.t->primes, c.N);
+    post(c);
+}
+
+void launch_mul_scalar(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int comps, int limbs)
+{
+    dim3 grid(ew_blocks(c.N, 2), limbs, B * comps);
+    k_mul_scalar<<<grid, 256, 0, c.stream>>>(out, a, sc, c.t->primes, comps, c.N);
+    post(c);
+}
+
+void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int limbs)
+{
+    dim3 grid(ew_blocks(c.N, 1), limbs, B * 2);
+    k_add_scalar_c0<<<grid, 256, 0, c.stream>>>(out, a, sc, c.t->primes, c.N);
+    post(c);
+}
+
+void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate)
+{
+    dim3 grid(ew_blocks(c.N, 1), limbs, B);
+    k_tensor<<<grid, 256, 0, c.stream>>>(out3, a, b, c.t->primes, c.N, accumulate);
+    post(c);
+}
+
+void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int B, int comps, int limbs)
+{
+    dim3 grid(ew_blocks(c.N, 1), limbs, B * comps);
+    k_automorphism<<<grid, 256, 0, c.stream>>>(out, in, g, comps, c.log_n);
+    post(c);
+}
+
+void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int, View out, View in, int B, int groups,
+                          size_t gstride_out, size_t gstride_in)
+{
+    HX_CHECK(B * groups < 65536, HX_EINVAL, "conversion batch too large");
+    dim3 grid(ew_blocks(c.N, 1), 1, B * groups);
+    k_basis_convert<<<grid, 256, 0, c.stream>>>(tab_dev, out, in, c.t->primes, groups, gstride_out, gstride_in, c.N);
+    post(c);
+}
+
+void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
+                   const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B)
+{
+    dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
+    k_key_ip<<<grid, 256, 0, c.stream>>>(acc, D, dnt, dnt_bstride, key, c.t->primes, n_all, n_q, K, limbs, ndig, g,
+                                         c.log_n);
+    post(c);
+}
+
+void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
+                          int limbs, View add, int add_mask, uint64_t g)
+{
+    dim3 grid(ew_blocks(c.N, 1), limbs, B * 2);
+    k_moddown_final<<<grid, 256, 0, c.stream>>>(out, acc, conv, tab, c.t->primes, add, add_mask, g, c.log_n);
+    post(c);
+}
+
+void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps, int top)
+{
+    dim3 grid(ew_blocks(c.N, 1), top, B * comps);
+    k_rescale_prep<<<grid, 256, 0, c.stream>>>(r, xtop, tab, c.t->primes, comps, top, c.N);
+    post(c);
+}
+
+void launch_rescale_final(const LaunchCtx &c, View out, View in, View r, const RescaleTable *tab, int B, int comps,
+                          int top)
+{
+    dim3 grid(ew_blocks(c.N, 1), top, B * comps);
+    k_rescale_final<<<grid, 256, 0, c.stream>>>(out, in, r, tab, c.t->primes, comps, c.N);
+    post(c);
+}
+
+void launch_keygen_b(const LaunchCtx &c, uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s,
+                     const uint64_t *sp, const uint64_t *gad, int rows, const int *, bool to_mont)
+{
+    dim3 grid(ew_blocks(c.N, 1), rows, 1);
+    k_keygen_b<<<grid, 256, 0, c.stream>>>(b, const_cast<uint64_t *>(a), e, s, sp, gad, c.t->primes, c.N, to_mont);
+    post(c);
+}
+
+void launch_encrypt_combine(const LaunchCtx &c, uint64_t *ct, const uint64_t *v, const uint64_t *e0,
+                            const uint64_t *e1, const uint64_t *m, const uint64_t *pk, int n_q, int limbs)
+{
+    dim3 grid(ew_blocks(c.N, 1), limbs, 1);
+    k_encrypt_combine<<<grid, 256, 0, c.stream>>>(ct, v, e0, e1, m, pk, c.t->primes, n_q, limbs, c.N);
+    post(c);
+}
+
+void launch_signed_to_rows(const LaunchCtx &c, uint64_t *out, const int64_t *in, int rows, int n_in_polys,
+                           size_t in_stride, const int *prime_dev)
+{
+    dim3 grid(ew_blocks(c.N, 1), rows, n_in_polys);
+    k_signed_to_rows<<<grid, 256, 0, c.stream>>>(out, in, rows, in_stride, prime_dev, c.t->primes, c.N);
+    post(c);
+}
+
+void launch_to_mont(const LaunchCtx &c, uint64_t *p, int rows, const int *prime_dev)
+{
+    dim3 grid(ew_blocks(c.N, 1), rows, 1);
+    k_to_mont<<<grid, 256, 0, c.stream>>>(p, prime_dev, c.t->primes, c.N);
+    post(c);
+}
+
+void launch_mul_rows(const LaunchCtx &c, uint64_t *out, const uint64_t *a, const uint64_t *b, int rows)
+{
+    dim3 grid(ew_blocks(c.N, 1), rows, 1);
+    k_mul_rows<<<grid, 256, 0, c.stream>>>(out, a, b, c.t->primes, c.N);
+    post(c);
+}
+
+void launch_ddec_shares(const LaunchCtx &c, uint64_t *out, View ct, const uint64_t *shares, int n_parties, int B)
+{
+    dim3 grid(ew_blocks(c.N, 1), n_parties + 1, B);
+    k_ddec_shares<<<grid, 256, 0, c.stream>>>(out, ct, shares, c.t->primes, n_parties, c.N);
+    post(c);
+}
+
+} // namespace hx

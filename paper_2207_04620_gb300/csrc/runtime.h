@@ -1,0 +1,162 @@
+// Host runtime: context, keys, batched ciphertext buffers and the evaluator.
+#pragma once
+#include <map>
+#include <memory>
+#include <vector>
+
+#include "host_math.h"
+#include "internal.h"
+
+namespace hx {
+
+enum Counter { C_ADD, C_MULPT, C_ROT, C_ROT_HOIST, C_MULCT, C_KS, C_MODUP, C_RESCALE, C_REFRESH, C_LAUNCH, C_NUM };
+
+// stream-ordered device allocation (cudaMallocAsync on the device's pool)
+struct DevBuf {
+    uint64_t *p = nullptr;
+    size_t words = 0;
+    cudaStream_t stream = nullptr;
+    DevBuf(size_t w, cudaStream_t s);
+    ~DevBuf();
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+};
+typedef std::shared_ptr<DevBuf> BufPtr;
+
+// `B` ciphertexts (or 3-component tensors) of `comps` x `limbs` rows; storage
+// [B][comps][cap][N] so that a level drop keeps the buffer.
+struct Cts {
+    BufPtr buf;
+    uint64_t *d = nullptr;
+    int B = 0, comps = 2, limbs = 0, cap = 0;
+    double scale = 0;
+    size_t cstride(int N) const { return (size_t)cap * N; }
+    size_t bstride(int N) const { return (size_t)comps * cap * N; }
+    View view(int N) const { return View{d, bstride(N), cstride(N)}; }
+};
+
+struct SwitchKey {
+    BufPtr buf;  // [dnum][2][n_all][N] Montgomery form
+};
+
+} // namespace hx
+
+struct hx_context {
+    int log_n = 0, N = 0, n_q = 0, K = 0, n_all = 0, dnum = 0;
+    std::vector<uint64_t> primes;  // Q then P
+    std::vector<uint64_t> psi;
+    double scale = 0, sigma = 0;
+    std::vector<hx::PrimeConst> h_primes;
+    std::vector<hx::ConvTable> h_modup;        // [(n_q+1) * dnum]
+    std::vector<hx::ModDownTable> h_moddown;   // [n_q+1]
+    std::vector<hx::RescaleTable> h_rescale;   // [n_q+1]
+    hx::DeviceTables t;
+    hx::DeviceTables *t_dev = nullptr;
+    int *d_prime_ids = nullptr;                // 0..n_all-1
+    std::unique_ptr<hx::Encoder> enc;
+    std::unique_ptr<hx::GaussianCdt> cdt;
+    uint64_t counters[hx::C_NUM] = {0};
+    std::map<std::pair<int, int>, hx_matmul_plan *> plans;
+    int device = 0;
+};
+
+struct hx_keyset {
+    hx_context *ctx = nullptr;
+    int n_parties = 0;
+    uint64_t seed = 0;
+    std::vector<std::vector<int64_t>> s_parts;  // ternary shares
+    std::vector<int64_t> s;                     // sum of the shares
+    hx::BufPtr s_ntt;                           // [n_all][N]
+    hx::BufPtr s_parts0;                        // [n_parties][N] share mod q_0, NTT form
+    hx::BufPtr pk;                              // [2][n_q][N]
+    hx::SwitchKey relin;
+    std::map<uint64_t, hx::SwitchKey> rot;      // galois element -> key
+};
+
+struct hx_ct {
+    hx_context *ctx = nullptr;
+    hx::Cts c;  // B = 1
+};
+
+struct hx_matmul_plan {
+    hx_context *ctx = nullptr;
+    int h = 0, limbs = 0, beta = 0, b = 0;
+    bool alg3 = true;
+    struct Mask {
+        int kind;  // 0 mu, 1 zeta, 2 v
+        int index;
+        int limbs;
+        double scale;
+        std::vector<int32_t> vec;  // logical 0/1 vector of length h^2
+        hx::BufPtr pt;             // [limbs][N] Montgomery form, NTT
+    };
+    std::vector<Mask> masks;
+    std::map<std::pair<int, int>, int> index;
+};
+
+namespace hx {
+
+// ---- evaluator (eval.cu) ----------------------------------------------------
+struct Eval {
+    hx_context &ctx;
+    cudaStream_t s;
+    LaunchCtx lc() { return LaunchCtx{ctx.log_n, ctx.N, &ctx.t, s, &ctx.counters[C_LAUNCH]}; }
+    Eval(hx_context &c, cudaStream_t st) : ctx(c), s(st) {}
+
+    Cts alloc(int B, int comps, int limbs);
+    Cts add(const Cts &a, const Cts &b, bool sub = false);
+    void add_inplace(Cts &a, const Cts &b);
+    Cts mul_plain(const Cts &a, const uint64_t *pt_mont, double pt_scale);
+    Cts mul_int(const Cts &a, int64_t c, double new_scale = 0);
+    Cts add_const(const Cts &a, double value);
+    Cts tensor(const Cts &a, const Cts &b);
+    void tensor_acc(Cts &acc, const Cts &a, const Cts &b);
+    Cts relinearize(const Cts &d, const SwitchKey &rk);
+    Cts rescale(const Cts &a);
+    Cts drop(const Cts &a, int limbs);  // shares storage
+    Cts copy(const Cts &a);
+    Cts rotate(const Cts &a, int64_t k, const hx_keyset &ks);
+    std::vector<Cts> rotate_hoisted(const Cts &a, const std::vector<int64_t> &ks, const hx_keyset &keys);
+    // hoisting in two steps: the ModUp of c1 once, then any number of rotations
+    BufPtr hoist(const Cts &a);
+    Cts rotate_hoisted_one(const Cts &a, const BufPtr &D, int64_t k, const hx_keyset &keys);
+    void check_same(const Cts &a, const Cts &b);
+
+    // hybrid key switching pieces
+    BufPtr modup(const View &d, int B, int limbs);
+    Cts ks_finish(const BufPtr &D, const View &dnt, int B, int limbs, const SwitchKey &key, uint64_t g,
+                  const View &add, int add_mask, uint64_t add_g);
+    void ntt_inplace(uint64_t *p, size_t gstride, int groups, const std::vector<int> &rows_off,
+                     const std::vector<int> &rows_prime, bool inverse);
+    void ntt_oop(const uint64_t *src, size_t sgs, uint64_t *dst, size_t dgs, int groups,
+                 const std::vector<int> &src_off, const std::vector<int> &dst_off, const std::vector<int> &prime,
+                 bool inverse);
+    const SwitchKey &rot_key(const hx_keyset &ks, uint64_t g);
+};
+
+Scalars scalars_for(const hx_context &ctx, int limbs, int64_t c);
+void upload_plaintext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst_mont);
+
+// ---- keys / encryption (keys.cu) ---------------------------------------------
+void keygen(hx_context &ctx, hx_keyset &ks, int n_parties, uint64_t seed, cudaStream_t s);
+void add_rotation_keys(hx_context &ctx, hx_keyset &ks, const std::vector<int64_t> &steps, cudaStream_t s);
+Cts encrypt_coeffs(hx_context &ctx, const hx_keyset &ks, const int64_t *m, double scale, int limbs, uint64_t seed,
+                   uint32_t tag, uint32_t index, cudaStream_t s);
+// centered coefficients of c0 + c1 s mod q_0 for every batch entry: [B][N]
+std::vector<int64_t> decrypt_coeffs(hx_context &ctx, const hx_keyset &ks, const Cts &c, cudaStream_t s);
+
+// ---- schedules (schedules.cu) -------------------------------------------------
+hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s);
+std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs);
+Cts matmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &A, const Cts &B,
+                 cudaStream_t s);
+Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k, bool relu, bool allow_refresh,
+               uint64_t refresh_seed, cudaStream_t s);
+
+// ---- context (context.cu) -------------------------------------------------------
+void build_context(hx_context &ctx, const hx_params &p);
+void destroy_context(hx_context &ctx);
+Cts gather(hx_context &ctx, const hx_ct *const *cts, size_t count, cudaStream_t s);
+void scatter(hx_context &ctx, const Cts &b, hx_ct **out, cudaStream_t s);
+
+} // namespace hx

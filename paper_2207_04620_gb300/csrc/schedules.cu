@@ -1,0 +1,404 @@
+// Schedules of the paper's method on batched ciphertexts:
+//  * HE-LinTrans (Alg. 2) with the baby-step/giant-step split of App. B,
+//  * HE-MatMult (Alg. 3) with the multiplexer trick of App. B and the
+//    iota_beta packing of App. E, plus a depth-2 rearrangement of Steps 2-3
+//    for chains with exactly two levels above q_0,
+//  * the composite sign g_d^(k) and ReLU (Sec. 4, Alg. 5) with a host
+//    simulation of DBootstrap when the levels run out.
+#include <algorithm>
+#include <cmath>
+
+#include "runtime.h"
+
+namespace hx {
+
+namespace {
+
+int baby_steps(int h)
+{
+    int lg = 0;
+    while ((1 << lg) < h) lg++;
+    return 1 << ((lg + 1) / 2);  // 2^ceil(log2(h)/2)
+}
+
+int floordiv(int a, int b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+int posmod(int a, int b) { return ((a % b) + b) % b; }
+
+// diagonal vectors of Sec. 3.6 (logical length h^2)
+std::vector<int32_t> diag_mu(int h, int k)
+{
+    std::vector<int32_t> v(h * h, 0);
+    for (int t = 0; t < h * h; t++) {
+        if (k >= 0)
+            v[t] = (t - h * k >= 0 && t - h * k < h - k);
+        else
+            v[t] = (t - (h + k) * h >= -k && t - (h + k) * h < h);
+    }
+    return v;
+}
+std::vector<int32_t> diag_zeta(int h, int k)
+{
+    std::vector<int32_t> v(h * h, 0);
+    for (int t = 0; t < h * h; t++) v[t] = (t % h == k);
+    return v;
+}
+std::vector<int32_t> diag_v(int h, int k)
+{
+    std::vector<int32_t> v(h * h, 0);
+    for (int t = 0; t < h * h; t++) v[t] = ((t % h) < h - k);
+    return v;
+}
+// R(v, r): (v_r, ..., v_{n-1}, v_0, ..., v_{r-1})
+std::vector<int32_t> rot(const std::vector<int32_t> &v, int r)
+{
+    const int n = (int)v.size();
+    std::vector<int32_t> o(n);
+    for (int t = 0; t < n; t++) o[t] = v[posmod(t + r, n)];
+    return o;
+}
+
+} // namespace
+
+std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs)
+{
+    const int b = baby_steps(h);
+    const bool alg3 = limbs >= 4;
+    std::vector<int64_t> s;
+    for (int l = -h + 1; l < h; l++) {
+        s.push_back((int64_t)beta * posmod(l, b));
+        s.push_back((int64_t)beta * b * floordiv(l, b));
+    }
+    if (alg3) {
+        for (int l = 0; l < h; l++) {
+            s.push_back((int64_t)beta * h * (l % b));
+            s.push_back((int64_t)beta * h * b * (l / b));
+        }
+    } else {
+        for (int l = 1; l < h; l++) s.push_back((int64_t)beta * h * l);
+    }
+    for (int k = 1; k < h; k++) {
+        s.push_back((int64_t)beta * k);
+        s.push_back((int64_t)beta * (k - h));
+        s.push_back((int64_t)beta * h * k);
+    }
+    const int64_t n = (int64_t)beta * h * h;
+    std::vector<int64_t> out;
+    for (int64_t x : s) {
+        int64_t r = ((x % n) + n) % n;
+        if (r) out.push_back(r);
+    }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+    return out;
+}
+
+hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
+{
+    HX_CHECK(h >= 2 && (h & (h - 1)) == 0 && h * h <= ctx.N / 2, HX_EINVAL, "h must be a power of two with h^2 <= N/2");
+    HX_CHECK(limbs <= ctx.n_q, HX_EINVAL, "level above the chain");
+    HX_CHECK(limbs >= 3, HX_ELEVEL, "HE-MatMult needs at least 3 limbs");
+    std::unique_ptr<hx_matmul_plan> p(new hx_matmul_plan);
+    p->ctx = &ctx;
+    p->h = h;
+    p->limbs = limbs;
+    p->beta = ctx.N / 2 / (h * h);
+    p->b = baby_steps(h);
+    p->alg3 = limbs >= 4;
+    const int b = p->b;
+    auto add = [&](int kind, int idx, std::vector<int32_t> vec, int lm) {
+        hx_matmul_plan::Mask m;
+        m.kind = kind;
+        m.index = idx;
+        m.limbs = lm;
+        m.scale = (double)ctx.primes[lm - 1];
+        m.vec = std::move(vec);
+        p->index[{kind, idx}] = (int)p->masks.size();
+        p->masks.push_back(std::move(m));
+    };
+    for (int l = -h + 1; l < h; l++) add(0, l, rot(diag_mu(h, l), -b * floordiv(l, b)), limbs);
+    for (int l = 0; l < h; l++)
+        add(1, l, p->alg3 ? rot(diag_zeta(h, l), -h * b * (l / b)) : diag_zeta(h, l), limbs);
+    if (p->alg3)
+        for (int k = 1; k < h; k++) add(2, k, rot(diag_v(h, k), -k), limbs - 1);
+    // encode every mask with the library's encoder (expanded over the beta packed matrices)
+    std::vector<double> slots(ctx.N / 2);
+    std::vector<int64_t> coeffs(ctx.N);
+    for (auto &m : p->masks) {
+        for (int t = 0; t < h * h; t++)
+            for (int j = 0; j < p->beta; j++) slots[(size_t)t * p->beta + j] = m.vec[t];
+        ctx.enc->encode(slots.data(), slots.size(), m.scale, coeffs.data());
+        m.pt = std::make_shared<DevBuf>((size_t)m.limbs * ctx.N, s);
+        upload_plaintext(ctx, s, coeffs.data(), m.limbs, m.pt->p);
+    }
+    return p.release();
+}
+
+namespace {
+
+const uint64_t *mask_pt(const hx_matmul_plan &p, int kind, int idx, double *scale)
+{
+    auto it = p.index.find({kind, idx});
+    HX_CHECK(it != p.index.end(), HX_EINVAL, "missing mask");
+    *scale = p.masks[it->second].scale;
+    return p.masks[it->second].pt->p;
+}
+
+// Alg. 2 over diagonals stride*l, l in [lmin, lmax], split l = b*i + j:
+// sum_i Rot( sum_j Mul_pt(Rot(ct, stride*j), mask_l), stride*b*i ); not rescaled.
+Cts lintrans(Eval &ev, const hx_keyset &ks, const Cts &ct, int lmin, int lmax, int stride, const hx_matmul_plan &p,
+             int kind)
+{
+    const int b = p.b, beta = p.beta;
+    std::map<int, std::vector<std::pair<int, int>>> groups;
+    std::vector<int> js;
+    for (int l = lmin; l <= lmax; l++) {
+        const int i = floordiv(l, b), j = posmod(l, b);
+        groups[i].push_back({j, l});
+        if (std::find(js.begin(), js.end(), j) == js.end()) js.push_back(j);
+    }
+    std::sort(js.begin(), js.end());
+    std::vector<int64_t> steps;
+    for (int j : js) steps.push_back((int64_t)beta * stride * j);
+    std::vector<Cts> babies = ev.rotate_hoisted(ct, steps, ks);
+    std::map<int, int> jpos;
+    for (size_t k = 0; k < js.size(); k++) jpos[js[k]] = (int)k;
+    Cts acc;
+    bool have = false;
+    for (auto &kv : groups) {
+        const int i = kv.first;
+        Cts inner;
+        bool hi = false;
+        for (auto &jl : kv.second) {
+            double sc;
+            const uint64_t *pt = mask_pt(p, kind, jl.second, &sc);
+            Cts term = ev.mul_plain(babies[jpos[jl.first]], pt, sc);
+            if (!hi) {
+                inner = term;
+                hi = true;
+            } else {
+                ev.add_inplace(inner, term);
+            }
+        }
+        if (i != 0) inner = ev.rotate(inner, (int64_t)beta * stride * b * i, ks);
+        if (!have) {
+            acc = inner;
+            have = true;
+        } else {
+            ev.add_inplace(acc, inner);
+        }
+    }
+    return acc;
+}
+
+Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Cts &A, const Cts &B)
+{
+    hx_context &ctx = ev.ctx;
+    const int h = p.h, beta = p.beta;
+    Cts A0 = ev.rescale(lintrans(ev, ks, A, -h + 1, h - 1, 1, p, 0));
+    Cts B0 = ev.rescale(lintrans(ev, ks, B, 0, h - 1, h, p, 1));
+    // Step 2 (multiplexer trick): A^(k) = Rot(M_k, k) + Rot(q*A0 - M_k, k-h)
+    const uint64_t qt = ctx.primes[A0.limbs - 1];
+    Cts A0s = ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt);
+    Cts A0d = ev.drop(A0, A0.limbs - 1);
+    Cts B0d = ev.drop(B0, B0.limbs - 1);
+    // B^(k) = Rot(B0, h*k): all from one ModUp (hoisted)
+    std::vector<int64_t> bsteps;
+    for (int k = 1; k < h; k++) bsteps.push_back((int64_t)beta * h * k);
+    Cts acc = ev.tensor(A0d, B0d);
+    BufPtr DB = ev.hoist(B0d);  // one ModUp serves every B^(k)
+    for (int k = 1; k < h; k++) {
+        Cts Bk = ev.rotate_hoisted_one(B0d, DB, bsteps[k - 1], ks);
+        double sc;
+        const uint64_t *pt = mask_pt(p, 2, k, &sc);
+        Cts M = ev.mul_plain(A0, pt, sc);
+        Cts Nk = ev.add(A0s, M, true);
+        Cts X = ev.rotate(M, (int64_t)beta * k, ks);
+        ev.add_inplace(X, ev.rotate(Nk, (int64_t)beta * (k - h), ks));
+        Cts Ak = ev.rescale(X);
+        ev.tensor_acc(acc, Ak, Bk);
+    }
+    return ev.rescale(ev.relinearize(acc, ks.relin));
+}
+
+Cts matmul_depth2(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Cts &A, const Cts &B)
+{
+    const int h = p.h, beta = p.beta;
+    Cts A0 = ev.rescale(lintrans(ev, ks, A, -h + 1, h - 1, 1, p, 0));
+    std::vector<int64_t> st;
+    for (int l = 1; l < h; l++) st.push_back((int64_t)beta * h * l);
+    std::vector<Cts> Rb = ev.rotate_hoisted(B, st, ks);
+    std::vector<Cts> prefix(h + 1);  // prefix[m] = S_m = sum_{l<m} T_l
+    for (int l = 0; l < h; l++) {
+        double sc;
+        const uint64_t *pt = mask_pt(p, 1, l, &sc);
+        Cts T = ev.mul_plain(l == 0 ? B : Rb[l - 1], pt, sc);
+        prefix[l + 1] = l == 0 ? T : ev.add(prefix[l], T);
+    }
+    Rb.clear();
+    const Cts &Bfull = prefix[h];
+    Cts B0 = ev.rescale(Bfull);
+    std::vector<int64_t> ast;
+    for (int k = 1; k < h; k++) ast.push_back((int64_t)beta * k);
+    for (int k = 1; k < h; k++) ast.push_back((int64_t)beta * (k - h));
+    std::vector<Cts> RA = ev.rotate_hoisted(A0, ast, ks);
+    Cts acc = ev.tensor(A0, B0);
+    for (int k = 1; k < h; k++) {
+        Cts X = ev.rescale(prefix[h - k]);
+        Cts Y = ev.rescale(ev.add(Bfull, prefix[h - k], true));
+        ev.tensor_acc(acc, RA[k - 1], ev.rotate(X, (int64_t)beta * h * k, ks));
+        ev.tensor_acc(acc, RA[h - 1 + k - 1], ev.rotate(Y, (int64_t)beta * h * k, ks));
+    }
+    return ev.rescale(ev.relinearize(acc, ks.relin));
+}
+
+} // namespace
+
+Cts matmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &A, const Cts &B,
+                 cudaStream_t s)
+{
+    HX_CHECK(A.comps == 2 && B.comps == 2 && A.B == B.B, HX_EINVAL, "matmul needs two batches of ciphertexts");
+    HX_CHECK(A.limbs == plan.limbs && B.limbs == plan.limbs, HX_ELEVEL, "inputs are not at the plan's level");
+    HX_CHECK(A.scale == B.scale, HX_ESCALE, "inputs must share the scale");
+    Eval ev(ctx, s);
+    return plan.alg3 ? matmul_alg3(ev, ks, plan, A, B) : matmul_depth2(ev, ks, plan, A, B);
+}
+
+// ---- Sec. 4: composite sign ------------------------------------------------------
+
+namespace {
+
+int64_t binom(int n, int k)
+{
+    int64_t r = 1;
+    for (int i = 1; i <= k; i++) r = r * (n - k + i) / i;
+    return r;
+}
+
+// n_j with g_d(m) = sum_j n_j m^(2j+1) / 2^(2d-1), from
+// g_d(m) = sum_i 4^-i C(2i,i) m (1-m^2)^i
+std::vector<int64_t> g_int_coeffs(int d)
+{
+    std::vector<int64_t> n(d + 1, 0);
+    for (int j = 0; j <= d; j++) {
+        int64_t twice = 0;  // 2 * 2^(2d-1) * coefficient
+        for (int i = j; i <= d; i++)
+            twice += (j % 2 ? -1 : 1) * binom(2 * i, i) * binom(i, j) * ((int64_t)1 << (2 * d - 2 * i));
+        n[j] = twice / 2;
+    }
+    return n;
+}
+
+Cts square_rs(Eval &ev, const hx_keyset &ks, const Cts &a, const Cts &b)
+{
+    return ev.rescale(ev.relinearize(ev.tensor(a, b), ks.relin));
+}
+
+// bring ct to `target` limbs at scale target_scale, times c_real: drop to
+// target+1 limbs, multiply by round(c_real*target_scale*q_target/scale),
+// rescale; the result is declared to have target_scale
+Cts level_adjust(Eval &ev, const Cts &ct, int target, double c_real, double target_scale)
+{
+    HX_CHECK(ct.limbs > target, HX_ELEVEL, "cannot raise the level");
+    Cts x = ct.limbs > target + 1 ? ev.drop(ct, target + 1) : ct;
+    const uint64_t qt = ev.ctx.primes[target];
+    const double c = round_half_away(c_real * target_scale * (double)qt / ct.scale);
+    HX_CHECK(std::fabs(c) < 4.6e18, HX_EINVAL, "level-adjust constant too large");
+    Cts y = ev.rescale(ev.mul_int(x, (int64_t)c));
+    y.scale = target_scale;
+    return y;
+}
+
+Cts eval_g(Eval &ev, const hx_keyset &ks, const Cts &x, int d)
+{
+    const std::vector<int64_t> n = g_int_coeffs(d);
+    std::vector<Cts> y(d + 1);
+    y[1] = square_rs(ev, ks, x, x);
+    for (int j = 2; j <= d; j++) {
+        if (j % 2 == 0) {
+            y[j] = square_rs(ev, ks, y[j / 2], y[j / 2]);
+        } else {
+            const Cts &a = y[j - 1];
+            Cts y1 = y[1].limbs > a.limbs ? level_adjust(ev, y[1], a.limbs, 1.0, a.scale) : y[1];
+            y[j] = square_rs(ev, ks, a, y1);
+        }
+    }
+    int lp = y[1].limbs;
+    for (int j = 1; j <= d; j++) lp = std::min(lp, y[j].limbs);
+    double sp = 0;
+    for (int j = 1; j <= d; j++)
+        if (y[j].limbs == lp) {
+            sp = y[j].scale;
+            break;
+        }
+    Cts P;
+    for (int j = 1; j <= d; j++) {
+        Cts t = y[j].limbs > lp ? level_adjust(ev, y[j], lp, (double)n[j], sp) : ev.mul_int(y[j], n[j]);
+        if (j == 1)
+            P = t;
+        else
+            ev.add_inplace(P, t);
+    }
+    P = ev.add_const(P, (double)n[0]);
+    Cts xa = level_adjust(ev, x, lp, 1.0 / std::ldexp(1.0, 2 * d - 1), sp);
+    return square_rs(ev, ks, xa, P);
+}
+
+int g_depth(int d)
+{
+    std::vector<int> lev(d + 1, 0);
+    lev[1] = 1;
+    int mx = 1;
+    for (int j = 2; j <= d; j++) {
+        lev[j] = (j % 2 == 0) ? lev[j / 2] + 1 : std::max(lev[j - 1], lev[1]) + 1;
+        mx = std::max(mx, lev[j]);
+    }
+    return mx + 1;
+}
+
+// host simulation of DBootstrap: collective decryption, integer rescaling of
+// the plaintext coefficients to the default scale, re-encryption at the top
+Cts refresh(hx_context &ctx, const hx_keyset &ks, const Cts &ct, uint64_t seed, int counter, cudaStream_t s)
+{
+    std::vector<int64_t> poly = decrypt_coeffs(ctx, ks, ct, s);
+    const double ratio = ctx.scale / ct.scale;
+    std::vector<int64_t> m(ctx.N);
+    Eval ev(ctx, s);
+    Cts out = ev.alloc(ct.B, 2, ctx.n_q);
+    out.scale = ctx.scale;
+    for (int b = 0; b < ct.B; b++) {
+        for (int i = 0; i < ctx.N; i++) m[i] = (int64_t)round_half_away((double)poly[(size_t)b * ctx.N + i] * ratio);
+        Cts one = encrypt_coeffs(ctx, ks, m.data(), ctx.scale, ctx.n_q, seed, 1 + counter, b, s);
+        HX_CUDA(cudaMemcpyAsync(out.d + (size_t)b * out.bstride(ctx.N), one.d, sizeof(uint64_t) * one.bstride(ctx.N),
+                                cudaMemcpyDeviceToDevice, s));
+    }
+    ctx.counters[C_REFRESH] += ct.B;
+    return out;
+}
+
+} // namespace
+
+Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k, bool relu, bool allow_refresh,
+               uint64_t refresh_seed, cudaStream_t s)
+{
+    HX_CHECK(d >= 1 && d <= 4 && k >= 1 && k <= 64, HX_EINVAL, "need 1 <= d <= 4 and 1 <= k <= 64");
+    HX_CHECK(x.comps == 2, HX_EINVAL, "sign needs ciphertexts");
+    Eval ev(ctx, s);
+    const int dg = g_depth(d);
+    Cts m = x;
+    int refreshes = 0;
+    for (int it = 0; it < k; it++) {
+        const int need = dg + ((relu && it == k - 1) ? 1 : 0);
+        if (m.limbs - 1 < need) {
+            HX_CHECK(allow_refresh, HX_ELEVEL, "levels exhausted");
+            HX_CHECK(ctx.n_q - 1 >= need, HX_ELEVEL, "chain too short for one composition");
+            m = refresh(ctx, ks, m, refresh_seed, refreshes++, s);
+        }
+        m = eval_g(ev, ks, m, d);
+    }
+    if (!relu) return m;
+    Cts s1 = ev.add_const(m, 1.0);
+    Cts xa = level_adjust(ev, x, m.limbs, 0.5, m.scale);
+    return square_rs(ev, ks, xa, s1);
+}
+
+} // namespace hx

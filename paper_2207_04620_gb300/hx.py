@@ -1,0 +1,390 @@
+"""Python binding of libhx (include/hx.h): ctypes argument marshalling only.
+
+Every function keeps the C name and forwards to the CUDA library; all
+computation happens in the library's kernels.  Handles are opaque integers.
+If libhx.so has not been built the first call raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhx.so")
+_lib = None
+
+c_int, c_double, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+c_u64, c_i64, c_u32, c_vp = ctypes.c_uint64, ctypes.c_int64, ctypes.c_uint32, ctypes.c_void_p
+P_u64 = ctypes.POINTER(ctypes.c_uint64)
+P_i64 = ctypes.POINTER(ctypes.c_int64)
+P_i32 = ctypes.POINTER(ctypes.c_int32)
+P_dbl = ctypes.POINTER(ctypes.c_double)
+PP = ctypes.POINTER(c_vp)
+
+HX_MAX_Q, HX_MAX_P = 60, 6
+STATUS = {0: "HX_OK", -1: "HX_EINVAL", -2: "HX_ENOMEM", -3: "HX_ELEVEL", -4: "HX_ESCALE", -5: "HX_EKEY",
+          -6: "HX_ETIMEOUT", -7: "HX_ECUDA", -8: "HX_EPARTY"}
+COUNTERS = ["Add", "Mul_pt", "Rot", "RotHoisted", "Mul_ct", "KeySwitch", "ModUp", "Rescale", "Refresh", "launches"]
+
+
+class HxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class hx_params(ctypes.Structure):
+    _fields_ = [("log_n", c_int), ("n_q", c_int), ("q_bits", c_int * HX_MAX_Q), ("n_p", c_int),
+                ("p_bits", c_int * HX_MAX_P), ("log2_scale", c_double), ("sigma", c_double)]
+
+
+_SIGS = {
+    "hx_last_error": (ctypes.c_char_p, []),
+    "hx_context_create": (c_int, [ctypes.POINTER(hx_params), PP]),
+    "hx_context_destroy": (None, [c_vp]),
+    "hx_context_primes": (c_int, [c_vp, P_u64, c_int]),
+    "hx_context_n": (c_int, [c_vp]),
+    "hx_keygen": (c_int, [c_vp, c_int, c_u64, P_i32, c_size_t, PP]),
+    "hx_keyset_add_rotations": (c_int, [c_vp, c_vp, P_i32, c_size_t]),
+    "hx_keyset_export_switch_key": (c_i64, [c_vp, c_u64, P_u64, c_size_t]),
+    "hx_keyset_export_public_key": (c_i64, [c_vp, P_u64, c_size_t]),
+    "hx_keyset_destroy": (None, [c_vp]),
+    "hx_encode": (c_int, [c_vp, P_dbl, c_size_t, c_double, P_i64]),
+    "hx_encrypt": (c_int, [c_vp, c_vp, P_dbl, c_size_t, c_int, c_u64, PP]),
+    "hx_encrypt_coeffs": (c_int, [c_vp, c_vp, P_i64, c_double, c_int, c_u64, c_u32, c_u32, PP]),
+    "hx_decrypt": (c_int, [c_vp, c_vp, c_vp, P_dbl, c_size_t]),
+    "hx_decrypt_coeffs": (c_int, [c_vp, c_vp, c_vp, P_i64]),
+    "hx_ct_import": (c_int, [c_vp, P_u64, c_int, c_int, c_double, PP]),
+    "hx_ct_export": (c_i64, [c_vp, P_u64, c_size_t]),
+    "hx_ct_info": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), P_dbl]),
+    "hx_ct_destroy": (None, [c_vp]),
+    "hx_add": (c_int, [c_vp, c_vp, c_vp, PP, c_vp]),
+    "hx_sub": (c_int, [c_vp, c_vp, c_vp, PP, c_vp]),
+    "hx_mul_plain": (c_int, [c_vp, c_vp, P_i64, c_double, PP, c_vp]),
+    "hx_mul_int": (c_int, [c_vp, c_vp, c_i64, c_double, PP, c_vp]),
+    "hx_add_const": (c_int, [c_vp, c_vp, c_double, PP, c_vp]),
+    "hx_tensor": (c_int, [c_vp, c_vp, c_vp, PP, c_vp]),
+    "hx_relinearize": (c_int, [c_vp, c_vp, c_vp, PP, c_vp]),
+    "hx_rescale": (c_int, [c_vp, c_vp, PP, c_vp]),
+    "hx_drop": (c_int, [c_vp, c_vp, c_int, PP, c_vp]),
+    "hx_rotate": (c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, PP, c_vp]),
+    "hx_rotate_hoisted": (c_int, [c_vp, c_vp, c_vp, P_i32, c_int, PP, c_vp]),
+    "hx_ntt": (c_int, [c_vp, c_vp, c_int, c_int, P_i32, c_int, c_vp]),
+    "hx_matmul_plan_create": (c_int, [c_vp, c_int, c_int, PP]),
+    "hx_matmul_plan_num_masks": (c_int, [c_vp]),
+    "hx_matmul_plan_set_mask": (c_int, [c_vp, c_vp, c_int, P_i64]),
+    "hx_matmul_plan_destroy": (None, [c_vp]),
+    "hx_matmul_rotation_steps": (c_int, [c_vp, c_int, c_int, P_i32, c_int]),
+    "hx_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, PP, c_vp]),
+    "hx_matmul_batch": (c_int, [c_vp, c_vp, c_vp, PP, PP, c_int, c_size_t, PP, c_vp]),
+    "hx_sign_approx": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
+    "hx_sign_approx_batch": (c_int, [c_vp, c_vp, PP, c_size_t, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
+    "hx_counters": (c_int, [c_vp, P_u64, c_int]),
+    "hx_counters_reset": (None, [c_vp]),
+}
+
+
+def lib():
+    """Loads libhx.so (built by paper_2207_04620_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libhx.so is not built (run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_symbols() -> list:
+    return list(_SIGS)
+
+
+def _chk(st: int) -> int:
+    if st < 0:
+        raise HxError(st, lib().hx_last_error().decode())
+    return st
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)  # torch.cuda.Stream
+
+
+def _u64p(a):
+    return a.ctypes.data_as(P_u64)
+
+
+def _i64p(a):
+    return a.ctypes.data_as(P_i64)
+
+
+def _i32arr(xs):
+    a = np.ascontiguousarray(np.array(list(xs), dtype=np.int32))
+    return a, a.ctypes.data_as(P_i32)
+
+
+def _out():
+    return c_vp()
+
+
+# ---- context -----------------------------------------------------------------
+
+def hx_context_create(log_n: int, q_bits, p_bits, log2_scale: float, sigma: float = 3.2) -> int:
+    p = hx_params()
+    p.log_n, p.n_q, p.n_p = log_n, len(q_bits), len(p_bits)
+    for i, b in enumerate(q_bits):
+        p.q_bits[i] = b
+    for i, b in enumerate(p_bits):
+        p.p_bits[i] = b
+    p.log2_scale, p.sigma = float(log2_scale), float(sigma)
+    out = _out()
+    _chk(lib().hx_context_create(ctypes.byref(p), ctypes.byref(out)))
+    return out.value
+
+
+def hx_context_destroy(ctx: int) -> None:
+    lib().hx_context_destroy(ctx)
+
+
+def hx_context_primes(ctx: int) -> list:
+    buf = np.zeros(HX_MAX_Q + HX_MAX_P, dtype=np.uint64)
+    n = _chk(lib().hx_context_primes(ctx, _u64p(buf), buf.size))
+    return [int(x) for x in buf[:n]]
+
+
+def hx_context_n(ctx: int) -> int:
+    return _chk(lib().hx_context_n(ctx))
+
+
+# ---- keys ----------------------------------------------------------------------
+
+def hx_keygen(ctx: int, n_parties: int, seed: int, rot_steps=()) -> int:
+    arr, ptr = _i32arr(rot_steps)
+    out = _out()
+    _chk(lib().hx_keygen(ctx, n_parties, seed, ptr, arr.size, ctypes.byref(out)))
+    return out.value
+
+
+def hx_keyset_add_rotations(ctx: int, ks: int, steps) -> None:
+    arr, ptr = _i32arr(steps)
+    _chk(lib().hx_keyset_add_rotations(ctx, ks, ptr, arr.size))
+
+
+def hx_keyset_export_switch_key(ctx: int, ks: int, galois: int, dnum: int, n_all: int) -> np.ndarray:
+    n = hx_context_n(ctx)
+    buf = np.zeros(dnum * 2 * n_all * n, dtype=np.uint64)
+    _chk(lib().hx_keyset_export_switch_key(ks, galois, _u64p(buf), buf.size))
+    return buf.reshape(dnum, 2, n_all, n)
+
+
+def hx_keyset_export_public_key(ctx: int, ks: int, n_q: int) -> np.ndarray:
+    n = hx_context_n(ctx)
+    buf = np.zeros(2 * n_q * n, dtype=np.uint64)
+    _chk(lib().hx_keyset_export_public_key(ks, _u64p(buf), buf.size))
+    return buf.reshape(2, n_q, n)
+
+
+def hx_keyset_destroy(ks: int) -> None:
+    lib().hx_keyset_destroy(ks)
+
+
+# ---- encoding, encryption ---------------------------------------------------------
+
+def hx_encode(ctx: int, slots, scale: float) -> np.ndarray:
+    z = np.ascontiguousarray(np.asarray(slots, dtype=np.float64))
+    out = np.zeros(hx_context_n(ctx), dtype=np.int64)
+    _chk(lib().hx_encode(ctx, z.ctypes.data_as(P_dbl), z.size, scale, _i64p(out)))
+    return out
+
+
+def hx_encrypt(ctx: int, ks: int, slots, limbs: int = 0, seed: int = 0) -> int:
+    z = np.ascontiguousarray(np.asarray(slots, dtype=np.float64))
+    out = _out()
+    _chk(lib().hx_encrypt(ctx, ks, z.ctypes.data_as(P_dbl), z.size, limbs, seed, ctypes.byref(out)))
+    return out.value
+
+
+def hx_encrypt_coeffs(ctx: int, ks: int, coeffs, scale: float, limbs: int, seed: int, tag: int = 0,
+                      index: int = 0) -> int:
+    m = np.ascontiguousarray(np.asarray(coeffs, dtype=np.int64))
+    out = _out()
+    _chk(lib().hx_encrypt_coeffs(ctx, ks, _i64p(m), scale, limbs, seed, tag, index, ctypes.byref(out)))
+    return out.value
+
+
+def hx_decrypt(ctx: int, ks: int, ct: int, n: int | None = None) -> np.ndarray:
+    n = hx_context_n(ctx) // 2 if n is None else n
+    out = np.zeros(n, dtype=np.float64)
+    _chk(lib().hx_decrypt(ctx, ks, ct, out.ctypes.data_as(P_dbl), n))
+    return out
+
+
+def hx_decrypt_coeffs(ctx: int, ks: int, ct: int) -> np.ndarray:
+    out = np.zeros(hx_context_n(ctx), dtype=np.int64)
+    _chk(lib().hx_decrypt_coeffs(ctx, ks, ct, _i64p(out)))
+    return out
+
+
+# ---- ciphertext handles -----------------------------------------------------------
+
+def hx_ct_import(ctx: int, residues: np.ndarray, scale: float) -> int:
+    a = np.ascontiguousarray(residues, dtype=np.uint64)
+    comps, limbs, _ = a.shape
+    out = _out()
+    _chk(lib().hx_ct_import(ctx, _u64p(a), comps, limbs, scale, ctypes.byref(out)))
+    return out.value
+
+
+def hx_ct_info(ct: int):
+    c, l, s = c_int(), c_int(), c_double()
+    _chk(lib().hx_ct_info(ct, ctypes.byref(c), ctypes.byref(l), ctypes.byref(s)))
+    return c.value, l.value, s.value
+
+
+def hx_ct_export(ctx: int, ct: int) -> np.ndarray:
+    comps, limbs, _ = hx_ct_info(ct)
+    n = hx_context_n(ctx)
+    buf = np.zeros(comps * limbs * n, dtype=np.uint64)
+    _chk(lib().hx_ct_export(ct, _u64p(buf), buf.size))
+    return buf.reshape(comps, limbs, n)
+
+
+def hx_ct_destroy(ct: int) -> None:
+    lib().hx_ct_destroy(ct)
+
+
+# ---- single operations --------------------------------------------------------------
+
+def _op(name, *args, stream=None):
+    out = _out()
+    _chk(getattr(lib(), name)(*args, ctypes.byref(out), _stream(stream)))
+    return out.value
+
+
+def hx_add(ctx, a, b, stream=None):
+    return _op("hx_add", ctx, a, b, stream=stream)
+
+
+def hx_sub(ctx, a, b, stream=None):
+    return _op("hx_sub", ctx, a, b, stream=stream)
+
+
+def hx_mul_plain(ctx, a, pt_coeffs, pt_scale, stream=None):
+    m = np.ascontiguousarray(np.asarray(pt_coeffs, dtype=np.int64))
+    return _op("hx_mul_plain", ctx, a, _i64p(m), pt_scale, stream=stream)
+
+
+def hx_mul_int(ctx, a, c, new_scale=0.0, stream=None):
+    return _op("hx_mul_int", ctx, a, int(c), float(new_scale), stream=stream)
+
+
+def hx_add_const(ctx, a, value, stream=None):
+    return _op("hx_add_const", ctx, a, float(value), stream=stream)
+
+
+def hx_tensor(ctx, a, b, stream=None):
+    return _op("hx_tensor", ctx, a, b, stream=stream)
+
+
+def hx_relinearize(ctx, ks, d, stream=None):
+    return _op("hx_relinearize", ctx, ks, d, stream=stream)
+
+
+def hx_rescale(ctx, a, stream=None):
+    return _op("hx_rescale", ctx, a, stream=stream)
+
+
+def hx_drop(ctx, a, limbs, stream=None):
+    return _op("hx_drop", ctx, a, limbs, stream=stream)
+
+
+def hx_rotate(ctx, ks, a, k, stream=None):
+    return _op("hx_rotate", ctx, ks, a, int(k), stream=stream)
+
+
+def hx_rotate_hoisted(ctx, ks, a, steps, stream=None) -> list:
+    arr, ptr = _i32arr(steps)
+    outs = (c_vp * max(1, arr.size))()
+    _chk(lib().hx_rotate_hoisted(ctx, ks, a, ptr, arr.size, outs, _stream(stream)))
+    return [outs[i] for i in range(arr.size)]
+
+
+def hx_ntt(ctx: int, dev_ptr: int, n_polys: int, prime_idx, inverse: bool = False, stream=None) -> None:
+    arr, ptr = _i32arr(prime_idx)
+    _chk(lib().hx_ntt(ctx, dev_ptr, n_polys, arr.size, ptr, int(bool(inverse)), _stream(stream)))
+
+
+# ---- HE-MatMult ----------------------------------------------------------------------
+
+def hx_matmul_plan_create(ctx: int, h: int, limbs: int) -> int:
+    out = _out()
+    _chk(lib().hx_matmul_plan_create(ctx, h, limbs, ctypes.byref(out)))
+    return out.value
+
+
+def hx_matmul_plan_num_masks(plan: int) -> int:
+    return _chk(lib().hx_matmul_plan_num_masks(plan))
+
+
+def hx_matmul_plan_set_mask(ctx: int, plan: int, i: int, coeffs) -> None:
+    m = np.ascontiguousarray(np.asarray(coeffs, dtype=np.int64))
+    _chk(lib().hx_matmul_plan_set_mask(ctx, plan, i, _i64p(m)))
+
+
+def hx_matmul_plan_destroy(plan: int) -> None:
+    lib().hx_matmul_plan_destroy(plan)
+
+
+def hx_matmul_rotation_steps(ctx: int, h: int, limbs: int) -> list:
+    buf = np.zeros(4096, dtype=np.int32)
+    n = _chk(lib().hx_matmul_rotation_steps(ctx, h, limbs, buf.ctypes.data_as(P_i32), buf.size))
+    return [int(x) for x in buf[:n]]
+
+
+def hx_matmul(ctx, ks, A, B, h, stream=None) -> int:
+    return _op("hx_matmul", ctx, ks, A, B, h, stream=stream)
+
+
+def hx_matmul_batch(ctx, ks, plan, As, Bs, h, stream=None) -> list:
+    n = len(As)
+    a = (c_vp * n)(*As)
+    b = (c_vp * n)(*Bs)
+    outs = (c_vp * n)()
+    _chk(lib().hx_matmul_batch(ctx, ks, plan, a, b, h, n, outs, _stream(stream)))
+    return [outs[i] for i in range(n)]
+
+
+# ---- sign / ReLU -------------------------------------------------------------------
+
+def hx_sign_approx(ctx, ks, x, d, k, relu=False, allow_refresh=True, refresh_seed=0, stream=None) -> int:
+    return _op("hx_sign_approx", ctx, ks, x, d, k, int(relu), int(allow_refresh), refresh_seed, stream=stream)
+
+
+def hx_sign_approx_batch(ctx, ks, xs, d, k, relu=False, allow_refresh=True, refresh_seed=0, stream=None) -> list:
+    n = len(xs)
+    a = (c_vp * n)(*xs)
+    outs = (c_vp * n)()
+    _chk(lib().hx_sign_approx_batch(ctx, ks, a, n, d, k, int(relu), int(allow_refresh), refresh_seed, outs,
+                                    _stream(stream)))
+    return [outs[i] for i in range(n)]
+
+
+# ---- counters ------------------------------------------------------------------------
+
+def hx_counters(ctx: int) -> dict:
+    buf = np.zeros(16, dtype=np.uint64)
+    n = _chk(lib().hx_counters(ctx, _u64p(buf), buf.size))
+    return {COUNTERS[i]: int(buf[i]) for i in range(n)}
+
+
+def hx_counters_reset(ctx: int) -> None:
+    lib().hx_counters_reset(ctx)

@@ -1,0 +1,327 @@
+"""GPU parity: the CUDA library, called through its C ABI, against the oracle
+element by element (bit-exact residues), and decrypted results against FP64."""
+import numpy as np
+import pytest
+
+from oracle import ckks as C
+from oracle import hercules as Hc
+from paper_2207_04620_gb300 import hx, workloads
+
+from hxpair import PARAMS, Pair
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2207_04620_gb300 import build
+
+    build.build()
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+@pytest.fixture(scope="module")
+def cfg0():
+    pr = Pair("cfg0", rot_steps=[1, 3, -5, 64, 200])
+    yield pr
+    pr.close()
+
+
+@pytest.fixture(scope="module")
+def alg3():
+    pr = Pair("alg3", n_parties=3, rot_steps=[1, 7, -2])
+    yield pr
+    pr.close()
+
+
+# ---- a1: NTT -----------------------------------------------------------------------
+
+@pytest.mark.parametrize("log_n", [11, 12, 13, 14, 15, 16])
+def test_ntt_bit_exact(log_n):
+    import torch
+
+    octx = C.Context(log_n, [60, 45, 40], [61], 40)
+    ctx = hx.hx_context_create(log_n, [60, 45, 40], [61], 40)
+    try:
+        primes = octx.q + octx.p
+        n_polys = 3
+        x = workloads.residues(log_n, primes, n_polys, octx.N)
+        want_f = octx.ntt(x, primes * n_polys)
+        dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
+        hx.hx_ntt(ctx, dev.data_ptr(), n_polys, [0, 1, 2, 3], inverse=False)
+        torch.cuda.synchronize()
+        got = dev.cpu().numpy().view(np.uint64)
+        assert np.array_equal(got, want_f)
+        hx.hx_ntt(ctx, dev.data_ptr(), n_polys, [0, 1, 2, 3], inverse=True)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy().view(np.uint64), x)
+        # inverse on independent data
+        want_i = octx.intt(x, primes * n_polys)
+        dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
+        hx.hx_ntt(ctx, dev.data_ptr(), n_polys, [0, 1, 2, 3], inverse=True)
+        torch.cuda.synchronize()
+        assert np.array_equal(dev.cpu().numpy().view(np.uint64), want_i)
+    finally:
+        hx.hx_context_destroy(ctx)
+
+
+def test_ntt_edge_cases(cfg0):
+    import torch
+
+    # zero polynomials, the maximum residue q-1 everywhere, and an empty batch
+    q = cfg0.octx.q
+    x = np.stack([np.zeros(cfg0.N, dtype=np.uint64), np.full(cfg0.N, q[1] - 1, dtype=np.uint64)])
+    dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
+    hx.hx_ntt(cfg0.ctx, dev.data_ptr(), 1, [0, 1])
+    hx.hx_ntt(cfg0.ctx, dev.data_ptr(), 0, [0, 1])
+    torch.cuda.synchronize()
+    assert np.array_equal(dev.cpu().numpy().view(np.uint64), cfg0.octx.ntt(x, [q[0], q[1]]))
+    with pytest.raises(hx.HxError):
+        hx.hx_ntt(cfg0.ctx, dev.data_ptr(), 1, [0, 99])
+
+
+# ---- keys, encryption, decryption --------------------------------------------------
+
+def test_keygen_bit_exact(cfg0):
+    o, ctx = cfg0.oks, cfg0.ctx
+    pk = hx.hx_keyset_export_public_key(ctx, cfg0.ks, cfg0.octx.n_q)
+    assert np.array_equal(pk[0], o.pk_b) and np.array_equal(pk[1], o.pk_a)
+    n_all = cfg0.octx.n_q + cfg0.octx.K
+    rk = hx.hx_keyset_export_switch_key(ctx, cfg0.ks, 0, cfg0.octx.dnum, n_all)
+    assert np.array_equal(rk[:, 0], o.relin.b) and np.array_equal(rk[:, 1], o.relin.a)
+    for g, key in o.rot.items():
+        k = hx.hx_keyset_export_switch_key(ctx, cfg0.ks, g, cfg0.octx.dnum, n_all)
+        assert np.array_equal(k[:, 0], key.b) and np.array_equal(k[:, 1], key.a)
+
+
+def test_encrypt_and_decrypt_bit_exact(alg3):
+    z = workloads.sign_inputs(5, alg3.octx.S)
+    m = C.encode_real(alg3.N, z, alg3.octx.scale)
+    for limbs, tag, index in ((5, 0, 0), (3, 2, 7)):
+        want = C.encrypt_coeffs(alg3.octx, alg3.oks, m, alg3.octx.scale, limbs, 99, tag, index)
+        h = hx.hx_encrypt_coeffs(alg3.ctx, alg3.ks, m, alg3.octx.scale, limbs, 99, tag, index)
+        assert alg3.same(h, want)
+        assert np.array_equal(hx.hx_decrypt_coeffs(alg3.ctx, alg3.ks, h), C.decrypt_poly(alg3.octx, alg3.oks, want))
+        hx.hx_ct_destroy(h)
+
+
+def test_library_encoder_matches_oracle_encoder(cfg0):
+    z = workloads.sign_inputs(6, cfg0.octx.S)
+    a = hx.hx_encode(cfg0.ctx, z, 2.0 ** 40)
+    b = C.encode_real(cfg0.N, z, 2.0 ** 40)
+    # different FFT orderings on the two sides: rounding may differ by one unit
+    assert np.abs(a - b).max() <= 1 and np.mean(a == b) > 0.99
+
+
+def test_encrypt_decrypt_roundtrip_library(cfg0):
+    z = workloads.sign_inputs(7, cfg0.octx.S)
+    h = hx.hx_encrypt(cfg0.ctx, cfg0.ks, z, 0, 42)
+    # fresh noise v*e + e0 + e1*s: |coeff| < 6 sigma (1 + 2 n_parties sqrt(N)), slots add sqrt(N)
+    n = cfg0.N
+    bound = 6 * 3.2 * (1 + 2 * cfg0.n_parties * np.sqrt(n)) * np.sqrt(n) / 2.0 ** 40
+    assert np.abs(hx.hx_decrypt(cfg0.ctx, cfg0.ks, h) - z).max() < bound
+    hx.hx_ct_destroy(h)
+
+
+# ---- a2-a5: evaluation primitives --------------------------------------------------
+
+def test_evaluation_primitives_bit_exact(alg3):
+    pr, octx, ctx = alg3, alg3.octx, alg3.ctx
+    ev = C.Evaluator(octx, pr.oks)
+    z, w = workloads.sign_inputs(1, octx.S), workloads.sign_inputs(2, octx.S)
+    A, B = pr.encrypt(z, 11), pr.encrypt(w, 12)
+    a, b = pr.to_lib(A), pr.to_lib(B)
+    handles = []
+
+    def chk(h, want):
+        handles.append(h)
+        assert pr.same(h, want)
+        return h
+
+    chk(hx.hx_add(ctx, a, b), ev.add(A, B))
+    chk(hx.hx_sub(ctx, a, b), ev.sub(A, B))
+    pt = C.encode_real(octx.N, w, float(octx.q[4]))
+    ptn = octx.ntt(octx.signed_to_rows(pt, octx.q), octx.q)
+    chk(hx.hx_mul_plain(ctx, a, pt, float(octx.q[4])), ev.mul_plain(A, ptn, float(octx.q[4])))
+    for c in (3, -7, int(octx.q[2]), -(1 << 40) - 5):
+        chk(hx.hx_mul_int(ctx, a, c), ev.mul_int(A, c))
+    chk(hx.hx_add_const(ctx, a, -0.375), ev.add_const(A, -0.375))
+    T = ev.tensor(A, B)
+    t = chk(hx.hx_tensor(ctx, a, b), T)
+    R = ev.relinearize(T)
+    r = chk(hx.hx_relinearize(ctx, pr.ks, t), R)
+    chk(hx.hx_rescale(ctx, r), ev.rescale(R))
+    chk(hx.hx_rescale(ctx, t), ev.rescale(T))          # 3-component rescale
+    chk(hx.hx_drop(ctx, a, 2), ev.drop(A, 2))
+    for k in (1, 7, -2, 0):
+        chk(hx.hx_rotate(ctx, pr.ks, a, k), ev.rotate(A, k))
+    hs = hx.hx_rotate_hoisted(ctx, pr.ks, a, [1, 7, -2])
+    for h_, W in zip(hs, ev.rotate_hoisted(A, [1, 7, -2])):
+        chk(h_, W)
+    # the same operations one level lower (partial last digit of the gadget)
+    A3, a3 = ev.drop(A, 3), hx.hx_drop(ctx, a, 3)
+    handles.append(a3)
+    chk(hx.hx_rotate(ctx, pr.ks, a3, 7), ev.rotate(A3, 7))
+    chk(hx.hx_relinearize(ctx, pr.ks, hx.hx_tensor(ctx, a3, a3)), ev.relinearize(ev.tensor(A3, A3)))
+    for h_ in handles + [a, b]:
+        hx.hx_ct_destroy(h_)
+
+
+def test_error_statuses(cfg0):
+    ctx = cfg0.ctx
+    a = cfg0.to_lib(cfg0.encrypt(np.ones(4), 1))
+    with pytest.raises(hx.HxError) as e:
+        hx.hx_rotate(ctx, cfg0.ks, a, 2)  # no key for 2
+    assert e.value.code == -5
+    b = hx.hx_mul_int(ctx, a, 2, new_scale=3.0)
+    with pytest.raises(hx.HxError) as e:
+        hx.hx_add(ctx, a, b)
+    assert e.value.code == -4
+    one = hx.hx_drop(ctx, a, 1)
+    with pytest.raises(hx.HxError) as e:
+        hx.hx_rescale(ctx, one)
+    assert e.value.code == -3
+    with pytest.raises(hx.HxError) as e:
+        hx.hx_matmul(ctx, cfg0.ks, one, one, 16)
+    assert e.value.code == -3
+    with pytest.raises(hx.HxError):
+        hx.hx_matmul_plan_create(ctx, 12, 3)    # h not a power of two
+    for h_ in (a, b, one):
+        hx.hx_ct_destroy(h_)
+
+
+# ---- a6-a7: HE-MatMult ----------------------------------------------------------------
+
+def _matmul_case(name, h, seeds, count):
+    p = PARAMS[name]
+    limbs = len(p["q_bits"])
+    beta = (1 << p["log_n"]) // 2 // (h * h)
+    steps = Hc.matmul_rotation_steps(h, beta, limbs)
+    pr = Pair(name, rot_steps=steps)
+    assert hx.hx_matmul_rotation_steps(pr.ctx, h, limbs) == steps
+    return pr, beta, limbs
+
+
+@pytest.mark.parametrize("name,h", [("cfg0", 16), ("alg3", 8), ("alg3", 32)])
+def test_matmul_bit_exact_and_accurate(name, h):
+    pr, beta, limbs = _matmul_case(name, h, 0, 2)
+    try:
+        octx = pr.octx
+        masks = Hc.MaskProvider(octx, h, limbs)
+        plan = hx.hx_matmul_plan_create(pr.ctx, h, limbs)
+        assert hx.hx_matmul_plan_num_masks(plan) == len(masks.entries)
+        for i in range(len(masks.entries)):
+            hx.hx_matmul_plan_set_mask(pr.ctx, plan, i, masks.coeffs(i))
+        count = 2
+        mats_a = [workloads.matrices(10 + i, beta, h) for i in range(count)]
+        mats_b = [workloads.matrices(20 + i, beta, h) for i in range(count)]
+        A = [pr.encrypt(workloads.pack(m, h, beta), 30 + i) for i, m in enumerate(mats_a)]
+        B = [pr.encrypt(workloads.pack(m, h, beta), 40 + i) for i, m in enumerate(mats_b)]
+        outs = hx.hx_matmul_batch(pr.ctx, pr.ks, plan, [pr.to_lib(x) for x in A], [pr.to_lib(x) for x in B], h)
+        ev = C.Evaluator(octx, pr.oks)
+        for i in range(count):
+            want = Hc.matmul(ev, A[i], B[i], h, masks)
+            assert pr.same(outs[i], want)
+            got = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, outs[i]), h, beta)
+            err = max(np.abs(g - a @ b).max() for g, a, b in zip(got, mats_a[i], mats_b[i]))
+            assert err <= 2 ** -20, err
+        hx.hx_matmul_plan_destroy(plan)
+    finally:
+        pr.close()
+
+
+def test_matmul_library_masks_end_to_end():
+    """The product path: library encryption, library masks, library decryption;
+    config 0 (N=2^12, h=16, one product with the other packed slots zero)."""
+    pr, beta, limbs = _matmul_case("cfg0", 16, 0, 1)
+    try:
+        A = workloads.matrices(0, 1, 16)
+        B = workloads.matrices(1, 1, 16)
+        a = hx.hx_encrypt(pr.ctx, pr.ks, workloads.pack(A, 16, beta), 0, 5)
+        b = hx.hx_encrypt(pr.ctx, pr.ks, workloads.pack(B, 16, beta), 0, 6)
+        out = hx.hx_matmul(pr.ctx, pr.ks, a, b, 16)
+        got = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, out), 16, beta)
+        assert np.abs(got[0] - A[0] @ B[0]).max() <= 2 ** -20
+        assert all(np.abs(g).max() <= 2 ** -20 for g in got[1:])
+    finally:
+        pr.close()
+
+
+def test_matmul_batched_equals_one_at_a_time():
+    pr, beta, limbs = _matmul_case("alg3", 8, 0, 3)
+    try:
+        h = 8
+        cts_a = [hx.hx_encrypt(pr.ctx, pr.ks, workloads.pack(workloads.matrices(i, beta, h), h, beta), 0, i)
+                 for i in range(3)]
+        cts_b = [hx.hx_encrypt(pr.ctx, pr.ks, workloads.pack(workloads.matrices(9 + i, beta, h), h, beta), 0, 9 + i)
+                 for i in range(3)]
+        batched = hx.hx_matmul_batch(pr.ctx, pr.ks, 0, cts_a, cts_b, h)
+        for i in range(3):
+            single = hx.hx_matmul(pr.ctx, pr.ks, cts_a[i], cts_b[i], h)
+            assert np.array_equal(hx.hx_ct_export(pr.ctx, single), hx.hx_ct_export(pr.ctx, batched[i]))
+    finally:
+        pr.close()
+
+
+@pytest.mark.slow
+def test_matmul_config1_bit_exact():
+    """Config 1 shape: N=2^14, 8 limbs, h=64 (beta=2), one ciphertext pair."""
+    pr, beta, limbs = _matmul_case("cfg1", 64, 0, 1)
+    try:
+        h = 64
+        masks = Hc.MaskProvider(pr.octx, h, limbs)
+        plan = hx.hx_matmul_plan_create(pr.ctx, h, limbs)
+        for i in range(len(masks.entries)):
+            hx.hx_matmul_plan_set_mask(pr.ctx, plan, i, masks.coeffs(i))
+        ma, mb = workloads.matrices(1, beta, h), workloads.matrices(2, beta, h)
+        A, B = pr.encrypt(workloads.pack(ma, h, beta), 3), pr.encrypt(workloads.pack(mb, h, beta), 4)
+        out = hx.hx_matmul_batch(pr.ctx, pr.ks, plan, [pr.to_lib(A)], [pr.to_lib(B)], h)[0]
+        want = Hc.matmul(C.Evaluator(pr.octx, pr.oks), A, B, h, masks)
+        assert pr.same(out, want)
+        got = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, out), h, beta)
+        assert max(np.abs(g - a @ b).max() for g, a, b in zip(got, ma, mb)) <= 2 ** -18
+    finally:
+        pr.close()
+
+
+# ---- a8: composite sign and ReLU ------------------------------------------------------
+
+@pytest.mark.parametrize("relu", [False, True])
+def test_sign_bit_exact_with_refresh(relu):
+    pr = Pair("sign")
+    try:
+        octx = pr.octx
+        xs = [workloads.sign_inputs(50 + i, octx.S) for i in range(2)]
+        cts = [pr.encrypt(x, 60 + i) for i, x in enumerate(xs)]
+        outs = hx.hx_sign_approx_batch(pr.ctx, pr.ks, [pr.to_lib(c) for c in cts], 4, 8, relu=relu,
+                                       allow_refresh=True, refresh_seed=777)
+        for i in range(2):
+            ev = C.Evaluator(octx, pr.oks)
+            want = Hc.sign_approx(ev, cts[i], 4, 8, relu=relu, refresh_seed=777, index=i)
+            assert ev.counts["Refresh"] == 2
+            assert pr.same(outs[i], want)
+            got = hx.hx_decrypt(pr.ctx, pr.ks, outs[i])
+            ref = Hc.g_iter(4, 8, xs[i])
+            ref = xs[i] * (1 + ref) / 2 if relu else ref
+            assert np.abs(got - ref).max() < 2 ** -18
+        with pytest.raises(hx.HxError) as e:
+            hx.hx_sign_approx(pr.ctx, pr.ks, pr.to_lib(cts[0]), 4, 8, allow_refresh=False)
+        assert e.value.code == -3
+    finally:
+        pr.close()
+
+
+def test_sign_degrees_1_to_4_single_composition():
+    pr = Pair("sign")
+    try:
+        x = workloads.sign_inputs(3, pr.octx.S)
+        ct = pr.encrypt(x, 4)
+        for d in (1, 2, 3, 4):
+            ev = C.Evaluator(pr.octx, pr.oks)
+            want = Hc.sign_approx(ev, ct, d, 1)
+            h = hx.hx_sign_approx(pr.ctx, pr.ks, pr.to_lib(ct), d, 1, allow_refresh=False)
+            assert pr.same(h, want)
+    finally:
+        pr.close()
