@@ -1,0 +1,411 @@
+"""Benchmark: encrypted 64x64 matrix products per second (the paper's packed
+O(h)-rotation HE-MatMult, Alg. 3 with App. B/E) on one GB300, batched.
+
+Workload (one step): 32 independent 64x64 FP64 products, packed two per
+ciphertext pair (beta = 2), i.e. 16 ciphertext pairs in one batched call;
+CKKS N = 2^14, Q = 1x60 + 7x45 bits, P = 2x60 bits, scale 2^45, matrix
+entries uniform in [-1, 1] from fixed seeds.  Prints one JSON line.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hx|reference]
+
+--impl reference times the CPU oracle (oracle/) on the host cores on the
+same workload, one ciphertext pair (two products) per step.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+LOG_N, Q_BITS, P_BITS, LOG2_SCALE = 14, [60] + [45] * 7, [60, 60], 45
+H, PAIRS = 64, 16
+N_SLOTS = (1 << LOG_N) // 2
+BETA = N_SLOTS // (H * H)
+PRODUCTS = PAIRS * BETA
+METRIC = "encrypted 64x64 matmuls/s (batched HE-MatMult, CKKS N=2^14)"
+WORKLOAD = ("cfg1: %d independent 64x64 products per step = %d ciphertext pairs x beta=%d packed products; "
+            "CKKS N=2^14, Q=1x60+7x45 bit, P=2x60 bit, scale 2^45, entries U[-1,1] seeded" % (PRODUCTS, PAIRS, BETA))
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def sha_of(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.proc = None
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if uuid:
+            cmd[1:1] = ["-i", uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- CPU oracle (baseline leg and reference arm) -----------------------------------------
+
+def oracle_setup():
+    from oracle import ckks as C
+    from oracle import hercules as Hc
+    from paper_2207_04620_gb300 import workloads
+
+    octx = C.Context(LOG_N, Q_BITS, P_BITS, LOG2_SCALE)
+    steps = Hc.matmul_rotation_steps(H, BETA, len(Q_BITS))
+    oks = C.keygen(octx, 2, 2024, rot_steps=steps)
+    masks = Hc.MaskProvider(octx, H, len(Q_BITS))
+    for i in range(len(masks.entries)):
+        masks.coeffs(i)
+    a = C.encrypt(octx, oks, workloads.pack(workloads.matrices(100, BETA, H), H, BETA), 1)
+    b = C.encrypt(octx, oks, workloads.pack(workloads.matrices(200, BETA, H), H, BETA), 2)
+    return octx, oks, masks, a, b
+
+
+def oracle_step(state):
+    from oracle import ckks as C
+    from oracle import hercules as Hc
+
+    octx, oks, masks, a, b = state
+    t0 = time.perf_counter()
+    Hc.matmul(C.Evaluator(octx, oks), a, b, H, masks)
+    return time.perf_counter() - t0
+
+
+def cpu_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    state = oracle_setup()
+    for _ in range(args.warmup):
+        oracle_step(state)
+    ts = [oracle_step(state) for _ in range(args.steps)]
+    t = sum(ts) / len(ts)
+    value = BETA / t
+    sample = "one ciphertext pair (%d packed 64x64 products) per step through the oracle's full Alg. 3 schedule" % BETA
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matmul/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "matmul/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "matmul/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- GPU arm ----------------------------------------------------------------------------
+
+def run_hx(args, world, rank, local):
+    import torch
+
+    from paper_2207_04620_gb300 import hx, workloads
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if rank == 0:
+        import __graft_entry__
+
+        __graft_entry__.build()
+    barrier(world)
+    stream = torch.cuda.current_stream()
+    ctx = hx.hx_context_create(LOG_N, Q_BITS, P_BITS, LOG2_SCALE)
+    limbs = len(Q_BITS)
+    steps = hx.hx_matmul_rotation_steps(ctx, H, limbs)
+    ks = hx.hx_keygen(ctx, 2, 2024 + rank, steps)
+    plan = hx.hx_matmul_plan_create(ctx, H, limbs)
+    mats_a = [workloads.matrices(1000 * rank + 2 * i, BETA, H) for i in range(PAIRS)]
+    mats_b = [workloads.matrices(1000 * rank + 2 * i + 1, BETA, H) for i in range(PAIRS)]
+    A = [hx.hx_encrypt(ctx, ks, workloads.pack(m, H, BETA), 0, 10 + i) for i, m in enumerate(mats_a)]
+    B = [hx.hx_encrypt(ctx, ks, workloads.pack(m, H, BETA), 0, 50 + i) for i, m in enumerate(mats_b)]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step():
+        outs = hx.hx_matmul_batch(ctx, ks, plan, A, B, H, stream=stream)
+        return outs
+
+    def drop(outs):
+        for o in outs:
+            hx.hx_ct_destroy(o)
+
+    props = torch.cuda.get_device_properties(dev)
+    sampler = ClockSampler(getattr(props, "uuid", None) and "GPU-" + str(props.uuid))
+    for _ in range(args.warmup):
+        drop(step())
+    torch.cuda.synchronize()
+    # accuracy of one output pair against FP64
+    outs = step()
+    got = workloads.unpack(hx.hx_decrypt(ctx, ks, outs[0]), H, BETA)
+    max_err = float(max(np.abs(g - a @ b).max() for g, a, b in zip(got, mats_a[0], mats_b[0])))
+    drop(outs)
+
+    # timed region: events on the launching stream, L2 flushed between steps
+    c0 = hx.hx_counters(ctx)
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier(world)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("timed")
+        e0.record(stream)
+        outs = step()
+        e1.record(stream)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        drop(outs)
+    c1 = hx.hx_counters(ctx)
+    clocks = sampler.stop()
+    ms = sum(times) / len(times)
+    ms_max = max_over_ranks(ms, world)
+    value = PRODUCTS * world / (ms_max / 1e3)
+    launches = (c1["launches"] - c0["launches"])
+
+    # live per-kernel timing (profiling pass over the same step, events on the launching stream)
+    hx.hx_profile_enable(ctx, True)
+    flush.zero_()
+    torch.cuda.synchronize()
+    drop(step())
+    prof = hx.hx_profile_read(ctx)
+    hx.hx_profile_enable(ctx, False)
+    total_ms = sum(v[1] for v in prof.values())
+    shares = {k: round(v[1] / total_ms, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
+    dom = max(prof, key=lambda k: prof[k][1])
+    n_launch, dom_ms, dom_bytes = prof[dom]
+    achieved = dom_bytes / (dom_ms / 1e3) / 1e9
+    peak, peak_kind = peaks()
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tfile):
+        with open(tfile) as f:
+            tj = json.load(f)
+        ent = tj.get(dom)
+        if ent and ent.get("kernels_sha") == sha_of(os.path.join(ROOT, "paper_2207_04620_gb300", "csrc", "kernels.cu")):
+            # captured on a smaller launch of the same kernel; traffic grows with the residues processed
+            traffic = round(ent["dram_bytes_per_alg_byte"] * dom_bytes / n_launch)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                "launches": n_launch, "avg_launch_us": round(dom_ms / n_launch * 1e3, 2),
+                "alg_bytes_per_launch": dom_bytes / n_launch}
+
+    # end to end through the C ABI with host buffers: H2D of the step's input
+    # ciphertexts from pinned memory, the batched product, D2H of the results
+    host_a = [torch.from_numpy(hx.hx_ct_export(ctx, x).view(np.int64)).pin_memory() for x in A]
+    host_b = [torch.from_numpy(hx.hx_ct_export(ctx, x).view(np.int64)).pin_memory() for x in B]
+    scale = hx.hx_ct_info(A[0])[2]
+    h2d = sum(t.numel() * 8 for t in host_a + host_b)
+    e2e_t, d2h = [], 0
+    for it in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        ia = [hx.hx_ct_import(ctx, t.numpy().view(np.uint64), scale) for t in host_a]
+        ib = [hx.hx_ct_import(ctx, t.numpy().view(np.uint64), scale) for t in host_b]
+        outs = hx.hx_matmul_batch(ctx, ks, plan, ia, ib, H, stream=stream)
+        res = [hx.hx_ct_export(ctx, o) for o in outs]
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+        d2h = sum(r.nbytes for r in res)
+        drop(outs + ia + ib)
+    e2e_s = max_over_ranks(sum(e2e_t) / len(e2e_t), world)
+
+    # one launch sequence per product pair (no batching) on the same GPU
+    per_op_pairs = min(args.per_op_pairs, PAIRS)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(per_op_pairs):
+        o = hx.hx_matmul(ctx, ks, A[i], B[i], H, stream=stream)
+        torch.cuda.synchronize()
+        hx.hx_ct_destroy(o)
+    per_op = per_op_pairs * BETA / (time.perf_counter() - t0)
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": round(value, 2), "unit": "matmul/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": round(ms_max, 3), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "parallelism": "replicas only (one independent batch per GPU)",
+                           "l2": "flushed between timed steps (512 MB write outside the events)",
+                           "per_step_launch": "one hx_matmul_batch C-ABI call"},
+                "e2e": {"value": round(PRODUCTS * world / e2e_s, 2), "unit": "matmul/s",
+                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+                "gpu_launches": launches,
+                "clocks": clocks,
+                "roofline": roofline,
+                "kernel_shares": shares,
+                "per_op": {"value": round(per_op, 2), "unit": "matmul/s",
+                           "what": "hx_matmul on one ciphertext pair per call, %d pairs, synchronised" % per_op_pairs},
+                "accuracy": {"max_abs_err_vs_fp64": max_err, "bound": 2.0 ** -18}}
+    hx.hx_matmul_plan_destroy(plan)
+    for x in A + B:
+        hx.hx_ct_destroy(x)
+    hx.hx_keyset_destroy(ks)
+    hx.hx_context_destroy(ctx)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        state = oracle_setup()
+        t = oracle_step(state)
+        line["cpu_baseline"] = {"value": round(BETA / t, 4), "unit": "matmul/s", "cores": cpu_cores(),
+                                "kind": "oracle",
+                                "sample": "one ciphertext pair (%d packed products) through the oracle's Alg. 3, "
+                                          "%.1f s" % (BETA, t)}
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+def run_micro(args):
+    """NTT alone: forward then inverse transform of `rows` limbs of one ring
+    degree, in place, timed with CUDA events.  Algorithmic traffic: one read
+    and one write of every residue per transform (16 B per coefficient)."""
+    import torch
+
+    from paper_2207_04620_gb300 import hx, workloads
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    log_n = args.log_n
+    ctx = hx.hx_context_create(log_n, Q_BITS, P_BITS, LOG2_SCALE)
+    primes = hx.hx_context_primes(ctx)
+    n = 1 << log_n
+    rows = args.rows
+    per = len(primes)
+    polys = max(1, rows // per)
+    x = torch.from_numpy(workloads.residues(7, primes, polys, n).view(np.int64)).cuda()
+    stream = torch.cuda.current_stream()
+    idx = list(range(per))
+    for _ in range(args.warmup):
+        hx.hx_ntt(ctx, x.data_ptr(), polys, idx, False, stream)
+        hx.hx_ntt(ctx, x.data_ptr(), polys, idx, True, stream)
+    torch.cuda.synchronize()
+    fw, iv = [], []
+    for _ in range(args.steps):
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record(stream)
+        hx.hx_ntt(ctx, x.data_ptr(), polys, idx, False, stream)
+        e[1].record(stream)
+        hx.hx_ntt(ctx, x.data_ptr(), polys, idx, True, stream)
+        e[2].record(stream)
+        torch.cuda.synchronize()
+        fw.append(e[0].elapsed_time(e[1]))
+        iv.append(e[1].elapsed_time(e[2]))
+    byt = 16.0 * polys * per * n
+    peak, kind = peaks()
+    res = {"micro": "ntt", "log_n": log_n, "rows": polys * per, "bytes_per_transform": byt,
+           "fwd_ms": statistics.median(fw), "inv_ms": statistics.median(iv),
+           "fwd_gbs": byt / statistics.median(fw) / 1e6, "inv_gbs": byt / statistics.median(iv) / 1e6,
+           "peak_gbs": peak, "peak_kind": kind}
+    res["fwd_frac"] = res["fwd_gbs"] / peak
+    res["inv_frac"] = res["inv_gbs"] / peak
+    print(json.dumps(res), flush=True)
+    hx.hx_context_destroy(ctx)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--micro", choices=["ntt"], default=None)
+    ap.add_argument("--log-n", type=int, default=14)
+    ap.add_argument("--rows", type=int, default=1600)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hx", choices=["hx", "reference"])
+    ap.add_argument("--per-op-pairs", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.micro:
+        return run_micro(args)
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_hx(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -203,6 +203,17 @@ hx_status hx_sign_approx_batch(hx_context *ctx, const hx_keyset *ks, const hx_ct
 int hx_counters(const hx_context *ctx, uint64_t *out, int cap);
 void hx_counters_reset(hx_context *ctx);
 
+/* ---- profiling ------------------------------------------------------------- */
+/* While enabled, every kernel launch of the context is bracketed by CUDA events
+ * recorded on its launching stream, grouped by kernel class.  Enabling clears
+ * earlier records.  hx_profile_read synchronizes the device and reports class
+ * i (0-based): its name, the number of launches, their summed duration in ms
+ * and their summed algorithmic bytes (the reads and writes the operation needs
+ * at least, 8 bytes per residue); returns the number of classes, or HX_EINVAL
+ * for i out of range. */
+hx_status hx_profile_enable(hx_context *ctx, int on);
+int hx_profile_read(hx_context *ctx, int i, char *name, size_t cap, uint64_t *launches, double *ms, double *bytes);
+
 #ifdef __cplusplus
 }
 #endif

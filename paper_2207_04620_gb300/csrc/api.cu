@@ -498,4 +498,42 @@ void hx_counters_reset(hx_context *ctx)
     if (ctx) memset(ctx->counters, 0, sizeof(ctx->counters));
 }
 
+hx_status hx_profile_enable(hx_context *ctx, int on)
+{
+    HX_TRY
+    need(ctx, "null argument");
+    HX_CUDA(cudaDeviceSynchronize());
+    ctx->prof.clear();
+    ctx->profiling = on != 0;
+    return HX_OK;
+    HX_END
+}
+
+int hx_profile_read(hx_context *ctx, int i, char *name, size_t cap, uint64_t *launches, double *ms, double *bytes)
+{
+    HX_TRY
+    need(ctx, "null argument");
+    if (i < 0 || i >= K_NCLASS) return HX_EINVAL;
+    HX_CUDA(cudaDeviceSynchronize());
+    uint64_t n = 0;
+    double t = 0, b = 0;
+    for (auto &r : ctx->prof.recs)
+        if (r.cls == i) {
+            float e = 0;
+            HX_CUDA(cudaEventElapsedTime(&e, r.a, r.b));
+            n++;
+            t += e;
+            b += r.bytes;
+        }
+    if (name && cap) {
+        strncpy(name, kclass_names[i], cap - 1);
+        name[cap - 1] = 0;
+    }
+    if (launches) *launches = n;
+    if (ms) *ms = t;
+    if (bytes) *bytes = b;
+    return K_NCLASS;
+    HX_END
+}
+
 } // extern "C"

@@ -75,12 +75,29 @@ struct DeviceTables {
     RescaleTable *rescale = nullptr;// [n_q+1] by limbs
 };
 
+// Per-kernel-class timing with CUDA events recorded on the launching stream
+// (enabled only while profiling; the events bracket every launch of a class).
+struct Profiler {
+    struct Rec {
+        int cls;
+        cudaEvent_t a, b;
+        double bytes;
+    };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get();
+    void clear();
+};
+enum KClass { K_NTT, K_KEYIP, K_CONV, K_MODDOWN, K_RESCALE, K_TENSOR, K_MULPT, K_ELEM, K_AUTO, K_MISC, K_NCLASS };
+extern const char *const kclass_names[K_NCLASS];
+
 // ---- kernel launchers (kernels.cu) ----------------------------------------------
 struct LaunchCtx {
     int log_n, N;
     const DeviceTables *t;
     cudaStream_t stream;
     uint64_t *launches;
+    Profiler *prof = nullptr;
 };
 
 void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse);

@@ -554,6 +554,27 @@ __global__ void k_ddec_shares(uint64_t *out, View ct, const uint64_t *shares, co
 
 inline int ew_blocks(int n, int per_thread) { return (n / per_thread + 255) / 256; }
 
+// records a start/stop event pair around the launches in its scope when profiling
+struct Timed {
+    const LaunchCtx &c;
+    Profiler::Rec r;
+    Timed(const LaunchCtx &cc, int cls, double bytes) : c(cc)
+    {
+        if (!c.prof) return;
+        r.cls = cls;
+        r.bytes = bytes;
+        r.a = c.prof->get();
+        r.b = c.prof->get();
+        cudaEventRecord(r.a, c.stream);
+    }
+    ~Timed()
+    {
+        if (!c.prof) return;
+        cudaEventRecord(r.b, c.stream);
+        c.prof->recs.push_back(r);
+    }
+};
+
 inline void post(const LaunchCtx &c, int k = 1)
 {
     if (c.launches) *c.launches += k;
@@ -563,8 +584,34 @@ inline void post(const LaunchCtx &c, int k = 1)
 
 } // namespace
 
+const char *const kclass_names[K_NCLASS] = {"ntt", "key_inner_product", "basis_convert", "moddown_final",
+                                            "rescale", "tensor", "mul_plain", "add_sub_copy", "automorphism",
+                                            "other"};
+
+cudaEvent_t Profiler::get()
+{
+    if (pool.empty()) {
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+}
+
+void Profiler::clear()
+{
+    for (auto &r : recs) {
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    recs.clear();
+}
+
 void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse)
 {
+    Timed tm_(c, K_NTT, 16.0 * rows.n_rows * rows.n_groups * c.N);
     if (rows.n_rows <= 0 || rows.n_groups <= 0) return;
     HX_CHECK(rows.n_rows <= MAX_NTT_ROWS && rows.n_groups < 65536, HX_EINVAL, "NTT batch too large");
     const int logm1 = c.log_n / 2, logm2 = c.log_n - logm1;
@@ -580,6 +627,7 @@ void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse)
 
 void launch_add(const LaunchCtx &c, View out, View a, View b, int B, int comps, int limbs, bool sub)
 {
+    Timed tm_(c, K_ELEM, 24.0 * B * comps * limbs * c.N);
     dim3 grid(ew_blocks(c.N, 2), limbs, B * comps);
     k_add<<<grid, 256, 0, c.stream>>>(out, a, b, c.t->primes, comps, c.N, sub);
     post(c);
@@ -587,6 +635,7 @@ void launch_add(const LaunchCtx &c, View out, View a, View b, int B, int comps, 
 
 void launch_copy(const LaunchCtx &c, View out, View a, int B, int comps, int limbs)
 {
+    Timed tm_(c, K_ELEM, 16.0 * B * comps * limbs * c.N);
     dim3 grid(ew_blocks(c.N, 2), limbs, B * comps);
     k_copy<<<grid, 256, 0, c.stream>>>(out, a, comps, c.N);
     post(c);
@@ -594,6 +643,7 @@ void launch_copy(const LaunchCtx &c, View out, View a, int B, int comps, int lim
 
 void launch_mul_plain(const LaunchCtx &c, View out, View a, const uint64_t *pt, int B, int limbs)
 {
+    Timed tm_(c, K_MULPT, 8.0 * (4 * B + 1) * limbs * c.N);
     dim3 grid(ew_blocks(c.N, 2), limbs, B * 2);
     k_mul_plain<<<grid, 256, 0, c.stream>>>(out, a, pt, c.t->primes, c.N);
     post(c);
@@ -601,6 +651,7 @@ void launch_mul_plain(const LaunchCtx &c, View out, View a, const uint64_t *pt, 
 
 void launch_mul_scalar(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int comps, int limbs)
 {
+    Timed tm_(c, K_ELEM, 16.0 * B * comps * limbs * c.N);
     dim3 grid(ew_blocks(c.N, 2), limbs, B * comps);
     k_mul_scalar<<<grid, 256, 0, c.stream>>>(out, a, sc, c.t->primes, comps, c.N);
     post(c);
@@ -608,6 +659,7 @@ void launch_mul_scalar(const LaunchCtx &c, View out, View a, const Scalars &sc, 
 
 void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int limbs)
 {
+    Timed tm_(c, K_ELEM, 32.0 * B * limbs * c.N);
     dim3 grid(ew_blocks(c.N, 1), limbs, B * 2);
     k_add_scalar_c0<<<grid, 256, 0, c.stream>>>(out, a, sc, c.t->primes, c.N);
     post(c);
@@ -615,6 +667,7 @@ void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &s
 
 void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate)
 {
+    Timed tm_(c, K_TENSOR, 8.0 * B * limbs * c.N * (accumulate ? 10 : 7));
     dim3 grid(ew_blocks(c.N, 1), limbs, B);
     k_tensor<<<grid, 256, 0, c.stream>>>(out3, a, b, c.t->primes, c.N, accumulate);
     post(c);
@@ -622,6 +675,7 @@ void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int lim
 
 void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int B, int comps, int limbs)
 {
+    Timed tm_(c, K_AUTO, 16.0 * B * comps * limbs * c.N);
     dim3 grid(ew_blocks(c.N, 1), limbs, B * comps);
     k_automorphism<<<grid, 256, 0, c.stream>>>(out, in, g, comps, c.log_n);
     post(c);
@@ -630,6 +684,7 @@ void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int 
 void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int, View out, View in, int B, int groups,
                           size_t gstride_out, size_t gstride_in)
 {
+    Timed tm_(c, K_CONV, 0.0);
     HX_CHECK(B * groups < 65536, HX_EINVAL, "conversion batch too large");
     dim3 grid(ew_blocks(c.N, 1), 1, B * groups);
     k_basis_convert<<<grid, 256, 0, c.stream>>>(tab_dev, out, in, c.t->primes, groups, gstride_out, gstride_in, c.N);
@@ -639,6 +694,7 @@ void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int, Vie
 void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
                    const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B)
 {
+    Timed tm_(c, K_KEYIP, 8.0 * c.N * ((double)B * ndig * (limbs + K) + 2.0 * ndig * (limbs + K) + 2.0 * B * (limbs + K)));
     dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
     k_key_ip<<<grid, 256, 0, c.stream>>>(acc, D, dnt, dnt_bstride, key, c.t->primes, n_all, n_q, K, limbs, ndig, g,
                                          c.log_n);
@@ -648,6 +704,7 @@ void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64
 void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
                           int limbs, View add, int add_mask, uint64_t g)
 {
+    Timed tm_(c, K_MODDOWN, 8.0 * B * 2 * limbs * c.N * ((add_mask ? 4.0 : 3.0)));
     dim3 grid(ew_blocks(c.N, 1), limbs, B * 2);
     k_moddown_final<<<grid, 256, 0, c.stream>>>(out, acc, conv, tab, c.t->primes, add, add_mask, g, c.log_n);
     post(c);
@@ -655,6 +712,7 @@ void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, con
 
 void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps, int top)
 {
+    Timed tm_(c, K_RESCALE, 8.0 * B * comps * (top + 1) * c.N);
     dim3 grid(ew_blocks(c.N, 1), top, B * comps);
     k_rescale_prep<<<grid, 256, 0, c.stream>>>(r, xtop, tab, c.t->primes, comps, top, c.N);
     post(c);
@@ -663,6 +721,7 @@ void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTab
 void launch_rescale_final(const LaunchCtx &c, View out, View in, View r, const RescaleTable *tab, int B, int comps,
                           int top)
 {
+    Timed tm_(c, K_RESCALE, 24.0 * B * comps * top * c.N);
     dim3 grid(ew_blocks(c.N, 1), top, B * comps);
     k_rescale_final<<<grid, 256, 0, c.stream>>>(out, in, r, tab, c.t->primes, comps, c.N);
     post(c);

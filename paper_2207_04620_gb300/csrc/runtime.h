@@ -58,6 +58,8 @@ struct hx_context {
     uint64_t counters[hx::C_NUM] = {0};
     std::map<std::pair<int, int>, hx_matmul_plan *> plans;
     int device = 0;
+    hx::Profiler prof;
+    bool profiling = false;
 };
 
 struct hx_keyset {
@@ -100,7 +102,10 @@ namespace hx {
 struct Eval {
     hx_context &ctx;
     cudaStream_t s;
-    LaunchCtx lc() { return LaunchCtx{ctx.log_n, ctx.N, &ctx.t, s, &ctx.counters[C_LAUNCH]}; }
+    LaunchCtx lc()
+    {
+        return LaunchCtx{ctx.log_n, ctx.N, &ctx.t, s, &ctx.counters[C_LAUNCH], ctx.profiling ? &ctx.prof : nullptr};
+    }
     Eval(hx_context &c, cudaStream_t st) : ctx(c), s(st) {}
 
     Cts alloc(int B, int comps, int limbs);

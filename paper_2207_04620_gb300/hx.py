@@ -83,6 +83,8 @@ _SIGS = {
     "hx_sign_approx_batch": (c_int, [c_vp, c_vp, PP, c_size_t, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
     "hx_counters": (c_int, [c_vp, P_u64, c_int]),
     "hx_counters_reset": (None, [c_vp]),
+    "hx_profile_enable": (c_int, [c_vp, c_int]),
+    "hx_profile_read": (c_int, [c_vp, c_int, ctypes.c_char_p, c_size_t, P_u64, P_dbl, P_dbl]),
 }
 
 
@@ -388,3 +390,24 @@ def hx_counters(ctx: int) -> dict:
 
 def hx_counters_reset(ctx: int) -> None:
     lib().hx_counters_reset(ctx)
+
+
+# ---- profiling --------------------------------------------------------------------------
+
+def hx_profile_enable(ctx: int, on: bool) -> None:
+    _chk(lib().hx_profile_enable(ctx, int(bool(on))))
+
+
+def hx_profile_read(ctx: int) -> dict:
+    """{class name: (launches, total ms, algorithmic bytes)} for the classes with launches."""
+    out = {}
+    i = 0
+    while True:
+        name = ctypes.create_string_buffer(64)
+        n, ms, b = c_u64(), c_double(), c_double()
+        total = _chk(lib().hx_profile_read(ctx, i, name, 64, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b)))
+        if n.value:
+            out[name.value.decode()] = (int(n.value), ms.value, b.value)
+        i += 1
+        if i >= total:
+            return out
