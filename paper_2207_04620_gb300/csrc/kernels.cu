@@ -26,13 +26,97 @@ __device__ __forceinline__ int galois_src(int j, uint64_t g, int log_n)
 }
 
 // ---- NTT ----------------------------------------------------------------------
+//
+// A phase holds, in shared memory, n_sub independent sub-transforms of M = 2^L
+// points (element e of sub-transform k at sh[k*sk + e*se (+ e/16 padding)]).
+// Its L local stages run as two register passes: each thread loads 2^R
+// elements spaced t = M >> (S0+R) apart, applies R radix-2 stages in
+// registers (2^R - 1 twiddle loads for R*2^(R-1) butterflies) and stores them
+// back.  Global stage of local stage s is g0 + s; the twiddle of a butterfly
+// at global stage G on global element j is tw[2^G + (j >> (log N - G))].
 
+__device__ __forceinline__ void bf_ct(uint64_t &x, uint64_t &y, const ulonglong2 w, uint64_t q, uint64_t two_q)
+{
+    uint64_t a = x;
+    if (a >= two_q) a -= two_q;
+    const uint64_t t = shoup_lazy(y, w.x, w.y, q);
+    x = a + t;
+    y = a - t + two_q;
+}
+
+__device__ __forceinline__ void bf_gs(uint64_t &x, uint64_t &y, const ulonglong2 w, uint64_t q, uint64_t two_q)
+{
+    uint64_t u = x + y;
+    if (u >= two_q) u -= two_q;
+    const uint64_t d = x - y + two_q;
+    x = u;
+    y = shoup_lazy(d, w.x, w.y, q);
+}
+
+template <int L, int R, int S0, bool INV, bool KFAST, bool PAD>
+__device__ __forceinline__ void ntt_pass(uint64_t *sh, int n_sub, int sk, int se, const ulonglong2 *__restrict__ tw,
+                                         int g0, int blk0, int blk_step, uint64_t q, int nthr)
+{
+    constexpr int M = 1 << L, RR = 1 << R, TL = M >> (S0 + R), ITEMS = M >> R;
+    const uint64_t two_q = 2 * q;
+    for (int w = threadIdx.x; w < ITEMS * n_sub; w += nthr) {
+        const int k = KFAST ? w % n_sub : w / ITEMS;
+        const int u = KFAST ? w / n_sub : w % ITEMS;
+        const int hi = u / TL, lo = u % TL;
+        const int base = hi * TL * RR + lo;
+        const int blk = blk0 + k * blk_step;
+        uint64_t v[RR];
+#pragma unroll
+        for (int m = 0; m < RR; m++) {
+            const int e = base + m * TL;
+            v[m] = sh[k * sk + e * se + (PAD ? (e >> 4) : 0)];
+        }
+        if (!INV) {
+#pragma unroll
+            for (int vv = 0; vv < R; vv++) {
+                const int s = S0 + vv, half = RR >> (vv + 1);
+                const int tbase = (1 << (g0 + s)) + (blk << s) + (hi << vv);
+#pragma unroll
+                for (int gl = 0; gl < (1 << vv); gl++) {
+                    const ulonglong2 wv = tw[tbase + gl];
+#pragma unroll
+                    for (int j = 0; j < half; j++) bf_ct(v[gl * 2 * half + j], v[gl * 2 * half + j + half], wv, q, two_q);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int vv = R - 1; vv >= 0; vv--) {
+                const int s = S0 + vv, half = RR >> (vv + 1);
+                const int tbase = (1 << (g0 + s)) + (blk << s) + (hi << vv);
+#pragma unroll
+                for (int gl = 0; gl < (1 << vv); gl++) {
+                    const ulonglong2 wv = tw[tbase + gl];
+#pragma unroll
+                    for (int j = 0; j < half; j++) bf_gs(v[gl * 2 * half + j], v[gl * 2 * half + j + half], wv, q, two_q);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < RR; m++) {
+            const int e = base + m * TL;
+            sh[k * sk + e * se + (PAD ? (e >> 4) : 0)] = v[m];
+        }
+    }
+}
+
+template <int L> struct Split {
+    static constexpr int R1 = (L + 1) / 2;  // first pass (stages 0..R1-1)
+    static constexpr int R2 = L - R1;       // second pass
+};
+
+// column phase: the first LOGM stages on M rows of stride N2 (COLS adjacent columns per block)
 template <int LOGM, int COLS, bool INV>
-__global__ void __launch_bounds__(((1 << LOGM) * COLS) / 8)
+__global__ void __launch_bounds__((1 << (LOGM - Split<LOGM>::R1)) * COLS)
 k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
            const ulonglong2 *__restrict__ tw_all, int log_n)
 {
-    constexpr int M = 1 << LOGM, E = M * COLS, T = E / 8;
+    constexpr int M = 1 << LOGM, E = M * COLS, R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
+    constexpr int T = (M >> R1) * COLS;
     extern __shared__ uint64_t sh[];
     const int N = 1 << log_n, N2 = N >> LOGM;
     const int row = blockIdx.y, g = blockIdx.z;
@@ -42,74 +126,38 @@ k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
     const uint64_t *src = INV ? R.dst + doff : R.src + soff;  // first phase of the forward transform
     uint64_t *dst = R.dst + doff;
     const PrimeConst P = primes[pr];
-    const uint64_t q = P.q, two_q = 2 * q;
     const ulonglong2 *tw = tw_all + (size_t)pr * N;
     const int c0 = blockIdx.x * COLS;
-    for (int i = threadIdx.x; i < E; i += T) {
-        const int r = i / COLS, c = i % COLS;
-        sh[i] = src[(size_t)r * N2 + c0 + c];
-    }
+    for (int i = threadIdx.x; i < E; i += T) sh[i] = src[(size_t)(i / COLS) * N2 + c0 + (i % COLS)];
     __syncthreads();
     if (!INV) {
-#pragma unroll 1
-        for (int s = 0; s < LOGM; s++) {
-            const int lt = LOGM - 1 - s;  // t = 2^lt rows
-#pragma unroll
-            for (int it = 0; it < E / 2 / T; it++) {
-                const int b = threadIdx.x + it * T;
-                const int c = b % COLS, bf = b / COLS;
-                const int grp = bf >> lt, k = bf & ((1 << lt) - 1);
-                const int r0 = (grp << (lt + 1)) + k;
-                const ulonglong2 w = tw[(1 << s) + grp];
-                uint64_t x = sh[r0 * COLS + c];
-                const uint64_t y = sh[(r0 + (1 << lt)) * COLS + c];
-                if (x >= two_q) x -= two_q;
-                const uint64_t t = shoup_lazy(y, w.x, w.y, q);
-                sh[r0 * COLS + c] = x + t;
-                sh[(r0 + (1 << lt)) * COLS + c] = x - t + two_q;
-            }
-            __syncthreads();
-        }
-        for (int i = threadIdx.x; i < E; i += T) {
-            const int r = i / COLS, c = i % COLS;
-            dst[(size_t)r * N2 + c0 + c] = sh[i];
-        }
+        ntt_pass<LOGM, R1, 0, false, true, false>(sh, COLS, 1, COLS, tw, 0, 0, 0, P.q, T);
+        __syncthreads();
+        ntt_pass<LOGM, R2, R1, false, true, false>(sh, COLS, 1, COLS, tw, 0, 0, 0, P.q, T);
+        __syncthreads();
+        for (int i = threadIdx.x; i < E; i += T) dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = sh[i];
     } else {
-#pragma unroll 1
-        for (int s = LOGM - 1; s >= 0; s--) {
-            const int lt = LOGM - 1 - s;
-#pragma unroll
-            for (int it = 0; it < E / 2 / T; it++) {
-                const int b = threadIdx.x + it * T;
-                const int c = b % COLS, bf = b / COLS;
-                const int grp = bf >> lt, k = bf & ((1 << lt) - 1);
-                const int r0 = (grp << (lt + 1)) + k;
-                const ulonglong2 w = tw[(1 << s) + grp];
-                const uint64_t x = sh[r0 * COLS + c];
-                const uint64_t y = sh[(r0 + (1 << lt)) * COLS + c];
-                uint64_t u = x + y;
-                if (u >= two_q) u -= two_q;
-                sh[r0 * COLS + c] = u;
-                sh[(r0 + (1 << lt)) * COLS + c] = shoup_lazy(x - y + two_q, w.x, w.y, q);
-            }
-            __syncthreads();
-        }
-        for (int i = threadIdx.x; i < E; i += T) {
-            const int r = i / COLS, c = i % COLS;
-            dst[(size_t)r * N2 + c0 + c] = shoup(sh[i], P.n_inv, P.n_inv_sh, q);
-        }
+        ntt_pass<LOGM, R2, R1, true, true, false>(sh, COLS, 1, COLS, tw, 0, 0, 0, P.q, T);
+        __syncthreads();
+        ntt_pass<LOGM, R1, 0, true, true, false>(sh, COLS, 1, COLS, tw, 0, 0, 0, P.q, T);
+        __syncthreads();
+        for (int i = threadIdx.x; i < E; i += T)
+            dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = shoup(sh[i], P.n_inv, P.n_inv_sh, P.q);
     }
 }
 
+// row phase: the remaining LOGM stages on ROWS contiguous blocks of M words
 template <int LOGM, int ROWS, bool INV>
-__global__ void __launch_bounds__(((1 << LOGM) * ROWS) / 8)
+__global__ void __launch_bounds__((1 << (LOGM - Split<LOGM>::R1)) * ROWS)
 k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
            const ulonglong2 *__restrict__ tw_all, int log_n)
 {
-    constexpr int M = 1 << LOGM, E = M * ROWS, T = E / 8;
+    constexpr int M = 1 << LOGM, E = M * ROWS, R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
+    constexpr int T = (M >> R1) * ROWS;
+    constexpr int SK = M + M / 16;  // padded block stride
     extern __shared__ uint64_t sh[];
     const int N = 1 << log_n;
-    const int logm1 = log_n - LOGM;  // stages done by the column phase
+    const int g0 = log_n - LOGM;
     const int row = blockIdx.y, g = blockIdx.z;
     const int pr = R.prime[row];
     const size_t doff = (size_t)g * R.dst_gs + (size_t)R.dst_off[row] * N;
@@ -119,59 +167,34 @@ k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
     const PrimeConst P = primes[pr];
     const uint64_t q = P.q, two_q = 2 * q;
     const ulonglong2 *tw = tw_all + (size_t)pr * N;
-    const int r_base = blockIdx.x * ROWS;  // first block of M words
+    const int r_base = blockIdx.x * ROWS;
     const size_t base = (size_t)r_base * M;
-    for (int i = threadIdx.x; i < E; i += T) sh[i] = src[base + i];
+    for (int i = threadIdx.x; i < E; i += T) {
+        const int k = i / M, e = i % M;
+        sh[k * SK + e + (e >> 4)] = src[base + i];
+    }
     __syncthreads();
     if (!INV) {
-#pragma unroll 1
-        for (int s = 0; s < LOGM; s++) {
-            const int lt = LOGM - 1 - s;
-            const int m = 1 << (logm1 + s);
-#pragma unroll
-            for (int it = 0; it < E / 2 / T; it++) {
-                const int b = threadIdx.x + it * T;
-                const int rr = b / (M / 2), bf = b % (M / 2);
-                const int grp = bf >> lt, k = bf & ((1 << lt) - 1);
-                const int c0 = rr * M + (grp << (lt + 1)) + k;
-                const ulonglong2 w = tw[m + ((r_base + rr) << s) + grp];
-                uint64_t x = sh[c0];
-                const uint64_t y = sh[c0 + (1 << lt)];
-                if (x >= two_q) x -= two_q;
-                const uint64_t t = shoup_lazy(y, w.x, w.y, q);
-                sh[c0] = x + t;
-                sh[c0 + (1 << lt)] = x - t + two_q;
-            }
-            __syncthreads();
-        }
+        ntt_pass<LOGM, R1, 0, false, false, true>(sh, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+        __syncthreads();
+        ntt_pass<LOGM, R2, R1, false, false, true>(sh, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+        __syncthreads();
         for (int i = threadIdx.x; i < E; i += T) {
-            uint64_t v = sh[i];
+            const int k = i / M, e = i % M;
+            uint64_t v = sh[k * SK + e + (e >> 4)];
             if (v >= two_q) v -= two_q;
             if (v >= q) v -= q;
             dst[base + i] = v;
         }
     } else {
-#pragma unroll 1
-        for (int s = LOGM - 1; s >= 0; s--) {
-            const int lt = LOGM - 1 - s;
-            const int m = 1 << (logm1 + s);
-#pragma unroll
-            for (int it = 0; it < E / 2 / T; it++) {
-                const int b = threadIdx.x + it * T;
-                const int rr = b / (M / 2), bf = b % (M / 2);
-                const int grp = bf >> lt, k = bf & ((1 << lt) - 1);
-                const int c0 = rr * M + (grp << (lt + 1)) + k;
-                const ulonglong2 w = tw[m + ((r_base + rr) << s) + grp];
-                const uint64_t x = sh[c0];
-                const uint64_t y = sh[c0 + (1 << lt)];
-                uint64_t u = x + y;
-                if (u >= two_q) u -= two_q;
-                sh[c0] = u;
-                sh[c0 + (1 << lt)] = shoup_lazy(x - y + two_q, w.x, w.y, q);
-            }
-            __syncthreads();
+        ntt_pass<LOGM, R2, R1, true, false, true>(sh, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+        __syncthreads();
+        ntt_pass<LOGM, R1, 0, true, false, true>(sh, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+        __syncthreads();
+        for (int i = threadIdx.x; i < E; i += T) {
+            const int k = i / M, e = i % M;
+            dst[base + i] = sh[k * SK + e + (e >> 4)];
         }
-        for (int i = threadIdx.x; i < E; i += T) dst[base + i] = sh[i];
     }
 }
 
@@ -181,6 +204,7 @@ void ntt_cols(const LaunchCtx &c, const NttRows &rows)
     constexpr int M = 1 << LOGM;
     constexpr int COLS = (M >= 256) ? 16 : 2048 / M;
     constexpr int E = M * COLS;
+    constexpr int T = (M >> Split<LOGM>::R1) * COLS;
     const int N2 = c.N >> LOGM;
     dim3 grid(N2 / COLS, rows.n_rows, rows.n_groups);
     const size_t smem = (size_t)E * 8;
@@ -189,8 +213,8 @@ void ntt_cols(const LaunchCtx &c, const NttRows &rows)
         cudaFuncSetAttribute(k_ntt_cols<LOGM, COLS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_ntt_cols<LOGM, COLS, INV><<<grid, E / 8, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
-                                                                 c.log_n);
+    k_ntt_cols<LOGM, COLS, INV><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
+                                                            c.log_n);
 }
 
 template <int LOGM, bool INV>
@@ -198,17 +222,17 @@ void ntt_rows(const LaunchCtx &c, const NttRows &rows)
 {
     constexpr int M = 1 << LOGM;
     constexpr int ROWS = (M >= 256) ? 16 : 2048 / M;
-    constexpr int E = M * ROWS;
+    constexpr int T = (M >> Split<LOGM>::R1) * ROWS;
     const int N1 = c.N >> LOGM;
     dim3 grid(N1 / ROWS, rows.n_rows, rows.n_groups);
-    const size_t smem = (size_t)E * 8;
+    const size_t smem = (size_t)ROWS * (M + M / 16) * 8;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_ntt_rows<LOGM, ROWS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    k_ntt_rows<LOGM, ROWS, INV><<<grid, E / 8, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
-                                                                 c.log_n);
+    k_ntt_rows<LOGM, ROWS, INV><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
+                                                            c.log_n);
 }
 
 template <bool INV>
@@ -231,7 +255,6 @@ void ntt_rows_dispatch(const LaunchCtx &c, const NttRows &r, int logm)
     case 6: ntt_rows<6, INV>(c, r); break;
     case 7: ntt_rows<7, INV>(c, r); break;
     case 8: ntt_rows<8, INV>(c, r); break;
-    case 9: ntt_rows<9, INV>(c, r); break;
     default: throw Error{HX_EINVAL, "unsupported NTT size"};
     }
 }
