@@ -154,6 +154,25 @@ hx_status hx_rotate(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, int32_
 hx_status hx_rotate_hoisted(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, const int32_t *steps, int n,
                             hx_ct **outs, void *stream);
 
+/* Rotation that allocates no device memory.  The paper has no counterpart:
+ * this serves callers that cannot request device memory when they rotate (a
+ * process whose memory manager already holds the device, a latency-bound
+ * loop that must avoid cudaMalloc's synchronisation, a host that forbids
+ * plug-ins from allocating after start-up).  `in` and `out` are device
+ * buffers of one ciphertext, [2][limbs][N] words, NTT form, at `limbs`
+ * limbs (distinct, caller-owned).  Every intermediate lives in one static
+ * device array of HX_NOALLOC_SCRATCH_BYTES that the library holds on every
+ * device it is loaded on until the process exits; a rotation needing more
+ * (8*N*(4*limbs + (ceil(limbs/n_p) + 2)*(limbs + n_p)) bytes) returns
+ * HX_EINVAL.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All
+ * calls share the array: calls whose work overlaps on the GPU (other streams,
+ * other threads) race and must be serialised by the caller.  The result is
+ * identical to hx_rotate's. */
+#define HX_NOALLOC_SCRATCH_BYTES (16ull << 20)
+hx_status hx_rotate_noalloc(hx_context *ctx, const hx_keyset *ks, const uint64_t *in, int limbs, uint64_t *out,
+                            int32_t k, void *stream);
+
 /* ---- raw kernels on caller device buffers (for parity tests and benches) --- */
 /* In-place forward (inverse != 0: inverse) negacyclic NTT of n_polys
  * polynomials laid out [n_polys][limbs][N] in device memory; limb l is taken

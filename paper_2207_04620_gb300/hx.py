@@ -72,6 +72,7 @@ _SIGS = {
     "hx_rotate": (c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, PP, c_vp]),
     "hx_rotate_hoisted": (c_int, [c_vp, c_vp, c_vp, P_i32, c_int, PP, c_vp]),
     "hx_ntt": (c_int, [c_vp, c_vp, c_int, c_int, P_i32, c_int, c_vp]),
+    "hx_rotate_noalloc": (c_int, [c_vp, c_vp, c_vp, c_int, c_vp, ctypes.c_int32, c_vp]),
     "hx_matmul_plan_create": (c_int, [c_vp, c_int, c_int, PP]),
     "hx_matmul_plan_num_masks": (c_int, [c_vp]),
     "hx_matmul_plan_set_mask": (c_int, [c_vp, c_vp, c_int, P_i64]),
@@ -318,6 +319,12 @@ def hx_rotate_hoisted(ctx, ks, a, steps, stream=None) -> list:
     outs = (c_vp * max(1, arr.size))()
     _chk(lib().hx_rotate_hoisted(ctx, ks, a, ptr, arr.size, outs, _stream(stream)))
     return [outs[i] for i in range(arr.size)]
+
+
+def hx_rotate_noalloc(ctx: int, ks: int, in_ptr: int, limbs: int, out_ptr: int, k: int, stream=None) -> None:
+    """Rotation of the ciphertext at device address in_ptr ([2][limbs][N] words) into out_ptr,
+    using the library's static scratch instead of device allocations."""
+    _chk(lib().hx_rotate_noalloc(ctx, ks, in_ptr, limbs, out_ptr, int(k), _stream(stream)))
 
 
 def hx_ntt(ctx: int, dev_ptr: int, n_polys: int, prime_idx, inverse: bool = False, stream=None) -> None:
