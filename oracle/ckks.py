@@ -750,6 +750,40 @@ class Evaluator:
         ks0, ks1 = self.keyswitch(c1, key, ct.limbs)
         return Ciphertext(np.stack([self.ctx.add(c0, ks0, pr), ks1]), ct.scale)
 
+    def hoist(self, ct: Ciphertext) -> list:
+        """The ModUp of c1 shared by several rotations of ct."""
+        return self.modup(ct.c[1], ct.limbs)
+
+    def hoisted_mux(self, ct: Ciphertext, digits: list, k1: int, k2: int, v_ext: np.ndarray, v_scale: float,
+                    c: int) -> Ciphertext:
+        """v . Rot(ct, k1) + (1 - v) . Rot(ct, k2) from one ModUp (`digits`),
+        with the selection applied before ModDown in the extended basis P*Q:
+          Z = c*IP_{k2} + v*(IP_{k1} - IP_{k2}),  out = (C0 + MD(Z_0), MD(Z_1)),
+          C0 = c*sigma_{k2}(c0) + v*(sigma_{k1}(c0) - sigma_{k2}(c0)),
+        where v is the mask encoded at scale `c` = v_scale (rows: Q_l then P) and
+        c*x stands for the encoding of 1 at that scale.  The result has scale
+        ct.scale * v_scale."""
+        ctx = self.ctx
+        limbs = ct.limbs
+        ext = ctx.q[:limbs] + ctx.p
+        pr = self._prim(limbs)
+        g1, key1 = self._rot_key(k1)
+        g2, key2 = self._rot_key(k2)
+        x0, x1 = self.inner_product(digits, key1, limbs, galois=g1)
+        y0, y1 = self.inner_product(digits, key2, limbs, galois=g2)
+        cs = [c % t for t in ext]
+        z = [ctx.add(ctx.mul_scalar(y, cs, ext), ctx.mul(v_ext, ctx.sub(x, y, ext), ext), ext)
+             for x, y in ((x0, y0), (x1, y1))]
+        m0, m1 = self.moddown(z[0], limbs), self.moddown(z[1], limbs)
+        s1 = ctx.automorphism(ct.c[0], g1)
+        s2 = ctx.automorphism(ct.c[0], g2)
+        c0 = ctx.add(ctx.mul_scalar(s2, cs[:limbs], pr), ctx.mul(v_ext[:limbs], ctx.sub(s1, s2, pr), pr), pr)
+        self._count("Rot", 2)
+        self._count("RotHoisted", 2)
+        self._count("Mul_pt")
+        self._count("Add")
+        return Ciphertext(np.stack([ctx.add(c0, m0, pr), m1]), ct.scale * v_scale)
+
     def rotate_hoisted(self, ct: Ciphertext, steps) -> list:
         """Several rotations of one ciphertext sharing a single ModUp of c1
         (reading R10): Rot_k = (sigma_g(c0) + MD(<sigma_g(D), swk_g>_0),

@@ -164,7 +164,8 @@ def plan_masks(h: int, limbs: int):
       mu   : l = -h+1..h-1, vector R(u^mu_l, -b*floor(l/b))            at `limbs`
       zeta : l = 0..h-1, R(u^zeta_{hl}, -h*b*floor(l/b)) for Alg. 3,
              u^zeta_{hl} unrotated for the depth-2 variant              at `limbs`
-      v    : k = 1..h-1, R(v_k, -k)                                      at `limbs`-1 (Alg. 3 only)
+      v    : k = 1..h-1, v_k (Step 2 selects after rotating)              at `limbs`-1 (Alg. 3 only),
+             used in the extended basis q_0..q_{l-1}, p_0..p_{K-1}
     A mask multiplying a ciphertext of l limbs is encoded at scale q_{l-1}."""
     variant = matmul_variant(limbs)
     b = baby_steps(h)
@@ -178,7 +179,7 @@ def plan_masks(h: int, limbs: int):
             out.append(("zeta", l, diag_zeta(h, l), limbs))
     if variant == "alg3":
         for k in range(1, h):
-            out.append(("v", k, R(diag_v(h, k), -k), limbs - 1))
+            out.append(("v", k, diag_v(h, k), limbs - 1))
     return out
 
 
@@ -224,10 +225,11 @@ class MaskProvider:
             self._coeffs[i] = C.encode_real(self.ctx.N, expand(vec, self.beta), float(self.ctx.q[lm - 1]))
         return self._coeffs[i]
 
-    def plaintext(self, kind: str, k: int):
+    def plaintext(self, kind: str, k: int, extended: bool = False):
+        """NTT-form mask over q_0..q_{l-1} (and p_0..p_{K-1} if extended)."""
         i = self.index[(kind, k)]
         lm = self.entries[i][3]
-        prim = self.ctx.q[:lm]
+        prim = self.ctx.q[:lm] + (self.ctx.p if extended else [])
         pt = self.ctx.ntt(self.ctx.signed_to_rows(self.coeffs(i), prim), prim)
         return pt, float(self.ctx.q[lm - 1])
 
@@ -276,16 +278,15 @@ def _matmul_alg3(ev, A, B, h, masks):
     # Step 1-1 / 1-2: A0 = U^mu a, B0 = U^zeta b
     A0 = ev.rescale(lintrans_bsgs(ev, A, range(-h + 1, h), 1, masks, "mu"))
     B0 = ev.rescale(lintrans_bsgs(ev, B, range(h), h, masks, "zeta"))
-    # Step 2 with the multiplexer trick (App. B): with M_k = Mul_pt(A0, R(v_k,-k)),
-    # A^(k) = Rot(M_k, k) + Rot(q*A0 - M_k, k-h); q*A0 is A0 at the mask scale.
+    # Step 2 (App. B multiplexer, applied after hoisting): A^(k) = v_k . R(A0, k)
+    # + (1 - v_k) . R(A0, k-h); every rotation of A0 shares one ModUp and the
+    # selection happens in the extended basis before a single ModDown per k.
     qt = ev.ctx.q[A0.limbs - 1]
-    A0s = ev.mul_int(A0, qt, new_scale=A0.scale * float(qt))
+    D = ev.hoist(A0)
     Ak = [ev.drop(A0, A0.limbs - 1)]
     for k in range(1, h):
-        pt, sc = masks.plaintext("v", k)
-        M = ev.mul_plain(A0, pt, sc)
-        Nk = ev.sub(A0s, M)
-        Ak.append(ev.rescale(ev.add(ev.rotate(M, beta * k), ev.rotate(Nk, beta * (k - h)))))
+        v_ext, sc = masks.plaintext("v", k, extended=True)
+        Ak.append(ev.rescale(ev.hoisted_mux(A0, D, beta * k, beta * (k - h), v_ext, sc, qt)))
     # B^(k) = Rot(B0, h*k): all rotations of one ciphertext, hoisted
     B0d = ev.drop(B0, B0.limbs - 1)
     Bk = [B0d] + ev.rotate_hoisted(B0d, [beta * h * k for k in range(1, h)])
@@ -344,8 +345,8 @@ def slot_matmul(a: np.ndarray, b: np.ndarray, h: int, beta: int = 1, variant: st
             B0 += Rb_(expand(R(diag_zeta(h, l), -h * bb * i), beta) * Rb_(b, h * j), h * bb * i)
         out = A0 * B0
         for k in range(1, h):
-            M = A0 * expand(R(diag_v(h, k), -k), beta)
-            Ak = Rb_(M, k) + Rb_(A0 - M, k - h)
+            v = expand(diag_v(h, k), beta)
+            Ak = v * Rb_(A0, k) + (1 - v) * Rb_(A0, k - h)
             out += Ak * Rb_(B0, h * k)
         return out
     T = [expand(diag_zeta(h, l), beta) * Rb_(b, h * l) for l in range(h)]

@@ -403,7 +403,10 @@ hx_status hx_matmul_plan_set_mask(hx_context *ctx, hx_matmul_plan *plan, int i, 
     HX_TRY
     need(ctx && plan && coeffs && i >= 0 && i < (int)plan->masks.size(), "bad mask index");
     auto &m = plan->masks[i];
-    upload_plaintext(*ctx, nullptr, coeffs, m.limbs, m.pt->p);
+    if (m.extended)
+        upload_plaintext_ext(*ctx, nullptr, coeffs, m.limbs, m.pt->p);
+    else
+        upload_plaintext(*ctx, nullptr, coeffs, m.limbs, m.pt->p);
     return HX_OK;
     HX_END
 }

@@ -256,6 +256,41 @@ Cts Eval::rotate_hoisted_one(const Cts &a, const BufPtr &D, int64_t k, const hx_
     return o;
 }
 
+Cts Eval::hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, const uint64_t *v_ext, double v_scale,
+                      uint64_t c, const hx_keyset &keys)
+{
+    const int N = ctx.N, K = ctx.K, limbs = a.limbs, ext = limbs + K, nd = (limbs + K - 1) / K, B = a.B;
+    const uint64_t g1 = galois_for_step(k1, ctx.log_n), g2 = galois_for_step(k2, ctx.log_n);
+    HX_CHECK(g1 != 1 && g2 != 1, HX_EINVAL, "selection needs two proper rotations");
+    const SwitchKey &key1 = rot_key(keys, g1), &key2 = rot_key(keys, g2);
+    Scalars cs;
+    for (int t = 0; t < ext; t++) {
+        const uint64_t q = ctx.primes[t < limbs ? t : ctx.n_q + (t - limbs)];
+        cs.v[t] = c % q;
+        cs.sh[t] = shoup_companion(cs.v[t], q);
+    }
+    const View c1{a.d + a.cstride(N), a.bstride(N), a.cstride(N)};
+    DevBuf z((size_t)B * 2 * ext * N, s);
+    View zv{z.p, (size_t)2 * ext * N, (size_t)ext * N};
+    launch_key_ip_mux(lc(), zv, D->p, c1.p, c1.bstride, key1.buf->p, key2.buf->p, v_ext, cs, ctx.n_all, ctx.n_q, K,
+                      limbs, nd, g1, g2, B);
+    ntt_inplace(z.p, (size_t)ext * N, 2 * B, iota_vec(limbs, K), iota_vec(ctx.n_q, K), true);
+    DevBuf conv((size_t)B * 2 * limbs * N, s);
+    launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), limbs,
+                         View{conv.p, (size_t)limbs * N, 0}, View{z.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0);
+    ntt_inplace(conv.p, (size_t)limbs * N, 2 * B, iota_vec(0, limbs), iota_vec(0, limbs), false);
+    Cts o = alloc(B, 2, limbs);
+    launch_moddown_final_mux(lc(), o.view(N), zv, View{conv.p, (size_t)2 * limbs * N, (size_t)limbs * N},
+                             ctx.t.moddown + limbs, B, limbs, a.view(N), v_ext, cs, g1, g2);
+    o.scale = a.scale * v_scale;
+    ctx.counters[C_ROT] += 2 * B;
+    ctx.counters[C_ROT_HOIST] += 2 * B;
+    ctx.counters[C_MULPT] += B;
+    ctx.counters[C_ADD] += B;
+    ctx.counters[C_KS] += B;
+    return o;
+}
+
 std::vector<Cts> Eval::rotate_hoisted(const Cts &a, const std::vector<int64_t> &ks, const hx_keyset &keys)
 {
     BufPtr D;
@@ -294,6 +329,23 @@ void upload_plaintext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, in
     ev.ntt_inplace(dst, 0, 1, iota_vec(0, limbs), iota_vec(0, limbs), false);
     launch_to_mont(ev.lc(), dst, limbs, ctx.d_prime_ids);
     HX_CUDA(cudaStreamSynchronize(s));  // the pageable source must outlive the copy
+}
+
+void upload_plaintext_ext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst)
+{
+    Eval ev(ctx, s);
+    const int ext = limbs + ctx.K;
+    std::vector<int> pr(ext);
+    for (int t = 0; t < ext; t++) pr[t] = t < limbs ? t : ctx.n_q + (t - limbs);
+    DevBuf tmp((size_t)ctx.N, s);
+    DevBuf ids((ext + 1) / 2, s);
+    HX_CUDA(cudaMemcpyAsync(tmp.p, coeffs, sizeof(int64_t) * ctx.N, cudaMemcpyHostToDevice, s));
+    HX_CUDA(cudaMemcpyAsync(ids.p, pr.data(), sizeof(int) * ext, cudaMemcpyHostToDevice, s));
+    const int *idp = reinterpret_cast<const int *>(ids.p);
+    launch_signed_to_rows(ev.lc(), dst, reinterpret_cast<const int64_t *>(tmp.p), ext, 1, ctx.N, idp);
+    ev.ntt_inplace(dst, 0, 1, iota_vec(0, ext), pr, false);
+    launch_to_mont(ev.lc(), dst, ext, idp);
+    HX_CUDA(cudaStreamSynchronize(s));
 }
 
 } // namespace hx

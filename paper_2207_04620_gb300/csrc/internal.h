@@ -115,6 +115,12 @@ void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64
 // out_c = (acc_c - conv_c) * P^-1, plus add_c[galois(j)] for the components set in add_mask
 void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
                           int limbs, View add, int add_mask, uint64_t add_galois);
+// two hoisted rotations selected by a mask in the extended basis (see kernels.cu)
+void launch_key_ip_mux(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
+                       const uint64_t *key1, const uint64_t *key2, const uint64_t *v, const Scalars &cs, int n_all,
+                       int n_q, int K, int limbs, int ndig, uint64_t g1, uint64_t g2, int B);
+void launch_moddown_final_mux(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
+                              int limbs, View src, const uint64_t *v, const Scalars &cs, uint64_t g1, uint64_t g2);
 void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps,
                          int top);
 void launch_rescale_final(const LaunchCtx &c, View out, View in, View r, const RescaleTable *tab, int B,

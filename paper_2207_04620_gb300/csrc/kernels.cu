@@ -446,6 +446,75 @@ __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_
     }
 }
 
+// Two hoisted rotations of one ciphertext (Galois elements g1, g2) selected
+// by a mask before ModDown, in the extended basis:
+//   z_h[t] = c*y_h[t] + v[t]*(x_h[t] - y_h[t]),  x = <sigma_g1(D), swk1>, y = <sigma_g2(D), swk2>
+// v (rows Q_l then P) is in Montgomery form; cs holds c mod each row's prime.
+__global__ void k_key_ip_mux(View out, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt,
+                             size_t dnt_bstride, const uint64_t *__restrict__ key1, const uint64_t *__restrict__ key2,
+                             const uint64_t *__restrict__ v, const __grid_constant__ Scalars cs,
+                             const PrimeConst *__restrict__ primes, int n_all, int n_q, int K, int limbs, int ndig,
+                             uint64_t g1, uint64_t g2, int log_n)
+{
+    const int n = 1 << log_n;
+    const int t = blockIdx.y, bi = blockIdx.z;
+    const int ext = limbs + K;
+    const int pr = t < limbs ? t : n_q + (t - limbs);
+    const PrimeConst P = primes[pr];
+    const size_t dig_stride = (size_t)ext * n;
+    const uint64_t *Db = D + (size_t)bi * ndig * dig_stride;
+    const uint64_t *db = dnt + bi * dnt_bstride;
+    const int own_digit = t < limbs ? t / K : -1;
+    const uint64_t c = cs.v[t], csh = cs.sh[t];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int j1 = galois_src(j, g1, log_n), j2 = galois_src(j, g2, log_n);
+        Acc128 x0, x1, y0, y1;
+        for (int d = 0; d < ndig; d++) {
+            const uint64_t *row = (d == own_digit) ? db + (size_t)t * n : Db + d * dig_stride + (size_t)t * n;
+            const uint64_t a = row[j1], b = row[j2];
+            const size_t ko = (size_t)d * 2 * n_all * n + (size_t)pr * n + j;
+            x0.mac(a, key1[ko]);
+            x1.mac(a, key1[ko + (size_t)n_all * n]);
+            y0.mac(b, key2[ko]);
+            y1.mac(b, key2[ko + (size_t)n_all * n]);
+        }
+        const uint64_t vv = v[(size_t)t * n + j];
+        const uint64_t xr0 = mont128(x0.hi, x0.lo, P), yr0 = mont128(y0.hi, y0.lo, P);
+        const uint64_t xr1 = mont128(x1.hi, x1.lo, P), yr1 = mont128(y1.hi, y1.lo, P);
+        const uint64_t d0 = submod(xr0, yr0, P.q), d1 = submod(xr1, yr1, P.q);
+        const uint64_t z0 = addmod(shoup(yr0, c, csh, P.q), mont128(__umul64hi(vv, d0), vv * d0, P), P.q);
+        const uint64_t z1 = addmod(shoup(yr1, c, csh, P.q), mont128(__umul64hi(vv, d1), vv * d1, P), P.q);
+        out.p[bi * out.bstride + (size_t)t * n + j] = z0;
+        out.p[bi * out.bstride + out.cstride + (size_t)t * n + j] = z1;
+    }
+}
+
+// ModDown epilogue of k_key_ip_mux: out_h = (z_h - conv_h) * P^-1, plus for h = 0
+// c*sigma_g2(c0) + v*(sigma_g1(c0) - sigma_g2(c0))
+__global__ void k_moddown_final_mux(View out, View acc, View conv, const ModDownTable *__restrict__ tab,
+                                    const PrimeConst *__restrict__ primes, View src, const uint64_t *__restrict__ v,
+                                    const __grid_constant__ Scalars cs, uint64_t g1, uint64_t g2, int log_n)
+{
+    const int n = 1 << log_n;
+    const int t = blockIdx.y, bc = blockIdx.z, bi = bc / 2, ci = bc % 2;
+    const PrimeConst P = primes[t];
+    const uint64_t q = P.q, w = tab->pinv[t], wsh = tab->pinv_sh[t];
+    const uint64_t *a = acc.p + bi * acc.bstride + ci * acc.cstride + (size_t)t * n;
+    const uint64_t *cv = conv.p + bi * conv.bstride + ci * conv.cstride + (size_t)t * n;
+    uint64_t *o = out.p + bi * out.bstride + ci * out.cstride + (size_t)t * n;
+    const uint64_t *c0 = src.p + bi * src.bstride + (size_t)t * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        uint64_t r = shoup(submod(a[j], cv[j], q), w, wsh, q);
+        if (ci == 0) {
+            const uint64_t s1 = c0[galois_src(j, g1, log_n)], s2 = c0[galois_src(j, g2, log_n)];
+            const uint64_t vv = v[(size_t)t * n + j], d = submod(s1, s2, q);
+            const uint64_t sel = addmod(shoup(s2, cs.v[t], cs.sh[t], q), mont128(__umul64hi(vv, d), vv * d, P), q);
+            r = addmod(r, sel, q);
+        }
+        o[j] = r;
+    }
+}
+
 // out_c[t] = (acc_c[t] - conv_c[t]) * P^-1 (+ add_c[t][galois(j)] for the components in add_mask)
 __global__ void k_moddown_final(View out, View acc, View conv, const ModDownTable *__restrict__ tab,
                                 const PrimeConst *__restrict__ primes, View add, int add_mask, uint64_t g, int log_n)
@@ -721,6 +790,27 @@ void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64
     dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
     k_key_ip<<<grid, 256, 0, c.stream>>>(acc, D, dnt, dnt_bstride, key, c.t->primes, n_all, n_q, K, limbs, ndig, g,
                                          c.log_n);
+    post(c);
+}
+
+void launch_key_ip_mux(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
+                       const uint64_t *key1, const uint64_t *key2, const uint64_t *v, const Scalars &cs, int n_all,
+                       int n_q, int K, int limbs, int ndig, uint64_t g1, uint64_t g2, int B)
+{
+    Timed tm_(c, K_KEYIP, 8.0 * c.N * ((double)B * ndig * (limbs + K) + 4.0 * ndig * (limbs + K) + (limbs + K) +
+                                        2.0 * B * (limbs + K)));
+    dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
+    k_key_ip_mux<<<grid, 256, 0, c.stream>>>(out, D, dnt, dnt_bstride, key1, key2, v, cs, c.t->primes, n_all, n_q, K,
+                                             limbs, ndig, g1, g2, c.log_n);
+    post(c);
+}
+
+void launch_moddown_final_mux(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
+                              int limbs, View src, const uint64_t *v, const Scalars &cs, uint64_t g1, uint64_t g2)
+{
+    Timed tm_(c, K_MODDOWN, 8.0 * B * limbs * c.N * 9.0);
+    dim3 grid(ew_blocks(c.N, 1), limbs, B * 2);
+    k_moddown_final_mux<<<grid, 256, 0, c.stream>>>(out, acc, conv, tab, c.t->primes, src, v, cs, g1, g2, c.log_n);
     post(c);
 }
 

@@ -88,6 +88,7 @@ struct hx_matmul_plan {
         int kind;  // 0 mu, 1 zeta, 2 v
         int index;
         int limbs;
+        bool extended;  // stored over q_0..q_{limbs-1} and the special primes
         double scale;
         std::vector<int32_t> vec;  // logical 0/1 vector of length h^2
         hx::BufPtr pt;             // [limbs][N] Montgomery form, NTT
@@ -125,6 +126,11 @@ struct Eval {
     // hoisting in two steps: the ModUp of c1 once, then any number of rotations
     BufPtr hoist(const Cts &a);
     Cts rotate_hoisted_one(const Cts &a, const BufPtr &D, int64_t k, const hx_keyset &keys);
+    // v . Rot(a, k1) + (1 - v) . Rot(a, k2) from the ModUp D of a; the selection is applied in
+    // the extended basis before one ModDown; v_ext: mask over Q_l then P (Montgomery), encoded
+    // at scale v_scale whose integer value is c
+    Cts hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, const uint64_t *v_ext, double v_scale,
+                    uint64_t c, const hx_keyset &keys);
     void check_same(const Cts &a, const Cts &b);
 
     // hybrid key switching pieces
@@ -141,6 +147,8 @@ struct Eval {
 
 Scalars scalars_for(const hx_context &ctx, int limbs, int64_t c);
 void upload_plaintext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst_mont);
+// the same over q_0..q_{limbs-1}, p_0..p_{K-1}
+void upload_plaintext_ext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst_mont);
 
 // ---- keys / encryption (keys.cu) ---------------------------------------------
 void keygen(hx_context &ctx, hx_keyset &ks, int n_parties, uint64_t seed, cudaStream_t s);

@@ -105,21 +105,22 @@ hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
     p->b = baby_steps(h);
     p->alg3 = limbs >= 4;
     const int b = p->b;
-    auto add = [&](int kind, int idx, std::vector<int32_t> vec, int lm) {
+    auto add = [&](int kind, int idx, std::vector<int32_t> vec, int lm, bool extended) {
         hx_matmul_plan::Mask m;
         m.kind = kind;
         m.index = idx;
         m.limbs = lm;
+        m.extended = extended;
         m.scale = (double)ctx.primes[lm - 1];
         m.vec = std::move(vec);
         p->index[{kind, idx}] = (int)p->masks.size();
         p->masks.push_back(std::move(m));
     };
-    for (int l = -h + 1; l < h; l++) add(0, l, rot(diag_mu(h, l), -b * floordiv(l, b)), limbs);
+    for (int l = -h + 1; l < h; l++) add(0, l, rot(diag_mu(h, l), -b * floordiv(l, b)), limbs, false);
     for (int l = 0; l < h; l++)
-        add(1, l, p->alg3 ? rot(diag_zeta(h, l), -h * b * (l / b)) : diag_zeta(h, l), limbs);
-    if (p->alg3)
-        for (int k = 1; k < h; k++) add(2, k, rot(diag_v(h, k), -k), limbs - 1);
+        add(1, l, p->alg3 ? rot(diag_zeta(h, l), -h * b * (l / b)) : diag_zeta(h, l), limbs, false);
+    if (p->alg3)  // Step 2 selects after rotating: v_k itself, in the extended basis
+        for (int k = 1; k < h; k++) add(2, k, diag_v(h, k), limbs - 1, true);
     // encode every mask with the library's encoder (expanded over the beta packed matrices)
     std::vector<double> slots(ctx.N / 2);
     std::vector<int64_t> coeffs(ctx.N);
@@ -127,8 +128,13 @@ hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
         for (int t = 0; t < h * h; t++)
             for (int j = 0; j < p->beta; j++) slots[(size_t)t * p->beta + j] = m.vec[t];
         ctx.enc->encode(slots.data(), slots.size(), m.scale, coeffs.data());
-        m.pt = std::make_shared<DevBuf>((size_t)m.limbs * ctx.N, s);
-        upload_plaintext(ctx, s, coeffs.data(), m.limbs, m.pt->p);
+        if (m.extended) {
+            m.pt = std::make_shared<DevBuf>((size_t)(m.limbs + ctx.K) * ctx.N, s);
+            upload_plaintext_ext(ctx, s, coeffs.data(), m.limbs, m.pt->p);
+        } else {
+            m.pt = std::make_shared<DevBuf>((size_t)m.limbs * ctx.N, s);
+            upload_plaintext(ctx, s, coeffs.data(), m.limbs, m.pt->p);
+        }
     }
     return p.release();
 }
@@ -196,25 +202,19 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
     const int h = p.h, beta = p.beta;
     Cts A0 = ev.rescale(lintrans(ev, ks, A, -h + 1, h - 1, 1, p, 0));
     Cts B0 = ev.rescale(lintrans(ev, ks, B, 0, h - 1, h, p, 1));
-    // Step 2 (multiplexer trick): A^(k) = Rot(M_k, k) + Rot(q*A0 - M_k, k-h)
+    // Step 2 (App. B multiplexer after hoisting): A^(k) = v_k . Rot(A0, k) + (1 - v_k) . Rot(A0, k-h),
+    // all rotations of A0 from one ModUp, the selection before a single ModDown per k
     const uint64_t qt = ctx.primes[A0.limbs - 1];
-    Cts A0s = ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt);
     Cts A0d = ev.drop(A0, A0.limbs - 1);
     Cts B0d = ev.drop(B0, B0.limbs - 1);
-    // B^(k) = Rot(B0, h*k): all from one ModUp (hoisted)
-    std::vector<int64_t> bsteps;
-    for (int k = 1; k < h; k++) bsteps.push_back((int64_t)beta * h * k);
     Cts acc = ev.tensor(A0d, B0d);
-    BufPtr DB = ev.hoist(B0d);  // one ModUp serves every B^(k)
+    BufPtr DA = ev.hoist(A0);
+    BufPtr DB = ev.hoist(B0d);  // one ModUp serves every B^(k) = Rot(B0, h*k)
     for (int k = 1; k < h; k++) {
-        Cts Bk = ev.rotate_hoisted_one(B0d, DB, bsteps[k - 1], ks);
+        Cts Bk = ev.rotate_hoisted_one(B0d, DB, (int64_t)beta * h * k, ks);
         double sc;
-        const uint64_t *pt = mask_pt(p, 2, k, &sc);
-        Cts M = ev.mul_plain(A0, pt, sc);
-        Cts Nk = ev.add(A0s, M, true);
-        Cts X = ev.rotate(M, (int64_t)beta * k, ks);
-        ev.add_inplace(X, ev.rotate(Nk, (int64_t)beta * (k - h), ks));
-        Cts Ak = ev.rescale(X);
+        const uint64_t *v = mask_pt(p, 2, k, &sc);
+        Cts Ak = ev.rescale(ev.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, qt, ks));
         ev.tensor_acc(acc, Ak, Bk);
     }
     return ev.rescale(ev.relinearize(acc, ks.relin));

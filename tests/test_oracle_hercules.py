@@ -116,6 +116,7 @@ class DryEvaluator(C.Evaluator):
     def __init__(self, ctx):
         self.ctx, self.counts = ctx, {}
 
+
     def add(self, a, b):
         self._count("Add")
         return a
@@ -153,9 +154,19 @@ class DryEvaluator(C.Evaluator):
             self.rotate(ct, k)
         return [ct for _ in steps]
 
+    def hoist(self, ct):
+        return None
+
+    def hoisted_mux(self, ct, digits, k1, k2, v_ext, v_scale, c):
+        self.rotate(ct, k1)
+        self.rotate(ct, k2)
+        self._count("Mul_pt")
+        self._count("Add")
+        return _DryCt(ct.limbs, ct.scale * v_scale)
+
 
 class _DryMasks(H.MaskProvider):
-    def plaintext(self, kind, k):
+    def plaintext(self, kind, k, extended=False):
         i = self.index[(kind, k)]
         return None, float(self.ctx.q[self.entries[i][3] - 1])
 
