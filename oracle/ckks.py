@@ -750,6 +750,33 @@ class Evaluator:
         ks0, ks1 = self.keyswitch(c1, key, ct.limbs)
         return Ciphertext(np.stack([self.ctx.add(c0, ks0, pr), ks1]), ct.scale)
 
+    def rotate_sum(self, items) -> Ciphertext:
+        """sum_i Rot(ct_i, k_i) with one ModDown for the whole sum: each term's
+        key-switch output stays in the extended basis P*Q until the end.  All
+        ct_i share level and scale; a term with k = 0 is added unrotated."""
+        ctx = self.ctx
+        limbs = items[0][0].limbs
+        ext = ctx.q[:limbs] + ctx.p
+        pr = self._prim(limbs)
+        base = [np.zeros((limbs, ctx.N), dtype=np.uint64) for _ in range(2)]
+        acc = None
+        for ct, k in items:
+            g, key = self._rot_key(k)
+            if key is None:
+                base = [ctx.add(base[i], ct.c[i], pr) for i in range(2)]
+                continue
+            self._count("Rot")
+            self._count("KeySwitch")
+            c0 = ctx.automorphism(ct.c[0], g)
+            c1 = ctx.automorphism(ct.c[1], g)
+            x0, x1 = self.inner_product(self.modup(c1, limbs), key, limbs)
+            acc = [x0, x1] if acc is None else [ctx.add(acc[0], x0, ext), ctx.add(acc[1], x1, ext)]
+            base[0] = ctx.add(base[0], c0, pr)
+        self._count("Add", len(items) - 1)
+        if acc is not None:
+            base = [ctx.add(base[0], self.moddown(acc[0], limbs), pr), ctx.add(base[1], self.moddown(acc[1], limbs), pr)]
+        return Ciphertext(np.stack(base), items[0][0].scale)
+
     def hoist(self, ct: Ciphertext) -> list:
         """The ModUp of c1 shared by several rotations of ct."""
         return self.modup(ct.c[1], ct.limbs)

@@ -250,17 +250,16 @@ def lintrans_bsgs(ev: C.Evaluator, ct: C.Ciphertext, ls, stride: int, masks: Mas
         groups.setdefault(l // b, []).append((l % b, l))
     js = sorted({j for g in groups.values() for j, _ in g})
     babies = dict(zip(js, ev.rotate_hoisted(ct, [beta * stride * j for j in js])))
-    acc = None
+    items = []
     for i in sorted(groups):
         inner = None
         for j, l in groups[i]:
             pt, sc = masks.plaintext(kind, l)
             term = ev.mul_plain(babies[j], pt, sc)
             inner = term if inner is None else ev.add(inner, term)
-        if i != 0:
-            inner = ev.rotate(inner, beta * stride * b * i)
-        acc = inner if acc is None else ev.add(acc, inner)
-    return acc
+        items.append((inner, beta * stride * b * i))
+    # giant steps: one ModDown for the whole sum (reading R10)
+    return ev.rotate_sum(items)
 
 
 def matmul(ev: C.Evaluator, A: C.Ciphertext, B: C.Ciphertext, h: int, masks: MaskProvider | None = None):
@@ -281,20 +280,18 @@ def _matmul_alg3(ev, A, B, h, masks):
     # Step 2 (App. B multiplexer, applied after hoisting): A^(k) = v_k . R(A0, k)
     # + (1 - v_k) . R(A0, k-h); every rotation of A0 shares one ModUp and the
     # selection happens in the extended basis before a single ModDown per k.
+    # A^(k) stays at scale Delta*q_t (no rescale per k); B^(k) = R(B0, h*k)
+    # stays at the same level; A^(0) = q_t * A0.
     qt = ev.ctx.q[A0.limbs - 1]
-    D = ev.hoist(A0)
-    Ak = [ev.drop(A0, A0.limbs - 1)]
+    DA = ev.hoist(A0)
+    Bk = [B0] + ev.rotate_hoisted(B0, [beta * h * k for k in range(1, h)])
+    # Step 3: sum_k A^(k) (x) B^(k), one relinearisation, then the two rescales
+    acc = ev.tensor(ev.mul_int(A0, qt, new_scale=A0.scale * float(qt)), Bk[0])
     for k in range(1, h):
         v_ext, sc = masks.plaintext("v", k, extended=True)
-        Ak.append(ev.rescale(ev.hoisted_mux(A0, D, beta * k, beta * (k - h), v_ext, sc, qt)))
-    # B^(k) = Rot(B0, h*k): all rotations of one ciphertext, hoisted
-    B0d = ev.drop(B0, B0.limbs - 1)
-    Bk = [B0d] + ev.rotate_hoisted(B0d, [beta * h * k for k in range(1, h)])
-    # Step 3: sum_k A^(k) (x) B^(k), one relinearisation and one rescale (reading R10)
-    acc = ev.tensor(Ak[0], Bk[0])
-    for k in range(1, h):
-        acc = ev.add(acc, ev.tensor(Ak[k], Bk[k]))
-    return ev.rescale(ev.relinearize(acc))
+        Ak = ev.hoisted_mux(A0, DA, beta * k, beta * (k - h), v_ext, sc, qt)
+        acc = ev.add(acc, ev.tensor(Ak, Bk[k]))
+    return ev.rescale(ev.rescale(ev.relinearize(acc)))
 
 
 def _matmul_depth2(ev, A, B, h, masks):

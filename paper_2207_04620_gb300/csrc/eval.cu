@@ -187,16 +187,58 @@ Cts Eval::ks_finish(const BufPtr &D, const View &dnt, int B, int limbs, const Sw
     DevBuf acc((size_t)B * 2 * ext * N, s);
     View accv{acc.p, (size_t)2 * ext * N, (size_t)ext * N};
     launch_key_ip(lc(), accv, D->p, dnt.p, dnt.bstride, key.buf->p, ctx.n_all, ctx.n_q, K, limbs, nd, g, B);
-    // ModDown of both components
-    ntt_inplace(acc.p, (size_t)ext * N, 2 * B, iota_vec(limbs, K), iota_vec(ctx.n_q, K), true);
+    ctx.counters[C_KS] += B;
+    return moddown_add(accv, B, limbs, add, add_mask, add_g);
+}
+
+Cts Eval::moddown_add(const View &accv, int B, int limbs, const View &add, int add_mask, uint64_t add_g)
+{
+    const int N = ctx.N, K = ctx.K, ext = limbs + K;
+    ntt_inplace(accv.p, (size_t)ext * N, 2 * B, iota_vec(limbs, K), iota_vec(ctx.n_q, K), true);
     DevBuf conv((size_t)B * 2 * limbs * N, s);
     launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), limbs,
-                         View{conv.p, (size_t)limbs * N, 0}, View{acc.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0);
+                         View{conv.p, (size_t)limbs * N, 0}, View{accv.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0);
     ntt_inplace(conv.p, (size_t)limbs * N, 2 * B, iota_vec(0, limbs), iota_vec(0, limbs), false);
     Cts o = alloc(B, 2, limbs);
     launch_moddown_final(lc(), o.view(N), accv, View{conv.p, (size_t)2 * limbs * N, (size_t)limbs * N},
                          ctx.t.moddown + limbs, B, limbs, add, add_mask, add_g);
-    ctx.counters[C_KS] += B;
+    return o;
+}
+
+Cts Eval::rotate_sum(const std::vector<std::pair<Cts, int64_t>> &items, const hx_keyset &keys)
+{
+    HX_CHECK(!items.empty(), HX_EINVAL, "empty rotation sum");
+    const Cts &f = items[0].first;
+    const int N = ctx.N, K = ctx.K, limbs = f.limbs, B = f.B, ext = limbs + K, nd = (limbs + K - 1) / K;
+    Cts base = alloc(B, 2, limbs);
+    base.scale = f.scale;
+    HX_CUDA(cudaMemsetAsync(base.d, 0, sizeof(uint64_t) * base.bstride(N) * B, s));
+    DevBuf acc((size_t)B * 2 * ext * N, s);
+    View accv{acc.p, (size_t)2 * ext * N, (size_t)ext * N};
+    bool any = false;
+    for (auto &it : items) {
+        const Cts &ct = it.first;
+        check_same(ct, f);
+        const uint64_t g = galois_for_step(it.second, ctx.log_n);
+        if (g == 1) {
+            add_inplace(base, ct);
+            continue;
+        }
+        const SwitchKey &key = rot_key(keys, g);
+        Cts t = alloc(B, 1, limbs);
+        View c1{ct.d + ct.cstride(N), ct.bstride(N), ct.cstride(N)};
+        launch_automorphism(lc(), t.view(N), c1, g, B, 1, limbs);
+        BufPtr D = modup(t.view(N), B, limbs);
+        launch_key_ip(lc(), accv, D->p, t.d, t.bstride(N), key.buf->p, ctx.n_all, ctx.n_q, K, limbs, nd, 1, B, any);
+        launch_automorphism(lc(), base.view(N), ct.view(N), g, B, 1, limbs, true);  // base.c0 += sigma_g(c0)
+        any = true;
+        ctx.counters[C_ROT] += B;
+        ctx.counters[C_KS] += B;
+        ctx.counters[C_ADD] += B;
+    }
+    if (!any) return base;
+    Cts o = moddown_add(accv, B, limbs, base.view(N), 3, 1);
+    o.scale = f.scale;
     return o;
 }
 

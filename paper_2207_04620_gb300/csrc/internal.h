@@ -107,11 +107,13 @@ void launch_mul_plain(const LaunchCtx &c, View out, View a, const uint64_t *pt_m
 void launch_mul_scalar(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int comps, int limbs);
 void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int limbs);
 void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate);
-void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int B, int comps, int limbs);
+void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int B, int comps, int limbs,
+                         bool accumulate = false);
 void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int n_dst_rows_max, View out, View in,
                           int B, int groups, size_t group_stride_out, size_t group_stride_in);
 void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
-                   const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B);
+                   const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B,
+                   bool accumulate = false);
 // out_c = (acc_c - conv_c) * P^-1, plus add_c[galois(j)] for the components set in add_mask
 void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
                           int limbs, View add, int add_mask, uint64_t add_galois);

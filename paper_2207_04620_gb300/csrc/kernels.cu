@@ -365,14 +365,19 @@ __global__ void k_tensor(View out, View a, View b, const PrimeConst *__restrict_
     }
 }
 
-__global__ void k_automorphism(View out, View in, uint64_t g, int comps, int log_n)
+// out = sigma_g(in) (accumulate: out += sigma_g(in), rows modulo prime index = row)
+__global__ void k_automorphism(View out, View in, uint64_t g, int comps, int log_n, bool accumulate,
+                               const PrimeConst *__restrict__ primes)
 {
     const int n = 1 << log_n;
     const int l = blockIdx.y, bc = blockIdx.z, bi = bc / comps, ci = bc % comps;
     const size_t oo = bi * out.bstride + ci * out.cstride + (size_t)l * n;
     const size_t oi = bi * in.bstride + ci * in.cstride + (size_t)l * n;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-        out.p[oo + j] = in.p[oi + galois_src(j, g, log_n)];
+    const uint64_t q = accumulate ? primes[l].q : 0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const uint64_t v = in.p[oi + galois_src(j, g, log_n)];
+        out.p[oo + j] = accumulate ? addmod(out.p[oo + j], v, q) : v;
+    }
 }
 
 // Fast basis conversion; grid: x over coefficients, z = b * groups + grp
@@ -421,7 +426,7 @@ __global__ void k_basis_convert(const ConvTable *__restrict__ tabs, View out, Vi
 // elsewhere.  Keys are in Montgomery form, so one reduction gives the sum.
 __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt, size_t dnt_bstride,
                          const uint64_t *__restrict__ key, const PrimeConst *__restrict__ primes, int n_all, int n_q,
-                         int K, int limbs, int ndig, uint64_t g, int log_n)
+                         int K, int limbs, int ndig, uint64_t g, int log_n, bool accumulate)
 {
     const int n = 1 << log_n;
     const int t = blockIdx.y, bi = blockIdx.z;
@@ -441,8 +446,14 @@ __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_
             a0.mac(x, kd[0]);
             a1.mac(x, kd[(size_t)n_all * n]);
         }
-        acc.p[bi * acc.bstride + (size_t)t * n + j] = mont128(a0.hi, a0.lo, P);
-        acc.p[bi * acc.bstride + acc.cstride + (size_t)t * n + j] = mont128(a1.hi, a1.lo, P);
+        uint64_t r0 = mont128(a0.hi, a0.lo, P), r1 = mont128(a1.hi, a1.lo, P);
+        uint64_t *o0 = acc.p + bi * acc.bstride + (size_t)t * n + j, *o1 = o0 + acc.cstride;
+        if (accumulate) {
+            r0 = addmod(r0, *o0, P.q);
+            r1 = addmod(r1, *o1, P.q);
+        }
+        *o0 = r0;
+        *o1 = r1;
     }
 }
 
@@ -765,11 +776,12 @@ void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int lim
     post(c);
 }
 
-void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int B, int comps, int limbs)
+void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int B, int comps, int limbs,
+                         bool accumulate)
 {
-    Timed tm_(c, K_AUTO, 16.0 * B * comps * limbs * c.N);
+    Timed tm_(c, K_AUTO, (accumulate ? 24.0 : 16.0) * B * comps * limbs * c.N);
     dim3 grid(ew_blocks(c.N, 1), limbs, B * comps);
-    k_automorphism<<<grid, 256, 0, c.stream>>>(out, in, g, comps, c.log_n);
+    k_automorphism<<<grid, 256, 0, c.stream>>>(out, in, g, comps, c.log_n, accumulate, c.t->primes);
     post(c);
 }
 
@@ -784,12 +796,13 @@ void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int, Vie
 }
 
 void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
-                   const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B)
+                   const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B,
+                   bool accumulate)
 {
     Timed tm_(c, K_KEYIP, 8.0 * c.N * ((double)B * ndig * (limbs + K) + 2.0 * ndig * (limbs + K) + 2.0 * B * (limbs + K)));
     dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
     k_key_ip<<<grid, 256, 0, c.stream>>>(acc, D, dnt, dnt_bstride, key, c.t->primes, n_all, n_q, K, limbs, ndig, g,
-                                         c.log_n);
+                                         c.log_n, accumulate);
     post(c);
 }
 

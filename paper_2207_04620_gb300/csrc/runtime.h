@@ -137,6 +137,10 @@ struct Eval {
     BufPtr modup(const View &d, int B, int limbs);
     Cts ks_finish(const BufPtr &D, const View &dnt, int B, int limbs, const SwitchKey &key, uint64_t g,
                   const View &add, int add_mask, uint64_t add_g);
+    // ModDown of an extended-basis pair accv ([B][2][limbs+K][N]) plus `add`
+    Cts moddown_add(const View &accv, int B, int limbs, const View &add, int add_mask, uint64_t add_g);
+    // sum_i Rot(ct_i, k_i) with a single ModDown (terms with k = 0 are added unrotated)
+    Cts rotate_sum(const std::vector<std::pair<Cts, int64_t>> &items, const hx_keyset &keys);
     void ntt_inplace(uint64_t *p, size_t gstride, int groups, const std::vector<int> &rows_off,
                      const std::vector<int> &rows_prime, bool inverse);
     void ntt_oop(const uint64_t *src, size_t sgs, uint64_t *dst, size_t dgs, int groups,

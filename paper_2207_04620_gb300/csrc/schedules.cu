@@ -168,8 +168,7 @@ Cts lintrans(Eval &ev, const hx_keyset &ks, const Cts &ct, int lmin, int lmax, i
     std::vector<Cts> babies = ev.rotate_hoisted(ct, steps, ks);
     std::map<int, int> jpos;
     for (size_t k = 0; k < js.size(); k++) jpos[js[k]] = (int)k;
-    Cts acc;
-    bool have = false;
+    std::vector<std::pair<Cts, int64_t>> items;
     for (auto &kv : groups) {
         const int i = kv.first;
         Cts inner;
@@ -185,15 +184,10 @@ Cts lintrans(Eval &ev, const hx_keyset &ks, const Cts &ct, int lmin, int lmax, i
                 ev.add_inplace(inner, term);
             }
         }
-        if (i != 0) inner = ev.rotate(inner, (int64_t)beta * stride * b * i, ks);
-        if (!have) {
-            acc = inner;
-            have = true;
-        } else {
-            ev.add_inplace(acc, inner);
-        }
+        items.push_back({inner, (int64_t)beta * stride * b * i});
     }
-    return acc;
+    // giant steps: one ModDown for the whole sum
+    return ev.rotate_sum(items, ks);
 }
 
 Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Cts &A, const Cts &B)
@@ -203,21 +197,21 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
     Cts A0 = ev.rescale(lintrans(ev, ks, A, -h + 1, h - 1, 1, p, 0));
     Cts B0 = ev.rescale(lintrans(ev, ks, B, 0, h - 1, h, p, 1));
     // Step 2 (App. B multiplexer after hoisting): A^(k) = v_k . Rot(A0, k) + (1 - v_k) . Rot(A0, k-h),
-    // all rotations of A0 from one ModUp, the selection before a single ModDown per k
+    // all rotations of A0 from one ModUp, the selection before a single ModDown per k.  A^(k)
+    // keeps the mask scale (no rescale per k); B^(k) = Rot(B0, h*k) stays at the same level.
     const uint64_t qt = ctx.primes[A0.limbs - 1];
-    Cts A0d = ev.drop(A0, A0.limbs - 1);
-    Cts B0d = ev.drop(B0, B0.limbs - 1);
-    Cts acc = ev.tensor(A0d, B0d);
+    Cts acc = ev.tensor(ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt), B0);
     BufPtr DA = ev.hoist(A0);
-    BufPtr DB = ev.hoist(B0d);  // one ModUp serves every B^(k) = Rot(B0, h*k)
+    BufPtr DB = ev.hoist(B0);  // one ModUp serves every B^(k)
     for (int k = 1; k < h; k++) {
-        Cts Bk = ev.rotate_hoisted_one(B0d, DB, (int64_t)beta * h * k, ks);
+        Cts Bk = ev.rotate_hoisted_one(B0, DB, (int64_t)beta * h * k, ks);
         double sc;
         const uint64_t *v = mask_pt(p, 2, k, &sc);
-        Cts Ak = ev.rescale(ev.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, qt, ks));
+        Cts Ak = ev.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, qt, ks);
         ev.tensor_acc(acc, Ak, Bk);
     }
-    return ev.rescale(ev.relinearize(acc, ks.relin));
+    // Step 3: one relinearisation, then the two rescales
+    return ev.rescale(ev.rescale(ev.relinearize(acc, ks.relin)));
 }
 
 Cts matmul_depth2(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Cts &A, const Cts &B)
