@@ -190,6 +190,7 @@ def run_hx(args, world, rank, local):
     barrier(world)
     stream = torch.cuda.current_stream()
     ctx = hx.hx_context_create(LOG_N, Q_BITS, P_BITS, LOG2_SCALE)
+    tiles = hx.hx_autotune(ctx, stream=torch.cuda.current_stream())
     limbs = len(Q_BITS)
     steps = hx.hx_matmul_rotation_steps(ctx, H, limbs)
     ks = hx.hx_keygen(ctx, 2, 2024 + rank, steps)
@@ -308,7 +309,8 @@ def run_hx(args, world, rank, local):
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
                 "config": {"workload": WORKLOAD, "parallelism": "replicas only (one independent batch per GPU)",
                            "l2": "flushed between timed steps (512 MB write outside the events)",
-                           "per_step_launch": "one hx_matmul_batch C-ABI call"},
+                           "per_step_launch": "one hx_matmul_batch C-ABI call",
+                           "ntt_tiles_autotuned": tiles},
                 "e2e": {"value": round(PRODUCTS * world / e2e_s, 2), "unit": "matmul/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                 "gpu_launches": launches,
@@ -347,6 +349,7 @@ def run_micro(args):
     __graft_entry__.build()
     log_n = args.log_n
     ctx = hx.hx_context_create(log_n, Q_BITS, P_BITS, LOG2_SCALE)
+    tiles = hx.hx_autotune(ctx) if args.tiles is None else hx.hx_ntt_tiles(ctx, [int(t) for t in args.tiles.split(",")])
     primes = hx.hx_context_primes(ctx)
     n = 1 << log_n
     rows = args.rows
@@ -372,7 +375,7 @@ def run_micro(args):
         iv.append(e[1].elapsed_time(e[2]))
     byt = 16.0 * polys * per * n
     peak, kind = peaks()
-    res = {"micro": "ntt", "log_n": log_n, "rows": polys * per, "bytes_per_transform": byt,
+    res = {"micro": "ntt", "log_n": log_n, "rows": polys * per, "bytes_per_transform": byt, "tiles": tiles,
            "fwd_ms": statistics.median(fw), "inv_ms": statistics.median(iv),
            "fwd_gbs": byt / statistics.median(fw) / 1e6, "inv_gbs": byt / statistics.median(iv) / 1e6,
            "peak_gbs": peak, "peak_kind": kind}
@@ -387,6 +390,7 @@ def main():
     ap.add_argument("--micro", choices=["ntt"], default=None)
     ap.add_argument("--log-n", type=int, default=14)
     ap.add_argument("--rows", type=int, default=1600)
+    ap.add_argument("--tiles", default=None, help="NTT tile widths per phase, e.g. 16,16,16,16 (default: autotune)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)

@@ -222,6 +222,17 @@ hx_status hx_sign_approx_batch(hx_context *ctx, const hx_keyset *ks, const hx_ct
 int hx_counters(const hx_context *ctx, uint64_t *out, int cap);
 void hx_counters_reset(hx_context *ctx);
 
+/* ---- autotuning ------------------------------------------------------------- */
+/* Times each NTT tile width (8, 16 or 32 sub-transforms per block, for each of
+ * the four phase kernels: forward column, forward row, inverse column, inverse
+ * row) on this device with a scratch buffer of 256 limbs, and keeps the fastest
+ * for the context.  Every choice computes identical residues.  choice[4]
+ * (may be NULL) receives the chosen widths. */
+hx_status hx_autotune(hx_context *ctx, int32_t *choice, void *stream);
+/* Sets (set != NULL: widths 8, 16 or 32 per phase, in the order above) and/or
+ * reads (get != NULL) the NTT tile widths of the context. */
+hx_status hx_ntt_tiles(hx_context *ctx, const int32_t *set, int32_t *get);
+
 /* ---- profiling ------------------------------------------------------------- */
 /* While enabled, every kernel launch of the context is bracketed by CUDA events
  * recorded on its launching stream, grouped by kernel class.  Enabling clears

@@ -501,6 +501,47 @@ void hx_counters_reset(hx_context *ctx)
     if (ctx) memset(ctx->counters, 0, sizeof(ctx->counters));
 }
 
+hx_status hx_autotune(hx_context *ctx, int32_t *choice, void *stream)
+{
+    HX_TRY
+    need(ctx, "null argument");
+    const int rows = 256;
+    DevBuf buf((size_t)rows * ctx->N, S(stream));
+    HX_CUDA(cudaMemsetAsync(buf.p, 0, sizeof(uint64_t) * rows * ctx->N, S(stream)));
+    Eval ev(*ctx, S(stream));
+    int best[4] = {1, 1, 1, 1};
+    float ms[4];
+    autotune_ntt(ev.lc(), buf.p, rows, best, ms);
+    static const int widths[NTT_VARIANTS] = {8, 16, 32};
+    for (int i = 0; i < 4; i++) {
+        ctx->t.ntt_var[i] = best[i];
+        if (choice) choice[i] = widths[best[i]];
+    }
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_ntt_tiles(hx_context *ctx, const int32_t *set, int32_t *get)
+{
+    HX_TRY
+    need(ctx, "null argument");
+    static const int widths[NTT_VARIANTS] = {8, 16, 32};
+    if (set) {
+        int v[4];
+        for (int i = 0; i < 4; i++) {
+            v[i] = -1;
+            for (int k = 0; k < NTT_VARIANTS; k++)
+                if (set[i] == widths[k]) v[i] = k;
+            need(v[i] >= 0, "tile width must be 8, 16 or 32");
+        }
+        for (int i = 0; i < 4; i++) ctx->t.ntt_var[i] = v[i];
+    }
+    if (get)
+        for (int i = 0; i < 4; i++) get[i] = widths[ctx->t.ntt_var[i]];
+    return HX_OK;
+    HX_END
+}
+
 hx_status hx_profile_enable(hx_context *ctx, int on)
 {
     HX_TRY

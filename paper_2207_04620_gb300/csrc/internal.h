@@ -16,6 +16,7 @@ namespace hx {
 constexpr int MAXP = HX_MAX_Q + HX_MAX_P;
 constexpr int MAXK = HX_MAX_P;
 constexpr int MAX_NTT_ROWS = 1024;
+constexpr int NTT_VARIANTS = 3;  // tile widths 8, 16, 32
 
 // Fast basis conversion table (Han-Ki hybrid key switching, no correction):
 // out_t = sum_i [x_i * qhat_i^-1]_{q_i} * (qhat_i mod t)  (mod t)
@@ -59,6 +60,17 @@ struct Scalars {
     uint64_t v[MAXP], sh[MAXP];
 };
 
+// Inner sums of a baby-step/giant-step linear transform: for every group g,
+// out_g = sum_m baby_m (.) mask[g][m] over the babies whose mask is present.
+constexpr int MAC_MAX_BABY = 16, MAC_MAX_GROUP = 32;
+struct MacArgs {
+    int n_baby, n_group;
+    const uint64_t *baby[MAC_MAX_BABY];
+    size_t baby_bstride, baby_cstride;
+    const uint64_t *mask[MAC_MAX_GROUP][MAC_MAX_BABY];  // Montgomery form, [limbs][N]; null if absent
+    uint64_t *out;                                      // [group][B][2][limbs][N]
+};
+
 // A batch of polynomials with `comps` components of `limbs` rows each:
 // word (b, c, l, j) at p + b*bstride + c*cstride + l*N + j.
 struct View {
@@ -73,6 +85,7 @@ struct DeviceTables {
     ConvTable *modup = nullptr;     // [(n_q+1) * dnum] by (limbs, digit)
     ModDownTable *moddown = nullptr;// [n_q+1] by limbs
     RescaleTable *rescale = nullptr;// [n_q+1] by limbs
+    int ntt_var[4] = {1, 1, 1, 1};  // tile width per phase: fwd cols, fwd rows, inv cols, inv rows
 };
 
 // Per-kernel-class timing with CUDA events recorded on the launching stream
@@ -101,6 +114,8 @@ struct LaunchCtx {
 };
 
 void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse);
+// times the NTT tile widths on `rows` limbs of buf and writes the fastest per phase
+void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float *ms_out);
 void launch_add(const LaunchCtx &c, View out, View a, View b, int B, int comps, int limbs, bool sub);
 void launch_copy(const LaunchCtx &c, View out, View a, int B, int comps, int limbs);
 void launch_mul_plain(const LaunchCtx &c, View out, View a, const uint64_t *pt_mont, int B, int limbs);
@@ -117,6 +132,7 @@ void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64
 // out_c = (acc_c - conv_c) * P^-1, plus add_c[galois(j)] for the components set in add_mask
 void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
                           int limbs, View add, int add_mask, uint64_t add_galois);
+void launch_lintrans_mac(const LaunchCtx &c, const MacArgs &a, int B, int limbs, int n_terms);
 // two hoisted rotations selected by a mask in the extended basis (see kernels.cu)
 void launch_key_ip_mux(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
                        const uint64_t *key1, const uint64_t *key2, const uint64_t *v, const Scalars &cs, int n_all,

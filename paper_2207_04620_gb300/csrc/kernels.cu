@@ -109,7 +109,8 @@ template <int L> struct Split {
     static constexpr int R2 = L - R1;       // second pass
 };
 
-// column phase: the first LOGM stages on M rows of stride N2 (COLS adjacent columns per block)
+// column phase: the first LOGM stages on M rows of stride N2 (COLS adjacent columns
+// per block); its twiddles (indices below M) are staged in shared memory
 template <int LOGM, int COLS, bool INV>
 __global__ void __launch_bounds__((1 << (LOGM - Split<LOGM>::R1)) * COLS)
 k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
@@ -118,6 +119,7 @@ k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
     constexpr int M = 1 << LOGM, E = M * COLS, R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
     constexpr int T = (M >> R1) * COLS;
     extern __shared__ uint64_t sh[];
+    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(sh + E);
     const int N = 1 << log_n, N2 = N >> LOGM;
     const int row = blockIdx.y, g = blockIdx.z;
     const int pr = R.prime[row];
@@ -128,18 +130,19 @@ k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
     const PrimeConst P = primes[pr];
     const ulonglong2 *tw = tw_all + (size_t)pr * N;
     const int c0 = blockIdx.x * COLS;
+    for (int i = threadIdx.x; i < M; i += T) stw[i] = tw[i];
     for (int i = threadIdx.x; i < E; i += T) sh[i] = src[(size_t)(i / COLS) * N2 + c0 + (i % COLS)];
     __syncthreads();
     if (!INV) {
-        ntt_pass<LOGM, R1, 0, false, true, false>(sh, COLS, 1, COLS, tw, 0, 0, 0, P.q, T);
+        ntt_pass<LOGM, R1, 0, false, true, false>(sh, COLS, 1, COLS, stw, 0, 0, 0, P.q, T);
         __syncthreads();
-        ntt_pass<LOGM, R2, R1, false, true, false>(sh, COLS, 1, COLS, tw, 0, 0, 0, P.q, T);
+        ntt_pass<LOGM, R2, R1, false, true, false>(sh, COLS, 1, COLS, stw, 0, 0, 0, P.q, T);
         __syncthreads();
         for (int i = threadIdx.x; i < E; i += T) dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = sh[i];
     } else {
-        ntt_pass<LOGM, R2, R1, true, true, false>(sh, COLS, 1, COLS, tw, 0, 0, 0, P.q, T);
+        ntt_pass<LOGM, R2, R1, true, true, false>(sh, COLS, 1, COLS, stw, 0, 0, 0, P.q, T);
         __syncthreads();
-        ntt_pass<LOGM, R1, 0, true, true, false>(sh, COLS, 1, COLS, tw, 0, 0, 0, P.q, T);
+        ntt_pass<LOGM, R1, 0, true, true, false>(sh, COLS, 1, COLS, stw, 0, 0, 0, P.q, T);
         __syncthreads();
         for (int i = threadIdx.x; i < E; i += T)
             dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = shoup(sh[i], P.n_inv, P.n_inv_sh, P.q);
@@ -198,16 +201,19 @@ k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
     }
 }
 
-template <int LOGM, bool INV>
-void ntt_cols(const LaunchCtx &c, const NttRows &rows)
+// tile widths the autotuner chooses from (sub-transforms per block)
+constexpr int kNttTiles[NTT_VARIANTS] = {8, 16, 32};
+
+template <int LOGM, int COLS, bool INV>
+void ntt_cols_w(const LaunchCtx &c, const NttRows &rows)
 {
     constexpr int M = 1 << LOGM;
-    constexpr int COLS = (M >= 256) ? 16 : 2048 / M;
     constexpr int E = M * COLS;
     constexpr int T = (M >> Split<LOGM>::R1) * COLS;
     const int N2 = c.N >> LOGM;
+    HX_CHECK(N2 % COLS == 0, HX_EINVAL, "NTT tile wider than the ring");
     dim3 grid(N2 / COLS, rows.n_rows, rows.n_groups);
-    const size_t smem = (size_t)E * 8;
+    const size_t smem = (size_t)E * 8 + (size_t)M * 16;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_ntt_cols<LOGM, COLS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -217,13 +223,13 @@ void ntt_cols(const LaunchCtx &c, const NttRows &rows)
                                                             c.log_n);
 }
 
-template <int LOGM, bool INV>
-void ntt_rows(const LaunchCtx &c, const NttRows &rows)
+template <int LOGM, int ROWS, bool INV>
+void ntt_rows_w(const LaunchCtx &c, const NttRows &rows)
 {
     constexpr int M = 1 << LOGM;
-    constexpr int ROWS = (M >= 256) ? 16 : 2048 / M;
     constexpr int T = (M >> Split<LOGM>::R1) * ROWS;
     const int N1 = c.N >> LOGM;
+    HX_CHECK(N1 % ROWS == 0, HX_EINVAL, "NTT tile wider than the ring");
     dim3 grid(N1 / ROWS, rows.n_rows, rows.n_groups);
     const size_t smem = (size_t)ROWS * (M + M / 16) * 8;
     static bool attr = false;
@@ -235,26 +241,31 @@ void ntt_rows(const LaunchCtx &c, const NttRows &rows)
                                                             c.log_n);
 }
 
-template <bool INV>
-void ntt_cols_dispatch(const LaunchCtx &c, const NttRows &r, int logm)
+template <bool INV, int LOGM>
+void ntt_phase_l(const LaunchCtx &c, const NttRows &r, bool cols, int var)
 {
-    switch (logm) {
-    case 5: ntt_cols<5, INV>(c, r); break;
-    case 6: ntt_cols<6, INV>(c, r); break;
-    case 7: ntt_cols<7, INV>(c, r); break;
-    case 8: ntt_cols<8, INV>(c, r); break;
-    default: throw Error{HX_EINVAL, "unsupported NTT size"};
+    // the tile must not be wider than the other dimension of the ring
+    const int other = c.N >> LOGM;
+    while (var > 0 && kNttTiles[var] > other) var--;
+    if (cols) {
+        if (var == 0) ntt_cols_w<LOGM, 8, INV>(c, r);
+        else if (var == 1) ntt_cols_w<LOGM, 16, INV>(c, r);
+        else ntt_cols_w<LOGM, 32, INV>(c, r);
+    } else {
+        if (var == 0) ntt_rows_w<LOGM, 8, INV>(c, r);
+        else if (var == 1) ntt_rows_w<LOGM, 16, INV>(c, r);
+        else ntt_rows_w<LOGM, 32, INV>(c, r);
     }
 }
 
 template <bool INV>
-void ntt_rows_dispatch(const LaunchCtx &c, const NttRows &r, int logm)
+void ntt_phase(const LaunchCtx &c, const NttRows &r, bool cols, int logm, int var)
 {
     switch (logm) {
-    case 5: ntt_rows<5, INV>(c, r); break;
-    case 6: ntt_rows<6, INV>(c, r); break;
-    case 7: ntt_rows<7, INV>(c, r); break;
-    case 8: ntt_rows<8, INV>(c, r); break;
+    case 5: ntt_phase_l<INV, 5>(c, r, cols, var); break;
+    case 6: ntt_phase_l<INV, 6>(c, r, cols, var); break;
+    case 7: ntt_phase_l<INV, 7>(c, r, cols, var); break;
+    case 8: ntt_phase_l<INV, 8>(c, r, cols, var); break;
     default: throw Error{HX_EINVAL, "unsupported NTT size"};
     }
 }
@@ -286,6 +297,30 @@ __global__ void k_copy(View out, View a, int comps, int n)
     const size_t oa = bi * a.bstride + ci * a.cstride + (size_t)l * n;
     for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2)
         *reinterpret_cast<ulonglong2 *>(out.p + oo + j) = *reinterpret_cast<const ulonglong2 *>(a.p + oa + j);
+}
+
+__global__ void k_lintrans_mac(const __grid_constant__ MacArgs A, const PrimeConst *__restrict__ primes, int B,
+                               int limbs, int n)
+{
+    const int l = blockIdx.y, bc = blockIdx.z, bi = bc / 2, ci = bc % 2;
+    const PrimeConst P = primes[l];
+    const size_t ob = bi * A.baby_bstride + ci * A.baby_cstride + (size_t)l * n;
+    const size_t gstride = (size_t)B * 2 * limbs * n;
+    const size_t oo = ((size_t)bi * 2 + ci) * limbs * n + (size_t)l * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        uint64_t v[MAC_MAX_BABY];
+#pragma unroll
+        for (int m = 0; m < MAC_MAX_BABY; m++) v[m] = m < A.n_baby ? A.baby[m][ob + j] : 0;
+        for (int g = 0; g < A.n_group; g++) {
+            Acc128 acc;
+#pragma unroll
+            for (int m = 0; m < MAC_MAX_BABY; m++) {
+                const uint64_t *mk = A.mask[g][m];
+                if (m < A.n_baby && mk) acc.mac(v[m], mk[(size_t)l * n + j]);
+            }
+            A.out[g * gstride + oo + j] = mont128(acc.hi, acc.lo, P);
+        }
+    }
 }
 
 // out_c = a_c * pt  with pt in Montgomery form (pt * 2^64 mod q): one reduction
@@ -718,14 +753,60 @@ void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse)
     if (rows.n_rows <= 0 || rows.n_groups <= 0) return;
     HX_CHECK(rows.n_rows <= MAX_NTT_ROWS && rows.n_groups < 65536, HX_EINVAL, "NTT batch too large");
     const int logm1 = c.log_n / 2, logm2 = c.log_n - logm1;
+    const int *v = c.t->ntt_var;
     if (!inverse) {
-        ntt_cols_dispatch<false>(c, rows, logm1);
-        ntt_rows_dispatch<false>(c, rows, logm2);
+        ntt_phase<false>(c, rows, true, logm1, v[0]);
+        ntt_phase<false>(c, rows, false, logm2, v[1]);
     } else {
-        ntt_rows_dispatch<true>(c, rows, logm2);
-        ntt_cols_dispatch<true>(c, rows, logm1);
+        ntt_phase<true>(c, rows, false, logm2, v[3]);
+        ntt_phase<true>(c, rows, true, logm1, v[2]);
     }
     post(c, 2);
+}
+
+void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float *ms_out)
+{
+    // times every tile width of each phase on `rows` limbs (one prime each) in place
+    NttRows *r = new NttRows();
+    std::unique_ptr<NttRows> guard(r);
+    r->src = r->dst = buf;
+    r->src_gs = r->dst_gs = 0;
+    r->n_groups = 1;
+    r->n_rows = rows;
+    for (int i = 0; i < rows; i++) {
+        r->src_off[i] = r->dst_off[i] = (int16_t)i;
+        r->prime[i] = 0;
+    }
+    const int logm1 = c.log_n / 2, logm2 = c.log_n - logm1;
+    cudaEvent_t e0, e1;
+    HX_CUDA(cudaEventCreate(&e0));
+    HX_CUDA(cudaEventCreate(&e1));
+    for (int ph = 0; ph < 4; ph++) {
+        const bool cols = ph == 0 || ph == 2, inv = ph >= 2;
+        float best_ms = 1e30f;
+        for (int v = 0; v < NTT_VARIANTS; v++) {
+            if (kNttTiles[v] > (c.N >> (cols ? logm1 : logm2))) continue;
+            auto run = [&]() {
+                if (inv) ntt_phase<true>(c, *r, cols, cols ? logm1 : logm2, v);
+                else ntt_phase<false>(c, *r, cols, cols ? logm1 : logm2, v);
+            };
+            run();  // warm-up
+            HX_CUDA(cudaEventRecord(e0, c.stream));
+            for (int it = 0; it < 5; it++) run();
+            HX_CUDA(cudaEventRecord(e1, c.stream));
+            HX_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            HX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best[ph] = v;
+            }
+        }
+        if (ms_out) ms_out[ph] = best_ms / 5;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    HX_CUDA(cudaGetLastError());
 }
 
 void launch_add(const LaunchCtx &c, View out, View a, View b, int B, int comps, int limbs, bool sub)
@@ -803,6 +884,14 @@ void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64
     dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
     k_key_ip<<<grid, 256, 0, c.stream>>>(acc, D, dnt, dnt_bstride, key, c.t->primes, n_all, n_q, K, limbs, ndig, g,
                                          c.log_n, accumulate);
+    post(c);
+}
+
+void launch_lintrans_mac(const LaunchCtx &c, const MacArgs &a, int B, int limbs, int n_terms)
+{
+    Timed tm_(c, K_MULPT, 8.0 * limbs * c.N * ((double)B * 2 * (a.n_baby + a.n_group) + n_terms));
+    dim3 grid(ew_blocks(c.N, 1), limbs, B * 2);
+    k_lintrans_mac<<<grid, 256, 0, c.stream>>>(a, c.t->primes, B, limbs, c.N);
     post(c);
 }
 

@@ -168,23 +168,42 @@ Cts lintrans(Eval &ev, const hx_keyset &ks, const Cts &ct, int lmin, int lmax, i
     std::vector<Cts> babies = ev.rotate_hoisted(ct, steps, ks);
     std::map<int, int> jpos;
     for (size_t k = 0; k < js.size(); k++) jpos[js[k]] = (int)k;
-    std::vector<std::pair<Cts, int64_t>> items;
+    // every inner sum sum_j Mul_pt(baby_j, mask_(i,j)) in one fused launch
+    HX_CHECK((int)js.size() <= MAC_MAX_BABY && (int)groups.size() <= MAC_MAX_GROUP, HX_EINVAL,
+             "linear transform too wide for the fused inner sums");
+    const int N = ev.ctx.N, B = ct.B, limbs = ct.limbs;
+    std::unique_ptr<MacArgs> ma(new MacArgs());
+    ma->n_baby = (int)js.size();
+    ma->n_group = (int)groups.size();
+    for (size_t m = 0; m < js.size(); m++) ma->baby[m] = babies[m].d;
+    ma->baby_bstride = babies[0].bstride(N);
+    ma->baby_cstride = babies[0].cstride(N);
+    double sc = 0;
+    int g = 0, n_terms = 0;
     for (auto &kv : groups) {
-        const int i = kv.first;
-        Cts inner;
-        bool hi = false;
         for (auto &jl : kv.second) {
-            double sc;
-            const uint64_t *pt = mask_pt(p, kind, jl.second, &sc);
-            Cts term = ev.mul_plain(babies[jpos[jl.first]], pt, sc);
-            if (!hi) {
-                inner = term;
-                hi = true;
-            } else {
-                ev.add_inplace(inner, term);
-            }
+            ma->mask[g][jpos[jl.first]] = mask_pt(p, kind, jl.second, &sc);
+            n_terms++;
         }
-        items.push_back({inner, (int64_t)beta * stride * b * i});
+        g++;
+    }
+    BufPtr inner_buf = std::make_shared<DevBuf>((size_t)ma->n_group * B * 2 * limbs * N, ev.s);
+    ma->out = inner_buf->p;
+    launch_lintrans_mac(ev.lc(), *ma, B, limbs, n_terms);
+    ev.ctx.counters[C_MULPT] += (uint64_t)B * n_terms;
+    ev.ctx.counters[C_ADD] += (uint64_t)B * (n_terms - ma->n_group);
+    std::vector<std::pair<Cts, int64_t>> items;
+    g = 0;
+    for (auto &kv : groups) {
+        Cts inner;
+        inner.buf = inner_buf;
+        inner.d = inner_buf->p + (size_t)g * B * 2 * limbs * N;
+        inner.B = B;
+        inner.comps = 2;
+        inner.limbs = inner.cap = limbs;
+        inner.scale = ct.scale * sc;
+        items.push_back({inner, (int64_t)beta * stride * b * kv.first});
+        g++;
     }
     // giant steps: one ModDown for the whole sum
     return ev.rotate_sum(items, ks);

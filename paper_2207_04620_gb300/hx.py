@@ -84,6 +84,8 @@ _SIGS = {
     "hx_sign_approx_batch": (c_int, [c_vp, c_vp, PP, c_size_t, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
     "hx_counters": (c_int, [c_vp, P_u64, c_int]),
     "hx_counters_reset": (None, [c_vp]),
+    "hx_autotune": (c_int, [c_vp, P_i32, c_vp]),
+    "hx_ntt_tiles": (c_int, [c_vp, P_i32, P_i32]),
     "hx_profile_enable": (c_int, [c_vp, c_int]),
     "hx_profile_read": (c_int, [c_vp, c_int, ctypes.c_char_p, c_size_t, P_u64, P_dbl, P_dbl]),
 }
@@ -397,6 +399,27 @@ def hx_counters(ctx: int) -> dict:
 
 def hx_counters_reset(ctx: int) -> None:
     lib().hx_counters_reset(ctx)
+
+
+# ---- autotuning --------------------------------------------------------------------------
+
+def hx_autotune(ctx: int, stream=None) -> list:
+    """Picks the fastest NTT tile widths on this device; returns them per phase
+    (forward column, forward row, inverse column, inverse row)."""
+    arr = np.zeros(4, dtype=np.int32)
+    _chk(lib().hx_autotune(ctx, arr.ctypes.data_as(P_i32), _stream(stream)))
+    return [int(x) for x in arr]
+
+
+def hx_ntt_tiles(ctx: int, widths=None) -> list:
+    """Sets the NTT tile widths per phase (if given) and returns the current ones."""
+    get = np.zeros(4, dtype=np.int32)
+    setp = None
+    if widths is not None:
+        arr = np.ascontiguousarray(np.array(widths, dtype=np.int32))
+        setp = arr.ctypes.data_as(P_i32)
+    _chk(lib().hx_ntt_tiles(ctx, setp, get.ctypes.data_as(P_i32)))
+    return [int(x) for x in get]
 
 
 # ---- profiling --------------------------------------------------------------------------

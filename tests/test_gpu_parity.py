@@ -67,6 +67,31 @@ def test_ntt_bit_exact(log_n):
         hx.hx_context_destroy(ctx)
 
 
+@pytest.mark.parametrize("log_n", [11, 14, 16])
+def test_ntt_every_tile_width_and_autotune(log_n):
+    import torch
+
+    octx = C.Context(log_n, [60, 45], [61], 40)
+    ctx = hx.hx_context_create(log_n, [60, 45], [61], 40)
+    try:
+        primes = octx.q + octx.p
+        x = workloads.residues(3, primes, 2, octx.N)
+        want = octx.ntt(x, primes * 2)
+        for w in ([8] * 4, [16] * 4, [32] * 4, [8, 32, 16, 8]):
+            hx.hx_ntt_tiles(ctx, w)
+            dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
+            hx.hx_ntt(ctx, dev.data_ptr(), 2, [0, 1, 2])
+            torch.cuda.synchronize()
+            assert np.array_equal(dev.cpu().numpy().view(np.uint64), want), w
+            hx.hx_ntt(ctx, dev.data_ptr(), 2, [0, 1, 2], inverse=True)
+            torch.cuda.synchronize()
+            assert np.array_equal(dev.cpu().numpy().view(np.uint64), x), w
+        chosen = hx.hx_autotune(ctx)
+        assert all(c in (8, 16, 32) for c in chosen) and hx.hx_ntt_tiles(ctx) == chosen
+    finally:
+        hx.hx_context_destroy(ctx)
+
+
 def test_ntt_edge_cases(cfg0):
     import torch
 
