@@ -204,6 +204,21 @@ hx_status hx_matmul(hx_context *ctx, const hx_keyset *ks, const hx_ct *A, const 
 hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *A,
                           const hx_ct *const *B, int h, size_t count, hx_ct **out, void *stream);
 
+/* A captured batched product: the whole schedule of hx_matmul_batch for
+ * `count` ciphertext pairs at the plan's level, recorded once into a CUDA graph
+ * (its temporary allocations become graph memory nodes) over persistent input
+ * and output buffers.  hx_matmul_exec_run copies the inputs in, launches the
+ * graph on `stream` and returns fresh output handles; the residues equal
+ * hx_matmul_batch's.  Runs of one executor must not overlap. */
+typedef struct hx_matmul_exec hx_matmul_exec;
+hx_status hx_matmul_exec_create(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, size_t count,
+                                double scale, hx_matmul_exec **out);
+hx_status hx_matmul_exec_run(hx_matmul_exec *ex, const hx_ct *const *A, const hx_ct *const *B, hx_ct **out,
+                             void *stream);
+/* kernel launches one replay contains */
+int64_t hx_matmul_exec_launches(const hx_matmul_exec *ex);
+void hx_matmul_exec_destroy(hx_matmul_exec *ex);
+
 /* ---- sign / ReLU (Sec. 4, Alg. 5) ------------------------------------------ */
 /* g_d^(k)(x) (relu = 0) or ReLU(x) = x (1 + g_d^(k)(x)) / 2 (relu = 1), d in
  * [1, 4].  When the next composition no longer fits in the remaining levels,

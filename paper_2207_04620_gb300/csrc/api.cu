@@ -465,6 +465,109 @@ hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_
     HX_END
 }
 
+hx_status hx_matmul_exec_create(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, size_t count,
+                                double scale, hx_matmul_exec **out)
+{
+    HX_TRY
+    need(ctx && ks && plan && out && count >= 1 && count < 4096 && scale > 0, "bad argument");
+    *out = nullptr;
+    std::unique_ptr<hx_matmul_exec> ex(new hx_matmul_exec);
+    ex->ctx = ctx;
+    ex->ks = ks;
+    ex->plan = plan;
+    ex->count = count;
+    const size_t N = ctx->N;
+    auto persistent = [&](int limbs) {
+        Cts c;
+        c.B = (int)count;
+        c.comps = 2;
+        c.limbs = c.cap = limbs;
+        c.buf = std::make_shared<DevBuf>((size_t)count * 2 * limbs * N, true);
+        c.d = c.buf->p;
+        c.scale = scale;
+        return c;
+    };
+    ex->A = persistent(plan->limbs);
+    ex->B = persistent(plan->limbs);
+    ex->out = persistent(plan->alg3 ? plan->limbs - 3 : plan->limbs - 2);  // allocated before the capture
+    HX_CUDA(cudaMemset(ex->A.d, 0, sizeof(uint64_t) * ex->A.bstride(N) * count));
+    HX_CUDA(cudaMemset(ex->B.d, 0, sizeof(uint64_t) * ex->B.bstride(N) * count));
+    HX_CUDA(cudaDeviceSynchronize());
+    HX_CUDA(cudaStreamCreateWithFlags(&ex->cap, cudaStreamNonBlocking));
+    const uint64_t l0 = ctx->counters[C_LAUNCH];
+    uint64_t saved[C_NUM];
+    memcpy(saved, ctx->counters, sizeof(saved));
+    const bool prof = ctx->profiling;
+    ctx->profiling = false;
+    cudaGraph_t graph = nullptr;
+    HX_CUDA(cudaStreamBeginCapture(ex->cap, cudaStreamCaptureModeThreadLocal));
+    try {
+        Cts r = matmul_batch(*ctx, *ks, *plan, ex->A, ex->B, ex->cap);
+        HX_CHECK(r.limbs == ex->out.limbs, HX_EINVAL, "unexpected output level");
+        ex->out.scale = r.scale;
+        HX_CUDA(cudaMemcpyAsync(ex->out.d, r.d, sizeof(uint64_t) * r.bstride(N) * count, cudaMemcpyDeviceToDevice,
+                                ex->cap));
+    } catch (...) {
+        cudaStreamEndCapture(ex->cap, &graph);
+        if (graph) cudaGraphDestroy(graph);
+        ctx->profiling = prof;
+        throw;
+    }
+    HX_CUDA(cudaStreamEndCapture(ex->cap, &graph));
+    ctx->profiling = prof;
+    ex->launches = (int64_t)(ctx->counters[C_LAUNCH] - l0);
+    memcpy(ctx->counters, saved, sizeof(saved));  // a capture executes nothing
+    cudaError_t e = cudaGraphInstantiate(&ex->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    HX_CUDA(e);
+    *out = ex.release();
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_matmul_exec_run(hx_matmul_exec *ex, const hx_ct *const *A, const hx_ct *const *B, hx_ct **out,
+                             void *stream)
+{
+    HX_TRY
+    need(ex && A && B && out, "null argument");
+    hx_context &ctx = *ex->ctx;
+    const size_t N = ctx.N;
+    for (size_t i = 0; i < ex->count; i++) {
+        out[i] = nullptr;
+        need(A[i] && B[i], "null ciphertext");
+        HX_CHECK(A[i]->c.limbs == ex->plan->limbs && B[i]->c.limbs == ex->plan->limbs, HX_ELEVEL,
+                 "inputs are not at the executor's level");
+        HX_CHECK(A[i]->c.scale == ex->A.scale && B[i]->c.scale == ex->A.scale, HX_ESCALE,
+                 "inputs must have the executor's scale");
+    }
+    cudaStream_t s = S(stream);
+    for (size_t i = 0; i < ex->count; i++)
+        for (int c = 0; c < 2; c++) {
+            HX_CUDA(cudaMemcpyAsync(ex->A.d + i * ex->A.bstride(N) + c * ex->A.cstride(N),
+                                    A[i]->c.d + c * A[i]->c.cstride(N), sizeof(uint64_t) * ex->A.limbs * N,
+                                    cudaMemcpyDeviceToDevice, s));
+            HX_CUDA(cudaMemcpyAsync(ex->B.d + i * ex->B.bstride(N) + c * ex->B.cstride(N),
+                                    B[i]->c.d + c * B[i]->c.cstride(N), sizeof(uint64_t) * ex->B.limbs * N,
+                                    cudaMemcpyDeviceToDevice, s));
+        }
+    HX_CUDA(cudaGraphLaunch(ex->exec, s));
+    ctx.counters[C_LAUNCH] += ex->launches;
+    scatter(ctx, ex->out, out, s);
+    return HX_OK;
+    HX_END
+}
+
+int64_t hx_matmul_exec_launches(const hx_matmul_exec *ex) { return ex ? ex->launches : HX_EINVAL; }
+
+void hx_matmul_exec_destroy(hx_matmul_exec *ex)
+{
+    if (!ex) return;
+    cudaDeviceSynchronize();
+    if (ex->exec) cudaGraphExecDestroy(ex->exec);
+    if (ex->cap) cudaStreamDestroy(ex->cap);
+    delete ex;
+}
+
 hx_status hx_sign_approx(hx_context *ctx, const hx_keyset *ks, const hx_ct *x, int d, int k, int relu,
                          int allow_refresh, uint64_t refresh_seed, hx_ct **out, void *stream)
 {

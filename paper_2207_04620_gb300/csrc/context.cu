@@ -17,9 +17,24 @@ DevBuf::DevBuf(size_t w, cudaStream_t s) : words(w), stream(s)
     }
 }
 
+DevBuf::DevBuf(size_t w, bool) : words(w), pooled(false)
+{
+    if (w == 0) return;
+    cudaError_t e = cudaMalloc((void **)&p, w * sizeof(uint64_t));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{HX_ENOMEM, std::string("device allocation of ") + std::to_string(w * 8) + " bytes failed: " +
+                                   cudaGetErrorString(e)};
+    }
+}
+
 DevBuf::~DevBuf()
 {
-    if (p) cudaFreeAsync(p, stream);
+    if (!p) return;
+    if (pooled)
+        cudaFreeAsync(p, stream);
+    else
+        cudaFree(p);
 }
 
 namespace {

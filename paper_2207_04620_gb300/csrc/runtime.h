@@ -16,7 +16,9 @@ struct DevBuf {
     uint64_t *p = nullptr;
     size_t words = 0;
     cudaStream_t stream = nullptr;
+    bool pooled = true;  // false: plain cudaMalloc (outlives graph captures)
     DevBuf(size_t w, cudaStream_t s);
+    DevBuf(size_t w, bool persistent);
     ~DevBuf();
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
@@ -78,6 +80,17 @@ struct hx_keyset {
 struct hx_ct {
     hx_context *ctx = nullptr;
     hx::Cts c;  // B = 1
+};
+
+struct hx_matmul_exec {
+    hx_context *ctx = nullptr;
+    const hx_keyset *ks = nullptr;
+    const hx_matmul_plan *plan = nullptr;
+    size_t count = 0;
+    hx::Cts A, B, out;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap = nullptr;
+    int64_t launches = 0;
 };
 
 struct hx_matmul_plan {

@@ -80,6 +80,10 @@ _SIGS = {
     "hx_matmul_rotation_steps": (c_int, [c_vp, c_int, c_int, P_i32, c_int]),
     "hx_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, PP, c_vp]),
     "hx_matmul_batch": (c_int, [c_vp, c_vp, c_vp, PP, PP, c_int, c_size_t, PP, c_vp]),
+    "hx_matmul_exec_create": (c_int, [c_vp, c_vp, c_vp, c_size_t, c_double, PP]),
+    "hx_matmul_exec_run": (c_int, [c_vp, PP, PP, PP, c_vp]),
+    "hx_matmul_exec_launches": (c_i64, [c_vp]),
+    "hx_matmul_exec_destroy": (None, [c_vp]),
     "hx_sign_approx": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
     "hx_sign_approx_batch": (c_int, [c_vp, c_vp, PP, c_size_t, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
     "hx_counters": (c_int, [c_vp, P_u64, c_int]),
@@ -372,6 +376,29 @@ def hx_matmul_batch(ctx, ks, plan, As, Bs, h, stream=None) -> list:
     outs = (c_vp * n)()
     _chk(lib().hx_matmul_batch(ctx, ks, plan, a, b, h, n, outs, _stream(stream)))
     return [outs[i] for i in range(n)]
+
+
+def hx_matmul_exec_create(ctx, ks, plan, count, scale) -> int:
+    out = _out()
+    _chk(lib().hx_matmul_exec_create(ctx, ks, plan, count, float(scale), ctypes.byref(out)))
+    return out.value
+
+
+def hx_matmul_exec_run(ex, As, Bs, stream=None) -> list:
+    n = len(As)
+    a = (c_vp * n)(*As)
+    b = (c_vp * n)(*Bs)
+    outs = (c_vp * n)()
+    _chk(lib().hx_matmul_exec_run(ex, a, b, outs, _stream(stream)))
+    return [outs[i] for i in range(n)]
+
+
+def hx_matmul_exec_launches(ex) -> int:
+    return _chk(lib().hx_matmul_exec_launches(ex))
+
+
+def hx_matmul_exec_destroy(ex) -> None:
+    lib().hx_matmul_exec_destroy(ex)
 
 
 # ---- sign / ReLU -------------------------------------------------------------------

@@ -350,3 +350,27 @@ def test_sign_degrees_1_to_4_single_composition():
             assert pr.same(h, want)
     finally:
         pr.close()
+
+
+def test_matmul_graph_executor_equals_batched_call():
+    pr, beta, limbs = _matmul_case("alg3", 8, 0, 2)
+    try:
+        h = 8
+        A = [hx.hx_encrypt(pr.ctx, pr.ks, workloads.pack(workloads.matrices(i, beta, h), h, beta), 0, i)
+             for i in range(2)]
+        B = [hx.hx_encrypt(pr.ctx, pr.ks, workloads.pack(workloads.matrices(5 + i, beta, h), h, beta), 0, 5 + i)
+             for i in range(2)]
+        plan = hx.hx_matmul_plan_create(pr.ctx, h, limbs)
+        want = [hx.hx_ct_export(pr.ctx, o) for o in hx.hx_matmul_batch(pr.ctx, pr.ks, plan, A, B, h)]
+        scale = hx.hx_ct_info(A[0])[2]
+        ex = hx.hx_matmul_exec_create(pr.ctx, pr.ks, plan, 2, scale)
+        assert hx.hx_matmul_exec_launches(ex) > 100
+        for _ in range(2):  # replays reuse the graph's memory
+            got = hx.hx_matmul_exec_run(ex, A, B)
+            for g, w in zip(got, want):
+                assert np.array_equal(hx.hx_ct_export(pr.ctx, g), w)
+                hx.hx_ct_destroy(g)
+        hx.hx_matmul_exec_destroy(ex)
+        hx.hx_matmul_plan_destroy(plan)
+    finally:
+        pr.close()
