@@ -434,6 +434,137 @@ def run_sign(args):
     hx.hx_context_destroy(ctx)
 
 
+def run_serve(args):
+    """Serving stream (config-4 pattern): Poisson arrivals of mixed requests -- encrypted
+    matmuls (h in {16, 32, 64}, as the ring allows) and composite sign (g_4, one composition)
+    -- over CKKS rings N in {2^13, 2^14, 2^15} (and 2^16 with --full), chain 60 + 11x40 bit,
+    P = 3x60 bit, levels drawn per request; rotation keys resident; HBM-budget admission.
+    Capacity is measured closed-loop first; the open-loop run offers 0.8x capacity."""
+    import torch
+
+    from paper_2207_04620_gb300 import hx, workloads
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    rng = np.random.default_rng(2026)
+    log_ns = [13, 14, 15] + ([16] if args.full else [])
+    qb, pb = [60] + [40] * 11, [60] * 3
+    ctxs, keys = {}, {}
+    t_setup = time.perf_counter()
+    for ln in log_ns:
+        ctx = hx.hx_context_create(ln, qb, pb, 40)
+        hx.hx_autotune(ctx)
+        s = (1 << ln) // 2
+        hs = [h for h in (16, 32, 64, 128) if h * h <= s and (h <= 64 or args.full)]
+        steps = sorted({k for h in hs for k in hx.hx_matmul_rotation_steps(ctx, h, 8)})
+        ctxs[ln] = (ctx, hs)
+        keys[ln] = hx.hx_keygen(ctx, 2, 4000 + ln, steps)
+    n_req = args.requests
+    reqs = []
+    for i in range(n_req):
+        ln = int(rng.choice(log_ns))
+        ctx, hs = ctxs[ln]
+        s = (1 << ln) // 2
+        if rng.random() < 0.5:
+            h = int(rng.choice(hs))
+            limbs = int(rng.integers(4, 9))
+            beta = s // (h * h)
+            a = hx.hx_encrypt(ctx, keys[ln], workloads.pack(workloads.matrices(10 * i, beta, h), h, beta), limbs, i)
+            b = hx.hx_encrypt(ctx, keys[ln], workloads.pack(workloads.matrices(10 * i + 1, beta, h), h, beta), limbs,
+                              n_req + i)
+            reqs.append(("matmul", ln, (a, b, h), limbs))
+        else:
+            limbs = int(rng.integers(5, 9))
+            x = hx.hx_encrypt(ctx, keys[ln], workloads.sign_inputs(i, s), limbs, 2 * n_req + i)
+            reqs.append(("sign", ln, (x, 4, 1, 7 * i + 1), limbs))
+    # build every plan once (library masks) before timing
+    seen = set()
+    for kind, ln, a, limbs in reqs:
+        if kind == "matmul" and (ln, a[2], limbs) not in seen:
+            seen.add((ln, a[2], limbs))
+            hx.hx_ct_destroy(hx.hx_matmul(ctxs[ln][0], keys[ln], a[0], a[1], a[2]))
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    free, total = torch.cuda.mem_get_info()
+    budget = int(free * 0.85)
+    sv = hx.hx_server_create(budget, args.lanes, args.max_batch)
+    for ln in log_ns:
+        hx.hx_server_register_keys(sv, keys[ln])
+
+    def submit(r):
+        kind, ln, a, _ = r
+        ctx = ctxs[ln][0]
+        if kind == "matmul":
+            return hx.hx_server_submit_matmul(sv, ctx, keys[ln], a[0], a[1], a[2])
+        return hx.hx_server_submit_sign(sv, ctx, keys[ln], a[0], a[1], a[2], False, a[3])
+
+    def drain(pending_ids, lat):
+        for rid, res, st, l in hx.hx_server_poll(sv, wait=False):
+            if st != 0:
+                raise RuntimeError("request %d failed with status %d" % (rid, st))
+            lat[rid] = l
+            hx.hx_ct_destroy(res)
+            pending_ids.discard(rid)
+
+    # closed loop: the first 20% at once -> capacity
+    n_cap = max(20, n_req // 5)
+    lat_cap, pend = {}, set()
+    t0 = time.perf_counter()
+    for r in reqs[:n_cap]:
+        pend.add(submit(r))
+    while pend:
+        for rid, res, st, l in hx.hx_server_poll(sv, wait=True):
+            lat_cap[rid] = l
+            hx.hx_ct_destroy(res)
+            pend.discard(rid)
+    capacity = n_cap / (time.perf_counter() - t0)
+    # open loop: Poisson arrivals at rate 0.8 x capacity
+    rate = args.load * capacity
+    gaps = rng.exponential(1.0 / rate, n_req - n_cap)
+    lat, pend = {}, set()
+    sampler = ClockSampler()
+    t0 = time.perf_counter()
+    t_next = t0
+    for r, g in zip(reqs[n_cap:], gaps):
+        t_next += g
+        while True:
+            now = time.perf_counter()
+            if now >= t_next:
+                break
+            drain(pend, lat)
+            time.sleep(min(0.0005, t_next - now))
+        pend.add(submit(r))
+    while pend:
+        for rid, res, st, l in hx.hx_server_poll(sv, wait=True):
+            lat[rid] = l
+            hx.hx_ct_destroy(res)
+            pend.discard(rid)
+    elapsed = time.perf_counter() - t0
+    clocks = sampler.stop()
+    stats = hx.hx_server_stats(sv)
+    hx.hx_server_destroy(sv)
+    L = np.array(sorted(lat.values()))
+    line = {"metric": "serving p50/p99 ms (continuous batching, mixed encrypted matmul + sign)",
+            "value": round(float(np.percentile(L, 50)), 3), "p99_ms": round(float(np.percentile(L, 99)), 3),
+            "unit": "ms", "higher_is_better": False, "throughput_req_s": round(len(L) / elapsed, 2),
+            "offered_req_s": round(rate, 2), "capacity_req_s": round(capacity, 2), "requests": len(L),
+            "n_gpus": 1, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "Poisson arrivals at %.1fx closed-loop capacity; 50%% matmul h in {16,32,64} "
+                                   "(feasible per ring), 50%% sign g_4 (k=1); N in %s; Q=60+11x40, P=3x60 bit; "
+                                   "matmul limbs U{4..8}, sign limbs U{5..8}" % (args.load, [2 ** l for l in log_ns]),
+                       "lanes": args.lanes, "max_batch": args.max_batch, "hbm_budget_bytes": budget,
+                       "setup_s": round(setup_s, 1)},
+            "server": stats, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    for kind, ln, a, _ in reqs:
+        for h in (a[:2] if kind == "matmul" else a[:1]):
+            hx.hx_ct_destroy(h)
+    for ln in log_ns:
+        hx.hx_keyset_destroy(keys[ln])
+        hx.hx_context_destroy(ctxs[ln][0])
+
+
 def run_micro(args):
     """NTT alone: forward then inverse transform of `rows` limbs of one ring
     degree, in place, timed with CUDA events.  Algorithmic traffic: one read
@@ -486,7 +617,12 @@ def run_micro(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--micro", choices=["ntt"], default=None)
-    ap.add_argument("--workload", choices=["matmul", "sign"], default="matmul")
+    ap.add_argument("--workload", choices=["matmul", "sign", "serve"], default="matmul")
+    ap.add_argument("--requests", type=int, default=1000)
+    ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--lanes", type=int, default=4)
+    ap.add_argument("--max-batch", type=int, default=16)
+    ap.add_argument("--full", action="store_true", help="serving: add N=2^16 and h=128")
     ap.add_argument("--relu", action="store_true")
     ap.add_argument("--log-n", type=int, default=14)
     ap.add_argument("--rows", type=int, default=1600)
@@ -502,6 +638,8 @@ def main():
         return run_micro(args)
     if args.workload == "sign":
         return run_sign(args)
+    if args.workload == "serve":
+        return run_serve(args)
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

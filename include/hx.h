@@ -224,11 +224,44 @@ void hx_matmul_exec_destroy(hx_matmul_exec *ex);
  * [1, 4].  When the next composition no longer fits in the remaining levels,
  * the ciphertext is refreshed by a host-simulated DBootstrap (collective
  * decryption and re-encryption at the top level, randomness from
- * refresh_seed) if allow_refresh != 0, else HX_ELEVEL. */
+ * refresh_seed) if allow_refresh != 0, else HX_ELEVEL.  In the batch call,
+ * entry i uses refresh_seed + i, so every entry's result equals the single
+ * call's with that seed. */
 hx_status hx_sign_approx(hx_context *ctx, const hx_keyset *ks, const hx_ct *x, int d, int k, int relu,
                          int allow_refresh, uint64_t refresh_seed, hx_ct **out, void *stream);
 hx_status hx_sign_approx_batch(hx_context *ctx, const hx_keyset *ks, const hx_ct *const *x, size_t count, int d,
                                int k, int relu, int allow_refresh, uint64_t refresh_seed, hx_ct **out, void *stream);
+
+/* ---- serving (continuous batching) ----------------------------------------------- */
+/* A request server on the current device.  Requests queue on the host; a
+ * dispatcher forms a batch from the oldest pending request and the other
+ * pending requests of the same signature (context, keys, kind, level and h, or
+ * d/k/relu) whenever one of n_lanes CUDA streams is idle and the batch's
+ * estimated device memory fits in what hbm_budget_bytes leaves after the
+ * registered keys; the lanes run concurrently.  Each result equals the same
+ * request computed alone (hx_matmul, or hx_sign_approx with its
+ * refresh_seed).  Submitted ciphertexts stay referenced until their request
+ * completes, so the caller may destroy its handles at once. */
+typedef struct hx_server hx_server;
+hx_status hx_server_create(size_t hbm_budget_bytes, int n_lanes, int max_batch, hx_server **out);
+/* counts a keyset's device bytes against the budget (HX_ENOMEM if it does not fit) */
+hx_status hx_server_register_keys(hx_server *sv, const hx_keyset *ks);
+/* HX_ENOMEM if the request alone exceeds the budget */
+hx_status hx_server_submit_matmul(hx_server *sv, hx_context *ctx, const hx_keyset *ks, const hx_ct *A,
+                                  const hx_ct *B, int h, uint64_t *id);
+hx_status hx_server_submit_sign(hx_server *sv, hx_context *ctx, const hx_keyset *ks, const hx_ct *x, int d, int k,
+                                int relu, uint64_t refresh_seed, uint64_t *id);
+/* Moves up to cap completed requests out: ids, result handles (NULL on error),
+ * statuses and latencies (submission to completion of its batch on the GPU,
+ * ms).  wait != 0 blocks until at least one completes or nothing is pending.
+ * Returns the number moved. */
+int hx_server_poll(hx_server *sv, int wait, uint64_t *ids, hx_ct **results, int32_t *status, double *latency_ms,
+                   int cap);
+/* completed, batches, largest batch, most lanes busy at once, peak admitted
+ * bytes, key bytes, remaining budget, pending requests; returns the count */
+int hx_server_stats(hx_server *sv, uint64_t *out, int cap);
+/* waits for every submitted request, then stops the threads */
+void hx_server_destroy(hx_server *sv);
 
 /* ---- counters -------------------------------------------------------------- */
 /* Operation counters since the last reset, in this order: Add, Mul_pt,

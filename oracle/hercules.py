@@ -512,7 +512,7 @@ def refresh(ev: C.Evaluator, ct: C.Ciphertext, seed: int, counter: int, index: i
 
 
 def sign_approx(ev: C.Evaluator, x: C.Ciphertext, d: int, k: int, relu: bool = False,
-                refresh_seed: int | None = None, index: int = 0) -> C.Ciphertext:
+                refresh_seed: int | None = None) -> C.Ciphertext:
     """g_d^(k)(x) (Sec. 4.2) or ReLU(x) = x (1 + g_d^(k)(x)) / 2 (Sec. 4.4).
     Before a composition whose depth (plus the final ReLU product) no longer
     fits, the ciphertext is refreshed if a refresh seed is given."""
@@ -524,7 +524,7 @@ def sign_approx(ev: C.Evaluator, x: C.Ciphertext, d: int, k: int, relu: bool = F
         if m.limbs - 1 < need:
             if refresh_seed is None:
                 raise ValueError("levels exhausted")
-            m = refresh(ev, m, refresh_seed, refreshes, index)
+            m = refresh(ev, m, refresh_seed, refreshes)
             refreshes += 1
         m = eval_g(ev, m, d)
     if not relu:

@@ -426,23 +426,13 @@ int hx_matmul_rotation_steps(const hx_context *ctx, int h, int limbs, int32_t *o
     return (int)st.size();
 }
 
-static const hx_matmul_plan *cached_plan(hx_context *ctx, int h, int limbs)
-{
-    auto key = std::make_pair(h, limbs);
-    auto it = ctx->plans.find(key);
-    if (it != ctx->plans.end()) return it->second;
-    hx_matmul_plan *p = make_plan(*ctx, h, limbs, nullptr);
-    ctx->plans[key] = p;
-    return p;
-}
-
 hx_status hx_matmul(hx_context *ctx, const hx_keyset *ks, const hx_ct *A, const hx_ct *B, int h, hx_ct **out,
                     void *stream)
 {
     HX_TRY
     need(ctx && ks && A && B && out, "null argument");
     *out = nullptr;
-    const hx_matmul_plan *p = cached_plan(ctx, h, A->c.limbs);
+    const hx_matmul_plan *p = cached_plan(*ctx, h, A->c.limbs);
     *out = wrap(ctx, matmul_batch(*ctx, *ks, *p, A->c, B->c, S(stream)));
     return HX_OK;
     HX_END
@@ -457,7 +447,7 @@ hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_
     need(count < 4096, "batch too large");
     Cts a = gather(*ctx, A, count, S(stream));
     Cts b = gather(*ctx, B, count, S(stream));
-    const hx_matmul_plan *p = plan ? plan : cached_plan(ctx, h, a.limbs);
+    const hx_matmul_plan *p = plan ? plan : cached_plan(*ctx, h, a.limbs);
     need(p->h == h, "plan built for another h");
     Cts r = matmul_batch(*ctx, *ks, *p, a, b, S(stream));
     scatter(*ctx, r, out, S(stream));
@@ -496,7 +486,7 @@ hx_status hx_matmul_exec_create(hx_context *ctx, const hx_keyset *ks, const hx_m
     HX_CUDA(cudaStreamCreateWithFlags(&ex->cap, cudaStreamNonBlocking));
     const uint64_t l0 = ctx->counters[C_LAUNCH];
     uint64_t saved[C_NUM];
-    memcpy(saved, ctx->counters, sizeof(saved));
+    for (int i = 0; i < C_NUM; i++) saved[i] = ctx->counters[i];
     const bool prof = ctx->profiling;
     ctx->profiling = false;
     cudaGraph_t graph = nullptr;
@@ -516,7 +506,7 @@ hx_status hx_matmul_exec_create(hx_context *ctx, const hx_keyset *ks, const hx_m
     HX_CUDA(cudaStreamEndCapture(ex->cap, &graph));
     ctx->profiling = prof;
     ex->launches = (int64_t)(ctx->counters[C_LAUNCH] - l0);
-    memcpy(ctx->counters, saved, sizeof(saved));  // a capture executes nothing
+    for (int i = 0; i < C_NUM; i++) ctx->counters[i] = saved[i];  // a capture executes nothing
     cudaError_t e = cudaGraphInstantiate(&ex->exec, graph, 0);
     cudaGraphDestroy(graph);
     HX_CUDA(e);
@@ -574,7 +564,7 @@ hx_status hx_sign_approx(hx_context *ctx, const hx_keyset *ks, const hx_ct *x, i
     HX_TRY
     need(ctx && ks && x && out, "null argument");
     *out = nullptr;
-    *out = wrap(ctx, sign_batch(*ctx, *ks, x->c, d, k, relu != 0, allow_refresh != 0, refresh_seed, S(stream)));
+    *out = wrap(ctx, sign_batch(*ctx, *ks, x->c, d, k, relu != 0, allow_refresh != 0, {refresh_seed}, S(stream)));
     return HX_OK;
     HX_END
 }
@@ -586,7 +576,9 @@ hx_status hx_sign_approx_batch(hx_context *ctx, const hx_keyset *ks, const hx_ct
     need(ctx && ks && x && out && count >= 1 && count < 4096, "bad argument");
     for (size_t i = 0; i < count; i++) out[i] = nullptr;
     Cts a = gather(*ctx, x, count, S(stream));
-    Cts r = sign_batch(*ctx, *ks, a, d, k, relu != 0, allow_refresh != 0, refresh_seed, S(stream));
+    std::vector<uint64_t> seeds(count);
+    for (size_t i = 0; i < count; i++) seeds[i] = refresh_seed + i;
+    Cts r = sign_batch(*ctx, *ks, a, d, k, relu != 0, allow_refresh != 0, seeds, S(stream));
     scatter(*ctx, r, out, S(stream));
     return HX_OK;
     HX_END
@@ -601,7 +593,8 @@ int hx_counters(const hx_context *ctx, uint64_t *out, int cap)
 
 void hx_counters_reset(hx_context *ctx)
 {
-    if (ctx) memset(ctx->counters, 0, sizeof(ctx->counters));
+    if (ctx)
+        for (int i = 0; i < C_NUM; i++) ctx->counters[i] = 0;
 }
 
 hx_status hx_autotune(hx_context *ctx, int32_t *choice, void *stream)

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -109,7 +110,7 @@ struct LaunchCtx {
     int log_n, N;
     const DeviceTables *t;
     cudaStream_t stream;
-    uint64_t *launches;
+    std::atomic<uint64_t> *launches;
     Profiler *prof = nullptr;
 };
 

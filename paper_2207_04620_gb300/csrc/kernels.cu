@@ -214,11 +214,10 @@ void ntt_cols_w(const LaunchCtx &c, const NttRows &rows)
     HX_CHECK(N2 % COLS == 0, HX_EINVAL, "NTT tile wider than the ring");
     dim3 grid(N2 / COLS, rows.n_rows, rows.n_groups);
     const size_t smem = (size_t)E * 8 + (size_t)M * 16;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_ntt_cols<LOGM, COLS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    static const bool attr =  // thread-safe one-time setup
+        cudaFuncSetAttribute(k_ntt_cols<LOGM, COLS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+        cudaSuccess;
+    (void)attr;
     k_ntt_cols<LOGM, COLS, INV><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
                                                             c.log_n);
 }
@@ -232,11 +231,10 @@ void ntt_rows_w(const LaunchCtx &c, const NttRows &rows)
     HX_CHECK(N1 % ROWS == 0, HX_EINVAL, "NTT tile wider than the ring");
     dim3 grid(N1 / ROWS, rows.n_rows, rows.n_groups);
     const size_t smem = (size_t)ROWS * (M + M / 16) * 8;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_ntt_rows<LOGM, ROWS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    static const bool attr =  // thread-safe one-time setup
+        cudaFuncSetAttribute(k_ntt_rows<LOGM, ROWS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+        cudaSuccess;
+    (void)attr;
     k_ntt_rows<LOGM, ROWS, INV><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
                                                             c.log_n);
 }

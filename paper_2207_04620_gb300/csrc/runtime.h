@@ -2,6 +2,7 @@
 #pragma once
 #include <map>
 #include <memory>
+#include <mutex>
 #include <vector>
 
 #include "host_math.h"
@@ -57,7 +58,8 @@ struct hx_context {
     int *d_prime_ids = nullptr;                // 0..n_all-1
     std::unique_ptr<hx::Encoder> enc;
     std::unique_ptr<hx::GaussianCdt> cdt;
-    uint64_t counters[hx::C_NUM] = {0};
+    std::atomic<uint64_t> counters[hx::C_NUM] = {};
+    std::mutex plan_mu;  // guards `plans`
     std::map<std::pair<int, int>, hx_matmul_plan *> plans;
     int device = 0;
     hx::Profiler prof;
@@ -177,11 +179,14 @@ std::vector<int64_t> decrypt_coeffs(hx_context &ctx, const hx_keyset &ks, const 
 
 // ---- schedules (schedules.cu) -------------------------------------------------
 hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s);
+// the context's plan for (h, limbs) with library masks, built on first use (thread-safe)
+const hx_matmul_plan *cached_plan(hx_context &ctx, int h, int limbs);
 std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs);
 Cts matmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &A, const Cts &B,
                  cudaStream_t s);
+// refresh randomness of entry b: SplitMix64 streams keyed by refresh_seeds[b] (tag 1 + refresh index)
 Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k, bool relu, bool allow_refresh,
-               uint64_t refresh_seed, cudaStream_t s);
+               const std::vector<uint64_t> &refresh_seeds, cudaStream_t s);
 
 // ---- context (context.cu) -------------------------------------------------------
 void build_context(hx_context &ctx, const hx_params &p);

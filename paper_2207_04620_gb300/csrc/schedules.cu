@@ -139,6 +139,17 @@ hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
     return p.release();
 }
 
+const hx_matmul_plan *cached_plan(hx_context &ctx, int h, int limbs)
+{
+    std::lock_guard<std::mutex> lk(ctx.plan_mu);
+    auto key = std::make_pair(h, limbs);
+    auto it = ctx.plans.find(key);
+    if (it != ctx.plans.end()) return it->second;
+    hx_matmul_plan *p = make_plan(ctx, h, limbs, nullptr);
+    ctx.plans[key] = p;
+    return p;
+}
+
 namespace {
 
 const uint64_t *mask_pt(const hx_matmul_plan &p, int kind, int idx, double *scale)
@@ -370,7 +381,8 @@ int g_depth(int d)
 
 // host simulation of DBootstrap: collective decryption, integer rescaling of
 // the plaintext coefficients to the default scale, re-encryption at the top
-Cts refresh(hx_context &ctx, const hx_keyset &ks, const Cts &ct, uint64_t seed, int counter, cudaStream_t s)
+Cts refresh(hx_context &ctx, const hx_keyset &ks, const Cts &ct, const std::vector<uint64_t> &seeds, int counter,
+            cudaStream_t s)
 {
     std::vector<int64_t> poly = decrypt_coeffs(ctx, ks, ct, s);
     const double ratio = ctx.scale / ct.scale;
@@ -380,7 +392,7 @@ Cts refresh(hx_context &ctx, const hx_keyset &ks, const Cts &ct, uint64_t seed, 
     out.scale = ctx.scale;
     for (int b = 0; b < ct.B; b++) {
         for (int i = 0; i < ctx.N; i++) m[i] = (int64_t)round_half_away((double)poly[(size_t)b * ctx.N + i] * ratio);
-        Cts one = encrypt_coeffs(ctx, ks, m.data(), ctx.scale, ctx.n_q, seed, 1 + counter, b, s);
+        Cts one = encrypt_coeffs(ctx, ks, m.data(), ctx.scale, ctx.n_q, seeds[b], 1 + counter, 0, s);
         HX_CUDA(cudaMemcpyAsync(out.d + (size_t)b * out.bstride(ctx.N), one.d, sizeof(uint64_t) * one.bstride(ctx.N),
                                 cudaMemcpyDeviceToDevice, s));
     }
@@ -391,8 +403,9 @@ Cts refresh(hx_context &ctx, const hx_keyset &ks, const Cts &ct, uint64_t seed, 
 } // namespace
 
 Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k, bool relu, bool allow_refresh,
-               uint64_t refresh_seed, cudaStream_t s)
+               const std::vector<uint64_t> &refresh_seeds, cudaStream_t s)
 {
+    HX_CHECK((int)refresh_seeds.size() == x.B, HX_EINVAL, "one refresh seed per batch entry");
     HX_CHECK(d >= 1 && d <= 4 && k >= 1 && k <= 64, HX_EINVAL, "need 1 <= d <= 4 and 1 <= k <= 64");
     HX_CHECK(x.comps == 2, HX_EINVAL, "sign needs ciphertexts");
     Eval ev(ctx, s);
@@ -404,7 +417,7 @@ Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k,
         if (m.limbs - 1 < need) {
             HX_CHECK(allow_refresh, HX_ELEVEL, "levels exhausted");
             HX_CHECK(ctx.n_q - 1 >= need, HX_ELEVEL, "chain too short for one composition");
-            m = refresh(ctx, ks, m, refresh_seed, refreshes++, s);
+            m = refresh(ctx, ks, m, refresh_seeds, refreshes++, s);
         }
         m = eval_g(ev, ks, m, d);
     }

@@ -86,6 +86,13 @@ _SIGS = {
     "hx_matmul_exec_destroy": (None, [c_vp]),
     "hx_sign_approx": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
     "hx_sign_approx_batch": (c_int, [c_vp, c_vp, PP, c_size_t, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
+    "hx_server_create": (c_int, [c_size_t, c_int, c_int, PP]),
+    "hx_server_register_keys": (c_int, [c_vp, c_vp]),
+    "hx_server_submit_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_int, P_u64]),
+    "hx_server_submit_sign": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, c_int, c_int, c_u64, P_u64]),
+    "hx_server_poll": (c_int, [c_vp, c_int, P_u64, PP, P_i32, P_dbl, c_int]),
+    "hx_server_stats": (c_int, [c_vp, P_u64, c_int]),
+    "hx_server_destroy": (None, [c_vp]),
     "hx_counters": (c_int, [c_vp, P_u64, c_int]),
     "hx_counters_reset": (None, [c_vp]),
     "hx_autotune": (c_int, [c_vp, P_i32, c_vp]),
@@ -414,6 +421,55 @@ def hx_sign_approx_batch(ctx, ks, xs, d, k, relu=False, allow_refresh=True, refr
     _chk(lib().hx_sign_approx_batch(ctx, ks, a, n, d, k, int(relu), int(allow_refresh), refresh_seed, outs,
                                     _stream(stream)))
     return [outs[i] for i in range(n)]
+
+
+# ---- serving ------------------------------------------------------------------------------
+
+SERVER_STATS = ["completed", "batches", "largest_batch", "max_busy_lanes", "peak_admitted_bytes", "key_bytes",
+                "budget_left", "pending"]
+
+
+def hx_server_create(hbm_budget_bytes: int, n_lanes: int, max_batch: int) -> int:
+    out = _out()
+    _chk(lib().hx_server_create(int(hbm_budget_bytes), n_lanes, max_batch, ctypes.byref(out)))
+    return out.value
+
+
+def hx_server_register_keys(sv: int, ks: int) -> None:
+    _chk(lib().hx_server_register_keys(sv, ks))
+
+
+def hx_server_submit_matmul(sv, ctx, ks, A, B, h) -> int:
+    rid = c_u64()
+    _chk(lib().hx_server_submit_matmul(sv, ctx, ks, A, B, h, ctypes.byref(rid)))
+    return rid.value
+
+
+def hx_server_submit_sign(sv, ctx, ks, x, d, k, relu=False, refresh_seed=0) -> int:
+    rid = c_u64()
+    _chk(lib().hx_server_submit_sign(sv, ctx, ks, x, d, k, int(relu), refresh_seed, ctypes.byref(rid)))
+    return rid.value
+
+
+def hx_server_poll(sv: int, wait: bool = True, cap: int = 256) -> list:
+    """[(id, result handle or None, status, latency ms)]"""
+    ids = np.zeros(cap, dtype=np.uint64)
+    res = (c_vp * cap)()
+    st = np.zeros(cap, dtype=np.int32)
+    lat = np.zeros(cap, dtype=np.float64)
+    n = _chk(lib().hx_server_poll(sv, int(bool(wait)), _u64p(ids), res, st.ctypes.data_as(P_i32),
+                                  lat.ctypes.data_as(P_dbl), cap))
+    return [(int(ids[i]), res[i], int(st[i]), float(lat[i])) for i in range(n)]
+
+
+def hx_server_stats(sv: int) -> dict:
+    buf = np.zeros(8, dtype=np.uint64)
+    n = _chk(lib().hx_server_stats(sv, _u64p(buf), 8))
+    return {SERVER_STATS[i]: int(buf[i]) for i in range(n)}
+
+
+def hx_server_destroy(sv: int) -> None:
+    lib().hx_server_destroy(sv)
 
 
 # ---- counters ------------------------------------------------------------------------

@@ -324,7 +324,7 @@ def test_sign_bit_exact_with_refresh(relu):
                                        allow_refresh=True, refresh_seed=777)
         for i in range(2):
             ev = C.Evaluator(octx, pr.oks)
-            want = Hc.sign_approx(ev, cts[i], 4, 8, relu=relu, refresh_seed=777, index=i)
+            want = Hc.sign_approx(ev, cts[i], 4, 8, relu=relu, refresh_seed=777 + i)
             assert ev.counts["Refresh"] == 2
             assert pr.same(outs[i], want)
             got = hx.hx_decrypt(pr.ctx, pr.ks, outs[i])

@@ -1,0 +1,114 @@
+"""Continuous-batching server: every result equals the same request computed
+alone, requests are batched and overlap across lanes, and admission respects
+the HBM budget."""
+import numpy as np
+import pytest
+
+from oracle import hercules as Hc
+from paper_2207_04620_gb300 import hx, workloads
+
+from hxpair import PARAMS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    from paper_2207_04620_gb300 import build
+
+    build.build()
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    p = PARAMS["alg3"]
+    ctx = hx.hx_context_create(p["log_n"], p["q_bits"], p["p_bits"], p["log2_scale"])
+    s = (1 << p["log_n"]) // 2
+    steps = sorted(set(Hc.matmul_rotation_steps(8, s // 64, 5)) | set(Hc.matmul_rotation_steps(16, s // 256, 5)))
+    ks = hx.hx_keygen(ctx, 2, 31, steps)
+    yield ctx, ks, s
+    hx.hx_keyset_destroy(ks)
+    hx.hx_context_destroy(ctx)
+
+
+def _requests(ctx, ks, s):
+    """(kind, args) of a mixed stream: matmuls of h = 8 and 16 at 5 and 4 limbs, signs of d = 2 and 4."""
+    reqs = []
+    for i in range(10):
+        if i % 3 == 2:
+            d = 4 if i % 2 else 2
+            x = hx.hx_encrypt(ctx, ks, workloads.sign_inputs(i, s), 5, 100 + i)
+            reqs.append(("sign", (x, d, 1, 1000 + i)))
+        else:
+            h = 8 if i % 2 else 16
+            beta = s // (h * h)
+            limbs = 5 if i % 4 < 2 else 4
+            a = hx.hx_encrypt(ctx, ks, workloads.pack(workloads.matrices(i, beta, h), h, beta), limbs, 200 + i)
+            b = hx.hx_encrypt(ctx, ks, workloads.pack(workloads.matrices(50 + i, beta, h), h, beta), limbs, 300 + i)
+            reqs.append(("matmul", (a, b, h)))
+    return reqs
+
+
+def _submit(sv, ctx, ks, kind, args):
+    if kind == "matmul":
+        return hx.hx_server_submit_matmul(sv, ctx, ks, *args)
+    x, d, k, seed = args
+    return hx.hx_server_submit_sign(sv, ctx, ks, x, d, k, relu=False, refresh_seed=seed)
+
+
+def _alone(ctx, ks, kind, args):
+    if kind == "matmul":
+        return hx.hx_matmul(ctx, ks, *args)
+    x, d, k, seed = args
+    return hx.hx_sign_approx(ctx, ks, x, d, k, relu=False, allow_refresh=True, refresh_seed=seed)
+
+
+def _collect(sv, n):
+    got = {}
+    while len(got) < n:
+        for rid, res, st, lat in hx.hx_server_poll(sv, wait=True):
+            got[rid] = (res, st, lat)
+    return got
+
+
+def test_results_in_the_mix_equal_results_alone(setup):
+    ctx, ks, s = setup
+    reqs = _requests(ctx, ks, s)
+    sv = hx.hx_server_create(64 << 30, 3, 4)
+    hx.hx_server_register_keys(sv, ks)
+    ids = [_submit(sv, ctx, ks, kind, args) for kind, args in reqs]
+    got = _collect(sv, len(ids))
+    stats = hx.hx_server_stats(sv)
+    hx.hx_server_destroy(sv)
+    assert stats["completed"] == len(reqs) and stats["batches"] < len(reqs)  # some requests shared a batch
+    for rid, (kind, args) in zip(ids, reqs):
+        res, st, lat = got[rid]
+        assert st == 0 and lat > 0
+        alone = _alone(ctx, ks, kind, args)
+        assert np.array_equal(hx.hx_ct_export(ctx, res), hx.hx_ct_export(ctx, alone)), kind
+        hx.hx_ct_destroy(res)
+        hx.hx_ct_destroy(alone)
+
+
+def test_admission_by_budget_and_rejection(setup):
+    ctx, ks, s = setup
+    h, beta = 8, s // 64
+    a = hx.hx_encrypt(ctx, ks, workloads.pack(workloads.matrices(1, beta, h), h, beta), 5, 1)
+    b = hx.hx_encrypt(ctx, ks, workloads.pack(workloads.matrices(2, beta, h), h, beta), 5, 2)
+    one = 48 * 2 * 5 * (2 * s) * 8          # the server's estimate for one such product
+    sv = hx.hx_server_create(one + one // 2, 3, 8)   # room for exactly one at a time
+    ids = [hx.hx_server_submit_matmul(sv, ctx, ks, a, b, h) for _ in range(4)]
+    hx.hx_ct_destroy(a)                      # the server keeps its own reference
+    hx.hx_ct_destroy(b)
+    got = _collect(sv, 4)
+    stats = hx.hx_server_stats(sv)
+    assert all(got[i][1] == 0 for i in ids)
+    assert stats["max_busy_lanes"] == 1 and stats["peak_admitted_bytes"] <= one + one // 2
+    outs = [hx.hx_ct_export(ctx, got[i][0]) for i in ids]
+    assert all(np.array_equal(o, outs[0]) for o in outs)
+    hx.hx_server_destroy(sv)
+    tiny = hx.hx_server_create(one // 2, 1, 1)
+    c = hx.hx_encrypt(ctx, ks, np.ones(4), 5, 3)
+    with pytest.raises(hx.HxError) as e:
+        hx.hx_server_submit_matmul(tiny, ctx, ks, c, c, h)
+    assert e.value.code == -2
+    hx.hx_server_destroy(tiny)
