@@ -78,6 +78,7 @@ void build_context(hx_context &c, const hx_params &p)
     for (int b : bits) HX_CHECK(b >= 20 && b <= 61, HX_EINVAL, "prime sizes must be in [20, 61] bits");
     HX_CHECK(p.sigma > 0 && p.sigma < 100 && p.log2_scale > 0 && p.log2_scale < 62, HX_EINVAL, "bad sigma or scale");
     HX_CUDA(cudaGetDevice(&c.device));
+    HX_CUDA(cudaDeviceGetAttribute(&c.t.n_sm, cudaDevAttrMultiProcessorCount, c.device));
     c.log_n = p.log_n;
     c.N = 1 << p.log_n;
     c.n_q = p.n_q;

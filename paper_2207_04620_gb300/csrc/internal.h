@@ -87,6 +87,7 @@ struct DeviceTables {
     ModDownTable *moddown = nullptr;// [n_q+1] by limbs
     RescaleTable *rescale = nullptr;// [n_q+1] by limbs
     int ntt_var[4] = {1, 1, 1, 1};  // tile width per phase: fwd cols, fwd rows, inv cols, inv rows
+    int n_sm = 1;                   // multiprocessors of the device
 };
 
 // Per-kernel-class timing with CUDA events recorded on the launching stream

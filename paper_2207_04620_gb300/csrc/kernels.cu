@@ -6,6 +6,7 @@
 // stages: N1 rows of stride N2) and a row phase (the remaining stages on N2
 // contiguous words), each staged through shared memory.  Every global word is
 // read and written once per phase with 128-byte coalesced row segments.
+#include <algorithm>
 #include <cstdio>
 
 #include "internal.h"
@@ -109,95 +110,167 @@ template <int L> struct Split {
     static constexpr int R2 = L - R1;       // second pass
 };
 
+// Asynchronous global->shared copies (cp.async): the next tile streams in while
+// the current one is transformed.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// tile t of a phase -> (group, row, position along the row)
+struct TileId {
+    int g, row, bx;
+};
+__device__ __forceinline__ TileId tile_of(int t, int nb, int n_rows)
+{
+    TileId r;
+    r.bx = t % nb;
+    const int rest = t / nb;
+    r.row = rest % n_rows;
+    r.g = rest / n_rows;
+    return r;
+}
+
 // column phase: the first LOGM stages on M rows of stride N2 (COLS adjacent columns
-// per block); its twiddles (indices below M) are staged in shared memory
+// per tile); each block loops over tiles with the next tile (and its twiddles,
+// indices below M) prefetched into the other half of shared memory
 template <int LOGM, int COLS, bool INV>
 __global__ void __launch_bounds__((1 << (LOGM - Split<LOGM>::R1)) * COLS)
 k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
-           const ulonglong2 *__restrict__ tw_all, int log_n)
+           const ulonglong2 *__restrict__ tw_all, int log_n, int n_tiles)
 {
     constexpr int M = 1 << LOGM, E = M * COLS, R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
     constexpr int T = (M >> R1) * COLS;
     extern __shared__ uint64_t sh[];
-    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(sh + E);
-    const int N = 1 << log_n, N2 = N >> LOGM;
-    const int row = blockIdx.y, g = blockIdx.z;
-    const int pr = R.prime[row];
-    const size_t doff = (size_t)g * R.dst_gs + (size_t)R.dst_off[row] * N;
-    const size_t soff = (size_t)g * R.src_gs + (size_t)R.src_off[row] * N;
-    const uint64_t *src = INV ? R.dst + doff : R.src + soff;  // first phase of the forward transform
-    uint64_t *dst = R.dst + doff;
-    const PrimeConst P = primes[pr];
-    const ulonglong2 *tw = tw_all + (size_t)pr * N;
-    const int c0 = blockIdx.x * COLS;
-    for (int i = threadIdx.x; i < M; i += T) stw[i] = tw[i];
-    for (int i = threadIdx.x; i < E; i += T) sh[i] = src[(size_t)(i / COLS) * N2 + c0 + (i % COLS)];
-    __syncthreads();
-    if (!INV) {
-        ntt_pass<LOGM, R1, 0, false, true, false>(sh, COLS, 1, COLS, stw, 0, 0, 0, P.q, T);
+    uint64_t *buf[2] = {sh, sh + E};
+    ulonglong2 *stw[2] = {reinterpret_cast<ulonglong2 *>(sh + 2 * E), reinterpret_cast<ulonglong2 *>(sh + 2 * E) + M};
+    const int N = 1 << log_n, N2 = N >> LOGM, nb = N2 / COLS;
+    auto prefetch = [&](int t, int slot) {
+        const TileId id = tile_of(t, nb, R.n_rows);
+        const int pr = R.prime[id.row];
+        const uint64_t *src = INV ? R.dst + (size_t)id.g * R.dst_gs + (size_t)R.dst_off[id.row] * N
+                                  : R.src + (size_t)id.g * R.src_gs + (size_t)R.src_off[id.row] * N;
+        const int c0 = id.bx * COLS;
+        for (int i = threadIdx.x; i < E / 2; i += T) {  // 16-byte pieces of COLS-word row segments
+            const int r = (2 * i) / COLS, c = (2 * i) % COLS;
+            cp_async16(buf[slot] + 2 * i, src + (size_t)r * N2 + c0 + c);
+        }
+        const ulonglong2 *tw = tw_all + (size_t)pr * N;
+        for (int i = threadIdx.x; i < M; i += T) cp_async16(stw[slot] + i, tw + i);
+        cp_async_commit();
+    };
+    int t = blockIdx.x, slot = 0;
+    if (t < n_tiles) prefetch(t, 0);
+    for (; t < n_tiles; t += gridDim.x, slot ^= 1) {
+        const int tn = t + gridDim.x;
+        if (tn < n_tiles) {
+            prefetch(tn, slot ^ 1);
+            cp_async_wait_all_but_one();
+        } else {
+            cp_async_wait_all();
+        }
         __syncthreads();
-        ntt_pass<LOGM, R2, R1, false, true, false>(sh, COLS, 1, COLS, stw, 0, 0, 0, P.q, T);
-        __syncthreads();
-        for (int i = threadIdx.x; i < E; i += T) dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = sh[i];
-    } else {
-        ntt_pass<LOGM, R2, R1, true, true, false>(sh, COLS, 1, COLS, stw, 0, 0, 0, P.q, T);
-        __syncthreads();
-        ntt_pass<LOGM, R1, 0, true, true, false>(sh, COLS, 1, COLS, stw, 0, 0, 0, P.q, T);
-        __syncthreads();
-        for (int i = threadIdx.x; i < E; i += T)
-            dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = shoup(sh[i], P.n_inv, P.n_inv_sh, P.q);
+        const TileId id = tile_of(t, nb, R.n_rows);
+        const PrimeConst P = primes[R.prime[id.row]];
+        uint64_t *dst = R.dst + (size_t)id.g * R.dst_gs + (size_t)R.dst_off[id.row] * N;
+        const int c0 = id.bx * COLS;
+        uint64_t *b = buf[slot];
+        if (!INV) {
+            ntt_pass<LOGM, R1, 0, false, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
+            __syncthreads();
+            ntt_pass<LOGM, R2, R1, false, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
+            __syncthreads();
+            for (int i = threadIdx.x; i < E; i += T) dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = b[i];
+        } else {
+            ntt_pass<LOGM, R2, R1, true, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
+            __syncthreads();
+            ntt_pass<LOGM, R1, 0, true, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
+            __syncthreads();
+            for (int i = threadIdx.x; i < E; i += T)
+                dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = shoup(b[i], P.n_inv, P.n_inv_sh, P.q);
+        }
+        __syncthreads();  // this half is refilled by the prefetch two tiles later
     }
 }
 
-// row phase: the remaining LOGM stages on ROWS contiguous blocks of M words
+// row phase: the remaining LOGM stages on ROWS contiguous blocks of M words per tile
+// (padded layout, one spare word per 16), next tile prefetched in 8-byte pieces
 template <int LOGM, int ROWS, bool INV>
 __global__ void __launch_bounds__((1 << (LOGM - Split<LOGM>::R1)) * ROWS)
 k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
-           const ulonglong2 *__restrict__ tw_all, int log_n)
+           const ulonglong2 *__restrict__ tw_all, int log_n, int n_tiles)
 {
     constexpr int M = 1 << LOGM, E = M * ROWS, R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
     constexpr int T = (M >> R1) * ROWS;
     constexpr int SK = M + M / 16;  // padded block stride
     extern __shared__ uint64_t sh[];
+    uint64_t *buf[2] = {sh, sh + ROWS * SK};
     const int N = 1 << log_n;
     const int g0 = log_n - LOGM;
-    const int row = blockIdx.y, g = blockIdx.z;
-    const int pr = R.prime[row];
-    const size_t doff = (size_t)g * R.dst_gs + (size_t)R.dst_off[row] * N;
-    const size_t soff = (size_t)g * R.src_gs + (size_t)R.src_off[row] * N;
-    const uint64_t *src = INV ? R.src + soff : R.dst + doff;  // first phase of the inverse transform
-    uint64_t *dst = R.dst + doff;
-    const PrimeConst P = primes[pr];
-    const uint64_t q = P.q, two_q = 2 * q;
-    const ulonglong2 *tw = tw_all + (size_t)pr * N;
-    const int r_base = blockIdx.x * ROWS;
-    const size_t base = (size_t)r_base * M;
-    for (int i = threadIdx.x; i < E; i += T) {
-        const int k = i / M, e = i % M;
-        sh[k * SK + e + (e >> 4)] = src[base + i];
-    }
-    __syncthreads();
-    if (!INV) {
-        ntt_pass<LOGM, R1, 0, false, false, true>(sh, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
-        __syncthreads();
-        ntt_pass<LOGM, R2, R1, false, false, true>(sh, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
-        __syncthreads();
+    const int nb = (N >> LOGM) / ROWS;
+    auto prefetch = [&](int t, int slot) {
+        const TileId id = tile_of(t, nb, R.n_rows);
+        const uint64_t *src = INV ? R.src + (size_t)id.g * R.src_gs + (size_t)R.src_off[id.row] * N
+                                  : R.dst + (size_t)id.g * R.dst_gs + (size_t)R.dst_off[id.row] * N;
+        const size_t base = (size_t)id.bx * ROWS * M;
         for (int i = threadIdx.x; i < E; i += T) {
             const int k = i / M, e = i % M;
-            uint64_t v = sh[k * SK + e + (e >> 4)];
-            if (v >= two_q) v -= two_q;
-            if (v >= q) v -= q;
-            dst[base + i] = v;
+            cp_async8(buf[slot] + k * SK + e + (e >> 4), src + base + i);
         }
-    } else {
-        ntt_pass<LOGM, R2, R1, true, false, true>(sh, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
-        __syncthreads();
-        ntt_pass<LOGM, R1, 0, true, false, true>(sh, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
-        __syncthreads();
-        for (int i = threadIdx.x; i < E; i += T) {
-            const int k = i / M, e = i % M;
-            dst[base + i] = sh[k * SK + e + (e >> 4)];
+        cp_async_commit();
+    };
+    int t = blockIdx.x, slot = 0;
+    if (t < n_tiles) prefetch(t, 0);
+    for (; t < n_tiles; t += gridDim.x, slot ^= 1) {
+        const int tn = t + gridDim.x;
+        if (tn < n_tiles) {
+            prefetch(tn, slot ^ 1);
+            cp_async_wait_all_but_one();
+        } else {
+            cp_async_wait_all();
         }
+        __syncthreads();
+        const TileId id = tile_of(t, nb, R.n_rows);
+        const int pr = R.prime[id.row];
+        const PrimeConst P = primes[pr];
+        const uint64_t q = P.q, two_q = 2 * q;
+        const ulonglong2 *tw = tw_all + (size_t)pr * N;
+        uint64_t *dst = R.dst + (size_t)id.g * R.dst_gs + (size_t)R.dst_off[id.row] * N;
+        const int r_base = id.bx * ROWS;
+        const size_t base = (size_t)r_base * M;
+        uint64_t *b = buf[slot];
+        if (!INV) {
+            ntt_pass<LOGM, R1, 0, false, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+            __syncthreads();
+            ntt_pass<LOGM, R2, R1, false, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+            __syncthreads();
+            for (int i = threadIdx.x; i < E; i += T) {
+                const int k = i / M, e = i % M;
+                uint64_t v = b[k * SK + e + (e >> 4)];
+                if (v >= two_q) v -= two_q;
+                if (v >= q) v -= q;
+                dst[base + i] = v;
+            }
+        } else {
+            ntt_pass<LOGM, R2, R1, true, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+            __syncthreads();
+            ntt_pass<LOGM, R1, 0, true, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+            __syncthreads();
+            for (int i = threadIdx.x; i < E; i += T) {
+                const int k = i / M, e = i % M;
+                dst[base + i] = b[k * SK + e + (e >> 4)];
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -212,14 +285,21 @@ void ntt_cols_w(const LaunchCtx &c, const NttRows &rows)
     constexpr int T = (M >> Split<LOGM>::R1) * COLS;
     const int N2 = c.N >> LOGM;
     HX_CHECK(N2 % COLS == 0, HX_EINVAL, "NTT tile wider than the ring");
-    dim3 grid(N2 / COLS, rows.n_rows, rows.n_groups);
-    const size_t smem = (size_t)E * 8 + (size_t)M * 16;
+    const long long n_tiles = (long long)(N2 / COLS) * rows.n_rows * rows.n_groups;
+    HX_CHECK(n_tiles < (1ll << 31), HX_EINVAL, "NTT batch too large");
+    const size_t smem = (size_t)E * 16 + (size_t)M * 32;  // two tiles + two twiddle sets
     static const bool attr =  // thread-safe one-time setup
         cudaFuncSetAttribute(k_ntt_cols<LOGM, COLS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
         cudaSuccess;
     (void)attr;
+    static const int per_sm = [&] {
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_ntt_cols<LOGM, COLS, INV>, T, smem);
+        return v;
+    }();
+    const int grid = (int)std::min<long long>(n_tiles, (long long)std::max(1, per_sm) * c.t->n_sm);
     k_ntt_cols<LOGM, COLS, INV><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
-                                                            c.log_n);
+                                                            c.log_n, (int)n_tiles);
 }
 
 template <int LOGM, int ROWS, bool INV>
@@ -229,14 +309,21 @@ void ntt_rows_w(const LaunchCtx &c, const NttRows &rows)
     constexpr int T = (M >> Split<LOGM>::R1) * ROWS;
     const int N1 = c.N >> LOGM;
     HX_CHECK(N1 % ROWS == 0, HX_EINVAL, "NTT tile wider than the ring");
-    dim3 grid(N1 / ROWS, rows.n_rows, rows.n_groups);
-    const size_t smem = (size_t)ROWS * (M + M / 16) * 8;
+    const long long n_tiles = (long long)(N1 / ROWS) * rows.n_rows * rows.n_groups;
+    HX_CHECK(n_tiles < (1ll << 31), HX_EINVAL, "NTT batch too large");
+    const size_t smem = (size_t)ROWS * (M + M / 16) * 16;  // two tiles
     static const bool attr =  // thread-safe one-time setup
         cudaFuncSetAttribute(k_ntt_rows<LOGM, ROWS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
         cudaSuccess;
     (void)attr;
+    static const int per_sm = [&] {
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_ntt_rows<LOGM, ROWS, INV>, T, smem);
+        return v;
+    }();
+    const int grid = (int)std::min<long long>(n_tiles, (long long)std::max(1, per_sm) * c.t->n_sm);
     k_ntt_rows<LOGM, ROWS, INV><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
-                                                            c.log_n);
+                                                            c.log_n, (int)n_tiles);
 }
 
 template <bool INV, int LOGM>
