@@ -363,6 +363,14 @@ def run_hx(args, world, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def g4_iter(x, k):
+    """FP64 g_4^(k) with the printed g_4 = (35m^9 - 180m^7 + 378m^5 - 420m^3 + 315m)/128 (Sec. 4.2)."""
+    for _ in range(k):
+        y = x * x
+        x = x * ((((35 * y - 180) * y + 378) * y - 420) * y + 315) / 128.0
+    return x
+
+
 def run_sign(args):
     """Config 2: g_4^(8) (sign, or ReLU with --relu) on 64 ciphertexts of 16384 slots each, CKKS
     N=2^15, Q = 60 + 15x40 bit, P = 3x60 bit, scale 2^40, inputs uniform in [-1,-2^-8] U [2^-8,1];
@@ -405,17 +413,10 @@ def run_sign(args):
                 hx.hx_ct_destroy(o)
     clocks = sampler.stop()
     t = sum(times) / len(times)
-    # FP64 composite from the printed g_4 = (35m^9 - 180m^7 + 378m^5 - 420m^3 + 315m)/128 (Sec. 4.2)
-    def g4_iter(x):
-        for _ in range(k):
-            y = x * x
-            x = x * ((((35 * y - 180) * y + 378) * y - 420) * y + 315) / 128.0
-        return x
-
     errs_sgn, errs_g = [], []
     for i in range(4):
         got = hx.hx_decrypt(ctx, ks, outs[i])
-        g = g4_iter(xs[i])
+        g = g4_iter(xs[i], k)
         ref = xs[i] * (1 + g) / 2 if args.relu else g
         exact = np.maximum(xs[i], 0) if args.relu else np.sign(xs[i])
         errs_sgn.append(float(np.abs(got - exact).max()))
@@ -429,6 +430,91 @@ def run_sign(args):
             "config": {"workload": "cfg2: 64 ciphertexts x 16384 slots, |x| in [2^-8, 1], d=4, k=8, two host refreshes "
                                    "per step (timed with host wall clock: they cross the host)"},
             "max_err_vs_exact": max(errs_sgn), "max_err_vs_fp64_composite": max(errs_g), "clocks": clocks}
+    print(json.dumps(line), flush=True)
+    hx.hx_keyset_destroy(ks)
+    hx.hx_context_destroy(ctx)
+
+
+def run_dense(args):
+    """Config 3: one encrypted dense layer 784 -> 128, feedforward and backpropagation (Fig. 5),
+    batch of 64 inputs, 64 x 64 blocks (2 x 13 block products, packed 4 per ciphertext: 8
+    ciphertext pairs per HE-MatMult batch), ReLU by g_4^(8)(E/4), CKKS N=2^15, Q = 60 + 15x40 bit,
+    P = 3x60 bit, scale 2^40; weights N(0, 0.05), inputs U[0,1], upstream gradient N(0, 0.1).
+    The host refreshes inside the composite sign are in the timed region."""
+    import torch
+
+    from paper_2207_04620_gb300 import hx, workloads
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    cfg = workloads.CONFIGS["cfg3_dense784x128_n15"]
+    h, d, k, div = cfg["h"], cfg["d"], cfg["k"], cfg["input_div"]
+    ctx = hx.hx_context_create(cfg["log_n"], cfg["q_bits"], cfg["p_bits"], cfg["log2_scale"])
+    hx.hx_autotune(ctx)
+    ks = hx.hx_keygen(ctx, 2, 81, hx.hx_dense_rotation_steps(ctx, h))
+    beta = (1 << cfg["log_n"]) // 2 // (h * h)
+    W, X, G = workloads.dense_inputs(3, cfg["rows"], cfg["n_in"], cfg["batch"])
+    Wp, Xp, Gp = workloads.dense_pack(W, X, G, h, beta)
+    n_out, groups = len(Wp), len(Xp)
+    Wc = [hx.hx_encrypt(ctx, ks, Wp[i][g], 0, 1000 + 10 * i + g) for i in range(n_out) for g in range(groups)]
+    Xc = [hx.hx_encrypt(ctx, ks, Xp[g], 0, 2000 + g) for g in range(groups)]
+    Gc = [hx.hx_encrypt(ctx, ks, Gp[i], 0, 3000 + i) for i in range(n_out)]
+    stream = torch.cuda.current_stream()
+
+    def step(seed):
+        return hx.hx_dense_layer(ctx, ks, Wc, Xc, Gc, h, n_out, groups, d, k, div, refresh_seed=seed, stream=stream)
+
+    def free(res):
+        for part in res:
+            for c in part:
+                hx.hx_ct_destroy(c)
+
+    for w in range(args.warmup):
+        free(step(w))
+    torch.cuda.synchronize()
+    sampler = ClockSampler()
+    times = []
+    for it in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res = step(100 + it)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+        if it < args.steps - 1:
+            free(res)
+    clocks = sampler.stop()
+    t = sum(times) / len(times)
+    E, M, dW = res
+    Wb = workloads.blocks(W, h)
+    Xb = [r[0] for r in workloads.blocks(X, h)]
+    Gb = [r[0] for r in workloads.blocks(G, h)]
+    err = {"E": 0.0, "relu_vs_fp64_composite": 0.0, "relu_vs_exact": 0.0, "dW_vs_fp64_composite": 0.0}
+    for i in range(n_out):
+        e_ref = sum(a @ b for a, b in zip(Wb[i], Xb))
+        s_ref = g4_iter(e_ref / div, k)
+        l_ref = (1 + s_ref) / 2 * Gb[i]
+        e = workloads.unpack(hx.hx_decrypt(ctx, ks, E[i]), h, beta)[0]
+        m = workloads.unpack(hx.hx_decrypt(ctx, ks, M[i]), h, beta)[0]
+        err["E"] = max(err["E"], float(np.abs(e - e_ref).max()))
+        err["relu_vs_fp64_composite"] = max(err["relu_vs_fp64_composite"],
+                                            float(np.abs(m - e_ref * (1 + s_ref) / 2).max()))
+        err["relu_vs_exact"] = max(err["relu_vs_exact"], float(np.abs(m - np.maximum(e_ref, 0)).max()))
+        for g in range(groups):
+            got = workloads.unpack(hx.hx_decrypt(ctx, ks, dW[i * groups + g]), h, beta)
+            for q in range(beta):
+                j = beta * g + q
+                if j < len(Xb):
+                    err["dW_vs_fp64_composite"] = max(err["dW_vs_fp64_composite"],
+                                                      float(np.abs(got[q] - l_ref @ Xb[j].T).max()))
+    free(res)
+    line = {"metric": "encrypted dense layer 784->128 forward+backward, layers/s (batch 64, CKKS N=2^15)",
+            "value": round(1.0 / t, 4), "unit": "layer/s", "ms_per_step": round(t * 1e3, 1),
+            "steps": args.steps, "warmup": args.warmup, "n_gpus": 1, "higher_is_better": True, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "cfg3: W 128x784 (padded 128x832), X 784x64, h=64, beta=4, 8+8 ciphertext pairs "
+                                   "per HE-MatMult batch, ReLU g_4^(8)(E/4), host refreshes timed (host wall clock)"},
+            "max_abs_err": err, "clocks": clocks}
     print(json.dumps(line), flush=True)
     hx.hx_keyset_destroy(ks)
     hx.hx_context_destroy(ctx)
@@ -617,7 +703,7 @@ def run_micro(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--micro", choices=["ntt"], default=None)
-    ap.add_argument("--workload", choices=["matmul", "sign", "serve"], default="matmul")
+    ap.add_argument("--workload", choices=["matmul", "sign", "dense", "serve"], default="matmul")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--lanes", type=int, default=4)
@@ -640,6 +726,8 @@ def main():
         return run_sign(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "dense":
+        return run_dense(args)
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -204,6 +204,17 @@ hx_status hx_matmul(hx_context *ctx, const hx_keyset *ks, const hx_ct *A, const 
 hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *A,
                           const hx_ct *const *B, int h, size_t count, hx_ct **out, void *stream);
 
+/* ---- transpose (App. C) ---------------------------------------------------------- */
+/* A^T for each of the beta packed h x h matrices of `count` ciphertexts at one
+ * level (>= 2 limbs): sum over the 2h-1 diagonals (h-1)s of U^T with the
+ * baby-step/giant-step split, one rescale.  plan may be NULL (library masks);
+ * a transpose plan's masks are the diagonals s = -h+1..h-1 in that order and
+ * can be replaced with hx_matmul_plan_set_mask. */
+hx_status hx_transpose_plan_create(hx_context *ctx, int h, int limbs, hx_matmul_plan **out);
+int hx_transpose_rotation_steps(const hx_context *ctx, int h, int32_t *out, int cap);
+hx_status hx_transpose(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *x,
+                       int h, size_t count, hx_ct **out, void *stream);
+
 /* A captured batched product: the whole schedule of hx_matmul_batch for
  * `count` ciphertext pairs at the plan's level, recorded once into a CUDA graph
  * (its temporary allocations become graph memory nodes) over persistent input
@@ -231,6 +242,33 @@ hx_status hx_sign_approx(hx_context *ctx, const hx_keyset *ks, const hx_ct *x, i
                          int allow_refresh, uint64_t refresh_seed, hx_ct **out, void *stream);
 hx_status hx_sign_approx_batch(hx_context *ctx, const hx_keyset *ks, const hx_ct *const *x, size_t count, int d,
                                int k, int relu, int allow_refresh, uint64_t refresh_seed, hx_ct **out, void *stream);
+
+/* ---- one dense layer, feedforward and backpropagation (Fig. 5) ------------------ */
+/* Blocks of h x h, beta = (N/2)/h^2 per ciphertext, packed as in App. E:
+ *   W[i*groups + g]  packs W_{i,j}, j = beta*g .. beta*g + beta - 1, at positions 0..beta-1
+ *   X[g]             packs X_j for the same j (the inputs of a batch of h as columns)
+ *   G[i]             packs the upstream gradient G_i at position 0, zero elsewhere
+ * all W and X at one level and scale, G at a level no lower than the activation's.
+ * Outputs (new handles, owned by the caller):
+ *   E[i]   position 0: E_i = sum_j W_{i,j} X_j (other positions hold partial sums)
+ *   M[i]   position 0: ReLU(E_i) = E_i (1 + s_i) / 2, s_i = g_d^(k)(E_i / input_div)
+ *   dW[i*groups + g]  position p: L_i X_{beta*g+p}^T, L_i = ((1 + s_i)/2) . G_i
+ * Steps: one batched HE-MatMult over all (i, g); sums over g; a rotate-and-add
+ * fold of the beta positions; the composite sign (entry i refreshed with
+ * refresh_seed + i, as in hx_sign_approx_batch); L_i copied to every position
+ * by rotations; the X_g transposed (App. C) and brought to L's level and scale;
+ * a second batched HE-MatMult.  The three plans (NULL: the context's cached
+ * plan for the level reached) are a matmul plan at W's level, a transpose plan
+ * at X's level and a matmul plan at L's level.  Rotation keys:
+ * hx_dense_rotation_steps.
+ * Errors: HX_EINVAL (shapes, h), HX_ELEVEL (chain too short), HX_EKEY. */
+hx_status hx_dense_layer(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *fwd_plan,
+                         const hx_matmul_plan *transpose_plan, const hx_matmul_plan *bwd_plan, const hx_ct *const *W,
+                         const hx_ct *const *X, const hx_ct *const *G, int h, int n_out, int groups, int d, int k,
+                         double input_div, uint64_t refresh_seed, hx_ct **E, hx_ct **M, hx_ct **dW, void *stream);
+/* Rotation steps hx_dense_layer uses (both HE-MatMult variants, the transpose,
+ * and +-2^t for t < log2(beta)); returns their count, writes up to cap. */
+int hx_dense_rotation_steps(const hx_context *ctx, int h, int32_t *out, int cap);
 
 /* ---- serving (continuous batching) ----------------------------------------------- */
 /* A request server on the current device.  Requests queue on the host; a

@@ -362,28 +362,38 @@ def slot_transpose(a: np.ndarray, h: int, beta: int = 1) -> np.ndarray:
     return out
 
 
-def transpose(ev: C.Evaluator, ct: C.Ciphertext, h: int):
-    """App. C: U^T a = sum_s t_{(h-1)s} . R(a, (h-1)s), 2h-1 diagonals, with
-    the baby-step/giant-step split on s; masks encoded here at scale q_{l-1}."""
-    ctx = ev.ctx
-    beta = ctx.S // (h * h)
+def transpose_masks(h: int):
+    """Masks of the transpose, in plan order s = -h+1..h-1: R(t_(h-1)s, -(h-1)*b*floor(s/b))."""
     b = baby_steps(h)
-    sc = float(ctx.q[ct.limbs - 1])
-    prim = ctx.q[: ct.limbs]
+    return [("T", sh, R(diag_transpose(h, sh), -(h - 1) * b * (sh // b))) for sh in range(-h + 1, h)]
 
-    class _M:
-        pass
 
-    m = _M()
-    m.h, m.beta = h, beta
+def transpose_rotation_steps(h: int, beta: int) -> list:
+    b = baby_steps(h)
+    st = set()
+    for sh in range(-h + 1, h):
+        st.add(beta * (h - 1) * (sh % b))
+        st.add(beta * (h - 1) * b * (sh // b))
+    n = beta * h * h
+    return sorted({k % n for k in st} - {0})
 
-    def plaintext(kind, s):
-        vec = R(diag_transpose(h, s), -(h - 1) * b * (s // b))
-        c = C.encode_real(ctx.N, expand(vec, beta), sc)
-        return ctx.ntt(ctx.signed_to_rows(c, prim), prim), sc
 
-    m.plaintext = plaintext
-    return ev.rescale(lintrans_bsgs(ev, ct, range(-h + 1, h), h - 1, m, "T"))
+class TransposeMasks(MaskProvider):
+    """Mask plaintexts of App. C's transpose (diagonals (h-1)s), encoded at scale q_{l-1}."""
+
+    def __init__(self, ctx: C.Context, h: int, limbs: int):
+        self.ctx, self.h, self.limbs = ctx, h, limbs
+        self.beta = ctx.S // (h * h)
+        self.entries = [(kind, sh, vec, limbs) for kind, sh, vec in transpose_masks(h)]
+        self.index = {(kind, k): i for i, (kind, k, _, _) in enumerate(self.entries)}
+        self._coeffs = {}
+
+
+def transpose(ev: C.Evaluator, ct: C.Ciphertext, h: int, masks: "TransposeMasks | None" = None):
+    """App. C: U^T a = sum_s t_{(h-1)s} . R(a, (h-1)s) over the 2h-1 diagonals,
+    baby-step/giant-step split on s, then one rescale."""
+    masks = masks or TransposeMasks(ev.ctx, h, ct.limbs)
+    return ev.rescale(lintrans_bsgs(ev, ct, range(-h + 1, h), h - 1, masks, "T"))
 
 
 # ----------------------------------------------------------------------------
@@ -532,3 +542,72 @@ def sign_approx(ev: C.Evaluator, x: C.Ciphertext, d: int, k: int, relu: bool = F
     s1 = ev.add_const(m, 1.0)
     xa = level_adjust(ev, x, m.limbs, 0.5, m.scale)
     return _square_rs(ev, xa, s1)
+
+
+# ----------------------------------------------------------------------------
+# Fig. 5: one dense layer, feedforward then backpropagation (reading R19)
+# ----------------------------------------------------------------------------
+
+
+def dense_layer(ev: C.Evaluator, W, X, G, h: int, d: int, k: int, input_div: float, refresh_seed: int,
+                masks: dict | None = None):
+    """One dense layer over h x h blocks packed beta = S/h^2 per ciphertext.
+
+    W[i][g] packs W_{i,j}, j = beta*g + p at position p; X[g] packs X_j (a
+    batch of h inputs as columns); G[i] packs the upstream gradient G_i at
+    position 0.  Feedforward: E_i = sum_j W_{i,j} X_j, i.e. the block products,
+    their sum over g and a rotate-and-add over the beta positions (position 0
+    then holds E_i); s_i = g_d^(k)(E_i / input_div); ReLU(E_i) = E_i (1+s_i)/2.
+    Backpropagation: L_i = phi'(E_i) . G_i with phi' = (1+s_i)/2, copied to
+    every position by rotations, and dW_{i,j} = L_i X_j^T with the X_j
+    transposed (App. C) and brought to L's level and scale.
+    masks: optional {"fwd", "transpose", "bwd"} mask providers."""
+    masks = masks or {}
+    S = ev.ctx.S
+    beta = S // (h * h)
+    n_out, groups = len(W), len(X)
+    fwd = masks.get("fwd") or MaskProvider(ev.ctx, h, X[0].limbs)
+    E = []
+    for i in range(n_out):
+        acc = None
+        for g in range(groups):
+            p = matmul(ev, W[i][g], X[g], h, fwd)
+            acc = p if acc is None else ev.add(acc, p)
+        t = 1
+        while t < beta:
+            acc = ev.add(acc, ev.rotate(acc, t))
+            t *= 2
+        E.append(acc)
+    M, L = [], []
+    for i in range(n_out):
+        # E / input_div at E's scale, one level down (a scale of input_div * Delta would square
+        # away from Delta through the composition)
+        e_in = level_adjust(ev, E[i], E[i].limbs - 1, 1.0 / input_div, E[i].scale)
+        s1 = ev.add_const(sign_approx(ev, e_in, d, k, refresh_seed=refresh_seed + i), 1.0)
+        m = _square_rs(ev, ev.drop(E[i], s1.limbs), s1)
+        m.scale *= 2
+        li = _square_rs(ev, s1, ev.drop(G[i], s1.limbs))
+        li.scale *= 2
+        t = 1
+        while t < beta:
+            li = ev.add(li, ev.rotate(li, S - t))
+            t *= 2
+        M.append(m)
+        L.append(li)
+    tr = masks.get("transpose") or TransposeMasks(ev.ctx, h, X[0].limbs)
+    XT = [level_adjust(ev, transpose(ev, x, h, tr), L[0].limbs, 1.0, L[0].scale) for x in X]
+    bwd = masks.get("bwd") or MaskProvider(ev.ctx, h, L[0].limbs)
+    dW = [[matmul(ev, L[i], XT[g], h, bwd) for g in range(groups)] for i in range(n_out)]
+    return E, M, dW
+
+
+def dense_rotation_steps(h: int, beta: int) -> list:
+    """Rotations dense_layer uses: both HE-MatMult variants, the transpose, +-2^t for 2^t < beta."""
+    st = set(matmul_rotation_steps(h, beta, 4)) | set(matmul_rotation_steps(h, beta, 3))
+    st |= set(transpose_rotation_steps(h, beta))
+    n = beta * h * h
+    t = 1
+    while t < beta:
+        st |= {t, n - t}
+        t *= 2
+    return sorted(st)

@@ -448,9 +448,41 @@ hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_
     Cts a = gather(*ctx, A, count, S(stream));
     Cts b = gather(*ctx, B, count, S(stream));
     const hx_matmul_plan *p = plan ? plan : cached_plan(*ctx, h, a.limbs);
-    need(p->h == h, "plan built for another h");
+    need(p->h == h && p->kind == 0, "plan built for another h");
     Cts r = matmul_batch(*ctx, *ks, *p, a, b, S(stream));
     scatter(*ctx, r, out, S(stream));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_transpose_plan_create(hx_context *ctx, int h, int limbs, hx_matmul_plan **out)
+{
+    HX_TRY
+    need(ctx && out, "null argument");
+    *out = nullptr;
+    *out = make_transpose_plan(*ctx, h, limbs, nullptr);
+    return HX_OK;
+    HX_END
+}
+
+int hx_transpose_rotation_steps(const hx_context *ctx, int h, int32_t *out, int cap)
+{
+    if (!ctx || h < 2 || (h & (h - 1)) || h * h > ctx->N / 2) return HX_EINVAL;
+    std::vector<int64_t> st = transpose_rotation_steps(h, ctx->N / 2 / (h * h));
+    for (int i = 0; i < (int)st.size() && i < cap; i++) out[i] = (int32_t)st[i];
+    return (int)st.size();
+}
+
+hx_status hx_transpose(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *x,
+                       int h, size_t count, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(ctx && ks && x && out && count >= 1 && count < 4096, "bad argument");
+    for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    Cts a = gather(*ctx, x, count, S(stream));
+    const hx_matmul_plan *p = plan ? plan : cached_transpose_plan(*ctx, h, a.limbs);
+    need(p->h == h && p->kind == 1, "plan built for another shape");
+    scatter(*ctx, transpose_batch(*ctx, *ks, *p, a, S(stream)), out, S(stream));
     return HX_OK;
     HX_END
 }
@@ -582,6 +614,49 @@ hx_status hx_sign_approx_batch(hx_context *ctx, const hx_keyset *ks, const hx_ct
     scatter(*ctx, r, out, S(stream));
     return HX_OK;
     HX_END
+}
+
+hx_status hx_dense_layer(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *fwd_plan,
+                         const hx_matmul_plan *transpose_plan, const hx_matmul_plan *bwd_plan, const hx_ct *const *W,
+                         const hx_ct *const *X, const hx_ct *const *G, int h, int n_out, int groups, int d, int k,
+                         double input_div, uint64_t refresh_seed, hx_ct **E, hx_ct **M, hx_ct **dW, void *stream)
+{
+    HX_TRY
+    need(ctx && ks && W && X && G && E && M && dW, "null argument");
+    need(n_out >= 1 && groups >= 1 && (size_t)n_out * groups < 4096, "bad block counts");
+    for (int i = 0; i < n_out; i++) E[i] = M[i] = nullptr;
+    for (int i = 0; i < n_out * groups; i++) dW[i] = nullptr;
+    need(h >= 2 && (h & (h - 1)) == 0 && h * h <= ctx->N / 2, "h must be a power of two with h^2 <= N/2");
+    std::vector<const hx_ct *> wg((size_t)n_out * groups);
+    for (int i = 0; i < n_out; i++)
+        for (int g = 0; g < groups; g++) wg[(size_t)g * n_out + i] = W[(size_t)i * groups + g];
+    Cts w = gather(*ctx, wg.data(), wg.size(), S(stream));
+    Cts x = gather(*ctx, X, groups, S(stream));
+    Cts gr = gather(*ctx, G, n_out, S(stream));
+    need(!fwd_plan || fwd_plan->kind == 0, "fwd_plan is not a matmul plan");
+    need(!bwd_plan || bwd_plan->kind == 0, "bwd_plan is not a matmul plan");
+    need(!transpose_plan || transpose_plan->kind == 1, "transpose_plan is not a transpose plan");
+    DensePlans plans;
+    plans.fwd = fwd_plan;
+    plans.transpose = transpose_plan;
+    plans.bwd = bwd_plan;
+    DenseResult r = dense_batch(*ctx, *ks, plans, w, x, gr, h, d, k, input_div, refresh_seed, S(stream));
+    std::vector<hx_ct *> dg((size_t)n_out * groups);
+    scatter(*ctx, r.E, E, S(stream));
+    scatter(*ctx, r.M, M, S(stream));
+    scatter(*ctx, r.dW, dg.data(), S(stream));
+    for (int i = 0; i < n_out; i++)
+        for (int g = 0; g < groups; g++) dW[(size_t)i * groups + g] = dg[(size_t)g * n_out + i];
+    return HX_OK;
+    HX_END
+}
+
+int hx_dense_rotation_steps(const hx_context *ctx, int h, int32_t *out, int cap)
+{
+    if (!ctx || h < 2 || (h & (h - 1)) || h * h > ctx->N / 2) return HX_EINVAL;
+    std::vector<int64_t> st = dense_rotation_steps(h, ctx->N / 2 / (h * h));
+    for (int i = 0; i < (int)st.size() && i < cap; i++) out[i] = (int32_t)st[i];
+    return (int)st.size();
 }
 
 int hx_counters(const hx_context *ctx, uint64_t *out, int cap)

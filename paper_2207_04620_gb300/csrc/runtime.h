@@ -1,6 +1,7 @@
 // Host runtime: context, keys, batched ciphertext buffers and the evaluator.
 #pragma once
 #include <map>
+#include <tuple>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -60,7 +61,7 @@ struct hx_context {
     std::unique_ptr<hx::GaussianCdt> cdt;
     std::atomic<uint64_t> counters[hx::C_NUM] = {};
     std::mutex plan_mu;  // guards `plans`
-    std::map<std::pair<int, int>, hx_matmul_plan *> plans;
+    std::map<std::tuple<int, int, int>, hx_matmul_plan *> plans;  // (kind, h, limbs)
     int device = 0;
     hx::Profiler prof;
     bool profiling = false;
@@ -97,10 +98,11 @@ struct hx_matmul_exec {
 
 struct hx_matmul_plan {
     hx_context *ctx = nullptr;
+    int kind = 0;  // 0: HE-MatMult (Alg. 3), 1: transpose (App. C)
     int h = 0, limbs = 0, beta = 0, b = 0;
     bool alg3 = true;
     struct Mask {
-        int kind;  // 0 mu, 1 zeta, 2 v
+        int kind;  // 0 mu, 1 zeta, 2 v, 3 transpose diagonal
         int index;
         int limbs;
         bool extended;  // stored over q_0..q_{limbs-1} and the special primes
@@ -181,12 +183,25 @@ std::vector<int64_t> decrypt_coeffs(hx_context &ctx, const hx_keyset &ks, const 
 hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s);
 // the context's plan for (h, limbs) with library masks, built on first use (thread-safe)
 const hx_matmul_plan *cached_plan(hx_context &ctx, int h, int limbs);
+hx_matmul_plan *make_transpose_plan(hx_context &ctx, int h, int limbs, cudaStream_t s);
+const hx_matmul_plan *cached_transpose_plan(hx_context &ctx, int h, int limbs);
+std::vector<int64_t> transpose_rotation_steps(int h, int beta);
+Cts transpose_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &x, cudaStream_t s);
 std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs);
 Cts matmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &A, const Cts &B,
                  cudaStream_t s);
 // refresh randomness of entry b: SplitMix64 streams keyed by refresh_seeds[b] (tag 1 + refresh index)
 Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k, bool relu, bool allow_refresh,
                const std::vector<uint64_t> &refresh_seeds, cudaStream_t s);
+struct DenseResult {
+    Cts E, M, dW;
+};
+struct DensePlans {
+    const hx_matmul_plan *fwd = nullptr, *transpose = nullptr, *bwd = nullptr;  // null: the cached plan
+};
+DenseResult dense_batch(hx_context &ctx, const hx_keyset &ks, const DensePlans &plans, const Cts &W, const Cts &X,
+                        const Cts &G, int h, int d, int k, double input_div, uint64_t refresh_seed, cudaStream_t s);
+std::vector<int64_t> dense_rotation_steps(int h, int beta);
 
 // ---- context (context.cu) -------------------------------------------------------
 void build_context(hx_context &ctx, const hx_params &p);

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <set>
+
 #include "runtime.h"
 
 namespace hx {
@@ -48,6 +50,19 @@ std::vector<int32_t> diag_v(int h, int k)
     for (int t = 0; t < h * h; t++) v[t] = ((t % h) < h - k);
     return v;
 }
+// diagonal (h-1)s of the transpose (App. C): 1 at t = (h+1)i + s, max(0,-s) <= i < h - max(0,s)
+std::vector<int32_t> diag_transpose(int h, int sh)
+{
+    std::vector<int32_t> v(h * h, 0);
+    for (int t = 0; t < h * h; t++) {
+        const int d = t - sh;
+        if (d % (h + 1) != 0) continue;
+        const int i = d >= 0 ? d / (h + 1) : -((-d + h) / (h + 1));
+        v[t] = (i >= std::max(0, -sh) && i < h - std::max(0, sh));
+    }
+    return v;
+}
+
 // R(v, r): (v_r, ..., v_{n-1}, v_0, ..., v_{r-1})
 std::vector<int32_t> rot(const std::vector<int32_t> &v, int r)
 {
@@ -92,6 +107,8 @@ std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs)
     return out;
 }
 
+void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s);
+
 hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
 {
     HX_CHECK(h >= 2 && (h & (h - 1)) == 0 && h * h <= ctx.N / 2, HX_EINVAL, "h must be a power of two with h^2 <= N/2");
@@ -121,6 +138,14 @@ hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
         add(1, l, p->alg3 ? rot(diag_zeta(h, l), -h * b * (l / b)) : diag_zeta(h, l), limbs, false);
     if (p->alg3)  // Step 2 selects after rotating: v_k itself, in the extended basis
         for (int k = 1; k < h; k++) add(2, k, diag_v(h, k), limbs - 1, true);
+    encode_plan_masks(ctx, *p, s);
+    return p.release();
+}
+
+void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s)
+{
+    hx_matmul_plan *p = &pl;
+    const int h = p->h;
     // encode every mask with the library's encoder (expanded over the beta packed matrices)
     std::vector<double> slots(ctx.N / 2);
     std::vector<int64_t> coeffs(ctx.N);
@@ -136,13 +161,65 @@ hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
             upload_plaintext(ctx, s, coeffs.data(), m.limbs, m.pt->p);
         }
     }
+}
+
+hx_matmul_plan *make_transpose_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
+{
+    HX_CHECK(h >= 2 && (h & (h - 1)) == 0 && h * h <= ctx.N / 2, HX_EINVAL, "h must be a power of two with h^2 <= N/2");
+    HX_CHECK(limbs >= 2 && limbs <= ctx.n_q, HX_ELEVEL, "the transpose needs a level to rescale");
+    std::unique_ptr<hx_matmul_plan> p(new hx_matmul_plan);
+    p->ctx = &ctx;
+    p->kind = 1;
+    p->h = h;
+    p->limbs = limbs;
+    p->beta = ctx.N / 2 / (h * h);
+    p->b = baby_steps(h);
+    p->alg3 = false;
+    for (int sh = -h + 1; sh < h; sh++) {
+        hx_matmul_plan::Mask m;
+        m.kind = 3;
+        m.index = sh;
+        m.limbs = limbs;
+        m.extended = false;
+        m.scale = (double)ctx.primes[limbs - 1];
+        m.vec = rot(diag_transpose(h, sh), -(h - 1) * p->b * floordiv(sh, p->b));
+        p->index[{3, sh}] = (int)p->masks.size();
+        p->masks.push_back(std::move(m));
+    }
+    encode_plan_masks(ctx, *p, s);
     return p.release();
+}
+
+const hx_matmul_plan *cached_transpose_plan(hx_context &ctx, int h, int limbs)
+{
+    std::lock_guard<std::mutex> lk(ctx.plan_mu);
+    auto key = std::make_tuple(1, h, limbs);
+    auto it = ctx.plans.find(key);
+    if (it != ctx.plans.end()) return it->second;
+    hx_matmul_plan *p = make_transpose_plan(ctx, h, limbs, nullptr);
+    ctx.plans[key] = p;
+    return p;
+}
+
+std::vector<int64_t> transpose_rotation_steps(int h, int beta)
+{
+    const int b = baby_steps(h);
+    const int64_t n = (int64_t)beta * h * h;
+    std::vector<int64_t> out;
+    for (int sh = -h + 1; sh < h; sh++)
+        for (int64_t x : {(int64_t)beta * (h - 1) * posmod(sh, b), (int64_t)beta * (h - 1) * b * floordiv(sh, b)}) {
+            const int64_t r = ((x % n) + n) % n;
+            if (r) out.push_back(r);
+        }
+    std::sort(out.begin(), out.end());
+    out.erase(std::unique(out.begin(), out.end()), out.end());
+    return out;
 }
 
 const hx_matmul_plan *cached_plan(hx_context &ctx, int h, int limbs)
 {
     std::lock_guard<std::mutex> lk(ctx.plan_mu);
-    auto key = std::make_pair(h, limbs);
+    auto key = std::make_tuple(0, h, limbs);
     auto it = ctx.plans.find(key);
     if (it != ctx.plans.end()) return it->second;
     hx_matmul_plan *p = make_plan(ctx, h, limbs, nullptr);
@@ -277,9 +354,18 @@ Cts matmul_depth2(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const 
 
 } // namespace
 
+Cts transpose_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &x, cudaStream_t s)
+{
+    HX_CHECK(plan.kind == 1, HX_EINVAL, "not a transpose plan");
+    HX_CHECK(x.comps == 2 && x.limbs == plan.limbs, HX_ELEVEL, "input is not at the plan's level");
+    Eval ev(ctx, s);
+    return ev.rescale(lintrans(ev, ks, x, -plan.h + 1, plan.h - 1, plan.h - 1, plan, 3));
+}
+
 Cts matmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &A, const Cts &B,
                  cudaStream_t s)
 {
+    HX_CHECK(plan.kind == 0, HX_EINVAL, "not a matmul plan");
     HX_CHECK(A.comps == 2 && B.comps == 2 && A.B == B.B, HX_EINVAL, "matmul needs two batches of ciphertexts");
     HX_CHECK(A.limbs == plan.limbs && B.limbs == plan.limbs, HX_ELEVEL, "inputs are not at the plan's level");
     HX_CHECK(A.scale == B.scale, HX_ESCALE, "inputs must share the scale");
@@ -425,6 +511,107 @@ Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k,
     Cts s1 = ev.add_const(m, 1.0);
     Cts xa = level_adjust(ev, x, m.limbs, 0.5, m.scale);
     return square_rs(ev, ks, xa, s1);
+}
+
+// ---- Fig. 5: one dense layer, feedforward then backpropagation ------------------
+//
+// W holds the weight blocks g-major (entry g*n_out + i packs W_{i,j} for
+// j = beta*g .. beta*g + beta - 1 at positions 0..beta-1), X the input
+// blocks (entry g packs X_j the same way), G the upstream gradient (entry i
+// packs G_i at position 0, zero elsewhere).
+
+namespace {
+
+Cts slice(const hx_context &ctx, const Cts &a, int first, int count)
+{
+    Cts o = a;
+    o.B = count;
+    o.d = a.d + (size_t)first * a.bstride(ctx.N);
+    return o;
+}
+
+// entry g*times + i = a[g]
+Cts repeat_each(Eval &ev, const Cts &a, int times)
+{
+    Cts o = ev.alloc(a.B * times, a.comps, a.limbs);
+    o.scale = a.scale;
+    const size_t N = ev.ctx.N;
+    for (int g = 0; g < a.B; g++)
+        launch_copy(ev.lc(), View{o.d + (size_t)g * times * o.bstride(N), o.bstride(N), o.cstride(N)},
+                    View{a.d + (size_t)g * a.bstride(N), 0, a.cstride(N)}, times, a.comps, a.limbs);
+    return o;
+}
+
+// entry g*a.B + i = a[i]
+Cts repeat_block(Eval &ev, const Cts &a, int times)
+{
+    Cts o = ev.alloc(a.B * times, a.comps, a.limbs);
+    o.scale = a.scale;
+    const size_t N = ev.ctx.N;
+    for (int g = 0; g < times; g++)
+        launch_copy(ev.lc(), View{o.d + (size_t)g * a.B * o.bstride(N), o.bstride(N), o.cstride(N)}, a.view(ev.ctx.N),
+                    a.B, a.comps, a.limbs);
+    return o;
+}
+
+} // namespace
+
+std::vector<int64_t> dense_rotation_steps(int h, int beta)
+{
+    std::set<int64_t> st;
+    for (int limbs : {3, 4})
+        for (int64_t k : plan_rotation_steps(h, beta, limbs)) st.insert(k);
+    for (int64_t k : transpose_rotation_steps(h, beta)) st.insert(k);
+    const int64_t S = (int64_t)beta * h * h;
+    for (int64_t t = 1; t < beta; t *= 2) {
+        st.insert(t);
+        st.insert(S - t);
+    }
+    return std::vector<int64_t>(st.begin(), st.end());
+}
+
+DenseResult dense_batch(hx_context &ctx, const hx_keyset &ks, const DensePlans &plans, const Cts &W, const Cts &X,
+                        const Cts &G, int h, int d, int k, double input_div, uint64_t refresh_seed, cudaStream_t s)
+{
+    const int n_out = G.B, groups = X.B;
+    HX_CHECK(W.comps == 2 && X.comps == 2 && G.comps == 2, HX_EINVAL, "dense layer needs ciphertexts");
+    HX_CHECK(n_out >= 1 && groups >= 1 && W.B == n_out * groups, HX_EINVAL, "need n_out*groups weight ciphertexts");
+    HX_CHECK(input_div > 0, HX_EINVAL, "input_div must be positive");
+    const int64_t S = ctx.N / 2;
+    const int beta = (int)(S / ((int64_t)h * h));
+    Eval ev(ctx, s);
+    // feedforward: every block product in one batched HE-MatMult
+    const hx_matmul_plan *pf = plans.fwd ? plans.fwd : cached_plan(ctx, h, W.limbs);
+    HX_CHECK(pf->h == h, HX_EINVAL, "feedforward plan built for another h");
+    Cts P = matmul_batch(ctx, ks, *pf, W, repeat_each(ev, X, n_out), s);
+    Cts E = ev.copy(slice(ctx, P, 0, n_out));
+    for (int g = 1; g < groups; g++) ev.add_inplace(E, slice(ctx, P, g * n_out, n_out));
+    for (int t = 1; t < beta; t *= 2) E = ev.add(E, ev.rotate(E, t, ks));  // position 0 sums the beta positions
+    // E / input_div at E's scale, one level down (a scale of input_div * Delta would square away from
+    // Delta through the composition)
+    HX_CHECK(E.limbs >= 2, HX_ELEVEL, "levels exhausted before the activation");
+    Cts Ein = level_adjust(ev, E, E.limbs - 1, 1.0 / input_div, E.scale);
+    std::vector<uint64_t> seeds(n_out);
+    for (int i = 0; i < n_out; i++) seeds[i] = refresh_seed + (uint64_t)i;
+    Cts s1 = ev.add_const(sign_batch(ctx, ks, Ein, d, k, false, true, seeds, s), 1.0);  // 2 phi'(E)
+    HX_CHECK(G.limbs >= s1.limbs && s1.limbs >= 2, HX_ELEVEL, "levels exhausted before the activation");
+    DenseResult r;
+    r.E = E;
+    r.M = square_rs(ev, ks, ev.drop(E, s1.limbs), s1);  // ReLU(E) = E (1 + s) / 2
+    r.M.scale *= 2;
+    // backpropagation: L = phi'(E) . G, copied to every packed position
+    Cts L = square_rs(ev, ks, s1, ev.drop(G, s1.limbs));
+    L.scale *= 2;
+    for (int t = 1; t < beta; t *= 2) L = ev.add(L, ev.rotate(L, S - t, ks));
+    const hx_matmul_plan *pt = plans.transpose ? plans.transpose : cached_transpose_plan(ctx, h, X.limbs);
+    HX_CHECK(pt->h == h, HX_EINVAL, "transpose plan built for another h");
+    Cts XT = transpose_batch(ctx, ks, *pt, X, s);
+    HX_CHECK(XT.limbs > L.limbs, HX_ELEVEL, "transposed inputs below the gradient's level");
+    Cts XTa = level_adjust(ev, XT, L.limbs, 1.0, L.scale);
+    const hx_matmul_plan *pb = plans.bwd ? plans.bwd : cached_plan(ctx, h, L.limbs);
+    HX_CHECK(pb->h == h, HX_EINVAL, "backpropagation plan built for another h");
+    r.dW = matmul_batch(ctx, ks, *pb, repeat_block(ev, L, groups), repeat_each(ev, XTa, n_out), s);
+    return r;
 }
 
 } // namespace hx

@@ -80,12 +80,18 @@ _SIGS = {
     "hx_matmul_rotation_steps": (c_int, [c_vp, c_int, c_int, P_i32, c_int]),
     "hx_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, PP, c_vp]),
     "hx_matmul_batch": (c_int, [c_vp, c_vp, c_vp, PP, PP, c_int, c_size_t, PP, c_vp]),
+    "hx_transpose_plan_create": (c_int, [c_vp, c_int, c_int, PP]),
+    "hx_transpose_rotation_steps": (c_int, [c_vp, c_int, P_i32, c_int]),
+    "hx_transpose": (c_int, [c_vp, c_vp, c_vp, PP, c_int, c_size_t, PP, c_vp]),
     "hx_matmul_exec_create": (c_int, [c_vp, c_vp, c_vp, c_size_t, c_double, PP]),
     "hx_matmul_exec_run": (c_int, [c_vp, PP, PP, PP, c_vp]),
     "hx_matmul_exec_launches": (c_i64, [c_vp]),
     "hx_matmul_exec_destroy": (None, [c_vp]),
     "hx_sign_approx": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
     "hx_sign_approx_batch": (c_int, [c_vp, c_vp, PP, c_size_t, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
+    "hx_dense_layer": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, PP, PP, PP, c_int, c_int, c_int, c_int, c_int, c_double,
+                                c_u64, PP, PP, PP, c_vp]),
+    "hx_dense_rotation_steps": (c_int, [c_vp, c_int, P_i32, c_int]),
     "hx_server_create": (c_int, [c_size_t, c_int, c_int, PP]),
     "hx_server_register_keys": (c_int, [c_vp, c_vp]),
     "hx_server_submit_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_int, P_u64]),
@@ -385,6 +391,26 @@ def hx_matmul_batch(ctx, ks, plan, As, Bs, h, stream=None) -> list:
     return [outs[i] for i in range(n)]
 
 
+def hx_transpose_plan_create(ctx: int, h: int, limbs: int) -> int:
+    out = _out()
+    _chk(lib().hx_transpose_plan_create(ctx, h, limbs, ctypes.byref(out)))
+    return out.value
+
+
+def hx_transpose_rotation_steps(ctx: int, h: int) -> list:
+    buf = np.zeros(4096, dtype=np.int32)
+    n = _chk(lib().hx_transpose_rotation_steps(ctx, h, buf.ctypes.data_as(P_i32), buf.size))
+    return [int(x) for x in buf[:n]]
+
+
+def hx_transpose(ctx, ks, plan, xs, h, stream=None) -> list:
+    n = len(xs)
+    a = (c_vp * n)(*xs)
+    outs = (c_vp * n)()
+    _chk(lib().hx_transpose(ctx, ks, plan, a, h, n, outs, _stream(stream)))
+    return [outs[i] for i in range(n)]
+
+
 def hx_matmul_exec_create(ctx, ks, plan, count, scale) -> int:
     out = _out()
     _chk(lib().hx_matmul_exec_create(ctx, ks, plan, count, float(scale), ctypes.byref(out)))
@@ -421,6 +447,29 @@ def hx_sign_approx_batch(ctx, ks, xs, d, k, relu=False, allow_refresh=True, refr
     _chk(lib().hx_sign_approx_batch(ctx, ks, a, n, d, k, int(relu), int(allow_refresh), refresh_seed, outs,
                                     _stream(stream)))
     return [outs[i] for i in range(n)]
+
+
+# ---- dense layer (Fig. 5) ----------------------------------------------------------------
+
+def hx_dense_layer(ctx, ks, W, X, G, h, n_out, groups, d, k, input_div, refresh_seed=0, plans=(0, 0, 0),
+                   stream=None):
+    """W: n_out*groups handles (i-major), X: groups handles, G: n_out handles; plans: (feedforward,
+    transpose, backpropagation) plan handles, 0 for the cached ones; returns (E, M, dW)."""
+    w = (c_vp * len(W))(*W)
+    x = (c_vp * len(X))(*X)
+    g = (c_vp * len(G))(*G)
+    e = (c_vp * n_out)()
+    m = (c_vp * n_out)()
+    dw = (c_vp * (n_out * groups))()
+    _chk(lib().hx_dense_layer(ctx, ks, plans[0], plans[1], plans[2], w, x, g, h, n_out, groups, d, k,
+                              float(input_div), refresh_seed, e, m, dw, _stream(stream)))
+    return [e[i] for i in range(n_out)], [m[i] for i in range(n_out)], [dw[i] for i in range(n_out * groups)]
+
+
+def hx_dense_rotation_steps(ctx: int, h: int) -> list:
+    buf = np.zeros(4096, dtype=np.int32)
+    n = _chk(lib().hx_dense_rotation_steps(ctx, h, buf.ctypes.data_as(P_i32), buf.size))
+    return [int(x) for x in buf[:n]]
 
 
 # ---- serving ------------------------------------------------------------------------------

@@ -290,6 +290,96 @@ def test_matmul_batched_equals_one_at_a_time():
         pr.close()
 
 
+@pytest.mark.parametrize("h", [8, 16])
+def test_transpose_bit_exact(h):
+    p = PARAMS["alg3"]
+    beta = (1 << p["log_n"]) // 2 // (h * h)
+    pr = Pair("alg3", rot_steps=Hc.transpose_rotation_steps(h, beta))
+    try:
+        assert hx.hx_transpose_rotation_steps(pr.ctx, h) == Hc.transpose_rotation_steps(h, beta)
+        masks = Hc.TransposeMasks(pr.octx, h, pr.octx.n_q)
+        plan = hx.hx_transpose_plan_create(pr.ctx, h, pr.octx.n_q)
+        assert hx.hx_matmul_plan_num_masks(plan) == 2 * h - 1
+        for i in range(2 * h - 1):
+            hx.hx_matmul_plan_set_mask(pr.ctx, plan, i, masks.coeffs(i))
+        mats = [workloads.matrices(70 + i, beta, h) for i in range(2)]
+        cts = [pr.encrypt(workloads.pack(m, h, beta), 80 + i) for i, m in enumerate(mats)]
+        outs = hx.hx_transpose(pr.ctx, pr.ks, plan, [pr.to_lib(c) for c in cts], h)
+        for i in range(2):
+            assert pr.same(outs[i], Hc.transpose(C.Evaluator(pr.octx, pr.oks), cts[i], h, masks))
+            got = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, outs[i]), h, beta)
+            assert max(np.abs(g - m.T).max() for g, m in zip(got, mats[i])) < 2 ** -20
+        hx.hx_matmul_plan_destroy(plan)
+    finally:
+        pr.close()
+
+
+def test_dense_layer_bit_exact():
+    """Fig. 5, one layer through hx_dense_layer: E, ReLU(E) and dW equal the
+    oracle's composition bit for bit (ragged shapes: 30 x 180 weights, 12 input
+    blocks in two groups of beta = 8, one refresh per output block), and decrypt
+    to the FP64 computation of the same functions."""
+    h, d, k, div, seed = 16, 2, 5, 4.0, 31
+    p = PARAMS["sign"]
+    S = (1 << p["log_n"]) // 2
+    beta = S // (h * h)
+    pr = Pair("sign", rot_steps=Hc.dense_rotation_steps(h, beta))
+    try:
+        assert hx.hx_dense_rotation_steps(pr.ctx, h) == Hc.dense_rotation_steps(h, beta)
+        W, X, G = workloads.dense_inputs(7, 30, 180, h)
+        Wp, Xp, Gp = workloads.dense_pack(W, X, G, h, beta)
+        n_out, groups = len(Wp), len(Xp)
+        Wc = [[pr.encrypt(Wp[i][g], 500 + 10 * i + g) for g in range(groups)] for i in range(n_out)]
+        Xc = [pr.encrypt(Xp[g], 600 + g) for g in range(groups)]
+        Gc = [pr.encrypt(Gp[i], 700 + i) for i in range(n_out)]
+        top = pr.octx.n_q
+        # level of L: E at top-3, E/div one lower, then the compositions with refreshes
+        m, dg = top - 4, Hc.g_depth(d)
+        for _ in range(k):
+            if m - 1 < dg:
+                m = top
+            m -= dg
+        lb = m - 1
+        masks = {"fwd": Hc.MaskProvider(pr.octx, h, top), "transpose": Hc.TransposeMasks(pr.octx, h, top),
+                 "bwd": Hc.MaskProvider(pr.octx, h, lb)}
+        plans = [hx.hx_matmul_plan_create(pr.ctx, h, top), hx.hx_transpose_plan_create(pr.ctx, h, top),
+                 hx.hx_matmul_plan_create(pr.ctx, h, lb)]
+        for plan, mk in zip(plans, (masks["fwd"], masks["transpose"], masks["bwd"])):
+            for i in range(len(mk.entries)):
+                hx.hx_matmul_plan_set_mask(pr.ctx, plan, i, mk.coeffs(i))
+        E, M, dW = hx.hx_dense_layer(pr.ctx, pr.ks, [pr.to_lib(c) for row in Wc for c in row],
+                                     [pr.to_lib(c) for c in Xc], [pr.to_lib(c) for c in Gc], h, n_out, groups, d, k,
+                                     div, refresh_seed=seed, plans=plans)
+        ev = C.Evaluator(pr.octx, pr.oks)
+        oE, oM, odW = Hc.dense_layer(ev, Wc, Xc, Gc, h, d, k, div, seed, masks=masks)
+        assert oM[0].limbs == lb
+        for i in range(n_out):
+            assert pr.same(E[i], oE[i]) and pr.same(M[i], oM[i])
+            for g in range(groups):
+                assert pr.same(dW[i * groups + g], odW[i][g])
+        Wb = workloads.blocks(W, h)
+        Xb = [r[0] for r in workloads.blocks(X, h)]
+        Gb = [r[0] for r in workloads.blocks(G, h)]
+        for i in range(n_out):
+            e_ref = sum(a @ b for a, b in zip(Wb[i], Xb))
+            s_ref = Hc.g_iter(d, k, e_ref / div)
+            l_ref = (1 + s_ref) / 2 * Gb[i]
+            e = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, E[i]), h, beta)[0]
+            mm = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, M[i]), h, beta)[0]
+            assert np.abs(e - e_ref).max() < 2 ** -16
+            assert np.abs(mm - e_ref * (1 + s_ref) / 2).max() < 2 ** -14
+            for g in range(groups):
+                got = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, dW[i * groups + g]), h, beta)
+                for q in range(beta):
+                    j = beta * g + q
+                    want = l_ref @ Xb[j].T if j < len(Xb) else np.zeros((h, h))
+                    assert np.abs(got[q] - want).max() < 2 ** -14
+        for plan in plans:
+            hx.hx_matmul_plan_destroy(plan)
+    finally:
+        pr.close()
+
+
 @pytest.mark.slow
 def test_matmul_config1_bit_exact():
     """Config 1 shape: N=2^14, 8 limbs, h=64 (beta=2), one ciphertext pair."""

@@ -275,6 +275,17 @@ def test_encrypted_matmul_oracle(enc_ctx, limbs):
     assert max(np.abs(g - a @ b).max() for g, a, b in zip(got, As, Bs)) < 2 ** -18
 
 
+def test_encrypted_transpose_oracle():
+    ctx = C.Context(10, [60, 40, 40], [60], 40)
+    h = 8
+    beta = ctx.S // (h * h)
+    ks = C.keygen(ctx, 2, 3, rot_steps=H.transpose_rotation_steps(h, beta))
+    ms = [np.random.default_rng(i).uniform(-1, 1, (h, h)) for i in range(beta)]
+    out = H.transpose(C.Evaluator(ctx, ks), C.encrypt(ctx, ks, H.pack(ms, h, beta), 5), h)
+    got = H.unpack(C.decrypt(ctx, ks, out), h, beta)
+    assert out.limbs == 2 and max(np.abs(g - m.T).max() for g, m in zip(got, ms)) < 2 ** -20
+
+
 def test_encrypted_sign_and_relu_oracle():
     ctx = C.Context(9, [60] + [40] * 15, [60] * 3, 40)
     ks = C.keygen(ctx, 2, 9)
@@ -289,3 +300,43 @@ def test_encrypted_sign_and_relu_oracle():
     assert np.abs(C.decrypt(ctx, ks, r) - np.maximum(x, 0)).max() < 2 ** -18
     with pytest.raises(ValueError):
         H.sign_approx(C.Evaluator(ctx, ks), ct, 4, 8)
+
+
+def test_dense_layer_oracle():
+    """Fig. 5, one layer: the oracle's encrypted feedforward and backpropagation
+    decrypt to the FP64 computation of the same functions: E = W X,
+    M = E (1 + g_d^(k)(E/4)) / 2 and dW_j = (((1 + g_d^(k)(E/4)) / 2) . G) X_j^T,
+    on ragged shapes (rows and inputs not multiples of h, a partly filled
+    second group), with one refresh per output block inside the sign."""
+    from paper_2207_04620_gb300 import workloads as wl
+    h, d, k, div = 8, 2, 5, 4.0
+    ctx = C.Context(10, [60] + [40] * 15, [60] * 3, 40)
+    beta = ctx.S // (h * h)
+    ks = C.keygen(ctx, 2, 91, rot_steps=H.dense_rotation_steps(h, beta))
+    ev = C.Evaluator(ctx, ks)
+    W, X, G = wl.dense_inputs(5, 14, 90, h)
+    Wp, Xp, Gp = wl.dense_pack(W, X, G, h, beta)
+    n_out, groups = len(Wp), len(Xp)
+    assert (n_out, groups) == (2, 2)
+    Wc = [[C.encrypt(ctx, ks, Wp[i][g], 200 + 10 * i + g) for g in range(groups)] for i in range(n_out)]
+    Xc = [C.encrypt(ctx, ks, Xp[g], 300 + g) for g in range(groups)]
+    Gc = [C.encrypt(ctx, ks, Gp[i], 400 + i) for i in range(n_out)]
+    E, M, dW = H.dense_layer(ev, Wc, Xc, Gc, h, d, k, div, refresh_seed=17)
+    assert ev.counts.get("Refresh", 0) == n_out
+    Eb = wl.blocks(W, h)
+    Xb = [r[0] for r in wl.blocks(X, h)]
+    Gb = [r[0] for r in wl.blocks(G, h)]
+    for i in range(n_out):
+        e_ref = sum(a @ b for a, b in zip(Eb[i], Xb))
+        s_ref = H.g_iter(d, k, e_ref / div)
+        l_ref = (1 + s_ref) / 2 * Gb[i]
+        e = H.unpack(C.decrypt(ctx, ks, E[i]), h, beta)[0]
+        m = H.unpack(C.decrypt(ctx, ks, M[i]), h, beta)[0]
+        assert np.abs(e - e_ref).max() < 2 ** -16
+        assert np.abs(m - e_ref * (1 + s_ref) / 2).max() < 2 ** -14
+        for g in range(groups):
+            got = H.unpack(C.decrypt(ctx, ks, dW[i][g]), h, beta)
+            for p in range(beta):
+                j = beta * g + p
+                want = l_ref @ Xb[j].T if j < len(Xb) else np.zeros((h, h))
+                assert np.abs(got[p] - want).max() < 2 ** -14
