@@ -229,6 +229,19 @@ hx_status hx_matmul_exec_run(hx_matmul_exec *ex, const hx_ct *const *A, const hx
 /* kernel launches one replay contains */
 int64_t hx_matmul_exec_launches(const hx_matmul_exec *ex);
 void hx_matmul_exec_destroy(hx_matmul_exec *ex);
+/* The same replay with host buffers: copies host_A and host_B
+ * ([count][2][limbs][N] words each, the executor's level and scale) to the
+ * device, replays the graph and copies the products ([count][2][out_limbs][N],
+ * hx_matmul_exec_out_info) to host_out, all enqueued on `stream`; returns
+ * without waiting.  The buffers must stay valid until the stream has reached
+ * this point; page-locked buffers let the copies run asynchronously.  Calls on
+ * one executor must be ordered (one stream, or waited for): they share its
+ * device buffers.  Two executors on two streams overlap one batch's copies
+ * with the other's evaluation. */
+hx_status hx_matmul_exec_run_host(hx_matmul_exec *ex, const uint64_t *host_A, const uint64_t *host_B,
+                                  uint64_t *host_out, void *stream);
+hx_status hx_matmul_exec_out_info(const hx_matmul_exec *ex, int *limbs, double *scale);
+
 
 /* ---- sign / ReLU (Sec. 4, Alg. 5) ------------------------------------------ */
 /* g_d^(k)(x) (relu = 0) or ReLU(x) = x (1 + g_d^(k)(x)) / 2 (relu = 1), d in

@@ -579,6 +579,34 @@ hx_status hx_matmul_exec_run(hx_matmul_exec *ex, const hx_ct *const *A, const hx
     HX_END
 }
 
+hx_status hx_matmul_exec_run_host(hx_matmul_exec *ex, const uint64_t *host_A, const uint64_t *host_B,
+                                  uint64_t *host_out, void *stream)
+{
+    HX_TRY
+    need(ex && host_A && host_B && host_out, "null argument");
+    const size_t N = ex->ctx->N;
+    cudaStream_t s = S(stream);
+    // the executor's buffers are [count][2][limbs][N] with no gaps, the host layout
+    HX_CUDA(cudaMemcpyAsync(ex->A.d, host_A, sizeof(uint64_t) * ex->A.bstride(N) * ex->count, cudaMemcpyHostToDevice,
+                            s));
+    HX_CUDA(cudaMemcpyAsync(ex->B.d, host_B, sizeof(uint64_t) * ex->B.bstride(N) * ex->count, cudaMemcpyHostToDevice,
+                            s));
+    HX_CUDA(cudaGraphLaunch(ex->exec, s));
+    ex->ctx->counters[C_LAUNCH] += ex->launches;
+    HX_CUDA(cudaMemcpyAsync(host_out, ex->out.d, sizeof(uint64_t) * ex->out.bstride(N) * ex->count,
+                            cudaMemcpyDeviceToHost, s));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_matmul_exec_out_info(const hx_matmul_exec *ex, int *limbs, double *scale)
+{
+    if (!ex) return HX_EINVAL;
+    if (limbs) *limbs = ex->out.limbs;
+    if (scale) *scale = ex->out.scale;
+    return HX_OK;
+}
+
 int64_t hx_matmul_exec_launches(const hx_matmul_exec *ex) { return ex ? ex->launches : HX_EINVAL; }
 
 void hx_matmul_exec_destroy(hx_matmul_exec *ex)

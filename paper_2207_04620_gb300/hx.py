@@ -86,6 +86,8 @@ _SIGS = {
     "hx_matmul_exec_create": (c_int, [c_vp, c_vp, c_vp, c_size_t, c_double, PP]),
     "hx_matmul_exec_run": (c_int, [c_vp, PP, PP, PP, c_vp]),
     "hx_matmul_exec_launches": (c_i64, [c_vp]),
+    "hx_matmul_exec_run_host": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "hx_matmul_exec_out_info": (c_int, [c_vp, ctypes.POINTER(c_int), ctypes.POINTER(c_double)]),
     "hx_matmul_exec_destroy": (None, [c_vp]),
     "hx_sign_approx": (c_int, [c_vp, c_vp, c_vp, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
     "hx_sign_approx_batch": (c_int, [c_vp, c_vp, PP, c_size_t, c_int, c_int, c_int, c_int, c_u64, PP, c_vp]),
@@ -424,6 +426,18 @@ def hx_matmul_exec_run(ex, As, Bs, stream=None) -> list:
     outs = (c_vp * n)()
     _chk(lib().hx_matmul_exec_run(ex, a, b, outs, _stream(stream)))
     return [outs[i] for i in range(n)]
+
+
+def hx_matmul_exec_run_host(ex, host_a: int, host_b: int, host_out: int, stream=None) -> None:
+    """host_a, host_b, host_out: host addresses of [count][2][limbs][N] words (page-locked for
+    asynchronous copies); returns once the copies and the replay are enqueued."""
+    _chk(lib().hx_matmul_exec_run_host(ex, host_a, host_b, host_out, _stream(stream)))
+
+
+def hx_matmul_exec_out_info(ex):
+    limbs, scale = c_int(), c_double()
+    _chk(lib().hx_matmul_exec_out_info(ex, ctypes.byref(limbs), ctypes.byref(scale)))
+    return limbs.value, scale.value
 
 
 def hx_matmul_exec_launches(ex) -> int:

@@ -460,6 +460,19 @@ def test_matmul_graph_executor_equals_batched_call():
             for g, w in zip(got, want):
                 assert np.array_equal(hx.hx_ct_export(pr.ctx, g), w)
                 hx.hx_ct_destroy(g)
+        # the host-buffer replay: page-locked inputs in, products out, same residues
+        import torch
+
+        host_a = torch.from_numpy(np.stack([hx.hx_ct_export(pr.ctx, x) for x in A]).view(np.int64)).pin_memory()
+        host_b = torch.from_numpy(np.stack([hx.hx_ct_export(pr.ctx, x) for x in B]).view(np.int64)).pin_memory()
+        out_limbs, out_scale = hx.hx_matmul_exec_out_info(ex)
+        assert out_limbs == want[0].shape[1]
+        host_out = torch.zeros((2, 2, out_limbs, pr.N), dtype=torch.int64).pin_memory()
+        stream = torch.cuda.Stream()
+        hx.hx_matmul_exec_run_host(ex, host_a.data_ptr(), host_b.data_ptr(), host_out.data_ptr(), stream=stream)
+        stream.synchronize()
+        for i in range(2):
+            assert np.array_equal(host_out[i].numpy().view(np.uint64), want[i])
         hx.hx_matmul_exec_destroy(ex)
         hx.hx_matmul_plan_destroy(plan)
     finally:
