@@ -720,9 +720,82 @@ def run_micro(args):
     hx.hx_context_destroy(ctx)
 
 
+def run_micro_aggregate(args):
+    """Alg. 6 Aggregation alone: the model update w - eta/(B N) * sum_i g_i for the 8
+    gradient ciphertexts of one 784->128 layer (h=64, beta=4 packing) from 16 parties,
+    CKKS N=2^15, 16 limbs.  The streaming sum reads every party's ciphertext once
+    (algorithmic traffic: (parties + 1) ciphertexts of 2 x 16 x 2^15 words per model
+    ciphertext); the rescale and the final addition follow it."""
+    import torch
+
+    from paper_2207_04620_gb300 import hx
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    log_n, qb, pb = 15, [60] + [40] * 15, [60] * 3
+    parties, count = args.parties, 8
+    ctx = hx.hx_context_create(log_n, qb, pb, 40)
+    ks = hx.hx_keygen(ctx, 2, 5, [])
+    n_slots = (1 << log_n) // 2
+    rng = np.random.default_rng(11)
+    w = [rng.normal(0, 0.05, n_slots) for _ in range(count)]
+    wc = [hx.hx_encrypt(ctx, ks, w[m], 0, 10 + m) for m in range(count)]
+    g0 = [rng.normal(0, 0.01, n_slots) for _ in range(count)]
+    gc = []
+    for i in range(parties):
+        for m in range(count):
+            gc.append(hx.hx_encrypt(ctx, ks, g0[m] * (1 + 0.01 * i), 0, 1000 + 100 * i + m))
+    c = 0.1 / (4 * parties)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        for o in hx.hx_aggregate(ctx, gc, parties, wc, c, stream=stream):
+            hx.hx_ct_destroy(o)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+    times = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        outs = hx.hx_aggregate(ctx, gc, parties, wc, c, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        for o in outs[1:]:
+            hx.hx_ct_destroy(o)
+        last = outs[0]
+        if len(times) < args.steps:
+            hx.hx_ct_destroy(last)
+    want = w[0] - c * sum(g0[0] * (1 + 0.01 * i) for i in range(parties))
+    err = float(np.abs(hx.hx_decrypt(ctx, ks, last) - want).max())
+    hx.hx_ct_destroy(last)
+    # the streaming kernel alone, from the library's per-class CUDA events
+    hx.hx_profile_enable(ctx, True)
+    flush.zero_()
+    torch.cuda.synchronize()
+    for o in hx.hx_aggregate(ctx, gc, parties, wc, c, stream=stream):
+        hx.hx_ct_destroy(o)
+    prof = hx.hx_profile_read(ctx)
+    hx.hx_profile_enable(ctx, False)
+    _, agg_ms, agg_bytes = prof["aggregate"]
+    peak, kind = peaks()
+    gbs = agg_bytes / (agg_ms / 1e3) / 1e9
+    res = {"micro": "aggregate", "parties": parties, "ciphertexts": count, "log_n": log_n, "limbs": len(qb),
+           "call_ms": statistics.median(times), "kernel_ms": agg_ms, "kernel_bytes": agg_bytes,
+           "kernel_gbs": round(gbs, 1), "peak_gbs": peak, "peak_kind": kind, "frac": round(gbs / peak, 4),
+           "max_abs_err_vs_fp64": err,
+           "note": "call = sum + constant (one streaming kernel), rescale, addition, handle copies"}
+    print(json.dumps(res), flush=True)
+    hx.hx_keyset_destroy(ks)
+    hx.hx_context_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--micro", choices=["ntt"], default=None)
+    ap.add_argument("--micro", choices=["ntt", "aggregate"], default=None)
+    ap.add_argument("--parties", type=int, default=16)
     ap.add_argument("--workload", choices=["matmul", "sign", "dense", "serve"], default="matmul")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--load", type=float, default=0.8)
@@ -740,6 +813,8 @@ def main():
     ap.add_argument("--per-op-pairs", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.micro == "aggregate":
+        return run_micro_aggregate(args)
     if args.micro:
         return run_micro(args)
     if args.workload == "sign":

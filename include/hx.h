@@ -283,6 +283,18 @@ hx_status hx_dense_layer(hx_context *ctx, const hx_keyset *ks, const hx_matmul_p
  * and +-2^t for t < log2(beta)); returns their count, writes up to cap. */
 int hx_dense_rotation_steps(const hx_context *ctx, int h, int32_t *out, int cap);
 
+/* ---- server aggregation (Alg. 6, Aggregation) ------------------------------------ */
+/* out[m] = models[m] - eta_over_bn * sum_i grads[i*count + m] for m < count:
+ * the parties' encrypted gradients are summed in one streaming pass that
+ * reads them in place (16-byte loads, HBM-bound), the factor eta/(B*N) is the
+ * integer constant of a level adjustment (round(-eta_over_bn * scale_model *
+ * q_t / scale_grad), t = limbs - 1) applied in the same pass, then one rescale
+ * and the addition to the model dropped to t limbs.  All gradients share one
+ * scale and the models' level (>= 2 limbs); the result is at limbs - 1 with
+ * the model's scale.  Errors: HX_EINVAL, HX_ESCALE, HX_ELEVEL. */
+hx_status hx_aggregate(hx_context *ctx, const hx_ct *const *grads, size_t n_parties, const hx_ct *const *models,
+                       size_t count, double eta_over_bn, hx_ct **out, void *stream);
+
 /* ---- serving (continuous batching) ----------------------------------------------- */
 /* A request server on the current device.  Requests queue on the host; a
  * dispatcher forms a batch from the oldest pending request and the other

@@ -611,3 +611,25 @@ def dense_rotation_steps(h: int, beta: int) -> list:
         st |= {t, n - t}
         t *= 2
     return sorted(st)
+
+
+# ----------------------------------------------------------------------------
+# Alg. 6, Aggregation: the server's model update
+# ----------------------------------------------------------------------------
+
+
+def aggregate(ev: C.Evaluator, grads, models, eta_over_bn: float):
+    """grads[i][m]: party i's encrypted gradient for model ciphertext m.
+    The server sums the parties' gradients (Add), multiplies the sum by
+    eta/(B*N) and subtracts it from the model (Mul_pt, Sub).  The constant is
+    applied as a level adjustment of the sum to one level below the model at
+    the model's scale (its integer round(-eta/(B*N) * scale_w * q_t / scale_g),
+    then RS), so the update is added to the model dropped to that level."""
+    out = []
+    for m, w in enumerate(models):
+        acc = grads[0][m]
+        for i in range(1, len(grads)):
+            acc = ev.add(acc, grads[i][m])
+        upd = level_adjust(ev, acc, w.limbs - 1, -eta_over_bn, w.scale)
+        out.append(ev.add(ev.drop(w, w.limbs - 1), upd))
+    return out

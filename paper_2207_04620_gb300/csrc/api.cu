@@ -687,6 +687,24 @@ int hx_dense_rotation_steps(const hx_context *ctx, int h, int32_t *out, int cap)
     return (int)st.size();
 }
 
+hx_status hx_aggregate(hx_context *ctx, const hx_ct *const *grads, size_t n_parties, const hx_ct *const *models,
+                       size_t count, double eta_over_bn, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(ctx && grads && models && out && n_parties >= 1 && count >= 1 && count < 4096 && n_parties < 65536,
+         "bad argument");
+    for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    std::vector<const Cts *> g(n_parties * count);
+    for (size_t i = 0; i < g.size(); i++) {
+        need(grads[i] && grads[i]->ctx == ctx, "gradient from another context");
+        g[i] = &grads[i]->c;
+    }
+    Cts m = gather(*ctx, models, count, S(stream));
+    scatter(*ctx, aggregate(*ctx, g, (int)n_parties, m, eta_over_bn, S(stream)), out, S(stream));
+    return HX_OK;
+    HX_END
+}
+
 int hx_counters(const hx_context *ctx, uint64_t *out, int cap)
 {
     if (!ctx) return HX_EINVAL;

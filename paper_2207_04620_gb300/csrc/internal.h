@@ -103,7 +103,7 @@ struct Profiler {
     cudaEvent_t get();
     void clear();
 };
-enum KClass { K_NTT, K_KEYIP, K_CONV, K_MODDOWN, K_RESCALE, K_TENSOR, K_MULPT, K_ELEM, K_AUTO, K_MISC, K_NCLASS };
+enum KClass { K_NTT, K_KEYIP, K_CONV, K_MODDOWN, K_RESCALE, K_TENSOR, K_MULPT, K_ELEM, K_AUTO, K_AGG, K_MISC, K_NCLASS };
 extern const char *const kclass_names[K_NCLASS];
 
 // ---- kernel launchers (kernels.cu) ----------------------------------------------
@@ -120,6 +120,14 @@ void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse);
 void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float *ms_out);
 void launch_add(const LaunchCtx &c, View out, View a, View b, int B, int comps, int limbs, bool sub);
 void launch_copy(const LaunchCtx &c, View out, View a, int B, int comps, int limbs);
+// one ciphertext read in place: component c, limb l at p + c*cstride + l*N
+struct AggSrc {
+    const uint64_t *p;
+    uint64_t cstride;
+};
+// out[m] = C * sum_i src[i*count + m] (per limb, C given as Scalars), for m < count
+void launch_aggregate(const LaunchCtx &c, View out, const AggSrc *src_dev, int n_parties, int count, int comps,
+                      int limbs, const Scalars &C);
 void launch_mul_plain(const LaunchCtx &c, View out, View a, const uint64_t *pt_mont, int B, int limbs);
 void launch_mul_scalar(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int comps, int limbs);
 void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int limbs);

@@ -384,6 +384,47 @@ __global__ void k_copy(View out, View a, int comps, int n)
         *reinterpret_cast<ulonglong2 *>(out.p + oo + j) = *reinterpret_cast<const ulonglong2 *>(a.p + oa + j);
 }
 
+// Alg. 6 Aggregation: the sum over parties of one gradient ciphertext, times a
+// constant, streamed from the parties' buffers in place (16-byte loads, four
+// parties in flight per thread, a Barrett reduction every 4 terms).
+__global__ void k_aggregate(View out, const AggSrc *__restrict__ src, int n_parties, int count,
+                            const __grid_constant__ Scalars C, const PrimeConst *__restrict__ primes, int comps, int n)
+{
+    const int l = blockIdx.y, bc = blockIdx.z, m = bc / comps, ci = bc % comps;
+    const PrimeConst P = primes[l];
+    const size_t off = (size_t)l * n;
+    uint64_t *o = out.p + m * out.bstride + ci * out.cstride + off;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        uint64_t s0 = 0, s1 = 0;
+        int i = 0;
+        for (; i + 4 <= n_parties; i += 4) {
+            ulonglong2 x[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                const AggSrc a = src[(size_t)(i + u) * count + m];
+                x[u] = __ldcs(reinterpret_cast<const ulonglong2 *>(a.p + ci * a.cstride + off + j));
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                s0 += x[u].x;
+                s1 += x[u].y;
+            }
+            s0 = reduce64(s0, P.q, P.bar);  // below q + 4q < 2^64 before the reduction
+            s1 = reduce64(s1, P.q, P.bar);
+        }
+        for (; i < n_parties; i++) {
+            const AggSrc a = src[(size_t)i * count + m];
+            const ulonglong2 x = __ldcs(reinterpret_cast<const ulonglong2 *>(a.p + ci * a.cstride + off + j));
+            s0 = reduce64(s0 + x.x, P.q, P.bar);
+            s1 = reduce64(s1 + x.y, P.q, P.bar);
+        }
+        ulonglong2 r;
+        r.x = shoup(reduce64(s0, P.q, P.bar), C.v[l], C.sh[l], P.q);
+        r.y = shoup(reduce64(s1, P.q, P.bar), C.v[l], C.sh[l], P.q);
+        *reinterpret_cast<ulonglong2 *>(o + j) = r;
+    }
+}
+
 __global__ void k_lintrans_mac(const __grid_constant__ MacArgs A, const PrimeConst *__restrict__ primes, int B,
                                int limbs, int n)
 {
@@ -809,7 +850,7 @@ inline void post(const LaunchCtx &c, int k = 1)
 
 const char *const kclass_names[K_NCLASS] = {"ntt", "key_inner_product", "basis_convert", "moddown_final",
                                             "rescale", "tensor", "mul_plain", "add_sub_copy", "automorphism",
-                                            "other"};
+                                            "aggregate", "other"};
 
 cudaEvent_t Profiler::get()
 {
@@ -907,6 +948,16 @@ void launch_copy(const LaunchCtx &c, View out, View a, int B, int comps, int lim
     Timed tm_(c, K_ELEM, 16.0 * B * comps * limbs * c.N);
     dim3 grid(ew_blocks(c.N, 2), limbs, B * comps);
     k_copy<<<grid, 256, 0, c.stream>>>(out, a, comps, c.N);
+    post(c);
+}
+
+void launch_aggregate(const LaunchCtx &c, View out, const AggSrc *src_dev, int n_parties, int count, int comps,
+                      int limbs, const Scalars &C)
+{
+    Timed tm_(c, K_AGG, 8.0 * (n_parties + 1.0) * count * comps * limbs * c.N);
+    HX_CHECK(count * comps < 65536 && limbs < 65536, HX_EINVAL, "aggregation batch too large");
+    dim3 grid(ew_blocks(c.N, 2), limbs, count * comps);
+    k_aggregate<<<grid, 256, 0, c.stream>>>(out, src_dev, n_parties, count, C, c.t->primes, comps, c.N);
     post(c);
 }
 

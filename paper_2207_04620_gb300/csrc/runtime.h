@@ -202,6 +202,8 @@ struct DensePlans {
 DenseResult dense_batch(hx_context &ctx, const hx_keyset &ks, const DensePlans &plans, const Cts &W, const Cts &X,
                         const Cts &G, int h, int d, int k, double input_div, uint64_t refresh_seed, cudaStream_t s);
 std::vector<int64_t> dense_rotation_steps(int h, int beta);
+Cts aggregate(hx_context &ctx, const std::vector<const Cts *> &grads, int n_parties, const Cts &models, double c_real,
+              cudaStream_t s);
 
 // ---- context (context.cu) -------------------------------------------------------
 void build_context(hx_context &ctx, const hx_params &p);

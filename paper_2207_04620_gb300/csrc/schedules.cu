@@ -614,4 +614,39 @@ DenseResult dense_batch(hx_context &ctx, const hx_keyset &ks, const DensePlans &
     return r;
 }
 
+// ---- Alg. 6 Aggregation ----------------------------------------------------------
+// out[m] = models[m] - c_real * sum_i grads[i*count + m]: the sum and the integer
+// constant of the level adjustment (round(-c_real * scale_model * q_t / scale_grad),
+// t = limbs - 1) in one streaming pass over the parties' ciphertexts in place,
+// then the rescale by q_t and the addition to the model one level down.
+
+Cts aggregate(hx_context &ctx, const std::vector<const Cts *> &grads, int n_parties, const Cts &models, double c_real,
+              cudaStream_t s)
+{
+    const int count = models.B;
+    HX_CHECK(n_parties >= 1 && (int)grads.size() == n_parties * count, HX_EINVAL, "need n_parties*count gradients");
+    const Cts &g0 = *grads[0];
+    HX_CHECK(models.comps == 2 && models.limbs >= 2, HX_ELEVEL, "the update needs a level to rescale");
+    for (const Cts *g : grads) {
+        HX_CHECK(g->B == 1 && g->comps == 2 && g->limbs == models.limbs, HX_ESCALE,
+                 "gradients must be ciphertexts at the models' level");
+        HX_CHECK(g->scale == g0.scale, HX_ESCALE, "gradients must share the scale");
+    }
+    Eval ev(ctx, s);
+    const int L = models.limbs, target = L - 1;
+    const double cr = round_half_away(-c_real * models.scale * (double)ctx.primes[target] / g0.scale);
+    HX_CHECK(std::fabs(cr) < 4.6e18, HX_EINVAL, "update constant too large");
+    std::vector<AggSrc> tab(grads.size());
+    for (size_t i = 0; i < grads.size(); i++) tab[i] = AggSrc{grads[i]->d, (uint64_t)grads[i]->cstride(ctx.N)};
+    DevBuf tab_dev((tab.size() * sizeof(AggSrc) + 7) / 8, s);
+    HX_CUDA(cudaMemcpyAsync(tab_dev.p, tab.data(), tab.size() * sizeof(AggSrc), cudaMemcpyHostToDevice, s));
+    Cts sum = ev.alloc(count, 2, L);
+    sum.scale = g0.scale;
+    launch_aggregate(ev.lc(), sum.view(ctx.N), reinterpret_cast<const AggSrc *>(tab_dev.p), n_parties, count, 2, L,
+                     scalars_for(ctx, L, (int64_t)cr));
+    Cts upd = ev.rescale(sum);
+    upd.scale = models.scale;
+    return ev.add(ev.drop(models, target), upd);
+}
+
 } // namespace hx

@@ -94,6 +94,7 @@ _SIGS = {
     "hx_dense_layer": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, PP, PP, PP, c_int, c_int, c_int, c_int, c_int, c_double,
                                 c_u64, PP, PP, PP, c_vp]),
     "hx_dense_rotation_steps": (c_int, [c_vp, c_int, P_i32, c_int]),
+    "hx_aggregate": (c_int, [c_vp, PP, c_size_t, PP, c_size_t, c_double, PP, c_vp]),
     "hx_server_create": (c_int, [c_size_t, c_int, c_int, PP]),
     "hx_server_register_keys": (c_int, [c_vp, c_vp]),
     "hx_server_submit_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_int, P_u64]),
@@ -484,6 +485,18 @@ def hx_dense_rotation_steps(ctx: int, h: int) -> list:
     buf = np.zeros(4096, dtype=np.int32)
     n = _chk(lib().hx_dense_rotation_steps(ctx, h, buf.ctypes.data_as(P_i32), buf.size))
     return [int(x) for x in buf[:n]]
+
+
+# ---- aggregation (Alg. 6) -----------------------------------------------------------------
+
+def hx_aggregate(ctx, grads, n_parties, models, eta_over_bn, stream=None) -> list:
+    """grads: n_parties*len(models) handles, party-major; returns the updated models."""
+    count = len(models)
+    g = (c_vp * len(grads))(*grads)
+    m = (c_vp * count)(*models)
+    outs = (c_vp * count)()
+    _chk(lib().hx_aggregate(ctx, g, n_parties, m, count, float(eta_over_bn), outs, _stream(stream)))
+    return [outs[i] for i in range(count)]
 
 
 # ---- serving ------------------------------------------------------------------------------

@@ -380,6 +380,28 @@ def test_dense_layer_bit_exact():
         pr.close()
 
 
+@pytest.mark.parametrize("n_parties", [1, 5, 9])
+def test_aggregate_bit_exact(alg3, n_parties):
+    """Alg. 6 Aggregation through hx_aggregate (the parties' gradients read in
+    place; 1, 5 and 9 parties cover the four-party chunks and the tail) equals
+    the oracle's Add/level-adjust/Add chain and decrypts to w - c * sum_i g_i."""
+    pr = alg3
+    count, c = 3, 0.05 / (8 * max(n_parties, 1))
+    rng = np.random.default_rng(40 + n_parties)
+    w = [rng.uniform(-1, 1, pr.N // 2) for _ in range(count)]
+    g = [[rng.uniform(-1, 1, pr.N // 2) for _ in range(count)] for _ in range(n_parties)]
+    wc = [pr.encrypt(w[m], 900 + m) for m in range(count)]
+    gc = [[pr.encrypt(g[i][m], 1000 + 10 * i + m) for m in range(count)] for i in range(n_parties)]
+    outs = hx.hx_aggregate(pr.ctx, [pr.to_lib(x) for row in gc for x in row], n_parties,
+                           [pr.to_lib(x) for x in wc], c)
+    want = Hc.aggregate(C.Evaluator(pr.octx, pr.oks), gc, wc, c)
+    for m in range(count):
+        assert pr.same(outs[m], want[m])
+        ref = w[m] - c * sum(g[i][m] for i in range(n_parties))
+        assert np.abs(hx.hx_decrypt(pr.ctx, pr.ks, outs[m]) - ref).max() < 2 ** -22
+        hx.hx_ct_destroy(outs[m])
+
+
 @pytest.mark.slow
 def test_matmul_config1_bit_exact():
     """Config 1 shape: N=2^14, 8 limbs, h=64 (beta=2), one ciphertext pair."""

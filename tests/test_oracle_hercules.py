@@ -340,3 +340,23 @@ def test_dense_layer_oracle():
                 j = beta * g + p
                 want = l_ref @ Xb[j].T if j < len(Xb) else np.zeros((h, h))
                 assert np.abs(got[p] - want).max() < 2 ** -14
+
+
+def test_aggregate_oracle():
+    """Alg. 6 Aggregation: the updated model decrypts to w - eta/(B N) * sum_i g_i
+    (FP64), for 5 parties and two model ciphertexts; the level drops by one and
+    the model's scale is kept."""
+    ctx = C.Context(10, [60, 40, 40, 40], [60], 40)
+    ks = C.keygen(ctx, 2, 7)
+    ev = C.Evaluator(ctx, ks)
+    rng = np.random.default_rng(3)
+    n_parties, count, c = 5, 2, 0.01 / (4 * 5)
+    w = [rng.uniform(-1, 1, ctx.S) for _ in range(count)]
+    g = [[rng.uniform(-1, 1, ctx.S) for _ in range(count)] for _ in range(n_parties)]
+    wc = [C.encrypt(ctx, ks, w[m], 10 + m) for m in range(count)]
+    gc = [[C.encrypt(ctx, ks, g[i][m], 100 + 10 * i + m) for m in range(count)] for i in range(n_parties)]
+    out = H.aggregate(ev, gc, wc, c)
+    for m in range(count):
+        assert out[m].limbs == wc[m].limbs - 1 and out[m].scale == wc[m].scale
+        want = w[m] - c * sum(g[i][m] for i in range(n_parties))
+        assert np.abs(C.decrypt(ctx, ks, out[m]) - want).max() < 2 ** -22
