@@ -246,9 +246,9 @@ hx_status hx_matmul_exec_out_info(const hx_matmul_exec *ex, int *limbs, double *
 /* ---- sign / ReLU (Sec. 4, Alg. 5) ------------------------------------------ */
 /* g_d^(k)(x) (relu = 0) or ReLU(x) = x (1 + g_d^(k)(x)) / 2 (relu = 1), d in
  * [1, 4].  When the next composition no longer fits in the remaining levels,
- * the ciphertext is refreshed by a host-simulated DBootstrap (collective
- * decryption and re-encryption at the top level, randomness from
- * refresh_seed) if allow_refresh != 0, else HX_ELEVEL.  In the batch call,
+ * the ciphertext is refreshed by the collective DBootstrap protocol
+ * (hx_dbootstrap, masked decryption shares and re-encryption shares,
+ * randomness from refresh_seed) if allow_refresh != 0, else HX_ELEVEL.  In the batch call,
  * entry i uses refresh_seed + i, so every entry's result equals the single
  * call's with that seed. */
 hx_status hx_sign_approx(hx_context *ctx, const hx_keyset *ks, const hx_ct *x, int d, int k, int relu,
@@ -282,6 +282,24 @@ hx_status hx_dense_layer(hx_context *ctx, const hx_keyset *ks, const hx_matmul_p
 /* Rotation steps hx_dense_layer uses (both HE-MatMult variants, the transpose,
  * and +-2^t for t < log2(beta)); returns their count, writes up to cap. */
 int hx_dense_rotation_steps(const hx_context *ctx, int h, int32_t *out, int cap);
+
+/* ---- collective protocols (Fig. 1 items 13-14, toy scale, parties simulated) ---- */
+/* DKeySwitch: re-encrypts ct (under the collective key of `from`) under the
+ * public key of `to` without decryption.  Party i draws u_i (ternary) and
+ * e0_i, e1_i (Gaussian, the context's sigma) from SplitMix64 streams (seed,
+ * purpose, i, 0) and contributes (s_i*c1 + u_i*b' + e0_i, u_i*a' + e1_i); the
+ * result (c0 + sum, sum) keeps ct's level and scale and decrypts under `to`. */
+hx_status hx_dkeyswitch(hx_context *ctx, const hx_keyset *from, const hx_keyset *to, const hx_ct *ct, uint64_t seed,
+                        hx_ct **out, void *stream);
+/* DBootstrap: collective refresh to the top level and the default scale.
+ * Each party masks its decryption share at q_0 with a uniform M_i in
+ * [-bound, bound], bound = (floor(q_0/4) - 1)/n_parties, so the combined value
+ * is Delta_ct*m + e + sum M_i (|m| small enough that it stays below q_0/4);
+ * it is rescaled to Delta and re-encrypted against a common reference
+ * polynomial with shares -s_i*a - round(M_i*Delta/Delta_ct) + e1_i.  The same
+ * protocol refreshes inside hx_sign_approx (refresh index k uses stream
+ * index k; batch entry i the seed refresh_seed + i). */
+hx_status hx_dbootstrap(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, uint64_t seed, hx_ct **out, void *stream);
 
 /* ---- server aggregation (Alg. 6, Aggregation) ------------------------------------ */
 /* out[m] = models[m] - eta_over_bn * sum_i grads[i*count + m] for m < count:

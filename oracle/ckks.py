@@ -150,6 +150,8 @@ PURPOSE_SK, PURPOSE_PK_A, PURPOSE_PK_E = 1, 2, 3
 PURPOSE_KEY_A, PURPOSE_KEY_E = 4, 5
 PURPOSE_ENC_V, PURPOSE_ENC_E0, PURPOSE_ENC_E1 = 6, 7, 8
 PURPOSE_SMUDGE = 9
+PURPOSE_PCKS_U, PURPOSE_PCKS_E0, PURPOSE_PCKS_E1 = 10, 11, 12
+PURPOSE_DB_MASK, PURPOSE_DB_E0, PURPOSE_DB_E1, PURPOSE_DB_CRP = 13, 14, 15, 16
 
 
 def mix64(z: int) -> int:
@@ -530,6 +532,65 @@ def decrypt_poly(ctx: Context, ks: KeySet, ct: Ciphertext, smudge_sigma: float =
     q = ctx.q[0]
     coef = np.where(coef > q // 2, coef - q, coef)  # q < 2^63 so int64 is safe
     return coef
+
+
+def dkeyswitch(ctx: Context, ks_from: KeySet, ks_to: KeySet, ct: Ciphertext, seed: int, index: int = 0) -> Ciphertext:
+    """DKeySwitch (Fig. 1 item 13), the collective public-key switch (reading
+    R20): party i draws u_i (ternary), e0_i, e1_i (Gaussian) and publishes
+    h0_i = s_i c1 + u_i b' + e0_i and h1_i = u_i a' + e1_i, with (b', a') the
+    target public key; the new ciphertext is (c0 + sum h0_i, sum h1_i).  It
+    decrypts under the target secret s' because b' + a' s' is small."""
+    prim = ctx.q[: ct.limbs]
+    h0 = ct.c[0].copy()
+    h1 = np.zeros_like(h0)
+    for i, sp in enumerate(ks_from.s_parts_ntt):
+        u = sample_ternary(Stream(seed, PURPOSE_PCKS_U, i, index), ctx.N)
+        e0 = sample_gaussian(Stream(seed, PURPOSE_PCKS_E0, i, index), ctx.N, ctx.sigma)
+        e1 = sample_gaussian(Stream(seed, PURPOSE_PCKS_E1, i, index), ctx.N, ctx.sigma)
+        un = ctx.ntt(ctx.signed_to_rows(u, prim), prim)
+        e0n = ctx.ntt(ctx.signed_to_rows(e0, prim), prim)
+        e1n = ctx.ntt(ctx.signed_to_rows(e1, prim), prim)
+        share0 = ctx.add(ctx.add(ctx.mul(sp[: ct.limbs], ct.c[1], prim), ctx.mul(un, ks_to.pk_b[: ct.limbs], prim), prim),
+                         e0n, prim)
+        share1 = ctx.add(ctx.mul(un, ks_to.pk_a[: ct.limbs], prim), e1n, prim)
+        h0 = ctx.add(h0, share0, prim)
+        h1 = ctx.add(h1, share1, prim)
+    return Ciphertext(np.stack([h0, h1]), ct.scale)
+
+
+def dbootstrap(ctx: Context, ks: KeySet, ct: Ciphertext, seed: int, counter: int = 0) -> Ciphertext:
+    """DBootstrap (Fig. 1 item 14), the collective refresh (reading R17):
+    1. party i masks its decryption share at q_0: c1 s_i + M_i + e0_i with M_i
+       uniform in [-bound, bound], bound = (floor(q_0/4) - 1) // n_parties;
+    2. v = centered(c0 + sum of the shares mod q_0) = Delta_ct m + e + sum M_i,
+       which stays below q_0/2, is rescaled: m' = round(v Delta / Delta_ct);
+    3. against a common reference polynomial a (uniform over Q, NTT form),
+       party i publishes -s_i a - round(M_i Delta / Delta_ct) + e1_i, and the
+       refreshed ciphertext is (m' + sum of those shares, a) at the top level
+       and scale Delta."""
+    N, q0, prim = ctx.N, ctx.q[0], ctx.q
+    n_p = len(ks.s_parts)
+    bound = (q0 // 4 - 1) // n_p
+    ratio = ctx.scale / ct.scale
+    q0l = [q0]
+    acc = ctx.intt(ct.c[0, :1], q0l)[0].astype(object)
+    w_parts = []
+    for i, sp in enumerate(ks.s_parts_ntt):
+        M = sample_uniform(Stream(seed, PURPOSE_DB_MASK, i, counter), 2 * bound + 1, N).astype(np.int64) - bound
+        e0 = sample_gaussian(Stream(seed, PURPOSE_DB_E0, i, counter), N, ctx.sigma)
+        share = ctx.intt(ctx.mul(ct.c[1, :1], sp[:1], q0l), q0l)[0].astype(object)
+        acc = (acc + share + (M + e0).astype(object)) % q0
+        e1 = sample_gaussian(Stream(seed, PURPOSE_DB_E1, i, counter), N, ctx.sigma)
+        w_parts.append(-round_half_away(M.astype(np.float64) * ratio).astype(np.int64) + e1)
+    v = np.array([int(x) - q0 if int(x) > q0 // 2 else int(x) for x in acc], dtype=np.int64)
+    m_new = round_half_away(v.astype(np.float64) * ratio).astype(np.int64)
+    st = Stream(seed, PURPOSE_DB_CRP, 0, counter)
+    a = np.stack([sample_uniform(st, t, N) for t in prim])
+    c0 = ctx.ntt(ctx.signed_to_rows(m_new, prim), prim)
+    for i, sp in enumerate(ks.s_parts_ntt):
+        w = ctx.ntt(ctx.signed_to_rows(w_parts[i], prim), prim)
+        c0 = ctx.add(c0, ctx.sub(w, ctx.mul(sp[: ctx.n_q], a, prim), prim), prim)
+    return Ciphertext(np.stack([c0, a]), float(ctx.scale))
 
 
 def decrypt(ctx: Context, ks: KeySet, ct: Ciphertext, n: int | None = None) -> np.ndarray:

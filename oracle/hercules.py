@@ -509,16 +509,11 @@ def g_depth(d: int) -> int:
     return max(lev.values()) + 1
 
 
-def refresh(ev: C.Evaluator, ct: C.Ciphertext, seed: int, counter: int, index: int = 0) -> C.Ciphertext:
-    """Host simulation of DBootstrap (Fig. 1 item 14, reading R17): collective
-    decryption to integer coefficients, rescaling of those integers to the
-    default scale, re-encryption at the top level."""
-    ctx = ev.ctx
-    poly = C.decrypt_poly(ctx, ev.ks, ct)
-    ratio = ctx.scale / ct.scale
-    m = C.round_half_away(poly.astype(np.float64) * ratio).astype(np.int64)
+def refresh(ev: C.Evaluator, ct: C.Ciphertext, seed: int, counter: int) -> C.Ciphertext:
+    """DBootstrap (Fig. 1 item 14) between compositions (reading R17): the
+    collective refresh protocol to the top level and the default scale."""
     ev._count("Refresh")
-    return C.encrypt_coeffs(ctx, ev.ks, m, ctx.scale, ctx.n_q, seed, tag=1 + counter, index=index)
+    return C.dbootstrap(ev.ctx, ev.ks, ct, seed, counter)
 
 
 def sign_approx(ev: C.Evaluator, x: C.Ciphertext, d: int, k: int, relu: bool = False,

@@ -705,6 +705,29 @@ hx_status hx_aggregate(hx_context *ctx, const hx_ct *const *grads, size_t n_part
     HX_END
 }
 
+hx_status hx_dkeyswitch(hx_context *ctx, const hx_keyset *from, const hx_keyset *to, const hx_ct *ct, uint64_t seed,
+                        hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(ctx && from && to && ct && out, "null argument");
+    *out = nullptr;
+    need(from->ctx == ctx && to->ctx == ctx && ct->ctx == ctx, "keys or ciphertext from another context");
+    *out = wrap(ctx, dkeyswitch(*ctx, *from, *to, ct->c, seed, S(stream)));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_dbootstrap(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, uint64_t seed, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(ctx && ks && ct && out, "null argument");
+    *out = nullptr;
+    need(ks->ctx == ctx && ct->ctx == ctx, "keys or ciphertext from another context");
+    *out = wrap(ctx, dbootstrap(*ctx, *ks, ct->c, {seed}, 0, S(stream)));
+    return HX_OK;
+    HX_END
+}
+
 int hx_counters(const hx_context *ctx, uint64_t *out, int cap)
 {
     if (!ctx) return HX_EINVAL;

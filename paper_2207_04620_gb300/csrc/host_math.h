@@ -23,7 +23,9 @@ uint64_t galois_for_step(int64_t k, int log_n);    // 5^(k mod N/2) mod 2N
 // (seed, purpose, a, b): state0 = seed ^ mix64(key + gamma), draw i returns
 // mix64(state0 + (i+1)*gamma), key = purpose<<56 | a<<32 | b.
 enum Purpose : uint64_t {
-    P_SK = 1, P_PK_A = 2, P_PK_E = 3, P_KEY_A = 4, P_KEY_E = 5, P_ENC_V = 6, P_ENC_E0 = 7, P_ENC_E1 = 8, P_SMUDGE = 9
+    P_SK = 1, P_PK_A = 2, P_PK_E = 3, P_KEY_A = 4, P_KEY_E = 5, P_ENC_V = 6, P_ENC_E0 = 7, P_ENC_E1 = 8, P_SMUDGE = 9,
+    P_PCKS_U = 10, P_PCKS_E0 = 11, P_PCKS_E1 = 12,                    // collective key switch
+    P_DB_MASK = 13, P_DB_E0 = 14, P_DB_E1 = 15, P_DB_CRP = 16          // collective refresh
 };
 uint64_t mix64(uint64_t z);
 struct Stream {

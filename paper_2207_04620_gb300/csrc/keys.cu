@@ -63,6 +63,83 @@ void gen_switch_key(hx_context &ctx, hx_keyset &ks, uint64_t key_id, const uint6
     }
 }
 
+// Fig. 1 item 13, every party's share for entry b at limb l, summed:
+//   out0 = c0 + sum_i (s_i c1 + u_i b' + e0_i),  out1 = sum_i (u_i a' + e1_i)
+// S: [n_parties][limbs][N]; R: [B][n_parties][3 (u, e0, e1)][limbs][N]; pk: [2][n_q][N]
+__global__ void k_pcks(View out, View ct, const uint64_t *__restrict__ S, const uint64_t *__restrict__ R,
+                       const uint64_t *__restrict__ pk, const PrimeConst *__restrict__ primes, int np, int limbs,
+                       int n_q, int n)
+{
+    const int l = blockIdx.y, bi = blockIdx.z;
+    const PrimeConst P = primes[l];
+    const uint64_t *c0 = ct.p + bi * ct.bstride + (size_t)l * n, *c1 = c0 + ct.cstride;
+    const uint64_t *pb = pk + (size_t)l * n, *pa = pk + ((size_t)n_q + l) * n;
+    const size_t poly = (size_t)limbs * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        uint64_t h0 = c0[j], h1 = 0;
+        const uint64_t x1 = c1[j], bb = pb[j], aa = pa[j];
+        for (int i = 0; i < np; i++) {
+            const uint64_t *r = R + ((size_t)bi * np + i) * 3 * poly + (size_t)l * n + j;
+            const uint64_t u = r[0], e0 = r[poly], e1 = r[2 * poly];
+            const uint64_t s0 = addmod(mulmod(S[i * poly + (size_t)l * n + j], x1, P), mulmod(u, bb, P), P.q);
+            h0 = addmod(h0, addmod(s0, e0, P.q), P.q);
+            h1 = addmod(h1, addmod(mulmod(u, aa, P), e1, P.q), P.q);
+        }
+        out.p[bi * out.bstride + (size_t)l * n + j] = h0;
+        out.p[bi * out.bstride + out.cstride + (size_t)l * n + j] = h1;
+    }
+}
+
+// Fig. 1 item 14, re-encryption side for entry b at limb l:
+//   out0 = W[b][0] + sum_i (W[b][1+i] - s_i a_b),  out1 = a_b
+// W: [B][1 + n_parties][n_q][N] (NTT of m' and of the parties' -M'_i + e1_i); A: [B][n_q][N];
+// S: [n_parties][n_q][N]
+__global__ void k_dboot_combine(View out, const uint64_t *__restrict__ W, const uint64_t *__restrict__ A,
+                                const uint64_t *__restrict__ S, const PrimeConst *__restrict__ primes, int np, int n_q,
+                                int n)
+{
+    const int l = blockIdx.y, bi = blockIdx.z;
+    const PrimeConst P = primes[l];
+    const size_t poly = (size_t)n_q * n;
+    const uint64_t *w = W + (size_t)bi * (np + 1) * poly + (size_t)l * n;
+    const uint64_t *a = A + (size_t)bi * poly + (size_t)l * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        uint64_t c = w[j];
+        const uint64_t aj = a[j];
+        for (int i = 0; i < np; i++)
+            c = addmod(c, submod(w[(size_t)(i + 1) * poly + j], mulmod(S[i * poly + (size_t)l * n + j], aj, P), P.q),
+                       P.q);
+        out.p[bi * out.bstride + (size_t)l * n + j] = c;
+        out.p[bi * out.bstride + out.cstride + (size_t)l * n + j] = aj;
+    }
+}
+
+int blocks_for(int n) { return (n + 255) / 256; }
+
+// the parties' ternary shares as NTT-form residues over primes 0..rows-1
+BufPtr party_shares_ntt(hx_context &ctx, const hx_keyset &ks, int rows, cudaStream_t s)
+{
+    std::vector<int64_t> flat;
+    for (auto &v : ks.s_parts) flat.insert(flat.end(), v.begin(), v.end());
+    BufPtr out = std::make_shared<DevBuf>((size_t)ks.n_parties * rows * ctx.N, s);
+    signed_polys_to_ntt(ctx, s, flat, ks.n_parties, rows, out->p);
+    return out;
+}
+
+// DDec shares at q_0 in coefficient form, host copy: [B][1 + n_parties][N] (c0, then c1*s_i)
+std::vector<uint64_t> ddec_share_polys(hx_context &ctx, const hx_keyset &ks, const Cts &c, cudaStream_t s)
+{
+    const int N = ctx.N, np = ks.n_parties, B = c.B;
+    Eval ev(ctx, s);
+    DevBuf sh((size_t)B * (np + 1) * N, s);
+    launch_ddec_shares(ev.lc(), sh.p, c.view(N), ks.s_parts0->p, np, B);
+    ev.ntt_inplace(sh.p, (size_t)N, B * (np + 1), {0}, {0}, true);
+    std::vector<uint64_t> host((size_t)B * (np + 1) * N);
+    HX_CUDA(cudaMemcpyAsync(host.data(), sh.p, sizeof(uint64_t) * host.size(), cudaMemcpyDeviceToHost, s));
+    HX_CUDA(cudaStreamSynchronize(s));
+    return host;
+}
+
 } // namespace
 
 void keygen(hx_context &ctx, hx_keyset &ks, int n_parties, uint64_t seed, cudaStream_t s)
@@ -149,13 +226,7 @@ std::vector<int64_t> decrypt_coeffs(hx_context &ctx, const hx_keyset &ks, const 
 {
     HX_CHECK(c.comps == 2, HX_EINVAL, "decryption needs a 2-component ciphertext");
     const int N = ctx.N, np = ks.n_parties, B = c.B;
-    Eval ev(ctx, s);
-    DevBuf sh((size_t)B * (np + 1) * N, s);
-    launch_ddec_shares(ev.lc(), sh.p, c.view(N), ks.s_parts0->p, np, B);
-    ev.ntt_inplace(sh.p, (size_t)N, B * (np + 1), {0}, {0}, true);
-    std::vector<uint64_t> host((size_t)B * (np + 1) * N);
-    HX_CUDA(cudaMemcpyAsync(host.data(), sh.p, sizeof(uint64_t) * host.size(), cudaMemcpyDeviceToHost, s));
-    HX_CUDA(cudaStreamSynchronize(s));
+    const std::vector<uint64_t> host = ddec_share_polys(ctx, ks, c, s);
     const uint64_t q = ctx.primes[0];
     std::vector<int64_t> out((size_t)B * N);
     for (int b = 0; b < B; b++)
@@ -167,6 +238,106 @@ std::vector<int64_t> decrypt_coeffs(hx_context &ctx, const hx_keyset &ks, const 
             }
             out[(size_t)b * N + i] = acc > q / 2 ? (int64_t)acc - (int64_t)q : (int64_t)acc;
         }
+    return out;
+}
+
+// Fig. 1 item 13: collective public-key switch of every entry of ct to the
+// public key of `to`.  Party i draws u_i (ternary), e0_i, e1_i (Gaussian) from
+// streams (seed, purpose, i, b) and contributes (s_i c1 + u_i b' + e0_i,
+// u_i a' + e1_i); the sums are added to (c0, 0).
+Cts dkeyswitch(hx_context &ctx, const hx_keyset &from, const hx_keyset &to, const Cts &ct, uint64_t seed,
+               cudaStream_t s)
+{
+    HX_CHECK(ct.comps == 2, HX_EINVAL, "key switching needs a 2-component ciphertext");
+    const int N = ctx.N, np = from.n_parties, L = ct.limbs, B = ct.B;
+    Eval ev(ctx, s);
+    BufPtr S = party_shares_ntt(ctx, from, L, s);
+    std::vector<int64_t> host((size_t)B * np * 3 * N);
+    for (int b = 0; b < B; b++)
+        for (int i = 0; i < np; i++) {
+            int64_t *r = host.data() + ((size_t)b * np + i) * 3 * N;
+            Stream su(seed, P_PCKS_U, i, b), s0(seed, P_PCKS_E0, i, b), s1(seed, P_PCKS_E1, i, b);
+            sample_ternary(su, r, N);
+            for (int k = 0; k < N; k++) r[N + k] = ctx.cdt->draw(s0);
+            for (int k = 0; k < N; k++) r[2 * N + k] = ctx.cdt->draw(s1);
+        }
+    DevBuf R((size_t)B * np * 3 * L * N, s);
+    signed_polys_to_ntt(ctx, s, host, B * np * 3, L, R.p);
+    Cts out = ev.alloc(B, 2, L);
+    out.scale = ct.scale;
+    k_pcks<<<dim3(blocks_for(N), L, B), 256, 0, s>>>(out.view(N), ct.view(N), S->p, R.p, to.pk->p, ctx.t.primes, np, L,
+                                                    ctx.n_q, N);
+    HX_CUDA(cudaGetLastError());
+    ctx.counters[C_LAUNCH] += 1;
+    HX_CUDA(cudaStreamSynchronize(s));  // host staging buffers go out of scope
+    return out;
+}
+
+// Fig. 1 item 14: collective refresh of every entry b (seed seeds[b], refresh
+// index `counter`).  Party i adds a uniform mask M_i in [-bound, bound] (bound =
+// (floor(q_0/4) - 1) / n_parties) and Gaussian e0_i to its decryption share at
+// q_0, so the combined v = c0 + sum_i (c1 s_i + M_i + e0_i) mod q_0 is the
+// masked plaintext Delta_ct m + e + sum M_i (|v| < q_0/2); m' = round(v *
+// Delta/Delta_ct).  With a common reference polynomial a (uniform over Q, in
+// NTT form), party i's re-encryption share is -s_i a - M'_i + e1_i, M'_i =
+// round(M_i * Delta/Delta_ct); the output (m' + sum_i shares, a) is at the top
+// level and scale Delta.
+Cts dbootstrap(hx_context &ctx, const hx_keyset &ks, const Cts &ct, const std::vector<uint64_t> &seeds, int counter,
+               cudaStream_t s)
+{
+    HX_CHECK(ct.comps == 2, HX_EINVAL, "refresh needs a 2-component ciphertext");
+    HX_CHECK((int)seeds.size() == ct.B, HX_EINVAL, "one refresh seed per batch entry");
+    const int N = ctx.N, np = ks.n_parties, B = ct.B, nq = ctx.n_q;
+    const uint64_t q0 = ctx.primes[0];
+    const uint64_t bound = (q0 / 4 - 1) / (uint64_t)np;
+    const double ratio = ctx.scale / ct.scale;
+    const std::vector<uint64_t> sh = ddec_share_polys(ctx, ks, ct, s);
+    std::vector<int64_t> W((size_t)B * (np + 1) * N);
+    std::vector<uint64_t> A((size_t)B * nq * N);
+    std::vector<uint64_t> mask(N);
+    std::vector<int64_t> e(N);
+    std::vector<uint64_t> v(N);
+    for (int b = 0; b < B; b++) {
+        const uint64_t *shb = sh.data() + (size_t)b * (np + 1) * N;
+        for (int k = 0; k < N; k++) v[k] = shb[k];  // c0
+        int64_t *Wb = W.data() + (size_t)b * (np + 1) * N;
+        for (int i = 0; i < np; i++) {
+            Stream sm(seeds[b], P_DB_MASK, i, counter), s0(seeds[b], P_DB_E0, i, counter),
+                s1(seeds[b], P_DB_E1, i, counter);
+            sample_uniform(sm, 2 * bound + 1, mask.data(), N);
+            for (int k = 0; k < N; k++) {
+                const int64_t M = (int64_t)mask[k] - (int64_t)bound;
+                const int64_t e0 = ctx.cdt->draw(s0);
+                // party i's masked decryption share, added mod q_0
+                uint64_t t = shb[(size_t)(i + 1) * N + k];
+                const int64_t add = M + e0;
+                t = add >= 0 ? (t + (uint64_t)add) % q0 : (t + q0 - ((uint64_t)(-add)) % q0) % q0;
+                v[k] = (v[k] + t) % q0;
+                mask[k] = (uint64_t)M;  // keep the signed mask for the re-encryption share
+            }
+            int64_t *Wi = Wb + (size_t)(i + 1) * N;
+            for (int k = 0; k < N; k++)
+                Wi[k] = -(int64_t)round_half_away((double)(int64_t)mask[k] * ratio) + ctx.cdt->draw(s1);
+        }
+        for (int k = 0; k < N; k++) {
+            const int64_t c = v[k] > q0 / 2 ? (int64_t)v[k] - (int64_t)q0 : (int64_t)v[k];
+            Wb[k] = (int64_t)round_half_away((double)c * ratio);
+        }
+        Stream sa(seeds[b], P_DB_CRP, 0, counter);
+        for (int r = 0; r < nq; r++) sample_uniform(sa, ctx.primes[r], A.data() + ((size_t)b * nq + r) * N, N);
+    }
+    Eval ev(ctx, s);
+    DevBuf Wd((size_t)B * (np + 1) * nq * N, s), Ad((size_t)B * nq * N, s);
+    signed_polys_to_ntt(ctx, s, W, B * (np + 1), nq, Wd.p);
+    HX_CUDA(cudaMemcpyAsync(Ad.p, A.data(), sizeof(uint64_t) * A.size(), cudaMemcpyHostToDevice, s));
+    BufPtr S = party_shares_ntt(ctx, ks, nq, s);
+    Cts out = ev.alloc(B, 2, nq);
+    out.scale = ctx.scale;
+    k_dboot_combine<<<dim3(blocks_for(N), nq, B), 256, 0, s>>>(out.view(N), Wd.p, Ad.p, S->p, ctx.t.primes, np, nq, N);
+    HX_CUDA(cudaGetLastError());
+    ctx.counters[C_LAUNCH] += 1;
+    ctx.counters[C_REFRESH] += B;
+    HX_CUDA(cudaStreamSynchronize(s));  // host staging buffers go out of scope
     return out;
 }
 

@@ -178,6 +178,10 @@ Cts encrypt_coeffs(hx_context &ctx, const hx_keyset &ks, const int64_t *m, doubl
                    uint32_t tag, uint32_t index, cudaStream_t s);
 // centered coefficients of c0 + c1 s mod q_0 for every batch entry: [B][N]
 std::vector<int64_t> decrypt_coeffs(hx_context &ctx, const hx_keyset &ks, const Cts &c, cudaStream_t s);
+Cts dkeyswitch(hx_context &ctx, const hx_keyset &from, const hx_keyset &to, const Cts &ct, uint64_t seed,
+               cudaStream_t s);
+Cts dbootstrap(hx_context &ctx, const hx_keyset &ks, const Cts &ct, const std::vector<uint64_t> &seeds, int counter,
+               cudaStream_t s);
 
 // ---- schedules (schedules.cu) -------------------------------------------------
 hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s);

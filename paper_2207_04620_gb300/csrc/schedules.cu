@@ -465,27 +465,6 @@ int g_depth(int d)
     return mx + 1;
 }
 
-// host simulation of DBootstrap: collective decryption, integer rescaling of
-// the plaintext coefficients to the default scale, re-encryption at the top
-Cts refresh(hx_context &ctx, const hx_keyset &ks, const Cts &ct, const std::vector<uint64_t> &seeds, int counter,
-            cudaStream_t s)
-{
-    std::vector<int64_t> poly = decrypt_coeffs(ctx, ks, ct, s);
-    const double ratio = ctx.scale / ct.scale;
-    std::vector<int64_t> m(ctx.N);
-    Eval ev(ctx, s);
-    Cts out = ev.alloc(ct.B, 2, ctx.n_q);
-    out.scale = ctx.scale;
-    for (int b = 0; b < ct.B; b++) {
-        for (int i = 0; i < ctx.N; i++) m[i] = (int64_t)round_half_away((double)poly[(size_t)b * ctx.N + i] * ratio);
-        Cts one = encrypt_coeffs(ctx, ks, m.data(), ctx.scale, ctx.n_q, seeds[b], 1 + counter, 0, s);
-        HX_CUDA(cudaMemcpyAsync(out.d + (size_t)b * out.bstride(ctx.N), one.d, sizeof(uint64_t) * one.bstride(ctx.N),
-                                cudaMemcpyDeviceToDevice, s));
-    }
-    ctx.counters[C_REFRESH] += ct.B;
-    return out;
-}
-
 } // namespace
 
 Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k, bool relu, bool allow_refresh,
@@ -503,7 +482,7 @@ Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k,
         if (m.limbs - 1 < need) {
             HX_CHECK(allow_refresh, HX_ELEVEL, "levels exhausted");
             HX_CHECK(ctx.n_q - 1 >= need, HX_ELEVEL, "chain too short for one composition");
-            m = refresh(ctx, ks, m, refresh_seeds, refreshes++, s);
+            m = dbootstrap(ctx, ks, m, refresh_seeds, refreshes++, s);
         }
         m = eval_g(ev, ks, m, d);
     }

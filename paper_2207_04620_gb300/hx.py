@@ -95,6 +95,8 @@ _SIGS = {
                                 c_u64, PP, PP, PP, c_vp]),
     "hx_dense_rotation_steps": (c_int, [c_vp, c_int, P_i32, c_int]),
     "hx_aggregate": (c_int, [c_vp, PP, c_size_t, PP, c_size_t, c_double, PP, c_vp]),
+    "hx_dkeyswitch": (c_int, [c_vp, c_vp, c_vp, c_vp, c_u64, PP, c_vp]),
+    "hx_dbootstrap": (c_int, [c_vp, c_vp, c_vp, c_u64, PP, c_vp]),
     "hx_server_create": (c_int, [c_size_t, c_int, c_int, PP]),
     "hx_server_register_keys": (c_int, [c_vp, c_vp]),
     "hx_server_submit_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_int, P_u64]),
@@ -485,6 +487,16 @@ def hx_dense_rotation_steps(ctx: int, h: int) -> list:
     buf = np.zeros(4096, dtype=np.int32)
     n = _chk(lib().hx_dense_rotation_steps(ctx, h, buf.ctypes.data_as(P_i32), buf.size))
     return [int(x) for x in buf[:n]]
+
+
+# ---- collective protocols (Fig. 1 items 13-14) ---------------------------------------------
+
+def hx_dkeyswitch(ctx, ks_from, ks_to, ct, seed, stream=None) -> int:
+    return _op("hx_dkeyswitch", ctx, ks_from, ks_to, ct, seed, stream=stream)
+
+
+def hx_dbootstrap(ctx, ks, ct, seed, stream=None) -> int:
+    return _op("hx_dbootstrap", ctx, ks, ct, seed, stream=stream)
 
 
 # ---- aggregation (Alg. 6) -----------------------------------------------------------------

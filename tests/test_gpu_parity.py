@@ -402,6 +402,38 @@ def test_aggregate_bit_exact(alg3, n_parties):
         hx.hx_ct_destroy(outs[m])
 
 
+def test_dkeyswitch_bit_exact(alg3):
+    """DKeySwitch (Fig. 1 item 13) from the 3-party key to a 1-party server key:
+    residues equal the oracle's protocol, and the result decrypts under the
+    server key."""
+    pr = alg3
+    server = hx.hx_keygen(pr.ctx, 1, 99, [])
+    oserver = C.keygen(pr.octx, 1, 99, relin=False)
+    try:
+        z = np.random.default_rng(12).uniform(-1, 1, pr.N // 2)
+        ct = pr.encrypt(z, 77, limbs=3)
+        out = hx.hx_dkeyswitch(pr.ctx, pr.ks, server, pr.to_lib(ct), 21)
+        assert pr.same(out, C.dkeyswitch(pr.octx, pr.oks, oserver, ct, 21))
+        assert np.abs(hx.hx_decrypt(pr.ctx, server, out) - z).max() < 2 ** -25
+        hx.hx_ct_destroy(out)
+    finally:
+        hx.hx_keyset_destroy(server)
+
+
+def test_dbootstrap_bit_exact(alg3):
+    """DBootstrap (Fig. 1 item 14) of a one-limb ciphertext at scale 2^40:
+    residues equal the oracle's protocol (masked shares, common reference
+    polynomial), the output is at the top level and decrypts to the input."""
+    pr = alg3
+    z = np.random.default_rng(13).uniform(-1, 1, pr.N // 2)
+    ct = C.encrypt(pr.octx, pr.oks, z, 78, limbs=1, scale=2.0 ** 40)
+    out = hx.hx_dbootstrap(pr.ctx, pr.ks, pr.to_lib(ct), 31)
+    want = C.dbootstrap(pr.octx, pr.oks, ct, 31, 0)
+    assert want.limbs == pr.octx.n_q and pr.same(out, want)
+    assert np.abs(hx.hx_decrypt(pr.ctx, pr.ks, out) - z).max() < 2 ** -20
+    hx.hx_ct_destroy(out)
+
+
 @pytest.mark.slow
 def test_matmul_config1_bit_exact():
     """Config 1 shape: N=2^14, 8 limbs, h=64 (beta=2), one ciphertext pair."""

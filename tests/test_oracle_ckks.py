@@ -144,3 +144,35 @@ def test_keyswitch_decrypts_to_product_with_target_key(small):
         if r:  # one small integer polynomial, seen identically modulo every prime
             assert err == err0
         err0 = err
+
+
+def test_dkeyswitch_moves_ciphertext_to_target_key(small):
+    """DKeySwitch (Fig. 1 item 13): after the collective switch the ciphertext
+    decrypts under the target (server) key to the same slots, within the
+    added noise u*e' + e0 + e1*s' (summed over 3 parties), and no longer under
+    the collective key; level and scale are kept."""
+    ctx, ks = small
+    server = C.keygen(ctx, 1, 99, relin=False)
+    z = np.random.default_rng(5).uniform(-1, 1, ctx.S)
+    ct = C.encrypt(ctx, ks, z, seed=8, limbs=3)
+    out = C.dkeyswitch(ctx, ks, server, ct, seed=21)
+    assert out.limbs == 3 and out.scale == ct.scale
+    bound = 3 * 6 * ctx.sigma * (2 + 2 * math.sqrt(ctx.N)) * math.sqrt(ctx.N) / ctx.scale
+    assert np.abs(C.decrypt(ctx, server, out) - z).max() < bound + 2 ** -25
+    assert np.abs(C.decrypt(ctx, ks, out) - z).max() > 1.0
+
+
+def test_dbootstrap_refreshes_to_top_level(small):
+    """DBootstrap (Fig. 1 item 14): a ciphertext at one limb with scale 2^38
+    comes back at the top level with the default scale and the same slots
+    (the parties' masks, up to 2^57, cancel: an uncancelled mask would show
+    as an error near 2^17); refreshes with another seed or counter differ."""
+    ctx, ks = small
+    z = np.random.default_rng(6).uniform(-1, 1, ctx.S)
+    ct = C.encrypt(ctx, ks, z, seed=9, limbs=1, scale=2.0 ** 38)
+    out = C.dbootstrap(ctx, ks, ct, seed=31, counter=0)
+    assert out.limbs == ctx.n_q and out.scale == ctx.scale
+    assert np.abs(C.decrypt(ctx, ks, out) - z).max() < 2 ** -20
+    other = C.dbootstrap(ctx, ks, ct, seed=31, counter=1)
+    assert not np.array_equal(other.c, out.c)
+    assert np.abs(C.decrypt(ctx, ks, other) - z).max() < 2 ** -20
