@@ -183,9 +183,11 @@ def plan_masks(h: int, limbs: int):
     return out
 
 
-def matmul_rotation_steps(h: int, beta: int, limbs: int) -> list:
+def matmul_rotation_steps(h: int, beta: int, limbs: int, t: int | None = None) -> list:
     """Every rotation amount one product uses, reduced mod S = beta*h^2
-    (rotations are cyclic on the slots), sorted, without 0."""
+    (rotations are cyclic on the slots), sorted, without 0; with t < h those of
+    the rectangular product (k < t, plus the row-block folds)."""
+    t = h if t is None else t
     variant = matmul_variant(limbs)
     b = baby_steps(h)
     s = set()
@@ -196,13 +198,17 @@ def matmul_rotation_steps(h: int, beta: int, limbs: int) -> list:
         for l in range(h):
             s.add(beta * h * (l % b))
             s.add(beta * h * b * (l // b))
-        for k in range(1, h):
+        for k in range(1, t):
             s.update({beta * k, beta * (k - h), beta * h * k})
     else:
         for l in range(1, h):
             s.add(beta * h * l)
-        for k in range(1, h):
+        for k in range(1, t):
             s.update({beta * k, beta * (k - h), beta * h * k})
+    e = t
+    while e < h:
+        s.add(beta * h * e)
+        e *= 2
     n_slots = beta * h * h
     return sorted({k % n_slots for k in s} - {0})
 
@@ -262,17 +268,38 @@ def lintrans_bsgs(ev: C.Evaluator, ct: C.Ciphertext, ls, stride: int, masks: Mas
     return ev.rotate_sum(items)
 
 
-def matmul(ev: C.Evaluator, A: C.Ciphertext, B: C.Ciphertext, h: int, masks: MaskProvider | None = None):
-    """HE-MatMult of beta = S/h^2 packed pairs (Alg. 3 / App. E)."""
+def matmul(ev: C.Evaluator, A: C.Ciphertext, B: C.Ciphertext, h: int, masks: MaskProvider | None = None,
+           t: int | None = None):
+    """HE-MatMult of beta = S/h^2 packed pairs (Alg. 3 / App. E).  With t < h
+    only the terms k < t of Step 2/3 are formed (Alg. "41", lines 3-10)."""
     if A.limbs != B.limbs:
         raise ValueError("A and B must be at the same level")
+    t = h if t is None else t
     masks = masks or MaskProvider(ev.ctx, h, A.limbs)
     if matmul_variant(A.limbs) == "alg3":
-        return _matmul_alg3(ev, A, B, h, masks)
-    return _matmul_depth2(ev, A, B, h, masks)
+        return _matmul_alg3(ev, A, B, h, masks, t)
+    return _matmul_depth2(ev, A, B, h, masks, t)
 
 
-def _matmul_alg3(ev, A, B, h, masks):
+def rmatmul(ev: C.Evaluator, At: C.Ciphertext, B: C.Ciphertext, h: int, t: int, masks: MaskProvider | None = None):
+    """HE-RMatMult (App. D, Alg. "41"): At packs A~ = (A; ...; A), h/t vertical
+    copies of a t x h matrix A (t a power of two dividing h).  The square
+    schedule with its k-sum cut to k < t leaves, in row block j, the terms
+    k = j t + i of A.B; log2(h/t) rotate-and-add steps by t*h*2^e rows fold
+    the blocks, so every block holds A.B (h/t copies, as the input)."""
+    if t < 1 or h % t or t & (t - 1):
+        raise ValueError("t must be a power of two dividing h")
+    out = matmul(ev, At, B, h, masks, t)
+    beta = ev.ctx.S // (h * h)
+    e = t
+    while e < h:
+        out = ev.add(out, ev.rotate(out, beta * h * e))
+        e *= 2
+    return out
+
+
+def _matmul_alg3(ev, A, B, h, masks, t=None):
+    t = h if t is None else t
     beta = masks.beta
     # Step 1-1 / 1-2: A0 = U^mu a, B0 = U^zeta b
     A0 = ev.rescale(lintrans_bsgs(ev, A, range(-h + 1, h), 1, masks, "mu"))
@@ -284,21 +311,22 @@ def _matmul_alg3(ev, A, B, h, masks):
     # stays at the same level; A^(0) = q_t * A0.
     qt = ev.ctx.q[A0.limbs - 1]
     DA = ev.hoist(A0)
-    Bk = [B0] + ev.rotate_hoisted(B0, [beta * h * k for k in range(1, h)])
+    Bk = [B0] + ev.rotate_hoisted(B0, [beta * h * k for k in range(1, t)])
     # Step 3: sum_k A^(k) (x) B^(k), one relinearisation, then the two rescales
     acc = ev.tensor(ev.mul_int(A0, qt, new_scale=A0.scale * float(qt)), Bk[0])
-    for k in range(1, h):
+    for k in range(1, t):
         v_ext, sc = masks.plaintext("v", k, extended=True)
         Ak = ev.hoisted_mux(A0, DA, beta * k, beta * (k - h), v_ext, sc, qt)
         acc = ev.add(acc, ev.tensor(Ak, Bk[k]))
     return ev.rescale(ev.rescale(ev.relinearize(acc)))
 
 
-def _matmul_depth2(ev, A, B, h, masks):
+def _matmul_depth2(ev, A, B, h, masks, t=None):
     """Reading R9: with T_l = u^zeta_{hl} . R(b, hl) and S_m = sum_{l<m} T_l,
     v_k . R(B0, hk) = R(S_{h-k}, hk) and v_{k-h} . R(B0, hk) = R(B0 - S_{h-k}, hk),
     so A.B = A0.B0 + sum_{k>=1} R(A0,k).R(S_{h-k},hk) + R(A0,k-h).R(B0-S_{h-k},hk)
     needs one level for the masks and one for the ct x ct products."""
+    t = h if t is None else t
     beta = masks.beta
     A0 = ev.rescale(lintrans_bsgs(ev, A, range(-h + 1, h), 1, masks, "mu"))
     Rb = [B] + ev.rotate_hoisted(B, [beta * h * l for l in range(1, h)])
@@ -311,13 +339,13 @@ def _matmul_depth2(ev, A, B, h, masks):
         prefix.append(ev.add(prefix[-1], T[l]))
     Bfull = prefix[h]
     B0 = ev.rescale(Bfull)
-    RA = ev.rotate_hoisted(A0, [beta * k for k in range(1, h)] + [beta * (k - h) for k in range(1, h)])
+    RA = ev.rotate_hoisted(A0, [beta * k for k in range(1, t)] + [beta * (k - h) for k in range(1, t)])
     acc = ev.tensor(A0, B0)
-    for k in range(1, h):
+    for k in range(1, t):
         X = ev.rescale(prefix[h - k])
         Y = ev.rescale(ev.sub(Bfull, prefix[h - k]))
         acc = ev.add(acc, ev.tensor(RA[k - 1], ev.rotate(X, beta * h * k)))
-        acc = ev.add(acc, ev.tensor(RA[h - 1 + k - 1], ev.rotate(Y, beta * h * k)))
+        acc = ev.add(acc, ev.tensor(RA[t - 1 + k - 1], ev.rotate(Y, beta * h * k)))
     return ev.rescale(ev.relinearize(acc))
 
 
@@ -326,8 +354,10 @@ def _matmul_depth2(ev, A, B, h, masks):
 # ----------------------------------------------------------------------------
 
 
-def slot_matmul(a: np.ndarray, b: np.ndarray, h: int, beta: int = 1, variant: str = "alg3") -> np.ndarray:
-    """Runs the masks and rotations of `matmul` on plain slot vectors."""
+def slot_matmul(a: np.ndarray, b: np.ndarray, h: int, beta: int = 1, variant: str = "alg3",
+                t: int | None = None) -> np.ndarray:
+    """Runs the masks and rotations of `matmul` on plain slot vectors (terms k < t)."""
+    t = h if t is None else t
     n = beta * h * h
     Rb_ = lambda v, k: np.roll(v, -(beta * k) % n)
     bb = baby_steps(h)
@@ -341,7 +371,7 @@ def slot_matmul(a: np.ndarray, b: np.ndarray, h: int, beta: int = 1, variant: st
             i, j = l // bb, l % bb
             B0 += Rb_(expand(R(diag_zeta(h, l), -h * bb * i), beta) * Rb_(b, h * j), h * bb * i)
         out = A0 * B0
-        for k in range(1, h):
+        for k in range(1, t):
             v = expand(diag_v(h, k), beta)
             Ak = v * Rb_(A0, k) + (1 - v) * Rb_(A0, k - h)
             out += Ak * Rb_(B0, h * k)
@@ -349,8 +379,19 @@ def slot_matmul(a: np.ndarray, b: np.ndarray, h: int, beta: int = 1, variant: st
     T = [expand(diag_zeta(h, l), beta) * Rb_(b, h * l) for l in range(h)]
     Sm = np.cumsum(np.vstack([np.zeros(n)] + T), axis=0)
     out = A0 * Sm[h]
-    for k in range(1, h):
+    for k in range(1, t):
         out += Rb_(A0, k) * Rb_(Sm[h - k], h * k) + Rb_(A0, k - h) * Rb_(Sm[h] - Sm[h - k], h * k)
+    return out
+
+
+def slot_rmatmul(a: np.ndarray, b: np.ndarray, h: int, t: int, beta: int = 1, variant: str = "alg3") -> np.ndarray:
+    """`rmatmul` on plain slot vectors: the cut k-sum, then the row-block folds."""
+    n = beta * h * h
+    out = slot_matmul(a, b, h, beta, variant, t)
+    e = t
+    while e < h:
+        out = out + np.roll(out, -(beta * h * e) % n)
+        e *= 2
     return out
 
 

@@ -360,3 +360,67 @@ def test_aggregate_oracle():
         assert out[m].limbs == wc[m].limbs - 1 and out[m].scale == wc[m].scale
         want = w[m] - c * sum(g[i][m] for i in range(n_parties))
         assert np.abs(C.decrypt(ctx, ks, out[m]) - want).max() < 2 ** -22
+
+
+@pytest.mark.parametrize("h,t", [(4, 1), (4, 2), (8, 2), (8, 4), (16, 4), (16, 8), (32, 8)])
+@pytest.mark.parametrize("variant", ["alg3", "depth2"])
+def test_slot_rectangular_matmul(h, t, variant):
+    """App. D: with A~ = (A; ...; A) (h/t copies of a t x h matrix A), the cut
+    k-sum plus the row-block folds leaves h/t copies of A.B (t x h) in every
+    packed matrix; also a direct check of the key lemma's consequence: row
+    block j of sum_{i<t} phi^i(mu(A~)) . pi^i(zeta(B)) is the k = j t + i part."""
+    beta = 2
+    rng = np.random.default_rng(100 * h + t)
+    As = [rng.uniform(-1, 1, (t, h)) for _ in range(beta)]
+    Bs = [rng.uniform(-1, 1, (h, h)) for _ in range(beta)]
+    At = [np.vstack([A] * (h // t)) for A in As]
+    out = H.unpack(H.slot_rmatmul(H.pack(At, h, beta), H.pack(Bs, h, beta), h, t, beta, variant), h, beta)
+    for o, A, B in zip(out, As, Bs):
+        assert np.abs(o - np.vstack([A @ B] * (h // t))).max() < 1e-12
+    A, B = As[0], Bs[0]
+    part = sum(H.phi(H.mu(At[0]), i) * H.pi_(H.zeta(B), i) for i in range(t))
+    for j in range(h // t):
+        want = sum((H.phi(H.mu(np.vstack([A] * (h // t))), j * t + i) * H.pi_(H.zeta(B), j * t + i))[:t]
+                   for i in range(t))
+        assert np.allclose(part[j * t:(j + 1) * t], want)
+
+
+def test_rectangular_operation_counts_h64():
+    """App. D Table (Alg. "41"): Step 2 takes 3(t-1) rotations and t-1 masks,
+    Step 3 t ciphertext products, Step 4 log2(h/t) rotations; Step 1 is the
+    square product's."""
+    h, t = 64, 8
+    ctx = C.Context(14, [60] + [45] * 7, [60, 60], 45)
+    masks = _DryMasks(ctx, h, 8)
+    ev = DryEvaluator(ctx)
+    x = _DryCt(8, ctx.scale)
+    H.matmul(ev, x, x, h, masks)
+    sq = dict(ev.counts)
+    ev.counts = {}
+    H.rmatmul(ev, x, x, h, t, masks)
+    rc = dict(ev.counts)
+    step1_rot = sq["Rot"] - 3 * (h - 1)
+    assert rc["Rot"] == step1_rot + 3 * (t - 1) + int(math.log2(h // t))
+    assert rc["Mul_ct"] == t
+    assert rc["Mul_pt"] == sq["Mul_pt"] - (h - t)
+    beta = masks.beta
+    steps = H.matmul_rotation_steps(h, beta, 8, t)
+    assert set(steps) < set(H.matmul_rotation_steps(h, beta, 8)) | {beta * h * e for e in (8, 16, 32)}
+    assert {beta * h * e for e in (8, 16, 32)} <= set(steps)
+
+
+@pytest.mark.parametrize("limbs", [3, 5])
+def test_encrypted_rectangular_matmul_oracle(limbs):
+    """HE-RMatMult on ciphertexts decrypts to h/t copies of A.B for every packed pair."""
+    ctx = C.Context(10, [60] + [40] * (limbs - 1), [60], 40)
+    h, t = 8, 2
+    beta = ctx.S // (h * h)
+    ks = C.keygen(ctx, 2, 6, rot_steps=H.matmul_rotation_steps(h, beta, limbs, t))
+    rng = np.random.default_rng(7 + limbs)
+    As = [rng.uniform(-1, 1, (t, h)) for _ in range(beta)]
+    Bs = [rng.uniform(-1, 1, (h, h)) for _ in range(beta)]
+    At = C.encrypt(ctx, ks, H.pack([np.vstack([A] * (h // t)) for A in As], h, beta), 13)
+    B = C.encrypt(ctx, ks, H.pack(Bs, h, beta), 14)
+    out = H.rmatmul(C.Evaluator(ctx, ks), At, B, h, t)
+    got = H.unpack(C.decrypt(ctx, ks, out), h, beta)
+    assert max(np.abs(g - np.vstack([a @ b] * (h // t))).max() for g, a, b in zip(got, As, Bs)) < 2 ** -18
