@@ -720,6 +720,75 @@ def run_micro(args):
     hx.hx_context_destroy(ctx)
 
 
+def run_rmatmul(args):
+    """Rectangular products (App. D, Alg. "41") at the config-1 ring: 16 ciphertext pairs x beta=2,
+    each a (t x 64) . (64 x 64) product with A packed as 64/t vertical copies; CKKS N=2^14,
+    Q = 60 + 7x45 bit, P = 2x60 bit; L2 flushed between steps.  The square product of the same
+    batch is timed beside it."""
+    import torch
+
+    from paper_2207_04620_gb300 import hx, workloads
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    t, pairs = args.t, PAIRS
+    ctx = hx.hx_context_create(LOG_N, Q_BITS, P_BITS, LOG2_SCALE)
+    hx.hx_autotune(ctx)
+    limbs = len(Q_BITS)
+    ks = hx.hx_keygen(ctx, 2, 31, sorted(set(hx.hx_rmatmul_rotation_steps(ctx, H, t, limbs))
+                                         | set(hx.hx_matmul_rotation_steps(ctx, H, limbs))))
+    plan = hx.hx_matmul_plan_create(ctx, H, limbs)
+    rng = np.random.default_rng(5)
+    As = [[rng.uniform(-1, 1, (t, H)) for _ in range(BETA)] for _ in range(pairs)]
+    Bs = [workloads.matrices(300 + i, BETA, H) for i in range(pairs)]
+    At = [hx.hx_encrypt(ctx, ks, workloads.pack([np.vstack([a] * (H // t)) for a in As[i]], H, BETA), 0, 10 + i)
+          for i in range(pairs)]
+    Bc = [hx.hx_encrypt(ctx, ks, workloads.pack(Bs[i], H, BETA), 0, 50 + i) for i in range(pairs)]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            for o in fn():
+                hx.hx_ct_destroy(o)
+        ts, outs = [], None
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            if len(ts) < args.steps:
+                for o in outs:
+                    hx.hx_ct_destroy(o)
+        return sum(ts) / len(ts), outs
+
+    rect_ms, outs = timed(lambda: hx.hx_rmatmul_batch(ctx, ks, plan, At, Bc, H, t, stream=stream))
+    got = workloads.unpack(hx.hx_decrypt(ctx, ks, outs[0]), H, BETA)
+    err = float(max(np.abs(g - np.vstack([a @ b] * (H // t))).max() for g, a, b in zip(got, As[0], Bs[0])))
+    for o in outs:
+        hx.hx_ct_destroy(o)
+    sq_ms, outs = timed(lambda: hx.hx_matmul_batch(ctx, ks, plan, At, Bc, H, stream=stream))
+    for o in outs:
+        hx.hx_ct_destroy(o)
+    n = pairs * BETA
+    line = {"metric": "encrypted (%dx64).(64x64) rectangular products/s (HE-RMatMult, CKKS N=2^14)" % t,
+            "value": round(n / (rect_ms / 1e3), 2), "unit": "product/s", "ms_per_step": round(rect_ms, 3),
+            "steps": args.steps, "warmup": args.warmup, "n_gpus": 1, "higher_is_better": True, "dtype": "u64",
+            "data": "synthetic",
+            "config": {"workload": "32 rectangular products per step (16 ciphertext pairs x beta=2), t=%d, h=64" % t,
+                       "l2": "flushed between steps"},
+            "square_same_batch": {"value": round(n / (sq_ms / 1e3), 2), "unit": "matmul/s", "ms_per_step": round(sq_ms, 3)},
+            "max_abs_err_vs_fp64": err}
+    print(json.dumps(line), flush=True)
+    hx.hx_keyset_destroy(ks)
+    hx.hx_context_destroy(ctx)
+
+
 def run_micro_aggregate(args):
     """Alg. 6 Aggregation alone: the model update w - eta/(B N) * sum_i g_i for the 8
     gradient ciphertexts of one 784->128 layer (h=64, beta=4 packing) from 16 parties,
@@ -796,7 +865,8 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--micro", choices=["ntt", "aggregate"], default=None)
     ap.add_argument("--parties", type=int, default=16)
-    ap.add_argument("--workload", choices=["matmul", "sign", "dense", "serve"], default="matmul")
+    ap.add_argument("--workload", choices=["matmul", "sign", "dense", "serve", "rmatmul"], default="matmul")
+    ap.add_argument("--t", type=int, default=16, help="rows of A in the rectangular product")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--lanes", type=int, default=4)
@@ -823,6 +893,8 @@ def main():
         return run_serve(args)
     if args.workload == "dense":
         return run_dense(args)
+    if args.workload == "rmatmul":
+        return run_rmatmul(args)
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)

@@ -204,6 +204,19 @@ hx_status hx_matmul(hx_context *ctx, const hx_keyset *ks, const hx_ct *A, const 
 hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *A,
                           const hx_ct *const *B, int h, size_t count, hx_ct **out, void *stream);
 
+/* ---- rectangular product (App. D) ------------------------------------------------ */
+/* Rectangular product (App. D, Alg. "41"): At[i] packs A~ = (A; ...; A), the
+ * h/t vertical copies of a t x h matrix A (t a power of two dividing h), in
+ * each of its beta positions; B[i] packs h x h matrices.  The result packs
+ * h/t vertical copies of A.B (t x h), so it can enter another rectangular
+ * product as it is.  Same plan, level and scale rules as hx_matmul_batch
+ * (3 levels with >= 4 limbs, 2 with 3 limbs); Step 2/3 run t - 1 terms
+ * instead of h - 1, then log2(h/t) rotate-and-add folds by t*h*2^e rows. */
+hx_status hx_rmatmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *At,
+                           const hx_ct *const *B, int h, int t, size_t count, hx_ct **out, void *stream);
+/* Rotation steps of hx_rmatmul_batch at `limbs`; returns the count, writes up to cap. */
+int hx_rmatmul_rotation_steps(const hx_context *ctx, int h, int t, int limbs, int32_t *out, int cap);
+
 /* ---- transpose (App. C) ---------------------------------------------------------- */
 /* A^T for each of the beta packed h x h matrices of `count` ciphertexts at one
  * level (>= 2 limbs): sum over the 2h-1 diagonals (h-1)s of U^T with the

@@ -455,6 +455,30 @@ hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_
     HX_END
 }
 
+int hx_rmatmul_rotation_steps(const hx_context *ctx, int h, int t, int limbs, int32_t *out, int cap)
+{
+    if (!ctx || h < 2 || (h & (h - 1)) || h * h > ctx->N / 2 || limbs < 3) return HX_EINVAL;
+    if (t < 1 || t > h || (t & (t - 1))) return HX_EINVAL;
+    std::vector<int64_t> st = plan_rotation_steps(h, ctx->N / 2 / (h * h), limbs, t);
+    for (int i = 0; i < (int)st.size() && i < cap; i++) out[i] = (int32_t)st[i];
+    return (int)st.size();
+}
+
+hx_status hx_rmatmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *At,
+                           const hx_ct *const *B, int h, int t, size_t count, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(ctx && ks && At && B && out && count >= 1 && count < 4096, "bad argument");
+    for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    Cts a = gather(*ctx, At, count, S(stream));
+    Cts b = gather(*ctx, B, count, S(stream));
+    const hx_matmul_plan *p = plan ? plan : cached_plan(*ctx, h, a.limbs);
+    need(p->h == h && p->kind == 0, "plan built for another h");
+    scatter(*ctx, rmatmul_batch(*ctx, *ks, *p, a, b, t, S(stream)), out, S(stream));
+    return HX_OK;
+    HX_END
+}
+
 hx_status hx_transpose_plan_create(hx_context *ctx, int h, int limbs, hx_matmul_plan **out)
 {
     HX_TRY

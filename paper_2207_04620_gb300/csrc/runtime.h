@@ -191,9 +191,11 @@ hx_matmul_plan *make_transpose_plan(hx_context &ctx, int h, int limbs, cudaStrea
 const hx_matmul_plan *cached_transpose_plan(hx_context &ctx, int h, int limbs);
 std::vector<int64_t> transpose_rotation_steps(int h, int beta);
 Cts transpose_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &x, cudaStream_t s);
-std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs);
+std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs, int t = 0);  // t = 0: t = h
 Cts matmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &A, const Cts &B,
-                 cudaStream_t s);
+                 cudaStream_t s, int t = 0);  // t < h: the cut k-sum of the rectangular product
+Cts rmatmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &At, const Cts &B, int t,
+                  cudaStream_t s);
 // refresh randomness of entry b: SplitMix64 streams keyed by refresh_seeds[b] (tag 1 + refresh index)
 Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k, bool relu, bool allow_refresh,
                const std::vector<uint64_t> &refresh_seeds, cudaStream_t s);

@@ -74,8 +74,9 @@ std::vector<int32_t> rot(const std::vector<int32_t> &v, int r)
 
 } // namespace
 
-std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs)
+std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs, int t)
 {
+    t = t ? t : h;
     const int b = baby_steps(h);
     const bool alg3 = limbs >= 4;
     std::vector<int64_t> s;
@@ -91,11 +92,12 @@ std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs)
     } else {
         for (int l = 1; l < h; l++) s.push_back((int64_t)beta * h * l);
     }
-    for (int k = 1; k < h; k++) {
+    for (int k = 1; k < t; k++) {
         s.push_back((int64_t)beta * k);
         s.push_back((int64_t)beta * (k - h));
         s.push_back((int64_t)beta * h * k);
     }
+    for (int e = t; e < h; e *= 2) s.push_back((int64_t)beta * h * e);
     const int64_t n = (int64_t)beta * h * h;
     std::vector<int64_t> out;
     for (int64_t x : s) {
@@ -297,7 +299,8 @@ Cts lintrans(Eval &ev, const hx_keyset &ks, const Cts &ct, int lmin, int lmax, i
     return ev.rotate_sum(items, ks);
 }
 
-Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Cts &A, const Cts &B)
+// t < h: only the terms k < t of Steps 2-3 (the rectangular product, App. D)
+Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Cts &A, const Cts &B, int t)
 {
     hx_context &ctx = ev.ctx;
     const int h = p.h, beta = p.beta;
@@ -310,7 +313,7 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
     Cts acc = ev.tensor(ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt), B0);
     BufPtr DA = ev.hoist(A0);
     BufPtr DB = ev.hoist(B0);  // one ModUp serves every B^(k)
-    for (int k = 1; k < h; k++) {
+    for (int k = 1; k < t; k++) {
         Cts Bk = ev.rotate_hoisted_one(B0, DB, (int64_t)beta * h * k, ks);
         double sc;
         const uint64_t *v = mask_pt(p, 2, k, &sc);
@@ -321,7 +324,7 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
     return ev.rescale(ev.rescale(ev.relinearize(acc, ks.relin)));
 }
 
-Cts matmul_depth2(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Cts &A, const Cts &B)
+Cts matmul_depth2(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Cts &A, const Cts &B, int t)
 {
     const int h = p.h, beta = p.beta;
     Cts A0 = ev.rescale(lintrans(ev, ks, A, -h + 1, h - 1, 1, p, 0));
@@ -339,15 +342,15 @@ Cts matmul_depth2(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const 
     const Cts &Bfull = prefix[h];
     Cts B0 = ev.rescale(Bfull);
     std::vector<int64_t> ast;
-    for (int k = 1; k < h; k++) ast.push_back((int64_t)beta * k);
-    for (int k = 1; k < h; k++) ast.push_back((int64_t)beta * (k - h));
+    for (int k = 1; k < t; k++) ast.push_back((int64_t)beta * k);
+    for (int k = 1; k < t; k++) ast.push_back((int64_t)beta * (k - h));
     std::vector<Cts> RA = ev.rotate_hoisted(A0, ast, ks);
     Cts acc = ev.tensor(A0, B0);
-    for (int k = 1; k < h; k++) {
+    for (int k = 1; k < t; k++) {
         Cts X = ev.rescale(prefix[h - k]);
         Cts Y = ev.rescale(ev.add(Bfull, prefix[h - k], true));
         ev.tensor_acc(acc, RA[k - 1], ev.rotate(X, (int64_t)beta * h * k, ks));
-        ev.tensor_acc(acc, RA[h - 1 + k - 1], ev.rotate(Y, (int64_t)beta * h * k, ks));
+        ev.tensor_acc(acc, RA[t - 1 + k - 1], ev.rotate(Y, (int64_t)beta * h * k, ks));
     }
     return ev.rescale(ev.relinearize(acc, ks.relin));
 }
@@ -363,14 +366,29 @@ Cts transpose_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &
 }
 
 Cts matmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &A, const Cts &B,
-                 cudaStream_t s)
+                 cudaStream_t s, int t)
 {
+    t = t ? t : plan.h;
+    HX_CHECK(t >= 1 && t <= plan.h, HX_EINVAL, "t must be in [1, h]");
     HX_CHECK(plan.kind == 0, HX_EINVAL, "not a matmul plan");
     HX_CHECK(A.comps == 2 && B.comps == 2 && A.B == B.B, HX_EINVAL, "matmul needs two batches of ciphertexts");
     HX_CHECK(A.limbs == plan.limbs && B.limbs == plan.limbs, HX_ELEVEL, "inputs are not at the plan's level");
     HX_CHECK(A.scale == B.scale, HX_ESCALE, "inputs must share the scale");
     Eval ev(ctx, s);
-    return plan.alg3 ? matmul_alg3(ev, ks, plan, A, B) : matmul_depth2(ev, ks, plan, A, B);
+    return plan.alg3 ? matmul_alg3(ev, ks, plan, A, B, t) : matmul_depth2(ev, ks, plan, A, B, t);
+}
+
+// App. D, Alg. "41": A~ packs h/t vertical copies of a t x h matrix; the k-sum
+// cut to t terms, then log2(h/t) rotate-and-add folds by t*h*2^e rows leave
+// h/t copies of A.B
+Cts rmatmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &At, const Cts &B, int t,
+                  cudaStream_t s)
+{
+    HX_CHECK(t >= 1 && plan.h % t == 0 && (t & (t - 1)) == 0, HX_EINVAL, "t must be a power of two dividing h");
+    Cts out = matmul_batch(ctx, ks, plan, At, B, s, t);
+    Eval ev(ctx, s);
+    for (int e = t; e < plan.h; e *= 2) out = ev.add(out, ev.rotate(out, (int64_t)plan.beta * plan.h * e, ks));
+    return out;
 }
 
 // ---- Sec. 4: composite sign ------------------------------------------------------

@@ -80,6 +80,8 @@ _SIGS = {
     "hx_matmul_rotation_steps": (c_int, [c_vp, c_int, c_int, P_i32, c_int]),
     "hx_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, PP, c_vp]),
     "hx_matmul_batch": (c_int, [c_vp, c_vp, c_vp, PP, PP, c_int, c_size_t, PP, c_vp]),
+    "hx_rmatmul_batch": (c_int, [c_vp, c_vp, c_vp, PP, PP, c_int, c_int, c_size_t, PP, c_vp]),
+    "hx_rmatmul_rotation_steps": (c_int, [c_vp, c_int, c_int, c_int, P_i32, c_int]),
     "hx_transpose_plan_create": (c_int, [c_vp, c_int, c_int, PP]),
     "hx_transpose_rotation_steps": (c_int, [c_vp, c_int, P_i32, c_int]),
     "hx_transpose": (c_int, [c_vp, c_vp, c_vp, PP, c_int, c_size_t, PP, c_vp]),
@@ -394,6 +396,21 @@ def hx_matmul_batch(ctx, ks, plan, As, Bs, h, stream=None) -> list:
     outs = (c_vp * n)()
     _chk(lib().hx_matmul_batch(ctx, ks, plan, a, b, h, n, outs, _stream(stream)))
     return [outs[i] for i in range(n)]
+
+
+def hx_rmatmul_batch(ctx, ks, plan, Ats, Bs, h, t, stream=None) -> list:
+    n = len(Ats)
+    a = (c_vp * n)(*Ats)
+    b = (c_vp * n)(*Bs)
+    outs = (c_vp * n)()
+    _chk(lib().hx_rmatmul_batch(ctx, ks, plan, a, b, h, t, n, outs, _stream(stream)))
+    return [outs[i] for i in range(n)]
+
+
+def hx_rmatmul_rotation_steps(ctx: int, h: int, t: int, limbs: int) -> list:
+    buf = np.zeros(4096, dtype=np.int32)
+    n = _chk(lib().hx_rmatmul_rotation_steps(ctx, h, t, limbs, buf.ctypes.data_as(P_i32), buf.size))
+    return [int(x) for x in buf[:n]]
 
 
 def hx_transpose_plan_create(ctx: int, h: int, limbs: int) -> int:

@@ -257,6 +257,41 @@ def test_matmul_bit_exact_and_accurate(name, h):
         pr.close()
 
 
+@pytest.mark.parametrize("name,h,t", [("cfg0", 16, 4), ("alg3", 8, 2), ("alg3", 16, 1), ("alg3", 16, 8)])
+def test_rectangular_matmul_bit_exact(name, h, t):
+    """App. D (Alg. "41") through hx_rmatmul_batch: residues equal the oracle's
+    HE-RMatMult for both variants (cfg0 runs the depth-2 one) and the result
+    decrypts to h/t copies of A.B for every packed pair."""
+    p = PARAMS[name]
+    limbs = len(p["q_bits"])
+    beta = (1 << p["log_n"]) // 2 // (h * h)
+    steps = Hc.matmul_rotation_steps(h, beta, limbs, t)
+    pr = Pair(name, rot_steps=steps)
+    try:
+        assert hx.hx_rmatmul_rotation_steps(pr.ctx, h, t, limbs) == steps
+        masks = Hc.MaskProvider(pr.octx, h, limbs)
+        plan = hx.hx_matmul_plan_create(pr.ctx, h, limbs)
+        for i in range(len(masks.entries)):
+            hx.hx_matmul_plan_set_mask(pr.ctx, plan, i, masks.coeffs(i))
+        rng = np.random.default_rng(h + t)
+        As = [[rng.uniform(-1, 1, (t, h)) for _ in range(beta)] for _ in range(2)]
+        Bs = [workloads.matrices(60 + i, beta, h) for i in range(2)]
+        At = [pr.encrypt(workloads.pack([np.vstack([a] * (h // t)) for a in As[i]], h, beta), 70 + i)
+              for i in range(2)]
+        Bc = [pr.encrypt(workloads.pack(Bs[i], h, beta), 80 + i) for i in range(2)]
+        outs = hx.hx_rmatmul_batch(pr.ctx, pr.ks, plan, [pr.to_lib(c) for c in At], [pr.to_lib(c) for c in Bc], h, t)
+        for i in range(2):
+            want = Hc.rmatmul(C.Evaluator(pr.octx, pr.oks), At[i], Bc[i], h, t, masks)
+            assert pr.same(outs[i], want)
+            got = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, outs[i]), h, beta)
+            err = max(np.abs(g - np.vstack([a @ b] * (h // t))).max() for g, a, b in zip(got, As[i], Bs[i]))
+            assert err < 2 ** -16
+            hx.hx_ct_destroy(outs[i])
+        hx.hx_matmul_plan_destroy(plan)
+    finally:
+        pr.close()
+
+
 def test_matmul_library_masks_end_to_end():
     """The product path: library encryption, library masks, library decryption;
     config 0 (N=2^12, h=16, one product with the other packed slots zero)."""
