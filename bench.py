@@ -789,6 +789,56 @@ def run_rmatmul(args):
     hx.hx_context_destroy(ctx)
 
 
+def run_micro_encrypt(args):
+    """Client side (Fig. 1 items 3 and 5): encode + encrypt 64 slot vectors of 16384 values at the
+    config-2 ring (N=2^15, 16 limbs) as one device batch (hx_encrypt_batch, slots from host memory,
+    handles out), beside the host encoder + per-ciphertext encryption (hx_encrypt) of the same
+    inputs; the two give identical ciphertexts."""
+    import torch
+
+    from paper_2207_04620_gb300 import hx
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    log_n, qb, pb, count = 15, [60] + [40] * 15, [60] * 3, 64
+    ctx = hx.hx_context_create(log_n, qb, pb, 40)
+    ks = hx.hx_keygen(ctx, 2, 3, [])
+    z = np.random.default_rng(2).uniform(-1, 1, (count, (1 << log_n) // 2))
+    seeds = list(range(1000, 1000 + count))
+    for _ in range(args.warmup):
+        for o in hx.hx_encrypt_batch(ctx, ks, z, seeds):
+            hx.hx_ct_destroy(o)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        outs = hx.hx_encrypt_batch(ctx, ks, z, seeds)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t0)
+        for o in outs[1:]:
+            hx.hx_ct_destroy(o)
+        first = outs[0]
+        if len(ts) < args.steps:
+            hx.hx_ct_destroy(first)
+    t_dev = statistics.median(ts)
+    host_n = 8
+    t0 = time.perf_counter()
+    ref = [hx.hx_encrypt(ctx, ks, z[i], 0, seeds[i]) for i in range(host_n)]
+    t_host = (time.perf_counter() - t0) / host_n
+    same = bool(np.array_equal(hx.hx_ct_export(ctx, first), hx.hx_ct_export(ctx, ref[0])))
+    for o in ref + [first]:
+        hx.hx_ct_destroy(o)
+    res = {"micro": "encrypt", "log_n": log_n, "limbs": len(qb), "count": count,
+           "device_batch_ct_per_s": round(count / t_dev, 1), "device_batch_ms": round(t_dev * 1e3, 2),
+           "host_path_ct_per_s": round(1.0 / t_host, 1), "speedup": round(t_host * count / t_dev, 1),
+           "identical_to_host_path": same,
+           "note": "host wall clock; the device batch includes the H2D of the slots and the handle copies"}
+    print(json.dumps(res), flush=True)
+    hx.hx_keyset_destroy(ks)
+    hx.hx_context_destroy(ctx)
+
+
 def run_micro_aggregate(args):
     """Alg. 6 Aggregation alone: the model update w - eta/(B N) * sum_i g_i for the 8
     gradient ciphertexts of one 784->128 layer (h=64, beta=4 packing) from 16 parties,
@@ -863,7 +913,7 @@ def run_micro_aggregate(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--micro", choices=["ntt", "aggregate"], default=None)
+    ap.add_argument("--micro", choices=["ntt", "aggregate", "encrypt"], default=None)
     ap.add_argument("--parties", type=int, default=16)
     ap.add_argument("--workload", choices=["matmul", "sign", "dense", "serve", "rmatmul"], default="matmul")
     ap.add_argument("--t", type=int, default=16, help="rows of A in the rectangular product")
@@ -885,6 +935,8 @@ def main():
     args = ap.parse_args()
     if args.micro == "aggregate":
         return run_micro_aggregate(args)
+    if args.micro == "encrypt":
+        return run_micro_encrypt(args)
     if args.micro:
         return run_micro(args)
     if args.workload == "sign":

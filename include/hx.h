@@ -108,6 +108,17 @@ hx_status hx_encode(const hx_context *ctx, const double *slots, size_t n, double
 /* Enc(pk, Ecd(slots)) at `limbs` limbs (0 = all Q primes), default scale. */
 hx_status hx_encrypt(hx_context *ctx, const hx_keyset *ks, const double *slots, size_t n, int limbs, uint64_t seed,
                      hx_ct **out);
+/* Client side on the device: Ecd of `count` slot vectors (host, [count][n],
+ * n <= N/2, N >= 512) by a batched 2N-point FP64 FFT that repeats the host
+ * encoder's operations one by one, so coeffs ([count][N], host) equal
+ * hx_encode's bit for bit; HX_EINVAL if a coefficient reaches 2^62. */
+hx_status hx_encode_batch(hx_context *ctx, const double *slots, size_t n, size_t count, double scale, int64_t *coeffs,
+                          void *stream);
+/* Enc(pk, Ecd(slots_i)) for i < count with the device encoder and the
+ * encryption randomness drawn on the device from the same SplitMix64 streams
+ * (seed seeds[i], tag 0, index 0): out[i] equals hx_encrypt(..., seeds[i]). */
+hx_status hx_encrypt_batch(hx_context *ctx, const hx_keyset *ks, const double *slots, size_t n, size_t count, int limbs,
+                           const uint64_t *seeds, hx_ct **out, void *stream);
 /* Enc(pk, m) for N signed integer coefficients m at `scale`; tag/index select
  * the SplitMix64 streams of the encryption randomness. */
 hx_status hx_encrypt_coeffs(hx_context *ctx, const hx_keyset *ks, const int64_t *coeffs, double scale, int limbs,

@@ -181,6 +181,41 @@ hx_status hx_encrypt(hx_context *ctx, const hx_keyset *ks, const double *slots, 
     HX_END
 }
 
+hx_status hx_encode_batch(hx_context *ctx, const double *slots, size_t n, size_t count, double scale, int64_t *coeffs,
+                          void *stream)
+{
+    HX_TRY
+    need(ctx && slots && coeffs && count >= 1 && count < 65536 && n <= (size_t)ctx->N / 2 && scale > 0,
+         "bad argument");
+    cudaStream_t s = S(stream);
+    DevBuf in(std::max<size_t>(1, n * count), s), out((size_t)ctx->N * count, s);
+    if (n) HX_CUDA(cudaMemcpyAsync(in.p, slots, sizeof(double) * n * count, cudaMemcpyHostToDevice, s));
+    encode_batch(*ctx, reinterpret_cast<const double *>(in.p), n, (int)count, scale,
+                 reinterpret_cast<int64_t *>(out.p), (size_t)ctx->N, s);
+    HX_CUDA(cudaMemcpyAsync(coeffs, out.p, sizeof(int64_t) * ctx->N * count, cudaMemcpyDeviceToHost, s));
+    HX_CUDA(cudaStreamSynchronize(s));
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_encrypt_batch(hx_context *ctx, const hx_keyset *ks, const double *slots, size_t n, size_t count, int limbs,
+                           const uint64_t *seeds, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(ctx && ks && slots && seeds && out && count >= 1 && count < 65536 && n <= (size_t)ctx->N / 2,
+         "bad argument");
+    for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    cudaStream_t s = S(stream);
+    DevBuf in(std::max<size_t>(1, n * count), s);
+    if (n) HX_CUDA(cudaMemcpyAsync(in.p, slots, sizeof(double) * n * count, cudaMemcpyHostToDevice, s));
+    Cts c = encrypt_batch(*ctx, *ks, reinterpret_cast<const double *>(in.p), n, (int)count,
+                          limbs ? limbs : ctx->n_q, seeds, s);
+    scatter(*ctx, c, out, s);
+    HX_CUDA(cudaStreamSynchronize(s));
+    return HX_OK;
+    HX_END
+}
+
 hx_status hx_encrypt_coeffs(hx_context *ctx, const hx_keyset *ks, const int64_t *coeffs, double scale, int limbs,
                             uint64_t seed, uint32_t tag, uint32_t index, hx_ct **out)
 {

@@ -1,0 +1,233 @@
+// Client-side encoding and encryption of a batch on the device (Fig. 1 items 3
+// and 5): the canonical-embedding encoder as a batched 2N-point FP64 FFT and
+// the encryption randomness drawn from the same counter-based SplitMix64
+// streams as the host path, so every ciphertext equals hx_encrypt's.
+//
+// The FFT repeats the host encoder's arithmetic operation for operation
+// (bit-reversed placement, radix-2 decimation in time, the host's table of
+// 2N-th roots, products and sums rounded one at a time with the _rn
+// intrinsics, no fused multiply-add), which makes the two encoders agree bit
+// for bit.
+#include "runtime.h"
+
+namespace hx {
+
+namespace {
+
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+constexpr int kFftTile = 1024;  // points of the sub-transforms done in shared memory
+
+__device__ __forceinline__ uint64_t dmix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 w)
+{
+    return make_double2(__dsub_rn(__dmul_rn(a.x, w.x), __dmul_rn(a.y, w.y)),
+                        __dadd_rn(__dmul_rn(a.x, w.y), __dmul_rn(a.y, w.x)));
+}
+
+__device__ __forceinline__ void butterfly(double2 &u, double2 &v, double2 w)
+{
+    const double2 t = cmul(v, w);
+    const double2 a = u;
+    u = make_double2(__dadd_rn(a.x, t.x), __dadd_rn(a.y, t.y));
+    v = make_double2(__dsub_rn(a.x, t.x), __dsub_rn(a.y, t.y));
+}
+
+// slot j of vector b goes to the bit-reversed positions of exponents e_j and 2N - e_j
+__global__ void k_enc_place(double2 *A, const double *slots, size_t n_slots, const int *e, int log_m, int half_n)
+{
+    const int b = blockIdx.y;
+    const int m = 1 << log_m;
+    double2 *a = A + (size_t)b * m;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < half_n; j += gridDim.x * blockDim.x) {
+        const double z = (size_t)j < n_slots ? slots[(size_t)b * n_slots + j] : 0.0;
+        const unsigned p1 = __brev((unsigned)e[j]) >> (32 - log_m);
+        const unsigned p2 = __brev((unsigned)((m - e[j]) & (m - 1))) >> (32 - log_m);
+        a[p1] = make_double2(z, 0.0);
+        a[p2] = make_double2(z, 0.0);
+    }
+}
+
+// stages len = 2 .. kFftTile on contiguous tiles in shared memory
+__global__ void __launch_bounds__(kFftTile / 2) k_enc_fft_tile(double2 *A, const double2 *__restrict__ roots, int log_m)
+{
+    __shared__ double2 s[kFftTile];
+    const int m = 1 << log_m;
+    double2 *a = A + (size_t)blockIdx.y * m + (size_t)blockIdx.x * kFftTile;
+    for (int i = threadIdx.x; i < kFftTile; i += blockDim.x) s[i] = a[i];
+    __syncthreads();
+    for (int len = 2; len <= kFftTile; len <<= 1) {
+        const int half = len >> 1, step = m / len;
+        for (int t = threadIdx.x; t < kFftTile / 2; t += blockDim.x) {
+            const int g = t / half, k = t % half, i = g * len + k;
+            double2 u = s[i], v = s[i + half];
+            butterfly(u, v, roots[(size_t)k * step]);
+            s[i] = u;
+            s[i + half] = v;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < kFftTile; i += blockDim.x) a[i] = s[i];
+}
+
+// one later stage (len > kFftTile) over global memory
+__global__ void k_enc_fft_stage(double2 *A, const double2 *__restrict__ roots, int log_m, int len)
+{
+    const int m = 1 << log_m, half = len >> 1, step = m / len;
+    double2 *a = A + (size_t)blockIdx.y * m;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m / 2; t += gridDim.x * blockDim.x) {
+        const int g = t / half, k = t % half, i = g * len + k;
+        double2 u = a[i], v = a[i + half];
+        butterfly(u, v, roots[(size_t)k * step]);
+        a[i] = u;
+        a[i + half] = v;
+    }
+}
+
+__device__ __forceinline__ double round_half_away_d(double x)
+{
+    const double r = floor(__dadd_rn(fabs(x), 0.5));
+    return x < 0 ? -r : r;
+}
+
+// coefficient i = round(Re A_i / N * scale); |coefficient| >= 2^62 sets *err
+__global__ void k_enc_round(int64_t *out, size_t out_stride, const double2 *A, int log_m, int n, double scale,
+                            int *err)
+{
+    const int b = blockIdx.y;
+    const double2 *a = A + ((size_t)b << log_m);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = round_half_away_d(__dmul_rn(__ddiv_rn(a[i].x, (double)n), scale));
+        if (!(fabs(v) < 4611686018427387904.0)) {
+            atomicExch(err, 1);
+            out[b * out_stride + i] = 0;
+        } else {
+            out[b * out_stride + i] = (int64_t)v;
+        }
+    }
+}
+
+// encryption randomness of entry b: poly 0 ternary (v), 1 and 2 Gaussian (e0, e1);
+// state0[b*3 + p] is the stream's initial state, draw i = mix64(state0 + (i+1) gamma)
+__global__ void k_enc_sample(int64_t *out, size_t entry_stride, const uint64_t *__restrict__ state0,
+                             const uint64_t *__restrict__ th, int bound, int n)
+{
+    const int b = blockIdx.z, p = blockIdx.y;
+    const uint64_t st = state0[b * 3 + p];
+    int64_t *o = out + b * entry_stride + (size_t)p * n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint64_t r = dmix64(st + (uint64_t)(i + 1) * kGamma);
+        if (p == 0) {
+            const uint64_t t = r % 3;
+            o[i] = t == 2 ? -1 : (int64_t)t;
+        } else {
+            const uint64_t x = r >> 1;
+            int idx = 0;
+            while (idx < 2 * bound && x >= th[idx]) idx++;
+            o[i] = (int64_t)idx - bound;
+        }
+    }
+}
+
+int grid_for(size_t work) { return (int)std::min<size_t>((work + 255) / 256, 4096); }
+
+// device copies of the host encoder's tables (2N-th roots, 5^j mod 2N) and of
+// the Gaussian sampler's thresholds, built once per context
+const EncTables &enc_tables(hx_context &ctx)
+{
+    std::call_once(ctx.enc_once, [&] {
+        const int N = ctx.N;
+        EncTables &t = ctx.enc_dev;
+        t.roots = std::make_shared<DevBuf>((size_t)2 * N, true);
+        HX_CUDA(cudaMemcpy(t.roots->p, ctx.enc->roots.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice));
+        std::vector<int> e32(N / 2);
+        for (int j = 0; j < N / 2; j++) e32[j] = (int)ctx.enc->e[j];
+        t.e = std::make_shared<DevBuf>((size_t)(N / 2 + 1) / 2, true);
+        HX_CUDA(cudaMemcpy(t.e->p, e32.data(), sizeof(int) * e32.size(), cudaMemcpyHostToDevice));
+        t.th = std::make_shared<DevBuf>(ctx.cdt->th.size(), true);
+        HX_CUDA(cudaMemcpy(t.th->p, ctx.cdt->th.data(), sizeof(uint64_t) * ctx.cdt->th.size(),
+                           cudaMemcpyHostToDevice));
+    });
+    HX_CHECK(ctx.enc_dev.roots && ctx.enc_dev.e && ctx.enc_dev.th, HX_ECUDA, "encoder tables are missing");
+    return ctx.enc_dev;
+}
+
+} // namespace
+
+// coefficients of the canonical-embedding encoding of `count` slot vectors
+// (device, [count][N] int64), equal to Encoder::encode's
+void encode_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int count, double scale, int64_t *out,
+                  size_t out_stride, cudaStream_t s)
+{
+    const int N = ctx.N, log_m = ctx.log_n + 1, m = 2 * N;
+    HX_CHECK(m % kFftTile == 0, HX_EINVAL, "the device encoder needs N >= 512");
+    HX_CHECK(n_slots <= (size_t)N / 2 && count >= 1 && count < 65536, HX_EINVAL, "bad slot batch");
+    const EncTables &t = enc_tables(ctx);
+    DevBuf A((size_t)2 * m * count, s);
+    DevBuf err(1, s);
+    HX_CUDA(cudaMemsetAsync(A.p, 0, sizeof(double2) * (size_t)m * count, s));
+    HX_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    double2 *a = reinterpret_cast<double2 *>(A.p);
+    const double2 *roots = reinterpret_cast<const double2 *>(t.roots->p);
+    k_enc_place<<<dim3(grid_for(N / 2), count), 256, 0, s>>>(a, slots_dev, n_slots,
+                                                             reinterpret_cast<const int *>(t.e->p), log_m, N / 2);
+    k_enc_fft_tile<<<dim3(m / kFftTile, count), kFftTile / 2, 0, s>>>(a, roots, log_m);
+    for (int len = 2 * kFftTile; len <= m; len <<= 1)
+        k_enc_fft_stage<<<dim3(grid_for(m / 2), count), 256, 0, s>>>(a, roots, log_m, len);
+    k_enc_round<<<dim3(grid_for(N), count), 256, 0, s>>>(out, out_stride, a, log_m, N, scale,
+                                                         reinterpret_cast<int *>(err.p));
+    HX_CUDA(cudaGetLastError());
+    ctx.counters[C_LAUNCH] += 4 + (log_m - 10);
+    int herr = 0;
+    HX_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HX_CUDA(cudaStreamSynchronize(s));
+    HX_CHECK(herr == 0, HX_EINVAL, "encoded coefficient exceeds 2^62");
+}
+
+// Enc(pk, Ecd(slots_b)) for every b, seeds[b] as hx_encrypt's seed (tag 0, index 0)
+Cts encrypt_batch(hx_context &ctx, const hx_keyset &ks, const double *slots_dev, size_t n_slots, int count, int limbs,
+                  const uint64_t *seeds, cudaStream_t s)
+{
+    HX_CHECK(limbs >= 1 && limbs <= ctx.n_q, HX_EINVAL, "bad level");
+    const int N = ctx.N;
+    Eval ev(ctx, s);
+    const EncTables &t = enc_tables(ctx);
+    // per entry: [v, e0, e1, m] signed coefficients
+    DevBuf raw((size_t)count * 4 * N, s);
+    int64_t *r = reinterpret_cast<int64_t *>(raw.p);
+    std::vector<uint64_t> st((size_t)count * 3);
+    for (int b = 0; b < count; b++) {
+        st[b * 3 + 0] = Stream(seeds[b], P_ENC_V, 0, 0).state;
+        st[b * 3 + 1] = Stream(seeds[b], P_ENC_E0, 0, 0).state;
+        st[b * 3 + 2] = Stream(seeds[b], P_ENC_E1, 0, 0).state;
+    }
+    DevBuf st_dev(st.size(), s);
+    HX_CUDA(cudaMemcpyAsync(st_dev.p, st.data(), sizeof(uint64_t) * st.size(), cudaMemcpyHostToDevice, s));
+    k_enc_sample<<<dim3(grid_for(N), 3, count), 256, 0, s>>>(r, (size_t)4 * N, st_dev.p, t.th->p, ctx.cdt->bound, N);
+    HX_CUDA(cudaGetLastError());
+    ctx.counters[C_LAUNCH] += 1;
+    encode_batch(ctx, slots_dev, n_slots, count, ctx.scale, r + 3 * (size_t)N, (size_t)4 * N, s);
+    // residues over the first `limbs` primes, NTT form: [count*4][limbs][N]
+    DevBuf polys((size_t)count * 4 * limbs * N, s);
+    launch_signed_to_rows(ev.lc(), polys.p, r, limbs, count * 4, (size_t)N, ctx.d_prime_ids);
+    std::vector<int> rows(limbs);
+    for (int l = 0; l < limbs; l++) rows[l] = l;
+    ev.ntt_inplace(polys.p, (size_t)limbs * N, count * 4, rows, rows, false);
+    Cts c = ev.alloc(count, 2, limbs);
+    c.scale = ctx.scale;
+    const size_t st4 = (size_t)limbs * N;
+    for (int b = 0; b < count; b++) {
+        const uint64_t *pb = polys.p + (size_t)b * 4 * st4;
+        launch_encrypt_combine(ev.lc(), c.d + (size_t)b * c.bstride(N), pb, pb + st4, pb + 2 * st4, pb + 3 * st4,
+                               ks.pk->p, ctx.n_q, limbs);
+    }
+    HX_CUDA(cudaStreamSynchronize(s));  // the staging buffers above are released at return
+    return c;
+}
+
+} // namespace hx

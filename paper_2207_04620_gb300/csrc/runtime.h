@@ -45,6 +45,12 @@ struct SwitchKey {
 
 } // namespace hx
 
+namespace hx {
+struct EncTables {  // device tables of the client-side encoder
+    BufPtr roots, e, th;
+};
+} // namespace hx
+
 struct hx_context {
     int log_n = 0, N = 0, n_q = 0, K = 0, n_all = 0, dnum = 0;
     std::vector<uint64_t> primes;  // Q then P
@@ -65,6 +71,8 @@ struct hx_context {
     int device = 0;
     hx::Profiler prof;
     bool profiling = false;
+    std::once_flag enc_once;
+    hx::EncTables enc_dev;
 };
 
 struct hx_keyset {
@@ -202,6 +210,10 @@ Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k,
 struct DenseResult {
     Cts E, M, dW;
 };
+void encode_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int count, double scale, int64_t *out,
+                  size_t out_stride, cudaStream_t s);
+Cts encrypt_batch(hx_context &ctx, const hx_keyset &ks, const double *slots_dev, size_t n_slots, int count, int limbs,
+                  const uint64_t *seeds, cudaStream_t s);
 struct DensePlans {
     const hx_matmul_plan *fwd = nullptr, *transpose = nullptr, *bwd = nullptr;  // null: the cached plan
 };

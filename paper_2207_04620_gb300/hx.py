@@ -52,6 +52,8 @@ _SIGS = {
     "hx_keyset_export_public_key": (c_i64, [c_vp, P_u64, c_size_t]),
     "hx_keyset_destroy": (None, [c_vp]),
     "hx_encode": (c_int, [c_vp, P_dbl, c_size_t, c_double, P_i64]),
+    "hx_encode_batch": (c_int, [c_vp, P_dbl, c_size_t, c_size_t, c_double, P_i64, c_vp]),
+    "hx_encrypt_batch": (c_int, [c_vp, c_vp, P_dbl, c_size_t, c_size_t, c_int, P_u64, PP, c_vp]),
     "hx_encrypt": (c_int, [c_vp, c_vp, P_dbl, c_size_t, c_int, c_u64, PP]),
     "hx_encrypt_coeffs": (c_int, [c_vp, c_vp, P_i64, c_double, c_int, c_u64, c_u32, c_u32, PP]),
     "hx_decrypt": (c_int, [c_vp, c_vp, c_vp, P_dbl, c_size_t]),
@@ -233,6 +235,25 @@ def hx_encode(ctx: int, slots, scale: float) -> np.ndarray:
     out = np.zeros(hx_context_n(ctx), dtype=np.int64)
     _chk(lib().hx_encode(ctx, z.ctypes.data_as(P_dbl), z.size, scale, _i64p(out)))
     return out
+
+
+def hx_encode_batch(ctx: int, slots, scale: float, stream=None) -> np.ndarray:
+    """slots: [count][n] array; returns [count][N] int64 coefficients (device encoder)."""
+    z = np.ascontiguousarray(np.asarray(slots, dtype=np.float64))
+    count, n = z.shape
+    out = np.zeros((count, hx_context_n(ctx)), dtype=np.int64)
+    _chk(lib().hx_encode_batch(ctx, z.ctypes.data_as(P_dbl), n, count, float(scale), _i64p(out), _stream(stream)))
+    return out
+
+
+def hx_encrypt_batch(ctx: int, ks: int, slots, seeds, limbs: int = 0, stream=None) -> list:
+    z = np.ascontiguousarray(np.asarray(slots, dtype=np.float64))
+    count, n = z.shape
+    sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+    assert sd.size == count
+    outs = (c_vp * count)()
+    _chk(lib().hx_encrypt_batch(ctx, ks, z.ctypes.data_as(P_dbl), n, count, limbs, _u64p(sd), outs, _stream(stream)))
+    return [outs[i] for i in range(count)]
 
 
 def hx_encrypt(ctx: int, ks: int, slots, limbs: int = 0, seed: int = 0) -> int:

@@ -469,6 +469,30 @@ def test_dbootstrap_bit_exact(alg3):
     hx.hx_ct_destroy(out)
 
 
+@pytest.mark.parametrize("n", [None, 1000])
+def test_device_encode_and_encrypt_equal_host(alg3, n):
+    """The client-side batch on the device (FP64 FFT encoder, SplitMix64
+    samplers) gives the host encoder's coefficients and hx_encrypt's
+    ciphertexts bit for bit, at the top level and one level down, for full and
+    partial slot vectors; oversize coefficients are rejected."""
+    pr = alg3
+    n = pr.N // 2 if n is None else n
+    z = np.random.default_rng(n).uniform(-1, 1, (5, n))
+    scale = 2.0 ** 45
+    coeffs = hx.hx_encode_batch(pr.ctx, z, scale)
+    for i in range(5):
+        assert np.array_equal(coeffs[i], hx.hx_encode(pr.ctx, z[i], scale))
+    for limbs in (0, 3):
+        outs = hx.hx_encrypt_batch(pr.ctx, pr.ks, z, [300 + i for i in range(5)], limbs=limbs)
+        for i in range(5):
+            ref = hx.hx_encrypt(pr.ctx, pr.ks, z[i], limbs, 300 + i)
+            assert np.array_equal(hx.hx_ct_export(pr.ctx, outs[i]), hx.hx_ct_export(pr.ctx, ref))
+            hx.hx_ct_destroy(ref)
+            hx.hx_ct_destroy(outs[i])
+    with pytest.raises(hx.HxError):
+        hx.hx_encode_batch(pr.ctx, z * 1e9, 2.0 ** 45)
+
+
 @pytest.mark.slow
 def test_matmul_config1_bit_exact():
     """Config 1 shape: N=2^14, 8 limbs, h=64 (beta=2), one ciphertext pair."""
