@@ -196,6 +196,8 @@ def run_hx(args, world, rank, local):
     steps = hx.hx_matmul_rotation_steps(ctx, H, limbs)
     ks = hx.hx_keygen(ctx, 2, 2024 + rank, steps)
     plan = hx.hx_matmul_plan_create(ctx, H, limbs)
+    hx.hx_matmul_plan_bind_keys(ctx, plan, ks)  # Step 2 selection folded into the rotation keys
+    premasked_bytes = hx.hx_matmul_plan_bound_bytes(plan)
     mats_a = [workloads.matrices(1000 * rank + 2 * i, BETA, H) for i in range(PAIRS)]
     mats_b = [workloads.matrices(1000 * rank + 2 * i + 1, BETA, H) for i in range(PAIRS)]
     A = [hx.hx_encrypt(ctx, ks, workloads.pack(m, H, BETA), 0, 10 + i) for i, m in enumerate(mats_a)]
@@ -349,7 +351,8 @@ def run_hx(args, world, rank, local):
                            "l2": "flushed between timed steps (512 MB write outside the events)",
                            "per_step_launch": "one hx_matmul_exec_run C-ABI call: the batched schedule "
                                               "(hx_matmul_batch) captured once into a CUDA graph",
-                           "ntt_tiles_autotuned": tiles},
+                           "ntt_tiles_autotuned": tiles,
+                           "step2_premasked_key_bytes": premasked_bytes},
                 "e2e": {"value": round(PRODUCTS * world / e2e_s, 2), "unit": "matmul/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "what": "hx_matmul_exec_run_host per step: H2D of the 32 input ciphertexts from page-locked "

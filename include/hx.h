@@ -202,6 +202,16 @@ hx_status hx_ntt(hx_context *ctx, uint64_t *dev, int n_polys, int limbs, const i
 hx_status hx_matmul_plan_create(hx_context *ctx, int h, int limbs, hx_matmul_plan **out);
 int hx_matmul_plan_num_masks(const hx_matmul_plan *plan);
 hx_status hx_matmul_plan_set_mask(hx_context *ctx, hx_matmul_plan *plan, int i, const int64_t *coeffs);
+/* Folds Step 2's selection masks into copies of the rotation keys of `ks`
+ * (for every k: v_k * swk(k) and (q_t - v_k) * swk(k - h) on the extended
+ * basis), so each selection is one inner product over both keys and one
+ * reduction instead of two inner products, two reductions and the mask
+ * product.  Products with these keys give the same residues.  Costs
+ * hx_matmul_plan_bound_bytes(plan) of device memory (2(h-1) masked keys at the
+ * product's Step-2 level); replacing a mask with hx_matmul_plan_set_mask
+ * unbinds.  Alg. 3 plans (>= 4 limbs) only. */
+hx_status hx_matmul_plan_bind_keys(hx_context *ctx, hx_matmul_plan *plan, const hx_keyset *ks, void *stream);
+int64_t hx_matmul_plan_bound_bytes(const hx_matmul_plan *plan);
 void hx_matmul_plan_destroy(hx_matmul_plan *plan);
 /* Rotation steps (mod N/2, sorted, no 0) a product of this shape uses;
  * returns the count (writes at most cap) or a negative status. */

@@ -91,6 +91,8 @@ hx_status hx_keygen(hx_context *ctx, int n_parties, uint64_t seed, const int32_t
     need(ctx && out && (rot_steps || n_steps == 0), "null argument");
     *out = nullptr;
     std::unique_ptr<hx_keyset> ks(new hx_keyset);
+    static std::atomic<uint64_t> next_uid{1};
+    ks->uid = next_uid++;
     keygen(*ctx, *ks, n_parties, seed, nullptr);
     std::vector<int64_t> st(rot_steps, rot_steps + n_steps);
     add_rotation_keys(*ctx, *ks, st, nullptr);
@@ -438,12 +440,32 @@ hx_status hx_matmul_plan_set_mask(hx_context *ctx, hx_matmul_plan *plan, int i, 
     HX_TRY
     need(ctx && plan && coeffs && i >= 0 && i < (int)plan->masks.size(), "bad mask index");
     auto &m = plan->masks[i];
+    plan->bound_uid = 0;  // keys premasked with the old mask no longer apply
+    plan->premasked.clear();
     if (m.extended)
         upload_plaintext_ext(*ctx, nullptr, coeffs, m.limbs, m.pt->p);
     else
         upload_plaintext(*ctx, nullptr, coeffs, m.limbs, m.pt->p);
     return HX_OK;
     HX_END
+}
+
+hx_status hx_matmul_plan_bind_keys(hx_context *ctx, hx_matmul_plan *plan, const hx_keyset *ks, void *stream)
+{
+    HX_TRY
+    need(ctx && plan && ks && plan->ctx == ctx, "bad argument");
+    bind_plan_keys(*ctx, *plan, *ks, S(stream));
+    return HX_OK;
+    HX_END
+}
+
+int64_t hx_matmul_plan_bound_bytes(const hx_matmul_plan *plan)
+{
+    if (!plan) return HX_EINVAL;
+    int64_t b = 0;
+    for (auto &p : plan->premasked)
+        if (p) b += (int64_t)p->words * 8;
+    return b;
 }
 
 void hx_matmul_plan_destroy(hx_matmul_plan *plan)

@@ -299,7 +299,7 @@ Cts Eval::rotate_hoisted_one(const Cts &a, const BufPtr &D, int64_t k, const hx_
 }
 
 Cts Eval::hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, const uint64_t *v_ext, double v_scale,
-                      uint64_t c, const hx_keyset &keys)
+                      uint64_t c, const hx_keyset &keys, const uint64_t *premasked)
 {
     const int N = ctx.N, K = ctx.K, limbs = a.limbs, ext = limbs + K, nd = (limbs + K - 1) / K, B = a.B;
     const uint64_t g1 = galois_for_step(k1, ctx.log_n), g2 = galois_for_step(k2, ctx.log_n);
@@ -314,8 +314,11 @@ Cts Eval::hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, con
     const View c1{a.d + a.cstride(N), a.bstride(N), a.cstride(N)};
     DevBuf z((size_t)B * 2 * ext * N, s);
     View zv{z.p, (size_t)2 * ext * N, (size_t)ext * N};
-    launch_key_ip_mux(lc(), zv, D->p, c1.p, c1.bstride, key1.buf->p, key2.buf->p, v_ext, cs, ctx.n_all, ctx.n_q, K,
-                      limbs, nd, g1, g2, B);
+    if (premasked)
+        launch_key_ip_mux_pm(lc(), zv, D->p, c1.p, c1.bstride, premasked, ctx.n_q, K, limbs, nd, g1, g2, B);
+    else
+        launch_key_ip_mux(lc(), zv, D->p, c1.p, c1.bstride, key1.buf->p, key2.buf->p, v_ext, cs, ctx.n_all, ctx.n_q, K,
+                          limbs, nd, g1, g2, B);
     ntt_inplace(z.p, (size_t)ext * N, 2 * B, iota_vec(limbs, K), iota_vec(ctx.n_q, K), true);
     DevBuf conv((size_t)B * 2 * limbs * N, s);
     launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), limbs,

@@ -147,6 +147,15 @@ void launch_lintrans_mac(const LaunchCtx &c, const MacArgs &a, int B, int limbs,
 void launch_key_ip_mux(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
                        const uint64_t *key1, const uint64_t *key2, const uint64_t *v, const Scalars &cs, int n_all,
                        int n_q, int K, int limbs, int ndig, uint64_t g1, uint64_t g2, int B);
+// premasked keys of one selection: out = [2][ndig][2][ext][N] with
+// out[0] = v (.) key1, out[1] = (c - v) (.) key2 on the rows of the extended basis (Montgomery form);
+// cR[t] = c * 2^64 mod (prime of row t)
+void launch_premask_keys(const LaunchCtx &c, uint64_t *out, const uint64_t *key1, const uint64_t *key2,
+                         const uint64_t *v, const Scalars &cR, int n_all, int n_q, int K, int limbs, int ndig);
+// the inner products of a selection with premasked keys: z_h = sum_d sigma_g1(D_d) pk[0][d][h]
+// + sigma_g2(D_d) pk[1][d][h], one Montgomery reduction
+void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
+                          const uint64_t *pk, int n_q, int K, int limbs, int ndig, uint64_t g1, uint64_t g2, int B);
 void launch_moddown_final_mux(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
                               int limbs, View src, const uint64_t *v, const Scalars &cs, uint64_t g1, uint64_t g2);
 void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps,

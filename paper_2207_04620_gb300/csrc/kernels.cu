@@ -661,6 +661,60 @@ __global__ void k_key_ip_mux(View out, const uint64_t *__restrict__ D, const uin
     }
 }
 
+// premasked keys: rows t of the extended basis (Q_l then P), digits d < ndig
+__global__ void k_premask_keys(uint64_t *out, const uint64_t *__restrict__ key1, const uint64_t *__restrict__ key2,
+                               const uint64_t *__restrict__ v, const __grid_constant__ Scalars cR,
+                               const PrimeConst *__restrict__ primes, int n_all, int n_q, int K, int limbs, int ndig,
+                               int n)
+{
+    const int t = blockIdx.y, dh = blockIdx.z, d = dh / 2, h = dh % 2;
+    const int ext = limbs + K;
+    const int pr = t < limbs ? t : n_q + (t - limbs);
+    const PrimeConst P = primes[pr];
+    const size_t ko = ((size_t)d * 2 + h) * n_all * n + (size_t)pr * n;
+    uint64_t *o1 = out + (((size_t)d * 2 + h) * ext + t) * n;
+    uint64_t *o2 = o1 + (size_t)ndig * 2 * ext * n;
+    const uint64_t cr = cR.v[t];
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const uint64_t vv = v[(size_t)t * n + j], k1 = key1[ko + j], k2 = key2[ko + j];
+        const uint64_t w = submod(cr, vv, P.q);  // (c - v) in Montgomery form
+        o1[j] = mont128(__umul64hi(vv, k1), vv * k1, P);
+        o2[j] = mont128(__umul64hi(w, k2), w * k2, P);
+    }
+}
+
+__global__ void k_key_ip_mux_pm(View out, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt,
+                                size_t dnt_bstride, const uint64_t *__restrict__ pk,
+                                const PrimeConst *__restrict__ primes, int n_q, int K, int limbs, int ndig, uint64_t g1,
+                                uint64_t g2, int log_n)
+{
+    const int n = 1 << log_n;
+    const int t = blockIdx.y, bi = blockIdx.z;
+    const int ext = limbs + K;
+    const int pr = t < limbs ? t : n_q + (t - limbs);
+    const PrimeConst P = primes[pr];
+    const size_t dig_stride = (size_t)ext * n;
+    const uint64_t *Db = D + (size_t)bi * ndig * dig_stride;
+    const uint64_t *db = dnt + bi * dnt_bstride;
+    const int own_digit = t < limbs ? t / K : -1;
+    const size_t half = (size_t)ndig * 2 * ext * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int j1 = galois_src(j, g1, log_n), j2 = galois_src(j, g2, log_n);
+        Acc128 z0, z1;
+        for (int d = 0; d < ndig; d++) {
+            const uint64_t *row = (d == own_digit) ? db + (size_t)t * n : Db + d * dig_stride + (size_t)t * n;
+            const uint64_t a = row[j1], b = row[j2];
+            const size_t o = ((size_t)d * 2 * ext + t) * n + j;
+            z0.mac(a, pk[o]);
+            z0.mac(b, pk[half + o]);
+            z1.mac(a, pk[o + dig_stride]);
+            z1.mac(b, pk[half + o + dig_stride]);
+        }
+        out.p[bi * out.bstride + (size_t)t * n + j] = mont128(z0.hi, z0.lo, P);
+        out.p[bi * out.bstride + out.cstride + (size_t)t * n + j] = mont128(z1.hi, z1.lo, P);
+    }
+}
+
 // ModDown epilogue of k_key_ip_mux: out_h = (z_h - conv_h) * P^-1, plus for h = 0
 // c*sigma_g2(c0) + v*(sigma_g1(c0) - sigma_g2(c0))
 __global__ void k_moddown_final_mux(View out, View acc, View conv, const ModDownTable *__restrict__ tab,
@@ -1040,6 +1094,25 @@ void launch_key_ip_mux(const LaunchCtx &c, View out, const uint64_t *D, const ui
     dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
     k_key_ip_mux<<<grid, 256, 0, c.stream>>>(out, D, dnt, dnt_bstride, key1, key2, v, cs, c.t->primes, n_all, n_q, K,
                                              limbs, ndig, g1, g2, c.log_n);
+    post(c);
+}
+
+void launch_premask_keys(const LaunchCtx &c, uint64_t *out, const uint64_t *key1, const uint64_t *key2,
+                         const uint64_t *v, const Scalars &cR, int n_all, int n_q, int K, int limbs, int ndig)
+{
+    dim3 grid(ew_blocks(c.N, 1), limbs + K, ndig * 2);
+    k_premask_keys<<<grid, 256, 0, c.stream>>>(out, key1, key2, v, cR, c.t->primes, n_all, n_q, K, limbs, ndig, c.N);
+    post(c);
+}
+
+void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
+                          const uint64_t *pk, int n_q, int K, int limbs, int ndig, uint64_t g1, uint64_t g2, int B)
+{
+    Timed tm_(c, K_KEYIP, 8.0 * c.N * ((double)B * ndig * (limbs + K) + 4.0 * ndig * (limbs + K) +
+                                        2.0 * B * (limbs + K)));
+    dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
+    k_key_ip_mux_pm<<<grid, 256, 0, c.stream>>>(out, D, dnt, dnt_bstride, pk, c.t->primes, n_q, K, limbs, ndig, g1, g2,
+                                                c.log_n);
     post(c);
 }
 

@@ -77,6 +77,7 @@ struct hx_context {
 
 struct hx_keyset {
     hx_context *ctx = nullptr;
+    uint64_t uid = 0;  // unique per keyset of the process (plans bound to keys check it)
     int n_parties = 0;
     uint64_t seed = 0;
     std::vector<std::vector<int64_t>> s_parts;  // ternary shares
@@ -120,6 +121,10 @@ struct hx_matmul_plan {
     };
     std::vector<Mask> masks;
     std::map<std::pair<int, int>, int> index;
+    // Step 2 selection folded into the rotation keys of one keyset (optional):
+    // premasked[k] = [2][ndig][2][ext][N], v_k * swk(k) and (c - v_k) * swk(k-h)
+    uint64_t bound_uid = 0;
+    std::vector<hx::BufPtr> premasked;
 };
 
 namespace hx {
@@ -153,9 +158,10 @@ struct Eval {
     Cts rotate_hoisted_one(const Cts &a, const BufPtr &D, int64_t k, const hx_keyset &keys);
     // v . Rot(a, k1) + (1 - v) . Rot(a, k2) from the ModUp D of a; the selection is applied in
     // the extended basis before one ModDown; v_ext: mask over Q_l then P (Montgomery), encoded
-    // at scale v_scale whose integer value is c
+    // at scale v_scale whose integer value is c.  premasked (optional): the two rotation keys
+    // already multiplied by v and c - v (premask_keys), so the inner product gives the selection
     Cts hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, const uint64_t *v_ext, double v_scale,
-                    uint64_t c, const hx_keyset &keys);
+                    uint64_t c, const hx_keyset &keys, const uint64_t *premasked = nullptr);
     void check_same(const Cts &a, const Cts &b);
 
     // hybrid key switching pieces
@@ -202,6 +208,8 @@ Cts transpose_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &
 std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs, int t = 0);  // t = 0: t = h
 Cts matmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &A, const Cts &B,
                  cudaStream_t s, int t = 0);  // t < h: the cut k-sum of the rectangular product
+// folds the Step 2 selection masks of plan into copies of the rotation keys of ks
+void bind_plan_keys(hx_context &ctx, hx_matmul_plan &plan, const hx_keyset &ks, cudaStream_t s);
 Cts rmatmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &At, const Cts &B, int t,
                   cudaStream_t s);
 // refresh randomness of entry b: SplitMix64 streams keyed by refresh_seeds[b] (tag 1 + refresh index)

@@ -317,7 +317,8 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
         Cts Bk = ev.rotate_hoisted_one(B0, DB, (int64_t)beta * h * k, ks);
         double sc;
         const uint64_t *v = mask_pt(p, 2, k, &sc);
-        Cts Ak = ev.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, qt, ks);
+        const uint64_t *pm = (p.bound_uid && p.bound_uid == ks.uid) ? p.premasked[k]->p : nullptr;
+        Cts Ak = ev.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, qt, ks, pm);
         ev.tensor_acc(acc, Ak, Bk);
     }
     // Step 3: one relinearisation, then the two rescales
@@ -376,6 +377,38 @@ Cts matmul_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &pla
     HX_CHECK(A.scale == B.scale, HX_ESCALE, "inputs must share the scale");
     Eval ev(ctx, s);
     return plan.alg3 ? matmul_alg3(ev, ks, plan, A, B, t) : matmul_depth2(ev, ks, plan, A, B, t);
+}
+
+void bind_plan_keys(hx_context &ctx, hx_matmul_plan &plan, const hx_keyset &ks, cudaStream_t s)
+{
+    HX_CHECK(plan.kind == 0 && plan.alg3, HX_EINVAL, "only Alg. 3 product plans select in Step 2");
+    HX_CHECK(ks.ctx == &ctx && ks.uid, HX_EINVAL, "keys from another context");
+    const int h = plan.h, beta = plan.beta, K = ctx.K, limbs = plan.limbs - 1;  // A0's level
+    const int ext = limbs + K, nd = (limbs + K - 1) / K;
+    const size_t N = ctx.N;
+    Eval ev(ctx, s);
+    std::vector<BufPtr> pm(h);
+    for (int k = 1; k < h; k++) {
+        const uint64_t g1 = galois_for_step((int64_t)beta * k, ctx.log_n);
+        const uint64_t g2 = galois_for_step((int64_t)beta * (k - h), ctx.log_n);
+        auto it1 = ks.rot.find(g1), it2 = ks.rot.find(g2);
+        HX_CHECK(it1 != ks.rot.end() && it2 != ks.rot.end(), HX_EKEY, "missing Galois key for Step 2");
+        double sc;
+        const uint64_t *v = mask_pt(plan, 2, k, &sc);
+        const uint64_t c = ctx.primes[limbs - 1];
+        Scalars cR;
+        for (int t = 0; t < ext; t++) {
+            const uint64_t q = ctx.primes[t < limbs ? t : ctx.n_q + (t - limbs)];
+            cR.v[t] = (uint64_t)(((u128)(c % q) << 64) % q);
+            cR.sh[t] = 0;
+        }
+        pm[k] = std::make_shared<DevBuf>((size_t)2 * nd * 2 * ext * N, true);
+        launch_premask_keys(ev.lc(), pm[k]->p, it1->second.buf->p, it2->second.buf->p, v, cR, ctx.n_all, ctx.n_q, K,
+                            limbs, nd);
+    }
+    HX_CUDA(cudaStreamSynchronize(s));
+    plan.premasked = std::move(pm);
+    plan.bound_uid = ks.uid;
 }
 
 // App. D, Alg. "41": A~ packs h/t vertical copies of a t x h matrix; the k-sum

@@ -82,6 +82,8 @@ _SIGS = {
     "hx_matmul_rotation_steps": (c_int, [c_vp, c_int, c_int, P_i32, c_int]),
     "hx_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, PP, c_vp]),
     "hx_matmul_batch": (c_int, [c_vp, c_vp, c_vp, PP, PP, c_int, c_size_t, PP, c_vp]),
+    "hx_matmul_plan_bind_keys": (c_int, [c_vp, c_vp, c_vp, c_vp]),
+    "hx_matmul_plan_bound_bytes": (c_i64, [c_vp]),
     "hx_rmatmul_batch": (c_int, [c_vp, c_vp, c_vp, PP, PP, c_int, c_int, c_size_t, PP, c_vp]),
     "hx_rmatmul_rotation_steps": (c_int, [c_vp, c_int, c_int, c_int, P_i32, c_int]),
     "hx_transpose_plan_create": (c_int, [c_vp, c_int, c_int, PP]),
@@ -394,6 +396,14 @@ def hx_matmul_plan_num_masks(plan: int) -> int:
 def hx_matmul_plan_set_mask(ctx: int, plan: int, i: int, coeffs) -> None:
     m = np.ascontiguousarray(np.asarray(coeffs, dtype=np.int64))
     _chk(lib().hx_matmul_plan_set_mask(ctx, plan, i, _i64p(m)))
+
+
+def hx_matmul_plan_bind_keys(ctx: int, plan: int, ks: int, stream=None) -> None:
+    _chk(lib().hx_matmul_plan_bind_keys(ctx, plan, ks, _stream(stream)))
+
+
+def hx_matmul_plan_bound_bytes(plan: int) -> int:
+    return int(lib().hx_matmul_plan_bound_bytes(plan))
 
 
 def hx_matmul_plan_destroy(plan: int) -> None:

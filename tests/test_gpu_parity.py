@@ -587,6 +587,12 @@ def test_matmul_graph_executor_equals_batched_call():
         for i in range(2):
             assert np.array_equal(host_out[i].numpy().view(np.uint64), want[i])
         hx.hx_matmul_exec_destroy(ex)
+        # keys premasked with the plan's Step 2 selection: the same residues
+        hx.hx_matmul_plan_bind_keys(pr.ctx, plan, pr.ks)
+        assert hx.hx_matmul_plan_bound_bytes(plan) > 0
+        for g, w in zip(hx.hx_matmul_batch(pr.ctx, pr.ks, plan, A, B, h), want):
+            assert np.array_equal(hx.hx_ct_export(pr.ctx, g), w)
+            hx.hx_ct_destroy(g)
         hx.hx_matmul_plan_destroy(plan)
     finally:
         pr.close()
