@@ -292,6 +292,15 @@ def run_hx(args, world, rank, local):
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "launches": n_launch, "avg_launch_us": round(dom_ms / n_launch * 1e3, 2),
                 "alg_bytes_per_launch": dom_bytes / n_launch}
+    if dom == "ntt":
+        # the integer-issue ceiling beside it: one Shoup product per butterfly, log2(N)/32
+        # butterflies per algorithmic byte (N/2 log2 N butterflies per 16 N bytes)
+        shoup_s, mac_s = hx.hx_alu_calibrate(ctx, stream=stream)
+        bfly_s = achieved * 1e9 * LOG_N / 32.0
+        roofline["alu"] = {"butterflies_per_s": round(bfly_s / 1e9, 1), "shoup_products_per_s": round(shoup_s / 1e9, 1),
+                           "unit": "G/s", "frac": round(bfly_s / shoup_s, 4),
+                           "mac128_per_s": round(mac_s / 1e9, 1),
+                           "what": "measured on this GPU by hx_alu_calibrate (8 independent chains per thread)"}
 
     # end to end through the C ABI with host buffers: every step copies its input
     # ciphertexts from page-locked host memory, replays the graph and copies its
@@ -713,12 +722,17 @@ def run_micro(args):
         iv.append(e[1].elapsed_time(e[2]))
     byt = 16.0 * polys * per * n
     peak, kind = peaks()
+    shoup_s, _ = hx.hx_alu_calibrate(ctx, stream=stream)
     res = {"micro": "ntt", "log_n": log_n, "rows": polys * per, "bytes_per_transform": byt, "tiles": tiles,
            "fwd_ms": statistics.median(fw), "inv_ms": statistics.median(iv),
            "fwd_gbs": byt / statistics.median(fw) / 1e6, "inv_gbs": byt / statistics.median(iv) / 1e6,
            "peak_gbs": peak, "peak_kind": kind}
     res["fwd_frac"] = res["fwd_gbs"] / peak
     res["inv_frac"] = res["inv_gbs"] / peak
+    # integer-issue ceiling: butterflies/s against measured Shoup products/s
+    res["shoup_products_per_s"] = shoup_s
+    res["fwd_alu_frac"] = res["fwd_gbs"] * 1e9 * log_n / 32.0 / shoup_s
+    res["inv_alu_frac"] = res["inv_gbs"] * 1e9 * log_n / 32.0 / shoup_s
     print(json.dumps(res), flush=True)
     hx.hx_context_destroy(ctx)
 

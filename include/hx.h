@@ -378,6 +378,15 @@ int hx_server_stats(hx_server *sv, uint64_t *out, int cap);
 /* waits for every submitted request, then stops the threads */
 void hx_server_destroy(hx_server *sv);
 
+/* ---- ALU calibration ------------------------------------------------------------ */
+/* Measured throughput on this device of the two 64-bit multiplication forms
+ * the path is built from: Shoup products y*w - umulhi(y, w')*q (one per NTT
+ * butterfly) and 64x64 -> 128-bit multiply-accumulates (one per key inner
+ * product term), eight independent chains per thread on every SM.  These are
+ * the ceilings of the integer-issue-bound kernels, reported beside the HBM
+ * roofline. */
+hx_status hx_alu_calibrate(hx_context *ctx, double *shoup_per_s, double *mac_per_s, void *stream);
+
 /* ---- counters -------------------------------------------------------------- */
 /* Operation counters since the last reset, in this order: Add, Mul_pt,
  * Rot (full), Rot (hoisted), Mul_ct, KeySwitch, ModUp, Rescale, Refresh,

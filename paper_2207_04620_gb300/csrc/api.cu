@@ -809,6 +809,16 @@ hx_status hx_dbootstrap(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, u
     HX_END
 }
 
+hx_status hx_alu_calibrate(hx_context *ctx, double *shoup_per_s, double *mac_per_s, void *stream)
+{
+    HX_TRY
+    need(ctx && shoup_per_s && mac_per_s, "null argument");
+    Eval ev(*ctx, S(stream));
+    alu_calibrate(ev.lc(), ctx->primes[0], shoup_per_s, mac_per_s);
+    return HX_OK;
+    HX_END
+}
+
 int hx_counters(const hx_context *ctx, uint64_t *out, int cap)
 {
     if (!ctx) return HX_EINVAL;

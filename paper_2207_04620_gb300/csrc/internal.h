@@ -156,6 +156,8 @@ void launch_premask_keys(const LaunchCtx &c, uint64_t *out, const uint64_t *key1
 // + sigma_g2(D_d) pk[1][d][h], one Montgomery reduction
 void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
                           const uint64_t *pk, int n_q, int K, int limbs, int ndig, uint64_t g1, uint64_t g2, int B);
+// measured rates of Shoup products and 128-bit multiply-accumulates on every SM (per second)
+void alu_calibrate(const LaunchCtx &c, uint64_t q, double *shoup_per_s, double *mac_per_s);
 void launch_moddown_final_mux(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
                               int limbs, View src, const uint64_t *v, const Scalars &cs, uint64_t g1, uint64_t g2);
 void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps,

@@ -715,6 +715,46 @@ __global__ void k_key_ip_mux_pm(View out, const uint64_t *__restrict__ D, const 
     }
 }
 
+// ALU calibration: chains of Shoup products (the NTT butterfly's multiplication)
+// and of 64x64 -> 128-bit multiply-accumulates (the key inner product's), eight
+// independent chains per thread, every SM busy; the results are written so the
+// work is kept.
+__global__ void k_calib_shoup(uint64_t *out, int iters, uint64_t q, uint64_t w, uint64_t wsh)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t y[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) y[c] = (uint64_t)t * 8 + c;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) y[c] = shoup_lazy(y[c], w, wsh, q) + (uint64_t)c;
+    }
+    uint64_t x = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) x ^= y[c];
+    out[t] = x;
+}
+
+__global__ void k_calib_mac(uint64_t *out, int iters, uint64_t k0, uint64_t k1)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    uint64_t x[8];
+    Acc128 acc[8];
+#pragma unroll
+    for (int c = 0; c < 8; c++) x[c] = (uint64_t)t * 8 + c + 1;
+    for (int i = 0; i < iters; i++) {
+#pragma unroll
+        for (int c = 0; c < 8; c++) {
+            acc[c].mac(x[c], (i & 1) ? k1 : k0);
+            x[c] ^= acc[c].lo >> 7;
+        }
+    }
+    uint64_t r = 0;
+#pragma unroll
+    for (int c = 0; c < 8; c++) r ^= acc[c].lo ^ acc[c].hi;
+    out[t] = r;
+}
+
 // ModDown epilogue of k_key_ip_mux: out_h = (z_h - conv_h) * P^-1, plus for h = 0
 // c*sigma_g2(c0) + v*(sigma_g1(c0) - sigma_g2(c0))
 __global__ void k_moddown_final_mux(View out, View acc, View conv, const ModDownTable *__restrict__ tab,
@@ -1114,6 +1154,32 @@ void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const
     k_key_ip_mux_pm<<<grid, 256, 0, c.stream>>>(out, D, dnt, dnt_bstride, pk, c.t->primes, n_q, K, limbs, ndig, g1, g2,
                                                 c.log_n);
     post(c);
+}
+
+void alu_calibrate(const LaunchCtx &c, uint64_t q, double *shoup_per_s, double *mac_per_s)
+{
+    const int blocks = c.t->n_sm * 8, threads = 256, iters = 1024;
+    uint64_t *buf = nullptr;
+    HX_CUDA(cudaMallocAsync(&buf, sizeof(uint64_t) * blocks * threads, c.stream));
+    cudaEvent_t e[3];
+    for (auto &x : e) HX_CUDA(cudaEventCreate(&x));
+    const uint64_t w = (q >> 1) | 1, wsh = (uint64_t)(((unsigned __int128)w << 64) / q);
+    k_calib_shoup<<<blocks, threads, 0, c.stream>>>(buf, 16, q, w, wsh);  // warm-up
+    k_calib_mac<<<blocks, threads, 0, c.stream>>>(buf, 16, w, wsh);
+    HX_CUDA(cudaEventRecord(e[0], c.stream));
+    k_calib_shoup<<<blocks, threads, 0, c.stream>>>(buf, iters, q, w, wsh);
+    HX_CUDA(cudaEventRecord(e[1], c.stream));
+    k_calib_mac<<<blocks, threads, 0, c.stream>>>(buf, iters, w, wsh);
+    HX_CUDA(cudaEventRecord(e[2], c.stream));
+    HX_CUDA(cudaEventSynchronize(e[2]));
+    float ms1 = 0, ms2 = 0;
+    HX_CUDA(cudaEventElapsedTime(&ms1, e[0], e[1]));
+    HX_CUDA(cudaEventElapsedTime(&ms2, e[1], e[2]));
+    for (auto &x : e) cudaEventDestroy(x);
+    HX_CUDA(cudaFreeAsync(buf, c.stream));
+    const double ops = 8.0 * blocks * threads * iters;
+    *shoup_per_s = ops / (ms1 * 1e-3);
+    *mac_per_s = ops / (ms2 * 1e-3);
 }
 
 void launch_moddown_final_mux(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,

@@ -100,6 +100,7 @@ _SIGS = {
     "hx_dense_layer": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, PP, PP, PP, c_int, c_int, c_int, c_int, c_int, c_double,
                                 c_u64, PP, PP, PP, c_vp]),
     "hx_dense_rotation_steps": (c_int, [c_vp, c_int, P_i32, c_int]),
+    "hx_alu_calibrate": (c_int, [c_vp, P_dbl, P_dbl, c_vp]),
     "hx_aggregate": (c_int, [c_vp, PP, c_size_t, PP, c_size_t, c_double, PP, c_vp]),
     "hx_dkeyswitch": (c_int, [c_vp, c_vp, c_vp, c_vp, c_u64, PP, c_vp]),
     "hx_dbootstrap": (c_int, [c_vp, c_vp, c_vp, c_u64, PP, c_vp]),
@@ -609,6 +610,13 @@ def hx_server_destroy(sv: int) -> None:
 
 
 # ---- counters ------------------------------------------------------------------------
+
+def hx_alu_calibrate(ctx: int, stream=None):
+    """(Shoup products per second, 128-bit multiply-accumulates per second) measured on the device."""
+    a, b = c_double(), c_double()
+    _chk(lib().hx_alu_calibrate(ctx, ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+    return a.value, b.value
+
 
 def hx_counters(ctx: int) -> dict:
     buf = np.zeros(16, dtype=np.uint64)
