@@ -285,7 +285,7 @@ def run_hx(args, world, rank, local):
         with open(tfile) as f:
             tj = json.load(f)
         ent = tj.get(dom)
-        if ent and ent.get("kernels_sha") == sha_of(os.path.join(ROOT, "paper_2207_04620_gb300", "csrc", "kernels.cu")):
+        if ent and ent.get("kernels_sha") == sha_of(os.path.join(ROOT, "paper_2207_04620_gb300", "csrc", "ntt.cu")):
             # captured on a smaller launch of the same kernel; traffic grows with the residues processed
             traffic = round(ent["dram_bytes_per_alg_byte"] * dom_bytes / n_launch)
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",

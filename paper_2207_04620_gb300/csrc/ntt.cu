@@ -1,0 +1,410 @@
+// The negacyclic NTT of one limb = Cooley-Tukey (forward, natural ->
+// bit-reversed order, psi powers merged into the twiddles) and
+// Gentleman-Sande (inverse), split into a column phase (the first log2(N1)
+// stages: N1 rows of stride N2) and a row phase (the remaining stages on N2
+// contiguous words), each staged through shared memory.  Every global word is
+// read and written once per phase with 128-byte coalesced row segments.
+#include <algorithm>
+#include <cstdio>
+#include <memory>
+
+#include "launch_util.cuh"
+
+namespace hx {
+
+namespace {
+
+// ---- NTT ----------------------------------------------------------------------
+//
+// A phase holds, in shared memory, n_sub independent sub-transforms of M = 2^L
+// points (element e of sub-transform k at sh[k*sk + e*se (+ e/16 padding)]).
+// Its L local stages run as two register passes: each thread loads 2^R
+// elements spaced t = M >> (S0+R) apart, applies R radix-2 stages in
+// registers (2^R - 1 twiddle loads for R*2^(R-1) butterflies) and stores them
+// back.  Global stage of local stage s is g0 + s; the twiddle of a butterfly
+// at global stage G on global element j is tw[2^G + (j >> (log N - G))].
+
+__device__ __forceinline__ void bf_ct(uint64_t &x, uint64_t &y, const ulonglong2 w, uint64_t q, uint64_t two_q)
+{
+    uint64_t a = x;
+    if (a >= two_q) a -= two_q;
+    const uint64_t t = shoup_lazy(y, w.x, w.y, q);
+    x = a + t;
+    y = a - t + two_q;
+}
+
+__device__ __forceinline__ void bf_gs(uint64_t &x, uint64_t &y, const ulonglong2 w, uint64_t q, uint64_t two_q)
+{
+    uint64_t u = x + y;
+    if (u >= two_q) u -= two_q;
+    const uint64_t d = x - y + two_q;
+    x = u;
+    y = shoup_lazy(d, w.x, w.y, q);
+}
+
+template <int L, int R, int S0, bool INV, bool KFAST, bool PAD>
+__device__ __forceinline__ void ntt_pass(uint64_t *sh, int n_sub, int sk, int se, const ulonglong2 *__restrict__ tw,
+                                         int g0, int blk0, int blk_step, uint64_t q, int nthr)
+{
+    constexpr int M = 1 << L, RR = 1 << R, TL = M >> (S0 + R), ITEMS = M >> R;
+    const uint64_t two_q = 2 * q;
+    for (int w = threadIdx.x; w < ITEMS * n_sub; w += nthr) {
+        const int k = KFAST ? w % n_sub : w / ITEMS;
+        const int u = KFAST ? w / n_sub : w % ITEMS;
+        const int hi = u / TL, lo = u % TL;
+        const int base = hi * TL * RR + lo;
+        const int blk = blk0 + k * blk_step;
+        uint64_t v[RR];
+#pragma unroll
+        for (int m = 0; m < RR; m++) {
+            const int e = base + m * TL;
+            v[m] = sh[k * sk + e * se + (PAD ? (e >> 4) : 0)];
+        }
+        if (!INV) {
+#pragma unroll
+            for (int vv = 0; vv < R; vv++) {
+                const int s = S0 + vv, half = RR >> (vv + 1);
+                const int tbase = (1 << (g0 + s)) + (blk << s) + (hi << vv);
+#pragma unroll
+                for (int gl = 0; gl < (1 << vv); gl++) {
+                    const ulonglong2 wv = tw[tbase + gl];
+#pragma unroll
+                    for (int j = 0; j < half; j++) bf_ct(v[gl * 2 * half + j], v[gl * 2 * half + j + half], wv, q, two_q);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int vv = R - 1; vv >= 0; vv--) {
+                const int s = S0 + vv, half = RR >> (vv + 1);
+                const int tbase = (1 << (g0 + s)) + (blk << s) + (hi << vv);
+#pragma unroll
+                for (int gl = 0; gl < (1 << vv); gl++) {
+                    const ulonglong2 wv = tw[tbase + gl];
+#pragma unroll
+                    for (int j = 0; j < half; j++) bf_gs(v[gl * 2 * half + j], v[gl * 2 * half + j + half], wv, q, two_q);
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < RR; m++) {
+            const int e = base + m * TL;
+            sh[k * sk + e * se + (PAD ? (e >> 4) : 0)] = v[m];
+        }
+    }
+}
+
+template <int L> struct Split {
+    static constexpr int R1 = (L + 1) / 2;  // first pass (stages 0..R1-1)
+    static constexpr int R2 = L - R1;       // second pass
+};
+
+// Asynchronous global->shared copies (cp.async): the next tile streams in while
+// the current one is transformed.
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all_but_one() { asm volatile("cp.async.wait_group 1;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+// tile t of a phase -> (group, row, position along the row)
+struct TileId {
+    int g, row, bx;
+};
+__device__ __forceinline__ TileId tile_of(int t, int nb, int n_rows)
+{
+    TileId r;
+    r.bx = t % nb;
+    const int rest = t / nb;
+    r.row = rest % n_rows;
+    r.g = rest / n_rows;
+    return r;
+}
+
+// column phase: the first LOGM stages on M rows of stride N2 (COLS adjacent columns
+// per tile); each block loops over tiles with the next tile (and its twiddles,
+// indices below M) prefetched into the other half of shared memory
+template <int LOGM, int COLS, bool INV>
+__global__ void __launch_bounds__((1 << (LOGM - Split<LOGM>::R1)) * COLS)
+k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
+           const ulonglong2 *__restrict__ tw_all, int log_n, int n_tiles)
+{
+    constexpr int M = 1 << LOGM, E = M * COLS, R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
+    constexpr int T = (M >> R1) * COLS;
+    extern __shared__ uint64_t sh[];
+    uint64_t *buf[2] = {sh, sh + E};
+    ulonglong2 *stw[2] = {reinterpret_cast<ulonglong2 *>(sh + 2 * E), reinterpret_cast<ulonglong2 *>(sh + 2 * E) + M};
+    const int N = 1 << log_n, N2 = N >> LOGM, nb = N2 / COLS;
+    auto prefetch = [&](int t, int slot) {
+        const TileId id = tile_of(t, nb, R.n_rows);
+        const int pr = R.prime[id.row];
+        const uint64_t *src = INV ? R.dst + (size_t)id.g * R.dst_gs + (size_t)R.dst_off[id.row] * N
+                                  : R.src + (size_t)id.g * R.src_gs + (size_t)R.src_off[id.row] * N;
+        const int c0 = id.bx * COLS;
+        for (int i = threadIdx.x; i < E / 2; i += T) {  // 16-byte pieces of COLS-word row segments
+            const int r = (2 * i) / COLS, c = (2 * i) % COLS;
+            cp_async16(buf[slot] + 2 * i, src + (size_t)r * N2 + c0 + c);
+        }
+        const ulonglong2 *tw = tw_all + (size_t)pr * N;
+        for (int i = threadIdx.x; i < M; i += T) cp_async16(stw[slot] + i, tw + i);
+        cp_async_commit();
+    };
+    int t = blockIdx.x, slot = 0;
+    if (t < n_tiles) prefetch(t, 0);
+    for (; t < n_tiles; t += gridDim.x, slot ^= 1) {
+        const int tn = t + gridDim.x;
+        if (tn < n_tiles) {
+            prefetch(tn, slot ^ 1);
+            cp_async_wait_all_but_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const TileId id = tile_of(t, nb, R.n_rows);
+        const PrimeConst P = primes[R.prime[id.row]];
+        uint64_t *dst = R.dst + (size_t)id.g * R.dst_gs + (size_t)R.dst_off[id.row] * N;
+        const int c0 = id.bx * COLS;
+        uint64_t *b = buf[slot];
+        if (!INV) {
+            ntt_pass<LOGM, R1, 0, false, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
+            __syncthreads();
+            ntt_pass<LOGM, R2, R1, false, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
+            __syncthreads();
+            for (int i = threadIdx.x; i < E; i += T) dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = b[i];
+        } else {
+            ntt_pass<LOGM, R2, R1, true, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
+            __syncthreads();
+            ntt_pass<LOGM, R1, 0, true, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
+            __syncthreads();
+            for (int i = threadIdx.x; i < E; i += T)
+                dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = shoup(b[i], P.n_inv, P.n_inv_sh, P.q);
+        }
+        __syncthreads();  // this half is refilled by the prefetch two tiles later
+    }
+}
+
+// row phase: the remaining LOGM stages on ROWS contiguous blocks of M words per tile
+// (padded layout, one spare word per 16), next tile prefetched in 8-byte pieces
+template <int LOGM, int ROWS, bool INV>
+__global__ void __launch_bounds__((1 << (LOGM - Split<LOGM>::R1)) * ROWS)
+k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
+           const ulonglong2 *__restrict__ tw_all, int log_n, int n_tiles)
+{
+    constexpr int M = 1 << LOGM, E = M * ROWS, R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
+    constexpr int T = (M >> R1) * ROWS;
+    constexpr int SK = M + M / 16;  // padded block stride
+    extern __shared__ uint64_t sh[];
+    uint64_t *buf[2] = {sh, sh + ROWS * SK};
+    const int N = 1 << log_n;
+    const int g0 = log_n - LOGM;
+    const int nb = (N >> LOGM) / ROWS;
+    auto prefetch = [&](int t, int slot) {
+        const TileId id = tile_of(t, nb, R.n_rows);
+        const uint64_t *src = INV ? R.src + (size_t)id.g * R.src_gs + (size_t)R.src_off[id.row] * N
+                                  : R.dst + (size_t)id.g * R.dst_gs + (size_t)R.dst_off[id.row] * N;
+        const size_t base = (size_t)id.bx * ROWS * M;
+        for (int i = threadIdx.x; i < E; i += T) {
+            const int k = i / M, e = i % M;
+            cp_async8(buf[slot] + k * SK + e + (e >> 4), src + base + i);
+        }
+        cp_async_commit();
+    };
+    int t = blockIdx.x, slot = 0;
+    if (t < n_tiles) prefetch(t, 0);
+    for (; t < n_tiles; t += gridDim.x, slot ^= 1) {
+        const int tn = t + gridDim.x;
+        if (tn < n_tiles) {
+            prefetch(tn, slot ^ 1);
+            cp_async_wait_all_but_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const TileId id = tile_of(t, nb, R.n_rows);
+        const int pr = R.prime[id.row];
+        const PrimeConst P = primes[pr];
+        const uint64_t q = P.q, two_q = 2 * q;
+        const ulonglong2 *tw = tw_all + (size_t)pr * N;
+        uint64_t *dst = R.dst + (size_t)id.g * R.dst_gs + (size_t)R.dst_off[id.row] * N;
+        const int r_base = id.bx * ROWS;
+        const size_t base = (size_t)r_base * M;
+        uint64_t *b = buf[slot];
+        if (!INV) {
+            ntt_pass<LOGM, R1, 0, false, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+            __syncthreads();
+            ntt_pass<LOGM, R2, R1, false, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+            __syncthreads();
+            for (int i = threadIdx.x; i < E; i += T) {
+                const int k = i / M, e = i % M;
+                uint64_t v = b[k * SK + e + (e >> 4)];
+                if (v >= two_q) v -= two_q;
+                if (v >= q) v -= q;
+                dst[base + i] = v;
+            }
+        } else {
+            ntt_pass<LOGM, R2, R1, true, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+            __syncthreads();
+            ntt_pass<LOGM, R1, 0, true, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
+            __syncthreads();
+            for (int i = threadIdx.x; i < E; i += T) {
+                const int k = i / M, e = i % M;
+                dst[base + i] = b[k * SK + e + (e >> 4)];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// tile widths the autotuner chooses from (sub-transforms per block)
+constexpr int kNttTiles[NTT_VARIANTS] = {8, 16, 32};
+
+template <int LOGM, int COLS, bool INV>
+void ntt_cols_w(const LaunchCtx &c, const NttRows &rows)
+{
+    constexpr int M = 1 << LOGM;
+    constexpr int E = M * COLS;
+    constexpr int T = (M >> Split<LOGM>::R1) * COLS;
+    const int N2 = c.N >> LOGM;
+    HX_CHECK(N2 % COLS == 0, HX_EINVAL, "NTT tile wider than the ring");
+    const long long n_tiles = (long long)(N2 / COLS) * rows.n_rows * rows.n_groups;
+    HX_CHECK(n_tiles < (1ll << 31), HX_EINVAL, "NTT batch too large");
+    const size_t smem = (size_t)E * 16 + (size_t)M * 32;  // two tiles + two twiddle sets
+    static const bool attr =  // thread-safe one-time setup
+        cudaFuncSetAttribute(k_ntt_cols<LOGM, COLS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+        cudaSuccess;
+    (void)attr;
+    static const int per_sm = [&] {
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_ntt_cols<LOGM, COLS, INV>, T, smem);
+        return v;
+    }();
+    const int grid = (int)std::min<long long>(n_tiles, (long long)std::max(1, per_sm) * c.t->n_sm);
+    k_ntt_cols<LOGM, COLS, INV><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
+                                                            c.log_n, (int)n_tiles);
+}
+
+template <int LOGM, int ROWS, bool INV>
+void ntt_rows_w(const LaunchCtx &c, const NttRows &rows)
+{
+    constexpr int M = 1 << LOGM;
+    constexpr int T = (M >> Split<LOGM>::R1) * ROWS;
+    const int N1 = c.N >> LOGM;
+    HX_CHECK(N1 % ROWS == 0, HX_EINVAL, "NTT tile wider than the ring");
+    const long long n_tiles = (long long)(N1 / ROWS) * rows.n_rows * rows.n_groups;
+    HX_CHECK(n_tiles < (1ll << 31), HX_EINVAL, "NTT batch too large");
+    const size_t smem = (size_t)ROWS * (M + M / 16) * 16;  // two tiles
+    static const bool attr =  // thread-safe one-time setup
+        cudaFuncSetAttribute(k_ntt_rows<LOGM, ROWS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+        cudaSuccess;
+    (void)attr;
+    static const int per_sm = [&] {
+        int v = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_ntt_rows<LOGM, ROWS, INV>, T, smem);
+        return v;
+    }();
+    const int grid = (int)std::min<long long>(n_tiles, (long long)std::max(1, per_sm) * c.t->n_sm);
+    k_ntt_rows<LOGM, ROWS, INV><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
+                                                            c.log_n, (int)n_tiles);
+}
+
+template <bool INV, int LOGM>
+void ntt_phase_l(const LaunchCtx &c, const NttRows &r, bool cols, int var)
+{
+    // the tile must not be wider than the other dimension of the ring
+    const int other = c.N >> LOGM;
+    while (var > 0 && kNttTiles[var] > other) var--;
+    if (cols) {
+        if (var == 0) ntt_cols_w<LOGM, 8, INV>(c, r);
+        else if (var == 1) ntt_cols_w<LOGM, 16, INV>(c, r);
+        else ntt_cols_w<LOGM, 32, INV>(c, r);
+    } else {
+        if (var == 0) ntt_rows_w<LOGM, 8, INV>(c, r);
+        else if (var == 1) ntt_rows_w<LOGM, 16, INV>(c, r);
+        else ntt_rows_w<LOGM, 32, INV>(c, r);
+    }
+}
+
+template <bool INV>
+void ntt_phase(const LaunchCtx &c, const NttRows &r, bool cols, int logm, int var)
+{
+    switch (logm) {
+    case 5: ntt_phase_l<INV, 5>(c, r, cols, var); break;
+    case 6: ntt_phase_l<INV, 6>(c, r, cols, var); break;
+    case 7: ntt_phase_l<INV, 7>(c, r, cols, var); break;
+    case 8: ntt_phase_l<INV, 8>(c, r, cols, var); break;
+    default: throw Error{HX_EINVAL, "unsupported NTT size"};
+    }
+}
+
+} // namespace
+
+void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse)
+{
+    Timed tm_(c, K_NTT, 16.0 * rows.n_rows * rows.n_groups * c.N);
+    if (rows.n_rows <= 0 || rows.n_groups <= 0) return;
+    HX_CHECK(rows.n_rows <= MAX_NTT_ROWS && rows.n_groups < 65536, HX_EINVAL, "NTT batch too large");
+    const int logm1 = c.log_n / 2, logm2 = c.log_n - logm1;
+    const int *v = c.t->ntt_var;
+    if (!inverse) {
+        ntt_phase<false>(c, rows, true, logm1, v[0]);
+        ntt_phase<false>(c, rows, false, logm2, v[1]);
+    } else {
+        ntt_phase<true>(c, rows, false, logm2, v[3]);
+        ntt_phase<true>(c, rows, true, logm1, v[2]);
+    }
+    post(c, 2);
+}
+
+void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float *ms_out)
+{
+    // times every tile width of each phase on `rows` limbs (one prime each) in place
+    NttRows *r = new NttRows();
+    std::unique_ptr<NttRows> guard(r);
+    r->src = r->dst = buf;
+    r->src_gs = r->dst_gs = 0;
+    r->n_groups = 1;
+    r->n_rows = rows;
+    for (int i = 0; i < rows; i++) {
+        r->src_off[i] = r->dst_off[i] = (int16_t)i;
+        r->prime[i] = 0;
+    }
+    const int logm1 = c.log_n / 2, logm2 = c.log_n - logm1;
+    cudaEvent_t e0, e1;
+    HX_CUDA(cudaEventCreate(&e0));
+    HX_CUDA(cudaEventCreate(&e1));
+    for (int ph = 0; ph < 4; ph++) {
+        const bool cols = ph == 0 || ph == 2, inv = ph >= 2;
+        float best_ms = 1e30f;
+        for (int v = 0; v < NTT_VARIANTS; v++) {
+            if (kNttTiles[v] > (c.N >> (cols ? logm1 : logm2))) continue;
+            auto run = [&]() {
+                if (inv) ntt_phase<true>(c, *r, cols, cols ? logm1 : logm2, v);
+                else ntt_phase<false>(c, *r, cols, cols ? logm1 : logm2, v);
+            };
+            run();  // warm-up
+            HX_CUDA(cudaEventRecord(e0, c.stream));
+            for (int it = 0; it < 5; it++) run();
+            HX_CUDA(cudaEventRecord(e1, c.stream));
+            HX_CUDA(cudaEventSynchronize(e1));
+            float ms = 0;
+            HX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best_ms) {
+                best_ms = ms;
+                best[ph] = v;
+            }
+        }
+        if (ms_out) ms_out[ph] = best_ms / 5;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    HX_CUDA(cudaGetLastError());
+}
+
+} // namespace hx
