@@ -554,9 +554,10 @@ def run_dense(args):
 
 def run_serve(args):
     """Serving stream (config-4 pattern): Poisson arrivals of mixed requests -- encrypted
-    matmuls (h in {16, 32, 64}, as the ring allows) and composite sign (g_4, one composition)
-    -- over CKKS rings N in {2^13, 2^14, 2^15} (and 2^16 with --full), chain 60 + 11x40 bit,
-    P = 3x60 bit, levels drawn per request; rotation keys resident; HBM-budget admission.
+    matmuls (h in {16, 32, 64}, as the ring allows; 128 with --full) and composite sign (g_4, one
+    composition) -- over CKKS rings N in {2^13, 2^14, 2^15} (and 2^16 with --full), chain 60 + 19x40
+    bit, P = 3x60 bit, limb counts drawn per request (matmul U{3..20}: 3 runs the depth-2 product;
+    sign U{5..20}); rotation keys resident; HBM-budget admission.
     Capacity is measured closed-loop first; the open-loop run offers 0.8x capacity."""
     import torch
 
@@ -567,7 +568,7 @@ def run_serve(args):
     __graft_entry__.build()
     rng = np.random.default_rng(2026)
     log_ns = [13, 14, 15] + ([16] if args.full else [])
-    qb, pb = [60] + [40] * 11, [60] * 3
+    qb, pb = [60] + [40] * 19, [60] * 3
     ctxs, keys = {}, {}
     t_setup = time.perf_counter()
     for ln in log_ns:
@@ -575,7 +576,7 @@ def run_serve(args):
         hx.hx_autotune(ctx)
         s = (1 << ln) // 2
         hs = [h for h in (16, 32, 64, 128) if h * h <= s and (h <= 64 or args.full)]
-        steps = sorted({k for h in hs for k in hx.hx_matmul_rotation_steps(ctx, h, 8)})
+        steps = sorted({k for h in hs for lv in (3, 8) for k in hx.hx_matmul_rotation_steps(ctx, h, lv)})
         ctxs[ln] = (ctx, hs)
         keys[ln] = hx.hx_keygen(ctx, 2, 4000 + ln, steps)
     n_req = args.requests
@@ -586,14 +587,14 @@ def run_serve(args):
         s = (1 << ln) // 2
         if rng.random() < 0.5:
             h = int(rng.choice(hs))
-            limbs = int(rng.integers(4, 9))
+            limbs = int(rng.integers(3, 21))
             beta = s // (h * h)
             a = hx.hx_encrypt(ctx, keys[ln], workloads.pack(workloads.matrices(10 * i, beta, h), h, beta), limbs, i)
             b = hx.hx_encrypt(ctx, keys[ln], workloads.pack(workloads.matrices(10 * i + 1, beta, h), h, beta), limbs,
                               n_req + i)
             reqs.append(("matmul", ln, (a, b, h), limbs))
         else:
-            limbs = int(rng.integers(5, 9))
+            limbs = int(rng.integers(5, 21))
             x = hx.hx_encrypt(ctx, keys[ln], workloads.sign_inputs(i, s), limbs, 2 * n_req + i)
             reqs.append(("sign", ln, (x, 4, 1, 7 * i + 1), limbs))
     # build every plan once (library masks) before timing
@@ -669,8 +670,8 @@ def run_serve(args):
             "offered_req_s": round(rate, 2), "capacity_req_s": round(capacity, 2), "requests": len(L),
             "n_gpus": 1, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "Poisson arrivals at %.1fx closed-loop capacity; 50%% matmul h in {16,32,64} "
-                                   "(feasible per ring), 50%% sign g_4 (k=1); N in %s; Q=60+11x40, P=3x60 bit; "
-                                   "matmul limbs U{4..8}, sign limbs U{5..8}" % (args.load, [2 ** l for l in log_ns]),
+                                   "(feasible per ring), 50%% sign g_4 (k=1); N in %s; Q=60+19x40, P=3x60 bit; "
+                                   "matmul limbs U{3..20}, sign limbs U{5..20}" % (args.load, [2 ** l for l in log_ns]),
                        "lanes": args.lanes, "max_batch": args.max_batch, "hbm_budget_bytes": budget,
                        "setup_s": round(setup_s, 1)},
             "server": stats, "clocks": clocks}

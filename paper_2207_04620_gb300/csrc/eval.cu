@@ -365,6 +365,28 @@ Cts Eval::rescale(const Cts &a)
     return o;
 }
 
+void plaintext_from_device(hx_context &ctx, cudaStream_t s, const int64_t *dcoeffs, int limbs, bool extended,
+                           uint64_t *dst)
+{
+    Eval ev(ctx, s);
+    if (!extended) {
+        launch_signed_to_rows(ev.lc(), dst, dcoeffs, limbs, 1, ctx.N, ctx.d_prime_ids);
+        ev.ntt_inplace(dst, 0, 1, iota_vec(0, limbs), iota_vec(0, limbs), false);
+        launch_to_mont(ev.lc(), dst, limbs, ctx.d_prime_ids);
+        return;
+    }
+    const int ext = limbs + ctx.K;
+    std::vector<int> pr(ext);
+    for (int t = 0; t < ext; t++) pr[t] = t < limbs ? t : ctx.n_q + (t - limbs);
+    DevBuf ids((ext + 1) / 2, s);
+    HX_CUDA(cudaMemcpyAsync(ids.p, pr.data(), sizeof(int) * ext, cudaMemcpyHostToDevice, s));
+    const int *idp = reinterpret_cast<const int *>(ids.p);
+    launch_signed_to_rows(ev.lc(), dst, dcoeffs, ext, 1, ctx.N, idp);
+    ev.ntt_inplace(dst, 0, 1, iota_vec(0, ext), pr, false);
+    launch_to_mont(ev.lc(), dst, ext, idp);
+    HX_CUDA(cudaStreamSynchronize(s));  // the prime-index staging buffer is released at return
+}
+
 void upload_plaintext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst)
 {
     Eval ev(ctx, s);

@@ -184,6 +184,9 @@ Scalars scalars_for(const hx_context &ctx, int limbs, int64_t c);
 void upload_plaintext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst_mont);
 // the same over q_0..q_{limbs-1}, p_0..p_{K-1}
 void upload_plaintext_ext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst_mont);
+// the same from N signed coefficients already on the device (extended: over the special primes too)
+void plaintext_from_device(hx_context &ctx, cudaStream_t s, const int64_t *dcoeffs, int limbs, bool extended,
+                           uint64_t *dst);
 
 // ---- keys / encryption (keys.cu) ---------------------------------------------
 void keygen(hx_context &ctx, hx_keyset &ks, int n_parties, uint64_t seed, cudaStream_t s);

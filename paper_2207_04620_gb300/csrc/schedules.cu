@@ -148,20 +148,31 @@ void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s)
 {
     hx_matmul_plan *p = &pl;
     const int h = p->h;
-    // encode every mask with the library's encoder (expanded over the beta packed matrices)
-    std::vector<double> slots(ctx.N / 2);
-    std::vector<int64_t> coeffs(ctx.N);
-    for (auto &m : p->masks) {
-        for (int t = 0; t < h * h; t++)
-            for (int j = 0; j < p->beta; j++) slots[(size_t)t * p->beta + j] = m.vec[t];
-        ctx.enc->encode(slots.data(), slots.size(), m.scale, coeffs.data());
-        if (m.extended) {
-            m.pt = std::make_shared<DevBuf>((size_t)(m.limbs + ctx.K) * ctx.N, s);
-            upload_plaintext_ext(ctx, s, coeffs.data(), m.limbs, m.pt->p);
-        } else {
-            m.pt = std::make_shared<DevBuf>((size_t)m.limbs * ctx.N, s);
-            upload_plaintext(ctx, s, coeffs.data(), m.limbs, m.pt->p);
+    const size_t S = (size_t)ctx.N / 2;
+    // every mask expanded over the beta packed matrices, encoded by the device encoder (the same
+    // coefficients as the host encoder) in one batch per mask scale, then moved to NTT and
+    // Montgomery form on the device
+    std::map<double, std::vector<int>> by_scale;
+    for (int i = 0; i < (int)p->masks.size(); i++) by_scale[p->masks[i].scale].push_back(i);
+    for (auto &grp : by_scale) {
+        const std::vector<int> &ids = grp.second;
+        std::vector<double> slots(ids.size() * S);
+        for (size_t r = 0; r < ids.size(); r++) {
+            const auto &m = p->masks[ids[r]];
+            for (int t = 0; t < h * h; t++)
+                for (int j = 0; j < p->beta; j++) slots[r * S + (size_t)t * p->beta + j] = m.vec[t];
         }
+        DevBuf dslots(slots.size(), s), dco(ids.size() * ctx.N, s);
+        HX_CUDA(cudaMemcpyAsync(dslots.p, slots.data(), sizeof(double) * slots.size(), cudaMemcpyHostToDevice, s));
+        int64_t *co = reinterpret_cast<int64_t *>(dco.p);
+        encode_batch(ctx, reinterpret_cast<const double *>(dslots.p), S, (int)ids.size(), grp.first, co, ctx.N, s);
+        for (size_t r = 0; r < ids.size(); r++) {
+            auto &m = p->masks[ids[r]];
+            const int rows = m.extended ? m.limbs + ctx.K : m.limbs;
+            m.pt = std::make_shared<DevBuf>((size_t)rows * ctx.N, s);
+            plaintext_from_device(ctx, s, co + r * ctx.N, m.limbs, m.extended, m.pt->p);
+        }
+        HX_CUDA(cudaStreamSynchronize(s));  // the host slot staging goes out of scope
     }
 }
 
