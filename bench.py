@@ -857,6 +857,74 @@ def run_micro_encrypt(args):
     hx.hx_context_destroy(ctx)
 
 
+def run_micro_ntt_multi(args):
+    """Rings of uneven degree and limb count through one launch per phase (hx_ntt_multi) against one
+    hx_ntt call per ring, forward transforms in place, CUDA events on the stream: a large mix
+    (N = 2^13 with 12 limbs x 8 polynomials, 2^14 8 x 16, 2^15 16 x 4, 2^16 20 x 2) and 48 small
+    rings (N 2^12..2^14, 1..4 limbs, one polynomial each, the shape of a serving mix)."""
+    import torch
+
+    from paper_2207_04620_gb300 import hx, workloads
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    ctx_of = {}
+
+    def make_jobs(specs):
+        jobs, bufs, byt = [], [], 0.0
+        for ln, limbs, polys in specs:
+            if ln not in ctx_of:
+                c = hx.hx_context_create(ln, [60] + [40] * 19, [60] * 2, 40)
+                hx.hx_autotune(c)
+                ctx_of[ln] = c
+            ctx = ctx_of[ln]
+            primes = hx.hx_context_primes(ctx)[:limbs]
+            x = torch.from_numpy(workloads.residues(ln + len(jobs), primes, polys, 1 << ln).view(np.int64)).cuda()
+            bufs.append(x)
+            jobs.append((ctx, x.data_ptr(), polys, list(range(limbs))))
+            byt += 16.0 * polys * limbs * (1 << ln)
+        return jobs, bufs, byt
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        ts = []
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    peak, kind = peaks()
+    cases = {"large": [(13, 12, 8), (14, 8, 16), (15, 16, 4), (16, 20, 2)],
+             "many_small": [(12 + (i % 3), 1 + (i % 4), 1) for i in range(48)]}
+    out = {"micro": "ntt_multi", "peak_gbs": peak, "peak_kind": kind,
+           "note": "fused: one persistent launch per phase for all rings (128-thread tiles, next tile "
+                   "prefetched); per-ring: one hx_ntt call (two launches, autotuned persistent kernels) per ring"}
+    for name, specs in cases.items():
+        jobs, bufs, byt = make_jobs(specs)
+
+        def separate():
+            for ctx, ptr, polys, pr in jobs:
+                hx.hx_ntt(ctx, ptr, polys, pr, False, stream)
+
+        def fused():
+            hx.hx_ntt_multi(jobs, False, stream)
+
+        ms_sep, ms_fus = timed(separate), timed(fused)
+        out[name] = {"rings": len(specs), "bytes": byt, "fused_ms": round(ms_fus, 4), "per_ring_ms": round(ms_sep, 4),
+                     "fused_gbs": round(byt / ms_fus / 1e6, 1), "per_ring_gbs": round(byt / ms_sep / 1e6, 1),
+                     "launches": {"fused": 2, "per_ring": 2 * len(specs)}}
+    print(json.dumps(out), flush=True)
+    for c in ctx_of.values():
+        hx.hx_context_destroy(c)
+
+
 def run_micro_aggregate(args):
     """Alg. 6 Aggregation alone: the model update w - eta/(B N) * sum_i g_i for the 8
     gradient ciphertexts of one 784->128 layer (h=64, beta=4 packing) from 16 parties,
@@ -931,7 +999,7 @@ def run_micro_aggregate(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--micro", choices=["ntt", "aggregate", "encrypt"], default=None)
+    ap.add_argument("--micro", choices=["ntt", "aggregate", "encrypt", "ntt-multi"], default=None)
     ap.add_argument("--parties", type=int, default=16)
     ap.add_argument("--workload", choices=["matmul", "sign", "dense", "serve", "rmatmul"], default="matmul")
     ap.add_argument("--t", type=int, default=16, help="rows of A in the rectangular product")
@@ -955,6 +1023,8 @@ def main():
         return run_micro_aggregate(args)
     if args.micro == "encrypt":
         return run_micro_encrypt(args)
+    if args.micro == "ntt-multi":
+        return run_micro_ntt_multi(args)
     if args.micro:
         return run_micro(args)
     if args.workload == "sign":

@@ -54,7 +54,7 @@ typedef struct hx_ct hx_ct;
 typedef struct hx_matmul_plan hx_matmul_plan;
 
 /* Parameters (Sec. 2.2: R_Q = Z_Q[X]/(X^N+1), Q = q_0...q_{L-1}).
- * log_n in [10, 17]; n_q Q primes of q_bits[i] bits (q_0 first), n_p special
+ * log_n in [11, 16]; n_q Q primes of q_bits[i] bits (q_0 first), n_p special
  * primes of p_bits[k] bits (hybrid key switching, digits of n_p primes);
  * every size in [20, 61].  Primes: for each size in this order, the largest
  * prime below 2^bits that is 1 mod 2N and not yet chosen.  Default encoding
@@ -185,6 +185,22 @@ hx_status hx_rotate_noalloc(hx_context *ctx, const hx_keyset *ks, const uint64_t
                             int32_t k, void *stream);
 
 /* ---- raw kernels on caller device buffers (for parity tests and benches) --- */
+/* Several rings in one launch per phase: every job's polynomials (its own
+ * context, so its own N, primes and twiddles) are transformed in place by one
+ * column-phase and one row-phase launch over the tiles of all jobs, with the
+ * same residues as hx_ntt on each job.  data: device [n_polys][n_limbs][N]
+ * words; prime_idx: host, n_limbs prime indices (rows of a polynomial).
+ * N from 2^11 to 2^16; all contexts on the current device; returns after the
+ * launches (the job table is staged on the stream). */
+typedef struct hx_ntt_job {
+    const hx_context *ctx;
+    uint64_t *data;
+    int n_polys;
+    int n_limbs;
+    const int32_t *prime_idx;
+} hx_ntt_job;
+hx_status hx_ntt_multi(const hx_ntt_job *jobs, int n_jobs, int inverse, void *stream);
+
 /* In-place forward (inverse != 0: inverse) negacyclic NTT of n_polys
  * polynomials laid out [n_polys][limbs][N] in device memory; limb l is taken
  * modulo prime index prime_idx[l] (host array; index into Q then P). */

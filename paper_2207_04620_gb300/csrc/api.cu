@@ -423,6 +423,38 @@ hx_status hx_ntt(hx_context *ctx, uint64_t *dev, int n_polys, int limbs, const i
     HX_END
 }
 
+hx_status hx_ntt_multi(const hx_ntt_job *jobs, int n_jobs, int inverse, void *stream)
+{
+    HX_TRY
+    need(jobs && n_jobs >= 1 && n_jobs <= 4096, "bad job list");
+    std::vector<NttJob> v(n_jobs);
+    int dev = -1;
+    for (int i = 0; i < n_jobs; i++) {
+        const hx_ntt_job &j = jobs[i];
+        need(j.ctx && (j.data || j.n_polys == 0) && j.prime_idx && j.n_polys >= 0, "null job field");
+        need(j.n_limbs >= 1 && j.n_limbs <= 64, "a job has 1..64 limbs");
+        need(dev < 0 || j.ctx->device == dev, "jobs on several devices");
+        dev = j.ctx->device;
+        NttJob &J = v[i];
+        J.data = j.data;
+        J.primes = j.ctx->t.primes;
+        J.tw_fwd = j.ctx->t.tw_fwd;
+        J.tw_inv = j.ctx->t.tw_inv;
+        J.log_n = j.ctx->log_n;
+        J.n_rows = j.n_polys * j.n_limbs;
+        J.n_limbs = j.n_limbs;
+        J.tile0_cols = J.tile0_rows = 0;
+        for (int l = 0; l < j.n_limbs; l++) {
+            need(j.prime_idx[l] >= 0 && j.prime_idx[l] < j.ctx->n_all, "bad prime index");
+            J.prime[l] = (int16_t)j.prime_idx[l];
+        }
+    }
+    hx_context *c0 = const_cast<hx_context *>(jobs[0].ctx);
+    launch_ntt_multi(S(stream), v, inverse != 0, c0->t.n_sm, &c0->counters[C_LAUNCH]);
+    return HX_OK;
+    HX_END
+}
+
 hx_status hx_matmul_plan_create(hx_context *ctx, int h, int limbs, hx_matmul_plan **out)
 {
     HX_TRY

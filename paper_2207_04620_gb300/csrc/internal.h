@@ -116,6 +116,20 @@ struct LaunchCtx {
 };
 
 void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse);
+// one job of a multi-ring NTT: n_rows rows of 2^log_n words at data (in place), row r modulo
+// prime[r % n_limbs] of its own context's tables
+struct NttJob {
+    uint64_t *data;
+    const PrimeConst *primes;
+    const ulonglong2 *tw_fwd, *tw_inv;
+    int log_n, n_rows, n_limbs;
+    int tile0_cols, tile0_rows;  // filled by the launcher
+    int16_t prime[64];
+};
+// every job's transform in one launch per phase (several ring degrees together)
+void launch_ntt_multi(cudaStream_t s, const std::vector<NttJob> &jobs, bool inverse, int n_sm,
+                      std::atomic<uint64_t> *launches);
+
 // times the NTT tile widths on `rows` limbs of buf and writes the fastest per phase
 void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float *ms_out);
 void launch_add(const LaunchCtx &c, View out, View a, View b, int B, int comps, int limbs, bool sub);

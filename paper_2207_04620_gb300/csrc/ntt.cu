@@ -343,6 +343,177 @@ void ntt_phase(const LaunchCtx &c, const NttRows &r, bool cols, int logm, int va
     }
 }
 
+// ---- several rings in one launch ------------------------------------------------
+// A job is n_rows rows of one ring (its own N, primes and twiddles), transformed
+// in place.  One persistent kernel per phase walks the tiles of every job, the
+// next tile (and for the column phase its twiddles) streaming into the other
+// half of shared memory while the current one is transformed; a tile's phase
+// size picks the template instance, with the tile width chosen so every
+// instance runs 128 threads.
+
+constexpr int kMultiT = 128;
+template <int LOGM> struct MultiW {  // tile width per phase size: (M >> R1) * W = 128 threads
+    static constexpr int W = kMultiT / ((1 << LOGM) >> Split<LOGM>::R1);
+};
+constexpr int kMultiColsBuf = 2048 + 2 * 256;  // words: the largest column tile and its twiddles
+constexpr int kMultiRowsBuf = 8 * (256 + 16);  // words: the largest padded row tile
+
+struct MultiTile {
+    uint64_t *row;
+    const ulonglong2 *tw;
+    const PrimeConst *primes;
+    int pr, logm, log_n, bx;
+};
+
+__device__ __forceinline__ MultiTile multi_tile(const NttJob *jobs, int n_jobs, int t, bool cols, bool inv)
+{
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) / 2;
+        if ((cols ? jobs[mid].tile0_cols : jobs[mid].tile0_rows) <= t) lo = mid;
+        else hi = mid - 1;
+    }
+    const NttJob &J = jobs[lo];
+    MultiTile m;
+    const int local = t - (cols ? J.tile0_cols : J.tile0_rows);
+    m.log_n = J.log_n;
+    m.logm = cols ? J.log_n / 2 : J.log_n - J.log_n / 2;
+    const int n = 1 << J.log_n;
+    const int W = kMultiT / ((1 << m.logm) >> ((m.logm + 1) / 2));
+    const int nb = (n >> m.logm) / W;
+    const int r = local / nb;
+    m.bx = local % nb;
+    m.pr = J.prime[r % J.n_limbs];
+    m.primes = J.primes;
+    m.row = J.data + (size_t)r * n;
+    m.tw = (inv ? J.tw_inv : J.tw_fwd) + (size_t)m.pr * n;
+    return m;
+}
+
+template <int LOGM>
+__device__ void multi_cols_load(uint64_t *b, const MultiTile &m)
+{
+    constexpr int M = 1 << LOGM, COLS = MultiW<LOGM>::W, E = M * COLS;
+    const int N2 = (1 << m.log_n) >> LOGM, c0 = m.bx * COLS;
+    ulonglong2 *stw = reinterpret_cast<ulonglong2 *>(b + 2048);
+    for (int i = threadIdx.x; i < E / 2; i += kMultiT) {
+        const int r = (2 * i) / COLS, c = (2 * i) % COLS;
+        cp_async16(b + 2 * i, m.row + (size_t)r * N2 + c0 + c);
+    }
+    for (int i = threadIdx.x; i < M; i += kMultiT) cp_async16(stw + i, m.tw + i);
+}
+
+template <int LOGM, bool INV>
+__device__ void multi_cols_run(uint64_t *b, const MultiTile &m, const PrimeConst &P)
+{
+    constexpr int M = 1 << LOGM, COLS = MultiW<LOGM>::W, E = M * COLS;
+    constexpr int R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
+    const int N2 = (1 << m.log_n) >> LOGM, c0 = m.bx * COLS;
+    const ulonglong2 *stw = reinterpret_cast<const ulonglong2 *>(b + 2048);
+    if (!INV) {
+        ntt_pass<LOGM, R1, 0, false, true, false>(b, COLS, 1, COLS, stw, 0, 0, 0, P.q, kMultiT);
+        __syncthreads();
+        ntt_pass<LOGM, R2, R1, false, true, false>(b, COLS, 1, COLS, stw, 0, 0, 0, P.q, kMultiT);
+        __syncthreads();
+        for (int i = threadIdx.x; i < E; i += kMultiT) m.row[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = b[i];
+    } else {
+        ntt_pass<LOGM, R2, R1, true, true, false>(b, COLS, 1, COLS, stw, 0, 0, 0, P.q, kMultiT);
+        __syncthreads();
+        ntt_pass<LOGM, R1, 0, true, true, false>(b, COLS, 1, COLS, stw, 0, 0, 0, P.q, kMultiT);
+        __syncthreads();
+        for (int i = threadIdx.x; i < E; i += kMultiT)
+            m.row[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = shoup(b[i], P.n_inv, P.n_inv_sh, P.q);
+    }
+}
+
+template <int LOGM>
+__device__ void multi_rows_load(uint64_t *b, const MultiTile &m)
+{
+    constexpr int M = 1 << LOGM, ROWS = MultiW<LOGM>::W, E = M * ROWS, SK = M + M / 16;
+    const size_t base = (size_t)m.bx * ROWS * M;
+    for (int i = threadIdx.x; i < E; i += kMultiT) {
+        const int k = i / M, e = i % M;
+        cp_async8(b + k * SK + e + (e >> 4), m.row + base + i);
+    }
+}
+
+template <int LOGM, bool INV>
+__device__ void multi_rows_run(uint64_t *b, const MultiTile &m, const PrimeConst &P)
+{
+    constexpr int M = 1 << LOGM, ROWS = MultiW<LOGM>::W, E = M * ROWS, SK = M + M / 16;
+    constexpr int R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
+    const int g0 = m.log_n - LOGM, r_base = m.bx * ROWS;
+    const size_t base = (size_t)r_base * M;
+    const uint64_t q = P.q, two_q = 2 * q;
+    if (!INV) {
+        ntt_pass<LOGM, R1, 0, false, false, true>(b, ROWS, SK, 1, m.tw, g0, r_base, 1, q, kMultiT);
+        __syncthreads();
+        ntt_pass<LOGM, R2, R1, false, false, true>(b, ROWS, SK, 1, m.tw, g0, r_base, 1, q, kMultiT);
+        __syncthreads();
+        for (int i = threadIdx.x; i < E; i += kMultiT) {
+            const int k = i / M, e = i % M;
+            uint64_t v = b[k * SK + e + (e >> 4)];
+            if (v >= two_q) v -= two_q;
+            if (v >= q) v -= q;
+            m.row[base + i] = v;
+        }
+    } else {
+        ntt_pass<LOGM, R2, R1, true, false, true>(b, ROWS, SK, 1, m.tw, g0, r_base, 1, q, kMultiT);
+        __syncthreads();
+        ntt_pass<LOGM, R1, 0, true, false, true>(b, ROWS, SK, 1, m.tw, g0, r_base, 1, q, kMultiT);
+        __syncthreads();
+        for (int i = threadIdx.x; i < E; i += kMultiT) {
+            const int k = i / M, e = i % M;
+            m.row[base + i] = b[k * SK + e + (e >> 4)];
+        }
+    }
+}
+
+template <bool INV, bool COLS_PHASE>
+__global__ void __launch_bounds__(kMultiT) k_ntt_multi(const NttJob *__restrict__ jobs, int n_jobs, int n_tiles)
+{
+    extern __shared__ uint64_t sh[];
+    constexpr int BUF = COLS_PHASE ? kMultiColsBuf : kMultiRowsBuf;
+    auto load = [&](const MultiTile &m, int slot) {
+        uint64_t *b = sh + slot * BUF;
+        switch (m.logm) {
+        case 5: COLS_PHASE ? multi_cols_load<5>(b, m) : multi_rows_load<5>(b, m); break;
+        case 6: COLS_PHASE ? multi_cols_load<6>(b, m) : multi_rows_load<6>(b, m); break;
+        case 7: COLS_PHASE ? multi_cols_load<7>(b, m) : multi_rows_load<7>(b, m); break;
+        default: COLS_PHASE ? multi_cols_load<8>(b, m) : multi_rows_load<8>(b, m); break;
+        }
+        cp_async_commit();
+    };
+    int t = blockIdx.x, slot = 0;
+    MultiTile cur{};
+    if (t < n_tiles) {
+        cur = multi_tile(jobs, n_jobs, t, COLS_PHASE, INV);
+        load(cur, 0);
+    }
+    for (; t < n_tiles; t += gridDim.x, slot ^= 1) {
+        const int tn = t + gridDim.x;
+        MultiTile nxt{};
+        if (tn < n_tiles) {
+            nxt = multi_tile(jobs, n_jobs, tn, COLS_PHASE, INV);
+            load(nxt, slot ^ 1);
+            cp_async_wait_all_but_one();
+        } else {
+            cp_async_wait_all();
+        }
+        __syncthreads();
+        const PrimeConst P = cur.primes[cur.pr];
+        uint64_t *b = sh + slot * BUF;
+        switch (cur.logm) {
+        case 5: COLS_PHASE ? multi_cols_run<5, INV>(b, cur, P) : multi_rows_run<5, INV>(b, cur, P); break;
+        case 6: COLS_PHASE ? multi_cols_run<6, INV>(b, cur, P) : multi_rows_run<6, INV>(b, cur, P); break;
+        case 7: COLS_PHASE ? multi_cols_run<7, INV>(b, cur, P) : multi_rows_run<7, INV>(b, cur, P); break;
+        default: COLS_PHASE ? multi_cols_run<8, INV>(b, cur, P) : multi_rows_run<8, INV>(b, cur, P); break;
+        }
+        __syncthreads();  // this half is refilled by the prefetch two tiles later
+        cur = nxt;
+    }
+}
+
 } // namespace
 
 void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse)
@@ -405,6 +576,46 @@ void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     HX_CUDA(cudaGetLastError());
+}
+
+void launch_ntt_multi(cudaStream_t s, const std::vector<NttJob> &jobs_in, bool inverse, int n_sm,
+                      std::atomic<uint64_t> *launches)
+{
+    std::vector<NttJob> jobs = jobs_in;
+    int tc = 0, tr = 0;
+    for (auto &J : jobs) {
+        HX_CHECK(J.log_n >= 11 && J.log_n <= 16, HX_EINVAL, "ring degree outside 2^11..2^16");
+        HX_CHECK(J.n_limbs >= 1 && J.n_limbs <= 64 && J.n_rows >= 0, HX_EINVAL, "bad job rows");
+        const int n = 1 << J.log_n, l1 = J.log_n / 2, l2 = J.log_n - l1;
+        const int w1 = 128 / ((1 << l1) >> ((l1 + 1) / 2)), w2 = 128 / ((1 << l2) >> ((l2 + 1) / 2));
+        J.tile0_cols = tc;
+        J.tile0_rows = tr;
+        const long long c = (long long)J.n_rows * ((n >> l1) / w1), r = (long long)J.n_rows * ((n >> l2) / w2);
+        HX_CHECK(tc + c < (1ll << 31) && tr + r < (1ll << 31), HX_EINVAL, "NTT batch too large");
+        tc += (int)c;
+        tr += (int)r;
+    }
+    if (tc == 0) return;
+    void *jd = nullptr;
+    HX_CUDA(cudaMallocAsync(&jd, jobs.size() * sizeof(NttJob), s));
+    HX_CUDA(cudaMemcpyAsync(jd, jobs.data(), jobs.size() * sizeof(NttJob), cudaMemcpyHostToDevice, s));
+    const NttJob *jp = reinterpret_cast<const NttJob *>(jd);
+    // two halves of shared memory per block (current tile, next tile)
+    const size_t smem_c = 2 * sizeof(uint64_t) * kMultiColsBuf, smem_r = 2 * sizeof(uint64_t) * kMultiRowsBuf;
+    const int grid_c = std::min(tc, n_sm * 8), grid_r = std::min(tr, n_sm * 8);
+    const int n_jobs = (int)jobs.size();
+    if (!inverse) {
+        k_ntt_multi<false, true><<<grid_c, kMultiT, smem_c, s>>>(jp, n_jobs, tc);
+        k_ntt_multi<false, false><<<grid_r, kMultiT, smem_r, s>>>(jp, n_jobs, tr);
+    } else {
+        k_ntt_multi<true, false><<<grid_r, kMultiT, smem_r, s>>>(jp, n_jobs, tr);
+        k_ntt_multi<true, true><<<grid_c, kMultiT, smem_c, s>>>(jp, n_jobs, tc);
+    }
+    const cudaError_t le = cudaGetLastError();
+    HX_CUDA(cudaFreeAsync(jd, s));
+    HX_CUDA(le);
+    if (launches) *launches += 2;
+    HX_CUDA(cudaStreamSynchronize(s));  // the host job vector is released at return
 }
 
 } // namespace hx

@@ -75,6 +75,7 @@ _SIGS = {
     "hx_rotate_hoisted": (c_int, [c_vp, c_vp, c_vp, P_i32, c_int, PP, c_vp]),
     "hx_ntt": (c_int, [c_vp, c_vp, c_int, c_int, P_i32, c_int, c_vp]),
     "hx_rotate_noalloc": (c_int, [c_vp, c_vp, c_vp, c_int, c_vp, ctypes.c_int32, c_vp]),
+    "hx_ntt_multi": (c_int, [c_vp, c_int, c_int, c_vp]),
     "hx_matmul_plan_create": (c_int, [c_vp, c_int, c_int, PP]),
     "hx_matmul_plan_num_masks": (c_int, [c_vp]),
     "hx_matmul_plan_set_mask": (c_int, [c_vp, c_vp, c_int, P_i64]),
@@ -380,6 +381,21 @@ def hx_rotate_noalloc(ctx: int, ks: int, in_ptr: int, limbs: int, out_ptr: int, 
 def hx_ntt(ctx: int, dev_ptr: int, n_polys: int, prime_idx, inverse: bool = False, stream=None) -> None:
     arr, ptr = _i32arr(prime_idx)
     _chk(lib().hx_ntt(ctx, dev_ptr, n_polys, arr.size, ptr, int(bool(inverse)), _stream(stream)))
+
+
+class _NttJob(ctypes.Structure):
+    _fields_ = [("ctx", c_vp), ("data", c_vp), ("n_polys", c_int), ("n_limbs", c_int), ("prime_idx", P_i32)]
+
+
+def hx_ntt_multi(jobs, inverse: bool = False, stream=None) -> None:
+    """jobs: (ctx, device pointer, n_polys, prime indices) per ring; one launch per phase for all."""
+    arr = (_NttJob * len(jobs))()
+    keep = []
+    for i, (ctx, ptr, n_polys, primes) in enumerate(jobs):
+        pa, pp = _i32arr(primes)
+        keep.append(pa)
+        arr[i] = _NttJob(ctx, ptr, n_polys, pa.size, pp)
+    _chk(lib().hx_ntt_multi(arr, len(jobs), int(bool(inverse)), _stream(stream)))
 
 
 # ---- HE-MatMult ----------------------------------------------------------------------

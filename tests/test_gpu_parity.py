@@ -67,6 +67,46 @@ def test_ntt_bit_exact(log_n):
         hx.hx_context_destroy(ctx)
 
 
+def test_ntt_multi_ring_one_launch_bit_exact():
+    """Rings of six degrees (2^11 .. 2^16) with uneven limb and polynomial counts
+    in one launch per phase: forward and inverse equal the oracle's transform
+    of every job."""
+    import torch
+
+    specs = [(11, 3, 2), (12, 1, 3), (13, 4, 1), (14, 2, 2), (15, 5, 1), (16, 2, 1)]  # (log_n, limbs, polys)
+    ctxs, octxs, xs, devs, jobs = [], [], [], [], []
+    try:
+        for ln, limbs, polys in specs:
+            qb = [60] + [45] * (limbs - 1)
+            octx = C.Context(ln, qb, [61], 45)
+            ctx = hx.hx_context_create(ln, qb, [61], 45)
+            primes = octx.q[:limbs]
+            x = workloads.residues(ln + limbs, primes, polys, octx.N)
+            dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
+            ctxs.append(ctx)
+            octxs.append((octx, primes * polys))
+            xs.append(x)
+            devs.append(dev)
+            jobs.append((ctx, dev.data_ptr(), polys, list(range(limbs))))
+        hx.hx_ntt_multi(jobs, inverse=False)
+        torch.cuda.synchronize()
+        for (octx, pr), x, dev in zip(octxs, xs, devs):
+            assert np.array_equal(dev.cpu().numpy().view(np.uint64), octx.ntt(x, pr))
+        hx.hx_ntt_multi(jobs, inverse=True)
+        torch.cuda.synchronize()
+        for x, dev in zip(xs, devs):
+            assert np.array_equal(dev.cpu().numpy().view(np.uint64), x)
+        for (octx, pr), x, dev in zip(octxs, xs, devs):
+            dev.copy_(torch.from_numpy(x.view(np.int64).copy()).cuda())
+        hx.hx_ntt_multi(jobs, inverse=True)
+        torch.cuda.synchronize()
+        for (octx, pr), x, dev in zip(octxs, xs, devs):
+            assert np.array_equal(dev.cpu().numpy().view(np.uint64), octx.intt(x, pr))
+    finally:
+        for c in ctxs:
+            hx.hx_context_destroy(c)
+
+
 @pytest.mark.parametrize("log_n", [11, 14, 16])
 def test_ntt_every_tile_width_and_autotune(log_n):
     import torch
