@@ -514,6 +514,8 @@ __global__ void __launch_bounds__(kMultiT) k_ntt_multi(const NttJob *__restrict_
     }
 }
 
+// ---- end of the several-ring kernels
+
 } // namespace
 
 void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse)
@@ -578,6 +580,7 @@ void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float 
     HX_CUDA(cudaGetLastError());
 }
 
+// ---- several rings: launcher
 void launch_ntt_multi(cudaStream_t s, const std::vector<NttJob> &jobs_in, bool inverse, int n_sm,
                       std::atomic<uint64_t> *launches)
 {
@@ -617,5 +620,7 @@ void launch_ntt_multi(cudaStream_t s, const std::vector<NttJob> &jobs_in, bool i
     if (launches) *launches += 2;
     HX_CUDA(cudaStreamSynchronize(s));  // the host job vector is released at return
 }
+
+// ---- end of the several-ring launcher
 
 } // namespace hx
