@@ -17,6 +17,8 @@ PARAMS = {
     "cfg1": dict(log_n=14, q_bits=[60] + [45] * 7, p_bits=[60, 60], log2_scale=45),
     # the sign chain of config 2 on a smaller ring: 60 + 15*40, three special primes
     "sign": dict(log_n=12, q_bits=[60] + [40] * 15, p_bits=[60] * 3, log2_scale=40),
+    # config 2 itself: N=2^15
+    "cfg2": dict(log_n=15, q_bits=[60] + [40] * 15, p_bits=[60] * 3, log2_scale=40),
 }
 
 

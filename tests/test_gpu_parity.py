@@ -554,6 +554,106 @@ def test_matmul_config1_bit_exact():
         pr.close()
 
 
+@pytest.mark.slow
+def test_matmul_config1_full_batch_graph_sampled_bit_exact():
+    """Config 1 at full size in the launch configuration the bench times: 16
+    ciphertext pairs (32 products of 64x64) through the captured graph with the
+    Step-2 keys premasked; pairs 0 and 15 equal the oracle's HE-MatMult bit for
+    bit and every product decrypts to A@B within 2^-18."""
+    pr, beta, limbs = _matmul_case("cfg1", 64, 0, 1)
+    try:
+        h, pairs = 64, 16
+        masks = Hc.MaskProvider(pr.octx, h, limbs)
+        plan = hx.hx_matmul_plan_create(pr.ctx, h, limbs)
+        for i in range(len(masks.entries)):
+            hx.hx_matmul_plan_set_mask(pr.ctx, plan, i, masks.coeffs(i))
+        hx.hx_matmul_plan_bind_keys(pr.ctx, plan, pr.ks)
+        ma = [workloads.matrices(2 * i, beta, h) for i in range(pairs)]
+        mb = [workloads.matrices(2 * i + 1, beta, h) for i in range(pairs)]
+        A = [pr.encrypt(workloads.pack(ma[i], h, beta), 10 + i) for i in range(pairs)]
+        B = [pr.encrypt(workloads.pack(mb[i], h, beta), 50 + i) for i in range(pairs)]
+        ex = hx.hx_matmul_exec_create(pr.ctx, pr.ks, plan, pairs, A[0].scale)
+        outs = hx.hx_matmul_exec_run(ex, [pr.to_lib(c) for c in A], [pr.to_lib(c) for c in B])
+        for i in (0, pairs - 1):
+            assert pr.same(outs[i], Hc.matmul(C.Evaluator(pr.octx, pr.oks), A[i], B[i], h, masks))
+        for i in range(pairs):
+            got = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, outs[i]), h, beta)
+            assert max(np.abs(g - a @ b).max() for g, a, b in zip(got, ma[i], mb[i])) <= 2 ** -18
+            hx.hx_ct_destroy(outs[i])
+        hx.hx_matmul_exec_destroy(ex)
+        hx.hx_matmul_plan_destroy(plan)
+    finally:
+        pr.close()
+
+
+@pytest.mark.slow
+def test_sign_config2_full_batch_sampled_bit_exact():
+    """Config 2 at full size as the bench runs it: 64 ciphertexts of 16384 slots,
+    N=2^15, 16 limbs, g_4^(8) with two collective refreshes per entry in one
+    batch call; entries 0 and 63 equal the oracle bit for bit and every entry
+    decrypts to the FP64 composite within 2^-16."""
+    pr = Pair("cfg2")
+    try:
+        octx, count = pr.octx, 64
+        xs = [workloads.sign_inputs(500 + i, octx.S) for i in range(count)]
+        cts = [pr.encrypt(x, 900 + i) for i, x in enumerate(xs)]
+        outs = hx.hx_sign_approx_batch(pr.ctx, pr.ks, [pr.to_lib(c) for c in cts], 4, 8, allow_refresh=True,
+                                       refresh_seed=101)
+        for i in (0, count - 1):
+            ev = C.Evaluator(octx, pr.oks)
+            assert pr.same(outs[i], Hc.sign_approx(ev, cts[i], 4, 8, refresh_seed=101 + i))
+            assert ev.counts["Refresh"] == 2
+        for i in range(count):
+            got = hx.hx_decrypt(pr.ctx, pr.ks, outs[i])
+            assert np.abs(got - Hc.g_iter(4, 8, xs[i])).max() < 2 ** -16
+            hx.hx_ct_destroy(outs[i])
+    finally:
+        pr.close()
+
+
+@pytest.mark.slow
+def test_dense_config3_full_size_against_fp64():
+    """Config 3 at full size (784 -> 128, batch 64, h = 64, N = 2^15, 16 limbs) through
+    hx_dense_layer with the library's plans: E, ReLU(E) and dW decrypt to the FP64
+    computation of the same functions (g_4^(8)(E/4) for the sign)."""
+    cfg = workloads.CONFIGS["cfg3_dense784x128_n15"]
+    h, d, k, div = cfg["h"], cfg["d"], cfg["k"], cfg["input_div"]
+    ctx = hx.hx_context_create(cfg["log_n"], cfg["q_bits"], cfg["p_bits"], cfg["log2_scale"])
+    try:
+        ks = hx.hx_keygen(ctx, 2, 81, hx.hx_dense_rotation_steps(ctx, h))
+        beta = (1 << cfg["log_n"]) // 2 // (h * h)
+        W, X, G = workloads.dense_inputs(3, cfg["rows"], cfg["n_in"], cfg["batch"])
+        Wp, Xp, Gp = workloads.dense_pack(W, X, G, h, beta)
+        n_out, groups = len(Wp), len(Xp)
+        assert (n_out, groups) == (2, 4)
+        Wc = [hx.hx_encrypt(ctx, ks, Wp[i][g], 0, 1000 + 10 * i + g) for i in range(n_out) for g in range(groups)]
+        Xc = [hx.hx_encrypt(ctx, ks, Xp[g], 0, 2000 + g) for g in range(groups)]
+        Gc = [hx.hx_encrypt(ctx, ks, Gp[i], 0, 3000 + i) for i in range(n_out)]
+        E, M, dW = hx.hx_dense_layer(ctx, ks, Wc, Xc, Gc, h, n_out, groups, d, k, div, refresh_seed=5)
+        Wb = workloads.blocks(W, h)
+        Xb = [r[0] for r in workloads.blocks(X, h)]
+        Gb = [r[0] for r in workloads.blocks(G, h)]
+        for i in range(n_out):
+            e_ref = sum(a @ b for a, b in zip(Wb[i], Xb))
+            s_ref = Hc.g_iter(d, k, e_ref / div)
+            l_ref = (1 + s_ref) / 2 * Gb[i]
+            e = workloads.unpack(hx.hx_decrypt(ctx, ks, E[i]), h, beta)[0]
+            m = workloads.unpack(hx.hx_decrypt(ctx, ks, M[i]), h, beta)[0]
+            assert np.abs(e - e_ref).max() < 2 ** -12
+            assert np.abs(m - e_ref * (1 + s_ref) / 2).max() < 2 ** -12
+            for g in range(groups):
+                got = workloads.unpack(hx.hx_decrypt(ctx, ks, dW[i * groups + g]), h, beta)
+                for q in range(beta):
+                    j = beta * g + q
+                    want = l_ref @ Xb[j].T if j < len(Xb) else np.zeros((h, h))
+                    assert np.abs(got[q] - want).max() < 2 ** -9
+        for c in E + M + dW + Wc + Xc + Gc:
+            hx.hx_ct_destroy(c)
+        hx.hx_keyset_destroy(ks)
+    finally:
+        hx.hx_context_destroy(ctx)
+
+
 # ---- a8: composite sign and ReLU ------------------------------------------------------
 
 @pytest.mark.parametrize("relu", [False, True])
