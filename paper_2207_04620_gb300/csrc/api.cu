@@ -629,6 +629,7 @@ hx_status hx_matmul_exec_create(hx_context *ctx, const hx_keyset *ks, const hx_m
     HX_CUDA(cudaMemset(ex->B.d, 0, sizeof(uint64_t) * ex->B.bstride(N) * count));
     HX_CUDA(cudaDeviceSynchronize());
     HX_CUDA(cudaStreamCreateWithFlags(&ex->cap, cudaStreamNonBlocking));
+    side_stream(*ctx, ex->cap);  // the schedule's side stream exists before the capture starts
     const uint64_t l0 = ctx->counters[C_LAUNCH];
     uint64_t saved[C_NUM];
     for (int i = 0; i < C_NUM; i++) saved[i] = ctx->counters[i];

@@ -229,11 +229,28 @@ void build_context(hx_context &c, const hx_params &p)
     c.cdt.reset(new GaussianCdt(c.sigma));
 }
 
+SideStream &side_stream(hx_context &ctx, cudaStream_t main)
+{
+    std::lock_guard<std::mutex> lk(ctx.side_mu);
+    SideStream &ss = ctx.side[main];
+    if (!ss.s) {
+        HX_CUDA(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+        for (auto &e : ss.e) HX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    return ss;
+}
+
 void destroy_context(hx_context &c)
 {
     for (auto &kv : c.plans) delete kv.second;
     c.plans.clear();
     cudaDeviceSynchronize();
+    for (auto &kv : c.side) {
+        for (auto &e : kv.second.e)
+            if (e) cudaEventDestroy(e);
+        if (kv.second.s) cudaStreamDestroy(kv.second.s);
+    }
+    c.side.clear();
     cudaFree(c.t.primes);
     cudaFree(c.t.tw_fwd);
     cudaFree(c.t.tw_inv);

@@ -49,6 +49,12 @@ namespace hx {
 struct EncTables {  // device tables of the client-side encoder
     BufPtr roots, e, th;
 };
+// a second stream paired with a caller's stream, for independent chains of one
+// schedule (fork/join by events; inside a capture it joins the same graph)
+struct SideStream {
+    cudaStream_t s = nullptr;
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+};
 } // namespace hx
 
 struct hx_context {
@@ -73,6 +79,8 @@ struct hx_context {
     bool profiling = false;
     std::once_flag enc_once;
     hx::EncTables enc_dev;
+    std::mutex side_mu;
+    std::map<cudaStream_t, hx::SideStream> side;  // keyed by the caller's stream
 };
 
 struct hx_keyset {
@@ -235,6 +243,8 @@ Cts aggregate(hx_context &ctx, const std::vector<const Cts *> &grads, int n_part
               cudaStream_t s);
 
 // ---- context (context.cu) -------------------------------------------------------
+// the side stream paired with `main` (created on first use, destroyed with the context)
+SideStream &side_stream(hx_context &ctx, cudaStream_t main);
 void build_context(hx_context &ctx, const hx_params &p);
 void destroy_context(hx_context &ctx);
 Cts gather(hx_context &ctx, const hx_ct *const *cts, size_t count, cudaStream_t s);

@@ -324,14 +324,27 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
     Cts acc = ev.tensor(ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt), B0);
     BufPtr DA = ev.hoist(A0);
     BufPtr DB = ev.hoist(B0);  // one ModUp serves every B^(k)
+    // the B^(k) chain runs on a side stream beside the A^(k) chain: fork after the hoists; each
+    // B^(k) is consumed on the main stream, and the side stream waits for that use before it
+    // frees B^(k); join before DB is released
+    SideStream &ss = side_stream(ctx, ev.s);
+    Eval ev2(ctx, ss.s);
+    HX_CUDA(cudaEventRecord(ss.e[0], ev.s));
+    HX_CUDA(cudaStreamWaitEvent(ss.s, ss.e[0], 0));
     for (int k = 1; k < t; k++) {
-        Cts Bk = ev.rotate_hoisted_one(B0, DB, (int64_t)beta * h * k, ks);
+        Cts Bk = ev2.rotate_hoisted_one(B0, DB, (int64_t)beta * h * k, ks);
+        HX_CUDA(cudaEventRecord(ss.e[1], ss.s));
         double sc;
         const uint64_t *v = mask_pt(p, 2, k, &sc);
         const uint64_t *pm = (p.bound_uid && p.bound_uid == ks.uid) ? p.premasked[k]->p : nullptr;
         Cts Ak = ev.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, qt, ks, pm);
+        HX_CUDA(cudaStreamWaitEvent(ev.s, ss.e[1], 0));
         ev.tensor_acc(acc, Ak, Bk);
+        HX_CUDA(cudaEventRecord(ss.e[2], ev.s));
+        HX_CUDA(cudaStreamWaitEvent(ss.s, ss.e[2], 0));
     }
+    HX_CUDA(cudaEventRecord(ss.e[3], ss.s));
+    HX_CUDA(cudaStreamWaitEvent(ev.s, ss.e[3], 0));
     // Step 3: one relinearisation, then the two rescales
     return ev.rescale(ev.rescale(ev.relinearize(acc, ks.relin)));
 }
