@@ -315,22 +315,27 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
 {
     hx_context &ctx = ev.ctx;
     const int h = p.h, beta = p.beta;
-    Cts A0 = ev.rescale(lintrans(ev, ks, A, -h + 1, h - 1, 1, p, 0));
-    Cts B0 = ev.rescale(lintrans(ev, ks, B, 0, h - 1, h, p, 1));
-    // Step 2 (App. B multiplexer after hoisting): A^(k) = v_k . Rot(A0, k) + (1 - v_k) . Rot(A0, k-h),
-    // all rotations of A0 from one ModUp, the selection before a single ModDown per k.  A^(k)
-    // keeps the mask scale (no rescale per k); B^(k) = Rot(B0, h*k) stays at the same level.
-    const uint64_t qt = ctx.primes[A0.limbs - 1];
-    Cts acc = ev.tensor(ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt), B0);
-    BufPtr DA = ev.hoist(A0);
-    BufPtr DB = ev.hoist(B0);  // one ModUp serves every B^(k)
-    // the B^(k) chain runs on a side stream beside the A^(k) chain: fork after the hoists; each
-    // B^(k) is consumed on the main stream, and the side stream waits for that use before it
-    // frees B^(k); join before DB is released
+    // the B side (B0 = U^zeta b, its hoisted ModUp and every B^(k) = Rot(B0, h*k)) runs on a side
+    // stream beside the A side: fork once the inputs are ready; every B-side buffer the main
+    // stream reads is freed on the side stream only after the side stream has waited for that
+    // read; join before the B-side buffers are released
     SideStream &ss = side_stream(ctx, ev.s);
     Eval ev2(ctx, ss.s);
     HX_CUDA(cudaEventRecord(ss.e[0], ev.s));
     HX_CUDA(cudaStreamWaitEvent(ss.s, ss.e[0], 0));
+    Cts B0 = ev2.rescale(lintrans(ev2, ks, B, 0, h - 1, h, p, 1));
+    BufPtr DB = ev2.hoist(B0);  // one ModUp serves every B^(k)
+    HX_CUDA(cudaEventRecord(ss.e[1], ss.s));
+    Cts A0 = ev.rescale(lintrans(ev, ks, A, -h + 1, h - 1, 1, p, 0));
+    BufPtr DA = ev.hoist(A0);
+    // Step 2 (App. B multiplexer after hoisting): A^(k) = v_k . Rot(A0, k) + (1 - v_k) . Rot(A0, k-h),
+    // all rotations of A0 from one ModUp, the selection before a single ModDown per k.  A^(k)
+    // keeps the mask scale (no rescale per k); B^(k) = Rot(B0, h*k) stays at the same level.
+    const uint64_t qt = ctx.primes[A0.limbs - 1];
+    HX_CUDA(cudaStreamWaitEvent(ev.s, ss.e[1], 0));
+    Cts acc = ev.tensor(ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt), B0);
+    HX_CUDA(cudaEventRecord(ss.e[2], ev.s));
+    HX_CUDA(cudaStreamWaitEvent(ss.s, ss.e[2], 0));
     for (int k = 1; k < t; k++) {
         Cts Bk = ev2.rotate_hoisted_one(B0, DB, (int64_t)beta * h * k, ks);
         HX_CUDA(cudaEventRecord(ss.e[1], ss.s));
@@ -343,6 +348,8 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
         HX_CUDA(cudaEventRecord(ss.e[2], ev.s));
         HX_CUDA(cudaStreamWaitEvent(ss.s, ss.e[2], 0));
     }
+    B0 = Cts();  // the B-side buffers go back to the pool on the side stream, before the join
+    DB.reset();
     HX_CUDA(cudaEventRecord(ss.e[3], ss.s));
     HX_CUDA(cudaStreamWaitEvent(ev.s, ss.e[3], 0));
     // Step 3: one relinearisation, then the two rescales
