@@ -235,6 +235,7 @@ SideStream &side_stream(hx_context &ctx, cudaStream_t main)
     SideStream &ss = ctx.side[main];
     if (!ss.s) {
         HX_CUDA(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
+        HX_CUDA(cudaStreamCreateWithFlags(&ss.s2, cudaStreamNonBlocking));
         for (auto &e : ss.e) HX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     }
     return ss;
@@ -249,6 +250,7 @@ void destroy_context(hx_context &c)
         for (auto &e : kv.second.e)
             if (e) cudaEventDestroy(e);
         if (kv.second.s) cudaStreamDestroy(kv.second.s);
+        if (kv.second.s2) cudaStreamDestroy(kv.second.s2);
     }
     c.side.clear();
     cudaFree(c.t.primes);

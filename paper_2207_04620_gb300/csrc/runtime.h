@@ -52,8 +52,8 @@ struct EncTables {  // device tables of the client-side encoder
 // a second stream paired with a caller's stream, for independent chains of one
 // schedule (fork/join by events; inside a capture it joins the same graph)
 struct SideStream {
-    cudaStream_t s = nullptr;
-    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaStream_t s = nullptr, s2 = nullptr;  // two side streams
+    cudaEvent_t e[8] = {};
 };
 } // namespace hx
 

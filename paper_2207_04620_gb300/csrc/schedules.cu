@@ -315,43 +315,65 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
 {
     hx_context &ctx = ev.ctx;
     const int h = p.h, beta = p.beta;
-    // the B side (B0 = U^zeta b, its hoisted ModUp and every B^(k) = Rot(B0, h*k)) runs on a side
-    // stream beside the A side: fork once the inputs are ready; every B-side buffer the main
-    // stream reads is freed on the side stream only after the side stream has waited for that
-    // read; join before the B-side buffers are released
+    // three chains on three streams: the B side (B0 = U^zeta b, its hoisted ModUp and every
+    // B^(k) = Rot(B0, h*k)) on side stream sb; the selections A^(k) and their products for even k
+    // on the main stream and for odd k on side stream sa, each into its own accumulator.  Every
+    // buffer a stream reads from another is released on its own stream only after that stream
+    // has waited for the read; everything is joined before the accumulators are summed.
     SideStream &ss = side_stream(ctx, ev.s);
-    Eval ev2(ctx, ss.s);
-    HX_CUDA(cudaEventRecord(ss.e[0], ev.s));
-    HX_CUDA(cudaStreamWaitEvent(ss.s, ss.e[0], 0));
-    Cts B0 = ev2.rescale(lintrans(ev2, ks, B, 0, h - 1, h, p, 1));
-    BufPtr DB = ev2.hoist(B0);  // one ModUp serves every B^(k)
-    HX_CUDA(cudaEventRecord(ss.e[1], ss.s));
+    Eval evb(ctx, ss.s), eva(ctx, ss.s2);
+    cudaEvent_t *e = ss.e;  // 0 fork, 1 B0 ready, 2 A0 ready, 3/4 B^(k) ready, 5/6 B^(k) used, 7 joins
+    HX_CUDA(cudaEventRecord(e[0], ev.s));
+    HX_CUDA(cudaStreamWaitEvent(ss.s, e[0], 0));
+    HX_CUDA(cudaStreamWaitEvent(ss.s2, e[0], 0));
+    Cts B0 = evb.rescale(lintrans(evb, ks, B, 0, h - 1, h, p, 1));
+    BufPtr DB = evb.hoist(B0);  // one ModUp serves every B^(k)
+    HX_CUDA(cudaEventRecord(e[1], ss.s));
     Cts A0 = ev.rescale(lintrans(ev, ks, A, -h + 1, h - 1, 1, p, 0));
     BufPtr DA = ev.hoist(A0);
     // Step 2 (App. B multiplexer after hoisting): A^(k) = v_k . Rot(A0, k) + (1 - v_k) . Rot(A0, k-h),
     // all rotations of A0 from one ModUp, the selection before a single ModDown per k.  A^(k)
     // keeps the mask scale (no rescale per k); B^(k) = Rot(B0, h*k) stays at the same level.
     const uint64_t qt = ctx.primes[A0.limbs - 1];
-    HX_CUDA(cudaStreamWaitEvent(ev.s, ss.e[1], 0));
+    Cts acc_odd = ev.alloc(A0.B, 3, A0.limbs);  // the odd-k accumulator, zero, owned by the main stream
+    HX_CUDA(cudaMemsetAsync(acc_odd.d, 0, sizeof(uint64_t) * acc_odd.bstride(ctx.N) * acc_odd.B, ev.s));
+    HX_CUDA(cudaEventRecord(e[2], ev.s));
+    HX_CUDA(cudaStreamWaitEvent(ss.s2, e[2], 0));
+    HX_CUDA(cudaStreamWaitEvent(ev.s, e[1], 0));
     Cts acc = ev.tensor(ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt), B0);
-    HX_CUDA(cudaEventRecord(ss.e[2], ev.s));
-    HX_CUDA(cudaStreamWaitEvent(ss.s, ss.e[2], 0));
+    acc_odd.scale = acc.scale;
+    HX_CUDA(cudaEventRecord(e[5], ev.s));
+    HX_CUDA(cudaStreamWaitEvent(ss.s, e[5], 0));  // B0's read by the main stream comes before its release
+    Cts held[2];  // B^(k) stays alive until its consumer's use is ordered before the release
     for (int k = 1; k < t; k++) {
-        Cts Bk = ev2.rotate_hoisted_one(B0, DB, (int64_t)beta * h * k, ks);
-        HX_CUDA(cudaEventRecord(ss.e[1], ss.s));
+        const int par = k & 1;
+        if (held[par].buf) {  // B^(k-2): released on sb after its consumer (same parity) used it
+            HX_CUDA(cudaStreamWaitEvent(ss.s, e[5 + par], 0));
+            held[par] = Cts();
+        }
+        held[par] = evb.rotate_hoisted_one(B0, DB, (int64_t)beta * h * k, ks);
+        HX_CUDA(cudaEventRecord(e[3 + par], ss.s));
+        Eval &ec = par ? eva : ev;
         double sc;
         const uint64_t *v = mask_pt(p, 2, k, &sc);
         const uint64_t *pm = (p.bound_uid && p.bound_uid == ks.uid) ? p.premasked[k]->p : nullptr;
-        Cts Ak = ev.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, qt, ks, pm);
-        HX_CUDA(cudaStreamWaitEvent(ev.s, ss.e[1], 0));
-        ev.tensor_acc(acc, Ak, Bk);
-        HX_CUDA(cudaEventRecord(ss.e[2], ev.s));
-        HX_CUDA(cudaStreamWaitEvent(ss.s, ss.e[2], 0));
+        Cts Ak = ec.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, qt, ks, pm);
+        HX_CUDA(cudaStreamWaitEvent(ec.s, e[3 + par], 0));
+        ec.tensor_acc(par ? acc_odd : acc, Ak, held[par]);
+        HX_CUDA(cudaEventRecord(e[5 + par], ec.s));
     }
-    B0 = Cts();  // the B-side buffers go back to the pool on the side stream, before the join
+    for (int par = 0; par < 2; par++)
+        if (held[par].buf) {
+            HX_CUDA(cudaStreamWaitEvent(ss.s, e[5 + par], 0));
+            held[par] = Cts();
+        }
+    B0 = Cts();  // the B-side buffers go back to the pool on sb, before the join
     DB.reset();
-    HX_CUDA(cudaEventRecord(ss.e[3], ss.s));
-    HX_CUDA(cudaStreamWaitEvent(ev.s, ss.e[3], 0));
+    HX_CUDA(cudaEventRecord(e[7], ss.s));
+    HX_CUDA(cudaStreamWaitEvent(ev.s, e[7], 0));
+    HX_CUDA(cudaEventRecord(e[7], ss.s2));
+    HX_CUDA(cudaStreamWaitEvent(ev.s, e[7], 0));
+    ev.add_inplace(acc, acc_odd);
     // Step 3: one relinearisation, then the two rescales
     return ev.rescale(ev.rescale(ev.relinearize(acc, ks.relin)));
 }
