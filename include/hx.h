@@ -428,7 +428,9 @@ hx_status hx_ntt_tiles(hx_context *ctx, const int32_t *set, int32_t *get);
  * i (0-based): its name, the number of launches, their summed duration in ms
  * and their summed algorithmic bytes (the reads and writes the operation needs
  * at least, 8 bytes per residue); returns the number of classes, or HX_EINVAL
- * for i out of range. */
+ * for i out of range.  While enabled, the product's independent chains run one
+ * after another on the caller's stream (not on side streams), so each event
+ * interval is one kernel running alone. */
 hx_status hx_profile_enable(hx_context *ctx, int on);
 int hx_profile_read(hx_context *ctx, int i, char *name, size_t cap, uint64_t *launches, double *ms, double *bytes);
 

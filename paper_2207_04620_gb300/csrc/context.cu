@@ -232,6 +232,15 @@ void build_context(hx_context &c, const hx_params &p)
 SideStream &side_stream(hx_context &ctx, cudaStream_t main)
 {
     std::lock_guard<std::mutex> lk(ctx.side_mu);
+    if (ctx.profiling) {
+        // per-kernel timing runs the chains one after another on the caller's stream, so every
+        // launch's event interval is that kernel alone
+        SideStream &ser = ctx.side_serial[main];
+        if (!ser.e[0])
+            for (auto &e : ser.e) HX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ser.s = ser.s2 = main;
+        return ser;
+    }
     SideStream &ss = ctx.side[main];
     if (!ss.s) {
         HX_CUDA(cudaStreamCreateWithFlags(&ss.s, cudaStreamNonBlocking));
@@ -253,6 +262,10 @@ void destroy_context(hx_context &c)
         if (kv.second.s2) cudaStreamDestroy(kv.second.s2);
     }
     c.side.clear();
+    for (auto &kv : c.side_serial)
+        for (auto &e : kv.second.e)
+            if (e) cudaEventDestroy(e);
+    c.side_serial.clear();
     cudaFree(c.t.primes);
     cudaFree(c.t.tw_fwd);
     cudaFree(c.t.tw_inv);

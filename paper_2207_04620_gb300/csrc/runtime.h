@@ -80,7 +80,8 @@ struct hx_context {
     std::once_flag enc_once;
     hx::EncTables enc_dev;
     std::mutex side_mu;
-    std::map<cudaStream_t, hx::SideStream> side;  // keyed by the caller's stream
+    std::map<cudaStream_t, hx::SideStream> side;         // keyed by the caller's stream
+    std::map<cudaStream_t, hx::SideStream> side_serial;  // profiling: the caller's stream itself
 };
 
 struct hx_keyset {
