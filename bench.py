@@ -472,7 +472,7 @@ def run_sign(args):
             "value": round(count / t, 3), "unit": "ct/s", "slots_per_s": round(count * n_slots / t, 1),
             "ms_per_step": round(t * 1e3, 2), "steps": args.steps, "warmup": args.warmup, "n_gpus": 1,
             "higher_is_better": True, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "cfg2: 64 ciphertexts x 16384 slots, |x| in [2^-8, 1], d=4, k=8, two host refreshes "
+            "config": {"workload": "cfg2: 64 ciphertexts x 16384 slots, |x| in [2^-8, 1], d=4, k=8, two collective refreshes "
                                    "per step (timed with host wall clock: they cross the host)"},
             "max_err_vs_exact": max(errs_sgn), "max_err_vs_fp64_composite": max(errs_g), "clocks": clocks}
     print(json.dumps(line), flush=True)

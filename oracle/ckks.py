@@ -205,6 +205,16 @@ def sample_uniform(stream: Stream, q: int, n: int) -> np.ndarray:
     return out
 
 
+def sample_uniform_wide(stream: Stream, m: int, n: int) -> np.ndarray:
+    """Uniform residues mod m without rejection: value j is (d_2j * 2^64 + d_(2j+1)) mod m for the
+    stream's draws d (reading R17: every value depends on its own two draws only, bias below
+    m / 2^128)."""
+    d = stream.draws(2 * n)
+    hi = d[0::2].astype(object)
+    lo = d[1::2].astype(object)
+    return np.array([int((int(a) << 64) | int(b)) % m for a, b in zip(hi, lo)], dtype=np.uint64)
+
+
 def sample_ternary(stream: Stream, n: int) -> np.ndarray:
     """Coefficients in {-1, 0, 1}: draw % 3 mapped 0->0, 1->1, 2->-1."""
     r = (stream.draws(n) % np.uint64(3)).astype(np.int64)
@@ -561,10 +571,12 @@ def dkeyswitch(ctx: Context, ks_from: KeySet, ks_to: KeySet, ct: Ciphertext, see
 def dbootstrap(ctx: Context, ks: KeySet, ct: Ciphertext, seed: int, counter: int = 0) -> Ciphertext:
     """DBootstrap (Fig. 1 item 14), the collective refresh (reading R17):
     1. party i masks its decryption share at q_0: c1 s_i + M_i + e0_i with M_i
-       uniform in [-bound, bound], bound = (floor(q_0/4) - 1) // n_parties;
+       uniform in [-bound, bound], bound = (floor(q_0/4) - 1) // n_parties
+       (sample_uniform_wide, stream (seed, purpose, party, refresh index));
     2. v = centered(c0 + sum of the shares mod q_0) = Delta_ct m + e + sum M_i,
        which stays below q_0/2, is rescaled: m' = round(v Delta / Delta_ct);
-    3. against a common reference polynomial a (uniform over Q, NTT form),
+    3. against a common reference polynomial a (uniform over Q, NTT form, row r
+       from stream (seed, purpose, r, refresh index)),
        party i publishes -s_i a - round(M_i Delta / Delta_ct) + e1_i, and the
        refreshed ciphertext is (m' + sum of those shares, a) at the top level
        and scale Delta."""
@@ -576,7 +588,7 @@ def dbootstrap(ctx: Context, ks: KeySet, ct: Ciphertext, seed: int, counter: int
     acc = ctx.intt(ct.c[0, :1], q0l)[0].astype(object)
     w_parts = []
     for i, sp in enumerate(ks.s_parts_ntt):
-        M = sample_uniform(Stream(seed, PURPOSE_DB_MASK, i, counter), 2 * bound + 1, N).astype(np.int64) - bound
+        M = sample_uniform_wide(Stream(seed, PURPOSE_DB_MASK, i, counter), 2 * bound + 1, N).astype(np.int64) - bound
         e0 = sample_gaussian(Stream(seed, PURPOSE_DB_E0, i, counter), N, ctx.sigma)
         share = ctx.intt(ctx.mul(ct.c[1, :1], sp[:1], q0l), q0l)[0].astype(object)
         acc = (acc + share + (M + e0).astype(object)) % q0
@@ -584,8 +596,7 @@ def dbootstrap(ctx: Context, ks: KeySet, ct: Ciphertext, seed: int, counter: int
         w_parts.append(-round_half_away(M.astype(np.float64) * ratio).astype(np.int64) + e1)
     v = np.array([int(x) - q0 if int(x) > q0 // 2 else int(x) for x in acc], dtype=np.int64)
     m_new = round_half_away(v.astype(np.float64) * ratio).astype(np.int64)
-    st = Stream(seed, PURPOSE_DB_CRP, 0, counter)
-    a = np.stack([sample_uniform(st, t, N) for t in prim])
+    a = np.stack([sample_uniform_wide(Stream(seed, PURPOSE_DB_CRP, r, counter), t, N) for r, t in enumerate(prim)])
     c0 = ctx.ntt(ctx.signed_to_rows(m_new, prim), prim)
     for i, sp in enumerate(ks.s_parts_ntt):
         w = ctx.ntt(ctx.signed_to_rows(w_parts[i], prim), prim)

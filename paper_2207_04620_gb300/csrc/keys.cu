@@ -114,6 +114,77 @@ __global__ void k_dboot_combine(View out, const uint64_t *__restrict__ W, const 
     }
 }
 
+constexpr uint64_t kGammaK = 0x9E3779B97F4A7C15ull;
+
+__device__ __forceinline__ uint64_t kmix64(uint64_t z)
+{
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// value j of the wide uniform sampler: (d_2j * 2^64 + d_(2j+1)) mod m, d_i = mix64(st + (i+1) gamma)
+__device__ __forceinline__ uint64_t uniform_wide_at(uint64_t st, int j, uint64_t m)
+{
+    const uint64_t hi = kmix64(st + (uint64_t)(2 * j + 1) * kGammaK);
+    const uint64_t lo = kmix64(st + (uint64_t)(2 * j + 2) * kGammaK);
+    return (uint64_t)((((unsigned __int128)hi << 64) | lo) % m);
+}
+
+// draw j of the discrete Gaussian (cumulative table th, 2*bound+1 entries)
+__device__ __forceinline__ int64_t gauss_at(uint64_t st, int j, const uint64_t *__restrict__ th, int bound)
+{
+    const uint64_t x = kmix64(st + (uint64_t)(j + 1) * kGammaK) >> 1;
+    int idx = 0;
+    while (idx < 2 * bound && x >= th[idx]) idx++;
+    return (int64_t)idx - bound;
+}
+
+__device__ __forceinline__ double round_half_away_dev(double x)
+{
+    const double r = floor(__dadd_rn(fabs(x), 0.5));
+    return x < 0 ? -r : r;
+}
+
+// Fig. 1 item 14, the masked decryption side for entry b, coefficient j: every party's share
+// c1*s_i (sh, coefficient form mod q_0, after c0) plus its mask M_i and e0_i, summed with c0;
+// the centered sum rescaled to the output scale (W[b][0]) and every party's re-encryption
+// coefficients -round(M_i * ratio) + e1_i (W[b][1+i]).  st: [B][n_parties][3] stream states
+// (mask, e0, e1).
+__global__ void k_dboot_shares(int64_t *W, const uint64_t *__restrict__ sh, const uint64_t *__restrict__ st,
+                               const uint64_t *__restrict__ th, int gbound, uint64_t mbound, uint64_t q0, double ratio,
+                               int np, int n)
+{
+    const int b = blockIdx.y;
+    const uint64_t *shb = sh + (size_t)b * (np + 1) * n;
+    int64_t *Wb = W + (size_t)b * (np + 1) * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        uint64_t v = shb[j];
+        for (int i = 0; i < np; i++) {
+            const uint64_t *s3 = st + ((size_t)b * np + i) * 3;
+            const int64_t M = (int64_t)uniform_wide_at(s3[0], j, 2 * mbound + 1) - (int64_t)mbound;
+            const int64_t add = M + gauss_at(s3[1], j, th, gbound);
+            uint64_t t = shb[(size_t)(i + 1) * n + j];
+            t = add >= 0 ? (t + (uint64_t)add) % q0 : (t + q0 - ((uint64_t)(-add)) % q0) % q0;
+            v = (v + t) % q0;
+            Wb[(size_t)(i + 1) * n + j] =
+                -(int64_t)round_half_away_dev(__dmul_rn((double)M, ratio)) + gauss_at(s3[2], j, th, gbound);
+        }
+        const int64_t c = v > q0 / 2 ? (int64_t)v - (int64_t)q0 : (int64_t)v;
+        Wb[j] = (int64_t)round_half_away_dev(__dmul_rn((double)c, ratio));
+    }
+}
+
+// the common reference polynomial of entry b: row r uniform mod q_r (NTT form), stream st[b][r]
+__global__ void k_dboot_crp(uint64_t *A, const uint64_t *__restrict__ st, const PrimeConst *__restrict__ primes,
+                            int nq, int n)
+{
+    const int r = blockIdx.y, b = blockIdx.z;
+    const uint64_t q = primes[r].q, s0 = st[(size_t)b * nq + r];
+    uint64_t *o = A + ((size_t)b * nq + r) * n;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) o[j] = uniform_wide_at(s0, j, q);
+}
+
 int blocks_for(int n) { return (n + 255) / 256; }
 
 // the parties' ternary shares as NTT-form residues over primes 0..rows-1
@@ -291,53 +362,43 @@ Cts dbootstrap(hx_context &ctx, const hx_keyset &ks, const Cts &ct, const std::v
     const uint64_t q0 = ctx.primes[0];
     const uint64_t bound = (q0 / 4 - 1) / (uint64_t)np;
     const double ratio = ctx.scale / ct.scale;
-    const std::vector<uint64_t> sh = ddec_share_polys(ctx, ks, ct, s);
-    std::vector<int64_t> W((size_t)B * (np + 1) * N);
-    std::vector<uint64_t> A((size_t)B * nq * N);
-    std::vector<uint64_t> mask(N);
-    std::vector<int64_t> e(N);
-    std::vector<uint64_t> v(N);
-    for (int b = 0; b < B; b++) {
-        const uint64_t *shb = sh.data() + (size_t)b * (np + 1) * N;
-        for (int k = 0; k < N; k++) v[k] = shb[k];  // c0
-        int64_t *Wb = W.data() + (size_t)b * (np + 1) * N;
-        for (int i = 0; i < np; i++) {
-            Stream sm(seeds[b], P_DB_MASK, i, counter), s0(seeds[b], P_DB_E0, i, counter),
-                s1(seeds[b], P_DB_E1, i, counter);
-            sample_uniform(sm, 2 * bound + 1, mask.data(), N);
-            for (int k = 0; k < N; k++) {
-                const int64_t M = (int64_t)mask[k] - (int64_t)bound;
-                const int64_t e0 = ctx.cdt->draw(s0);
-                // party i's masked decryption share, added mod q_0
-                uint64_t t = shb[(size_t)(i + 1) * N + k];
-                const int64_t add = M + e0;
-                t = add >= 0 ? (t + (uint64_t)add) % q0 : (t + q0 - ((uint64_t)(-add)) % q0) % q0;
-                v[k] = (v[k] + t) % q0;
-                mask[k] = (uint64_t)M;  // keep the signed mask for the re-encryption share
-            }
-            int64_t *Wi = Wb + (size_t)(i + 1) * N;
-            for (int k = 0; k < N; k++)
-                Wi[k] = -(int64_t)round_half_away((double)(int64_t)mask[k] * ratio) + ctx.cdt->draw(s1);
-        }
-        for (int k = 0; k < N; k++) {
-            const int64_t c = v[k] > q0 / 2 ? (int64_t)v[k] - (int64_t)q0 : (int64_t)v[k];
-            Wb[k] = (int64_t)round_half_away((double)c * ratio);
-        }
-        Stream sa(seeds[b], P_DB_CRP, 0, counter);
-        for (int r = 0; r < nq; r++) sample_uniform(sa, ctx.primes[r], A.data() + ((size_t)b * nq + r) * N, N);
-    }
     Eval ev(ctx, s);
-    DevBuf Wd((size_t)B * (np + 1) * nq * N, s), Ad((size_t)B * nq * N, s);
-    signed_polys_to_ntt(ctx, s, W, B * (np + 1), nq, Wd.p);
-    HX_CUDA(cudaMemcpyAsync(Ad.p, A.data(), sizeof(uint64_t) * A.size(), cudaMemcpyHostToDevice, s));
+    // every party's decryption share c1*s_i at q_0, coefficient form, on the device
+    DevBuf sh((size_t)B * (np + 1) * N, s);
+    launch_ddec_shares(ev.lc(), sh.p, ct.view(N), ks.s_parts0->p, np, B);
+    ev.ntt_inplace(sh.p, (size_t)N, B * (np + 1), {0}, {0}, true);
+    // stream states: masks and errors per (entry, party), the reference polynomial per (entry, row)
+    std::vector<uint64_t> st((size_t)B * np * 3), st_crp((size_t)B * nq);
+    for (int b = 0; b < B; b++) {
+        for (int i = 0; i < np; i++) {
+            st[((size_t)b * np + i) * 3 + 0] = Stream(seeds[b], P_DB_MASK, i, counter).state;
+            st[((size_t)b * np + i) * 3 + 1] = Stream(seeds[b], P_DB_E0, i, counter).state;
+            st[((size_t)b * np + i) * 3 + 2] = Stream(seeds[b], P_DB_E1, i, counter).state;
+        }
+        for (int r = 0; r < nq; r++) st_crp[(size_t)b * nq + r] = Stream(seeds[b], P_DB_CRP, r, counter).state;
+    }
+    DevBuf st_d(st.size(), s), stc_d(st_crp.size(), s), th_d(ctx.cdt->th.size(), s);
+    HX_CUDA(cudaMemcpyAsync(st_d.p, st.data(), sizeof(uint64_t) * st.size(), cudaMemcpyHostToDevice, s));
+    HX_CUDA(cudaMemcpyAsync(stc_d.p, st_crp.data(), sizeof(uint64_t) * st_crp.size(), cudaMemcpyHostToDevice, s));
+    HX_CUDA(cudaMemcpyAsync(th_d.p, ctx.cdt->th.data(), sizeof(uint64_t) * ctx.cdt->th.size(), cudaMemcpyHostToDevice,
+                            s));
+    DevBuf W((size_t)B * (np + 1) * N, s), Wd((size_t)B * (np + 1) * nq * N, s), Ad((size_t)B * nq * N, s);
+    k_dboot_shares<<<dim3(blocks_for(N), B), 256, 0, s>>>(reinterpret_cast<int64_t *>(W.p), sh.p, st_d.p, th_d.p,
+                                                          ctx.cdt->bound, bound, q0, ratio, np, N);
+    k_dboot_crp<<<dim3(blocks_for(N), nq, B), 256, 0, s>>>(Ad.p, stc_d.p, ctx.t.primes, nq, N);
+    HX_CUDA(cudaGetLastError());
+    // the rescaled plaintext and the parties' re-encryption coefficients over Q, NTT form
+    launch_signed_to_rows(ev.lc(), Wd.p, reinterpret_cast<const int64_t *>(W.p), nq, B * (np + 1), (size_t)N,
+                          ctx.d_prime_ids);
+    ev.ntt_inplace(Wd.p, (size_t)nq * N, B * (np + 1), iota_vec(0, nq), iota_vec(0, nq), false);
     BufPtr S = party_shares_ntt(ctx, ks, nq, s);
     Cts out = ev.alloc(B, 2, nq);
     out.scale = ctx.scale;
     k_dboot_combine<<<dim3(blocks_for(N), nq, B), 256, 0, s>>>(out.view(N), Wd.p, Ad.p, S->p, ctx.t.primes, np, nq, N);
     HX_CUDA(cudaGetLastError());
-    ctx.counters[C_LAUNCH] += 1;
+    ctx.counters[C_LAUNCH] += 3;
     ctx.counters[C_REFRESH] += B;
-    HX_CUDA(cudaStreamSynchronize(s));  // host staging buffers go out of scope
+    HX_CUDA(cudaStreamSynchronize(s));  // the host stream-state vectors go out of scope
     return out;
 }
 

@@ -38,6 +38,14 @@ def test_samplers():
     C.sample_uniform(s, 11, 100)
     raw = C.Stream(3, C.PURPOSE_KEY_A).draws(s.count) & np.uint64(15)
     assert int((raw < 11).sum()) == 100 and int(raw[-1]) < 11
+    # the wide sampler: value j from draws 2j and 2j+1 only; uniform over [0, m)
+    m = (1 << 57) + 12345
+    w = C.sample_uniform_wide(C.Stream(4, C.PURPOSE_DB_MASK), m, n)
+    d = C.Stream(4, C.PURPOSE_DB_MASK).draws(2 * n)
+    assert all(int(w[j]) == ((int(d[2 * j]) << 64) + int(d[2 * j + 1])) % m for j in (0, 1, 7, n - 1))
+    assert w.max() < m and abs(np.mean(w.astype(np.float64)) / m - 0.5) < 0.01
+    small = C.sample_uniform_wide(C.Stream(5, C.PURPOSE_DB_CRP), 7, n)
+    assert all(abs(np.mean(small == v) - 1 / 7) < 0.01 for v in range(7))
 
 
 @pytest.mark.parametrize("log_n", [5, 8])
