@@ -419,7 +419,7 @@ def g4_iter(x, k):
 def run_sign(args):
     """Config 2: g_4^(8) (sign, or ReLU with --relu) on 64 ciphertexts of 16384 slots each, CKKS
     N=2^15, Q = 60 + 15x40 bit, P = 3x60 bit, scale 2^40, inputs uniform in [-1,-2^-8] U [2^-8,1];
-    the host refresh (collective decryption + re-encryption) runs after compositions 3 and 6 and
+    the collective refresh (DBootstrap on the device) runs after compositions 3 and 6 and
     is inside the timed region."""
     import torch
 
@@ -472,8 +472,8 @@ def run_sign(args):
             "value": round(count / t, 3), "unit": "ct/s", "slots_per_s": round(count * n_slots / t, 1),
             "ms_per_step": round(t * 1e3, 2), "steps": args.steps, "warmup": args.warmup, "n_gpus": 1,
             "higher_is_better": True, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "cfg2: 64 ciphertexts x 16384 slots, |x| in [2^-8, 1], d=4, k=8, two collective refreshes "
-                                   "per step (timed with host wall clock: they cross the host)"},
+            "config": {"workload": "cfg2: 64 ciphertexts x 16384 slots, |x| in [2^-8, 1], d=4, k=8, two collective "
+                                   "refreshes per entry (DBootstrap shares on the device), host wall clock"},
             "max_err_vs_exact": max(errs_sgn), "max_err_vs_fp64_composite": max(errs_g), "clocks": clocks}
     print(json.dumps(line), flush=True)
     hx.hx_keyset_destroy(ks)
@@ -485,7 +485,7 @@ def run_dense(args):
     batch of 64 inputs, 64 x 64 blocks (2 x 13 block products, packed 4 per ciphertext: 8
     ciphertext pairs per HE-MatMult batch), ReLU by g_4^(8)(E/4), CKKS N=2^15, Q = 60 + 15x40 bit,
     P = 3x60 bit, scale 2^40; weights N(0, 0.05), inputs U[0,1], upstream gradient N(0, 0.1).
-    The host refreshes inside the composite sign are in the timed region."""
+    The collective refreshes inside the composite sign are in the timed region."""
     import torch
 
     from paper_2207_04620_gb300 import hx, workloads
@@ -558,7 +558,7 @@ def run_dense(args):
             "steps": args.steps, "warmup": args.warmup, "n_gpus": 1, "higher_is_better": True, "dtype": "u64",
             "data": "synthetic",
             "config": {"workload": "cfg3: W 128x784 (padded 128x832), X 784x64, h=64, beta=4, 8+8 ciphertext pairs "
-                                   "per HE-MatMult batch, ReLU g_4^(8)(E/4), host refreshes timed (host wall clock)"},
+                                   "per HE-MatMult batch, ReLU g_4^(8)(E/4), collective refreshes timed (host wall clock)"},
             "max_abs_err": err, "clocks": clocks}
     print(json.dumps(line), flush=True)
     hx.hx_keyset_destroy(ks)
