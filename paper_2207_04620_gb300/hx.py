@@ -439,6 +439,8 @@ def hx_matmul(ctx, ks, A, B, h, stream=None) -> int:
 
 def hx_matmul_batch(ctx, ks, plan, As, Bs, h, stream=None) -> list:
     n = len(As)
+    if len(Bs) != n:
+        raise ValueError("A and B batches differ in length")
     a = (c_vp * n)(*As)
     b = (c_vp * n)(*Bs)
     outs = (c_vp * n)()
@@ -448,6 +450,8 @@ def hx_matmul_batch(ctx, ks, plan, As, Bs, h, stream=None) -> list:
 
 def hx_rmatmul_batch(ctx, ks, plan, Ats, Bs, h, t, stream=None) -> list:
     n = len(Ats)
+    if len(Bs) != n:
+        raise ValueError("A and B batches differ in length")
     a = (c_vp * n)(*Ats)
     b = (c_vp * n)(*Bs)
     outs = (c_vp * n)()
@@ -489,6 +493,8 @@ def hx_matmul_exec_create(ctx, ks, plan, count, scale) -> int:
 
 def hx_matmul_exec_run(ex, As, Bs, stream=None) -> list:
     n = len(As)
+    if len(Bs) != n:
+        raise ValueError("A and B batches differ in length")
     a = (c_vp * n)(*As)
     b = (c_vp * n)(*Bs)
     outs = (c_vp * n)()
@@ -537,6 +543,8 @@ def hx_dense_layer(ctx, ks, W, X, G, h, n_out, groups, d, k, input_div, refresh_
                    stream=None):
     """W: n_out*groups handles (i-major), X: groups handles, G: n_out handles; plans: (feedforward,
     transpose, backpropagation) plan handles, 0 for the cached ones; returns (E, M, dW)."""
+    if n_out >= 1 and groups >= 1 and (len(W) != n_out * groups or len(X) != groups or len(G) != n_out):
+        raise ValueError("need n_out*groups weights, groups inputs and n_out gradients")
     w = (c_vp * len(W))(*W)
     x = (c_vp * len(X))(*X)
     g = (c_vp * len(G))(*G)
@@ -569,6 +577,8 @@ def hx_dbootstrap(ctx, ks, ct, seed, stream=None) -> int:
 def hx_aggregate(ctx, grads, n_parties, models, eta_over_bn, stream=None) -> list:
     """grads: n_parties*len(models) handles, party-major; returns the updated models."""
     count = len(models)
+    if len(grads) != n_parties * count:
+        raise ValueError("need n_parties * len(models) gradients")
     g = (c_vp * len(grads))(*grads)
     m = (c_vp * count)(*models)
     outs = (c_vp * count)()

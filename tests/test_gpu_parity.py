@@ -253,6 +253,16 @@ def test_error_statuses(cfg0):
     assert e.value.code == -3
     with pytest.raises(hx.HxError):
         hx.hx_matmul_plan_create(ctx, 12, 3)    # h not a power of two
+    # empty and malformed batches are refused before any launch
+    for call in (lambda: hx.hx_matmul_batch(ctx, cfg0.ks, 0, [], [], 16),
+                 lambda: hx.hx_sign_approx_batch(ctx, cfg0.ks, [], 2, 1),
+                 lambda: hx.hx_aggregate(ctx, [], 0, [a], 0.1),
+                 lambda: hx.hx_rmatmul_batch(ctx, cfg0.ks, 0, [a], [a], 16, 3),   # t not a power of two
+                 lambda: hx.hx_dense_layer(ctx, cfg0.ks, [a], [a], [a], 16, 0, 1, 2, 1, 4.0),  # no output block
+                 lambda: hx.hx_encode_batch(ctx, np.ones((1, 1 << 20)), 2.0 ** 40)):  # more slots than N/2
+        with pytest.raises(hx.HxError) as e:
+            call()
+        assert e.value.code == -1
     for h_ in (a, b, one):
         hx.hx_ct_destroy(h_)
 
@@ -648,6 +658,29 @@ def test_dense_config3_full_size_against_fp64():
                     want = l_ref @ Xb[j].T if j < len(Xb) else np.zeros((h, h))
                     assert np.abs(got[q] - want).max() < 2 ** -9
         for c in E + M + dW + Wc + Xc + Gc:
+            hx.hx_ct_destroy(c)
+        hx.hx_keyset_destroy(ks)
+    finally:
+        hx.hx_context_destroy(ctx)
+
+
+@pytest.mark.slow
+def test_matmul_largest_h_at_n15_against_fp64():
+    """The largest product a 2^15 ring packs: h = 128 (beta = 1, every slot used), Alg. 3
+    at 5 limbs with the library's masks; the decryption equals A@B (128-term dot products)."""
+    h, ln = 128, 15
+    qb = [60, 45, 45, 45, 45]
+    ctx = hx.hx_context_create(ln, qb, [60, 60], 45)
+    try:
+        ks = hx.hx_keygen(ctx, 2, 9, hx.hx_matmul_rotation_steps(ctx, h, len(qb)))
+        a, b = workloads.matrices(71, 1, h)[0], workloads.matrices(72, 1, h)[0]
+        A = hx.hx_encrypt(ctx, ks, workloads.pack([a], h, 1), 0, 1)
+        B = hx.hx_encrypt(ctx, ks, workloads.pack([b], h, 1), 0, 2)
+        out = hx.hx_matmul(ctx, ks, A, B, h)
+        assert hx.hx_ct_info(out)[1] == len(qb) - 3
+        got = workloads.unpack(hx.hx_decrypt(ctx, ks, out), h, 1)[0]
+        assert np.abs(got - a @ b).max() < 2 ** -14
+        for c in (A, B, out):
             hx.hx_ct_destroy(c)
         hx.hx_keyset_destroy(ks)
     finally:
