@@ -164,32 +164,45 @@ __global__ void k_add_scalar_c0(View out, View a, const __grid_constant__ Scalar
 }
 
 // (a0,a1) x (b0,b1) -> (a0b0, a0b1+a1b0, a1b1), optionally added to out
+// two adjacent coefficients per thread, 16-byte loads and stores
+__device__ __forceinline__ void tensor_one(uint64_t a0, uint64_t a1, uint64_t b0, uint64_t b1, const PrimeConst &P,
+                                           uint64_t &r0, uint64_t &r1, uint64_t &r2)
+{
+    Acc128 d1;
+    d1.mac(a0, b1);
+    d1.mac(a1, b0);
+    r0 = shoup(mont128(__umul64hi(a0, b0), a0 * b0, P), P.r_mod, P.r_mod_sh, P.q);
+    r1 = shoup(mont128(d1.hi, d1.lo, P), P.r_mod, P.r_mod_sh, P.q);
+    r2 = shoup(mont128(__umul64hi(a1, b1), a1 * b1, P), P.r_mod, P.r_mod_sh, P.q);
+}
+
 __global__ void k_tensor(View out, View a, View b, const PrimeConst *__restrict__ primes, int n, bool acc)
 {
     const int l = blockIdx.y, bi = blockIdx.z;
     const PrimeConst P = primes[l];
     const size_t la = bi * a.bstride + (size_t)l * n, lb = bi * b.bstride + (size_t)l * n;
     const size_t lo = bi * out.bstride + (size_t)l * n;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const uint64_t a0 = a.p[la + j], a1 = a.p[la + a.cstride + j];
-        const uint64_t b0 = b.p[lb + j], b1 = b.p[lb + b.cstride + j];
-        Acc128 d1;
-        d1.mac(a0, b1);
-        d1.mac(a1, b0);
-        uint64_t r0 = mont128(__umul64hi(a0, b0), a0 * b0, P);
-        uint64_t r1 = mont128(d1.hi, d1.lo, P);
-        uint64_t r2 = mont128(__umul64hi(a1, b1), a1 * b1, P);
-        r0 = shoup(r0, P.r_mod, P.r_mod_sh, P.q);
-        r1 = shoup(r1, P.r_mod, P.r_mod_sh, P.q);
-        r2 = shoup(r2, P.r_mod, P.r_mod_sh, P.q);
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 a0 = *reinterpret_cast<const ulonglong2 *>(a.p + la + j);
+        const ulonglong2 a1 = *reinterpret_cast<const ulonglong2 *>(a.p + la + a.cstride + j);
+        const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(b.p + lb + j);
+        const ulonglong2 b1 = *reinterpret_cast<const ulonglong2 *>(b.p + lb + b.cstride + j);
+        uint64_t x0, x1, x2, y0, y1, y2;
+        tensor_one(a0.x, a1.x, b0.x, b1.x, P, x0, x1, x2);
+        tensor_one(a0.y, a1.y, b0.y, b1.y, P, y0, y1, y2);
+        ulonglong2 r0 = make_ulonglong2(x0, y0), r1 = make_ulonglong2(x1, y1), r2 = make_ulonglong2(x2, y2);
+        ulonglong2 *o0 = reinterpret_cast<ulonglong2 *>(out.p + lo + j);
+        ulonglong2 *o1 = reinterpret_cast<ulonglong2 *>(out.p + lo + out.cstride + j);
+        ulonglong2 *o2 = reinterpret_cast<ulonglong2 *>(out.p + lo + 2 * out.cstride + j);
         if (acc) {
-            r0 = addmod(r0, out.p[lo + j], P.q);
-            r1 = addmod(r1, out.p[lo + out.cstride + j], P.q);
-            r2 = addmod(r2, out.p[lo + 2 * out.cstride + j], P.q);
+            const ulonglong2 x0 = *o0, x1 = *o1, x2 = *o2;
+            r0.x = addmod(r0.x, x0.x, P.q), r0.y = addmod(r0.y, x0.y, P.q);
+            r1.x = addmod(r1.x, x1.x, P.q), r1.y = addmod(r1.y, x1.y, P.q);
+            r2.x = addmod(r2.x, x2.x, P.q), r2.y = addmod(r2.y, x2.y, P.q);
         }
-        out.p[lo + j] = r0;
-        out.p[lo + out.cstride + j] = r1;
-        out.p[lo + 2 * out.cstride + j] = r2;
+        *o0 = r0;
+        *o1 = r1;
+        *o2 = r2;
     }
 }
 
@@ -436,15 +449,23 @@ __global__ void k_moddown_final_mux(View out, View acc, View conv, const ModDown
     const uint64_t *cv = conv.p + bi * conv.bstride + ci * conv.cstride + (size_t)t * n;
     uint64_t *o = out.p + bi * out.bstride + ci * out.cstride + (size_t)t * n;
     const uint64_t *c0 = src.p + bi * src.bstride + (size_t)t * n;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        uint64_t r = shoup(submod(a[j], cv[j], q), w, wsh, q);
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 av = *reinterpret_cast<const ulonglong2 *>(a + j);
+        const ulonglong2 cw = *reinterpret_cast<const ulonglong2 *>(cv + j);
+        uint64_t r[2] = {shoup(submod(av.x, cw.x, q), w, wsh, q), shoup(submod(av.y, cw.y, q), w, wsh, q)};
         if (ci == 0) {
-            const uint64_t s1 = c0[galois_src(j, g1, log_n)], s2 = c0[galois_src(j, g2, log_n)];
-            const uint64_t vv = v[(size_t)t * n + j], d = submod(s1, s2, q);
-            const uint64_t sel = addmod(shoup(s2, cs.v[t], cs.sh[t], q), mont128(__umul64hi(vv, d), vv * d, P), q);
-            r = addmod(r, sel, q);
+            const ulonglong2 vv2 = *reinterpret_cast<const ulonglong2 *>(v + (size_t)t * n + j);
+            const uint64_t vs[2] = {vv2.x, vv2.y};
+#pragma unroll
+            for (int u = 0; u < 2; u++) {
+                const uint64_t s1 = c0[galois_src(j + u, g1, log_n)], s2 = c0[galois_src(j + u, g2, log_n)];
+                const uint64_t d = submod(s1, s2, q);
+                const uint64_t sel =
+                    addmod(shoup(s2, cs.v[t], cs.sh[t], q), mont128(__umul64hi(vs[u], d), vs[u] * d, P), q);
+                r[u] = addmod(r[u], sel, q);
+            }
         }
-        o[j] = r;
+        *reinterpret_cast<ulonglong2 *>(o + j) = make_ulonglong2(r[0], r[1]);
     }
 }
 
@@ -460,10 +481,23 @@ __global__ void k_moddown_final(View out, View acc, View conv, const ModDownTabl
     uint64_t *o = out.p + bi * out.bstride + ci * out.cstride + (size_t)t * n;
     const bool has = (add_mask >> ci) & 1;
     const uint64_t *ap = has ? add.p + bi * add.bstride + ci * add.cstride + (size_t)t * n : nullptr;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        uint64_t r = shoup(submod(a[j], cv[j], q), w, wsh, q);
-        if (has) r = addmod(r, ap[g == 1 ? j : galois_src(j, g, log_n)], q);
-        o[j] = r;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 av = *reinterpret_cast<const ulonglong2 *>(a + j);
+        const ulonglong2 cw = *reinterpret_cast<const ulonglong2 *>(cv + j);
+        ulonglong2 r;
+        r.x = shoup(submod(av.x, cw.x, q), w, wsh, q);
+        r.y = shoup(submod(av.y, cw.y, q), w, wsh, q);
+        if (has) {
+            if (g == 1) {
+                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(ap + j);
+                r.x = addmod(r.x, x.x, q);
+                r.y = addmod(r.y, x.y, q);
+            } else {
+                r.x = addmod(r.x, ap[galois_src(j, g, log_n)], q);
+                r.y = addmod(r.y, ap[galois_src(j + 1, g, log_n)], q);
+            }
+        }
+        *reinterpret_cast<ulonglong2 *>(o + j) = r;
     }
 }
 
@@ -657,7 +691,7 @@ void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &s
 void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate)
 {
     Timed tm_(c, K_TENSOR, 8.0 * B * limbs * c.N * (accumulate ? 10 : 7));
-    dim3 grid(ew_blocks(c.N, 1), limbs, B);
+    dim3 grid(ew_blocks(c.N, 2), limbs, B);
     k_tensor<<<grid, 256, 0, c.stream>>>(out3, a, b, c.t->primes, c.N, accumulate);
     post(c);
 }
@@ -761,7 +795,7 @@ void launch_moddown_final_mux(const LaunchCtx &c, View out, View acc, View conv,
                               int limbs, View src, const uint64_t *v, const Scalars &cs, uint64_t g1, uint64_t g2)
 {
     Timed tm_(c, K_MODDOWN, 8.0 * B * limbs * c.N * 9.0);
-    dim3 grid(ew_blocks(c.N, 1), limbs, B * 2);
+    dim3 grid(ew_blocks(c.N, 2), limbs, B * 2);
     k_moddown_final_mux<<<grid, 256, 0, c.stream>>>(out, acc, conv, tab, c.t->primes, src, v, cs, g1, g2, c.log_n);
     post(c);
 }
@@ -770,7 +804,7 @@ void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, con
                           int limbs, View add, int add_mask, uint64_t g)
 {
     Timed tm_(c, K_MODDOWN, 8.0 * B * 2 * limbs * c.N * ((add_mask ? 4.0 : 3.0)));
-    dim3 grid(ew_blocks(c.N, 1), limbs, B * 2);
+    dim3 grid(ew_blocks(c.N, 2), limbs, B * 2);
     k_moddown_final<<<grid, 256, 0, c.stream>>>(out, acc, conv, tab, c.t->primes, add, add_mask, g, c.log_n);
     post(c);
 }
