@@ -225,10 +225,14 @@ __global__ void k_automorphism(View out, View in, uint64_t g, int comps, int log
 __global__ void k_basis_convert(const ConvTable *__restrict__ tabs, View out, View in, const PrimeConst *__restrict__ primes,
                                 int groups, size_t gstride_out, size_t gstride_in, int n)
 {
+    // two adjacent coefficients per thread (16-byte loads and stores); the table's constants
+    // staged in shared memory once per block
     const int bz = blockIdx.z, bi = bz / groups, gi = bz % groups;
     const ConvTable &T = tabs[gi];
     __shared__ uint64_t smont[MAXK * MAXP];
     __shared__ uint64_t sq[MAXP], sbar[MAXP], smneg[MAXP];
+    __shared__ uint64_t ssq[MAXK], sinv[MAXK], sinvsh[MAXK];
+    __shared__ int sdrow[MAXP], ssrow[MAXK];
     const int ns = T.n_src, nd = T.n_dst;
     for (int i = threadIdx.x; i < ns * nd; i += blockDim.x) smont[i] = T.mont[i / nd][i % nd];
     for (int d = threadIdx.x; d < nd; d += blockDim.x) {
@@ -236,27 +240,41 @@ __global__ void k_basis_convert(const ConvTable *__restrict__ tabs, View out, Vi
         sq[d] = P.q;
         sbar[d] = P.bar;
         smneg[d] = P.mneg;
+        sdrow[d] = T.dst_row[d];
+    }
+    for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+        ssq[i] = primes[T.src_prime[i]].q;
+        sinv[i] = T.inv[i];
+        sinvsh[i] = T.inv_sh[i];
+        ssrow[i] = T.src_row[i];
     }
     __syncthreads();
     const uint64_t *src = in.p + bi * in.bstride + gi * gstride_in;
     uint64_t *dst = out.p + bi * out.bstride + gi * gstride_out;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        uint64_t y[MAXK];
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        uint64_t y0[MAXK], y1[MAXK];
 #pragma unroll
         for (int i = 0; i < MAXK; i++) {
             if (i < ns) {
-                const uint64_t qi = primes[T.src_prime[i]].q;
-                y[i] = shoup(src[(size_t)T.src_row[i] * n + j], T.inv[i], T.inv_sh[i], qi);
+                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(src + (size_t)ssrow[i] * n + j);
+                y0[i] = shoup(x.x, sinv[i], sinvsh[i], ssq[i]);
+                y1[i] = shoup(x.y, sinv[i], sinvsh[i], ssq[i]);
             }
         }
         for (int d = 0; d < nd; d++) {
-            Acc128 acc;
+            Acc128 a0, a1;
 #pragma unroll
             for (int i = 0; i < MAXK; i++)
-                if (i < ns) acc.mac(y[i], smont[i * nd + d]);
-            const uint64_t q = sq[d];
-            const uint64_t r = csub(csub(acc.hi - __umul64hi(acc.hi, sbar[d]) * q, q) + mont64(acc.lo, q, smneg[d]), q);
-            dst[(size_t)T.dst_row[d] * n + j] = r;
+                if (i < ns) {
+                    const uint64_t m = smont[i * nd + d];
+                    a0.mac(y0[i], m);
+                    a1.mac(y1[i], m);
+                }
+            const uint64_t q = sq[d], bar = sbar[d], mneg = smneg[d];
+            ulonglong2 r;
+            r.x = csub(csub(a0.hi - __umul64hi(a0.hi, bar) * q, q) + mont64(a0.lo, q, mneg), q);
+            r.y = csub(csub(a1.hi - __umul64hi(a1.hi, bar) * q, q) + mont64(a1.lo, q, mneg), q);
+            *reinterpret_cast<ulonglong2 *>(dst + (size_t)sdrow[d] * n + j) = r;
         }
     }
 }
@@ -710,7 +728,7 @@ void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int, Vie
 {
     Timed tm_(c, K_CONV, 0.0);
     HX_CHECK(B * groups < 65536, HX_EINVAL, "conversion batch too large");
-    dim3 grid(ew_blocks(c.N, 1), 1, B * groups);
+    dim3 grid(ew_blocks(c.N, 2), 1, B * groups);
     k_basis_convert<<<grid, 256, 0, c.stream>>>(tab_dev, out, in, c.t->primes, groups, gstride_out, gstride_in, c.N);
     post(c);
 }
