@@ -296,20 +296,29 @@ __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_
     const uint64_t *Db = D + (size_t)bi * ndig * dig_stride;
     const uint64_t *db = dnt + bi * dnt_bstride;
     const int own_digit = t < limbs ? t / K : -1;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const int js = g == 1 ? j : galois_src(j, g, log_n);
-        Acc128 a0, a1;
+    // two adjacent outputs per thread: 16-byte key loads and stores, the sources gathered
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const int js0 = g == 1 ? j : galois_src(j, g, log_n), js1 = g == 1 ? j + 1 : galois_src(j + 1, g, log_n);
+        Acc128 a0, a1, b0, b1;
         for (int d = 0; d < ndig; d++) {
-            const uint64_t x = (d == own_digit) ? db[(size_t)t * n + js] : Db[d * dig_stride + (size_t)t * n + js];
+            const uint64_t *row = (d == own_digit) ? db + (size_t)t * n : Db + d * dig_stride + (size_t)t * n;
+            const uint64_t x0 = row[js0], x1 = row[js1];
             const uint64_t *kd = key + (size_t)d * 2 * n_all * n + (size_t)pr * n + j;
-            a0.mac(x, kd[0]);
-            a1.mac(x, kd[(size_t)n_all * n]);
+            const ulonglong2 k0 = *reinterpret_cast<const ulonglong2 *>(kd);
+            const ulonglong2 k1 = *reinterpret_cast<const ulonglong2 *>(kd + (size_t)n_all * n);
+            a0.mac(x0, k0.x);
+            b0.mac(x1, k0.y);
+            a1.mac(x0, k1.x);
+            b1.mac(x1, k1.y);
         }
-        uint64_t r0 = mont128(a0.hi, a0.lo, P), r1 = mont128(a1.hi, a1.lo, P);
-        uint64_t *o0 = acc.p + bi * acc.bstride + (size_t)t * n + j, *o1 = o0 + acc.cstride;
+        ulonglong2 r0 = make_ulonglong2(mont128(a0.hi, a0.lo, P), mont128(b0.hi, b0.lo, P));
+        ulonglong2 r1 = make_ulonglong2(mont128(a1.hi, a1.lo, P), mont128(b1.hi, b1.lo, P));
+        ulonglong2 *o0 = reinterpret_cast<ulonglong2 *>(acc.p + bi * acc.bstride + (size_t)t * n + j);
+        ulonglong2 *o1 = reinterpret_cast<ulonglong2 *>(acc.p + bi * acc.bstride + acc.cstride + (size_t)t * n + j);
         if (accumulate) {
-            r0 = addmod(r0, *o0, P.q);
-            r1 = addmod(r1, *o1, P.q);
+            const ulonglong2 p0 = *o0, p1 = *o1;
+            r0.x = addmod(r0.x, p0.x, P.q), r0.y = addmod(r0.y, p0.y, P.q);
+            r1.x = addmod(r1.x, p1.x, P.q), r1.y = addmod(r1.y, p1.y, P.q);
         }
         *o0 = r0;
         *o1 = r1;
@@ -396,20 +405,32 @@ __global__ void k_key_ip_mux_pm(View out, const uint64_t *__restrict__ D, const 
     const uint64_t *db = dnt + bi * dnt_bstride;
     const int own_digit = t < limbs ? t / K : -1;
     const size_t half = (size_t)ndig * 2 * ext * n;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const int j1 = galois_src(j, g1, log_n), j2 = galois_src(j, g2, log_n);
-        Acc128 z0, z1;
+    // two adjacent outputs per thread: 16-byte key loads and stores, the sources gathered
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const int j1a = galois_src(j, g1, log_n), j2a = galois_src(j, g2, log_n);
+        const int j1b = galois_src(j + 1, g1, log_n), j2b = galois_src(j + 1, g2, log_n);
+        Acc128 z0a, z1a, z0b, z1b;
         for (int d = 0; d < ndig; d++) {
             const uint64_t *row = (d == own_digit) ? db + (size_t)t * n : Db + d * dig_stride + (size_t)t * n;
-            const uint64_t a = row[j1], b = row[j2];
+            const uint64_t xa = row[j1a], ya = row[j2a], xb = row[j1b], yb = row[j2b];
             const size_t o = ((size_t)d * 2 * ext + t) * n + j;
-            z0.mac(a, pk[o]);
-            z0.mac(b, pk[half + o]);
-            z1.mac(a, pk[o + dig_stride]);
-            z1.mac(b, pk[half + o + dig_stride]);
+            const ulonglong2 p0 = *reinterpret_cast<const ulonglong2 *>(pk + o);
+            const ulonglong2 q0 = *reinterpret_cast<const ulonglong2 *>(pk + half + o);
+            const ulonglong2 p1 = *reinterpret_cast<const ulonglong2 *>(pk + o + dig_stride);
+            const ulonglong2 q1 = *reinterpret_cast<const ulonglong2 *>(pk + half + o + dig_stride);
+            z0a.mac(xa, p0.x);
+            z0a.mac(ya, q0.x);
+            z1a.mac(xa, p1.x);
+            z1a.mac(ya, q1.x);
+            z0b.mac(xb, p0.y);
+            z0b.mac(yb, q0.y);
+            z1b.mac(xb, p1.y);
+            z1b.mac(yb, q1.y);
         }
-        out.p[bi * out.bstride + (size_t)t * n + j] = mont128(z0.hi, z0.lo, P);
-        out.p[bi * out.bstride + out.cstride + (size_t)t * n + j] = mont128(z1.hi, z1.lo, P);
+        *reinterpret_cast<ulonglong2 *>(out.p + bi * out.bstride + (size_t)t * n + j) =
+            make_ulonglong2(mont128(z0a.hi, z0a.lo, P), mont128(z0b.hi, z0b.lo, P));
+        *reinterpret_cast<ulonglong2 *>(out.p + bi * out.bstride + out.cstride + (size_t)t * n + j) =
+            make_ulonglong2(mont128(z1a.hi, z1a.lo, P), mont128(z1b.hi, z1b.lo, P));
     }
 }
 
@@ -738,7 +759,7 @@ void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64
                    bool accumulate)
 {
     Timed tm_(c, K_KEYIP, 8.0 * c.N * ((double)B * ndig * (limbs + K) + 2.0 * ndig * (limbs + K) + 2.0 * B * (limbs + K)));
-    dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
+    dim3 grid(ew_blocks(c.N, 2), limbs + K, B);
     k_key_ip<<<grid, 256, 0, c.stream>>>(acc, D, dnt, dnt_bstride, key, c.t->primes, n_all, n_q, K, limbs, ndig, g,
                                          c.log_n, accumulate);
     post(c);
@@ -777,7 +798,7 @@ void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const
 {
     Timed tm_(c, K_KEYIP, 8.0 * c.N * ((double)B * ndig * (limbs + K) + 4.0 * ndig * (limbs + K) +
                                         2.0 * B * (limbs + K)));
-    dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
+    dim3 grid(ew_blocks(c.N, 2), limbs + K, B);
     k_key_ip_mux_pm<<<grid, 256, 0, c.stream>>>(out, D, dnt, dnt_bstride, pk, c.t->primes, n_q, K, limbs, ndig, g1, g2,
                                                 c.log_n);
     post(c);
