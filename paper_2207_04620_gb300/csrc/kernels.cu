@@ -92,26 +92,43 @@ __global__ void k_aggregate(View out, const AggSrc *__restrict__ src, int n_part
     }
 }
 
-__global__ void k_lintrans_mac(const __grid_constant__ MacArgs A, const PrimeConst *__restrict__ primes, int B,
-                               int limbs, int n)
+// one thread: both components of batch entry bi at two adjacent coefficients, so every mask
+// word loaded (16 bytes, two coefficients) serves four products; NB >= the number of babies
+template <int NB>
+__global__ void __launch_bounds__(128) k_lintrans_mac(const __grid_constant__ MacArgs A,
+                                                      const PrimeConst *__restrict__ primes, int B, int limbs, int n)
 {
-    const int l = blockIdx.y, bc = blockIdx.z, bi = bc / 2, ci = bc % 2;
+    const int l = blockIdx.y, bi = blockIdx.z;
     const PrimeConst P = primes[l];
-    const size_t ob = bi * A.baby_bstride + ci * A.baby_cstride + (size_t)l * n;
+    const size_t ob0 = bi * A.baby_bstride + (size_t)l * n, ob1 = ob0 + A.baby_cstride;
     const size_t gstride = (size_t)B * 2 * limbs * n;
-    const size_t oo = ((size_t)bi * 2 + ci) * limbs * n + (size_t)l * n;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        uint64_t v[MAC_MAX_BABY];
+    const size_t oo0 = (size_t)bi * 2 * limbs * n + (size_t)l * n, oo1 = oo0 + (size_t)limbs * n;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        ulonglong2 v0[NB], v1[NB];
 #pragma unroll
-        for (int m = 0; m < MAC_MAX_BABY; m++) v[m] = m < A.n_baby ? A.baby[m][ob + j] : 0;
-        for (int g = 0; g < A.n_group; g++) {
-            Acc128 acc;
-#pragma unroll
-            for (int m = 0; m < MAC_MAX_BABY; m++) {
-                const uint64_t *mk = A.mask[g][m];
-                if (m < A.n_baby && mk) acc.mac(v[m], mk[(size_t)l * n + j]);
+        for (int m = 0; m < NB; m++) {
+            if (m < A.n_baby) {
+                v0[m] = *reinterpret_cast<const ulonglong2 *>(A.baby[m] + ob0 + j);
+                v1[m] = *reinterpret_cast<const ulonglong2 *>(A.baby[m] + ob1 + j);
             }
-            A.out[g * gstride + oo + j] = mont128(acc.hi, acc.lo, P);
+        }
+        for (int g = 0; g < A.n_group; g++) {
+            Acc128 a0, a1, b0, b1;  // (component, coefficient)
+#pragma unroll
+            for (int m = 0; m < NB; m++) {
+                const uint64_t *mk = A.mask[g][m];
+                if (m < A.n_baby && mk) {
+                    const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(mk + (size_t)l * n + j);
+                    a0.mac(v0[m].x, w.x);
+                    a1.mac(v0[m].y, w.y);
+                    b0.mac(v1[m].x, w.x);
+                    b1.mac(v1[m].y, w.y);
+                }
+            }
+            *reinterpret_cast<ulonglong2 *>(A.out + g * gstride + oo0 + j) =
+                make_ulonglong2(mont128(a0.hi, a0.lo, P), mont128(a1.hi, a1.lo, P));
+            *reinterpret_cast<ulonglong2 *>(A.out + g * gstride + oo1 + j) =
+                make_ulonglong2(mont128(b0.hi, b0.lo, P), mont128(b1.hi, b1.lo, P));
         }
     }
 }
@@ -768,8 +785,10 @@ void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64
 void launch_lintrans_mac(const LaunchCtx &c, const MacArgs &a, int B, int limbs, int n_terms)
 {
     Timed tm_(c, K_MULPT, 8.0 * limbs * c.N * ((double)B * 2 * (a.n_baby + a.n_group) + n_terms));
-    dim3 grid(ew_blocks(c.N, 1), limbs, B * 2);
-    k_lintrans_mac<<<grid, 256, 0, c.stream>>>(a, c.t->primes, B, limbs, c.N);
+    dim3 grid((c.N / 2 + 127) / 128, limbs, B);
+    if (a.n_baby <= 4) k_lintrans_mac<4><<<grid, 128, 0, c.stream>>>(a, c.t->primes, B, limbs, c.N);
+    else if (a.n_baby <= 8) k_lintrans_mac<8><<<grid, 128, 0, c.stream>>>(a, c.t->primes, B, limbs, c.N);
+    else k_lintrans_mac<16><<<grid, 128, 0, c.stream>>>(a, c.t->primes, B, limbs, c.N);
     post(c);
 }
 
