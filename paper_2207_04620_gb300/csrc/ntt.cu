@@ -177,14 +177,22 @@ k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
             __syncthreads();
             ntt_pass<LOGM, R2, R1, false, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
             __syncthreads();
-            for (int i = threadIdx.x; i < E; i += T) dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = b[i];
+            for (int i = threadIdx.x; i < E / 2; i += T) {  // 16-byte stores of column pairs
+                const int r = (2 * i) / COLS, c = (2 * i) % COLS;
+                *reinterpret_cast<ulonglong2 *>(dst + (size_t)r * N2 + c0 + c) =
+                    *reinterpret_cast<const ulonglong2 *>(b + 2 * i);
+            }
         } else {
             ntt_pass<LOGM, R2, R1, true, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
             __syncthreads();
             ntt_pass<LOGM, R1, 0, true, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
             __syncthreads();
-            for (int i = threadIdx.x; i < E; i += T)
-                dst[(size_t)(i / COLS) * N2 + c0 + (i % COLS)] = shoup(b[i], P.n_inv, P.n_inv_sh, P.q);
+            for (int i = threadIdx.x; i < E / 2; i += T) {
+                const int r = (2 * i) / COLS, c = (2 * i) % COLS;
+                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(b + 2 * i);
+                *reinterpret_cast<ulonglong2 *>(dst + (size_t)r * N2 + c0 + c) =
+                    make_ulonglong2(shoup(x.x, P.n_inv, P.n_inv_sh, P.q), shoup(x.y, P.n_inv, P.n_inv_sh, P.q));
+            }
         }
         __syncthreads();  // this half is refilled by the prefetch two tiles later
     }
@@ -241,21 +249,25 @@ k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
             __syncthreads();
             ntt_pass<LOGM, R2, R1, false, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
             __syncthreads();
-            for (int i = threadIdx.x; i < E; i += T) {
-                const int k = i / M, e = i % M;
-                uint64_t v = b[k * SK + e + (e >> 4)];
-                if (v >= two_q) v -= two_q;
-                if (v >= q) v -= q;
-                dst[base + i] = v;
+            for (int i = threadIdx.x; i < E / 2; i += T) {  // pairs (e even, e+1) share a padding group
+                const int k = (2 * i) / M, e = (2 * i) % M;
+                const int sidx = k * SK + e + (e >> 4);
+                uint64_t v0 = b[sidx], v1 = b[sidx + 1];
+                if (v0 >= two_q) v0 -= two_q;
+                if (v0 >= q) v0 -= q;
+                if (v1 >= two_q) v1 -= two_q;
+                if (v1 >= q) v1 -= q;
+                *reinterpret_cast<ulonglong2 *>(dst + base + 2 * i) = make_ulonglong2(v0, v1);
             }
         } else {
             ntt_pass<LOGM, R2, R1, true, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
             __syncthreads();
             ntt_pass<LOGM, R1, 0, true, false, true>(b, ROWS, SK, 1, tw, g0, r_base, 1, q, T);
             __syncthreads();
-            for (int i = threadIdx.x; i < E; i += T) {
-                const int k = i / M, e = i % M;
-                dst[base + i] = b[k * SK + e + (e >> 4)];
+            for (int i = threadIdx.x; i < E / 2; i += T) {
+                const int k = (2 * i) / M, e = (2 * i) % M;
+                const int sidx = k * SK + e + (e >> 4);
+                *reinterpret_cast<ulonglong2 *>(dst + base + 2 * i) = make_ulonglong2(b[sidx], b[sidx + 1]);
             }
         }
         __syncthreads();
