@@ -58,7 +58,7 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sh, int n_sub, int sk, int se
 #pragma unroll
         for (int m = 0; m < RR; m++) {
             const int e = base + m * TL;
-            v[m] = sh[k * sk + e * se + (PAD ? (e >> 4) : 0)];
+            v[m] = sh[k * sk + e * se + (PAD ? 2 * (e >> 4) : 0)];
         }
         if (!INV) {
 #pragma unroll
@@ -88,7 +88,7 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sh, int n_sub, int sk, int se
 #pragma unroll
         for (int m = 0; m < RR; m++) {
             const int e = base + m * TL;
-            sh[k * sk + e * se + (PAD ? (e >> 4) : 0)] = v[m];
+            sh[k * sk + e * se + (PAD ? 2 * (e >> 4) : 0)] = v[m];
         }
     }
 }
@@ -207,7 +207,7 @@ k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
 {
     constexpr int M = 1 << LOGM, E = M * ROWS, R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
     constexpr int T = (M >> R1) * ROWS;
-    constexpr int SK = M + M / 16;  // padded block stride
+    constexpr int SK = M + M / 8;  // padded block stride (two spare words per 16)
     extern __shared__ uint64_t sh[];
     uint64_t *buf[2] = {sh, sh + ROWS * SK};
     const int N = 1 << log_n;
@@ -218,9 +218,9 @@ k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
         const uint64_t *src = INV ? R.src + (size_t)id.g * R.src_gs + (size_t)R.src_off[id.row] * N
                                   : R.dst + (size_t)id.g * R.dst_gs + (size_t)R.dst_off[id.row] * N;
         const size_t base = (size_t)id.bx * ROWS * M;
-        for (int i = threadIdx.x; i < E; i += T) {
-            const int k = i / M, e = i % M;
-            cp_async8(buf[slot] + k * SK + e + (e >> 4), src + base + i);
+        for (int i = threadIdx.x; i < E / 2; i += T) {  // 16-byte pieces: pairs stay in one padding group
+            const int k = (2 * i) / M, e = (2 * i) % M;
+            cp_async16(buf[slot] + k * SK + e + 2 * (e >> 4), src + base + 2 * i);
         }
         cp_async_commit();
     };
@@ -251,7 +251,7 @@ k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
             __syncthreads();
             for (int i = threadIdx.x; i < E / 2; i += T) {  // pairs (e even, e+1) share a padding group
                 const int k = (2 * i) / M, e = (2 * i) % M;
-                const int sidx = k * SK + e + (e >> 4);
+                const int sidx = k * SK + e + 2 * (e >> 4);
                 uint64_t v0 = b[sidx], v1 = b[sidx + 1];
                 if (v0 >= two_q) v0 -= two_q;
                 if (v0 >= q) v0 -= q;
@@ -266,7 +266,7 @@ k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
             __syncthreads();
             for (int i = threadIdx.x; i < E / 2; i += T) {
                 const int k = (2 * i) / M, e = (2 * i) % M;
-                const int sidx = k * SK + e + (e >> 4);
+                const int sidx = k * SK + e + 2 * (e >> 4);
                 *reinterpret_cast<ulonglong2 *>(dst + base + 2 * i) = make_ulonglong2(b[sidx], b[sidx + 1]);
             }
         }
@@ -311,7 +311,7 @@ void ntt_rows_w(const LaunchCtx &c, const NttRows &rows)
     HX_CHECK(N1 % ROWS == 0, HX_EINVAL, "NTT tile wider than the ring");
     const long long n_tiles = (long long)(N1 / ROWS) * rows.n_rows * rows.n_groups;
     HX_CHECK(n_tiles < (1ll << 31), HX_EINVAL, "NTT batch too large");
-    const size_t smem = (size_t)ROWS * (M + M / 16) * 16;  // two tiles
+    const size_t smem = (size_t)ROWS * (M + M / 8) * 16;  // two tiles
     static const bool attr =  // thread-safe one-time setup
         cudaFuncSetAttribute(k_ntt_rows<LOGM, ROWS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
         cudaSuccess;
@@ -368,7 +368,7 @@ template <int LOGM> struct MultiW {  // tile width per phase size: (M >> R1) * W
     static constexpr int W = kMultiT / ((1 << LOGM) >> Split<LOGM>::R1);
 };
 constexpr int kMultiColsBuf = 2048 + 2 * 256;  // words: the largest column tile and its twiddles
-constexpr int kMultiRowsBuf = 8 * (256 + 16);  // words: the largest padded row tile
+constexpr int kMultiRowsBuf = 8 * (256 + 32);  // words: the largest padded row tile
 
 struct MultiTile {
     uint64_t *row;
@@ -441,18 +441,18 @@ __device__ void multi_cols_run(uint64_t *b, const MultiTile &m, const PrimeConst
 template <int LOGM>
 __device__ void multi_rows_load(uint64_t *b, const MultiTile &m)
 {
-    constexpr int M = 1 << LOGM, ROWS = MultiW<LOGM>::W, E = M * ROWS, SK = M + M / 16;
+    constexpr int M = 1 << LOGM, ROWS = MultiW<LOGM>::W, E = M * ROWS, SK = M + M / 8;
     const size_t base = (size_t)m.bx * ROWS * M;
     for (int i = threadIdx.x; i < E; i += kMultiT) {
         const int k = i / M, e = i % M;
-        cp_async8(b + k * SK + e + (e >> 4), m.row + base + i);
+        cp_async8(b + k * SK + e + 2 * (e >> 4), m.row + base + i);
     }
 }
 
 template <int LOGM, bool INV>
 __device__ void multi_rows_run(uint64_t *b, const MultiTile &m, const PrimeConst &P)
 {
-    constexpr int M = 1 << LOGM, ROWS = MultiW<LOGM>::W, E = M * ROWS, SK = M + M / 16;
+    constexpr int M = 1 << LOGM, ROWS = MultiW<LOGM>::W, E = M * ROWS, SK = M + M / 8;
     constexpr int R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
     const int g0 = m.log_n - LOGM, r_base = m.bx * ROWS;
     const size_t base = (size_t)r_base * M;
@@ -464,7 +464,7 @@ __device__ void multi_rows_run(uint64_t *b, const MultiTile &m, const PrimeConst
         __syncthreads();
         for (int i = threadIdx.x; i < E; i += kMultiT) {
             const int k = i / M, e = i % M;
-            uint64_t v = b[k * SK + e + (e >> 4)];
+            uint64_t v = b[k * SK + e + 2 * (e >> 4)];
             if (v >= two_q) v -= two_q;
             if (v >= q) v -= q;
             m.row[base + i] = v;
@@ -476,7 +476,7 @@ __device__ void multi_rows_run(uint64_t *b, const MultiTile &m, const PrimeConst
         __syncthreads();
         for (int i = threadIdx.x; i < E; i += kMultiT) {
             const int k = i / M, e = i % M;
-            m.row[base + i] = b[k * SK + e + (e >> 4)];
+            m.row[base + i] = b[k * SK + e + 2 * (e >> 4)];
         }
     }
 }
