@@ -131,12 +131,28 @@ hx_status hx_decrypt(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, doub
  * coefficients of c0 + c1*s mod q_0. */
 hx_status hx_decrypt_coeffs(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, int64_t *coeffs);
 
+/* Collective decryption (DDec, Sec. 2.2) with the parties that actually sent
+ * their shares: present[i] != 0 for party i, n_present = the key set's party
+ * count (HX_EINVAL otherwise).  Every party's share is needed; a missing one
+ * returns HX_EPARTY, naming the party, before any work.  Otherwise as
+ * hx_decrypt. */
+hx_status hx_decrypt_parties(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, const uint8_t *present,
+                             size_t n_present, double *slots, size_t n);
+
 /* ---- ciphertext handles ---------------------------------------------------- */
 /* Import residues [comps][limbs][N] (NTT form) from host memory. */
 hx_status hx_ct_import(hx_context *ctx, const uint64_t *host, int comps, int limbs, double scale, hx_ct **out);
 /* Export residues [comps][limbs][N]; returns words written or a negative status. */
 int64_t hx_ct_export(const hx_ct *ct, uint64_t *host, size_t cap);
 hx_status hx_ct_info(const hx_ct *ct, int *comps, int *limbs, double *scale);
+/* Checkpoint a ciphertext to a file / restore it: "HXCT0001", then u32 log_n,
+ * comps, limbs, 0, f64 scale, the u64 moduli of its limbs, and the residues
+ * [comps][limbs][N] (NTT form), little-endian.  Loading checks the magic, the
+ * ring degree and the moduli against the context (HX_EINVAL otherwise).  Keys
+ * are not stored: keygen is deterministic in (seed, parties, steps). */
+hx_status hx_ct_save(hx_context *ctx, const hx_ct *ct, const char *path);
+hx_status hx_ct_load(hx_context *ctx, const char *path, hx_ct **out);
+
 void hx_ct_destroy(hx_ct *ct);
 
 /* ---- single operations on handles (Fig. 1 items 7-12) ----------------------- */
@@ -389,8 +405,18 @@ hx_status hx_server_submit_sign(hx_server *sv, hx_context *ctx, const hx_keyset 
 int hx_server_poll(hx_server *sv, int wait, uint64_t *ids, hx_ct **results, int32_t *status, double *latency_ms,
                    int cap);
 /* completed, batches, largest batch, most lanes busy at once, peak admitted
- * bytes, key bytes, remaining budget, pending requests; returns the count */
+ * bytes, key bytes, remaining budget, pending requests, requests expired at
+ * their deadline; returns the count (9) */
 int hx_server_stats(hx_server *sv, uint64_t *out, int cap);
+/* Deadline of a queued request, ms after its submission.  If it is still
+ * queued when the deadline passes it completes with status HX_ETIMEOUT, a
+ * NULL result and no GPU work; once dispatched it runs to the end.  HX_EINVAL
+ * if the request is not queued any more. */
+hx_status hx_server_set_deadline(hx_server *sv, uint64_t id, double ms);
+/* paused != 0 holds every queued request (deadlines still expire; a blocking
+ * poll returns when one does); 0 resumes.  hx_server_destroy resumes before it
+ * drains. */
+hx_status hx_server_pause(hx_server *sv, int paused);
 /* waits for every submitted request, then stops the threads */
 void hx_server_destroy(hx_server *sv);
 

@@ -609,6 +609,42 @@ def decrypt(ctx: Context, ks: KeySet, ct: Ciphertext, n: int | None = None) -> n
     return z if n is None else z[:n]
 
 
+# -- checkpoint files ----------------------------------------------------------
+# Layout (little-endian): b"HXCT0001"; u32 log_n, comps, limbs, 0; f64 scale;
+# u64 modulus of each limb; u64 residues [comps][limbs][N] in NTT form.
+
+CT_MAGIC = b"HXCT0001"
+
+
+def save_ciphertext(path: str, ctx: Context, ct: Ciphertext) -> None:
+    comps, limbs = ct.c.shape[0], ct.c.shape[1]
+    with open(path, "wb") as f:
+        f.write(CT_MAGIC)
+        f.write(np.array([ctx.log_n, comps, limbs, 0], dtype="<u4").tobytes())
+        f.write(np.array([ct.scale], dtype="<f8").tobytes())
+        f.write(np.array(ctx.q[:limbs], dtype="<u8").tobytes())
+        f.write(np.ascontiguousarray(ct.c, dtype="<u8").tobytes())
+
+
+def load_ciphertext(path: str, ctx: Context) -> Ciphertext:
+    raw = open(path, "rb").read()
+    if raw[:8] != CT_MAGIC:
+        raise ValueError("not a ciphertext file")
+    log_n, comps, limbs, _ = np.frombuffer(raw, dtype="<u4", count=4, offset=8)
+    if log_n != ctx.log_n:
+        raise ValueError("ring degree differs from the context")
+    scale = float(np.frombuffer(raw, dtype="<f8", count=1, offset=24)[0])
+    moduli = np.frombuffer(raw, dtype="<u8", count=limbs, offset=32)
+    if [int(x) for x in moduli] != list(ctx.q[:limbs]):
+        raise ValueError("moduli differ from the context")
+    words = int(comps) * int(limbs) * ctx.N
+    body = 32 + 8 * int(limbs)
+    if len(raw) != body + 8 * words:
+        raise ValueError("truncated ciphertext file")
+    c = np.frombuffer(raw, dtype="<u8", count=words, offset=body).astype(np.uint64)
+    return Ciphertext(c.reshape(int(comps), int(limbs), ctx.N), scale)
+
+
 def decrypt_crt(ctx: Context, ks: KeySet, ct: Ciphertext) -> list:
     """Full-modulus decryption with CRT reconstruction in Python integers
     (pins only): centered c0 + c1*s mod q_0...q_{limbs-1}."""

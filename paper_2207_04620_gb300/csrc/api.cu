@@ -253,6 +253,82 @@ hx_status hx_decrypt(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, doub
     HX_END
 }
 
+hx_status hx_decrypt_parties(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, const uint8_t *present,
+                             size_t n_present, double *slots, size_t n)
+{
+    HX_TRY
+    need(ctx && ks && ct && present && (slots || n == 0), "null argument");
+    need(n_present == (size_t)ks->n_parties, "one flag per party of the key set");
+    for (int i = 0; i < ks->n_parties; i++)
+        HX_CHECK(present[i], HX_EPARTY,
+                 "party " + std::to_string(i) + " sent no decryption share; DDec needs all " +
+                     std::to_string(ks->n_parties) + " parties");
+    HX_CUDA(cudaDeviceSynchronize());
+    std::vector<int64_t> v = decrypt_coeffs(*ctx, *ks, ct->c, nullptr);
+    ctx->enc->decode(v.data(), ct->c.scale, slots, std::min(n, (size_t)ctx->N / 2));
+    return HX_OK;
+    HX_END
+}
+
+// ciphertext file: "HXCT0001", u32 log_n, comps, limbs, 0, f64 scale, u64 moduli[limbs],
+// u64 residues[comps][limbs][N] (NTT form), all little-endian
+hx_status hx_ct_save(hx_context *ctx, const hx_ct *ct, const char *path)
+{
+    HX_TRY
+    need(ctx && ct && path, "null argument");
+    const Cts &c = ct->c;
+    const size_t N = ctx->N, words = (size_t)c.comps * c.limbs * N;
+    std::vector<uint64_t> host(words);
+    HX_CUDA(cudaDeviceSynchronize());
+    for (int k = 0; k < c.comps; k++)
+        HX_CUDA(cudaMemcpy(host.data() + (size_t)k * c.limbs * N, c.d + k * c.cstride(N), sizeof(uint64_t) * c.limbs * N,
+                           cudaMemcpyDeviceToHost));
+    FILE *f = fopen(path, "wb");
+    HX_CHECK(f, HX_EINVAL, std::string("cannot write ") + path);
+    const uint32_t hdr[4] = {(uint32_t)ctx->log_n, (uint32_t)c.comps, (uint32_t)c.limbs, 0};
+    bool ok = fwrite("HXCT0001", 1, 8, f) == 8 && fwrite(hdr, 4, 4, f) == 4 && fwrite(&c.scale, 8, 1, f) == 1 &&
+              fwrite(ctx->primes.data(), 8, c.limbs, f) == (size_t)c.limbs &&
+              fwrite(host.data(), 8, words, f) == words;
+    ok = (fclose(f) == 0) && ok;
+    HX_CHECK(ok, HX_EINVAL, std::string("short write to ") + path);
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_ct_load(hx_context *ctx, const char *path, hx_ct **out)
+{
+    HX_TRY
+    need(ctx && path && out, "null argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    HX_CHECK(f, HX_EINVAL, std::string("cannot read ") + path);
+    char magic[8];
+    uint32_t hdr[4];
+    double scale = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && fread(hdr, 4, 4, f) == 4 && fread(&scale, 8, 1, f) == 1;
+    std::vector<uint64_t> mod, host;
+    if (ok) ok = memcmp(magic, "HXCT0001", 8) == 0 && hdr[0] == (uint32_t)ctx->log_n && hdr[1] >= 2 && hdr[1] <= 3 &&
+                 hdr[2] >= 1 && hdr[2] <= (uint32_t)ctx->n_q && scale > 0;
+    if (ok) {
+        mod.resize(hdr[2]);
+        ok = fread(mod.data(), 8, hdr[2], f) == hdr[2];
+        for (uint32_t l = 0; ok && l < hdr[2]; l++) ok = mod[l] == ctx->primes[l];
+    }
+    if (ok) {
+        host.resize((size_t)hdr[1] * hdr[2] * ctx->N);
+        ok = fread(host.data(), 8, host.size(), f) == host.size() && fgetc(f) == EOF;
+    }
+    fclose(f);
+    HX_CHECK(ok, HX_EINVAL, std::string(path) + " is not a ciphertext file of this context");
+    Eval ev(*ctx, nullptr);
+    Cts c = ev.alloc(1, (int)hdr[1], (int)hdr[2]);
+    c.scale = scale;
+    HX_CUDA(cudaMemcpy(c.d, host.data(), sizeof(uint64_t) * host.size(), cudaMemcpyHostToDevice));
+    *out = wrap(ctx, c);
+    return HX_OK;
+    HX_END
+}
+
 hx_status hx_ct_import(hx_context *ctx, const uint64_t *host, int comps, int limbs, double scale, hx_ct **out)
 {
     HX_TRY

@@ -9,6 +9,9 @@
 // their batches concurrently, so requests that arrive while others are on the
 // GPU are admitted as lanes and memory free up.  A batch's results are views
 // into its output buffer, equal to what the same request computes alone.
+// A request may carry a deadline: if it is still queued when its deadline
+// passes, it completes with HX_ETIMEOUT and no GPU work (a batch already on
+// the GPU always runs to the end).
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -29,7 +32,7 @@ struct Request {
     Cts a, b;
     int h = 0, d = 0, k = 0, relu = 0;
     uint64_t seed = 0;
-    Clock::time_point t0;
+    Clock::time_point t0, deadline = Clock::time_point::max();
     size_t est = 0;
 };
 
@@ -72,7 +75,8 @@ struct hx_server {
     std::deque<Request> pending;
     std::deque<Done> done;
     uint64_t next_id = 1, n_batches = 0, n_done = 0, max_seen_batch = 0, max_busy = 0, n_inflight = 0;
-    bool stop = false;
+    uint64_t n_expired = 0;
+    bool stop = false, paused = false;
     struct Lane {
         cudaStream_t s = nullptr;
         std::thread th;
@@ -88,21 +92,53 @@ struct hx_server {
 
     void run_lane(Lane &L);
     void run_dispatch();
+    Clock::time_point expire_pending();  // returns the earliest deadline still ahead
 };
+
+Clock::time_point hx_server::expire_pending()
+{
+    const auto now = Clock::now();
+    Clock::time_point next = Clock::time_point::max();
+    bool any = false;
+    for (auto it = pending.begin(); it != pending.end();) {
+        if (it->deadline > now) {
+            next = std::min(next, it->deadline);
+            ++it;
+            continue;
+        }
+        Done d;
+        d.id = it->id;
+        d.status = HX_ETIMEOUT;
+        d.ctx = it->ctx;
+        d.latency_ms = std::chrono::duration<double, std::milli>(now - it->t0).count();
+        done.push_back(std::move(d));
+        n_done++;
+        n_expired++;
+        any = true;
+        it = pending.erase(it);  // drops the request's references to its inputs
+    }
+    if (any) cv_done.notify_all();
+    return next;
+}
 
 void hx_server::run_dispatch()
 {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lk(mu);
     while (!stop) {
+        const Clock::time_point next = expire_pending();
+        auto sleep = [&] {
+            if (next == Clock::time_point::max()) cv_dispatch.wait(lk);
+            else cv_dispatch.wait_until(lk, next);
+        };
         Lane *idle = nullptr;
         for (auto &l : lanes)
             if (!l->busy) {
                 idle = l.get();
                 break;
             }
-        if (pending.empty() || !idle) {
-            cv_dispatch.wait(lk);
+        if (pending.empty() || !idle || paused) {
+            sleep();
             continue;
         }
         // the oldest request leads; others with its signature join while they fit
@@ -119,7 +155,7 @@ void hx_server::run_dispatch()
             it = pending.erase(it);
         }
         if (batch.empty()) {  // the head does not fit yet: wait for memory to free up
-            cv_dispatch.wait(lk);
+            sleep();
             continue;
         }
         admitted += est;
@@ -329,10 +365,33 @@ int hx_server_stats(hx_server *sv, uint64_t *out, int cap)
 {
     if (!sv) return HX_EINVAL;
     std::lock_guard<std::mutex> lk(sv->mu);
-    const uint64_t v[8] = {sv->n_done, sv->n_batches, sv->max_seen_batch, sv->max_busy, sv->peak, sv->keys,
-                           sv->budget, (uint64_t)sv->pending.size()};
-    for (int i = 0; i < 8 && i < cap; i++) out[i] = v[i];
-    return 8;
+    const uint64_t v[9] = {sv->n_done, sv->n_batches, sv->max_seen_batch, sv->max_busy, sv->peak, sv->keys,
+                           sv->budget, (uint64_t)sv->pending.size(), sv->n_expired};
+    for (int i = 0; i < 9 && i < cap; i++) out[i] = v[i];
+    return 9;
+}
+
+hx_status hx_server_set_deadline(hx_server *sv, uint64_t id, double ms)
+{
+    if (!sv || !(ms >= 0)) return HX_EINVAL;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    for (auto &r : sv->pending)
+        if (r.id == id) {
+            r.deadline = r.t0 + std::chrono::duration_cast<Clock::duration>(std::chrono::duration<double, std::milli>(ms));
+            sv->cv_dispatch.notify_one();
+            return HX_OK;
+        }
+    set_error("request " + std::to_string(id) + " is not queued (already dispatched, completed or unknown)");
+    return HX_EINVAL;
+}
+
+hx_status hx_server_pause(hx_server *sv, int paused)
+{
+    if (!sv) return HX_EINVAL;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->paused = paused != 0;
+    sv->cv_dispatch.notify_one();
+    return HX_OK;
 }
 
 void hx_server_destroy(hx_server *sv)
@@ -340,6 +399,8 @@ void hx_server_destroy(hx_server *sv)
     if (!sv) return;
     {
         std::unique_lock<std::mutex> lk(sv->mu);
+        sv->paused = false;
+        sv->cv_dispatch.notify_one();
         sv->cv_done.wait(lk, [&] { return sv->pending.empty() && !sv->n_inflight; });
         sv->stop = true;
         sv->cv_dispatch.notify_all();

@@ -52,6 +52,9 @@ _SIGS = {
     "hx_keyset_export_public_key": (c_i64, [c_vp, P_u64, c_size_t]),
     "hx_keyset_destroy": (None, [c_vp]),
     "hx_encode": (c_int, [c_vp, P_dbl, c_size_t, c_double, P_i64]),
+    "hx_decrypt_parties": (c_int, [c_vp, c_vp, c_vp, ctypes.POINTER(ctypes.c_uint8), c_size_t, P_dbl, c_size_t]),
+    "hx_ct_save": (c_int, [c_vp, c_vp, ctypes.c_char_p]),
+    "hx_ct_load": (c_int, [c_vp, ctypes.c_char_p, PP]),
     "hx_encode_batch": (c_int, [c_vp, P_dbl, c_size_t, c_size_t, c_double, P_i64, c_vp]),
     "hx_encrypt_batch": (c_int, [c_vp, c_vp, P_dbl, c_size_t, c_size_t, c_int, P_u64, PP, c_vp]),
     "hx_encrypt": (c_int, [c_vp, c_vp, P_dbl, c_size_t, c_int, c_u64, PP]),
@@ -112,6 +115,8 @@ _SIGS = {
     "hx_server_poll": (c_int, [c_vp, c_int, P_u64, PP, P_i32, P_dbl, c_int]),
     "hx_server_stats": (c_int, [c_vp, P_u64, c_int]),
     "hx_server_destroy": (None, [c_vp]),
+    "hx_server_set_deadline": (c_int, [c_vp, c_u64, ctypes.c_double]),
+    "hx_server_pause": (c_int, [c_vp, c_int]),
     "hx_counters": (c_int, [c_vp, P_u64, c_int]),
     "hx_counters_reset": (None, [c_vp]),
     "hx_autotune": (c_int, [c_vp, P_i32, c_vp]),
@@ -295,6 +300,26 @@ def hx_ct_import(ctx: int, residues: np.ndarray, scale: float) -> int:
     comps, limbs, _ = a.shape
     out = _out()
     _chk(lib().hx_ct_import(ctx, _u64p(a), comps, limbs, scale, ctypes.byref(out)))
+    return out.value
+
+
+def hx_decrypt_parties(ctx: int, ks: int, ct: int, present, n: int | None = None) -> np.ndarray:
+    """DDec with a party mask (truthy = that party's share arrived)."""
+    flags = np.ascontiguousarray(np.asarray(present, dtype=np.uint8))
+    n = hx_context_n(ctx) // 2 if n is None else n
+    out = np.zeros(n)
+    _chk(lib().hx_decrypt_parties(ctx, ks, ct, flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), flags.size,
+                                  out.ctypes.data_as(P_dbl), n))
+    return out
+
+
+def hx_ct_save(ctx: int, ct: int, path: str) -> None:
+    _chk(lib().hx_ct_save(ctx, ct, path.encode()))
+
+
+def hx_ct_load(ctx: int, path: str) -> int:
+    out = _out()
+    _chk(lib().hx_ct_load(ctx, path.encode(), ctypes.byref(out)))
     return out.value
 
 
@@ -589,7 +614,7 @@ def hx_aggregate(ctx, grads, n_parties, models, eta_over_bn, stream=None) -> lis
 # ---- serving ------------------------------------------------------------------------------
 
 SERVER_STATS = ["completed", "batches", "largest_batch", "max_busy_lanes", "peak_admitted_bytes", "key_bytes",
-                "budget_left", "pending"]
+                "budget_left", "pending", "expired"]
 
 
 def hx_server_create(hbm_budget_bytes: int, n_lanes: int, max_batch: int) -> int:
@@ -626,9 +651,17 @@ def hx_server_poll(sv: int, wait: bool = True, cap: int = 256) -> list:
 
 
 def hx_server_stats(sv: int) -> dict:
-    buf = np.zeros(8, dtype=np.uint64)
-    n = _chk(lib().hx_server_stats(sv, _u64p(buf), 8))
-    return {SERVER_STATS[i]: int(buf[i]) for i in range(n)}
+    buf = np.zeros(len(SERVER_STATS), dtype=np.uint64)
+    n = _chk(lib().hx_server_stats(sv, _u64p(buf), len(SERVER_STATS)))
+    return {SERVER_STATS[i]: int(buf[i]) for i in range(min(n, len(SERVER_STATS)))}
+
+
+def hx_server_set_deadline(sv: int, rid: int, ms: float) -> None:
+    _chk(lib().hx_server_set_deadline(sv, rid, float(ms)))
+
+
+def hx_server_pause(sv: int, paused: bool) -> None:
+    _chk(lib().hx_server_pause(sv, int(bool(paused))))
 
 
 def hx_server_destroy(sv: int) -> None:

@@ -267,6 +267,52 @@ def test_error_statuses(cfg0):
         hx.hx_ct_destroy(h_)
 
 
+def test_checkpoint_files_cross_read(alg3, tmp_path):
+    # the oracle writes, the library reads, and the other way round, bit for bit
+    pr = alg3
+    ct = pr.encrypt(np.linspace(-1, 1, 8), 77, limbs=4)
+    p_or, p_lib = str(tmp_path / "oracle.ct"), str(tmp_path / "lib.ct")
+    C.save_ciphertext(p_or, pr.octx, ct)
+    h = hx.hx_ct_load(pr.ctx, p_or)
+    assert pr.same(h, ct)
+    r = hx.hx_rotate(pr.ctx, pr.ks, h, 7)
+    hx.hx_ct_save(pr.ctx, r, p_lib)
+    back = C.load_ciphertext(p_lib, pr.octx)
+    assert np.array_equal(back.c, C.Evaluator(pr.octx, pr.oks).rotate(ct, 7).c) and back.scale == ct.scale
+    C.save_ciphertext(p_or, pr.octx, back)
+    assert open(p_lib, "rb").read() == open(p_or, "rb").read()
+    # files of another ring, with a wrong modulus or cut short are refused
+    raw = open(p_lib, "rb").read()
+    other = C.Context(11, [60, 45], [60], 45)
+    C.save_ciphertext(p_or, other, C.Ciphertext(np.zeros((2, 2, 1 << 11), np.uint64), 2.0 ** 45))
+    for bad in (None, raw[:-8], raw[:32] + (int(raw[32]) ^ 2).to_bytes(1, "little") + raw[33:], raw + b"\0"):
+        if bad is not None:
+            open(p_or, "wb").write(bad)
+        with pytest.raises(hx.HxError) as e:
+            hx.hx_ct_load(pr.ctx, p_or)
+        assert e.value.code == -1
+    for x in (h, r):
+        hx.hx_ct_destroy(x)
+
+
+def test_decrypt_needs_every_party(alg3):
+    pr = alg3
+    z = np.linspace(-2, 2, 16)
+    a = pr.to_lib(pr.encrypt(z, 5))
+    full = hx.hx_decrypt(pr.ctx, pr.ks, a, 16)
+    assert np.array_equal(hx.hx_decrypt_parties(pr.ctx, pr.ks, a, [1] * pr.n_parties, 16), full)
+    assert np.allclose(full, z, atol=1e-6)
+    for missing in range(pr.n_parties):
+        flags = [int(i != missing) for i in range(pr.n_parties)]
+        with pytest.raises(hx.HxError) as e:
+            hx.hx_decrypt_parties(pr.ctx, pr.ks, a, flags, 16)
+        assert e.value.code == -8 and ("party %d" % missing) in str(e.value)
+    with pytest.raises(hx.HxError) as e:
+        hx.hx_decrypt_parties(pr.ctx, pr.ks, a, [1] * (pr.n_parties - 1), 16)
+    assert e.value.code == -1
+    hx.hx_ct_destroy(a)
+
+
 # ---- a6-a7: HE-MatMult ----------------------------------------------------------------
 
 def _matmul_case(name, h, seeds, count):

@@ -1,6 +1,6 @@
 """Continuous-batching server: every result equals the same request computed
-alone, requests are batched and overlap across lanes, and admission respects
-the HBM budget."""
+alone, requests are batched and overlap across lanes, admission respects the
+HBM budget, and queued requests past their deadline complete with HX_ETIMEOUT."""
 import numpy as np
 import pytest
 
@@ -112,3 +112,32 @@ def test_admission_by_budget_and_rejection(setup):
         hx.hx_server_submit_matmul(tiny, ctx, ks, c, c, h)
     assert e.value.code == -2
     hx.hx_server_destroy(tiny)
+
+
+def test_deadline_expires_queued_requests_only(setup):
+    ctx, ks, s = setup
+    h, beta = 8, s // 64
+    a = hx.hx_encrypt(ctx, ks, workloads.pack(workloads.matrices(3, beta, h), h, beta), 5, 4)
+    b = hx.hx_encrypt(ctx, ks, workloads.pack(workloads.matrices(4, beta, h), h, beta), 5, 5)
+    sv = hx.hx_server_create(64 << 30, 2, 4)
+    hx.hx_server_pause(sv, True)            # hold the queue so the deadlines below act on queued requests
+    late = hx.hx_server_submit_matmul(sv, ctx, ks, a, b, h)
+    kept = hx.hx_server_submit_matmul(sv, ctx, ks, a, b, h)
+    hx.hx_server_set_deadline(sv, late, 0.0)
+    hx.hx_server_set_deadline(sv, kept, 60e3)
+    first = hx.hx_server_poll(sv, wait=True)  # the expiry wakes the poll while the queue is still held
+    assert [(rid, res, st) for rid, res, st, _ in first] == [(late, None, -6)]
+    assert hx.hx_server_stats(sv)["pending"] == 1
+    hx.hx_server_pause(sv, False)
+    got = _collect(sv, 1)
+    assert got[kept][1] == 0
+    alone = hx.hx_matmul(ctx, ks, a, b, h)
+    assert np.array_equal(hx.hx_ct_export(ctx, got[kept][0]), hx.hx_ct_export(ctx, alone))
+    with pytest.raises(hx.HxError) as e:     # no longer queued
+        hx.hx_server_set_deadline(sv, kept, 1.0)
+    assert e.value.code == -1
+    stats = hx.hx_server_stats(sv)
+    assert stats["expired"] == 1 and stats["completed"] == 2
+    hx.hx_server_destroy(sv)
+    for x in (a, b, alone, got[kept][0]):
+        hx.hx_ct_destroy(x)

@@ -2,6 +2,7 @@
 definition, encryption round trips within the noise bound, homomorphic ops
 against plaintext arithmetic, rescale against exact integer rounding."""
 import math
+import struct
 
 import numpy as np
 import pytest
@@ -184,3 +185,23 @@ def test_dbootstrap_refreshes_to_top_level(small):
     other = C.dbootstrap(ctx, ks, ct, seed=31, counter=1)
     assert not np.array_equal(other.c, out.c)
     assert np.abs(C.decrypt(ctx, ks, other) - z).max() < 2 ** -20
+
+
+def test_ciphertext_file_layout_and_round_trip(small, tmp_path):
+    ctx, ks = small
+    ct = C.encrypt(ctx, ks, [0.25, -1.5, 3.0], seed=9, limbs=3)
+    path = str(tmp_path / "ct.bin")
+    C.save_ciphertext(path, ctx, ct)
+    raw = open(path, "rb").read()
+    # the layout written out field by field
+    want = b"HXCT0001" + struct.pack("<4I", ctx.log_n, 2, 3, 0) + struct.pack("<d", ct.scale)
+    want += struct.pack("<3Q", *ctx.q[:3])
+    want += b"".join(struct.pack("<Q", int(x)) for x in ct.c.reshape(-1))
+    assert raw == want
+    back = C.load_ciphertext(path, ctx)
+    assert back.scale == ct.scale and np.array_equal(back.c, ct.c)
+    assert np.allclose(C.decrypt(ctx, ks, back, 3), [0.25, -1.5, 3.0], atol=1e-6)
+    for bad in (b"HXCT0002" + raw[8:], raw[:-8], raw[:32] + struct.pack("<Q", ctx.q[0] + 2) + raw[40:]):
+        open(path, "wb").write(bad)
+        with pytest.raises(ValueError):
+            C.load_ciphertext(path, ctx)
