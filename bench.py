@@ -458,6 +458,14 @@ def run_sign(args):
                 hx.hx_ct_destroy(o)
     clocks = sampler.stop()
     t = sum(times) / len(times)
+    # live per-kernel-class shares of one more step (CUDA events per launch, chains serial)
+    hx.hx_profile_enable(ctx, True)
+    for o in step(999):
+        hx.hx_ct_destroy(o)
+    prof = hx.hx_profile_read(ctx)
+    hx.hx_profile_enable(ctx, False)
+    total_ms = sum(v[1] for v in prof.values())
+    shares = {c: round(v[1] / total_ms, 4) for c, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     errs_sgn, errs_g = [], []
     for i in range(4):
         got = hx.hx_decrypt(ctx, ks, outs[i])
@@ -474,7 +482,8 @@ def run_sign(args):
             "higher_is_better": True, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "cfg2: 64 ciphertexts x 16384 slots, |x| in [2^-8, 1], d=4, k=8, two collective "
                                    "refreshes per entry (DBootstrap shares on the device), host wall clock"},
-            "max_err_vs_exact": max(errs_sgn), "max_err_vs_fp64_composite": max(errs_g), "clocks": clocks}
+            "max_err_vs_exact": max(errs_sgn), "max_err_vs_fp64_composite": max(errs_g), "clocks": clocks,
+            "kernel_shares": shares, "kernel_ms_profiled": round(total_ms, 2)}
     print(json.dumps(line), flush=True)
     hx.hx_keyset_destroy(ks)
     hx.hx_context_destroy(ctx)
