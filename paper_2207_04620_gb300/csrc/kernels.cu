@@ -176,8 +176,10 @@ __global__ void k_add_scalar_c0(View out, View a, const __grid_constant__ Scalar
     const uint64_t q = primes[l].q, s = ci == 0 ? sc.v[l] : 0;
     const size_t oo = bi * out.bstride + ci * out.cstride + (size_t)l * n;
     const size_t oa = bi * a.bstride + ci * a.cstride + (size_t)l * n;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-        out.p[oo + j] = addmod(a.p[oa + j], s, q);
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(a.p + oa + j);
+        *reinterpret_cast<ulonglong2 *>(out.p + oo + j) = make_ulonglong2(addmod(x.x, s, q), addmod(x.y, s, q));
+    }
 }
 
 // (a0,a1) x (b0,b1) -> (a0b0, a0b1+a1b0, a1b1), optionally added to out
@@ -567,9 +569,12 @@ __global__ void k_rescale_prep(View r, View xtop, const RescaleTable *__restrict
     const uint64_t hm = tab->half_mod[i];
     const uint64_t *x = xtop.p + bi * xtop.bstride + ci * xtop.cstride;
     uint64_t *o = r.p + bi * r.bstride + ci * r.cstride + (size_t)i * n;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const uint64_t v = csub(x[j] + half, qt);
-        o[j] = submod(reduce64(v, Pi.q, Pi.bar), hm, Pi.q);
+    // two adjacent coefficients per thread (16-byte loads and stores)
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 xv = *reinterpret_cast<const ulonglong2 *>(x + j);
+        const uint64_t v0 = csub(xv.x + half, qt), v1 = csub(xv.y + half, qt);
+        *reinterpret_cast<ulonglong2 *>(o + j) = make_ulonglong2(submod(reduce64(v0, Pi.q, Pi.bar), hm, Pi.q),
+                                                                 submod(reduce64(v1, Pi.q, Pi.bar), hm, Pi.q));
     }
 }
 
@@ -581,8 +586,12 @@ __global__ void k_rescale_final(View out, View in, View r, const RescaleTable *_
     const uint64_t *a = in.p + bi * in.bstride + ci * in.cstride + (size_t)i * n;
     const uint64_t *rr = r.p + bi * r.bstride + ci * r.cstride + (size_t)i * n;
     uint64_t *o = out.p + bi * out.bstride + ci * out.cstride + (size_t)i * n;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
-        o[j] = shoup(submod(a[j], rr[j], q), w, wsh, q);
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 av = *reinterpret_cast<const ulonglong2 *>(a + j);
+        const ulonglong2 rv = *reinterpret_cast<const ulonglong2 *>(rr + j);
+        *reinterpret_cast<ulonglong2 *>(o + j) =
+            make_ulonglong2(shoup(submod(av.x, rv.x, q), w, wsh, q), shoup(submod(av.y, rv.y, q), w, wsh, q));
+    }
 }
 
 // b = e - a*s + gad_r * s'  (all NTT form, row r modulo prime r); optionally
@@ -739,7 +748,7 @@ void launch_mul_scalar(const LaunchCtx &c, View out, View a, const Scalars &sc, 
 void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int limbs)
 {
     Timed tm_(c, K_ELEM, 32.0 * B * limbs * c.N);
-    dim3 grid(ew_blocks(c.N, 1), limbs, B * 2);
+    dim3 grid(ew_blocks(c.N, 2), limbs, B * 2);
     k_add_scalar_c0<<<grid, 256, 0, c.stream>>>(out, a, sc, c.t->primes, c.N);
     post(c);
 }
@@ -870,7 +879,7 @@ void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, con
 void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps, int top)
 {
     Timed tm_(c, K_RESCALE, 8.0 * B * comps * (top + 1) * c.N);
-    dim3 grid(ew_blocks(c.N, 1), top, B * comps);
+    dim3 grid(ew_blocks(c.N, 2), top, B * comps);
     k_rescale_prep<<<grid, 256, 0, c.stream>>>(r, xtop, tab, c.t->primes, comps, top, c.N);
     post(c);
 }
@@ -879,7 +888,7 @@ void launch_rescale_final(const LaunchCtx &c, View out, View in, View r, const R
                           int top)
 {
     Timed tm_(c, K_RESCALE, 24.0 * B * comps * top * c.N);
-    dim3 grid(ew_blocks(c.N, 1), top, B * comps);
+    dim3 grid(ew_blocks(c.N, 2), top, B * comps);
     k_rescale_final<<<grid, 256, 0, c.stream>>>(out, in, r, tab, c.t->primes, comps, c.N);
     post(c);
 }
