@@ -660,30 +660,43 @@ def run_serve(args):
             hx.hx_ct_destroy(res)
             pend.discard(rid)
     capacity = n_cap / (time.perf_counter() - t0)
-    # open loop: Poisson arrivals at rate 0.8 x capacity
-    rate = args.load * capacity
-    gaps = rng.exponential(1.0 / rate, n_req - n_cap)
-    lat, pend = {}, set()
+    # open loop: Poisson arrivals at a fixed fraction of the capacity
+    def open_loop(load, batch):
+        rate = load * capacity
+        gaps = rng.exponential(1.0 / rate, len(batch))
+        lat, pend = {}, set()
+        t0 = time.perf_counter()
+        t_next = t0
+        for r, g in zip(batch, gaps):
+            t_next += g
+            while True:
+                now = time.perf_counter()
+                if now >= t_next:
+                    break
+                drain(pend, lat)
+                time.sleep(min(0.0005, t_next - now))
+            pend.add(submit(r))
+        while pend:
+            for rid, res, st, l in hx.hx_server_poll(sv, wait=True):
+                if st != 0:
+                    raise RuntimeError("request %d failed with status %d" % (rid, st))
+                lat[rid] = l
+                hx.hx_ct_destroy(res)
+                pend.discard(rid)
+        return lat, rate, time.perf_counter() - t0
+
     sampler = ClockSampler()
-    t0 = time.perf_counter()
-    t_next = t0
-    for r, g in zip(reqs[n_cap:], gaps):
-        t_next += g
-        while True:
-            now = time.perf_counter()
-            if now >= t_next:
-                break
-            drain(pend, lat)
-            time.sleep(min(0.0005, t_next - now))
-        pend.add(submit(r))
-    while pend:
-        for rid, res, st, l in hx.hx_server_poll(sv, wait=True):
-            lat[rid] = l
-            hx.hx_ct_destroy(res)
-            pend.discard(rid)
-    elapsed = time.perf_counter() - t0
+    lat, rate, elapsed = open_loop(args.load, reqs[n_cap:])
     clocks = sampler.stop()
     stats = hx.hx_server_stats(sv)
+    # the same request stream at other offered loads (below, near and above capacity)
+    sweep = []
+    for load in (0.5, 0.9, 1.1):
+        lt, rt, el = open_loop(load, reqs[n_cap:])
+        Ls = np.array(sorted(lt.values()))
+        sweep.append({"load": load, "offered_req_s": round(rt, 2), "throughput_req_s": round(len(Ls) / el, 2),
+                      "p50_ms": round(float(np.percentile(Ls, 50)), 3),
+                      "p99_ms": round(float(np.percentile(Ls, 99)), 3)})
     hx.hx_server_destroy(sv)
     L = np.array(sorted(lat.values()))
     line = {"metric": "serving p50/p99 ms (continuous batching, mixed encrypted matmul + sign)",
@@ -696,7 +709,7 @@ def run_serve(args):
                                    "matmul limbs U{3..20}, sign limbs U{5..20}" % (args.load, [2 ** l for l in log_ns]),
                        "lanes": args.lanes, "max_batch": args.max_batch, "hbm_budget_bytes": budget,
                        "setup_s": round(setup_s, 1)},
-            "server": stats, "clocks": clocks}
+            "server": stats, "clocks": clocks, "load_sweep": sweep}
     print(json.dumps(line), flush=True)
     for kind, ln, a, _ in reqs:
         for h in (a[:2] if kind == "matmul" else a[:1]):

@@ -241,8 +241,9 @@ __global__ void k_automorphism(View out, View in, uint64_t g, int comps, int log
 }
 
 // Fast basis conversion; grid: x over coefficients, z = b * groups + grp
-__global__ void k_basis_convert(const ConvTable *__restrict__ tabs, View out, View in, const PrimeConst *__restrict__ primes,
-                                int groups, size_t gstride_out, size_t gstride_in, int n)
+__global__ void __launch_bounds__(256, 4)
+    k_basis_convert(const ConvTable *__restrict__ tabs, View out, View in, const PrimeConst *__restrict__ primes,
+                    int groups, size_t gstride_out, size_t gstride_in, int n)
 {
     // two adjacent coefficients per thread (16-byte loads and stores); the table's constants
     // staged in shared memory once per block
