@@ -511,25 +511,31 @@ def _square_rs(ev, a, b):
 
 
 def eval_g(ev: C.Evaluator, x: C.Ciphertext, d: int) -> C.Ciphertext:
-    """One application of g_d on a ciphertext (reading R8): y^j = powers of
-    y = x^2 by squaring (even j) or y^(j-1)*y (odd j), the linear combination
-    P(y) = sum_j n_j y^j with integer n_j at the deepest level, then x*P(y)
-    with the 2^-(2d-1) folded into the level adjustment of x.  Ciphertexts of
-    equal level carry equal scales because every product is of two operands of
-    one level and scale."""
+    """One application of g_d (1 <= d <= 4) on a ciphertext (reading R8).
+    With y = x^2 and g_d(x) = x P(y) / 2^(2d-1), P(y) = sum_j n_j y^j with the
+    integer n_j of Sec. 4, P is split as n0 + n1 y + n2 y^2 + y^2 B(y) with
+    B(y) = n3 y + n4 y^2 (the terms present for this d): y and y^2 by squaring,
+    B at y^2's level, one product y^2 * B, the remaining terms brought to that
+    level, then x * P with the 2^-(2d-1) folded into the level adjustment of x.
+    Four ciphertext products for d = 3 and 4, two and three for d = 1 and 2.
+    Operands of one product always share level and scale."""
+    if not 1 <= d <= 4:
+        raise ValueError("eval_g covers 1 <= d <= 4")
     n = g_int_coeffs(d)
     y = {1: _square_rs(ev, x, x)}
-    for j in range(2, d + 1):
-        if j % 2 == 0:
-            y[j] = _square_rs(ev, y[j // 2], y[j // 2])
-        else:
-            a = y[j - 1]
-            y1 = level_adjust(ev, y[1], a.limbs, 1.0, a.scale) if y[1].limbs > a.limbs else y[1]
-            y[j] = _square_rs(ev, a, y1)
-    lp = min(v.limbs for v in y.values())
-    sp = next(v.scale for v in y.values() if v.limbs == lp)
-    terms = []
-    for j in range(1, d + 1):
+    if d >= 2:
+        y[2] = _square_rs(ev, y[1], y[1])
+    top = None  # y^2 B(y)
+    if d >= 3:
+        y1 = level_adjust(ev, y[1], y[2].limbs, 1.0, y[2].scale)
+        B = ev.mul_int(y1, n[3])
+        if d == 4:
+            B = ev.add(B, ev.mul_int(y[2], n[4]))
+        top = _square_rs(ev, y[2], B)
+    lead = top if top is not None else y[min(d, 2)]
+    lp, sp = lead.limbs, lead.scale
+    terms = [top] if top is not None else []
+    for j in range(1, min(d, 2) + 1):
         if y[j].limbs > lp:
             terms.append(level_adjust(ev, y[j], lp, float(n[j]), sp))
         else:
@@ -543,11 +549,9 @@ def eval_g(ev: C.Evaluator, x: C.Ciphertext, d: int) -> C.Ciphertext:
 
 
 def g_depth(d: int) -> int:
-    """Levels one application of eval_g consumes."""
-    lev = {1: 1}
-    for j in range(2, d + 1):
-        lev[j] = (lev[j // 2] + 1) if j % 2 == 0 else max(lev[j - 1], lev[1]) + 1
-    return max(lev.values()) + 1
+    """Levels one application of eval_g consumes: y, y^2 and y^2 B(y) take one
+    level each (as many as d needs), x * P one more."""
+    return min(d, 3) + 1
 
 
 def refresh(ev: C.Evaluator, ct: C.Ciphertext, seed: int, counter: int) -> C.Ciphertext:

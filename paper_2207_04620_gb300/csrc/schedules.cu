@@ -522,32 +522,29 @@ Cts level_adjust(Eval &ev, const Cts &ct, int target, double c_real, double targ
     return y;
 }
 
+// one application of g_d, 1 <= d <= 4 (Sec. 4, reading R8): with y = x^2,
+// P(y) = n0 + n1 y + n2 y^2 + y^2 (n3 y + n4 y^2) (the terms this d has), then
+// x * P with the 2^-(2d-1) folded into x's level adjustment; four ciphertext
+// products for d = 3 and 4
 Cts eval_g(Eval &ev, const hx_keyset &ks, const Cts &x, int d)
 {
     const std::vector<int64_t> n = g_int_coeffs(d);
-    std::vector<Cts> y(d + 1);
-    y[1] = square_rs(ev, ks, x, x);
-    for (int j = 2; j <= d; j++) {
-        if (j % 2 == 0) {
-            y[j] = square_rs(ev, ks, y[j / 2], y[j / 2]);
-        } else {
-            const Cts &a = y[j - 1];
-            Cts y1 = y[1].limbs > a.limbs ? level_adjust(ev, y[1], a.limbs, 1.0, a.scale) : y[1];
-            y[j] = square_rs(ev, ks, a, y1);
-        }
+    Cts y1 = square_rs(ev, ks, x, x), y2, top;
+    if (d >= 2) y2 = square_rs(ev, ks, y1, y1);
+    if (d >= 3) {
+        Cts B = ev.mul_int(level_adjust(ev, y1, y2.limbs, 1.0, y2.scale), n[3]);
+        if (d == 4) ev.add_inplace(B, ev.mul_int(y2, n[4]));
+        top = square_rs(ev, ks, y2, B);
     }
-    int lp = y[1].limbs;
-    for (int j = 1; j <= d; j++) lp = std::min(lp, y[j].limbs);
-    double sp = 0;
-    for (int j = 1; j <= d; j++)
-        if (y[j].limbs == lp) {
-            sp = y[j].scale;
-            break;
-        }
-    Cts P;
-    for (int j = 1; j <= d; j++) {
-        Cts t = y[j].limbs > lp ? level_adjust(ev, y[j], lp, (double)n[j], sp) : ev.mul_int(y[j], n[j]);
-        if (j == 1)
+    const Cts &lead = d >= 3 ? top : (d == 2 ? y2 : y1);
+    const int lp = lead.limbs;
+    const double sp = lead.scale;
+    Cts P = d >= 3 ? top : Cts();
+    const Cts *ys[3] = {nullptr, &y1, &y2};
+    for (int j = 1; j <= std::min(d, 2); j++) {
+        const Cts &yj = *ys[j];
+        Cts t = yj.limbs > lp ? level_adjust(ev, yj, lp, (double)n[j], sp) : ev.mul_int(yj, n[j]);
+        if (!P.buf)
             P = t;
         else
             ev.add_inplace(P, t);
@@ -557,17 +554,8 @@ Cts eval_g(Eval &ev, const hx_keyset &ks, const Cts &x, int d)
     return square_rs(ev, ks, xa, P);
 }
 
-int g_depth(int d)
-{
-    std::vector<int> lev(d + 1, 0);
-    lev[1] = 1;
-    int mx = 1;
-    for (int j = 2; j <= d; j++) {
-        lev[j] = (j % 2 == 0) ? lev[j / 2] + 1 : std::max(lev[j - 1], lev[1]) + 1;
-        mx = std::max(mx, lev[j]);
-    }
-    return mx + 1;
-}
+// levels one application of eval_g consumes: y, y^2 and y^2 B(y) as d needs them, then x * P
+int g_depth(int d) { return std::min(d, 3) + 1; }
 
 } // namespace
 
