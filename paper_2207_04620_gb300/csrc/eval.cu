@@ -347,7 +347,7 @@ std::vector<Cts> Eval::rotate_hoisted(const Cts &a, const std::vector<int64_t> &
     return out;
 }
 
-Cts Eval::rescale(const Cts &a)
+Cts Eval::rescale(const Cts &a, int64_t c)
 {
     HX_CHECK(a.limbs >= 2, HX_ELEVEL, "no level left to rescale");
     const int N = ctx.N, top = a.limbs - 1, comps = a.comps, B = a.B;
@@ -356,10 +356,14 @@ Cts Eval::rescale(const Cts &a)
     DevBuf r((size_t)B * comps * top * N, s);
     View rv{r.p, (size_t)comps * top * N, (size_t)top * N};
     const RescaleTable *tab = ctx.t.rescale + a.limbs;
-    launch_rescale_prep(lc(), rv, View{xtop.p, (size_t)comps * N, (size_t)N}, tab, B, comps, top);
+    // rescale(c * a) for an integer c: a's residues times c in the two elementwise passes
+    // (the top limb after its inverse NTT), the same values as multiplying first
+    const Scalars sc = c != 1 ? scalars_for(ctx, a.limbs, c) : Scalars{};
+    const Scalars *scp = c != 1 ? &sc : nullptr;
+    launch_rescale_prep(lc(), rv, View{xtop.p, (size_t)comps * N, (size_t)N}, tab, B, comps, top, scp);
     ntt_inplace(r.p, (size_t)top * N, B * comps, iota_vec(0, top), iota_vec(0, top), false);
     Cts o = alloc(B, comps, top);
-    launch_rescale_final(lc(), o.view(N), a.view(N), rv, tab, B, comps, top);
+    launch_rescale_final(lc(), o.view(N), a.view(N), rv, tab, B, comps, top, scp);
     o.scale = a.scale / (double)ctx.primes[top];
     ctx.counters[C_RESCALE] += B;
     return o;

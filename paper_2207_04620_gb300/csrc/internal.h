@@ -174,10 +174,10 @@ void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const
 void alu_calibrate(const LaunchCtx &c, uint64_t q, double *shoup_per_s, double *mac_per_s);
 void launch_moddown_final_mux(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
                               int limbs, View src, const uint64_t *v, const Scalars &cs, uint64_t g1, uint64_t g2);
-void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps,
-                         int top);
-void launch_rescale_final(const LaunchCtx &c, View out, View in, View r, const RescaleTable *tab, int B,
-                          int comps, int top);
+void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps, int top,
+                         const Scalars *sc = nullptr);
+void launch_rescale_final(const LaunchCtx &c, View out, View in, View r, const RescaleTable *tab, int B, int comps,
+                          int top, const Scalars *sc = nullptr);
 void launch_keygen_b(const LaunchCtx &c, uint64_t *b, const uint64_t *a, const uint64_t *e, const uint64_t *s,
                      const uint64_t *sp, const uint64_t *gadget_mask, int rows, const int *prime_of_row_dev,
                      bool to_mont);

@@ -562,7 +562,8 @@ __global__ void k_moddown_final(View out, View acc, View conv, const ModDownTabl
 
 // r_i = ([x + floor(q_t/2)]_{q_t} mod q_i - floor(q_t/2) mod q_i) for the lower limbs
 __global__ void k_rescale_prep(View r, View xtop, const RescaleTable *__restrict__ tab,
-                               const PrimeConst *__restrict__ primes, int comps, int top, int n)
+                               const PrimeConst *__restrict__ primes, int comps, int top, int n,
+                               const __grid_constant__ Scalars sc, bool scaled)
 {
     const int i = blockIdx.y, bc = blockIdx.z, bi = bc / comps, ci = bc % comps;
     const uint64_t qt = primes[top].q, half = tab->half;
@@ -572,7 +573,11 @@ __global__ void k_rescale_prep(View r, View xtop, const RescaleTable *__restrict
     uint64_t *o = r.p + bi * r.bstride + ci * r.cstride + (size_t)i * n;
     // two adjacent coefficients per thread (16-byte loads and stores)
     for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
-        const ulonglong2 xv = *reinterpret_cast<const ulonglong2 *>(x + j);
+        ulonglong2 xv = *reinterpret_cast<const ulonglong2 *>(x + j);
+        if (scaled) {  // the input times an integer: the inverse NTT is linear, so scale its output
+            xv.x = shoup(xv.x, sc.v[top], sc.sh[top], qt);
+            xv.y = shoup(xv.y, sc.v[top], sc.sh[top], qt);
+        }
         const uint64_t v0 = csub(xv.x + half, qt), v1 = csub(xv.y + half, qt);
         *reinterpret_cast<ulonglong2 *>(o + j) = make_ulonglong2(submod(reduce64(v0, Pi.q, Pi.bar), hm, Pi.q),
                                                                  submod(reduce64(v1, Pi.q, Pi.bar), hm, Pi.q));
@@ -580,7 +585,8 @@ __global__ void k_rescale_prep(View r, View xtop, const RescaleTable *__restrict
 }
 
 __global__ void k_rescale_final(View out, View in, View r, const RescaleTable *__restrict__ tab,
-                                const PrimeConst *__restrict__ primes, int comps, int n)
+                                const PrimeConst *__restrict__ primes, int comps, int n,
+                                const __grid_constant__ Scalars sc, bool scaled)
 {
     const int i = blockIdx.y, bc = blockIdx.z, bi = bc / comps, ci = bc % comps;
     const uint64_t q = primes[i].q, w = tab->qinv[i], wsh = tab->qinv_sh[i];
@@ -588,7 +594,11 @@ __global__ void k_rescale_final(View out, View in, View r, const RescaleTable *_
     const uint64_t *rr = r.p + bi * r.bstride + ci * r.cstride + (size_t)i * n;
     uint64_t *o = out.p + bi * out.bstride + ci * out.cstride + (size_t)i * n;
     for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
-        const ulonglong2 av = *reinterpret_cast<const ulonglong2 *>(a + j);
+        ulonglong2 av = *reinterpret_cast<const ulonglong2 *>(a + j);
+        if (scaled) {
+            av.x = shoup(av.x, sc.v[i], sc.sh[i], q);
+            av.y = shoup(av.y, sc.v[i], sc.sh[i], q);
+        }
         const ulonglong2 rv = *reinterpret_cast<const ulonglong2 *>(rr + j);
         *reinterpret_cast<ulonglong2 *>(o + j) =
             make_ulonglong2(shoup(submod(av.x, rv.x, q), w, wsh, q), shoup(submod(av.y, rv.y, q), w, wsh, q));
@@ -877,20 +887,23 @@ void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, con
     post(c);
 }
 
-void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps, int top)
+void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps, int top,
+                         const Scalars *sc)
 {
     Timed tm_(c, K_RESCALE, 8.0 * B * comps * (top + 1) * c.N);
     dim3 grid(ew_blocks(c.N, 2), top, B * comps);
-    k_rescale_prep<<<grid, 256, 0, c.stream>>>(r, xtop, tab, c.t->primes, comps, top, c.N);
+    k_rescale_prep<<<grid, 256, 0, c.stream>>>(r, xtop, tab, c.t->primes, comps, top, c.N, sc ? *sc : Scalars{},
+                                               sc != nullptr);
     post(c);
 }
 
 void launch_rescale_final(const LaunchCtx &c, View out, View in, View r, const RescaleTable *tab, int B, int comps,
-                          int top)
+                          int top, const Scalars *sc)
 {
     Timed tm_(c, K_RESCALE, 24.0 * B * comps * top * c.N);
     dim3 grid(ew_blocks(c.N, 2), top, B * comps);
-    k_rescale_final<<<grid, 256, 0, c.stream>>>(out, in, r, tab, c.t->primes, comps, c.N);
+    k_rescale_final<<<grid, 256, 0, c.stream>>>(out, in, r, tab, c.t->primes, comps, c.N, sc ? *sc : Scalars{},
+                                                sc != nullptr);
     post(c);
 }
 

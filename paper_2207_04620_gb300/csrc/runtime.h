@@ -157,7 +157,7 @@ struct Eval {
     Cts tensor(const Cts &a, const Cts &b);
     void tensor_acc(Cts &acc, const Cts &a, const Cts &b);
     Cts relinearize(const Cts &d, const SwitchKey &rk);
-    Cts rescale(const Cts &a);
+    Cts rescale(const Cts &a, int64_t c = 1);  // rescale(c * a), c an integer scalar
     Cts drop(const Cts &a, int limbs);  // shares storage
     Cts copy(const Cts &a);
     Cts rotate(const Cts &a, int64_t k, const hx_keyset &ks);

@@ -517,7 +517,7 @@ Cts level_adjust(Eval &ev, const Cts &ct, int target, double c_real, double targ
     const uint64_t qt = ev.ctx.primes[target];
     const double c = round_half_away(c_real * target_scale * (double)qt / ct.scale);
     HX_CHECK(std::fabs(c) < 4.6e18, HX_EINVAL, "level-adjust constant too large");
-    Cts y = ev.rescale(ev.mul_int(x, (int64_t)c));
+    Cts y = ev.rescale(x, (int64_t)c);
     y.scale = target_scale;
     return y;
 }
