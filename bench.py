@@ -449,10 +449,12 @@ def run_sign(args):
     times = []
     for it in range(args.steps):
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed")
         t0 = time.perf_counter()
         outs = step(100 + it)
         torch.cuda.synchronize()
         times.append(time.perf_counter() - t0)
+        torch.cuda.nvtx.range_pop()
         if it < args.steps - 1:
             for o in outs:
                 hx.hx_ct_destroy(o)
