@@ -253,6 +253,8 @@ def test_error_statuses(cfg0):
     assert e.value.code == -3
     with pytest.raises(hx.HxError):
         hx.hx_matmul_plan_create(ctx, 12, 3)    # h not a power of two
+    with pytest.raises(hx.HxError):
+        hx.hx_matmul_plan_create(ctx, 1, 3)     # 1x1 blocks are a plain slot product, not HE-MatMult
     # empty and malformed batches are refused before any launch
     for call in (lambda: hx.hx_matmul_batch(ctx, cfg0.ks, 0, [], [], 16),
                  lambda: hx.hx_sign_approx_batch(ctx, cfg0.ks, [], 2, 1),
@@ -325,7 +327,8 @@ def _matmul_case(name, h, seeds, count):
     return pr, beta, limbs
 
 
-@pytest.mark.parametrize("name,h", [("cfg0", 16), ("alg3", 8), ("alg3", 32)])
+@pytest.mark.parametrize("name,h", [("cfg0", 16), ("alg3", 8), ("alg3", 32),
+                                    ("cfg0", 2), ("alg3", 2), ("alg3", 4)])   # smallest blocks: one baby step
 def test_matmul_bit_exact_and_accurate(name, h):
     pr, beta, limbs = _matmul_case(name, h, 0, 2)
     try:
