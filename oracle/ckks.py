@@ -750,6 +750,40 @@ class Evaluator:
     def mul_relin(self, a: Ciphertext, b: Ciphertext) -> Ciphertext:
         return self.relinearize(self.tensor(a, b))
 
+    def relin_rescale(self, d: Ciphertext) -> Ciphertext:
+        """Relinearisation followed by RS as one division (reading R21).  With
+        acc_c the key inner product of d_2 over Q_l and P (hybrid key switching,
+        before ModDown), y_c = acc_c + P d_c is the relinearised component
+        times P, an element of Z_{Q_l P}.  Dividing by P q_top with rounding:
+        h = floor(P q_top / 2), the remainder r = Conv_{q_top,P -> Q_{l-1}}
+        ([y_c + h]_{P q_top}) - h is taken from the residues of y_c + h at
+        q_top and the special primes (fast conversion, reading R11), and
+        out_c = (y_c - r) (P q_top)^-1 over q_0 .. q_{l-2}.  Every output
+        coefficient is round(y_c / (P q_top)) minus an integer in [0, K]
+        (the conversion's overshoot)."""
+        if d.limbs < 2:
+            raise ValueError("no level left to rescale")
+        self._count("KeySwitch")
+        self._count("Rescale")
+        ctx = self.ctx
+        L = d.limbs
+        top = L - 1
+        qs, lower, qt = ctx.q[:L], ctx.q[:top], ctx.q[top]
+        src = [qt] + ctx.p
+        Pq = ctx.P * qt
+        h = Pq // 2
+        a0, a1 = self.inner_product(self.modup(d.c[2], L), self.ks.relin, L)
+        out = []
+        for acc, dc in ((a0, d.c[0]), (a1, d.c[1])):
+            y = ctx.add(acc[:L], ctx.mul_scalar(dc, [ctx.P % t for t in qs], qs), qs)
+            z = ctx.intt(np.concatenate([y[top:L], acc[L:]]), src)
+            z = ctx.add_scalar(z, [h % t for t in src], src)
+            r = ctx.basis_convert(z, src, lower)
+            r = ctx.add_scalar(r, [(t - h % t) % t for t in lower], lower)
+            r = ctx.ntt(r, lower)
+            out.append(ctx.mul_scalar(ctx.sub(y[:top], r, lower), [pow(Pq % t, -1, t) for t in lower], lower))
+        return Ciphertext(np.stack(out), d.scale / float(qt))
+
     # -- levels -----------------------------------------------------------------
     def drop(self, ct: Ciphertext, limbs: int) -> Ciphertext:
         """Discard the top primes (exact; the scale is unchanged)."""

@@ -205,3 +205,47 @@ def test_ciphertext_file_layout_and_round_trip(small, tmp_path):
         open(path, "wb").write(bad)
         with pytest.raises(ValueError):
             C.load_ciphertext(path, ctx)
+
+
+def _crt(rows, primes):
+    Q = math.prod(primes)
+    return [sum(int(rows[r, c]) * (Q // t) * pow(Q // t, -1, t) for r, t in enumerate(primes)) % Q
+            for c in range(rows.shape[1])]
+
+
+def test_relin_rescale_is_the_rounded_division_by_p_qtop(small):
+    """The fused relinearisation + rescale against exact integers: the
+    relinearised component times P is y = acc + P d (acc the key inner product
+    before ModDown, whose own pins are above); CRT-reconstructed, each output
+    coefficient must be round(y / (P q_top)) minus at most K, and the two-step
+    rescale(relinearize(d)) must agree within K + 1."""
+    ctx, ks = small
+    ev = C.Evaluator(ctx, ks)
+    rng = np.random.default_rng(12)
+    a = C.encrypt(ctx, ks, rng.uniform(-1, 1, ctx.S), 31)
+    b = C.encrypt(ctx, ks, rng.uniform(-1, 1, ctx.S), 32)
+    d = ev.tensor(a, b)
+    L = d.limbs
+    out = ev.relin_rescale(d)
+    two = ev.rescale(ev.relinearize(d))
+    assert out.limbs == L - 1 and out.scale == two.scale
+    qs, lower, qt = ctx.q[:L], ctx.q[:L - 1], ctx.q[L - 1]
+    Pq = ctx.P * qt
+    Ql = math.prod(lower)
+    acc = ev.inner_product(ev.modup(d.c[2], L), ks.relin, L)
+    for comp in range(2):
+        # y over Q_l and P, coefficient form: acc, plus P d_c on the Q rows
+        yq = ctx.intt(ctx.add(acc[comp][:L], ctx.mul_scalar(d.c[comp], [ctx.P % t for t in qs], qs), qs), qs)
+        yp = ctx.intt(acc[comp][L:], ctx.p)
+        Y = _crt(np.concatenate([yq, yp])[:, ::29], qs + ctx.p)
+        O = _crt(ctx.intt(out.c[comp], lower)[:, ::29], lower)
+        T = _crt(ctx.intt(two.c[comp], lower)[:, ::29], lower)
+        for y, o, t in zip(Y, O, T):
+            assert ((y + Pq // 2) // Pq - o) % Ql <= ctx.K
+            diff = (o - t) % Ql
+            assert min(diff, Ql - diff) <= ctx.K + 1
+    # K + 1 per coefficient in c0 and c1 is at most (K + 1)(1 + ||s||_1) per coefficient of the
+    # phase, and a slot sums N coefficients
+    z = C.decrypt(ctx, ks, out)
+    assert np.abs(z - C.decrypt(ctx, ks, two)).max() < ctx.N * (ctx.K + 1) * (1 + ctx.N) / out.scale
+    assert np.abs(z - C.decrypt(ctx, ks, a) * C.decrypt(ctx, ks, b)).max() < 2 ** -20
