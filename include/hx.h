@@ -173,6 +173,15 @@ hx_status hx_tensor(hx_context *ctx, const hx_ct *a, const hx_ct *b, hx_ct **out
 hx_status hx_relinearize(hx_context *ctx, const hx_keyset *ks, const hx_ct *d, hx_ct **out, void *stream);
 /* RS: divide by the top prime with rounding to nearest and drop it. */
 hx_status hx_rescale(hx_context *ctx, const hx_ct *a, hx_ct **out, void *stream);
+/* Relinearisation and RS of a 3-component tensor in one division: with
+ * acc the key inner product of d2 (before ModDown) and y = acc + P*(d0, d1),
+ * each output coefficient is round(y / (P*q_top)), one level down, scale /
+ * q_top.  The remainder modulo P*q_top is converted exactly (the fast
+ * conversion's overshoot is counted in FP64 and removed), so a coefficient
+ * is off by one only where that FP64 sum lies within rounding of an integer.
+ * One ModDown NTT pass fewer than hx_relinearize + hx_rescale; the two agree
+ * within 2 per coefficient.  HX_ELEVEL at one limb. */
+hx_status hx_relin_rescale(hx_context *ctx, const hx_keyset *ks, const hx_ct *d, hx_ct **out, void *stream);
 /* discard the top limbs down to `limbs` (exact) */
 hx_status hx_drop(hx_context *ctx, const hx_ct *a, int limbs, hx_ct **out, void *stream);
 /* Rot(a, k): slots move left by k (R(m, k)); HX_EKEY without the Galois key. */

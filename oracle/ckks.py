@@ -755,12 +755,16 @@ class Evaluator:
         acc_c the key inner product of d_2 over Q_l and P (hybrid key switching,
         before ModDown), y_c = acc_c + P d_c is the relinearised component
         times P, an element of Z_{Q_l P}.  Dividing by P q_top with rounding:
-        h = floor(P q_top / 2), the remainder r = Conv_{q_top,P -> Q_{l-1}}
-        ([y_c + h]_{P q_top}) - h is taken from the residues of y_c + h at
-        q_top and the special primes (fast conversion, reading R11), and
-        out_c = (y_c - r) (P q_top)^-1 over q_0 .. q_{l-2}.  Every output
-        coefficient is round(y_c / (P q_top)) minus an integer in [0, K]
-        (the conversion's overshoot)."""
+        h = floor(P q_top / 2), the remainder r = [y_c + h]_{P q_top} - h is
+        taken from the residues of y_c + h at q_top and the special primes by
+        basis conversion made exact with the floating-point correction of
+        Halevi, Polyakov and Shoup (2019): with z_i = [x_i shat_i^-1]_{s_i}
+        the fast conversion sum_i z_i shat_i overshoots by u P q_top,
+        u = floor(sum_i z_i / s_i), evaluated in FP64 (products and sums
+        rounded to nearest, left to right) and subtracted.  Then
+        out_c = (y_c - r) (P q_top)^-1 over q_0 .. q_{l-2}: round(y_c / (P q_top)),
+        off by one only where that FP64 sum falls within rounding of an
+        integer."""
         if d.limbs < 2:
             raise ValueError("no level left to rescale")
         self._count("KeySwitch")
@@ -778,8 +782,17 @@ class Evaluator:
             y = ctx.add(acc[:L], ctx.mul_scalar(dc, [ctx.P % t for t in qs], qs), qs)
             z = ctx.intt(np.concatenate([y[top:L], acc[L:]]), src)
             z = ctx.add_scalar(z, [h % t for t in src], src)
+            zs = ctx.mul_scalar(z, [pow(Pq // t % t, -1, t) for t in src], src)
+            v = np.zeros(ctx.N)
+            for i, t in enumerate(src):
+                v = v + zs[i].astype(np.float64) * (1.0 / float(t))
+            u = np.floor(v).astype(np.uint64)
             r = ctx.basis_convert(z, src, lower)
-            r = ctx.add_scalar(r, [(t - h % t) % t for t in lower], lower)
+            for i, t in enumerate(lower):
+                tt = np.uint64(t)
+                over = (u * np.uint64(Pq % t)) % tt  # u <= K <= 6: no 64-bit overflow for t < 2^61
+                r[i] = (r[i] + (tt - over)) % tt
+                r[i] = (r[i] + (tt - np.uint64(h % t))) % tt
             r = ctx.ntt(r, lower)
             out.append(ctx.mul_scalar(ctx.sub(y[:top], r, lower), [pow(Pq % t, -1, t) for t in lower], lower))
         return Ciphertext(np.stack(out), d.scale / float(qt))

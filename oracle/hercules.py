@@ -507,7 +507,8 @@ def level_adjust(ev: C.Evaluator, ct: C.Ciphertext, target: int, c_real: float, 
 
 
 def _square_rs(ev, a, b):
-    return ev.rescale(ev.relinearize(ev.tensor(a, b)))
+    """a * b, relinearised and rescaled in one division by P q_top (reading R21)."""
+    return ev.relin_rescale(ev.tensor(a, b))
 
 
 def eval_g(ev: C.Evaluator, x: C.Ciphertext, d: int) -> C.Ciphertext:

@@ -438,6 +438,15 @@ hx_status hx_relinearize(hx_context *ctx, const hx_keyset *ks, const hx_ct *d, h
     HX_END
 }
 
+hx_status hx_relin_rescale(hx_context *ctx, const hx_keyset *ks, const hx_ct *d, hx_ct **out, void *stream)
+{
+    HX_TRY
+    ONE_IN(ks && d)
+    *out = wrap(ctx, ev.relin_rescale(d->c, ks->relin));
+    return HX_OK;
+    HX_END
+}
+
 hx_status hx_rescale(hx_context *ctx, const hx_ct *a, hx_ct **out, void *stream)
 {
     HX_TRY

@@ -216,12 +216,67 @@ void build_context(hx_context &c, const hx_params &p)
             R.half_mod[i] = R.half % q;
         }
     }
+    // relinearisation + rescale tables, by limbs: divide by P q_top, q_top = q_{l-1}
+    c.h_relin_rs.assign(n_q + 1, RelinRescaleTable{});
+    for (int l = 2; l <= n_q; l++) {
+        RelinRescaleTable &M = c.h_relin_rs[l];
+        memset(&M, 0, sizeof(M));
+        ConvTable &T = M.conv;
+        T.n_src = K + 1;
+        T.n_dst = l - 1;
+        for (int k = 0; k <= K; k++) {  // sources: q_top, then the special primes (rows l-1 .. l+K-1)
+            T.src_row[k] = l - 1 + k;
+            T.src_prime[k] = k == 0 ? l - 1 : n_q + k - 1;
+        }
+        for (int i = 0; i < l - 1; i++) {
+            T.dst_row[i] = i;
+            T.dst_prime[i] = i;
+        }
+        auto prod_mod = [&](int skip, uint64_t t) {  // (P q_top / source skip) mod t, or P q_top mod t
+            uint64_t v = 1;
+            for (int k = 0; k <= K; k++)
+                if (k != skip) v = hmul(v, c.primes[T.src_prime[k]] % t, t);
+            return v;
+        };
+        for (int k = 0; k <= K; k++) {
+            const uint64_t sk = c.primes[T.src_prime[k]];
+            T.inv[k] = hinv(prod_mod(k, sk), sk);
+            T.inv_sh[k] = shoup_companion(T.inv[k], sk);
+            for (int i = 0; i < l - 1; i++) T.mont[k][i] = to_mont_host(prod_mod(k, c.primes[i]), c.primes[i]);
+        }
+        // h = floor(P q_top / 2) = (P q_top - 1) / 2, the product being odd: h = (P q_top - 1) * 2^-1 mod t
+        auto half_mod = [&](uint64_t t) {
+            const uint64_t pq = prod_mod(-1, t);
+            return hmul((pq + t - 1) % t, (t + 1) / 2, t);
+        };
+        T.shift = 1;
+        for (int k = 0; k <= K; k++) {
+            T.add_src[k] = half_mod(c.primes[T.src_prime[k]]);
+            T.inv_d[k] = 1.0 / (double)c.primes[T.src_prime[k]];
+        }
+        for (int i = 0; i < l - 1; i++) {
+            T.sub_dst[i] = half_mod(c.primes[i]);
+            T.prod_mod[i] = prod_mod(-1, c.primes[i]);
+        }
+        for (int i = 0; i < l; i++) {
+            const uint64_t t = c.primes[i];
+            uint64_t Pm = 1;
+            for (int m = 0; m < K; m++) Pm = hmul(Pm, c.primes[n_q + m] % t, t);
+            M.pmod[i] = Pm;
+            M.pmod_sh[i] = shoup_companion(Pm, t);
+            if (i < l - 1) {
+                M.pqinv[i] = hinv(prod_mod(-1, t), t);
+                M.pqinv_sh[i] = shoup_companion(M.pqinv[i], t);
+            }
+        }
+    }
     c.t.primes = upload(c.h_primes);
     c.t.tw_fwd = upload(twf);
     c.t.tw_inv = upload(twi);
     c.t.modup = upload(c.h_modup);
     c.t.moddown = upload(c.h_moddown);
     c.t.rescale = upload(c.h_rescale);
+    c.t.relin_rs = upload(c.h_relin_rs);
     std::vector<int> ids(n_all);
     for (int i = 0; i < n_all; i++) ids[i] = i;
     c.d_prime_ids = upload(ids);
@@ -271,6 +326,7 @@ void destroy_context(hx_context &c)
     cudaFree(c.t.tw_inv);
     cudaFree(c.t.modup);
     cudaFree(c.t.moddown);
+    cudaFree(c.t.relin_rs);
     cudaFree(c.t.rescale);
     cudaFree(c.d_prime_ids);
 }

@@ -164,7 +164,7 @@ BufPtr Eval::modup(const View &d, int B, int limbs)
     ntt_oop(d.p, d.bstride, coef.p, (size_t)limbs * N, B, iota_vec(0, limbs), iota_vec(0, limbs), iota_vec(0, limbs),
             true);
     BufPtr D = std::make_shared<DevBuf>((size_t)B * nd * ext * N, s);
-    launch_basis_convert(lc(), ctx.t.modup + (size_t)limbs * ctx.dnum, ext, View{D->p, (size_t)nd * ext * N, 0},
+    launch_basis_convert(lc(), ctx.t.modup + (size_t)limbs * ctx.dnum, K, View{D->p, (size_t)nd * ext * N, 0},
                          View{coef.p, (size_t)limbs * N, 0}, B, nd, (size_t)ext * N, 0);
     std::vector<int> off, pr;
     for (int j = 0; j < nd; j++) {
@@ -196,7 +196,7 @@ Cts Eval::moddown_add(const View &accv, int B, int limbs, const View &add, int a
     const int N = ctx.N, K = ctx.K, ext = limbs + K;
     ntt_inplace(accv.p, (size_t)ext * N, 2 * B, iota_vec(limbs, K), iota_vec(ctx.n_q, K), true);
     DevBuf conv((size_t)B * 2 * limbs * N, s);
-    launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), limbs,
+    launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), ctx.K,
                          View{conv.p, (size_t)limbs * N, 0}, View{accv.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0);
     ntt_inplace(conv.p, (size_t)limbs * N, 2 * B, iota_vec(0, limbs), iota_vec(0, limbs), false);
     Cts o = alloc(B, 2, limbs);
@@ -251,6 +251,41 @@ Cts Eval::relinearize(const Cts &d, const SwitchKey &rk)
     BufPtr D = modup(d2, d.B, d.limbs);
     Cts o = ks_finish(D, d2, d.B, d.limbs, rk, 1, d.view(N), 3, 1);
     o.scale = d.scale;
+    return o;
+}
+
+// Relinearisation and RS in one division by P q_top: the key inner product of d_2 over
+// Q_l and P; y_c = acc_c + P d_c (only q_top's row is formed in memory, the lower rows in
+// the epilogue); the remainder [y_c + h]_{P q_top} - h converted from q_top and the special
+// primes to Q_{l-1}; out_c = (y_c - remainder) (P q_top)^-1.
+Cts Eval::relin_rescale(const Cts &d, const SwitchKey &rk)
+{
+    HX_CHECK(d.comps == 3, HX_EINVAL, "relinearisation needs 3 components");
+    HX_CHECK(rk.buf, HX_EKEY, "no relinearisation key");
+    HX_CHECK(d.limbs >= 2, HX_ELEVEL, "no level left to rescale");
+    const int N = ctx.N, K = ctx.K, L = d.limbs, B = d.B, ext = L + K, nd = (L + K - 1) / K;
+    View d2{d.d + 2 * d.cstride(N), d.bstride(N), d.cstride(N)};
+    BufPtr D = modup(d2, B, L);
+    DevBuf acc((size_t)B * 2 * ext * N, s);
+    View accv{acc.p, (size_t)2 * ext * N, (size_t)ext * N};
+    launch_key_ip(lc(), accv, D->p, d2.p, d2.bstride, rk.buf->p, ctx.n_all, ctx.n_q, K, L, nd, 1, B);
+    ctx.counters[C_KS] += B;
+    D.reset();
+    const RelinRescaleTable *tab = ctx.t.relin_rs + L;
+    launch_relin_rs_top(lc(), accv, d.view(N), tab, B, L);
+    std::vector<int> rows = iota_vec(L - 1, K + 1), primes(K + 1);
+    primes[0] = L - 1;
+    for (int k = 0; k < K; k++) primes[k + 1] = ctx.n_q + k;
+    ntt_inplace(acc.p, (size_t)ext * N, 2 * B, rows, primes, true);
+    DevBuf conv((size_t)B * 2 * (L - 1) * N, s);
+    launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(tab), K + 1, View{conv.p, (size_t)(L - 1) * N, 0},
+                         View{acc.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0);
+    ntt_inplace(conv.p, (size_t)(L - 1) * N, 2 * B, iota_vec(0, L - 1), iota_vec(0, L - 1), false);
+    Cts o = alloc(B, 2, L - 1);
+    launch_relin_rs_final(lc(), o.view(N), accv, d.view(N),
+                          View{conv.p, (size_t)2 * (L - 1) * N, (size_t)(L - 1) * N}, tab, B, L);
+    o.scale = d.scale / (double)ctx.primes[L - 1];
+    ctx.counters[C_RESCALE] += B;
     return o;
 }
 
@@ -321,7 +356,7 @@ Cts Eval::hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, con
                           limbs, nd, g1, g2, B);
     ntt_inplace(z.p, (size_t)ext * N, 2 * B, iota_vec(limbs, K), iota_vec(ctx.n_q, K), true);
     DevBuf conv((size_t)B * 2 * limbs * N, s);
-    launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), limbs,
+    launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), ctx.K,
                          View{conv.p, (size_t)limbs * N, 0}, View{z.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0);
     ntt_inplace(conv.p, (size_t)limbs * N, 2 * B, iota_vec(0, limbs), iota_vec(0, limbs), false);
     Cts o = alloc(B, 2, limbs);

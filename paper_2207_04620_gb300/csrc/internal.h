@@ -15,7 +15,7 @@
 namespace hx {
 
 constexpr int MAXP = HX_MAX_Q + HX_MAX_P;
-constexpr int MAXK = HX_MAX_P;
+constexpr int MAXK = HX_MAX_P + 1;  // conversion sources: the special primes, plus q_top when RS joins ModDown
 constexpr int MAX_NTT_ROWS = 1024;
 constexpr int NTT_VARIANTS = 3;  // tile widths 8, 16, 32
 
@@ -29,11 +29,26 @@ struct ConvTable {
     int dst_prime[MAXP];
     uint64_t inv[MAXK], inv_sh[MAXK];   // [qhat_i^-1]_{q_i} with Shoup companion
     uint64_t mont[MAXK][MAXP];          // (qhat_i mod t) * 2^64 mod t (Montgomery form)
+    // shift != 0: the rounded division's remainder.  Convert x + h exactly (the overshoot
+    // u = floor(sum_i y_i / q_i), summed in FP64, times the source product is removed),
+    // then subtract h
+    int shift;
+    uint64_t add_src[MAXK];             // h mod q_i
+    double inv_d[MAXK];                 // 1 / q_i in FP64
+    uint64_t sub_dst[MAXP];             // h mod t
+    uint64_t prod_mod[MAXP];            // (product of the sources) mod t
 };
 
 struct ModDownTable {
     ConvTable conv;                      // P -> Q_l
     uint64_t pinv[MAXP], pinv_sh[MAXP];  // P^-1 mod q_i, Shoup
+};
+
+// relinearisation and rescale in one division by P * q_top (limbs l -> l-1)
+struct RelinRescaleTable {
+    ConvTable conv;                      // {q_top, P} -> Q_{l-1}, shifted by h = floor(P q_top / 2)
+    uint64_t pmod[MAXP], pmod_sh[MAXP];  // P mod q_i, i < l
+    uint64_t pqinv[MAXP], pqinv_sh[MAXP];  // (P q_top)^-1 mod q_i, i < l-1
 };
 
 struct RescaleTable {
@@ -86,6 +101,7 @@ struct DeviceTables {
     ConvTable *modup = nullptr;     // [(n_q+1) * dnum] by (limbs, digit)
     ModDownTable *moddown = nullptr;// [n_q+1] by limbs
     RescaleTable *rescale = nullptr;// [n_q+1] by limbs
+    RelinRescaleTable *relin_rs = nullptr;  // [n_q+1] by limbs
     int ntt_var[4] = {1, 1, 1, 1};  // tile width per phase: fwd cols, fwd rows, inv cols, inv rows
     int n_sm = 1;                   // multiprocessors of the device
 };
@@ -148,8 +164,8 @@ void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &s
 void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate);
 void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int B, int comps, int limbs,
                          bool accumulate = false);
-void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int n_dst_rows_max, View out, View in,
-                          int B, int groups, size_t group_stride_out, size_t group_stride_in);
+void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int max_src, View out, View in, int B,
+                          int groups, size_t gstride_out, size_t gstride_in);
 void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
                    const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B,
                    bool accumulate = false);
@@ -174,6 +190,9 @@ void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const
 void alu_calibrate(const LaunchCtx &c, uint64_t q, double *shoup_per_s, double *mac_per_s);
 void launch_moddown_final_mux(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
                               int limbs, View src, const uint64_t *v, const Scalars &cs, uint64_t g1, uint64_t g2);
+void launch_relin_rs_top(const LaunchCtx &c, View acc, View d, const RelinRescaleTable *tab, int B, int limbs);
+void launch_relin_rs_final(const LaunchCtx &c, View out, View acc, View d, View conv, const RelinRescaleTable *tab,
+                           int B, int limbs);
 void launch_rescale_prep(const LaunchCtx &c, View r, View xtop, const RescaleTable *tab, int B, int comps, int top,
                          const Scalars *sc = nullptr);
 void launch_rescale_final(const LaunchCtx &c, View out, View in, View r, const RescaleTable *tab, int B, int comps,

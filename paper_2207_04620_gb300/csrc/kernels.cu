@@ -241,7 +241,8 @@ __global__ void k_automorphism(View out, View in, uint64_t g, int comps, int log
 }
 
 // Fast basis conversion; grid: x over coefficients, z = b * groups + grp
-__global__ void __launch_bounds__(256, 4)
+template <int MK>  // at most MK sources (register arrays sized to it; four blocks per SM up to 4)
+__global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2)
     k_basis_convert(const ConvTable *__restrict__ tabs, View out, View in, const PrimeConst *__restrict__ primes,
                     int groups, size_t gstride_out, size_t gstride_in, int n)
 {
@@ -251,9 +252,11 @@ __global__ void __launch_bounds__(256, 4)
     const ConvTable &T = tabs[gi];
     __shared__ uint64_t smont[MAXK * MAXP];
     __shared__ uint64_t sq[MAXP], sbar[MAXP], smneg[MAXP];
-    __shared__ uint64_t ssq[MAXK], sinv[MAXK], sinvsh[MAXK];
+    __shared__ uint64_t ssq[MAXK], sinv[MAXK], sinvsh[MAXK], sadd[MAXK], ssub[MAXP], spq[MAXP];
+    __shared__ double sinvd[MAXK];
     __shared__ int sdrow[MAXP], ssrow[MAXK];
     const int ns = T.n_src, nd = T.n_dst;
+    const bool shift = T.shift != 0;
     for (int i = threadIdx.x; i < ns * nd; i += blockDim.x) smont[i] = T.mont[i / nd][i % nd];
     for (int d = threadIdx.x; d < nd; d += blockDim.x) {
         const PrimeConst P = primes[T.dst_prime[d]];
@@ -261,30 +264,50 @@ __global__ void __launch_bounds__(256, 4)
         sbar[d] = P.bar;
         smneg[d] = P.mneg;
         sdrow[d] = T.dst_row[d];
+        ssub[d] = T.sub_dst[d];
+        spq[d] = T.prod_mod[d];
     }
     for (int i = threadIdx.x; i < ns; i += blockDim.x) {
         ssq[i] = primes[T.src_prime[i]].q;
         sinv[i] = T.inv[i];
         sinvsh[i] = T.inv_sh[i];
         ssrow[i] = T.src_row[i];
+        sadd[i] = T.add_src[i];
+        sinvd[i] = T.inv_d[i];
     }
     __syncthreads();
     const uint64_t *src = in.p + bi * in.bstride + gi * gstride_in;
     uint64_t *dst = out.p + bi * out.bstride + gi * gstride_out;
     for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
-        uint64_t y0[MAXK], y1[MAXK];
+        uint64_t y0[MK], y1[MK];
 #pragma unroll
-        for (int i = 0; i < MAXK; i++) {
+        for (int i = 0; i < MK; i++) {
             if (i < ns) {
-                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(src + (size_t)ssrow[i] * n + j);
+                ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(src + (size_t)ssrow[i] * n + j);
+                if (shift) {
+                    x.x = addmod(x.x, sadd[i], ssq[i]);
+                    x.y = addmod(x.y, sadd[i], ssq[i]);
+                }
                 y0[i] = shoup(x.x, sinv[i], sinvsh[i], ssq[i]);
                 y1[i] = shoup(x.y, sinv[i], sinvsh[i], ssq[i]);
             }
         }
+        uint64_t u0 = 0, u1 = 0;  // overshoot of the fast conversion (shifted tables only)
+        if (shift) {
+            double v0 = 0.0, v1 = 0.0;  // products and sums rounded to nearest, in source order
+#pragma unroll
+            for (int i = 0; i < MK; i++)
+                if (i < ns) {
+                    v0 = __dadd_rn(v0, __dmul_rn(__ull2double_rn(y0[i]), sinvd[i]));
+                    v1 = __dadd_rn(v1, __dmul_rn(__ull2double_rn(y1[i]), sinvd[i]));
+                }
+            u0 = __double2ull_rd(v0);
+            u1 = __double2ull_rd(v1);
+        }
         for (int d = 0; d < nd; d++) {
             Acc128 a0, a1;
 #pragma unroll
-            for (int i = 0; i < MAXK; i++)
+            for (int i = 0; i < MK; i++)
                 if (i < ns) {
                     const uint64_t m = smont[i * nd + d];
                     a0.mac(y0[i], m);
@@ -294,6 +317,10 @@ __global__ void __launch_bounds__(256, 4)
             ulonglong2 r;
             r.x = csub(csub(a0.hi - __umul64hi(a0.hi, bar) * q, q) + mont64(a0.lo, q, mneg), q);
             r.y = csub(csub(a1.hi - __umul64hi(a1.hi, bar) * q, q) + mont64(a1.lo, q, mneg), q);
+            if (shift) {  // u <= sources - 1 <= 6, so u * (product mod q) < 2^64
+                r.x = submod(submod(r.x, reduce64(u0 * spq[d], q, bar), q), ssub[d], q);
+                r.y = submod(submod(r.y, reduce64(u1 * spq[d], q, bar), q), ssub[d], q);
+            }
             *reinterpret_cast<ulonglong2 *>(dst + (size_t)sdrow[d] * n + j) = r;
         }
     }
@@ -605,6 +632,45 @@ __global__ void k_rescale_final(View out, View in, View r, const RescaleTable *_
     }
 }
 
+// Relinearisation + rescale (division by P q_top).  Row l-1 (q_top) of each key-switched
+// component becomes y = acc + (P mod q_top) d, the value the conversion reads there.
+__global__ void k_relin_rs_top(View acc, View d, const RelinRescaleTable *__restrict__ tab,
+                               const PrimeConst *__restrict__ primes, int top, int n)
+{
+    const int bc = blockIdx.z, bi = bc / 2, ci = bc % 2;
+    const uint64_t q = primes[top].q, w = tab->pmod[top], wsh = tab->pmod_sh[top];
+    uint64_t *a = acc.p + bi * acc.bstride + ci * acc.cstride + (size_t)top * n;
+    const uint64_t *x = d.p + bi * d.bstride + ci * d.cstride + (size_t)top * n;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 av = *reinterpret_cast<const ulonglong2 *>(a + j);
+        const ulonglong2 xv = *reinterpret_cast<const ulonglong2 *>(x + j);
+        *reinterpret_cast<ulonglong2 *>(a + j) =
+            make_ulonglong2(addmod(av.x, shoup(xv.x, w, wsh, q), q), addmod(av.y, shoup(xv.y, w, wsh, q), q));
+    }
+}
+
+// out_i = (acc_i + P d_i - r_i) (P q_top)^-1 on the l-1 lower rows, r the converted remainder
+__global__ void k_relin_rs_final(View out, View acc, View d, View conv, const RelinRescaleTable *__restrict__ tab,
+                                 const PrimeConst *__restrict__ primes, int n)
+{
+    const int i = blockIdx.y, bc = blockIdx.z, bi = bc / 2, ci = bc % 2;
+    const uint64_t q = primes[i].q, pm = tab->pmod[i], pmsh = tab->pmod_sh[i];
+    const uint64_t w = tab->pqinv[i], wsh = tab->pqinv_sh[i];
+    const size_t row = (size_t)i * n;
+    const uint64_t *a = acc.p + bi * acc.bstride + ci * acc.cstride + row;
+    const uint64_t *x = d.p + bi * d.bstride + ci * d.cstride + row;
+    const uint64_t *r = conv.p + bi * conv.bstride + ci * conv.cstride + row;
+    uint64_t *o = out.p + bi * out.bstride + ci * out.cstride + row;
+    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+        const ulonglong2 av = *reinterpret_cast<const ulonglong2 *>(a + j);
+        const ulonglong2 xv = *reinterpret_cast<const ulonglong2 *>(x + j);
+        const ulonglong2 rv = *reinterpret_cast<const ulonglong2 *>(r + j);
+        const uint64_t y0 = addmod(av.x, shoup(xv.x, pm, pmsh, q), q), y1 = addmod(av.y, shoup(xv.y, pm, pmsh, q), q);
+        *reinterpret_cast<ulonglong2 *>(o + j) =
+            make_ulonglong2(shoup(submod(y0, rv.x, q), w, wsh, q), shoup(submod(y1, rv.y, q), w, wsh, q));
+    }
+}
+
 // b = e - a*s + gad_r * s'  (all NTT form, row r modulo prime r); optionally
 // b and a are left in Montgomery form for the key inner product.
 __global__ void k_keygen_b(uint64_t *b, uint64_t *a, const uint64_t *e, const uint64_t *s, const uint64_t *sp,
@@ -781,13 +847,19 @@ void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int 
     post(c);
 }
 
-void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int, View out, View in, int B, int groups,
-                          size_t gstride_out, size_t gstride_in)
+void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int max_src, View out, View in, int B,
+                          int groups, size_t gstride_out, size_t gstride_in)
 {
     Timed tm_(c, K_CONV, 0.0);
     HX_CHECK(B * groups < 65536, HX_EINVAL, "conversion batch too large");
+    HX_CHECK(max_src >= 1 && max_src <= MAXK, HX_EINVAL, "too many conversion sources");
     dim3 grid(ew_blocks(c.N, 2), 1, B * groups);
-    k_basis_convert<<<grid, 256, 0, c.stream>>>(tab_dev, out, in, c.t->primes, groups, gstride_out, gstride_in, c.N);
+    if (max_src <= 4)
+        k_basis_convert<4><<<grid, 256, 0, c.stream>>>(tab_dev, out, in, c.t->primes, groups, gstride_out, gstride_in,
+                                                       c.N);
+    else
+        k_basis_convert<MAXK><<<grid, 256, 0, c.stream>>>(tab_dev, out, in, c.t->primes, groups, gstride_out,
+                                                          gstride_in, c.N);
     post(c);
 }
 
@@ -884,6 +956,23 @@ void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, con
     Timed tm_(c, K_MODDOWN, 8.0 * B * 2 * limbs * c.N * ((add_mask ? 4.0 : 3.0)));
     dim3 grid(ew_blocks(c.N, 2), limbs, B * 2);
     k_moddown_final<<<grid, 256, 0, c.stream>>>(out, acc, conv, tab, c.t->primes, add, add_mask, g, c.log_n);
+    post(c);
+}
+
+void launch_relin_rs_top(const LaunchCtx &c, View acc, View d, const RelinRescaleTable *tab, int B, int limbs)
+{
+    Timed tm_(c, K_RESCALE, 24.0 * B * 2 * c.N);
+    dim3 grid(ew_blocks(c.N, 2), 1, B * 2);
+    k_relin_rs_top<<<grid, 256, 0, c.stream>>>(acc, d, tab, c.t->primes, limbs - 1, c.N);
+    post(c);
+}
+
+void launch_relin_rs_final(const LaunchCtx &c, View out, View acc, View d, View conv, const RelinRescaleTable *tab,
+                           int B, int limbs)
+{
+    Timed tm_(c, K_MODDOWN, 32.0 * B * 2 * (limbs - 1) * c.N);
+    dim3 grid(ew_blocks(c.N, 2), limbs - 1, B * 2);
+    k_relin_rs_final<<<grid, 256, 0, c.stream>>>(out, acc, d, conv, tab, c.t->primes, c.N);
     post(c);
 }
 

@@ -79,7 +79,7 @@ extern "C" hx_status hx_rotate_noalloc(hx_context *ctx, const hx_keyset *ks, con
         r.n_rows = limbs;
         for (int l = 0; l < limbs; l++) r.src_off[l] = r.dst_off[l] = r.prime[l] = (int16_t)l;
         launch_ntt(lc, r, true);
-        launch_basis_convert(lc, ctx->t.modup + (size_t)limbs * ctx->dnum, ext, View{D, (size_t)nd * ext * n, 0},
+        launch_basis_convert(lc, ctx->t.modup + (size_t)limbs * ctx->dnum, ctx->K, View{D, (size_t)nd * ext * n, 0},
                              View{coef, limbs * n, 0}, 1, nd, (size_t)ext * n, 0);
         r.src = r.dst = D;
         r.src_gs = r.dst_gs = (size_t)nd * ext * n;
@@ -106,7 +106,7 @@ extern "C" hx_status hx_rotate_noalloc(hx_context *ctx, const hx_keyset *ks, con
             r.prime[kk] = (int16_t)(ctx->n_q + kk);
         }
         launch_ntt(lc, r, true);
-        launch_basis_convert(lc, reinterpret_cast<const ConvTable *>(ctx->t.moddown + limbs), limbs,
+        launch_basis_convert(lc, reinterpret_cast<const ConvTable *>(ctx->t.moddown + limbs), ctx->K,
                              View{conv, limbs * n, 0}, View{acc, (size_t)ext * n, 0}, 2, 1, 0, 0);
         r.src = r.dst = conv;
         r.src_gs = r.dst_gs = limbs * n;

@@ -66,6 +66,7 @@ struct hx_context {
     std::vector<hx::ConvTable> h_modup;        // [(n_q+1) * dnum]
     std::vector<hx::ModDownTable> h_moddown;   // [n_q+1]
     std::vector<hx::RescaleTable> h_rescale;   // [n_q+1]
+    std::vector<hx::RelinRescaleTable> h_relin_rs;  // [n_q+1]
     hx::DeviceTables t;
     hx::DeviceTables *t_dev = nullptr;
     int *d_prime_ids = nullptr;                // 0..n_all-1
@@ -158,6 +159,7 @@ struct Eval {
     void tensor_acc(Cts &acc, const Cts &a, const Cts &b);
     Cts relinearize(const Cts &d, const SwitchKey &rk);
     Cts rescale(const Cts &a, int64_t c = 1);  // rescale(c * a), c an integer scalar
+    Cts relin_rescale(const Cts &d, const SwitchKey &rk);  // rescale(relinearize(d)) as one division
     Cts drop(const Cts &a, int limbs);  // shares storage
     Cts copy(const Cts &a);
     Cts rotate(const Cts &a, int64_t k, const hx_keyset &ks);

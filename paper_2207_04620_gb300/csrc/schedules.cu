@@ -502,9 +502,10 @@ std::vector<int64_t> g_int_coeffs(int d)
     return n;
 }
 
+// a * b, relinearised and rescaled in one division by P q_top (reading R21)
 Cts square_rs(Eval &ev, const hx_keyset &ks, const Cts &a, const Cts &b)
 {
-    return ev.rescale(ev.relinearize(ev.tensor(a, b), ks.relin));
+    return ev.relin_rescale(ev.tensor(a, b), ks.relin);
 }
 
 // bring ct to `target` limbs at scale target_scale, times c_real: drop to

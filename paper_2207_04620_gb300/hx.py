@@ -73,6 +73,7 @@ _SIGS = {
     "hx_tensor": (c_int, [c_vp, c_vp, c_vp, PP, c_vp]),
     "hx_relinearize": (c_int, [c_vp, c_vp, c_vp, PP, c_vp]),
     "hx_rescale": (c_int, [c_vp, c_vp, PP, c_vp]),
+    "hx_relin_rescale": (c_int, [c_vp, c_vp, c_vp, PP, c_vp]),
     "hx_drop": (c_int, [c_vp, c_vp, c_int, PP, c_vp]),
     "hx_rotate": (c_int, [c_vp, c_vp, c_vp, ctypes.c_int32, PP, c_vp]),
     "hx_rotate_hoisted": (c_int, [c_vp, c_vp, c_vp, P_i32, c_int, PP, c_vp]),
@@ -376,6 +377,10 @@ def hx_tensor(ctx, a, b, stream=None):
 
 def hx_relinearize(ctx, ks, d, stream=None):
     return _op("hx_relinearize", ctx, ks, d, stream=stream)
+
+
+def hx_relin_rescale(ctx, ks, d, stream=None):
+    return _op("hx_relin_rescale", ctx, ks, d, stream=stream)
 
 
 def hx_rescale(ctx, a, stream=None):

@@ -234,6 +234,33 @@ def test_evaluation_primitives_bit_exact(alg3):
         hx.hx_ct_destroy(h_)
 
 
+@pytest.mark.parametrize("name", ["cfg0", "alg3", "sign"])   # K = 1, 2, 3 special primes
+def test_relin_rescale_bit_exact(name):
+    """Relinearisation + RS in one division (hx_relin_rescale) against the
+    oracle at every level of the chain, and against the two-step path in slots."""
+    pr = Pair(name)
+    try:
+        ev = C.Evaluator(pr.octx, pr.oks)
+        top = len(pr.p["q_bits"])
+        rng = np.random.default_rng(5)
+        for limbs in range(top, 1, -1):
+            a = pr.encrypt(rng.uniform(-1, 1, 64), 50 + limbs, limbs=limbs)
+            b = pr.encrypt(rng.uniform(-1, 1, 64), 60 + limbs, limbs=limbs)
+            d = ev.tensor(a, b)
+            hd = hx.hx_tensor(pr.ctx, pr.to_lib(a), pr.to_lib(b))
+            out = hx.hx_relin_rescale(pr.ctx, pr.ks, hd)
+            assert pr.same(out, ev.relin_rescale(d)), limbs
+            two = hx.hx_rescale(pr.ctx, hx.hx_relinearize(pr.ctx, pr.ks, hd))
+            z, w = hx.hx_decrypt(pr.ctx, pr.ks, out, 64), hx.hx_decrypt(pr.ctx, pr.ks, two, 64)
+            assert np.abs(z - w).max() < 2 ** -20
+        one = hx.hx_tensor(pr.ctx, *(pr.to_lib(pr.encrypt(np.ones(4), 70 + i, limbs=1)) for i in range(2)))
+        with pytest.raises(hx.HxError) as e:
+            hx.hx_relin_rescale(pr.ctx, pr.ks, one)
+        assert e.value.code == -3
+    finally:
+        pr.close()
+
+
 def test_error_statuses(cfg0):
     ctx = cfg0.ctx
     a = cfg0.to_lib(cfg0.encrypt(np.ones(4), 1))

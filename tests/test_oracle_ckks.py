@@ -217,8 +217,9 @@ def test_relin_rescale_is_the_rounded_division_by_p_qtop(small):
     """The fused relinearisation + rescale against exact integers: the
     relinearised component times P is y = acc + P d (acc the key inner product
     before ModDown, whose own pins are above); CRT-reconstructed, each output
-    coefficient must be round(y / (P q_top)) minus at most K, and the two-step
-    rescale(relinearize(d)) must agree within K + 1."""
+    coefficient must be round(y / (P q_top)) (the corrected conversion is exact
+    but for an FP64 sum within rounding of an integer: off by one at most), and
+    the two-step rescale(relinearize(d)) must agree within 2."""
     ctx, ks = small
     ev = C.Evaluator(ctx, ks)
     rng = np.random.default_rng(12)
@@ -240,12 +241,16 @@ def test_relin_rescale_is_the_rounded_division_by_p_qtop(small):
         Y = _crt(np.concatenate([yq, yp])[:, ::29], qs + ctx.p)
         O = _crt(ctx.intt(out.c[comp], lower)[:, ::29], lower)
         T = _crt(ctx.intt(two.c[comp], lower)[:, ::29], lower)
+        exact = 0
         for y, o, t in zip(Y, O, T):
-            assert ((y + Pq // 2) // Pq - o) % Ql <= ctx.K
+            e = ((y + Pq // 2) // Pq - o) % Ql
+            assert min(e, Ql - e) <= 1
+            exact += e == 0
             diff = (o - t) % Ql
-            assert min(diff, Ql - diff) <= ctx.K + 1
-    # K + 1 per coefficient in c0 and c1 is at most (K + 1)(1 + ||s||_1) per coefficient of the
-    # phase, and a slot sums N coefficients
+            assert min(diff, Ql - diff) <= 2
+        assert exact == len(Y)
+    # 2 per coefficient in c0 and c1 is at most 2 (1 + ||s||_1) per coefficient of the phase,
+    # and a slot sums N coefficients
     z = C.decrypt(ctx, ks, out)
-    assert np.abs(z - C.decrypt(ctx, ks, two)).max() < ctx.N * (ctx.K + 1) * (1 + ctx.N) / out.scale
+    assert np.abs(z - C.decrypt(ctx, ks, two)).max() < ctx.N * 2 * (1 + ctx.N) / out.scale
     assert np.abs(z - C.decrypt(ctx, ks, a) * C.decrypt(ctx, ks, b)).max() < 2 ** -20
