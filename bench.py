@@ -604,6 +604,16 @@ def run_serve(args):
         ctxs[ln] = (ctx, hs)
         keys[ln] = hx.hx_keygen(ctx, 2, 4000 + ln, steps)
     n_req = args.requests
+    # Request parameters (kind, ring, h, level) come from the seeded generator; the encrypted
+    # inputs from small pools, two per (ring, h, level) for products and per (ring, level) for
+    # signs, so that 10k requests do not hold 10k input ciphertexts on the device.
+    pools = {}
+
+    def pooled(key, make):
+        if key not in pools:
+            pools[key] = [make(j) for j in range(2)]
+        return pools[key][int(rng.integers(0, 2))]
+
     reqs = []
     for i in range(n_req):
         ln = int(rng.choice(log_ns))
@@ -613,24 +623,54 @@ def run_serve(args):
             h = int(rng.choice(hs))
             limbs = int(rng.integers(3, 21))
             beta = s // (h * h)
-            a = hx.hx_encrypt(ctx, keys[ln], workloads.pack(workloads.matrices(10 * i, beta, h), h, beta), limbs, i)
-            b = hx.hx_encrypt(ctx, keys[ln], workloads.pack(workloads.matrices(10 * i + 1, beta, h), h, beta), limbs,
-                              n_req + i)
+
+            def make(j, ctx=ctx, ln=ln, h=h, beta=beta, limbs=limbs):
+                sd = 97 * (ln * 1000 + h * 32 + limbs) + j
+                return tuple(hx.hx_encrypt(ctx, keys[ln], workloads.pack(workloads.matrices(2 * sd + e, beta, h), h,
+                                                                          beta), limbs, 2 * sd + e) for e in (0, 1))
+            a, b = pooled(("m", ln, h, limbs), make)
             reqs.append(("matmul", ln, (a, b, h), limbs))
         else:
             limbs = int(rng.integers(5, 21))
-            x = hx.hx_encrypt(ctx, keys[ln], workloads.sign_inputs(i, s), limbs, 2 * n_req + i)
+
+            def make(j, ctx=ctx, ln=ln, s=s, limbs=limbs):
+                sd = 89 * (ln * 100 + limbs) + j
+                return hx.hx_encrypt(ctx, keys[ln], workloads.sign_inputs(sd, s), limbs, sd)
+            x = pooled(("s", ln, limbs), make)
             reqs.append(("sign", ln, (x, 4, 1, 7 * i + 1), limbs))
-    # build every plan once (library masks) before timing
-    seen = set()
-    for kind, ln, a, limbs in reqs:
-        if kind == "matmul" and (ln, a[2], limbs) not in seen:
-            seen.add((ln, a[2], limbs))
-            hx.hx_ct_destroy(hx.hx_matmul(ctxs[ln][0], keys[ln], a[0], a[1], a[2]))
+    if args.full:
+        # plans (encoded masks per ring, h and level; about 200 GB for every combination) are
+        # built on first use, and past a per-ring cap the least recently used are freed: the
+        # free memory less 24 GB for the server's batches, shared in proportion to N
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        room = max(0, free0 - (24 << 30))
+        weight = sum(1 << ln for ln in log_ns)
+        for ln in log_ns:
+            hx.hx_context_set_plan_cache(ctxs[ln][0], max(1, room * (1 << ln) // weight))
+    else:
+        # build every plan once (library masks) before timing
+        seen = set()
+        for kind, ln, a, limbs in reqs:
+            if kind == "matmul" and (ln, a[2], limbs) not in seen:
+                seen.add((ln, a[2], limbs))
+                hx.hx_ct_destroy(hx.hx_matmul(ctxs[ln][0], keys[ln], a[0], a[1], a[2]))
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_setup
+    # the server counts registered keys against its budget: give it the free memory (less what
+    # the capped plan caches may still take, and a margin) plus the keys already resident
+    probe = hx.hx_server_create(1 << 62, 1, 1)
+    for ln in log_ns:
+        hx.hx_server_register_keys(probe, keys[ln])
+    key_bytes = hx.hx_server_stats(probe)["key_bytes"]
+    hx.hx_server_destroy(probe)
     free, total = torch.cuda.mem_get_info()
-    budget = int(free * 0.85)
+    plan_room = 0
+    if args.full:
+        for ln in log_ns:
+            info = hx.hx_context_plan_cache_info(ctxs[ln][0])
+            plan_room += max(0, info["cap"] - info["bytes"])
+    budget = int(max(0, free - plan_room) * 0.9) + key_bytes
     sv = hx.hx_server_create(budget, args.lanes, args.max_batch)
     for ln in log_ns:
         hx.hx_server_register_keys(sv, keys[ln])
@@ -706,16 +746,24 @@ def run_serve(args):
             "unit": "ms", "higher_is_better": False, "throughput_req_s": round(len(L) / elapsed, 2),
             "offered_req_s": round(rate, 2), "capacity_req_s": round(capacity, 2), "requests": len(L),
             "n_gpus": 1, "dtype": "u64", "data": "synthetic",
-            "config": {"workload": "Poisson arrivals at %.1fx closed-loop capacity; 50%% matmul h in {16,32,64} "
+            "config": {"workload": "Poisson arrivals at %.1fx closed-loop capacity; 50%% matmul h in %s "
                                    "(feasible per ring), 50%% sign g_4 (k=1); N in %s; Q=60+19x40, P=3x60 bit; "
-                                   "matmul limbs U{3..20}, sign limbs U{5..20}" % (args.load, [2 ** l for l in log_ns]),
+                                   "matmul limbs U{3..20}, sign limbs U{5..20}"
+                                   % (args.load, sorted({h for ln in log_ns for h in ctxs[ln][1]}),
+                                      [2 ** l for l in log_ns]),
+                       "inputs": "two seeded ciphertexts (pairs) per (ring, h, level) and per (ring, level) for "
+                                 "signs, drawn per request",
+                       "plans": ("built on first use, least recently used freed past a per-ring cap (free memory "
+                                 "less 24 GB, in proportion to N)" if args.full else "all built before timing"),
                        "lanes": args.lanes, "max_batch": args.max_batch, "hbm_budget_bytes": budget,
                        "setup_s": round(setup_s, 1)},
-            "server": stats, "clocks": clocks, "load_sweep": sweep}
+            "server": stats, "clocks": clocks, "load_sweep": sweep,
+            "plan_cache": {str(2 ** ln): hx.hx_context_plan_cache_info(ctxs[ln][0]) for ln in log_ns}}
     print(json.dumps(line), flush=True)
-    for kind, ln, a, _ in reqs:
-        for h in (a[:2] if kind == "matmul" else a[:1]):
-            hx.hx_ct_destroy(h)
+    for entries in pools.values():
+        for e in entries:
+            for h in (e if isinstance(e, tuple) else (e,)):
+                hx.hx_ct_destroy(h)
     for ln in log_ns:
         hx.hx_keyset_destroy(keys[ln])
         hx.hx_context_destroy(ctxs[ln][0])

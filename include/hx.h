@@ -232,6 +232,17 @@ hx_status hx_ntt_multi(const hx_ntt_job *jobs, int n_jobs, int inverse, void *st
 hx_status hx_ntt(hx_context *ctx, uint64_t *dev, int n_polys, int limbs, const int32_t *prime_idx, int inverse,
                  void *stream);
 
+/* The cached HE-MatMult and transpose plans (encoded masks, one per (h, level))
+ * that hx_matmul, the batch calls without a plan, the dense layer and the
+ * server build on first use.  bytes > 0 caps the device memory they hold: past
+ * it the least recently used plans that no call is using are freed (a call
+ * keeps its plan until its stream has run the work that reads it; plans used
+ * inside a stream capture stay for the context's life); 0 = no cap (the
+ * default).  Info: plans, bytes held, cap (0 = none), plans freed so far;
+ * returns the count (4). */
+hx_status hx_context_set_plan_cache(hx_context *ctx, uint64_t bytes);
+int hx_context_plan_cache_info(hx_context *ctx, uint64_t *out, int cap);
+
 /* ---- HE-MatMult (Alg. 3 with App. B and App. E) ----------------------------- */
 /* A plan fixes h (a power of two, h*h <= N/2, beta = (N/2)/h^2 products per
  * ciphertext pair) and the input level.  limbs >= 4 runs Alg. 3; limbs == 3

@@ -600,14 +600,35 @@ int hx_matmul_rotation_steps(const hx_context *ctx, int h, int limbs, int32_t *o
     return (int)st.size();
 }
 
+hx_status hx_context_set_plan_cache(hx_context *ctx, uint64_t bytes)
+{
+    HX_TRY
+    need(ctx, "null argument");
+    std::lock_guard<std::mutex> lk(ctx->plan_mu);
+    ctx->plan_limit = bytes ? (size_t)bytes : SIZE_MAX;
+    trim_plan_cache(*ctx);
+    return HX_OK;
+    HX_END
+}
+
+int hx_context_plan_cache_info(hx_context *ctx, uint64_t *out, int cap)
+{
+    if (!ctx || (!out && cap > 0)) return HX_EINVAL;
+    std::lock_guard<std::mutex> lk(ctx->plan_mu);
+    const uint64_t v[4] = {(uint64_t)ctx->plans.size(), (uint64_t)ctx->plan_bytes,
+                           ctx->plan_limit == SIZE_MAX ? 0 : (uint64_t)ctx->plan_limit, ctx->plan_evictions};
+    for (int i = 0; i < 4 && i < cap; i++) out[i] = v[i];
+    return 4;
+}
+
 hx_status hx_matmul(hx_context *ctx, const hx_keyset *ks, const hx_ct *A, const hx_ct *B, int h, hx_ct **out,
                     void *stream)
 {
     HX_TRY
     need(ctx && ks && A && B && out, "null argument");
     *out = nullptr;
-    const hx_matmul_plan *p = cached_plan(*ctx, h, A->c.limbs);
-    *out = wrap(ctx, matmul_batch(*ctx, *ks, *p, A->c, B->c, S(stream)));
+    PlanUse p(*ctx, S(stream), cached_plan(*ctx, h, A->c.limbs));
+    *out = wrap(ctx, matmul_batch(*ctx, *ks, *p.p, A->c, B->c, S(stream)));
     return HX_OK;
     HX_END
 }
@@ -621,7 +642,8 @@ hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_
     need(count < 4096, "batch too large");
     Cts a = gather(*ctx, A, count, S(stream));
     Cts b = gather(*ctx, B, count, S(stream));
-    const hx_matmul_plan *p = plan ? plan : cached_plan(*ctx, h, a.limbs);
+    PlanUse held(*ctx, S(stream), plan ? nullptr : cached_plan(*ctx, h, a.limbs));
+    const hx_matmul_plan *p = plan ? plan : held.p.get();
     need(p->h == h && p->kind == 0, "plan built for another h");
     Cts r = matmul_batch(*ctx, *ks, *p, a, b, S(stream));
     scatter(*ctx, r, out, S(stream));
@@ -646,7 +668,8 @@ hx_status hx_rmatmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul
     for (size_t i = 0; i < count; i++) out[i] = nullptr;
     Cts a = gather(*ctx, At, count, S(stream));
     Cts b = gather(*ctx, B, count, S(stream));
-    const hx_matmul_plan *p = plan ? plan : cached_plan(*ctx, h, a.limbs);
+    PlanUse held(*ctx, S(stream), plan ? nullptr : cached_plan(*ctx, h, a.limbs));
+    const hx_matmul_plan *p = plan ? plan : held.p.get();
     need(p->h == h && p->kind == 0, "plan built for another h");
     scatter(*ctx, rmatmul_batch(*ctx, *ks, *p, a, b, t, S(stream)), out, S(stream));
     return HX_OK;
@@ -678,7 +701,8 @@ hx_status hx_transpose(hx_context *ctx, const hx_keyset *ks, const hx_matmul_pla
     need(ctx && ks && x && out && count >= 1 && count < 4096, "bad argument");
     for (size_t i = 0; i < count; i++) out[i] = nullptr;
     Cts a = gather(*ctx, x, count, S(stream));
-    const hx_matmul_plan *p = plan ? plan : cached_transpose_plan(*ctx, h, a.limbs);
+    PlanUse held(*ctx, S(stream), plan ? nullptr : cached_transpose_plan(*ctx, h, a.limbs));
+    const hx_matmul_plan *p = plan ? plan : held.p.get();
     need(p->h == h && p->kind == 1, "plan built for another shape");
     scatter(*ctx, transpose_batch(*ctx, *ks, *p, a, S(stream)), out, S(stream));
     return HX_OK;

@@ -307,9 +307,13 @@ SideStream &side_stream(hx_context &ctx, cudaStream_t main)
 
 void destroy_context(hx_context &c)
 {
-    for (auto &kv : c.plans) delete kv.second;
-    c.plans.clear();
     cudaDeviceSynchronize();
+    c.plans.clear();
+    c.plans_pinned.clear();
+    if (c.plan_stream) {
+        cudaStreamSynchronize(c.plan_stream);
+        cudaStreamDestroy(c.plan_stream);
+    }
     for (auto &kv : c.side) {
         for (auto &e : kv.second.e)
             if (e) cudaEventDestroy(e);

@@ -2,6 +2,7 @@
 #pragma once
 #include <map>
 #include <tuple>
+#include <cstdint>
 #include <memory>
 #include <mutex>
 #include <vector>
@@ -73,8 +74,19 @@ struct hx_context {
     std::unique_ptr<hx::Encoder> enc;
     std::unique_ptr<hx::GaussianCdt> cdt;
     std::atomic<uint64_t> counters[hx::C_NUM] = {};
-    std::mutex plan_mu;  // guards `plans`
-    std::map<std::tuple<int, int, int>, hx_matmul_plan *> plans;  // (kind, h, limbs)
+    // cached plans by (kind, h, limbs), shared with the calls that use them; beyond
+    // plan_limit bytes the least recently used plans that no call holds are freed
+    struct PlanEntry {
+        std::shared_ptr<hx_matmul_plan> p;
+        uint64_t last = 0;
+        size_t bytes = 0;
+    };
+    std::mutex plan_mu;  // guards the fields below
+    std::map<std::tuple<int, int, int>, PlanEntry> plans;
+    size_t plan_limit = SIZE_MAX, plan_bytes = 0;
+    uint64_t plan_tick = 0, plan_evictions = 0;
+    cudaStream_t plan_stream = nullptr;  // builds cached plans; their masks are freed in its order
+    std::vector<std::shared_ptr<const hx_matmul_plan>> plans_pinned;  // used inside a stream capture
     int device = 0;
     hx::Profiler prof;
     bool profiling = false;
@@ -214,9 +226,23 @@ Cts dbootstrap(hx_context &ctx, const hx_keyset &ks, const Cts &ct, const std::v
 // ---- schedules (schedules.cu) -------------------------------------------------
 hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s);
 // the context's plan for (h, limbs) with library masks, built on first use (thread-safe)
-const hx_matmul_plan *cached_plan(hx_context &ctx, int h, int limbs);
+std::shared_ptr<const hx_matmul_plan> cached_plan(hx_context &ctx, int h, int limbs);
+void trim_plan_cache(hx_context &ctx);  // caller holds plan_mu
+// keeps a cached plan referenced until stream s has run the work enqueued so far
+// (does not throw; on failure it waits for s)
+void hold_plan_until(hx_context &ctx, cudaStream_t s, std::shared_ptr<const hx_matmul_plan> p) noexcept;
+// a cached plan for one call on stream s, held past the call's work however the call ends
+struct PlanUse {
+    hx_context &ctx;
+    cudaStream_t s;
+    std::shared_ptr<const hx_matmul_plan> p;
+    PlanUse(hx_context &c, cudaStream_t st, std::shared_ptr<const hx_matmul_plan> q) : ctx(c), s(st), p(std::move(q)) {}
+    ~PlanUse() { hold_plan_until(ctx, s, std::move(p)); }
+    PlanUse(const PlanUse &) = delete;
+    PlanUse &operator=(const PlanUse &) = delete;
+};
 hx_matmul_plan *make_transpose_plan(hx_context &ctx, int h, int limbs, cudaStream_t s);
-const hx_matmul_plan *cached_transpose_plan(hx_context &ctx, int h, int limbs);
+std::shared_ptr<const hx_matmul_plan> cached_transpose_plan(hx_context &ctx, int h, int limbs);
 std::vector<int64_t> transpose_rotation_steps(int h, int beta);
 Cts transpose_batch(hx_context &ctx, const hx_keyset &ks, const hx_matmul_plan &plan, const Cts &x, cudaStream_t s);
 std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs, int t = 0);  // t = 0: t = h

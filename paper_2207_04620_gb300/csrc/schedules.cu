@@ -203,15 +203,92 @@ hx_matmul_plan *make_transpose_plan(hx_context &ctx, int h, int limbs, cudaStrea
     return p.release();
 }
 
-const hx_matmul_plan *cached_transpose_plan(hx_context &ctx, int h, int limbs)
+namespace {
+
+size_t plan_device_bytes(const hx_matmul_plan &p)
 {
+    size_t b = 0;
+    for (const auto &m : p.masks)
+        if (m.pt) b += m.pt->words * sizeof(uint64_t);
+    return b;
+}
+
+// the cached plan of (kind, h, limbs), built on first use (outside the lock, on the
+// context's plan stream); the cache may then drop least recently used plans no call holds
+std::shared_ptr<const hx_matmul_plan> cached(hx_context &ctx, int kind, int h, int limbs)
+{
+    const auto key = std::make_tuple(kind, h, limbs);
+    cudaStream_t ps;
+    {
+        std::lock_guard<std::mutex> lk(ctx.plan_mu);
+        auto it = ctx.plans.find(key);
+        if (it != ctx.plans.end()) {
+            it->second.last = ++ctx.plan_tick;
+            return it->second.p;
+        }
+        if (!ctx.plan_stream) HX_CUDA(cudaStreamCreateWithFlags(&ctx.plan_stream, cudaStreamNonBlocking));
+        ps = ctx.plan_stream;
+    }
+    std::shared_ptr<hx_matmul_plan> built(kind == 0 ? make_plan(ctx, h, limbs, ps)
+                                                    : make_transpose_plan(ctx, h, limbs, ps));
     std::lock_guard<std::mutex> lk(ctx.plan_mu);
-    auto key = std::make_tuple(1, h, limbs);
     auto it = ctx.plans.find(key);
-    if (it != ctx.plans.end()) return it->second;
-    hx_matmul_plan *p = make_transpose_plan(ctx, h, limbs, nullptr);
-    ctx.plans[key] = p;
-    return p;
+    if (it == ctx.plans.end()) {  // else another call built it meanwhile: keep that one
+        hx_context::PlanEntry e;
+        e.p = std::move(built);
+        e.bytes = plan_device_bytes(*e.p);
+        ctx.plan_bytes += e.bytes;
+        it = ctx.plans.emplace(key, std::move(e)).first;
+    }
+    it->second.last = ++ctx.plan_tick;
+    std::shared_ptr<const hx_matmul_plan> held = it->second.p;  // not evictable while returned
+    trim_plan_cache(ctx);
+    return held;
+}
+
+void release_plan(void *p) { delete static_cast<std::shared_ptr<const hx_matmul_plan> *>(p); }
+
+} // namespace
+
+void hold_plan_until(hx_context &ctx, cudaStream_t s, std::shared_ptr<const hx_matmul_plan> p) noexcept
+{
+    if (!p) return;
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();  // a captured graph may replay the work at any time: keep the plan
+        std::lock_guard<std::mutex> lk(ctx.plan_mu);
+        ctx.plans_pinned.push_back(std::move(p));
+        return;
+    }
+    // the reference is dropped by a host function once s reaches this point; it is never
+    // the last one (the cache frees only plans it alone holds), so no CUDA call runs there
+    auto *ref = new std::shared_ptr<const hx_matmul_plan>(std::move(p));
+    if (cudaLaunchHostFunc(s, release_plan, ref) != cudaSuccess) {
+        cudaGetLastError();
+        cudaStreamSynchronize(s);
+        delete ref;
+    }
+}
+
+void trim_plan_cache(hx_context &ctx)
+{
+    while (ctx.plan_bytes > ctx.plan_limit) {
+        auto victim = ctx.plans.end();
+        for (auto it = ctx.plans.begin(); it != ctx.plans.end(); ++it)
+            if (it->second.p.use_count() == 1 && (victim == ctx.plans.end() || it->second.last < victim->second.last))
+                victim = it;
+        if (victim == ctx.plans.end()) return;  // everything left is in use
+        // no call holds it and every stream that used it has passed that work (calls hold
+        // their plan until then), so its masks go back to the pool in the plan stream's order
+        ctx.plan_bytes -= victim->second.bytes;
+        ctx.plans.erase(victim);
+        ctx.plan_evictions++;
+    }
+}
+
+std::shared_ptr<const hx_matmul_plan> cached_transpose_plan(hx_context &ctx, int h, int limbs)
+{
+    return cached(ctx, 1, h, limbs);
 }
 
 std::vector<int64_t> transpose_rotation_steps(int h, int beta)
@@ -229,15 +306,9 @@ std::vector<int64_t> transpose_rotation_steps(int h, int beta)
     return out;
 }
 
-const hx_matmul_plan *cached_plan(hx_context &ctx, int h, int limbs)
+std::shared_ptr<const hx_matmul_plan> cached_plan(hx_context &ctx, int h, int limbs)
 {
-    std::lock_guard<std::mutex> lk(ctx.plan_mu);
-    auto key = std::make_tuple(0, h, limbs);
-    auto it = ctx.plans.find(key);
-    if (it != ctx.plans.end()) return it->second;
-    hx_matmul_plan *p = make_plan(ctx, h, limbs, nullptr);
-    ctx.plans[key] = p;
-    return p;
+    return cached(ctx, 0, h, limbs);
 }
 
 namespace {
@@ -653,7 +724,8 @@ DenseResult dense_batch(hx_context &ctx, const hx_keyset &ks, const DensePlans &
     const int beta = (int)(S / ((int64_t)h * h));
     Eval ev(ctx, s);
     // feedforward: every block product in one batched HE-MatMult
-    const hx_matmul_plan *pf = plans.fwd ? plans.fwd : cached_plan(ctx, h, W.limbs);
+    PlanUse pf_held(ctx, s, plans.fwd ? nullptr : cached_plan(ctx, h, W.limbs));
+    const hx_matmul_plan *pf = plans.fwd ? plans.fwd : pf_held.p.get();
     HX_CHECK(pf->h == h, HX_EINVAL, "feedforward plan built for another h");
     Cts P = matmul_batch(ctx, ks, *pf, W, repeat_each(ev, X, n_out), s);
     Cts E = ev.copy(slice(ctx, P, 0, n_out));
@@ -675,12 +747,14 @@ DenseResult dense_batch(hx_context &ctx, const hx_keyset &ks, const DensePlans &
     Cts L = square_rs(ev, ks, s1, ev.drop(G, s1.limbs));
     L.scale *= 2;
     for (int t = 1; t < beta; t *= 2) L = ev.add(L, ev.rotate(L, S - t, ks));
-    const hx_matmul_plan *pt = plans.transpose ? plans.transpose : cached_transpose_plan(ctx, h, X.limbs);
+    PlanUse pt_held(ctx, s, plans.transpose ? nullptr : cached_transpose_plan(ctx, h, X.limbs));
+    const hx_matmul_plan *pt = plans.transpose ? plans.transpose : pt_held.p.get();
     HX_CHECK(pt->h == h, HX_EINVAL, "transpose plan built for another h");
     Cts XT = transpose_batch(ctx, ks, *pt, X, s);
     HX_CHECK(XT.limbs > L.limbs, HX_ELEVEL, "transposed inputs below the gradient's level");
     Cts XTa = level_adjust(ev, XT, L.limbs, 1.0, L.scale);
-    const hx_matmul_plan *pb = plans.bwd ? plans.bwd : cached_plan(ctx, h, L.limbs);
+    PlanUse pb_held(ctx, s, plans.bwd ? nullptr : cached_plan(ctx, h, L.limbs));
+    const hx_matmul_plan *pb = plans.bwd ? plans.bwd : pb_held.p.get();
     HX_CHECK(pb->h == h, HX_EINVAL, "backpropagation plan built for another h");
     r.dW = matmul_batch(ctx, ks, *pb, repeat_block(ev, L, groups), repeat_each(ev, XTa, n_out), s);
     return r;

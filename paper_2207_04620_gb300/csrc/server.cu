@@ -184,6 +184,7 @@ void hx_server::run_lane(Lane &L)
         hx_context &ctx = *r0.ctx;
         int status = HX_OK;
         Cts out;
+        std::shared_ptr<const hx_matmul_plan> plan;
         try {
             Eval ev(ctx, L.s);
             const int B = (int)batch.size();
@@ -200,7 +201,8 @@ void hx_server::run_lane(Lane &L)
                 Cts Bc = ev.alloc(B, 2, r0.b.limbs);
                 Bc.scale = r0.b.scale;
                 for (int i = 0; i < B; i++) pack(Bc, i, batch[i].b);
-                out = matmul_batch(ctx, *r0.ks, *cached_plan(ctx, r0.h, r0.a.limbs), A, Bc, L.s);
+                plan = cached_plan(ctx, r0.h, r0.a.limbs);  // held until the lane's stream is done
+                out = matmul_batch(ctx, *r0.ks, *plan, A, Bc, L.s);
             } else {
                 std::vector<uint64_t> seeds;
                 for (auto &r : batch) seeds.push_back(r.seed);
@@ -213,6 +215,7 @@ void hx_server::run_lane(Lane &L)
             cudaStreamSynchronize(L.s);
         }
         const auto t1 = Clock::now();
+        plan.reset();
         lk.lock();
         for (size_t i = 0; i < batch.size(); i++) {
             Done d;
@@ -274,7 +277,7 @@ hx_status hx_server_register_keys(hx_server *sv, const hx_keyset *ks)
     for (auto *k : sv->registered)
         if (k == ks) return HX_OK;
     const size_t kb = key_bytes(*ks);
-    if (sv->keys + kb > sv->budget) {
+    if (kb > sv->budget) {  // the budget is already net of the keys registered before
         set_error("resident keys exceed the HBM budget");
         return HX_ENOMEM;
     }

@@ -109,6 +109,8 @@ _SIGS = {
     "hx_aggregate": (c_int, [c_vp, PP, c_size_t, PP, c_size_t, c_double, PP, c_vp]),
     "hx_dkeyswitch": (c_int, [c_vp, c_vp, c_vp, c_vp, c_u64, PP, c_vp]),
     "hx_dbootstrap": (c_int, [c_vp, c_vp, c_vp, c_u64, PP, c_vp]),
+    "hx_context_set_plan_cache": (c_int, [c_vp, c_u64]),
+    "hx_context_plan_cache_info": (c_int, [c_vp, P_u64, c_int]),
     "hx_server_create": (c_int, [c_size_t, c_int, c_int, PP]),
     "hx_server_register_keys": (c_int, [c_vp, c_vp]),
     "hx_server_submit_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_int, P_u64]),
@@ -461,6 +463,16 @@ def hx_matmul_rotation_steps(ctx: int, h: int, limbs: int) -> list:
     buf = np.zeros(4096, dtype=np.int32)
     n = _chk(lib().hx_matmul_rotation_steps(ctx, h, limbs, buf.ctypes.data_as(P_i32), buf.size))
     return [int(x) for x in buf[:n]]
+
+
+def hx_context_set_plan_cache(ctx: int, bytes_cap: int) -> None:
+    _chk(lib().hx_context_set_plan_cache(ctx, int(bytes_cap)))
+
+
+def hx_context_plan_cache_info(ctx: int) -> dict:
+    buf = np.zeros(4, dtype=np.uint64)
+    _chk(lib().hx_context_plan_cache_info(ctx, _u64p(buf), 4))
+    return {"plans": int(buf[0]), "bytes": int(buf[1]), "cap": int(buf[2]), "evicted": int(buf[3])}
 
 
 def hx_matmul(ctx, ks, A, B, h, stream=None) -> int:

@@ -141,3 +141,54 @@ def test_deadline_expires_queued_requests_only(setup):
     hx.hx_server_destroy(sv)
     for x in (a, b, alone, got[kept][0]):
         hx.hx_ct_destroy(x)
+
+
+def test_plan_cache_cap_frees_unused_plans(setup):
+    """With a 1-byte cap every cached plan but the one in use is freed after each
+    call; products stay identical to the uncapped ones, also through the server."""
+    ctx, ks, s = setup
+    reqs = [r for r in _requests(ctx, ks, s) if r[0] == "matmul"]
+    want = [hx.hx_ct_export(ctx, hx.hx_matmul(ctx, ks, *args)) for _, args in reqs]
+    assert hx.hx_context_plan_cache_info(ctx)["plans"] >= 3
+    hx.hx_context_set_plan_cache(ctx, 1)
+    info = hx.hx_context_plan_cache_info(ctx)
+    assert info["plans"] == 0 and info["bytes"] == 0 and info["cap"] == 1
+    for (kind, args), w in zip(reqs, want):
+        assert np.array_equal(hx.hx_ct_export(ctx, hx.hx_matmul(ctx, ks, *args)), w)
+        assert hx.hx_context_plan_cache_info(ctx)["plans"] <= 1
+    sv = hx.hx_server_create(64 << 30, 3, 4)
+    ids = [_submit(sv, ctx, ks, kind, args) for kind, args in reqs]
+    got = _collect(sv, len(ids))
+    hx.hx_server_destroy(sv)
+    for rid, w in zip(ids, want):
+        assert got[rid][1] == 0 and np.array_equal(hx.hx_ct_export(ctx, got[rid][0]), w)
+    assert hx.hx_context_plan_cache_info(ctx)["evicted"] >= len(reqs)
+    hx.hx_context_set_plan_cache(ctx, 0)
+
+
+def test_resident_keys_count_once_against_the_budget(setup):
+    ctx, ks, s = setup
+    ks2 = hx.hx_keygen(ctx, 2, 33, [1, 2])
+
+    def key_bytes(k):
+        probe = hx.hx_server_create(1 << 40, 1, 1)
+        hx.hx_server_register_keys(probe, k)
+        b = hx.hx_server_stats(probe)["key_bytes"]
+        hx.hx_server_destroy(probe)
+        return b
+
+    kb1, kb2 = key_bytes(ks), key_bytes(ks2)
+    sv = hx.hx_server_create(kb1 + kb2, 1, 1)       # exactly the two keysets
+    hx.hx_server_register_keys(sv, ks)
+    hx.hx_server_register_keys(sv, ks2)
+    hx.hx_server_register_keys(sv, ks)              # registering again counts nothing
+    st = hx.hx_server_stats(sv)
+    assert st["key_bytes"] == kb1 + kb2 and st["budget_left"] == 0
+    hx.hx_server_destroy(sv)
+    sv = hx.hx_server_create(kb1 + kb2 - 1, 1, 1)
+    hx.hx_server_register_keys(sv, ks)
+    with pytest.raises(hx.HxError) as e:
+        hx.hx_server_register_keys(sv, ks2)
+    assert e.value.code == -2
+    hx.hx_server_destroy(sv)
+    hx.hx_keyset_destroy(ks2)
