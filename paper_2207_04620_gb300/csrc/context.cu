@@ -30,7 +30,7 @@ DevBuf::DevBuf(size_t w, bool) : words(w), pooled(false)
 
 DevBuf::~DevBuf()
 {
-    if (!p) return;
+    if (!p || !owned) return;
     if (pooled)
         cudaFreeAsync(p, stream);
     else

@@ -190,6 +190,8 @@ void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const
 void alu_calibrate(const LaunchCtx &c, uint64_t q, double *shoup_per_s, double *mac_per_s);
 void launch_moddown_final_mux(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
                               int limbs, View src, const uint64_t *v, const Scalars &cs, uint64_t g1, uint64_t g2);
+// slots[r*S + t*beta + j] = bits[r*hh + t] for j < beta (masks expanded over the packed matrices)
+void launch_expand_masks(const LaunchCtx &c, double *slots, const uint8_t *bits, int m, int hh, int beta, size_t S);
 void launch_relin_rs_top(const LaunchCtx &c, View acc, View d, const RelinRescaleTable *tab, int B, int limbs);
 void launch_relin_rs_final(const LaunchCtx &c, View out, View acc, View d, View conv, const RelinRescaleTable *tab,
                            int B, int limbs);

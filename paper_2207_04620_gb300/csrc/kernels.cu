@@ -671,6 +671,13 @@ __global__ void k_relin_rs_final(View out, View acc, View d, View conv, const Re
     }
 }
 
+__global__ void k_expand_masks(double *slots, const uint8_t *__restrict__ bits, int hh, int beta, size_t S)
+{
+    const int r = blockIdx.y;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < S; i += (size_t)gridDim.x * blockDim.x)
+        slots[(size_t)r * S + i] = (double)bits[(size_t)r * hh + i / beta];
+}
+
 // b = e - a*s + gad_r * s'  (all NTT form, row r modulo prime r); optionally
 // b and a are left in Montgomery form for the key inner product.
 __global__ void k_keygen_b(uint64_t *b, uint64_t *a, const uint64_t *e, const uint64_t *s, const uint64_t *sp,
@@ -956,6 +963,14 @@ void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, con
     Timed tm_(c, K_MODDOWN, 8.0 * B * 2 * limbs * c.N * ((add_mask ? 4.0 : 3.0)));
     dim3 grid(ew_blocks(c.N, 2), limbs, B * 2);
     k_moddown_final<<<grid, 256, 0, c.stream>>>(out, acc, conv, tab, c.t->primes, add, add_mask, g, c.log_n);
+    post(c);
+}
+
+void launch_expand_masks(const LaunchCtx &c, double *slots, const uint8_t *bits, int m, int hh, int beta, size_t S)
+{
+    HX_CHECK(m >= 1 && m < 65536 && (size_t)hh * beta == S, HX_EINVAL, "bad mask expansion");
+    dim3 grid((unsigned)std::min<size_t>((S + 255) / 256, 4096), m, 1);
+    k_expand_masks<<<grid, 256, 0, c.stream>>>(slots, bits, hh, beta, S);
     post(c);
 }
 

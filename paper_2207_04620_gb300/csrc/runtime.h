@@ -20,8 +20,10 @@ struct DevBuf {
     size_t words = 0;
     cudaStream_t stream = nullptr;
     bool pooled = true;  // false: plain cudaMalloc (outlives graph captures)
+    bool owned = true;   // false: a view into a buffer someone else keeps alive
     DevBuf(size_t w, cudaStream_t s);
     DevBuf(size_t w, bool persistent);
+    DevBuf(uint64_t *view, size_t w) : p(view), words(w), pooled(false), owned(false) {}
     ~DevBuf();
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
@@ -147,6 +149,7 @@ struct hx_matmul_plan {
     // premasked[k] = [2][ndig][2][ext][N], v_k * swk(k) and (c - v_k) * swk(k-h)
     uint64_t bound_uid = 0;
     std::vector<hx::BufPtr> premasked;
+    std::vector<hx::BufPtr> storage;  // batched mask buffers the masks' views point into
 };
 
 namespace hx {

@@ -10,6 +10,8 @@
 
 #include <set>
 
+#include <tuple>
+
 #include "runtime.h"
 
 namespace hx {
@@ -144,35 +146,56 @@ hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
     return p.release();
 }
 
+static std::vector<int> iota_rows(int n)
+{
+    std::vector<int> v(n);
+    for (int i = 0; i < n; i++) v[i] = i;
+    return v;
+}
+
 void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s)
 {
     hx_matmul_plan *p = &pl;
-    const int h = p->h;
-    const size_t S = (size_t)ctx.N / 2;
-    // every mask expanded over the beta packed matrices, encoded by the device encoder (the same
-    // coefficients as the host encoder) in one batch per mask scale, then moved to NTT and
-    // Montgomery form on the device
-    std::map<double, std::vector<int>> by_scale;
-    for (int i = 0; i < (int)p->masks.size(); i++) by_scale[p->masks[i].scale].push_back(i);
-    for (auto &grp : by_scale) {
+    const int hh = p->h * p->h;
+    const size_t S = (size_t)ctx.N / 2, N = ctx.N;
+    Eval ev(ctx, s);
+    // masks of one scale and basis form a group: their 0/1 vectors (one byte per matrix entry)
+    // go up once, are expanded over the beta packed matrices on the device, encoded by the
+    // device encoder (the same coefficients as the host encoder) and moved to NTT and Montgomery
+    // form in one batch; every mask is a view into the group's buffer
+    std::map<std::tuple<double, int, bool>, std::vector<int>> groups;
+    for (int i = 0; i < (int)p->masks.size(); i++) {
+        const auto &m = p->masks[i];
+        groups[std::make_tuple(m.scale, m.limbs, m.extended)].push_back(i);
+    }
+    for (auto &grp : groups) {
         const std::vector<int> &ids = grp.second;
-        std::vector<double> slots(ids.size() * S);
-        for (size_t r = 0; r < ids.size(); r++) {
-            const auto &m = p->masks[ids[r]];
-            for (int t = 0; t < h * h; t++)
-                for (int j = 0; j < p->beta; j++) slots[r * S + (size_t)t * p->beta + j] = m.vec[t];
-        }
-        DevBuf dslots(slots.size(), s), dco(ids.size() * ctx.N, s);
-        HX_CUDA(cudaMemcpyAsync(dslots.p, slots.data(), sizeof(double) * slots.size(), cudaMemcpyHostToDevice, s));
+        const int M = (int)ids.size(), limbs = std::get<1>(grp.first);
+        const bool ext = std::get<2>(grp.first);
+        const int rows = ext ? limbs + ctx.K : limbs;
+        std::vector<uint8_t> bits((size_t)M * hh);
+        for (int r = 0; r < M; r++)
+            for (int t = 0; t < hh; t++) bits[(size_t)r * hh + t] = p->masks[ids[r]].vec[t] != 0;
+        std::vector<int> pr(rows), prM((size_t)M * rows);
+        for (int t = 0; t < rows; t++) pr[t] = t < limbs ? t : ctx.n_q + (t - limbs);
+        for (int r = 0; r < M; r++) std::copy(pr.begin(), pr.end(), prM.begin() + (size_t)r * rows);
+        DevBuf dbits((bits.size() + 7) / 8, s), dpr((prM.size() + 1) / 2, s);
+        HX_CUDA(cudaMemcpyAsync(dbits.p, bits.data(), bits.size(), cudaMemcpyHostToDevice, s));
+        HX_CUDA(cudaMemcpyAsync(dpr.p, prM.data(), sizeof(int) * prM.size(), cudaMemcpyHostToDevice, s));
+        DevBuf dslots((size_t)M * S, s), dco((size_t)M * N, s);
+        launch_expand_masks(ev.lc(), reinterpret_cast<double *>(dslots.p), reinterpret_cast<const uint8_t *>(dbits.p),
+                            M, hh, p->beta, S);
         int64_t *co = reinterpret_cast<int64_t *>(dco.p);
-        encode_batch(ctx, reinterpret_cast<const double *>(dslots.p), S, (int)ids.size(), grp.first, co, ctx.N, s);
-        for (size_t r = 0; r < ids.size(); r++) {
-            auto &m = p->masks[ids[r]];
-            const int rows = m.extended ? m.limbs + ctx.K : m.limbs;
-            m.pt = std::make_shared<DevBuf>((size_t)rows * ctx.N, s);
-            plaintext_from_device(ctx, s, co + r * ctx.N, m.limbs, m.extended, m.pt->p);
-        }
-        HX_CUDA(cudaStreamSynchronize(s));  // the host slot staging goes out of scope
+        encode_batch(ctx, reinterpret_cast<const double *>(dslots.p), S, M, std::get<0>(grp.first), co, N, s);
+        BufPtr G = std::make_shared<DevBuf>((size_t)M * rows * N, s);
+        const int *idp = reinterpret_cast<const int *>(dpr.p);
+        launch_signed_to_rows(ev.lc(), G->p, co, rows, M, N, idp);
+        ev.ntt_inplace(G->p, (size_t)rows * N, M, iota_rows(rows), pr, false);
+        launch_to_mont(ev.lc(), G->p, M * rows, idp);
+        for (int r = 0; r < M; r++)
+            p->masks[ids[r]].pt = std::make_shared<DevBuf>(G->p + (size_t)r * rows * N, (size_t)rows * N);
+        p->storage.push_back(G);
+        HX_CUDA(cudaStreamSynchronize(s));  // the staging buffers are released at the end of the group
     }
 }
 
@@ -208,8 +231,9 @@ namespace {
 size_t plan_device_bytes(const hx_matmul_plan &p)
 {
     size_t b = 0;
+    for (const auto &g : p.storage) b += g->words * sizeof(uint64_t);
     for (const auto &m : p.masks)
-        if (m.pt) b += m.pt->words * sizeof(uint64_t);
+        if (m.pt && m.pt->owned) b += m.pt->words * sizeof(uint64_t);
     return b;
 }
 
