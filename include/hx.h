@@ -100,6 +100,14 @@ int64_t hx_keyset_export_switch_key(const hx_keyset *ks, uint64_t galois, uint64
 /* Exports the public key [2 (b, a)][n_q][N]. */
 int64_t hx_keyset_export_public_key(const hx_keyset *ks, uint64_t *host, size_t cap);
 void hx_keyset_destroy(hx_keyset *ks);
+/* Keyset checkpoint: keys are a deterministic function of (seed, parties,
+ * Galois elements), so the file holds that recipe: "HXKS0001", u32 log_n,
+ * n_q, n_p, n_parties, u64 seed, u32 n_galois, 0, the u64 moduli of Q then P,
+ * the u64 Galois elements of the rotation keys ascending, little-endian.
+ * Loading checks the magic, ring, chain and moduli against the context and
+ * regenerates the same keys (HX_EINVAL for a file of another context). */
+hx_status hx_keyset_save(hx_context *ctx, const hx_keyset *ks, const char *path);
+hx_status hx_keyset_load(hx_context *ctx, const char *path, hx_keyset **out);
 
 /* ---- encoding / encryption / decryption (Fig. 1 items 3-6) ---------------- */
 /* Ecd: n <= N/2 real slots -> N signed integer coefficients at `scale`

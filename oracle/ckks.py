@@ -645,6 +645,45 @@ def load_ciphertext(path: str, ctx: Context) -> Ciphertext:
     return Ciphertext(c.reshape(int(comps), int(limbs), ctx.N), scale)
 
 
+# Keyset recipe (little-endian): b"HXKS0001"; u32 log_n, n_q, n_p, n_parties; u64 seed;
+# u32 number of Galois keys, 0; u64 moduli of Q then P; u64 Galois elements ascending.
+# Keys are a deterministic function of (seed, parties, Galois elements).
+
+KS_MAGIC = b"HXKS0001"
+
+
+def save_keyset(path: str, ctx: Context, ks: KeySet) -> None:
+    gal = sorted(ks.rot)
+    with open(path, "wb") as f:
+        f.write(KS_MAGIC)
+        f.write(np.array([ctx.log_n, ctx.n_q, ctx.K, len(ks.s_parts)], dtype="<u4").tobytes())
+        f.write(np.array([ks.seed], dtype="<u8").tobytes())
+        f.write(np.array([len(gal), 0], dtype="<u4").tobytes())
+        f.write(np.array(ctx.q + ctx.p, dtype="<u8").tobytes())
+        f.write(np.array(gal, dtype="<u8").tobytes())
+
+
+def load_keyset(path: str, ctx: Context) -> KeySet:
+    raw = open(path, "rb").read()
+    if raw[:8] != KS_MAGIC:
+        raise ValueError("not a keyset file")
+    log_n, n_q, n_p, parties = (int(v) for v in np.frombuffer(raw, dtype="<u4", count=4, offset=8))
+    seed = int(np.frombuffer(raw, dtype="<u8", count=1, offset=24)[0])
+    n_gal = int(np.frombuffer(raw, dtype="<u4", count=1, offset=32)[0])
+    if (log_n, n_q, n_p) != (ctx.log_n, ctx.n_q, ctx.K):
+        raise ValueError("keyset of another ring or chain")
+    moduli = [int(v) for v in np.frombuffer(raw, dtype="<u8", count=n_q + n_p, offset=40)]
+    if moduli != ctx.q + ctx.p:
+        raise ValueError("moduli differ from the context")
+    off = 40 + 8 * (n_q + n_p)
+    if len(raw) != off + 8 * n_gal:
+        raise ValueError("truncated keyset file")
+    ks = keygen(ctx, parties, seed)
+    for g in (int(v) for v in np.frombuffer(raw, dtype="<u8", count=n_gal, offset=off)):
+        ks.rot[g] = gen_switch_key(ctx, ks, g, ctx.automorphism(ks.s_ntt, g))
+    return ks
+
+
 def decrypt_crt(ctx: Context, ks: KeySet, ct: Ciphertext) -> list:
     """Full-modulus decryption with CRT reconstruction in Python integers
     (pins only): centered c0 + c1*s mod q_0...q_{limbs-1}."""

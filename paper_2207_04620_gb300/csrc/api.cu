@@ -1,5 +1,7 @@
 // extern "C" entry points of include/hx.h: argument checks, handle management
 // and error translation around the runtime.
+#include <algorithm>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <stdexcept>
@@ -98,6 +100,69 @@ hx_status hx_keygen(hx_context *ctx, int n_parties, uint64_t seed, const int32_t
     add_rotation_keys(*ctx, *ks, st, nullptr);
     *out = ks.release();
     return HX_OK;
+    HX_END
+}
+
+// keyset file: "HXKS0001", u32 log_n, n_q, n_p, n_parties, u64 seed, u32 n_galois, 0,
+// u64 moduli[n_q + n_p], u64 galois[n_galois] ascending, little-endian.  Keys are a
+// deterministic function of (seed, parties, Galois elements), so the file holds that recipe.
+hx_status hx_keyset_save(hx_context *ctx, const hx_keyset *ks, const char *path)
+{
+    HX_TRY
+    need(ctx && ks && path && ks->ctx == ctx, "null argument or keys of another context");
+    std::vector<uint64_t> gal;
+    for (const auto &kv : ks->rot) gal.push_back(kv.first);
+    std::sort(gal.begin(), gal.end());
+    FILE *f = fopen(path, "wb");
+    HX_CHECK(f, HX_EINVAL, std::string("cannot write ") + path);
+    const uint32_t hdr[4] = {(uint32_t)ctx->log_n, (uint32_t)ctx->n_q, (uint32_t)ctx->K, (uint32_t)ks->n_parties};
+    const uint32_t cnt[2] = {(uint32_t)gal.size(), 0};
+    bool ok = fwrite("HXKS0001", 1, 8, f) == 8 && fwrite(hdr, 4, 4, f) == 4 && fwrite(&ks->seed, 8, 1, f) == 1 &&
+              fwrite(cnt, 4, 2, f) == 2 && fwrite(ctx->primes.data(), 8, ctx->n_all, f) == (size_t)ctx->n_all &&
+              fwrite(gal.data(), 8, gal.size(), f) == gal.size();
+    ok = (fclose(f) == 0) && ok;
+    HX_CHECK(ok, HX_EINVAL, std::string("short write to ") + path);
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_keyset_load(hx_context *ctx, const char *path, hx_keyset **out)
+{
+    HX_TRY
+    need(ctx && path && out, "null argument");
+    *out = nullptr;
+    FILE *f = fopen(path, "rb");
+    HX_CHECK(f, HX_EINVAL, std::string("cannot read ") + path);
+    char magic[8];
+    uint32_t hdr[4], cnt[2];
+    uint64_t seed = 0;
+    std::vector<uint64_t> mod, gal;
+    bool ok = fread(magic, 1, 8, f) == 8 && fread(hdr, 4, 4, f) == 4 && fread(&seed, 8, 1, f) == 1 &&
+              fread(cnt, 4, 2, f) == 2;
+    if (ok) ok = memcmp(magic, "HXKS0001", 8) == 0 && hdr[0] == (uint32_t)ctx->log_n &&
+                 hdr[1] == (uint32_t)ctx->n_q && hdr[2] == (uint32_t)ctx->K && hdr[3] >= 1 && hdr[3] <= 64 &&
+                 cnt[0] <= (uint32_t)ctx->N;
+    if (ok) {
+        mod.resize(ctx->n_all);
+        gal.resize(cnt[0]);
+        ok = fread(mod.data(), 8, mod.size(), f) == mod.size() && fread(gal.data(), 8, gal.size(), f) == gal.size() &&
+             fgetc(f) == EOF;
+        for (int i = 0; ok && i < ctx->n_all; i++) ok = mod[i] == ctx->primes[i];
+    }
+    fclose(f);
+    HX_CHECK(ok, HX_EINVAL, std::string(path) + " is not a keyset file of this context");
+    // each Galois element back to its rotation step: 5^k mod 2N for k in [0, N/2)
+    std::vector<int64_t> steps;
+    const uint64_t two_n = 2ull * ctx->N;
+    for (uint64_t g : gal) {
+        uint64_t x = 1;
+        int64_t k = 0;
+        for (; k < ctx->N / 2 && x != g; k++) x = x * 5 % two_n;
+        HX_CHECK(x == g, HX_EINVAL, "Galois element " + std::to_string(g) + " is not a power of 5");
+        steps.push_back(k);
+    }
+    std::vector<int32_t> st(steps.begin(), steps.end());
+    return hx_keygen(ctx, (int)hdr[3], seed, st.data(), st.size(), out);
     HX_END
 }
 

@@ -54,6 +54,8 @@ _SIGS = {
     "hx_encode": (c_int, [c_vp, P_dbl, c_size_t, c_double, P_i64]),
     "hx_decrypt_parties": (c_int, [c_vp, c_vp, c_vp, ctypes.POINTER(ctypes.c_uint8), c_size_t, P_dbl, c_size_t]),
     "hx_ct_save": (c_int, [c_vp, c_vp, ctypes.c_char_p]),
+    "hx_keyset_save": (c_int, [c_vp, c_vp, ctypes.c_char_p]),
+    "hx_keyset_load": (c_int, [c_vp, ctypes.c_char_p, PP]),
     "hx_ct_load": (c_int, [c_vp, ctypes.c_char_p, PP]),
     "hx_encode_batch": (c_int, [c_vp, P_dbl, c_size_t, c_size_t, c_double, P_i64, c_vp]),
     "hx_encrypt_batch": (c_int, [c_vp, c_vp, P_dbl, c_size_t, c_size_t, c_int, P_u64, PP, c_vp]),
@@ -314,6 +316,16 @@ def hx_decrypt_parties(ctx: int, ks: int, ct: int, present, n: int | None = None
     _chk(lib().hx_decrypt_parties(ctx, ks, ct, flags.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), flags.size,
                                   out.ctypes.data_as(P_dbl), n))
     return out
+
+
+def hx_keyset_save(ctx: int, ks: int, path: str) -> None:
+    _chk(lib().hx_keyset_save(ctx, ks, path.encode()))
+
+
+def hx_keyset_load(ctx: int, path: str) -> int:
+    out = _out()
+    _chk(lib().hx_keyset_load(ctx, path.encode(), ctypes.byref(out)))
+    return out.value
 
 
 def hx_ct_save(ctx: int, ct: int, path: str) -> None:

@@ -324,6 +324,38 @@ def test_checkpoint_files_cross_read(alg3, tmp_path):
         hx.hx_ct_destroy(x)
 
 
+def test_keyset_files_cross_read(alg3, tmp_path):
+    """Keyset recipe files: the library writes, the oracle regenerates the same keys, and the
+    other way round; every rotation key and the public key agree residue for residue."""
+    pr = alg3
+    octx = pr.octx
+    dnum, n_all = octx.dnum, octx.n_q + octx.K
+    p_lib, p_or = str(tmp_path / "lib.ks"), str(tmp_path / "oracle.ks")
+    hx.hx_keyset_save(pr.ctx, pr.ks, p_lib)
+    oks = C.load_keyset(p_lib, octx)
+    assert sorted(oks.rot) == sorted(pr.oks.rot)
+    for g in oks.rot:
+        got = hx.hx_keyset_export_switch_key(pr.ctx, pr.ks, g, dnum, n_all)
+        assert np.array_equal(got[:, 0], oks.rot[g].b) and np.array_equal(got[:, 1], oks.rot[g].a)
+    C.save_keyset(p_or, octx, pr.oks)
+    assert open(p_or, "rb").read() == open(p_lib, "rb").read()
+    ks2 = hx.hx_keyset_load(pr.ctx, p_or)
+    try:
+        pk = hx.hx_keyset_export_public_key(pr.ctx, ks2, octx.n_q)
+        assert np.array_equal(pk[0], pr.oks.pk_b) and np.array_equal(pk[1], pr.oks.pk_a)
+        for g in pr.oks.rot:
+            got = hx.hx_keyset_export_switch_key(pr.ctx, ks2, g, dnum, n_all)
+            assert np.array_equal(got[:, 0], pr.oks.rot[g].b)
+    finally:
+        hx.hx_keyset_destroy(ks2)
+    raw = open(p_or, "rb").read()
+    for bad in (raw[:-8], raw[:40] + (int(raw[40]) ^ 2).to_bytes(1, "little") + raw[41:], raw + b"\0"):
+        open(p_or, "wb").write(bad)
+        with pytest.raises(hx.HxError) as e:
+            hx.hx_keyset_load(pr.ctx, p_or)
+        assert e.value.code == -1
+
+
 def test_decrypt_needs_every_party(alg3):
     pr = alg3
     z = np.linspace(-2, 2, 16)

@@ -254,3 +254,24 @@ def test_relin_rescale_is_the_rounded_division_by_p_qtop(small):
     z = C.decrypt(ctx, ks, out)
     assert np.abs(z - C.decrypt(ctx, ks, two)).max() < ctx.N * 2 * (1 + ctx.N) / out.scale
     assert np.abs(z - C.decrypt(ctx, ks, a) * C.decrypt(ctx, ks, b)).max() < 2 ** -20
+
+
+def test_keyset_file_layout_and_regeneration(small, tmp_path):
+    ctx, ks = small   # 3 parties, seed 7, rotations 1, 5, -3
+    path = str(tmp_path / "keys.bin")
+    C.save_keyset(path, ctx, ks)
+    raw = open(path, "rb").read()
+    gal = sorted(ks.rot)
+    want = b"HXKS0001" + struct.pack("<4I", ctx.log_n, ctx.n_q, ctx.K, 3) + struct.pack("<Q", 7)
+    want += struct.pack("<2I", len(gal), 0) + struct.pack("<%dQ" % (ctx.n_q + ctx.K), *(ctx.q + ctx.p))
+    want += struct.pack("<%dQ" % len(gal), *gal)
+    assert raw == want and len(gal) == 3
+    back = C.load_keyset(path, ctx)
+    assert np.array_equal(back.s_ntt, ks.s_ntt) and np.array_equal(back.pk_b, ks.pk_b)
+    assert np.array_equal(back.relin.b, ks.relin.b) and sorted(back.rot) == gal
+    for g in gal:
+        assert np.array_equal(back.rot[g].b, ks.rot[g].b) and np.array_equal(back.rot[g].a, ks.rot[g].a)
+    for bad in (b"HXKS0002" + raw[8:], raw[:-8], raw[:40] + struct.pack("<Q", ctx.q[0] + 2) + raw[48:]):
+        open(path, "wb").write(bad)
+        with pytest.raises(ValueError):
+            C.load_keyset(path, ctx)
