@@ -112,6 +112,31 @@ __global__ void k_enc_round(int64_t *out, size_t out_stride, const double2 *A, i
     }
 }
 
+// the encoder's real coefficients m_i = Re(a_i) / n, before the scale (k_enc_round's quotient)
+__global__ void k_enc_real(double *m, size_t m_stride, const double2 *A, int log_m, int n)
+{
+    const int b = blockIdx.y;
+    const double2 *a = A + ((size_t)b << log_m);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        m[b * m_stride + i] = __ddiv_rn(a[i].x, (double)n);
+}
+
+// out row r = round_half_away(m[idx[r]] * scale): k_enc_round's last two steps on cached quotients
+__global__ void k_enc_round_rows(int64_t *out, const double *m, const int *idx, int n, double scale, int *err)
+{
+    const int r = blockIdx.y;
+    const double *mr = m + (size_t)idx[r] * n;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = round_half_away_d(__dmul_rn(mr[i], scale));
+        if (!(fabs(v) < 4611686018427387904.0)) {
+            atomicExch(err, 1);
+            out[(size_t)r * n + i] = 0;
+        } else {
+            out[(size_t)r * n + i] = (int64_t)v;
+        }
+    }
+}
+
 // encryption randomness of entry b: poly 0 ternary (v), 1 and 2 Gaussian (e0, e1);
 // state0[b*3 + p] is the stream's initial state, draw i = mix64(state0 + (i+1) gamma)
 __global__ void k_enc_sample(int64_t *out, size_t entry_stride, const uint64_t *__restrict__ state0,
@@ -183,6 +208,46 @@ void encode_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int 
                                                          reinterpret_cast<int *>(err.p));
     HX_CUDA(cudaGetLastError());
     ctx.counters[C_LAUNCH] += 4 + (log_m - 10);
+    int herr = 0;
+    HX_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HX_CUDA(cudaStreamSynchronize(s));
+    HX_CHECK(herr == 0, HX_EINVAL, "encoded coefficient exceeds 2^62");
+}
+
+// the real coefficients of the encoding of every slot vector (scale not yet applied):
+// encode_batch's coefficients are round_half_away(m * scale) of these, bit for bit
+void encode_real_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int count, double *m_out,
+                       cudaStream_t s)
+{
+    const int N = ctx.N, log_m = ctx.log_n + 1, m = 2 * N;
+    HX_CHECK(m % kFftTile == 0, HX_EINVAL, "the device encoder needs N >= 512");
+    HX_CHECK(n_slots <= (size_t)N / 2 && count >= 1 && count < 65536, HX_EINVAL, "bad slot batch");
+    const EncTables &t = enc_tables(ctx);
+    DevBuf A((size_t)2 * m * count, s);
+    HX_CUDA(cudaMemsetAsync(A.p, 0, sizeof(double2) * (size_t)m * count, s));
+    double2 *a = reinterpret_cast<double2 *>(A.p);
+    const double2 *roots = reinterpret_cast<const double2 *>(t.roots->p);
+    k_enc_place<<<dim3(grid_for(N / 2), count), 256, 0, s>>>(a, slots_dev, n_slots,
+                                                             reinterpret_cast<const int *>(t.e->p), log_m, N / 2);
+    k_enc_fft_tile<<<dim3(m / kFftTile, count), kFftTile / 2, 0, s>>>(a, roots, log_m);
+    for (int len = 2 * kFftTile; len <= m; len <<= 1)
+        k_enc_fft_stage<<<dim3(grid_for(m / 2), count), 256, 0, s>>>(a, roots, log_m, len);
+    k_enc_real<<<dim3(grid_for(N), count), 256, 0, s>>>(m_out, (size_t)N, a, log_m, N);
+    HX_CUDA(cudaGetLastError());
+    ctx.counters[C_LAUNCH] += 4 + (log_m - 10);
+}
+
+// rows[r] of the output = the encoding at `scale` of the slot vector whose real coefficients
+// are row idx_dev[r] of m (count rows, N coefficients each)
+void encode_rows_from_real(hx_context &ctx, const double *m, const int *idx_dev, int count, double scale,
+                           int64_t *out, cudaStream_t s)
+{
+    HX_CHECK(count >= 1 && count < 65536, HX_EINVAL, "bad row count");
+    DevBuf err(1, s);
+    HX_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
+    k_enc_round_rows<<<dim3(grid_for(ctx.N), count), 256, 0, s>>>(out, m, idx_dev, ctx.N, scale,
+                                                                  reinterpret_cast<int *>(err.p));
+    HX_CUDA(cudaGetLastError());
     int herr = 0;
     HX_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     HX_CUDA(cudaStreamSynchronize(s));

@@ -310,6 +310,7 @@ void destroy_context(hx_context &c)
     cudaDeviceSynchronize();
     c.plans.clear();
     c.plans_pinned.clear();
+    c.mask_real.clear();
     if (c.plan_stream) {
         cudaStreamSynchronize(c.plan_stream);
         cudaStreamDestroy(c.plan_stream);

@@ -113,6 +113,13 @@ std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs, int t)
 
 void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s);
 
+// whether the masks' real coefficients of a plan shape are cached (then the 0/1 vectors are not needed)
+static bool mask_real_cached(hx_context &ctx, int kind, int h, bool alg3)
+{
+    std::lock_guard<std::mutex> lk(ctx.mask_real_mu);
+    return ctx.mask_real.count(std::make_tuple(kind, h, alg3)) != 0;
+}
+
 hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
 {
     HX_CHECK(h >= 2 && (h & (h - 1)) == 0 && h * h <= ctx.N / 2, HX_EINVAL, "h must be a power of two with h^2 <= N/2");
@@ -137,11 +144,13 @@ hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
         p->index[{kind, idx}] = (int)p->masks.size();
         p->masks.push_back(std::move(m));
     };
-    for (int l = -h + 1; l < h; l++) add(0, l, rot(diag_mu(h, l), -b * floordiv(l, b)), limbs, false);
+    const bool vecs = !mask_real_cached(ctx, 0, h, p->alg3);  // else the encodings are already known
+    using V = std::vector<int32_t>;
+    for (int l = -h + 1; l < h; l++) add(0, l, vecs ? rot(diag_mu(h, l), -b * floordiv(l, b)) : V(), limbs, false);
     for (int l = 0; l < h; l++)
-        add(1, l, p->alg3 ? rot(diag_zeta(h, l), -h * b * (l / b)) : diag_zeta(h, l), limbs, false);
+        add(1, l, !vecs ? V() : p->alg3 ? rot(diag_zeta(h, l), -h * b * (l / b)) : diag_zeta(h, l), limbs, false);
     if (p->alg3)  // Step 2 selects after rotating: v_k itself, in the extended basis
-        for (int k = 1; k < h; k++) add(2, k, diag_v(h, k), limbs - 1, true);
+        for (int k = 1; k < h; k++) add(2, k, vecs ? diag_v(h, k) : V(), limbs - 1, true);
     encode_plan_masks(ctx, *p, s);
     return p.release();
 }
@@ -156,15 +165,41 @@ static std::vector<int> iota_rows(int n)
 void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s)
 {
     hx_matmul_plan *p = &pl;
-    const int hh = p->h * p->h;
+    const int hh = p->h * p->h, M_all = (int)p->masks.size();
     const size_t S = (size_t)ctx.N / 2, N = ctx.N;
     Eval ev(ctx, s);
-    // masks of one scale and basis form a group: their 0/1 vectors (one byte per matrix entry)
-    // go up once, are expanded over the beta packed matrices on the device, encoded by the
-    // device encoder (the same coefficients as the host encoder) and moved to NTT and Montgomery
-    // form in one batch; every mask is a view into the group's buffer
+    // The encoder's real coefficients of every mask depend on the plan's shape only (kind, h,
+    // Alg. 3 or the depth-2 form), not on its level: they are computed once per context -- the
+    // 0/1 vectors (one byte per matrix entry) go up, are expanded over the beta packed matrices
+    // and transformed by the device encoder -- and a plan at any level scales and rounds them
+    // (the same coefficients as encoding at that scale, bit for bit).
+    const auto shape = std::make_tuple(p->kind, p->h, p->alg3);
+    BufPtr real;
+    {
+        std::lock_guard<std::mutex> lk(ctx.mask_real_mu);
+        auto it = ctx.mask_real.find(shape);
+        if (it != ctx.mask_real.end()) real = it->second;
+    }
+    if (!real) {
+        std::vector<uint8_t> bits((size_t)M_all * hh);
+        for (int r = 0; r < M_all; r++)
+            for (int t = 0; t < hh; t++) bits[(size_t)r * hh + t] = p->masks[r].vec[t] != 0;
+        DevBuf dbits((bits.size() + 7) / 8, s), dslots((size_t)M_all * S, s);
+        HX_CUDA(cudaMemcpyAsync(dbits.p, bits.data(), bits.size(), cudaMemcpyHostToDevice, s));
+        launch_expand_masks(ev.lc(), reinterpret_cast<double *>(dslots.p), reinterpret_cast<const uint8_t *>(dbits.p),
+                            M_all, hh, p->beta, S);
+        real = std::make_shared<DevBuf>((size_t)M_all * N, true);
+        encode_real_batch(ctx, reinterpret_cast<const double *>(dslots.p), S, M_all,
+                          reinterpret_cast<double *>(real->p), s);
+        HX_CUDA(cudaStreamSynchronize(s));
+        std::lock_guard<std::mutex> lk(ctx.mask_real_mu);
+        auto ins = ctx.mask_real.emplace(shape, real);  // another call may have made it meanwhile
+        real = ins.first->second;
+    }
+    // masks of one scale and basis form a group, moved to NTT and Montgomery form in one batch;
+    // every mask is a view into the group's buffer
     std::map<std::tuple<double, int, bool>, std::vector<int>> groups;
-    for (int i = 0; i < (int)p->masks.size(); i++) {
+    for (int i = 0; i < M_all; i++) {
         const auto &m = p->masks[i];
         groups[std::make_tuple(m.scale, m.limbs, m.extended)].push_back(i);
     }
@@ -173,20 +208,16 @@ void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s)
         const int M = (int)ids.size(), limbs = std::get<1>(grp.first);
         const bool ext = std::get<2>(grp.first);
         const int rows = ext ? limbs + ctx.K : limbs;
-        std::vector<uint8_t> bits((size_t)M * hh);
-        for (int r = 0; r < M; r++)
-            for (int t = 0; t < hh; t++) bits[(size_t)r * hh + t] = p->masks[ids[r]].vec[t] != 0;
-        std::vector<int> pr(rows), prM((size_t)M * rows);
+        std::vector<int> pr(rows), idx(ids.begin(), ids.end()), prM((size_t)M * rows);
         for (int t = 0; t < rows; t++) pr[t] = t < limbs ? t : ctx.n_q + (t - limbs);
         for (int r = 0; r < M; r++) std::copy(pr.begin(), pr.end(), prM.begin() + (size_t)r * rows);
-        DevBuf dbits((bits.size() + 7) / 8, s), dpr((prM.size() + 1) / 2, s);
-        HX_CUDA(cudaMemcpyAsync(dbits.p, bits.data(), bits.size(), cudaMemcpyHostToDevice, s));
+        DevBuf dpr((prM.size() + 1) / 2, s), didx((idx.size() + 1) / 2, s);
         HX_CUDA(cudaMemcpyAsync(dpr.p, prM.data(), sizeof(int) * prM.size(), cudaMemcpyHostToDevice, s));
-        DevBuf dslots((size_t)M * S, s), dco((size_t)M * N, s);
-        launch_expand_masks(ev.lc(), reinterpret_cast<double *>(dslots.p), reinterpret_cast<const uint8_t *>(dbits.p),
-                            M, hh, p->beta, S);
+        HX_CUDA(cudaMemcpyAsync(didx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
+        DevBuf dco((size_t)M * N, s);
         int64_t *co = reinterpret_cast<int64_t *>(dco.p);
-        encode_batch(ctx, reinterpret_cast<const double *>(dslots.p), S, M, std::get<0>(grp.first), co, N, s);
+        encode_rows_from_real(ctx, reinterpret_cast<const double *>(real->p), reinterpret_cast<const int *>(didx.p), M,
+                              std::get<0>(grp.first), co, s);
         BufPtr G = std::make_shared<DevBuf>((size_t)M * rows * N, s);
         const int *idp = reinterpret_cast<const int *>(dpr.p);
         launch_signed_to_rows(ev.lc(), G->p, co, rows, M, N, idp);
@@ -211,6 +242,7 @@ hx_matmul_plan *make_transpose_plan(hx_context &ctx, int h, int limbs, cudaStrea
     p->beta = ctx.N / 2 / (h * h);
     p->b = baby_steps(h);
     p->alg3 = false;
+    const bool vecs = !mask_real_cached(ctx, 1, h, false);
     for (int sh = -h + 1; sh < h; sh++) {
         hx_matmul_plan::Mask m;
         m.kind = 3;
@@ -218,7 +250,7 @@ hx_matmul_plan *make_transpose_plan(hx_context &ctx, int h, int limbs, cudaStrea
         m.limbs = limbs;
         m.extended = false;
         m.scale = (double)ctx.primes[limbs - 1];
-        m.vec = rot(diag_transpose(h, sh), -(h - 1) * p->b * floordiv(sh, p->b));
+        if (vecs) m.vec = rot(diag_transpose(h, sh), -(h - 1) * p->b * floordiv(sh, p->b));
         p->index[{3, sh}] = (int)p->masks.size();
         p->masks.push_back(std::move(m));
     }
