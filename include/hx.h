@@ -284,6 +284,13 @@ hx_status hx_matmul(hx_context *ctx, const hx_keyset *ks, const hx_ct *A, const 
  * (library masks for the inputs' level). */
 hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *A,
                           const hx_ct *const *B, int h, size_t count, hx_ct **out, void *stream);
+/* A batch with a matrix size per entry: entries of one (h[i], level, scale) are
+ * grouped and each group runs as one batched product (cached plans), the
+ * groups one after another on the stream; out[i] is entry i's product.  A[i]
+ * and B[i] must share level and scale (HX_ESCALE); on any error every out[i]
+ * is NULL. */
+hx_status hx_matmul_batch_mixed(hx_context *ctx, const hx_keyset *ks, const hx_ct *const *A, const hx_ct *const *B,
+                                const int *h, size_t count, hx_ct **out, void *stream);
 
 /* ---- rectangular product (App. D) ------------------------------------------------ */
 /* Rectangular product (App. D, Alg. "41"): At[i] packs A~ = (A; ...; A), the

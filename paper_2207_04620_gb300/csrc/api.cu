@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <stdexcept>
 
@@ -723,6 +724,55 @@ int hx_rmatmul_rotation_steps(const hx_context *ctx, int h, int t, int limbs, in
     std::vector<int64_t> st = plan_rotation_steps(h, ctx->N / 2 / (h * h), limbs, t);
     for (int i = 0; i < (int)st.size() && i < cap; i++) out[i] = (int32_t)st[i];
     return (int)st.size();
+}
+
+hx_status hx_matmul_batch_mixed(hx_context *ctx, const hx_keyset *ks, const hx_ct *const *A, const hx_ct *const *B,
+                                const int *h, size_t count, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(ctx && ks && A && B && h && out && count >= 1 && count < 65536, "bad argument");
+    for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    // entries of one (h, level, scale) form a group, in order of first appearance
+    std::map<std::tuple<int, int, double>, size_t> gid;
+    std::vector<std::vector<size_t>> groups;
+    for (size_t i = 0; i < count; i++) {
+        need(A[i] && B[i], "null ciphertext");
+        need(h[i] >= 2 && (h[i] & (h[i] - 1)) == 0 && h[i] * h[i] <= ctx->N / 2, "h must be a power of two with h^2 <= N/2");
+        HX_CHECK(A[i]->c.comps == 2 && B[i]->c.comps == 2 && A[i]->c.limbs == B[i]->c.limbs &&
+                     A[i]->c.scale == B[i]->c.scale,
+                 HX_ESCALE, "entry " + std::to_string(i) + ": A and B must be ciphertexts of one level and scale");
+        const auto key = std::make_tuple(h[i], A[i]->c.limbs, A[i]->c.scale);
+        auto it = gid.find(key);
+        if (it == gid.end()) {
+            it = gid.emplace(key, groups.size()).first;
+            groups.emplace_back();
+        }
+        groups[it->second].push_back(i);
+    }
+    const cudaStream_t s = S(stream);
+    std::vector<hx_ct *> res(count, nullptr);
+    try {
+        for (const auto &g : groups) {  // each group one batched product (its own chains inside)
+            std::vector<const hx_ct *> ga, gb;
+            for (size_t i : g) {
+                ga.push_back(A[i]);
+                gb.push_back(B[i]);
+            }
+            Cts a = gather(*ctx, ga.data(), g.size(), s);
+            Cts b = gather(*ctx, gb.data(), g.size(), s);
+            PlanUse plan(*ctx, s, cached_plan(*ctx, h[g[0]], a.limbs));
+            Cts r = matmul_batch(*ctx, *ks, *plan.p, a, b, s);
+            std::vector<hx_ct *> part(g.size(), nullptr);
+            scatter(*ctx, r, part.data(), s);
+            for (size_t k = 0; k < g.size(); k++) res[g[k]] = part[k];
+        }
+    } catch (...) {
+        for (hx_ct *c : res) delete c;
+        throw;
+    }
+    std::copy(res.begin(), res.end(), out);
+    return HX_OK;
+    HX_END
 }
 
 hx_status hx_rmatmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *At,

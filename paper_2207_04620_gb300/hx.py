@@ -54,6 +54,7 @@ _SIGS = {
     "hx_encode": (c_int, [c_vp, P_dbl, c_size_t, c_double, P_i64]),
     "hx_decrypt_parties": (c_int, [c_vp, c_vp, c_vp, ctypes.POINTER(ctypes.c_uint8), c_size_t, P_dbl, c_size_t]),
     "hx_ct_save": (c_int, [c_vp, c_vp, ctypes.c_char_p]),
+    "hx_matmul_batch_mixed": (c_int, [c_vp, c_vp, PP, PP, P_i32, c_size_t, PP, c_vp]),
     "hx_keyset_save": (c_int, [c_vp, c_vp, ctypes.c_char_p]),
     "hx_keyset_load": (c_int, [c_vp, ctypes.c_char_p, PP]),
     "hx_ct_load": (c_int, [c_vp, ctypes.c_char_p, PP]),
@@ -500,6 +501,17 @@ def hx_matmul_batch(ctx, ks, plan, As, Bs, h, stream=None) -> list:
     outs = (c_vp * n)()
     _chk(lib().hx_matmul_batch(ctx, ks, plan, a, b, h, n, outs, _stream(stream)))
     return [outs[i] for i in range(n)]
+
+
+def hx_matmul_batch_mixed(ctx: int, ks: int, A, B, h, stream=None) -> list:
+    """Products A[i] . B[i] with their own matrix size h[i] (grouped by size and level inside)."""
+    n = len(A)
+    if len(B) != n or len(h) != n or n == 0:
+        raise ValueError("A, B and h need one entry each per product")
+    a, b, out = (c_vp * n)(*A), (c_vp * n)(*B), (c_vp * n)()
+    hs = np.ascontiguousarray(np.asarray(h, dtype=np.int32))
+    _chk(lib().hx_matmul_batch_mixed(ctx, ks, a, b, hs.ctypes.data_as(P_i32), n, out, _stream(stream)))
+    return [out[i] for i in range(n)]
 
 
 def hx_rmatmul_batch(ctx, ks, plan, Ats, Bs, h, t, stream=None) -> list:

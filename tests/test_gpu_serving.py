@@ -192,3 +192,27 @@ def test_resident_keys_count_once_against_the_budget(setup):
     assert e.value.code == -2
     hx.hx_server_destroy(sv)
     hx.hx_keyset_destroy(ks2)
+
+
+def test_mixed_size_batch_equals_products_alone(setup):
+    """hx_matmul_batch_mixed: entries of different h and level in one call, grouped inside;
+    each product equals hx_matmul on that pair alone, and a malformed entry fails the whole
+    call with no outputs."""
+    ctx, ks, s = setup
+    reqs = [args for kind, args in _requests(ctx, ks, s) if kind == "matmul"]
+    A, B, H = [r[0] for r in reqs], [r[1] for r in reqs], [r[2] for r in reqs]
+    assert len(set(H)) == 2 and len({hx.hx_ct_info(a)[1] for a in A}) == 2
+    outs = hx.hx_matmul_batch_mixed(ctx, ks, A, B, H)
+    for a, b, h, o in zip(A, B, H, outs):
+        alone = hx.hx_matmul(ctx, ks, a, b, h)
+        assert np.array_equal(hx.hx_ct_export(ctx, o), hx.hx_ct_export(ctx, alone))
+        hx.hx_ct_destroy(alone)
+        hx.hx_ct_destroy(o)
+    low = hx.hx_drop(ctx, B[1], hx.hx_ct_info(B[1])[1] - 1)
+    with pytest.raises(hx.HxError) as e:
+        hx.hx_matmul_batch_mixed(ctx, ks, A[:2], [B[0], low], H[:2])
+    assert e.value.code == -4
+    with pytest.raises(hx.HxError) as e:
+        hx.hx_matmul_batch_mixed(ctx, ks, A[:2], B[:2], [H[0], 12])   # not a power of two
+    assert e.value.code == -1
+    hx.hx_ct_destroy(low)
