@@ -541,6 +541,13 @@ def run_dense(args):
             free(res)
     clocks = sampler.stop()
     t = sum(times) / len(times)
+    # live per-kernel-class shares of one more step (CUDA events per launch, chains serial)
+    hx.hx_profile_enable(ctx, True)
+    free(step(999))
+    prof = hx.hx_profile_read(ctx)
+    hx.hx_profile_enable(ctx, False)
+    total_ms = sum(v[1] for v in prof.values())
+    shares = {c: round(v[1] / total_ms, 4) for c, v in sorted(prof.items(), key=lambda kv: -kv[1][1])}
     E, M, dW = res
     Wb = workloads.blocks(W, h)
     Xb = [r[0] for r in workloads.blocks(X, h)]
@@ -570,7 +577,7 @@ def run_dense(args):
             "data": "synthetic",
             "config": {"workload": "cfg3: W 128x784 (padded 128x832), X 784x64, h=64, beta=4, 8+8 ciphertext pairs "
                                    "per HE-MatMult batch, ReLU g_4^(8)(E/4), collective refreshes timed (host wall clock)"},
-            "max_abs_err": err, "clocks": clocks}
+            "max_abs_err": err, "clocks": clocks, "kernel_shares": shares, "kernel_ms_profiled": round(total_ms, 2)}
     print(json.dumps(line), flush=True)
     hx.hx_keyset_destroy(ks)
     hx.hx_context_destroy(ctx)
