@@ -275,3 +275,24 @@ def test_keyset_file_layout_and_regeneration(small, tmp_path):
         open(path, "wb").write(bad)
         with pytest.raises(ValueError):
             C.load_keyset(path, ctx)
+
+
+def test_prime_chain_and_rounding_helpers():
+    sympy = pytest.importorskip("sympy")
+    ctx = C.Context(12, [60, 40, 40, 40], [60, 60], 40)
+    primes = ctx.q + ctx.p
+    assert len(set(primes)) == len(primes)
+    for q, bits in zip(primes, [60, 40, 40, 40, 60, 60]):
+        assert sympy.isprime(q) and q % (2 * ctx.N) == 1 and q < 2 ** bits and q > 2 ** (bits - 1)
+        for m in range(q - 40, q + 40, 2):  # the oracle's primality test agrees with sympy nearby
+            assert C.is_prime(m) == sympy.isprime(m)
+    # each is the largest such prime of its size below the previous one of that size (reading R13)
+    for q, bits in ((ctx.q[1], 40), (ctx.q[2], 40)):
+        m = q + 2 * ctx.N
+        while m < 2 ** bits:
+            assert not sympy.isprime(m) or m in primes
+            m += 2 * ctx.N
+    assert list(C.round_half_away(np.array([0.5, -0.5, 1.5, -1.5, 2.49, -2.51]))) == [1, -1, 2, -2, 2, -3]
+    for q in ctx.q:
+        psi = ctx.psi[q]
+        assert pow(psi, 2 * ctx.N, q) == 1 and pow(psi, ctx.N, q) == q - 1

@@ -424,3 +424,38 @@ def test_encrypted_rectangular_matmul_oracle(limbs):
     out = H.rmatmul(C.Evaluator(ctx, ks), At, B, h, t)
     got = H.unpack(C.decrypt(ctx, ks, out), h, beta)
     assert max(np.abs(g - np.vstack([a @ b] * (h // t))).max() for g, a, b in zip(got, As, Bs)) < 2 ** -18
+
+
+def test_eval_g_structure_and_values():
+    """One application of g_d (reading R8) on a ciphertext: decrypts to g_d(x) for d = 1..4,
+    uses g_depth(d) levels and min(d, 3) + 1 ciphertext products (x^2, y^2, y^2 B(y), x P
+    as d needs them); the scale stays the context's."""
+    ctx = C.Context(9, [60] + [40] * 6, [60] * 3, 40)
+    ks = C.keygen(ctx, 2, 5)
+    rng = np.random.default_rng(8)
+    x = rng.uniform(-1, 1, ctx.S)
+    ct = C.encrypt(ctx, ks, x, 13)
+    for d in (1, 2, 3, 4):
+        ev = C.Evaluator(ctx, ks)
+        out = H.eval_g(ev, ct, d)
+        assert out.limbs == ct.limbs - H.g_depth(d)
+        assert H.g_depth(d) == {1: 2, 2: 3, 3: 4, 4: 4}[d]
+        assert ev.counts["KeySwitch"] == min(d, 3) + 1
+        assert np.abs(C.decrypt(ctx, ks, out) - H.g_eval(d, x)).max() < 2 ** -20
+        assert abs(out.scale / ctx.scale - 1) < 2 ** -10
+
+
+def test_level_adjust_scales_and_drops():
+    """level_adjust brings a ciphertext to a lower level at a chosen scale, times a real
+    constant: the decryption is c * m within the rounding of the integer constant."""
+    ctx = C.Context(9, [60] + [40] * 4, [60, 60], 40)
+    ks = C.keygen(ctx, 2, 6)
+    x = np.linspace(-1, 1, ctx.S)
+    ct = C.encrypt(ctx, ks, x, 3)
+    ev = C.Evaluator(ctx, ks)
+    for target, c, sc in ((3, 1.0, ctx.scale), (1, -2.5, 2.0 ** 38), (2, 1 / 128, 2.0 ** 41)):
+        y = H.level_adjust(ev, ct, target, c, sc)
+        assert y.limbs == target and y.scale == sc
+        assert np.abs(C.decrypt(ctx, ks, y) - c * x).max() < 2 ** -20
+    with pytest.raises(ValueError):
+        H.level_adjust(ev, ct, ct.limbs, 1.0, ctx.scale)
