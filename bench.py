@@ -314,6 +314,11 @@ def run_hx(args, world, rank, local):
                            "unit": "G/s", "frac": round(bfly_s / shoup_s, 4),
                            "mac128_per_s": round(mac_s / 1e9, 1),
                            "what": "measured on this GPU by hx_alu_calibrate (8 independent chains per thread)"}
+    # every kernel class of the step against the same HBM peak (algorithmic bytes of its
+    # launches / their event-timed duration), the key-switching classes among them
+    class_roofline = {c: {"launches": v[0], "ms": round(v[1], 3), "gbs": round(v[2] / (v[1] / 1e3) / 1e9, 1),
+                          "frac": round(v[2] / (v[1] / 1e3) / 1e9 / peak, 4)}
+                      for c, v in sorted(prof.items(), key=lambda kv: -kv[1][1]) if v[1] > 0 and v[2] > 0}
 
     # end to end through the C ABI with host buffers: every step copies its input
     # ciphertexts from page-locked host memory, replays the graph and copies its
@@ -384,7 +389,7 @@ def run_hx(args, world, rank, local):
                 "gpu_launches": launches,
                 "clocks": clocks,
                 "roofline": roofline,
-                "kernel_shares": shares,
+                "kernel_shares": shares, "class_roofline": class_roofline,
                 "graph_kernel_nodes": graph_launches,
                 "plain_batched": {"value": round(PRODUCTS * world / (plain_ms / 1e3), 2), "unit": "matmul/s",
                                   "ms_per_step": round(plain_ms, 3),

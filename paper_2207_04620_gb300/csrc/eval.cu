@@ -165,7 +165,7 @@ BufPtr Eval::modup(const View &d, int B, int limbs)
             true);
     BufPtr D = std::make_shared<DevBuf>((size_t)B * nd * ext * N, s);
     launch_basis_convert(lc(), ctx.t.modup + (size_t)limbs * ctx.dnum, K, View{D->p, (size_t)nd * ext * N, 0},
-                         View{coef.p, (size_t)limbs * N, 0}, B, nd, (size_t)ext * N, 0);
+                         View{coef.p, (size_t)limbs * N, 0}, B, nd, (size_t)ext * N, 0, 8.0 * N * B * nd * ext);
     std::vector<int> off, pr;
     for (int j = 0; j < nd; j++) {
         const int lo = j * K, hi = std::min((j + 1) * K, limbs);
@@ -197,7 +197,8 @@ Cts Eval::moddown_add(const View &accv, int B, int limbs, const View &add, int a
     ntt_inplace(accv.p, (size_t)ext * N, 2 * B, iota_vec(limbs, K), iota_vec(ctx.n_q, K), true);
     DevBuf conv((size_t)B * 2 * limbs * N, s);
     launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), ctx.K,
-                         View{conv.p, (size_t)limbs * N, 0}, View{accv.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0);
+                         View{conv.p, (size_t)limbs * N, 0}, View{accv.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0,
+                         8.0 * N * 2 * B * (K + limbs));
     ntt_inplace(conv.p, (size_t)limbs * N, 2 * B, iota_vec(0, limbs), iota_vec(0, limbs), false);
     Cts o = alloc(B, 2, limbs);
     launch_moddown_final(lc(), o.view(N), accv, View{conv.p, (size_t)2 * limbs * N, (size_t)limbs * N},
@@ -279,7 +280,7 @@ Cts Eval::relin_rescale(const Cts &d, const SwitchKey &rk)
     ntt_inplace(acc.p, (size_t)ext * N, 2 * B, rows, primes, true);
     DevBuf conv((size_t)B * 2 * (L - 1) * N, s);
     launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(tab), K + 1, View{conv.p, (size_t)(L - 1) * N, 0},
-                         View{acc.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0);
+                         View{acc.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0, 8.0 * N * 2 * B * (K + L));
     ntt_inplace(conv.p, (size_t)(L - 1) * N, 2 * B, iota_vec(0, L - 1), iota_vec(0, L - 1), false);
     Cts o = alloc(B, 2, L - 1);
     launch_relin_rs_final(lc(), o.view(N), accv, d.view(N),
@@ -357,7 +358,8 @@ Cts Eval::hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, con
     ntt_inplace(z.p, (size_t)ext * N, 2 * B, iota_vec(limbs, K), iota_vec(ctx.n_q, K), true);
     DevBuf conv((size_t)B * 2 * limbs * N, s);
     launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), ctx.K,
-                         View{conv.p, (size_t)limbs * N, 0}, View{z.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0);
+                         View{conv.p, (size_t)limbs * N, 0}, View{z.p, (size_t)ext * N, 0}, 2 * B, 1, 0, 0,
+                         8.0 * N * 2 * B * (ctx.K + limbs));
     ntt_inplace(conv.p, (size_t)limbs * N, 2 * B, iota_vec(0, limbs), iota_vec(0, limbs), false);
     Cts o = alloc(B, 2, limbs);
     launch_moddown_final_mux(lc(), o.view(N), zv, View{conv.p, (size_t)2 * limbs * N, (size_t)limbs * N},

@@ -164,8 +164,9 @@ void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &s
 void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate);
 void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int B, int comps, int limbs,
                          bool accumulate = false);
+// alg_bytes: one read of every source row and one write of every destination row (profiling)
 void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int max_src, View out, View in, int B,
-                          int groups, size_t gstride_out, size_t gstride_in);
+                          int groups, size_t gstride_out, size_t gstride_in, double alg_bytes = 0.0);
 void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
                    const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B,
                    bool accumulate = false);

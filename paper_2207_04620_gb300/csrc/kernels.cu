@@ -855,9 +855,9 @@ void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int 
 }
 
 void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int max_src, View out, View in, int B,
-                          int groups, size_t gstride_out, size_t gstride_in)
+                          int groups, size_t gstride_out, size_t gstride_in, double alg_bytes)
 {
-    Timed tm_(c, K_CONV, 0.0);
+    Timed tm_(c, K_CONV, alg_bytes);
     HX_CHECK(B * groups < 65536, HX_EINVAL, "conversion batch too large");
     HX_CHECK(max_src >= 1 && max_src <= MAXK, HX_EINVAL, "too many conversion sources");
     dim3 grid(ew_blocks(c.N, 2), 1, B * groups);
