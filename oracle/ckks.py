@@ -255,9 +255,11 @@ def sample_gaussian(stream: Stream, n: int, sigma: float) -> np.ndarray:
 
 class Context:
     """Parameters: ring degree 2^log_n, Q primes of the given sizes (q_0
-    first), special primes, default scale 2^log2_scale, error width sigma."""
+    first), special primes, default scale 2^log2_scale, error width sigma, and
+    alpha, the primes per key-switching digit (reading R11; None = one per
+    special prime)."""
 
-    def __init__(self, log_n: int, q_bits, p_bits, log2_scale: float, sigma: float = 3.2):
+    def __init__(self, log_n: int, q_bits, p_bits, log2_scale: float, sigma: float = 3.2, alpha: int | None = None):
         self.log_n = log_n
         self.N = 1 << log_n
         self.S = self.N // 2
@@ -265,7 +267,8 @@ class Context:
         self.q = primes[: len(q_bits)]
         self.p = primes[len(q_bits):]
         self.n_q, self.K = len(self.q), len(self.p)
-        self.dnum = -(-self.n_q // self.K)
+        self.alpha = alpha or self.K
+        self.dnum = -(-self.n_q // self.alpha)
         self.scale = 2.0 ** log2_scale
         self.sigma = sigma
         self.psi = {x: find_psi(x, self.N) for x in primes}
@@ -461,7 +464,7 @@ def gen_switch_key(ctx: Context, ks: KeySet, key_id: int, sp_ntt: np.ndarray) ->
         e = sample_gaussian(Stream(ks.seed, PURPOSE_KEY_E, key_id, j), ctx.N, ctx.sigma)
         e_ntt = ctx.ntt(ctx.signed_to_rows(e, prim), prim)
         b = ctx.sub(e_ntt, ctx.mul(a, ks.s_ntt, prim), prim)
-        lo, hi = j * ctx.K, min((j + 1) * ctx.K, ctx.n_q)
+        lo, hi = j * ctx.alpha, min((j + 1) * ctx.alpha, ctx.n_q)
         sub_p = prim[lo:hi]
         gad = ctx.mul_scalar(sp_ntt[lo:hi], [ctx.P % t for t in sub_p], sub_p)
         b[lo:hi] = ctx.add(b[lo:hi], gad, sub_p)
@@ -646,7 +649,8 @@ def load_ciphertext(path: str, ctx: Context) -> Ciphertext:
 
 
 # Keyset recipe (little-endian): b"HXKS0001"; u32 log_n, n_q, n_p, n_parties; u64 seed;
-# u32 number of Galois keys, 0; u64 moduli of Q then P; u64 Galois elements ascending.
+# u32 number of Galois keys, primes per digit; u64 moduli of Q then P; u64 Galois elements
+# ascending.
 # Keys are a deterministic function of (seed, parties, Galois elements).
 
 KS_MAGIC = b"HXKS0001"
@@ -658,7 +662,7 @@ def save_keyset(path: str, ctx: Context, ks: KeySet) -> None:
         f.write(KS_MAGIC)
         f.write(np.array([ctx.log_n, ctx.n_q, ctx.K, len(ks.s_parts)], dtype="<u4").tobytes())
         f.write(np.array([ks.seed], dtype="<u8").tobytes())
-        f.write(np.array([len(gal), 0], dtype="<u4").tobytes())
+        f.write(np.array([len(gal), ctx.alpha], dtype="<u4").tobytes())
         f.write(np.array(ctx.q + ctx.p, dtype="<u8").tobytes())
         f.write(np.array(gal, dtype="<u8").tobytes())
 
@@ -669,9 +673,9 @@ def load_keyset(path: str, ctx: Context) -> KeySet:
         raise ValueError("not a keyset file")
     log_n, n_q, n_p, parties = (int(v) for v in np.frombuffer(raw, dtype="<u4", count=4, offset=8))
     seed = int(np.frombuffer(raw, dtype="<u8", count=1, offset=24)[0])
-    n_gal = int(np.frombuffer(raw, dtype="<u4", count=1, offset=32)[0])
-    if (log_n, n_q, n_p) != (ctx.log_n, ctx.n_q, ctx.K):
-        raise ValueError("keyset of another ring or chain")
+    n_gal, alpha = (int(v) for v in np.frombuffer(raw, dtype="<u4", count=2, offset=32))
+    if (log_n, n_q, n_p, alpha) != (ctx.log_n, ctx.n_q, ctx.K, ctx.alpha):
+        raise ValueError("keyset of another ring, chain or digit size")
     moduli = [int(v) for v in np.frombuffer(raw, dtype="<u8", count=n_q + n_p, offset=40)]
     if moduli != ctx.q + ctx.p:
         raise ValueError("moduli differ from the context")
@@ -870,7 +874,7 @@ class Evaluator:
 
     # -- hybrid key switching ---------------------------------------------------------
     def modup(self, d: np.ndarray, limbs: int) -> list:
-        """ModUp: for every digit j (K consecutive primes of Q_l), the digit's
+        """ModUp: for every digit j (alpha consecutive primes of Q_l), the digit's
         residues are extended by fast basis conversion to all other primes of
         Q_l and to the special primes.  Returns NTT-form arrays over
         q_0..q_{limbs-1}, p_0..p_{K-1}; on the digit's own primes the input is
@@ -880,8 +884,8 @@ class Evaluator:
         coef = ctx.intt(d, ctx.q[:limbs])
         ext = ctx.q[:limbs] + ctx.p
         digits = []
-        for j in range(-(-limbs // ctx.K)):
-            lo, hi = j * ctx.K, min((j + 1) * ctx.K, limbs)
+        for j in range(-(-limbs // ctx.alpha)):
+            lo, hi = j * ctx.alpha, min((j + 1) * ctx.alpha, limbs)
             src = ctx.q[lo:hi]
             tgt_idx = [i for i in range(len(ext)) if not lo <= i < hi]
             tgt = [ext[i] for i in tgt_idx]

@@ -263,7 +263,7 @@ def test_keyset_file_layout_and_regeneration(small, tmp_path):
     raw = open(path, "rb").read()
     gal = sorted(ks.rot)
     want = b"HXKS0001" + struct.pack("<4I", ctx.log_n, ctx.n_q, ctx.K, 3) + struct.pack("<Q", 7)
-    want += struct.pack("<2I", len(gal), 0) + struct.pack("<%dQ" % (ctx.n_q + ctx.K), *(ctx.q + ctx.p))
+    want += struct.pack("<2I", len(gal), ctx.alpha) + struct.pack("<%dQ" % (ctx.n_q + ctx.K), *(ctx.q + ctx.p))
     want += struct.pack("<%dQ" % len(gal), *gal)
     assert raw == want and len(gal) == 3
     back = C.load_keyset(path, ctx)
@@ -296,3 +296,32 @@ def test_prime_chain_and_rounding_helpers():
     for q in ctx.q:
         psi = ctx.psi[q]
         assert pow(psi, 2 * ctx.N, q) == 1 and pow(psi, ctx.N, q) == q - 1
+
+
+@pytest.mark.parametrize("alpha", [1, 2, 4])
+def test_keyswitch_with_digits_of_alpha_primes(alpha):
+    """Hybrid key switching with digits of alpha primes (reading R11; alpha above K when the
+    digit products stay near P): the switched ciphertext decrypts under the target key within
+    the noise bound, and products, rotations and the fused relinearise-rescale stay accurate."""
+    ctx = C.Context(10, [60] + [40] * 7, [60] * 3, 40, alpha=alpha)
+    assert ctx.dnum == -(-8 // alpha)
+    ks = C.keygen(ctx, 2, 11, rot_steps=[1, -4])
+    assert ks.relin.b.shape[0] == ctx.dnum
+    ev = C.Evaluator(ctx, ks)
+    rng = np.random.default_rng(alpha)
+    limbs = 7
+    d = np.stack([rng.integers(0, q, ctx.N, dtype=np.uint64) for q in ctx.q[:limbs]])
+    k0, k1 = ev.keyswitch(d, ks.relin, limbs)
+    pr = ctx.q[:limbs]
+    s2 = ctx.mul(ks.s_ntt[:limbs], ks.s_ntt[:limbs], pr)
+    diff = ctx.intt(ctx.sub(ctx.add(k0, ctx.mul(k1, ks.s_ntt[:limbs], pr), pr), ctx.mul(d, s2, pr), pr), pr)
+    # the digit products (up to 2^180 for alpha = 4) against P (about 2^180): noise of a few
+    # thousand units against a scale of 2^40
+    digit_bits = max(sum(math.log2(q) for q in ctx.q[j * alpha:(j + 1) * alpha]) for j in range(ctx.dnum))
+    bound = ctx.dnum * ctx.N * 20 * 2 ** (digit_bits - math.log2(ctx.P)) + ctx.N * 4
+    err = [int(v) if int(v) <= ctx.q[0] // 2 else int(v) - ctx.q[0] for v in diff[0]]
+    assert max(abs(e) for e in err) < bound
+    z, w = rng.uniform(-1, 1, ctx.S), rng.uniform(-1, 1, ctx.S)
+    a, b = C.encrypt(ctx, ks, z, 5, limbs=limbs), C.encrypt(ctx, ks, w, 6, limbs=limbs)
+    assert np.abs(C.decrypt(ctx, ks, ev.relin_rescale(ev.tensor(a, b))) - z * w).max() < 2 ** -20
+    assert np.abs(C.decrypt(ctx, ks, ev.rotate(a, -4)) - np.roll(z, 4)).max() < 2 ** -20
