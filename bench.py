@@ -434,7 +434,10 @@ def run_sign(args):
 
     __graft_entry__.build()
     log_n, qb, pb, count, d, k = 15, [60] + [40] * 15, [60] * 3, 64, 4, 8
-    ctx = hx.hx_context_create(log_n, qb, pb, 40)
+    # digits of four 40-bit primes: products up to about P (three 60-bit primes), the
+    # relinearisation noise stays far below the scale and the sign keeps its accuracy
+    alpha = 4 if args.alpha is None else args.alpha
+    ctx = hx.hx_context_create(log_n, qb, pb, 40, alpha=alpha)
     hx.hx_autotune(ctx)
     ks = hx.hx_keygen(ctx, 2, 77, [])
     n_slots = (1 << log_n) // 2
@@ -488,7 +491,8 @@ def run_sign(args):
             "ms_per_step": round(t * 1e3, 2), "steps": args.steps, "warmup": args.warmup, "n_gpus": 1,
             "higher_is_better": True, "dtype": "u64", "data": "synthetic",
             "config": {"workload": "cfg2: 64 ciphertexts x 16384 slots, |x| in [2^-8, 1], d=4, k=8, two collective "
-                                   "refreshes per entry (DBootstrap shares on the device), host wall clock"},
+                                   "refreshes per entry (DBootstrap shares on the device), host wall clock",
+                       "primes_per_digit": alpha or 3},
             "max_err_vs_exact": max(errs_sgn), "max_err_vs_fp64_composite": max(errs_g), "clocks": clocks,
             "kernel_shares": shares, "kernel_ms_profiled": round(total_ms, 2)}
     print(json.dumps(line), flush=True)
@@ -511,7 +515,7 @@ def run_dense(args):
     __graft_entry__.build()
     cfg = workloads.CONFIGS["cfg3_dense784x128_n15"]
     h, d, k, div = cfg["h"], cfg["d"], cfg["k"], cfg["input_div"]
-    ctx = hx.hx_context_create(cfg["log_n"], cfg["q_bits"], cfg["p_bits"], cfg["log2_scale"])
+    ctx = hx.hx_context_create(cfg["log_n"], cfg["q_bits"], cfg["p_bits"], cfg["log2_scale"], alpha=args.alpha or 0)
     hx.hx_autotune(ctx)
     ks = hx.hx_keygen(ctx, 2, 81, hx.hx_dense_rotation_steps(ctx, h))
     beta = (1 << cfg["log_n"]) // 2 // (h * h)
@@ -1106,6 +1110,8 @@ def main():
     ap.add_argument("--max-batch", type=int, default=16)
     ap.add_argument("--full", action="store_true", help="serving: add N=2^16 and h=128")
     ap.add_argument("--relu", action="store_true")
+    ap.add_argument("--alpha", type=int, default=None,
+                    help="sign/dense: primes per key-switching digit (0: K; default 4 for sign, K for dense)")
     ap.add_argument("--log-n", type=int, default=14)
     ap.add_argument("--rows", type=int, default=1600)
     ap.add_argument("--tiles", default=None, help="NTT tile widths per phase, e.g. 16,16,16,16 (default: autotune)")

@@ -68,6 +68,7 @@ typedef struct hx_params {
     int p_bits[HX_MAX_P];
     double log2_scale;
     double sigma;
+    int alpha;  /* primes per key-switching digit; 0 = n_p (one digit of n_p primes per special set) */
 } hx_params;
 
 const char *hx_last_error(void);
@@ -102,7 +103,8 @@ int64_t hx_keyset_export_public_key(const hx_keyset *ks, uint64_t *host, size_t 
 void hx_keyset_destroy(hx_keyset *ks);
 /* Keyset checkpoint: keys are a deterministic function of (seed, parties,
  * Galois elements), so the file holds that recipe: "HXKS0001", u32 log_n,
- * n_q, n_p, n_parties, u64 seed, u32 n_galois, 0, the u64 moduli of Q then P,
+ * n_q, n_p, n_parties, u64 seed, u32 n_galois, alpha (primes per digit), the
+ * u64 moduli of Q then P,
  * the u64 Galois elements of the rotation keys ascending, little-endian.
  * Loading checks the magic, ring, chain and moduli against the context and
  * regenerates the same keys (HX_EINVAL for a file of another context). */

@@ -104,7 +104,7 @@ hx_status hx_keygen(hx_context *ctx, int n_parties, uint64_t seed, const int32_t
     HX_END
 }
 
-// keyset file: "HXKS0001", u32 log_n, n_q, n_p, n_parties, u64 seed, u32 n_galois, 0,
+// keyset file: "HXKS0001", u32 log_n, n_q, n_p, n_parties, u64 seed, u32 n_galois, alpha,
 // u64 moduli[n_q + n_p], u64 galois[n_galois] ascending, little-endian.  Keys are a
 // deterministic function of (seed, parties, Galois elements), so the file holds that recipe.
 hx_status hx_keyset_save(hx_context *ctx, const hx_keyset *ks, const char *path)
@@ -117,7 +117,7 @@ hx_status hx_keyset_save(hx_context *ctx, const hx_keyset *ks, const char *path)
     FILE *f = fopen(path, "wb");
     HX_CHECK(f, HX_EINVAL, std::string("cannot write ") + path);
     const uint32_t hdr[4] = {(uint32_t)ctx->log_n, (uint32_t)ctx->n_q, (uint32_t)ctx->K, (uint32_t)ks->n_parties};
-    const uint32_t cnt[2] = {(uint32_t)gal.size(), 0};
+    const uint32_t cnt[2] = {(uint32_t)gal.size(), (uint32_t)ctx->alpha};
     bool ok = fwrite("HXKS0001", 1, 8, f) == 8 && fwrite(hdr, 4, 4, f) == 4 && fwrite(&ks->seed, 8, 1, f) == 1 &&
               fwrite(cnt, 4, 2, f) == 2 && fwrite(ctx->primes.data(), 8, ctx->n_all, f) == (size_t)ctx->n_all &&
               fwrite(gal.data(), 8, gal.size(), f) == gal.size();
@@ -142,7 +142,7 @@ hx_status hx_keyset_load(hx_context *ctx, const char *path, hx_keyset **out)
               fread(cnt, 4, 2, f) == 2;
     if (ok) ok = memcmp(magic, "HXKS0001", 8) == 0 && hdr[0] == (uint32_t)ctx->log_n &&
                  hdr[1] == (uint32_t)ctx->n_q && hdr[2] == (uint32_t)ctx->K && hdr[3] >= 1 && hdr[3] <= 64 &&
-                 cnt[0] <= (uint32_t)ctx->N;
+                 cnt[0] <= (uint32_t)ctx->N && cnt[1] == (uint32_t)ctx->alpha;
     if (ok) {
         mod.resize(ctx->n_all);
         gal.resize(cnt[0]);

@@ -84,7 +84,9 @@ void build_context(hx_context &c, const hx_params &p)
     c.n_q = p.n_q;
     c.K = p.n_p;
     c.n_all = p.n_q + p.n_p;
-    c.dnum = (p.n_q + p.n_p - 1) / p.n_p;
+    HX_CHECK(p.alpha >= 0 && p.alpha <= HX_MAX_P + 1, HX_EINVAL, "alpha must be in [0, 7] (0: one per special prime)");
+    c.alpha = p.alpha ? p.alpha : p.n_p;
+    c.dnum = (p.n_q + c.alpha - 1) / c.alpha;
     c.scale = std::pow(2.0, p.log2_scale);
     c.sigma = p.sigma;
     c.primes = choose_primes(p.log_n, bits);
@@ -127,12 +129,13 @@ void build_context(hx_context &c, const hx_params &p)
 
     // ModUp tables, by (limbs, digit)
     c.h_modup.assign((size_t)(n_q + 1) * c.dnum, ConvTable{});
+    const int A = c.alpha;
     for (int l = 1; l <= n_q; l++) {
-        const int ext = l + K, nd = (l + K - 1) / K;
+        const int ext = l + K, nd = (l + A - 1) / A;
         for (int j = 0; j < nd; j++) {
             ConvTable &T = c.h_modup[(size_t)l * c.dnum + j];
             memset(&T, 0, sizeof(T));
-            const int lo = j * K, hi = std::min((j + 1) * K, l);
+            const int lo = j * A, hi = std::min((j + 1) * A, l);
             T.n_src = hi - lo;
             for (int i = lo; i < hi; i++) {
                 T.src_row[i - lo] = i;

@@ -159,16 +159,16 @@ static std::vector<int> iota_vec(int a, int n)
 
 BufPtr Eval::modup(const View &d, int B, int limbs)
 {
-    const int N = ctx.N, K = ctx.K, ext = limbs + K, nd = (limbs + K - 1) / K;
+    const int N = ctx.N, K = ctx.K, A = ctx.alpha, ext = limbs + K, nd = (limbs + A - 1) / A;
     DevBuf coef((size_t)B * limbs * N, s);
     ntt_oop(d.p, d.bstride, coef.p, (size_t)limbs * N, B, iota_vec(0, limbs), iota_vec(0, limbs), iota_vec(0, limbs),
             true);
     BufPtr D = std::make_shared<DevBuf>((size_t)B * nd * ext * N, s);
-    launch_basis_convert(lc(), ctx.t.modup + (size_t)limbs * ctx.dnum, K, View{D->p, (size_t)nd * ext * N, 0},
+    launch_basis_convert(lc(), ctx.t.modup + (size_t)limbs * ctx.dnum, A, View{D->p, (size_t)nd * ext * N, 0},
                          View{coef.p, (size_t)limbs * N, 0}, B, nd, (size_t)ext * N, 0, 8.0 * N * B * nd * ext);
     std::vector<int> off, pr;
     for (int j = 0; j < nd; j++) {
-        const int lo = j * K, hi = std::min((j + 1) * K, limbs);
+        const int lo = j * A, hi = std::min((j + 1) * A, limbs);
         for (int r = 0; r < ext; r++) {
             if (r >= lo && r < hi) continue;
             off.push_back(j * ext + r);
@@ -183,10 +183,10 @@ BufPtr Eval::modup(const View &d, int B, int limbs)
 Cts Eval::ks_finish(const BufPtr &D, const View &dnt, int B, int limbs, const SwitchKey &key, uint64_t g,
                     const View &add, int add_mask, uint64_t add_g)
 {
-    const int N = ctx.N, K = ctx.K, ext = limbs + K, nd = (limbs + K - 1) / K;
+    const int N = ctx.N, K = ctx.K, ext = limbs + K, nd = (limbs + ctx.alpha - 1) / ctx.alpha;
     DevBuf acc((size_t)B * 2 * ext * N, s);
     View accv{acc.p, (size_t)2 * ext * N, (size_t)ext * N};
-    launch_key_ip(lc(), accv, D->p, dnt.p, dnt.bstride, key.buf->p, ctx.n_all, ctx.n_q, K, limbs, nd, g, B);
+    launch_key_ip(lc(), accv, D->p, dnt.p, dnt.bstride, key.buf->p, ctx.n_all, ctx.n_q, K, ctx.alpha, limbs, nd, g, B);
     ctx.counters[C_KS] += B;
     return moddown_add(accv, B, limbs, add, add_mask, add_g);
 }
@@ -210,7 +210,7 @@ Cts Eval::rotate_sum(const std::vector<std::pair<Cts, int64_t>> &items, const hx
 {
     HX_CHECK(!items.empty(), HX_EINVAL, "empty rotation sum");
     const Cts &f = items[0].first;
-    const int N = ctx.N, K = ctx.K, limbs = f.limbs, B = f.B, ext = limbs + K, nd = (limbs + K - 1) / K;
+    const int N = ctx.N, K = ctx.K, limbs = f.limbs, B = f.B, ext = limbs + K, nd = (limbs + ctx.alpha - 1) / ctx.alpha;
     Cts base = alloc(B, 2, limbs);
     base.scale = f.scale;
     HX_CUDA(cudaMemsetAsync(base.d, 0, sizeof(uint64_t) * base.bstride(N) * B, s));
@@ -230,7 +230,8 @@ Cts Eval::rotate_sum(const std::vector<std::pair<Cts, int64_t>> &items, const hx
         View c1{ct.d + ct.cstride(N), ct.bstride(N), ct.cstride(N)};
         launch_automorphism(lc(), t.view(N), c1, g, B, 1, limbs);
         BufPtr D = modup(t.view(N), B, limbs);
-        launch_key_ip(lc(), accv, D->p, t.d, t.bstride(N), key.buf->p, ctx.n_all, ctx.n_q, K, limbs, nd, 1, B, any);
+        launch_key_ip(lc(), accv, D->p, t.d, t.bstride(N), key.buf->p, ctx.n_all, ctx.n_q, K, ctx.alpha, limbs, nd, 1, B,
+                      any);
         launch_automorphism(lc(), base.view(N), ct.view(N), g, B, 1, limbs, true);  // base.c0 += sigma_g(c0)
         any = true;
         ctx.counters[C_ROT] += B;
@@ -264,12 +265,12 @@ Cts Eval::relin_rescale(const Cts &d, const SwitchKey &rk)
     HX_CHECK(d.comps == 3, HX_EINVAL, "relinearisation needs 3 components");
     HX_CHECK(rk.buf, HX_EKEY, "no relinearisation key");
     HX_CHECK(d.limbs >= 2, HX_ELEVEL, "no level left to rescale");
-    const int N = ctx.N, K = ctx.K, L = d.limbs, B = d.B, ext = L + K, nd = (L + K - 1) / K;
+    const int N = ctx.N, K = ctx.K, L = d.limbs, B = d.B, ext = L + K, nd = (L + ctx.alpha - 1) / ctx.alpha;
     View d2{d.d + 2 * d.cstride(N), d.bstride(N), d.cstride(N)};
     BufPtr D = modup(d2, B, L);
     DevBuf acc((size_t)B * 2 * ext * N, s);
     View accv{acc.p, (size_t)2 * ext * N, (size_t)ext * N};
-    launch_key_ip(lc(), accv, D->p, d2.p, d2.bstride, rk.buf->p, ctx.n_all, ctx.n_q, K, L, nd, 1, B);
+    launch_key_ip(lc(), accv, D->p, d2.p, d2.bstride, rk.buf->p, ctx.n_all, ctx.n_q, K, ctx.alpha, L, nd, 1, B);
     ctx.counters[C_KS] += B;
     D.reset();
     const RelinRescaleTable *tab = ctx.t.relin_rs + L;
@@ -337,7 +338,7 @@ Cts Eval::rotate_hoisted_one(const Cts &a, const BufPtr &D, int64_t k, const hx_
 Cts Eval::hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, const uint64_t *v_ext, double v_scale,
                       uint64_t c, const hx_keyset &keys, const uint64_t *premasked)
 {
-    const int N = ctx.N, K = ctx.K, limbs = a.limbs, ext = limbs + K, nd = (limbs + K - 1) / K, B = a.B;
+    const int N = ctx.N, K = ctx.K, limbs = a.limbs, ext = limbs + K, nd = (limbs + ctx.alpha - 1) / ctx.alpha, B = a.B;
     const uint64_t g1 = galois_for_step(k1, ctx.log_n), g2 = galois_for_step(k2, ctx.log_n);
     HX_CHECK(g1 != 1 && g2 != 1, HX_EINVAL, "selection needs two proper rotations");
     const SwitchKey &key1 = rot_key(keys, g1), &key2 = rot_key(keys, g2);
@@ -351,10 +352,10 @@ Cts Eval::hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, con
     DevBuf z((size_t)B * 2 * ext * N, s);
     View zv{z.p, (size_t)2 * ext * N, (size_t)ext * N};
     if (premasked)
-        launch_key_ip_mux_pm(lc(), zv, D->p, c1.p, c1.bstride, premasked, ctx.n_q, K, limbs, nd, g1, g2, B);
+        launch_key_ip_mux_pm(lc(), zv, D->p, c1.p, c1.bstride, premasked, ctx.n_q, K, ctx.alpha, limbs, nd, g1, g2, B);
     else
         launch_key_ip_mux(lc(), zv, D->p, c1.p, c1.bstride, key1.buf->p, key2.buf->p, v_ext, cs, ctx.n_all, ctx.n_q, K,
-                          limbs, nd, g1, g2, B);
+                          ctx.alpha, limbs, nd, g1, g2, B);
     ntt_inplace(z.p, (size_t)ext * N, 2 * B, iota_vec(limbs, K), iota_vec(ctx.n_q, K), true);
     DevBuf conv((size_t)B * 2 * limbs * N, s);
     launch_basis_convert(lc(), reinterpret_cast<const ConvTable *>(ctx.t.moddown + limbs), ctx.K,

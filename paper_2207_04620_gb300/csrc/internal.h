@@ -168,7 +168,7 @@ void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int 
 void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int max_src, View out, View in, int B,
                           int groups, size_t gstride_out, size_t gstride_in, double alg_bytes = 0.0);
 void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
-                   const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B,
+                   const uint64_t *key, int n_all, int n_q, int K, int alpha, int limbs, int ndig, uint64_t g, int B,
                    bool accumulate = false);
 // out_c = (acc_c - conv_c) * P^-1, plus add_c[galois(j)] for the components set in add_mask
 void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
@@ -177,7 +177,7 @@ void launch_lintrans_mac(const LaunchCtx &c, const MacArgs &a, int B, int limbs,
 // two hoisted rotations selected by a mask in the extended basis (see kernels.cu)
 void launch_key_ip_mux(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
                        const uint64_t *key1, const uint64_t *key2, const uint64_t *v, const Scalars &cs, int n_all,
-                       int n_q, int K, int limbs, int ndig, uint64_t g1, uint64_t g2, int B);
+                       int n_q, int K, int alpha, int limbs, int ndig, uint64_t g1, uint64_t g2, int B);
 // premasked keys of one selection: out = [2][ndig][2][ext][N] with
 // out[0] = v (.) key1, out[1] = (c - v) (.) key2 on the rows of the extended basis (Montgomery form);
 // cR[t] = c * 2^64 mod (prime of row t)
@@ -186,7 +186,8 @@ void launch_premask_keys(const LaunchCtx &c, uint64_t *out, const uint64_t *key1
 // the inner products of a selection with premasked keys: z_h = sum_d sigma_g1(D_d) pk[0][d][h]
 // + sigma_g2(D_d) pk[1][d][h], one Montgomery reduction
 void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
-                          const uint64_t *pk, int n_q, int K, int limbs, int ndig, uint64_t g1, uint64_t g2, int B);
+                          const uint64_t *pk, int n_q, int K, int alpha, int limbs, int ndig, uint64_t g1, uint64_t g2,
+                          int B);
 // measured rates of Shoup products and 128-bit multiply-accumulates on every SM (per second)
 void alu_calibrate(const LaunchCtx &c, uint64_t q, double *shoup_per_s, double *mac_per_s);
 void launch_moddown_final_mux(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,

@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2)
 // elsewhere.  Keys are in Montgomery form, so one reduction gives the sum.
 __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt, size_t dnt_bstride,
                          const uint64_t *__restrict__ key, const PrimeConst *__restrict__ primes, int n_all, int n_q,
-                         int K, int limbs, int ndig, uint64_t g, int log_n, bool accumulate)
+                         int K, int alpha, int limbs, int ndig, uint64_t g, int log_n, bool accumulate)
 {
     const int n = 1 << log_n;
     const int t = blockIdx.y, bi = blockIdx.z;
@@ -342,7 +342,7 @@ __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_
     const size_t dig_stride = (size_t)ext * n;
     const uint64_t *Db = D + (size_t)bi * ndig * dig_stride;
     const uint64_t *db = dnt + bi * dnt_bstride;
-    const int own_digit = t < limbs ? t / K : -1;
+    const int own_digit = t < limbs ? t / alpha : -1;  // digit j holds Q rows j*alpha ..
     // two adjacent outputs per thread: 16-byte key loads and stores, the sources gathered
     for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
         const int js0 = g == 1 ? j : galois_src(j, g, log_n), js1 = g == 1 ? j + 1 : galois_src(j + 1, g, log_n);
@@ -379,8 +379,8 @@ __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_
 __global__ void k_key_ip_mux(View out, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt,
                              size_t dnt_bstride, const uint64_t *__restrict__ key1, const uint64_t *__restrict__ key2,
                              const uint64_t *__restrict__ v, const __grid_constant__ Scalars cs,
-                             const PrimeConst *__restrict__ primes, int n_all, int n_q, int K, int limbs, int ndig,
-                             uint64_t g1, uint64_t g2, int log_n)
+                             const PrimeConst *__restrict__ primes, int n_all, int n_q, int K, int alpha, int limbs,
+                             int ndig, uint64_t g1, uint64_t g2, int log_n)
 {
     const int n = 1 << log_n;
     const int t = blockIdx.y, bi = blockIdx.z;
@@ -390,7 +390,7 @@ __global__ void k_key_ip_mux(View out, const uint64_t *__restrict__ D, const uin
     const size_t dig_stride = (size_t)ext * n;
     const uint64_t *Db = D + (size_t)bi * ndig * dig_stride;
     const uint64_t *db = dnt + bi * dnt_bstride;
-    const int own_digit = t < limbs ? t / K : -1;
+    const int own_digit = t < limbs ? t / alpha : -1;  // digit j holds Q rows j*alpha ..
     const uint64_t c = cs.v[t], csh = cs.sh[t];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const int j1 = galois_src(j, g1, log_n), j2 = galois_src(j, g2, log_n);
@@ -439,8 +439,8 @@ __global__ void k_premask_keys(uint64_t *out, const uint64_t *__restrict__ key1,
 
 __global__ void k_key_ip_mux_pm(View out, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt,
                                 size_t dnt_bstride, const uint64_t *__restrict__ pk,
-                                const PrimeConst *__restrict__ primes, int n_q, int K, int limbs, int ndig, uint64_t g1,
-                                uint64_t g2, int log_n)
+                                const PrimeConst *__restrict__ primes, int n_q, int K, int alpha, int limbs, int ndig,
+                                uint64_t g1, uint64_t g2, int log_n)
 {
     const int n = 1 << log_n;
     const int t = blockIdx.y, bi = blockIdx.z;
@@ -450,7 +450,7 @@ __global__ void k_key_ip_mux_pm(View out, const uint64_t *__restrict__ D, const 
     const size_t dig_stride = (size_t)ext * n;
     const uint64_t *Db = D + (size_t)bi * ndig * dig_stride;
     const uint64_t *db = dnt + bi * dnt_bstride;
-    const int own_digit = t < limbs ? t / K : -1;
+    const int own_digit = t < limbs ? t / alpha : -1;  // digit j holds Q rows j*alpha ..
     const size_t half = (size_t)ndig * 2 * ext * n;
     // two adjacent outputs per thread: 16-byte key loads and stores, the sources gathered
     for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
@@ -871,12 +871,12 @@ void launch_basis_convert(const LaunchCtx &c, const ConvTable *tab_dev, int max_
 }
 
 void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
-                   const uint64_t *key, int n_all, int n_q, int K, int limbs, int ndig, uint64_t g, int B,
+                   const uint64_t *key, int n_all, int n_q, int K, int alpha, int limbs, int ndig, uint64_t g, int B,
                    bool accumulate)
 {
     Timed tm_(c, K_KEYIP, 8.0 * c.N * ((double)B * ndig * (limbs + K) + 2.0 * ndig * (limbs + K) + 2.0 * B * (limbs + K)));
     dim3 grid(ew_blocks(c.N, 2), limbs + K, B);
-    k_key_ip<<<grid, 256, 0, c.stream>>>(acc, D, dnt, dnt_bstride, key, c.t->primes, n_all, n_q, K, limbs, ndig, g,
+    k_key_ip<<<grid, 256, 0, c.stream>>>(acc, D, dnt, dnt_bstride, key, c.t->primes, n_all, n_q, K, alpha, limbs, ndig, g,
                                          c.log_n, accumulate);
     post(c);
 }
@@ -893,13 +893,13 @@ void launch_lintrans_mac(const LaunchCtx &c, const MacArgs &a, int B, int limbs,
 
 void launch_key_ip_mux(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
                        const uint64_t *key1, const uint64_t *key2, const uint64_t *v, const Scalars &cs, int n_all,
-                       int n_q, int K, int limbs, int ndig, uint64_t g1, uint64_t g2, int B)
+                       int n_q, int K, int alpha, int limbs, int ndig, uint64_t g1, uint64_t g2, int B)
 {
     Timed tm_(c, K_KEYIP, 8.0 * c.N * ((double)B * ndig * (limbs + K) + 4.0 * ndig * (limbs + K) + (limbs + K) +
                                         2.0 * B * (limbs + K)));
     dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
     k_key_ip_mux<<<grid, 256, 0, c.stream>>>(out, D, dnt, dnt_bstride, key1, key2, v, cs, c.t->primes, n_all, n_q, K,
-                                             limbs, ndig, g1, g2, c.log_n);
+                                             alpha, limbs, ndig, g1, g2, c.log_n);
     post(c);
 }
 
@@ -912,12 +912,13 @@ void launch_premask_keys(const LaunchCtx &c, uint64_t *out, const uint64_t *key1
 }
 
 void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,
-                          const uint64_t *pk, int n_q, int K, int limbs, int ndig, uint64_t g1, uint64_t g2, int B)
+                          const uint64_t *pk, int n_q, int K, int alpha, int limbs, int ndig, uint64_t g1, uint64_t g2,
+                          int B)
 {
     Timed tm_(c, K_KEYIP, 8.0 * c.N * ((double)B * ndig * (limbs + K) + 4.0 * ndig * (limbs + K) +
                                         2.0 * B * (limbs + K)));
     dim3 grid(ew_blocks(c.N, 2), limbs + K, B);
-    k_key_ip_mux_pm<<<grid, 256, 0, c.stream>>>(out, D, dnt, dnt_bstride, pk, c.t->primes, n_q, K, limbs, ndig, g1, g2,
+    k_key_ip_mux_pm<<<grid, 256, 0, c.stream>>>(out, D, dnt, dnt_bstride, pk, c.t->primes, n_q, K, alpha, limbs, ndig, g1, g2,
                                                 c.log_n);
     post(c);
 }

@@ -52,7 +52,8 @@ void gen_switch_key(hx_context &ctx, hx_keyset &ks, uint64_t key_id, const uint6
         for (int r = 0; r < n_all; r++) sample_uniform(sa, ctx.primes[r], a.data() + (size_t)r * N, N);
         Stream se(ks.seed, P_KEY_E, key_id, j);
         for (int i = 0; i < N; i++) e[i] = ctx.cdt->draw(se);
-        for (int r = 0; r < n_all; r++) gad[r] = (r >= j * K && r < std::min((j + 1) * K, n_q)) ? P_mod[r] : 0;
+        const int A = ctx.alpha;  // digit j: primes j*A .. min((j+1)*A, n_q) - 1
+        for (int r = 0; r < n_all; r++) gad[r] = (r >= j * A && r < std::min((j + 1) * A, n_q)) ? P_mod[r] : 0;
         uint64_t *bj = out.buf->p + (size_t)(2 * j) * n_all * N;
         uint64_t *aj = bj + (size_t)n_all * N;
         HX_CUDA(cudaMemcpyAsync(aj, a.data(), sizeof(uint64_t) * a.size(), cudaMemcpyHostToDevice, s));

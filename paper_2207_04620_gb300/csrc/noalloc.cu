@@ -48,7 +48,7 @@ extern "C" hx_status hx_rotate_noalloc(hx_context *ctx, const hx_keyset *ks, con
     try {
         HX_CHECK(ctx && ks && in && out, HX_EINVAL, "null argument");
         HX_CHECK(limbs >= 1 && limbs <= ctx->n_q, HX_EINVAL, "bad level");
-        const int N = ctx->N, K = ctx->K, ext = limbs + K, nd = (limbs + K - 1) / K;
+        const int N = ctx->N, K = ctx->K, A = ctx->alpha, ext = limbs + K, nd = (limbs + A - 1) / A;
         const size_t n = (size_t)N;
         // tmp and coef: limbs rows each; D: nd*ext rows; acc: 2*ext rows; conv: 2*limbs rows
         const size_t need = n * (4 * (size_t)limbs + (size_t)(nd + 2) * ext);
@@ -79,13 +79,13 @@ extern "C" hx_status hx_rotate_noalloc(hx_context *ctx, const hx_keyset *ks, con
         r.n_rows = limbs;
         for (int l = 0; l < limbs; l++) r.src_off[l] = r.dst_off[l] = r.prime[l] = (int16_t)l;
         launch_ntt(lc, r, true);
-        launch_basis_convert(lc, ctx->t.modup + (size_t)limbs * ctx->dnum, ctx->K, View{D, (size_t)nd * ext * n, 0},
+        launch_basis_convert(lc, ctx->t.modup + (size_t)limbs * ctx->dnum, A, View{D, (size_t)nd * ext * n, 0},
                              View{coef, limbs * n, 0}, 1, nd, (size_t)ext * n, 0);
         r.src = r.dst = D;
         r.src_gs = r.dst_gs = (size_t)nd * ext * n;
         r.n_rows = 0;
         for (int j = 0; j < nd; j++) {
-            const int lo = j * K, hi = std::min((j + 1) * K, limbs);
+            const int lo = j * A, hi = std::min((j + 1) * A, limbs);
             for (int row = 0; row < ext; row++) {
                 if (row >= lo && row < hi) continue;
                 r.src_off[r.n_rows] = r.dst_off[r.n_rows] = (int16_t)(j * ext + row);
@@ -96,7 +96,7 @@ extern "C" hx_status hx_rotate_noalloc(hx_context *ctx, const hx_keyset *ks, con
         launch_ntt(lc, r, false);
         // key inner product and ModDown, sigma_g(c0) added to the first component
         View accv{acc, 2 * (size_t)ext * n, (size_t)ext * n};
-        launch_key_ip(lc, accv, D, tmp, limbs * n, it->second.buf->p, ctx->n_all, ctx->n_q, K, limbs, nd, 1, 1);
+        launch_key_ip(lc, accv, D, tmp, limbs * n, it->second.buf->p, ctx->n_all, ctx->n_q, K, A, limbs, nd, 1, 1);
         r.src = r.dst = acc;
         r.src_gs = r.dst_gs = (size_t)ext * n;
         r.n_groups = 2;

@@ -62,6 +62,7 @@ struct SideStream {
 
 struct hx_context {
     int log_n = 0, N = 0, n_q = 0, K = 0, n_all = 0, dnum = 0;
+    int alpha = 0;  // primes per key-switching digit (dnum = ceil(n_q / alpha))
     std::vector<uint64_t> primes;  // Q then P
     std::vector<uint64_t> psi;
     double scale = 0, sigma = 0;

@@ -564,7 +564,7 @@ void bind_plan_keys(hx_context &ctx, hx_matmul_plan &plan, const hx_keyset &ks, 
     HX_CHECK(plan.kind == 0 && plan.alg3, HX_EINVAL, "only Alg. 3 product plans select in Step 2");
     HX_CHECK(ks.ctx == &ctx && ks.uid, HX_EINVAL, "keys from another context");
     const int h = plan.h, beta = plan.beta, K = ctx.K, limbs = plan.limbs - 1;  // A0's level
-    const int ext = limbs + K, nd = (limbs + K - 1) / K;
+    const int ext = limbs + K, nd = (limbs + ctx.alpha - 1) / ctx.alpha;
     const size_t N = ctx.N;
     Eval ev(ctx, s);
     std::vector<BufPtr> pm(h);

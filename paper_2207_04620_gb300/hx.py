@@ -37,7 +37,7 @@ class HxError(RuntimeError):
 
 class hx_params(ctypes.Structure):
     _fields_ = [("log_n", c_int), ("n_q", c_int), ("q_bits", c_int * HX_MAX_Q), ("n_p", c_int),
-                ("p_bits", c_int * HX_MAX_P), ("log2_scale", c_double), ("sigma", c_double)]
+                ("p_bits", c_int * HX_MAX_P), ("log2_scale", c_double), ("sigma", c_double), ("alpha", c_int)]
 
 
 _SIGS = {
@@ -184,8 +184,9 @@ def _out():
 
 # ---- context -----------------------------------------------------------------
 
-def hx_context_create(log_n: int, q_bits, p_bits, log2_scale: float, sigma: float = 3.2) -> int:
+def hx_context_create(log_n: int, q_bits, p_bits, log2_scale: float, sigma: float = 3.2, alpha: int = 0) -> int:
     p = hx_params()
+    p.alpha = int(alpha)
     p.log_n, p.n_q, p.n_p = log_n, len(q_bits), len(p_bits)
     for i, b in enumerate(q_bits):
         p.q_bits[i] = b

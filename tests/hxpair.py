@@ -19,6 +19,8 @@ PARAMS = {
     "sign": dict(log_n=12, q_bits=[60] + [40] * 15, p_bits=[60] * 3, log2_scale=40),
     # config 2 itself: N=2^15
     "cfg2": dict(log_n=15, q_bits=[60] + [40] * 15, p_bits=[60] * 3, log2_scale=40),
+    # the sign chain with key-switching digits of four primes (about P each)
+    "sign_a4": dict(log_n=12, q_bits=[60] + [40] * 15, p_bits=[60] * 3, log2_scale=40, alpha=4),
 }
 
 
@@ -26,8 +28,8 @@ class Pair:
     def __init__(self, name: str, n_parties: int = 2, seed: int = 1234, rot_steps=()):
         p = PARAMS[name]
         self.p = p
-        self.octx = C.Context(p["log_n"], p["q_bits"], p["p_bits"], p["log2_scale"])
-        self.ctx = hx.hx_context_create(p["log_n"], p["q_bits"], p["p_bits"], p["log2_scale"])
+        self.octx = C.Context(p["log_n"], p["q_bits"], p["p_bits"], p["log2_scale"], alpha=p.get("alpha"))
+        self.ctx = hx.hx_context_create(p["log_n"], p["q_bits"], p["p_bits"], p["log2_scale"], alpha=p.get("alpha", 0))
         assert hx.hx_context_primes(self.ctx) == self.octx.q + self.octx.p
         self.seed, self.n_parties = seed, n_parties
         self.rot_steps = list(rot_steps)

@@ -261,6 +261,36 @@ def test_relin_rescale_bit_exact(name):
         pr.close()
 
 
+def test_digits_of_four_primes_bit_exact():
+    """Key-switching digits of alpha = 4 primes (three special primes, 40-bit chain): keys,
+    rotations, relinearisation, the fused relinearise-rescale and one g_4 composition equal
+    the oracle's with the same digits, residue for residue."""
+    pr = Pair("sign_a4", rot_steps=[1, -3])
+    try:
+        octx, ev = pr.octx, C.Evaluator(pr.octx, pr.oks)
+        assert octx.alpha == 4 and octx.dnum == 4
+        n_all = octx.n_q + octx.K
+        rk = hx.hx_keyset_export_switch_key(pr.ctx, pr.ks, 0, octx.dnum, n_all)
+        assert np.array_equal(rk[:, 0], pr.oks.relin.b) and np.array_equal(rk[:, 1], pr.oks.relin.a)
+        for g, key in pr.oks.rot.items():
+            k = hx.hx_keyset_export_switch_key(pr.ctx, pr.ks, g, octx.dnum, n_all)
+            assert np.array_equal(k[:, 0], key.b) and np.array_equal(k[:, 1], key.a)
+        rng = np.random.default_rng(3)
+        for limbs in (16, 11, 5):   # 4, 3 and 2 digits, the last ones partial
+            A = pr.encrypt(rng.uniform(-1, 1, 64), 10 + limbs, limbs=limbs)
+            B = pr.encrypt(rng.uniform(-1, 1, 64), 30 + limbs, limbs=limbs)
+            a, b = pr.to_lib(A), pr.to_lib(B)
+            assert pr.same(hx.hx_rotate(pr.ctx, pr.ks, a, -3), ev.rotate(A, -3))
+            d = hx.hx_tensor(pr.ctx, a, b)
+            assert pr.same(hx.hx_relinearize(pr.ctx, pr.ks, d), ev.relinearize(ev.tensor(A, B)))
+            assert pr.same(hx.hx_relin_rescale(pr.ctx, pr.ks, d), ev.relin_rescale(ev.tensor(A, B)))
+        x = pr.encrypt(workloads.sign_inputs(4, octx.S), 9)
+        want = Hc.sign_approx(C.Evaluator(octx, pr.oks), x, 4, 1)
+        assert pr.same(hx.hx_sign_approx(pr.ctx, pr.ks, pr.to_lib(x), 4, 1, allow_refresh=False), want)
+    finally:
+        pr.close()
+
+
 def test_error_statuses(cfg0):
     ctx = cfg0.ctx
     a = cfg0.to_lib(cfg0.encrypt(np.ones(4), 1))
