@@ -55,8 +55,10 @@ typedef struct hx_matmul_plan hx_matmul_plan;
 
 /* Parameters (Sec. 2.2: R_Q = Z_Q[X]/(X^N+1), Q = q_0...q_{L-1}).
  * log_n in [11, 16]; n_q Q primes of q_bits[i] bits (q_0 first), n_p special
- * primes of p_bits[k] bits (hybrid key switching, digits of n_p primes);
- * every size in [20, 61].  Primes: for each size in this order, the largest
+ * primes of p_bits[k] bits (hybrid key switching); key-switching digits of
+ * alpha consecutive Q primes (0 = n_p; at most 7; a digit's product should
+ * stay near or below the special primes' product, or the switch adds noise
+ * in proportion); every size in [20, 61].  Primes: for each size in this order, the largest
  * prime below 2^bits that is 1 mod 2N and not yet chosen.  Default encoding
  * scale 2^log2_scale; error sampler width sigma (discrete Gaussian on
  * [-floor(6 sigma), floor(6 sigma)]). */
@@ -68,7 +70,7 @@ typedef struct hx_params {
     int p_bits[HX_MAX_P];
     double log2_scale;
     double sigma;
-    int alpha;  /* primes per key-switching digit; 0 = n_p (one digit of n_p primes per special set) */
+    int alpha;  /* primes per key-switching digit; 0 = n_p */
 } hx_params;
 
 const char *hx_last_error(void);
