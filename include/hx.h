@@ -211,8 +211,10 @@ hx_status hx_rotate_hoisted(hx_context *ctx, const hx_keyset *ks, const hx_ct *a
  * limbs (distinct, caller-owned).  Every intermediate lives in one static
  * device array of HX_NOALLOC_SCRATCH_BYTES that the library holds on every
  * device it is loaded on until the process exits; a rotation needing more
- * (8*N*(4*limbs + (ceil(limbs/n_p) + 2)*(limbs + n_p)) bytes) returns
- * HX_EINVAL.  The first call on a device looks up the array's device address
+ * (8*N*(4*limbs + (ceil(limbs/alpha) + 2)*(limbs + n_p)) bytes, alpha the
+ * primes per key-switching digit: about 12 MB for N=2^14 at 8 limbs, 48 MB
+ * for N=2^16 at 8 limbs) returns HX_EINVAL, as do keys of another context and
+ * overlapping `in` and `out`.  The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress); make that first call before any stream capture.  All
  * calls share the array: calls whose work overlaps on the GPU (other streams,
  * other threads) race and must be serialised by the caller.  The result is

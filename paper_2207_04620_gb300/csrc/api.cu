@@ -49,6 +49,13 @@ void need(bool c, const char *msg)
     if (!c) throw hx::Error{HX_EINVAL, msg};
 }
 
+// Every handle records the context it was made in.  A handle of another context (another
+// ring degree or prime chain) would reach the kernels with that context's row length and
+// table indices, so it is rejected before any device work.
+void mine(const hx_context *ctx, const hx_keyset *ks) { need(ks->ctx == ctx, "keys of another context"); }
+void mine(const hx_context *ctx, const hx_ct *c) { need(c->ctx == ctx, "ciphertext of another context"); }
+void mine(const hx_context *ctx, const hx_matmul_plan *p) { need(p->ctx == ctx, "plan of another context"); }
+
 } // namespace
 
 namespace hx {
@@ -171,6 +178,7 @@ hx_status hx_keyset_add_rotations(hx_context *ctx, hx_keyset *ks, const int32_t 
 {
     HX_TRY
     need(ctx && ks && (rot_steps || n_steps == 0), "null argument");
+    mine(ctx, ks);
     std::vector<int64_t> st(rot_steps, rot_steps + n_steps);
     add_rotation_keys(*ctx, *ks, st, nullptr);
     return HX_OK;
@@ -239,6 +247,7 @@ hx_status hx_encrypt(hx_context *ctx, const hx_keyset *ks, const double *slots, 
     HX_TRY
     need(ctx && ks && (slots || n == 0) && out, "null argument");
     *out = nullptr;
+    mine(ctx, ks);
     need(n <= (size_t)ctx->N / 2, "too many slots");
     std::vector<int64_t> m(ctx->N);
     ctx->enc->encode(slots, n, ctx->scale, m.data());
@@ -273,6 +282,7 @@ hx_status hx_encrypt_batch(hx_context *ctx, const hx_keyset *ks, const double *s
     need(ctx && ks && slots && seeds && out && count >= 1 && count < 65536 && n <= (size_t)ctx->N / 2,
          "bad argument");
     for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    mine(ctx, ks);
     cudaStream_t s = S(stream);
     DevBuf in(std::max<size_t>(1, n * count), s);
     if (n) HX_CUDA(cudaMemcpyAsync(in.p, slots, sizeof(double) * n * count, cudaMemcpyHostToDevice, s));
@@ -290,6 +300,7 @@ hx_status hx_encrypt_coeffs(hx_context *ctx, const hx_keyset *ks, const int64_t 
     HX_TRY
     need(ctx && ks && coeffs && out, "null argument");
     *out = nullptr;
+    mine(ctx, ks);
     Cts c = encrypt_coeffs(*ctx, *ks, coeffs, scale, limbs ? limbs : ctx->n_q, seed, tag, index, nullptr);
     HX_CUDA(cudaStreamSynchronize(nullptr));
     *out = wrap(ctx, c);
@@ -301,6 +312,8 @@ hx_status hx_decrypt_coeffs(hx_context *ctx, const hx_keyset *ks, const hx_ct *c
 {
     HX_TRY
     need(ctx && ks && ct && coeffs, "null argument");
+    mine(ctx, ks);
+    mine(ctx, ct);
     HX_CUDA(cudaDeviceSynchronize());
     std::vector<int64_t> v = decrypt_coeffs(*ctx, *ks, ct->c, nullptr);
     memcpy(coeffs, v.data(), sizeof(int64_t) * ctx->N);
@@ -312,6 +325,8 @@ hx_status hx_decrypt(hx_context *ctx, const hx_keyset *ks, const hx_ct *ct, doub
 {
     HX_TRY
     need(ctx && ks && ct && (slots || n == 0), "null argument");
+    mine(ctx, ks);
+    mine(ctx, ct);
     HX_CUDA(cudaDeviceSynchronize());
     std::vector<int64_t> v = decrypt_coeffs(*ctx, *ks, ct->c, nullptr);
     ctx->enc->decode(v.data(), ct->c.scale, slots, std::min(n, (size_t)ctx->N / 2));
@@ -324,6 +339,8 @@ hx_status hx_decrypt_parties(hx_context *ctx, const hx_keyset *ks, const hx_ct *
 {
     HX_TRY
     need(ctx && ks && ct && present && (slots || n == 0), "null argument");
+    mine(ctx, ks);
+    mine(ctx, ct);
     need(n_present == (size_t)ks->n_parties, "one flag per party of the key set");
     for (int i = 0; i < ks->n_parties; i++)
         HX_CHECK(present[i], HX_EPARTY,
@@ -342,6 +359,7 @@ hx_status hx_ct_save(hx_context *ctx, const hx_ct *ct, const char *path)
 {
     HX_TRY
     need(ctx && ct && path, "null argument");
+    mine(ctx, ct);
     const Cts &c = ct->c;
     const size_t N = ctx->N, words = (size_t)c.comps * c.limbs * N;
     std::vector<uint64_t> host(words);
@@ -442,6 +460,8 @@ hx_status hx_add(hx_context *ctx, const hx_ct *a, const hx_ct *b, hx_ct **out, v
 {
     HX_TRY
     ONE_IN(a && b)
+    mine(ctx, a);
+    mine(ctx, b);
     *out = wrap(ctx, ev.add(a->c, b->c, false));
     return HX_OK;
     HX_END
@@ -451,6 +471,8 @@ hx_status hx_sub(hx_context *ctx, const hx_ct *a, const hx_ct *b, hx_ct **out, v
 {
     HX_TRY
     ONE_IN(a && b)
+    mine(ctx, a);
+    mine(ctx, b);
     *out = wrap(ctx, ev.add(a->c, b->c, true));
     return HX_OK;
     HX_END
@@ -461,6 +483,7 @@ hx_status hx_mul_plain(hx_context *ctx, const hx_ct *a, const int64_t *pt, doubl
 {
     HX_TRY
     ONE_IN(a && pt)
+    mine(ctx, a);
     DevBuf p((size_t)a->c.limbs * ctx->N, S(stream));
     upload_plaintext(*ctx, S(stream), pt, a->c.limbs, p.p);
     *out = wrap(ctx, ev.mul_plain(a->c, p.p, pt_scale));
@@ -472,6 +495,7 @@ hx_status hx_mul_int(hx_context *ctx, const hx_ct *a, int64_t c, double new_scal
 {
     HX_TRY
     ONE_IN(a)
+    mine(ctx, a);
     *out = wrap(ctx, ev.mul_int(a->c, c, new_scale));
     return HX_OK;
     HX_END
@@ -481,6 +505,7 @@ hx_status hx_add_const(hx_context *ctx, const hx_ct *a, double value, hx_ct **ou
 {
     HX_TRY
     ONE_IN(a)
+    mine(ctx, a);
     *out = wrap(ctx, ev.add_const(a->c, value));
     return HX_OK;
     HX_END
@@ -490,6 +515,8 @@ hx_status hx_tensor(hx_context *ctx, const hx_ct *a, const hx_ct *b, hx_ct **out
 {
     HX_TRY
     ONE_IN(a && b)
+    mine(ctx, a);
+    mine(ctx, b);
     *out = wrap(ctx, ev.tensor(a->c, b->c));
     return HX_OK;
     HX_END
@@ -499,6 +526,8 @@ hx_status hx_relinearize(hx_context *ctx, const hx_keyset *ks, const hx_ct *d, h
 {
     HX_TRY
     ONE_IN(ks && d)
+    mine(ctx, ks);
+    mine(ctx, d);
     *out = wrap(ctx, ev.relinearize(d->c, ks->relin));
     return HX_OK;
     HX_END
@@ -508,6 +537,8 @@ hx_status hx_relin_rescale(hx_context *ctx, const hx_keyset *ks, const hx_ct *d,
 {
     HX_TRY
     ONE_IN(ks && d)
+    mine(ctx, ks);
+    mine(ctx, d);
     *out = wrap(ctx, ev.relin_rescale(d->c, ks->relin));
     return HX_OK;
     HX_END
@@ -517,6 +548,7 @@ hx_status hx_rescale(hx_context *ctx, const hx_ct *a, hx_ct **out, void *stream)
 {
     HX_TRY
     ONE_IN(a)
+    mine(ctx, a);
     *out = wrap(ctx, ev.rescale(a->c));
     return HX_OK;
     HX_END
@@ -526,6 +558,7 @@ hx_status hx_drop(hx_context *ctx, const hx_ct *a, int limbs, hx_ct **out, void 
 {
     HX_TRY
     ONE_IN(a)
+    mine(ctx, a);
     need(limbs >= 1 && limbs <= a->c.limbs, "bad level");
     Cts c = ev.copy(ev.drop(a->c, limbs));
     *out = wrap(ctx, c);
@@ -537,6 +570,8 @@ hx_status hx_rotate(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, int32_
 {
     HX_TRY
     ONE_IN(ks && a)
+    mine(ctx, ks);
+    mine(ctx, a);
     *out = wrap(ctx, ev.rotate(a->c, k, *ks));
     return HX_OK;
     HX_END
@@ -548,6 +583,8 @@ hx_status hx_rotate_hoisted(hx_context *ctx, const hx_keyset *ks, const hx_ct *a
     HX_TRY
     need(ctx && ks && a && steps && outs && n >= 0, "null argument");
     for (int i = 0; i < n; i++) outs[i] = nullptr;
+    mine(ctx, ks);
+    mine(ctx, a);
     Eval ev(*ctx, S(stream));
     std::vector<int64_t> st(steps, steps + n);
     std::vector<Cts> r = ev.rotate_hoisted(a->c, st, *ks);
@@ -622,6 +659,7 @@ hx_status hx_matmul_plan_set_mask(hx_context *ctx, hx_matmul_plan *plan, int i, 
 {
     HX_TRY
     need(ctx && plan && coeffs && i >= 0 && i < (int)plan->masks.size(), "bad mask index");
+    mine(ctx, plan);
     auto &m = plan->masks[i];
     plan->bound_uid = 0;  // keys premasked with the old mask no longer apply
     plan->premasked.clear();
@@ -636,7 +674,9 @@ hx_status hx_matmul_plan_set_mask(hx_context *ctx, hx_matmul_plan *plan, int i, 
 hx_status hx_matmul_plan_bind_keys(hx_context *ctx, hx_matmul_plan *plan, const hx_keyset *ks, void *stream)
 {
     HX_TRY
-    need(ctx && plan && ks && plan->ctx == ctx, "bad argument");
+    need(ctx && plan && ks, "null argument");
+    mine(ctx, plan);
+    mine(ctx, ks);
     bind_plan_keys(*ctx, *plan, *ks, S(stream));
     return HX_OK;
     HX_END
@@ -693,6 +733,9 @@ hx_status hx_matmul(hx_context *ctx, const hx_keyset *ks, const hx_ct *A, const 
     HX_TRY
     need(ctx && ks && A && B && out, "null argument");
     *out = nullptr;
+    mine(ctx, ks);
+    mine(ctx, A);
+    mine(ctx, B);
     PlanUse p(*ctx, S(stream), cached_plan(*ctx, h, A->c.limbs));
     *out = wrap(ctx, matmul_batch(*ctx, *ks, *p.p, A->c, B->c, S(stream)));
     return HX_OK;
@@ -706,6 +749,8 @@ hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_
     need(ctx && ks && A && B && out && count >= 1, "null argument");
     for (size_t i = 0; i < count; i++) out[i] = nullptr;
     need(count < 4096, "batch too large");
+    mine(ctx, ks);
+    if (plan) mine(ctx, plan);
     Cts a = gather(*ctx, A, count, S(stream));
     Cts b = gather(*ctx, B, count, S(stream));
     PlanUse held(*ctx, S(stream), plan ? nullptr : cached_plan(*ctx, h, a.limbs));
@@ -732,11 +777,14 @@ hx_status hx_matmul_batch_mixed(hx_context *ctx, const hx_keyset *ks, const hx_c
     HX_TRY
     need(ctx && ks && A && B && h && out && count >= 1 && count < 65536, "bad argument");
     for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    mine(ctx, ks);
     // entries of one (h, level, scale) form a group, in order of first appearance
     std::map<std::tuple<int, int, double>, size_t> gid;
     std::vector<std::vector<size_t>> groups;
     for (size_t i = 0; i < count; i++) {
         need(A[i] && B[i], "null ciphertext");
+        mine(ctx, A[i]);
+        mine(ctx, B[i]);
         need(h[i] >= 2 && (h[i] & (h[i] - 1)) == 0 && h[i] * h[i] <= ctx->N / 2, "h must be a power of two with h^2 <= N/2");
         HX_CHECK(A[i]->c.comps == 2 && B[i]->c.comps == 2 && A[i]->c.limbs == B[i]->c.limbs &&
                      A[i]->c.scale == B[i]->c.scale,
@@ -781,6 +829,8 @@ hx_status hx_rmatmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul
     HX_TRY
     need(ctx && ks && At && B && out && count >= 1 && count < 4096, "bad argument");
     for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    mine(ctx, ks);
+    if (plan) mine(ctx, plan);
     Cts a = gather(*ctx, At, count, S(stream));
     Cts b = gather(*ctx, B, count, S(stream));
     PlanUse held(*ctx, S(stream), plan ? nullptr : cached_plan(*ctx, h, a.limbs));
@@ -815,6 +865,8 @@ hx_status hx_transpose(hx_context *ctx, const hx_keyset *ks, const hx_matmul_pla
     HX_TRY
     need(ctx && ks && x && out && count >= 1 && count < 4096, "bad argument");
     for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    mine(ctx, ks);
+    if (plan) mine(ctx, plan);
     Cts a = gather(*ctx, x, count, S(stream));
     PlanUse held(*ctx, S(stream), plan ? nullptr : cached_transpose_plan(*ctx, h, a.limbs));
     const hx_matmul_plan *p = plan ? plan : held.p.get();
@@ -830,6 +882,8 @@ hx_status hx_matmul_exec_create(hx_context *ctx, const hx_keyset *ks, const hx_m
     HX_TRY
     need(ctx && ks && plan && out && count >= 1 && count < 4096 && scale > 0, "bad argument");
     *out = nullptr;
+    mine(ctx, ks);
+    mine(ctx, plan);
     std::unique_ptr<hx_matmul_exec> ex(new hx_matmul_exec);
     ex->ctx = ctx;
     ex->ks = ks;
@@ -895,6 +949,8 @@ hx_status hx_matmul_exec_run(hx_matmul_exec *ex, const hx_ct *const *A, const hx
     for (size_t i = 0; i < ex->count; i++) {
         out[i] = nullptr;
         need(A[i] && B[i], "null ciphertext");
+        mine(ex->ctx, A[i]);
+        mine(ex->ctx, B[i]);
         HX_CHECK(A[i]->c.limbs == ex->plan->limbs && B[i]->c.limbs == ex->plan->limbs, HX_ELEVEL,
                  "inputs are not at the executor's level");
         HX_CHECK(A[i]->c.scale == ex->A.scale && B[i]->c.scale == ex->A.scale, HX_ESCALE,
@@ -962,6 +1018,8 @@ hx_status hx_sign_approx(hx_context *ctx, const hx_keyset *ks, const hx_ct *x, i
     HX_TRY
     need(ctx && ks && x && out, "null argument");
     *out = nullptr;
+    mine(ctx, ks);
+    mine(ctx, x);
     *out = wrap(ctx, sign_batch(*ctx, *ks, x->c, d, k, relu != 0, allow_refresh != 0, {refresh_seed}, S(stream)));
     return HX_OK;
     HX_END
@@ -973,6 +1031,7 @@ hx_status hx_sign_approx_batch(hx_context *ctx, const hx_keyset *ks, const hx_ct
     HX_TRY
     need(ctx && ks && x && out && count >= 1 && count < 4096, "bad argument");
     for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    mine(ctx, ks);
     Cts a = gather(*ctx, x, count, S(stream));
     std::vector<uint64_t> seeds(count);
     for (size_t i = 0; i < count; i++) seeds[i] = refresh_seed + i;
@@ -993,6 +1052,9 @@ hx_status hx_dense_layer(hx_context *ctx, const hx_keyset *ks, const hx_matmul_p
     for (int i = 0; i < n_out; i++) E[i] = M[i] = nullptr;
     for (int i = 0; i < n_out * groups; i++) dW[i] = nullptr;
     need(h >= 2 && (h & (h - 1)) == 0 && h * h <= ctx->N / 2, "h must be a power of two with h^2 <= N/2");
+    mine(ctx, ks);
+    for (const hx_matmul_plan *p : {fwd_plan, transpose_plan, bwd_plan})
+        if (p) mine(ctx, p);
     std::vector<const hx_ct *> wg((size_t)n_out * groups);
     for (int i = 0; i < n_out; i++)
         for (int g = 0; g < groups; g++) wg[(size_t)g * n_out + i] = W[(size_t)i * groups + g];

@@ -342,9 +342,14 @@ void destroy_context(hx_context &c)
 Cts gather(hx_context &ctx, const hx_ct *const *cts, size_t count, cudaStream_t s)
 {
     HX_CHECK(count >= 1, HX_EINVAL, "empty batch");
+    for (size_t i = 0; i < count; i++) {
+        HX_CHECK(cts[i], HX_EINVAL, "null ciphertext in a batch");
+        // a ciphertext of another context has another row length: never let it reach a copy or kernel
+        HX_CHECK(cts[i]->ctx == &ctx, HX_EINVAL, "ciphertext of another context in a batch");
+    }
     const Cts &f = cts[0]->c;
     for (size_t i = 0; i < count; i++) {
-        HX_CHECK(cts[i] && cts[i]->c.limbs == f.limbs && cts[i]->c.comps == f.comps, HX_ESCALE,
+        HX_CHECK(cts[i]->c.limbs == f.limbs && cts[i]->c.comps == f.comps, HX_ESCALE,
                  "batch entries must share level and shape");
         HX_CHECK(cts[i]->c.scale == f.scale, HX_ESCALE, "batch entries must share the scale");
     }

@@ -10,6 +10,8 @@
 // one static device array of fixed size that the library reserves on each
 // device it is loaded on, until the process exits.
 #include <mutex>
+#include <new>
+#include <stdexcept>
 
 #include "runtime.h"
 
@@ -55,6 +57,11 @@ extern "C" hx_status hx_rotate_noalloc(hx_context *ctx, const hx_keyset *ks, con
         HX_CHECK(need <= kScratchWords, HX_EINVAL,
                  "rotation needs " + std::to_string(need * 8) + " bytes of scratch, more than the " +
                      std::to_string((unsigned long long)HX_NOALLOC_SCRATCH_BYTES) + "-byte static scratch");
+        // keys of another context would be read with this context's row length and strides
+        HX_CHECK(ks->ctx == ctx, HX_EINVAL, "keys of another context");
+        // the last kernel reads sigma_g(c0) from `in` at permuted indices while it writes `out`
+        const size_t words = 2 * (size_t)limbs * N;
+        HX_CHECK(out + words <= in || in + words <= out, HX_EINVAL, "in and out overlap");
         cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
         const uint64_t g = galois_for_step(k, ctx->log_n);
         if (g == 1) {
@@ -122,5 +129,11 @@ extern "C" hx_status hx_rotate_noalloc(hx_context *ctx, const hx_keyset *ks, con
     } catch (const hx::Error &e) {
         set_error(e.msg);
         return e.code;
+    } catch (const std::bad_alloc &) {
+        set_error("host allocation failed");
+        return HX_ENOMEM;
+    } catch (const std::exception &e) {  // e.g. std::system_error from the mutex
+        set_error(e.what());
+        return HX_EINVAL;
     }
 }

@@ -308,6 +308,10 @@ hx_status hx_server_submit_matmul(hx_server *sv, hx_context *ctx, const hx_keyse
                                   const hx_ct *B, int h, uint64_t *id)
 {
     if (!ctx || !ks || !A || !B) return HX_EINVAL;
+    if (ks->ctx != ctx || A->ctx != ctx || B->ctx != ctx) {
+        set_error("keys or ciphertexts of another context");
+        return HX_EINVAL;
+    }
     if (A->c.limbs != B->c.limbs || A->c.comps != 2 || B->c.comps != 2) {
         set_error("A and B must be ciphertexts at one level");
         return HX_ESCALE;
@@ -326,6 +330,10 @@ hx_status hx_server_submit_sign(hx_server *sv, hx_context *ctx, const hx_keyset 
                                 int relu, uint64_t refresh_seed, uint64_t *id)
 {
     if (!ctx || !ks || !x || x->c.comps != 2) return HX_EINVAL;
+    if (ks->ctx != ctx || x->ctx != ctx) {
+        set_error("keys or ciphertext of another context");
+        return HX_EINVAL;
+    }
     Request r;
     r.kind = 1;
     r.ctx = ctx;

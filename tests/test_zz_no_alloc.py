@@ -32,7 +32,9 @@ def test_noalloc_rotation_matches_hx_rotate_twice(pair):
     for call, (seed, k) in enumerate(((1, 7), (2, -2))):
         ct = pair.encrypt(workloads.sign_inputs(seed, pair.octx.S), 10 + seed)
         h = pair.to_lib(ct)
-        want = hx.hx_ct_export(pair.ctx, hx.hx_rotate(pair.ctx, pair.ks, h, k))
+        rot = hx.hx_rotate(pair.ctx, pair.ks, h, k)
+        want = hx.hx_ct_export(pair.ctx, rot)
+        hx.hx_ct_destroy(rot)
         dev_in = torch.from_numpy(ct.c.view(np.int64).copy()).cuda()
         dev_out = torch.empty_like(dev_in)
         hx.hx_rotate_noalloc(pair.ctx, pair.ks, dev_in.data_ptr(), limbs, dev_out.data_ptr(), k,
@@ -44,11 +46,27 @@ def test_noalloc_rotation_matches_hx_rotate_twice(pair):
 
 
 def test_noalloc_rejects_oversized_rotation(pair):
-    # N = 2^16 with 8 limbs needs about 65 MB of scratch, above the static 16 MiB
+    import torch
+
+    # N = 2^16 with 8 limbs needs about 48 MB of scratch, above the static 16 MiB.  The
+    # buffers are real device buffers of that ciphertext's size, so a rejection that came
+    # later than the host-side checks would still stay inside them.
     ctx = hx.hx_context_create(16, [60] + [45] * 7, [60, 60], 45)
     try:
+        x = torch.zeros(2 * 8 * (1 << 16), dtype=torch.int64, device="cuda")
+        y = torch.zeros_like(x)
         with pytest.raises(hx.HxError) as e:
-            hx.hx_rotate_noalloc(ctx, pair.ks, 1 << 20, 8, 1 << 21, 1)
+            hx.hx_rotate_noalloc(ctx, pair.ks, x.data_ptr(), 8, y.data_ptr(), 1)
         assert e.value.code == -1 and "static scratch" in str(e.value)
     finally:
         hx.hx_context_destroy(ctx)
+
+
+def test_noalloc_rejects_overlapping_buffers(pair):
+    import torch
+
+    limbs = pair.octx.n_q
+    x = torch.zeros(3 * 2 * limbs * pair.N, dtype=torch.int64, device="cuda")
+    with pytest.raises(hx.HxError) as e:
+        hx.hx_rotate_noalloc(pair.ctx, pair.ks, x.data_ptr(), limbs, x.data_ptr() + 8 * limbs * pair.N, 1)
+    assert e.value.code == -1 and "overlap" in str(e.value)
