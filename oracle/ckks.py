@@ -352,8 +352,18 @@ class Context:
 
 
 # ----------------------------------------------------------------------------
-# Encoding (canonical embedding; readings R14)
+# Encoding (Fig. 1 item 3, Ecd; reading R14)
 # ----------------------------------------------------------------------------
+#
+# Coefficient i of the encoding of real slots z at scale D is the exact real
+#     x_i = D * (2/N) * sum_j z_j cos(pi * (i * e_j mod 2N) / N),   e_j = 5^j mod 2N,
+# rounded half away from zero; a value within TIE_BAND of a half-integer is taken
+# as that half-integer.  The sum is evaluated in double-double arithmetic (about
+# 106 bits), whose error is many orders of magnitude below the band, so the
+# integer is the one the exact value gives.
+
+TIE_BAND = 2.0 ** -20
+
 
 def round_half_away(x: np.ndarray) -> np.ndarray:
     return np.sign(x) * np.floor(np.abs(x) + 0.5)
@@ -370,35 +380,216 @@ def slot_exponents(n: int) -> np.ndarray:
     return e
 
 
-def encode_real(n: int, z, scale: float) -> np.ndarray:
-    """Slots -> signed integer coefficients:
-    m_i = (2/N) Re(sum_j z_j zeta^(-i e_j)), c_i = round(scale * m_i).
-    The sum is taken with a length-2N FFT of the scattered slots."""
+# ---- double-double arithmetic: a value is the unevaluated sum hi + lo of two doubles
+# (Dekker 1971; Knuth, TAOCP vol. 2, 4.2.2).  Each step is one IEEE double operation
+# rounded once (numpy never fuses a product into a sum).
+
+def _two_sum(a, b):
+    s = a + b
+    bb = s - a
+    return s, (a - (s - bb)) + (b - bb)
+
+
+def _fast_two_sum(a, b):  # |a| >= |b|
+    s = a + b
+    return s, b - (s - a)
+
+
+def _split(a):
+    c = 134217729.0 * a  # 2^27 + 1
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def _two_prod(a, b):
+    p = a * b
+    ah, al = _split(a)
+    bh, bl = _split(b)
+    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
+
+
+def dd_add(x, y):
+    s, e = _two_sum(x[0], y[0])
+    t, f = _two_sum(x[1], y[1])
+    s, e = _fast_two_sum(s, e + t)
+    return _fast_two_sum(s, e + f)
+
+
+def dd_neg(x):
+    return -x[0], -x[1]
+
+
+def dd_mul(x, y):
+    p, e = _two_prod(x[0], y[0])
+    return _fast_two_sum(p, e + (x[0] * y[1] + x[1] * y[0]))
+
+
+def dd_mul_double(x, d):
+    p, e = _two_prod(x[0], d)
+    return _fast_two_sum(p, e + x[1] * d)
+
+
+# ---- roots of unity from a 45-digit decimal evaluation
+
+def _decimal_pi(ctx):
+    """pi by Machin's formula 16 atan(1/5) - 4 atan(1/239), in the given decimal context."""
+    from decimal import Decimal
+
+    def atan_inv(k):
+        x = Decimal(1) / k
+        x2 = x * x
+        term, total, n = x, x, 1
+        eps = Decimal(10) ** -(ctx.prec + 2)
+        while abs(term) > eps:
+            term = -term * x2
+            n += 2
+            total += term / n
+        return total
+
+    return 16 * atan_inv(5) - 4 * atan_inv(239)
+
+
+def _decimal_cos_sin(phi, ctx):
+    """Taylor series of cos and sin at |phi| <= pi/4."""
+    from decimal import Decimal
+
+    eps = Decimal(10) ** -(ctx.prec + 2)
+    c, s = Decimal(1), phi
+    term_c, term_s, k = Decimal(1), phi, 0
+    p2 = phi * phi
+    while abs(term_c) > eps or abs(term_s) > eps:
+        term_c = -term_c * p2 / ((2 * k + 1) * (2 * k + 2))
+        term_s = -term_s * p2 / ((2 * k + 2) * (2 * k + 3))
+        c += term_c
+        s += term_s
+        k += 1
+    return c, s
+
+
+def _to_dd(d):
+    from decimal import Decimal
+
+    hi = float(d)
+    return hi, float(d - Decimal(hi))
+
+
+_ROOTS: dict = {}
+
+
+def roots_dd(m: int):
+    """w^k = exp(-2 pi i k / m) for k < m/2 as double-double (re, im) arrays: cos and sin of
+    2 pi k/m evaluated in 45-digit decimal arithmetic by Taylor series after reduction to an
+    angle of at most pi/4 (k = m/8 is pi/4), then rounded to double-double."""
+    if m in _ROOTS:
+        return _ROOTS[m]
+    from decimal import Context
+
+    dctx = Context(prec=45)
+    pi = _decimal_pi(dctx)
+    m8 = m // 8
+    table = [_decimal_cos_sin(dctx.multiply(pi, dctx.divide(2 * j, m)), dctx) for j in range(m8 + 1)]
+    re_h, re_l, im_h, im_l = (np.empty(m // 2) for _ in range(4))
+    for k in range(m // 2):
+        if k <= m8:
+            c, s = table[k]
+        elif k <= 2 * m8:
+            s, c = table[2 * m8 - k]
+        elif k <= 3 * m8:
+            s, c = table[k - 2 * m8]
+            c = -c
+        else:
+            c, s = table[4 * m8 - k]
+            c = -c
+        re_h[k], re_l[k] = _to_dd(c)
+        im_h[k], im_l[k] = _to_dd(-s)  # exp(-i theta) = cos theta - i sin theta
+    _ROOTS[m] = ((re_h, re_l), (im_h, im_l))
+    return _ROOTS[m]
+
+
+def fft_dd(re, im):
+    """Unnormalised DFT X_i = sum_k a_k exp(-2 pi i ik/m) along the last axis, double-double
+    complex values given as (hi, lo) pairs of arrays; radix-2 decimation in frequency
+    (Gentleman-Sande) with natural-order input, result returned in natural order."""
+    m = re[0].shape[-1]
+    (wr_h, wr_l), (wi_h, wi_l) = roots_dd(m)
+    lead = re[0].shape[:-1]
+    x = [a.copy() for a in (re[0], re[1], im[0], im[1])]
+    h = m // 2
+    while h >= 1:
+        blocks = m // (2 * h)
+        v = [a.reshape(lead + (blocks, 2, h)) for a in x]
+        a_re = (v[0][..., 0, :], v[1][..., 0, :])
+        a_im = (v[2][..., 0, :], v[3][..., 0, :])
+        b_re = (v[0][..., 1, :], v[1][..., 1, :])
+        b_im = (v[2][..., 1, :], v[3][..., 1, :])
+        step = m // (2 * h)
+        w_re = (wr_h[: h * step : step], wr_l[: h * step : step])
+        w_im = (wi_h[: h * step : step], wi_l[: h * step : step])
+        s_re, s_im = dd_add(a_re, b_re), dd_add(a_im, b_im)
+        d_re, d_im = dd_add(a_re, dd_neg(b_re)), dd_add(a_im, dd_neg(b_im))
+        t_re = dd_add(dd_mul(d_re, w_re), dd_neg(dd_mul(d_im, w_im)))
+        t_im = dd_add(dd_mul(d_re, w_im), dd_mul(d_im, w_re))
+        out = [np.empty_like(a) for a in v]
+        for o, top, bot in zip(out, (s_re[0], s_re[1], s_im[0], s_im[1]), (t_re[0], t_re[1], t_im[0], t_im[1])):
+            o[..., 0, :] = top
+            o[..., 1, :] = bot
+        x = [o.reshape(lead + (m,)) for o in out]
+        h //= 2
+    bits = m.bit_length() - 1
+    rev = np.array([int(format(i, "0%db" % bits)[::-1], 2) for i in range(m)])
+    return (x[0][..., rev], x[1][..., rev]), (x[2][..., rev], x[3][..., rev])
+
+
+def encode_real_coeffs(n: int, z) -> tuple:
+    """m_i = (2/N) sum_j z_j cos(pi (i e_j mod 2N)/N) for i < N, as double-double arrays
+    (hi, lo) of shape z.shape[:-1] + (N,): the encoding before the scale.  z: real slots
+    (last axis, at most N/2, zero-padded)."""
+    z = np.asarray(z, dtype=np.float64)
+    lead = z.shape[:-1]
     s = n // 2
-    zz = np.zeros(s, dtype=np.complex128)
-    z = np.asarray(z)
-    zz[: z.size] = z
+    zz = np.zeros(lead + (s,))
+    zz[..., : z.shape[-1]] = z
     e = slot_exponents(n)
-    big = np.zeros(2 * n, dtype=np.complex128)
-    big[e] = zz
-    big[(2 * n - e) % (2 * n)] = np.conj(zz)
-    m = np.fft.fft(big)[:n].real / n
-    c = round_half_away(m * scale)
-    if np.max(np.abs(c)) >= 2.0 ** 62:
+    big = np.zeros(lead + (2 * n,))
+    big[..., e] = zz
+    big[..., (2 * n - e) % (2 * n)] = zz  # the conjugate of a real slot
+    zero = np.zeros_like(big)
+    (xr_h, xr_l), _ = fft_dd((big, zero), (zero, zero))
+    return xr_h[..., :n] / n, xr_l[..., :n] / n  # division by a power of two is exact
+
+
+def round_dd(x) -> np.ndarray:
+    """Round hi + lo half away from zero (int64), a value within TIE_BAND of a half-integer
+    taken as the half-integer.  Integer and fractional parts are split from each word exactly."""
+    hi, lo = np.asarray(x[0], dtype=np.float64), np.asarray(x[1], dtype=np.float64)
+    if np.any(~np.isfinite(hi)) or np.max(np.abs(hi), initial=0.0) >= 2.0 ** 62:
         raise OverflowError("encoded coefficient exceeds 2^62")
-    return c.astype(np.int64)
+    r1, r2 = np.rint(hi), np.rint(lo)
+    d = (hi - r1) + (lo - r2)  # both differences exact; |d| <= 1
+    base = r1.astype(np.int64) + r2.astype(np.int64)
+    tie = np.abs(np.abs(d) - 0.5) <= TIE_BAND
+    up = np.where(tie, d > 0, d > 0.5)
+    down = np.where(tie, d < 0, d < -0.5)
+    c = base + up.astype(np.int64) - down.astype(np.int64)
+    # a tie x = base + sign(d)/2 rounds away from zero: toward +inf above zero, -inf below
+    neg_tie_up = tie & (d > 0) & (base < 0)    # x = base + 1/2 < 0: goes to base
+    pos_tie_dn = tie & (d < 0) & (base > 0)    # x = base - 1/2 > 0: goes to base
+    c = c - neg_tie_up.astype(np.int64) + pos_tie_dn.astype(np.int64)
+    if np.max(np.abs(c), initial=0) >= 2 ** 62:
+        raise OverflowError("encoded coefficient exceeds 2^62")
+    return c
 
 
-def encode_direct(n: int, z, scale: float) -> np.ndarray:
-    """Same map as encode_real, as the O(N^2) sum of the definition (pins)."""
-    s = n // 2
-    zz = np.zeros(s, dtype=np.complex128)
-    zz[: np.asarray(z).size] = z
-    e = slot_exponents(n)
-    i = np.arange(n)
-    ang = np.pi * np.outer(i, e) / n
-    m = (2.0 / n) * (np.cos(ang) @ zz.real + np.sin(ang) @ zz.imag)
-    return round_half_away(m * scale).astype(np.int64)
+def scale_round(m, scale: float) -> np.ndarray:
+    """c_i = round(scale * m_i) under the rule of round_dd, m a double-double array."""
+    return round_dd(dd_mul_double(m, float(scale)))
+
+
+def encode_real(n: int, z, scale: float) -> np.ndarray:
+    """Slots -> signed integer coefficients (Ecd): c_i = round(scale * m_i) with m_i the
+    exact canonical-embedding coefficient (see the section comment).  z may carry leading
+    batch axes."""
+    return scale_round(encode_real_coeffs(n, z), scale)
 
 
 def decode(n: int, coeffs: np.ndarray, scale: float) -> np.ndarray:

@@ -49,15 +49,99 @@ def test_samplers():
     assert all(abs(np.mean(small == v) - 1 / 7) < 0.01 for v in range(7))
 
 
-@pytest.mark.parametrize("log_n", [5, 8])
-def test_encoding_matches_definition(log_n):
+def exact_encoding(n, z, scale, band=2.0 ** -20):
+    """The encoding straight from its definition in 60-digit arithmetic (mpmath): x_i =
+    scale * (2/N) * sum_j z_j cos(pi (i e_j mod 2N) / N), rounded half away from zero, a
+    value within `band` of a half-integer counted as the half-integer."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 60
+    e = [pow(5, j, 2 * n) for j in range(n // 2)]
+    cos_t = [mp.cos(mp.pi * t / n) for t in range(2 * n)]
+    zs = [(j, mp.mpf(float(v))) for j, v in enumerate(z) if v != 0]
+    half, out = mp.mpf(1) / 2, []
+    for i in range(n):
+        acc = mp.mpf(0)
+        for j, v in zs:
+            acc += v * cos_t[(i * e[j]) % (2 * n)]
+        x = mp.mpf(float(scale)) * 2 * acc / n
+        f = mp.floor(x)
+        frac = x - f
+        if abs(frac - half) <= band:
+            r = f + 1 if x > 0 else f
+        else:
+            r = f + 1 if frac > half else f
+        out.append(int(r))
+    return np.array(out, dtype=np.int64)
+
+
+def _encoding_cases(n):
+    rng = np.random.default_rng(n)
+    s = n // 2
+    masks = np.zeros(s)
+    masks[rng.choice(s, s // 3, replace=False)] = 1.0
+    yield rng.uniform(-1, 1, s), 2.0 ** 30
+    yield rng.uniform(-1, 1, s), 2.0 ** 45
+    yield rng.uniform(-1, 1, s), float(C.find_primes(int(math.log2(n)), [60])[0])
+    yield masks, float(C.find_primes(int(math.log2(n)), [45])[0])
+    yield np.repeat(masks[: s // 4], 4), float(C.find_primes(int(math.log2(n)), [40])[0])
+    # exact ties: a quarter of the slots set makes x_0 = scale/2, a half-integer for odd scales
+    tie = np.zeros(s)
+    tie[: n // 4] = 1.0
+    yield tie, float(2 ** 45 - 1)
+    yield -tie, float(2 ** 45 - 1)
+
+
+@pytest.mark.parametrize("log_n", [4, 6, 8])
+def test_encoding_is_the_exactly_rounded_definition(log_n):
     n = 1 << log_n
-    rng = np.random.default_rng(log_n)
-    z = rng.uniform(-1, 1, n // 2)
-    a = C.encode_real(n, z, 2.0 ** 30)
-    b = C.encode_direct(n, z, 2.0 ** 30)
-    assert np.abs(a - b).max() <= 1
+    for z, scale in _encoding_cases(n):
+        want = exact_encoding(n, z, scale)
+        got = C.encode_real(n, z, scale)
+        assert np.array_equal(got, want), (log_n, scale, np.flatnonzero(got != want)[:8])
+
+
+def test_encoding_ties_round_away_from_zero():
+    n = 1 << 6
+    tie = np.zeros(n // 2)
+    tie[: n // 4] = 1.0
+    scale = float(2 ** 45 - 1)  # x_0 = scale / 2 exactly
+    assert C.encode_real(n, tie, scale)[0] == 2 ** 44
+    assert C.encode_real(n, -tie, scale)[0] == -(2 ** 44)
+    # one slot at scale 12 on N = 16: x_0 = 12 * (2/16) = 1.5 -> 2, and -1.5 -> -2
+    z = np.zeros(8)
+    z[0] = 1.0
+    assert C.encode_real(16, z, 12.0)[0] == 2 and C.encode_real(16, -z, 12.0)[0] == -2
+    # the band: the double-double rounding rule on values near, in and past it
+    hi = np.array([2.5, 2.5, 2.5, -2.5, 7.0, 2.0 ** 53])
+    lo = np.array([0.0, 2.0 ** -22, 2.0 ** -19, -(2.0 ** -22), 0.4999, 0.75])
+    assert list(C.round_dd((hi, lo))) == [3, 3, 3, -3, 7, 2 ** 53 + 1]
+    assert list(C.round_dd((np.array([2.5]), np.array([-(2.0 ** -19)])))) == [2]
+
+
+def test_encoding_fft_matches_direct_double_double_sum():
+    """At N = 2^11 the FFT-based encoder equals the O(N^2) sum of the definition, also taken
+    in double-double (same roots table, no FFT), coefficient for coefficient."""
+    n = 1 << 11
+    z = np.random.default_rng(11).uniform(-1, 1, n // 2)
+    e = C.slot_exponents(n)
+    (cr_h, cr_l), _ = C.roots_dd(4 * n)  # cos(2 pi k / 4N) = cos(pi k / 2N), k < 2N
+    cos_h = np.concatenate([cr_h[0::2], -cr_h[0::2]])  # cos(pi t / N), t < 2N
+    cos_l = np.concatenate([cr_l[0::2], -cr_l[0::2]])
+    i = np.arange(n)
+    acc = (np.zeros(n), np.zeros(n))
+    for j in range(n // 2):
+        t = (i * int(e[j])) % (2 * n)
+        acc = C.dd_add(acc, C.dd_mul_double((cos_h[t], cos_l[t]), z[j]))
+    m = (acc[0] * (2.0 / n), acc[1] * (2.0 / n))
+    for scale in (2.0 ** 45, float(C.find_primes(11, [60])[0])):
+        assert np.array_equal(C.scale_round(m, scale), C.encode_real(n, z, scale))
+
+
+def test_encoding_matches_polynomial_evaluation():
     # evaluating the integer polynomial at zeta^(5^j) (numpy polyval) gives back the slots
+    n = 1 << 8
+    z = np.random.default_rng(8).uniform(-1, 1, n // 2)
+    a = C.encode_real(n, z, 2.0 ** 30)
     zeta = np.exp(1j * np.pi / n)
     for j in range(n // 2):
         x = zeta ** pow(5, j, 2 * n)
