@@ -190,6 +190,35 @@ def run_reference(args, world, rank):
 
 # ---- GPU arm ----------------------------------------------------------------------------
 
+def other_metrics(args):
+    """The rest of the headline metric in compact, time-bounded form, each with its own clocks:
+    the NTT alone (N=2^14, 1600 limbs, forward and inverse GB/s), the config-2 composite sign
+    (64 ciphertexts, 3 timed steps) and a short serving stream (300 requests at 0.8x capacity)."""
+    out = {}
+    ns = argparse.Namespace(**vars(args))
+    ns.log_n, ns.rows, ns.steps, ns.warmup, ns.tiles = 14, 1600, 5, 3, None
+    m = run_micro(ns)
+    out["ntt_micro"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in m.items()
+                        if k in ("log_n", "rows", "tiles", "fwd_ms", "inv_ms", "fwd_gbs", "inv_gbs", "fwd_frac",
+                                 "inv_frac", "fwd_alu_frac", "inv_alu_frac", "peak_gbs", "peak_kind", "clocks")}
+    out["ntt_micro"]["what"] = "forward / inverse NTT of 1600 limbs of N=2^14 (210 MB, > L2) in place; " \
+                               "CUDA events, median of 5"
+    ns = argparse.Namespace(**vars(args))
+    ns.steps, ns.warmup, ns.relu, ns.alpha = 3, 1, False, None
+    sg = run_sign(ns)
+    out["sign_cfg2"] = {k: sg[k] for k in ("value", "unit", "ms_per_step", "steps", "max_err_vs_exact",
+                                            "max_err_vs_fp64_composite", "clocks", "kernel_shares")}
+    out["sign_cfg2"]["what"] = sg["metric"] + "; " + sg["config"]["workload"]
+    ns = argparse.Namespace(**vars(args))
+    ns.requests, ns.load, ns.lanes, ns.max_batch, ns.full, ns.sweep = 300, 0.8, 4, 16, False, False
+    sv = run_serve(ns)
+    out["serve"] = {"p50_ms": sv["value"], "p99_ms": sv["p99_ms"], "throughput_req_s": sv["throughput_req_s"],
+                    "offered_req_s": sv["offered_req_s"], "capacity_req_s": sv["capacity_req_s"],
+                    "requests": sv["requests"], "clocks": sv["clocks"],
+                    "what": "serving stream, " + sv["config"]["workload"]}
+    return out
+
+
 def run_hx(args, world, rank, local):
     import torch
 
@@ -402,6 +431,8 @@ def run_hx(args, world, rank, local):
         hx.hx_ct_destroy(x)
     hx.hx_keyset_destroy(ks)
     hx.hx_context_destroy(ctx)
+    if rank == 0 and world == 1 and not args.no_extras:
+        line.update(other_metrics(args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         state = oracle_setup()
         t = oracle_step(state)
@@ -495,9 +526,9 @@ def run_sign(args):
                        "primes_per_digit": alpha or 3},
             "max_err_vs_exact": max(errs_sgn), "max_err_vs_fp64_composite": max(errs_g), "clocks": clocks,
             "kernel_shares": shares, "kernel_ms_profiled": round(total_ms, 2)}
-    print(json.dumps(line), flush=True)
     hx.hx_keyset_destroy(ks)
     hx.hx_context_destroy(ctx)
+    return line
 
 
 def run_dense(args):
@@ -749,7 +780,7 @@ def run_serve(args):
     stats = hx.hx_server_stats(sv)
     # the same request stream at other offered loads (below, near and above capacity)
     sweep = []
-    for load in (0.5, 0.9, 1.1):
+    for load in ((0.5, 0.9, 1.1) if getattr(args, "sweep", True) else ()):
         lt, rt, el = open_loop(load, reqs[n_cap:])
         Ls = np.array(sorted(lt.values()))
         sweep.append({"load": load, "offered_req_s": round(rt, 2), "throughput_req_s": round(len(Ls) / el, 2),
@@ -775,7 +806,6 @@ def run_serve(args):
                        "setup_s": round(setup_s, 1)},
             "server": stats, "clocks": clocks, "load_sweep": sweep,
             "plan_cache": {str(2 ** ln): hx.hx_context_plan_cache_info(ctxs[ln][0]) for ln in log_ns}}
-    print(json.dumps(line), flush=True)
     for entries in pools.values():
         for e in entries:
             for h in (e if isinstance(e, tuple) else (e,)):
@@ -783,6 +813,7 @@ def run_serve(args):
     for ln in log_ns:
         hx.hx_keyset_destroy(keys[ln])
         hx.hx_context_destroy(ctxs[ln][0])
+    return line
 
 
 def run_micro(args):
@@ -812,6 +843,7 @@ def run_micro(args):
         hx.hx_ntt(ctx, x.data_ptr(), polys, idx, True, stream)
     torch.cuda.synchronize()
     fw, iv = [], []
+    sampler = ClockSampler()
     for _ in range(args.steps):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
@@ -822,21 +854,22 @@ def run_micro(args):
         torch.cuda.synchronize()
         fw.append(e[0].elapsed_time(e[1]))
         iv.append(e[1].elapsed_time(e[2]))
+    clocks = sampler.stop()
     byt = 16.0 * polys * per * n
     peak, kind = peaks()
     shoup_s, _ = hx.hx_alu_calibrate(ctx, stream=stream)
     res = {"micro": "ntt", "log_n": log_n, "rows": polys * per, "bytes_per_transform": byt, "tiles": tiles,
            "fwd_ms": statistics.median(fw), "inv_ms": statistics.median(iv),
            "fwd_gbs": byt / statistics.median(fw) / 1e6, "inv_gbs": byt / statistics.median(iv) / 1e6,
-           "peak_gbs": peak, "peak_kind": kind}
+           "peak_gbs": peak, "peak_kind": kind, "clocks": clocks}
     res["fwd_frac"] = res["fwd_gbs"] / peak
     res["inv_frac"] = res["inv_gbs"] / peak
     # integer-issue ceiling: butterflies/s against measured Shoup products/s
     res["shoup_products_per_s"] = shoup_s
     res["fwd_alu_frac"] = res["fwd_gbs"] * 1e9 * log_n / 32.0 / shoup_s
     res["inv_alu_frac"] = res["inv_gbs"] * 1e9 * log_n / 32.0 / shoup_s
-    print(json.dumps(res), flush=True)
     hx.hx_context_destroy(ctx)
+    return res
 
 
 def run_rmatmul(args):
@@ -1121,6 +1154,8 @@ def main():
     ap.add_argument("--impl", default="hx", choices=["hx", "reference"])
     ap.add_argument("--per-op-pairs", type=int, default=4)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default line without the NTT, sign and serving sub-records")
     args = ap.parse_args()
     if args.micro == "aggregate":
         return run_micro_aggregate(args)
@@ -1129,11 +1164,11 @@ def main():
     if args.micro == "ntt-multi":
         return run_micro_ntt_multi(args)
     if args.micro:
-        return run_micro(args)
+        return print(json.dumps(run_micro(args)), flush=True)
     if args.workload == "sign":
-        return run_sign(args)
+        return print(json.dumps(run_sign(args)), flush=True)
     if args.workload == "serve":
-        return run_serve(args)
+        return print(json.dumps(run_serve(args)), flush=True)
     if args.workload == "dense":
         return run_dense(args)
     if args.workload == "rmatmul":

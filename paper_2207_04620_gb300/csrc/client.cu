@@ -1,13 +1,16 @@
 // Client-side encoding and encryption of a batch on the device (Fig. 1 items 3
-// and 5): the canonical-embedding encoder as a batched 2N-point FP64 FFT and
-// the encryption randomness drawn from the same counter-based SplitMix64
-// streams as the host path, so every ciphertext equals hx_encrypt's.
+// and 5): the canonical-embedding encoder as a batched 2N-point FFT in
+// double-double arithmetic and the encryption randomness drawn from the same
+// counter-based SplitMix64 streams as the host path, so every ciphertext equals
+// hx_encrypt's.
 //
-// The FFT repeats the host encoder's arithmetic operation for operation
-// (bit-reversed placement, radix-2 decimation in time, the host's table of
-// 2N-th roots, products and sums rounded one at a time with the _rn
-// intrinsics, no fused multiply-add), which makes the two encoders agree bit
-// for bit.
+// Encoding is exact: coefficient i is scale * (2/N) * sum_j z_j cos(pi (i e_j
+// mod 2N)/N) rounded half away from zero (a value within 2^-20 of a
+// half-integer taken as that half-integer).  The sum is carried in
+// double-double numbers (about 106 bits; exact products by fused multiply-add,
+// Knuth's two-sum), so its error is far inside that band and the integer is the
+// one the exact value gives -- the host encoder's, whatever the order of the
+// operations.
 #include "runtime.h"
 
 namespace hx {
@@ -24,48 +27,112 @@ __device__ __forceinline__ uint64_t dmix64(uint64_t z)
     return z ^ (z >> 31);
 }
 
-__device__ __forceinline__ double2 cmul(double2 a, double2 w)
+// ---- double-double arithmetic, every operation rounded once (explicit _rn intrinsics: no
+// contraction by the compiler)
+struct ddv {
+    double hi, lo;
+};
+
+__device__ __forceinline__ ddv dd_two_sum(double a, double b)
 {
-    return make_double2(__dsub_rn(__dmul_rn(a.x, w.x), __dmul_rn(a.y, w.y)),
-                        __dadd_rn(__dmul_rn(a.x, w.y), __dmul_rn(a.y, w.x)));
+    const double s = __dadd_rn(a, b), v = __dsub_rn(s, a);
+    return ddv{s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, v)), __dsub_rn(b, v))};
 }
 
-__device__ __forceinline__ void butterfly(double2 &u, double2 &v, double2 w)
+__device__ __forceinline__ ddv dd_fast(double a, double b)
 {
-    const double2 t = cmul(v, w);
-    const double2 a = u;
-    u = make_double2(__dadd_rn(a.x, t.x), __dadd_rn(a.y, t.y));
-    v = make_double2(__dsub_rn(a.x, t.x), __dsub_rn(a.y, t.y));
+    const double s = __dadd_rn(a, b);
+    return ddv{s, __dsub_rn(b, __dsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ddv dd_plus(ddv x, ddv y)
+{
+    const ddv s = dd_two_sum(x.hi, y.hi), t = dd_two_sum(x.lo, y.lo);
+    const ddv u = dd_fast(s.hi, __dadd_rn(s.lo, t.hi));
+    return dd_fast(u.hi, __dadd_rn(u.lo, t.lo));
+}
+
+__device__ __forceinline__ ddv dd_minus(ddv x, ddv y) { return dd_plus(x, ddv{-y.hi, -y.lo}); }
+
+__device__ __forceinline__ ddv dd_times(ddv x, ddv y)
+{
+    const double p = __dmul_rn(x.hi, y.hi);
+    const double e = __fma_rn(x.hi, y.hi, -p);  // exact error of the leading product
+    const double c = __fma_rn(x.hi, y.lo, __dmul_rn(x.lo, y.hi));
+    return dd_fast(p, __dadd_rn(e, c));
+}
+
+__device__ __forceinline__ ddv dd_times_d(ddv x, double d)
+{
+    const double p = __dmul_rn(x.hi, d);
+    return dd_fast(p, __fma_rn(x.lo, d, __fma_rn(x.hi, d, -p)));
+}
+
+// a complex double-double point: (re.hi, re.lo, im.hi, im.lo)
+__device__ __forceinline__ void butterfly(double4 &u, double4 &v, const double4 w)
+{
+    const ddv vr{v.x, v.y}, vi{v.z, v.w}, wr{w.x, w.y}, wi{w.z, w.w};
+    const ddv tr = dd_minus(dd_times(vr, wr), dd_times(vi, wi));
+    const ddv ti = dd_plus(dd_times(vr, wi), dd_times(vi, wr));
+    const ddv ur{u.x, u.y}, ui{u.z, u.w};
+    const ddv a = dd_plus(ur, tr), b = dd_plus(ui, ti), c = dd_minus(ur, tr), d = dd_minus(ui, ti);
+    u = make_double4(a.hi, a.lo, b.hi, b.lo);
+    v = make_double4(c.hi, c.lo, d.hi, d.lo);
+}
+
+// hi + lo rounded half away from zero, |value - (k + 1/2)| <= 2^-20 counting as the tie;
+// *bad set past 2^62
+__device__ __forceinline__ int64_t round_coeff(ddv x, int *bad)
+{
+    if (!(fabs(x.hi) < 4611686018427387904.0)) {
+        *bad = 1;
+        return 0;
+    }
+    const double i1 = rint(x.hi), i2 = rint(x.lo);
+    const double f = __dadd_rn(__dsub_rn(x.hi, i1), __dsub_rn(x.lo, i2));
+    int64_t k = (int64_t)i1 + (int64_t)i2;
+    const double g = fabs(f);
+    if (fabs(__dsub_rn(g, 0.5)) <= 0x1p-20) {
+        // tie at k + 1/2 (f > 0) or k - 1/2 (f < 0): away from zero
+        if (f > 0) k += (k >= 0) ? 1 : 0;
+        else k -= (k <= 0) ? 1 : 0;
+    } else if (f > 0.5) {
+        k += 1;
+    } else if (f < -0.5) {
+        k -= 1;
+    }
+    if (k >= (int64_t(1) << 62) || k <= -(int64_t(1) << 62)) *bad = 1;
+    return k;
 }
 
 // slot j of vector b goes to the bit-reversed positions of exponents e_j and 2N - e_j
-__global__ void k_enc_place(double2 *A, const double *slots, size_t n_slots, const int *e, int log_m, int half_n)
+__global__ void k_enc_place(double4 *A, const double *slots, size_t n_slots, const int *e, int log_m, int half_n)
 {
     const int b = blockIdx.y;
     const int m = 1 << log_m;
-    double2 *a = A + (size_t)b * m;
+    double4 *a = A + (size_t)b * m;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < half_n; j += gridDim.x * blockDim.x) {
         const double z = (size_t)j < n_slots ? slots[(size_t)b * n_slots + j] : 0.0;
         const unsigned p1 = __brev((unsigned)e[j]) >> (32 - log_m);
         const unsigned p2 = __brev((unsigned)((m - e[j]) & (m - 1))) >> (32 - log_m);
-        a[p1] = make_double2(z, 0.0);
-        a[p2] = make_double2(z, 0.0);
+        a[p1] = make_double4(z, 0.0, 0.0, 0.0);
+        a[p2] = make_double4(z, 0.0, 0.0, 0.0);
     }
 }
 
-// stages len = 2 .. kFftTile on contiguous tiles in shared memory
-__global__ void __launch_bounds__(kFftTile / 2) k_enc_fft_tile(double2 *A, const double2 *__restrict__ roots, int log_m)
+// stages len = 2 .. kFftTile (radix-2 decimation in time) on contiguous tiles in shared memory
+__global__ void __launch_bounds__(kFftTile / 2) k_enc_fft_tile(double4 *A, const double4 *__restrict__ roots, int log_m)
 {
-    __shared__ double2 s[kFftTile];
+    __shared__ double4 s[kFftTile];
     const int m = 1 << log_m;
-    double2 *a = A + (size_t)blockIdx.y * m + (size_t)blockIdx.x * kFftTile;
+    double4 *a = A + (size_t)blockIdx.y * m + (size_t)blockIdx.x * kFftTile;
     for (int i = threadIdx.x; i < kFftTile; i += blockDim.x) s[i] = a[i];
     __syncthreads();
     for (int len = 2; len <= kFftTile; len <<= 1) {
         const int half = len >> 1, step = m / len;
         for (int t = threadIdx.x; t < kFftTile / 2; t += blockDim.x) {
             const int g = t / half, k = t % half, i = g * len + k;
-            double2 u = s[i], v = s[i + half];
+            double4 u = s[i], v = s[i + half];
             butterfly(u, v, roots[(size_t)k * step]);
             s[i] = u;
             s[i + half] = v;
@@ -76,64 +143,56 @@ __global__ void __launch_bounds__(kFftTile / 2) k_enc_fft_tile(double2 *A, const
 }
 
 // one later stage (len > kFftTile) over global memory
-__global__ void k_enc_fft_stage(double2 *A, const double2 *__restrict__ roots, int log_m, int len)
+__global__ void k_enc_fft_stage(double4 *A, const double4 *__restrict__ roots, int log_m, int len)
 {
     const int m = 1 << log_m, half = len >> 1, step = m / len;
-    double2 *a = A + (size_t)blockIdx.y * m;
+    double4 *a = A + (size_t)blockIdx.y * m;
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m / 2; t += gridDim.x * blockDim.x) {
         const int g = t / half, k = t % half, i = g * len + k;
-        double2 u = a[i], v = a[i + half];
+        double4 u = a[i], v = a[i + half];
         butterfly(u, v, roots[(size_t)k * step]);
         a[i] = u;
         a[i + half] = v;
     }
 }
 
-__device__ __forceinline__ double round_half_away_d(double x)
-{
-    const double r = floor(__dadd_rn(fabs(x), 0.5));
-    return x < 0 ? -r : r;
-}
-
-// coefficient i = round(Re A_i / N * scale); |coefficient| >= 2^62 sets *err
-__global__ void k_enc_round(int64_t *out, size_t out_stride, const double2 *A, int log_m, int n, double scale,
+// coefficient i = round(Re A_i / N * scale) under round_coeff; a coefficient past 2^62 sets *err
+__global__ void k_enc_round(int64_t *out, size_t out_stride, const double4 *A, int log_m, int n, double scale,
                             int *err)
 {
     const int b = blockIdx.y;
-    const double2 *a = A + ((size_t)b << log_m);
+    const double4 *a = A + ((size_t)b << log_m);
+    const double inv_n = 1.0 / n;  // a power of two: exact
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double v = round_half_away_d(__dmul_rn(__ddiv_rn(a[i].x, (double)n), scale));
-        if (!(fabs(v) < 4611686018427387904.0)) {
-            atomicExch(err, 1);
-            out[b * out_stride + i] = 0;
-        } else {
-            out[b * out_stride + i] = (int64_t)v;
-        }
+        int bad = 0;
+        const ddv m{__dmul_rn(a[i].x, inv_n), __dmul_rn(a[i].y, inv_n)};
+        const int64_t v = round_coeff(dd_times_d(m, scale), &bad);
+        if (bad) atomicExch(err, 1);
+        out[b * out_stride + i] = bad ? 0 : v;
     }
 }
 
-// the encoder's real coefficients m_i = Re(a_i) / n, before the scale (k_enc_round's quotient)
-__global__ void k_enc_real(double *m, size_t m_stride, const double2 *A, int log_m, int n)
+// the encoder's real coefficients m_i = Re(a_i) / n (double-double), before the scale
+__global__ void k_enc_real(double2 *m, size_t m_stride, const double4 *A, int log_m, int n)
 {
     const int b = blockIdx.y;
-    const double2 *a = A + ((size_t)b << log_m);
+    const double4 *a = A + ((size_t)b << log_m);
+    const double inv_n = 1.0 / n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        m[b * m_stride + i] = __ddiv_rn(a[i].x, (double)n);
+        m[b * m_stride + i] = make_double2(__dmul_rn(a[i].x, inv_n), __dmul_rn(a[i].y, inv_n));
 }
 
-// out row r = round_half_away(m[idx[r]] * scale): k_enc_round's last two steps on cached quotients
-__global__ void k_enc_round_rows(int64_t *out, const double *m, const int *idx, int n, double scale, int *err)
+// out row r = round(m[idx[r]] * scale): k_enc_round's last steps on cached coefficients
+__global__ void k_enc_round_rows(int64_t *out, const double2 *m, const int *idx, int n, double scale, int *err)
 {
     const int r = blockIdx.y;
-    const double *mr = m + (size_t)idx[r] * n;
+    const double2 *mr = m + (size_t)idx[r] * n;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double v = round_half_away_d(__dmul_rn(mr[i], scale));
-        if (!(fabs(v) < 4611686018427387904.0)) {
-            atomicExch(err, 1);
-            out[(size_t)r * n + i] = 0;
-        } else {
-            out[(size_t)r * n + i] = (int64_t)v;
-        }
+        int bad = 0;
+        const double2 v = mr[i];
+        const int64_t c = round_coeff(dd_times_d(ddv{v.x, v.y}, scale), &bad);
+        if (bad) atomicExch(err, 1);
+        out[(size_t)r * n + i] = bad ? 0 : c;
     }
 }
 
@@ -168,8 +227,16 @@ const EncTables &enc_tables(hx_context &ctx)
     std::call_once(ctx.enc_once, [&] {
         const int N = ctx.N;
         EncTables &t = ctx.enc_dev;
-        t.roots = std::make_shared<DevBuf>((size_t)2 * N, true);
-        HX_CUDA(cudaMemcpy(t.roots->p, ctx.enc->roots.data(), sizeof(double) * 2 * N, cudaMemcpyHostToDevice));
+        // the host encoder's double-double roots e^(-2 pi i k / 2N), k < N, as (re.hi, re.lo, im.hi, im.lo)
+        std::vector<double> r4((size_t)4 * N);
+        for (int k = 0; k < N; k++) {
+            r4[4 * k] = ctx.enc->roots_re[k].hi;
+            r4[4 * k + 1] = ctx.enc->roots_re[k].lo;
+            r4[4 * k + 2] = ctx.enc->roots_im[k].hi;
+            r4[4 * k + 3] = ctx.enc->roots_im[k].lo;
+        }
+        t.roots = std::make_shared<DevBuf>((size_t)4 * N, true);
+        HX_CUDA(cudaMemcpy(t.roots->p, r4.data(), sizeof(double) * r4.size(), cudaMemcpyHostToDevice));
         std::vector<int> e32(N / 2);
         for (int j = 0; j < N / 2; j++) e32[j] = (int)ctx.enc->e[j];
         t.e = std::make_shared<DevBuf>((size_t)(N / 2 + 1) / 2, true);
@@ -182,6 +249,25 @@ const EncTables &enc_tables(hx_context &ctx)
     return ctx.enc_dev;
 }
 
+// the 2N-point transforms of `count` slot vectors, in place in A ([count][2N] complex double-double)
+void enc_transform(hx_context &ctx, const EncTables &t, double4 *a, const double *slots_dev, size_t n_slots,
+                          int count, cudaStream_t s)
+{
+    const int N = ctx.N, log_m = ctx.log_n + 1, m = 2 * N;
+    const double4 *roots = reinterpret_cast<const double4 *>(t.roots->p);
+    HX_CUDA(cudaMemsetAsync(a, 0, sizeof(double4) * (size_t)m * count, s));
+    k_enc_place<<<dim3(grid_for(N / 2), count), 256, 0, s>>>(a, slots_dev, n_slots,
+                                                             reinterpret_cast<const int *>(t.e->p), log_m, N / 2);
+    k_enc_fft_tile<<<dim3(m / kFftTile, count), kFftTile / 2, 0, s>>>(a, roots, log_m);
+    for (int len = 2 * kFftTile; len <= m; len <<= 1)
+        k_enc_fft_stage<<<dim3(grid_for(m / 2), count), 256, 0, s>>>(a, roots, log_m, len);
+    HX_CUDA(cudaGetLastError());
+    ctx.counters[C_LAUNCH] += 2 + (log_m - 10);
+}
+
+// vectors transformed per pass: bounds the complex double-double work buffer (32 B per point)
+constexpr int kEncChunk = 64;
+
 } // namespace
 
 // coefficients of the canonical-embedding encoding of `count` slot vectors
@@ -193,53 +279,51 @@ void encode_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int 
     HX_CHECK(m % kFftTile == 0, HX_EINVAL, "the device encoder needs N >= 512");
     HX_CHECK(n_slots <= (size_t)N / 2 && count >= 1 && count < 65536, HX_EINVAL, "bad slot batch");
     const EncTables &t = enc_tables(ctx);
-    DevBuf A((size_t)2 * m * count, s);
+    const int chunk = std::min(count, kEncChunk);
+    DevBuf A((size_t)4 * m * chunk, s);
     DevBuf err(1, s);
-    HX_CUDA(cudaMemsetAsync(A.p, 0, sizeof(double2) * (size_t)m * count, s));
     HX_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
-    double2 *a = reinterpret_cast<double2 *>(A.p);
-    const double2 *roots = reinterpret_cast<const double2 *>(t.roots->p);
-    k_enc_place<<<dim3(grid_for(N / 2), count), 256, 0, s>>>(a, slots_dev, n_slots,
-                                                             reinterpret_cast<const int *>(t.e->p), log_m, N / 2);
-    k_enc_fft_tile<<<dim3(m / kFftTile, count), kFftTile / 2, 0, s>>>(a, roots, log_m);
-    for (int len = 2 * kFftTile; len <= m; len <<= 1)
-        k_enc_fft_stage<<<dim3(grid_for(m / 2), count), 256, 0, s>>>(a, roots, log_m, len);
-    k_enc_round<<<dim3(grid_for(N), count), 256, 0, s>>>(out, out_stride, a, log_m, N, scale,
+    double4 *a = reinterpret_cast<double4 *>(A.p);
+    for (int b0 = 0; b0 < count; b0 += chunk) {
+        const int c = std::min(chunk, count - b0);
+        enc_transform(ctx, t, a, slots_dev + (size_t)b0 * n_slots, n_slots, c, s);
+        k_enc_round<<<dim3(grid_for(N), c), 256, 0, s>>>(out + (size_t)b0 * out_stride, out_stride, a, log_m, N, scale,
                                                          reinterpret_cast<int *>(err.p));
-    HX_CUDA(cudaGetLastError());
-    ctx.counters[C_LAUNCH] += 4 + (log_m - 10);
+        HX_CUDA(cudaGetLastError());
+        ctx.counters[C_LAUNCH] += 1;
+    }
     int herr = 0;
     HX_CUDA(cudaMemcpyAsync(&herr, err.p, sizeof(int), cudaMemcpyDeviceToHost, s));
     HX_CUDA(cudaStreamSynchronize(s));
     HX_CHECK(herr == 0, HX_EINVAL, "encoded coefficient exceeds 2^62");
 }
 
-// the real coefficients of the encoding of every slot vector (scale not yet applied):
-// encode_batch's coefficients are round_half_away(m * scale) of these, bit for bit
-void encode_real_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int count, double *m_out,
+// the real coefficients of the encoding of every slot vector (scale not yet applied), as
+// double-double pairs [count][N]: encode_batch's coefficients are their rounded products with
+// the scale
+void encode_real_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int count, double2 *m_out,
                        cudaStream_t s)
 {
     const int N = ctx.N, log_m = ctx.log_n + 1, m = 2 * N;
     HX_CHECK(m % kFftTile == 0, HX_EINVAL, "the device encoder needs N >= 512");
     HX_CHECK(n_slots <= (size_t)N / 2 && count >= 1 && count < 65536, HX_EINVAL, "bad slot batch");
     const EncTables &t = enc_tables(ctx);
-    DevBuf A((size_t)2 * m * count, s);
-    HX_CUDA(cudaMemsetAsync(A.p, 0, sizeof(double2) * (size_t)m * count, s));
-    double2 *a = reinterpret_cast<double2 *>(A.p);
-    const double2 *roots = reinterpret_cast<const double2 *>(t.roots->p);
-    k_enc_place<<<dim3(grid_for(N / 2), count), 256, 0, s>>>(a, slots_dev, n_slots,
-                                                             reinterpret_cast<const int *>(t.e->p), log_m, N / 2);
-    k_enc_fft_tile<<<dim3(m / kFftTile, count), kFftTile / 2, 0, s>>>(a, roots, log_m);
-    for (int len = 2 * kFftTile; len <= m; len <<= 1)
-        k_enc_fft_stage<<<dim3(grid_for(m / 2), count), 256, 0, s>>>(a, roots, log_m, len);
-    k_enc_real<<<dim3(grid_for(N), count), 256, 0, s>>>(m_out, (size_t)N, a, log_m, N);
-    HX_CUDA(cudaGetLastError());
-    ctx.counters[C_LAUNCH] += 4 + (log_m - 10);
+    const int chunk = std::min(count, kEncChunk);
+    DevBuf A((size_t)4 * m * chunk, s);
+    double4 *a = reinterpret_cast<double4 *>(A.p);
+    for (int b0 = 0; b0 < count; b0 += chunk) {
+        const int c = std::min(chunk, count - b0);
+        enc_transform(ctx, t, a, slots_dev + (size_t)b0 * n_slots, n_slots, c, s);
+        k_enc_real<<<dim3(grid_for(N), c), 256, 0, s>>>(m_out + (size_t)b0 * N, (size_t)N, a, log_m, N);
+        HX_CUDA(cudaGetLastError());
+        ctx.counters[C_LAUNCH] += 1;
+    }
+    HX_CUDA(cudaStreamSynchronize(s));  // the work buffer is released at return
 }
 
 // rows[r] of the output = the encoding at `scale` of the slot vector whose real coefficients
 // are row idx_dev[r] of m (count rows, N coefficients each)
-void encode_rows_from_real(hx_context &ctx, const double *m, const int *idx_dev, int count, double scale,
+void encode_rows_from_real(hx_context &ctx, const double2 *m, const int *idx_dev, int count, double scale,
                            int64_t *out, cudaStream_t s)
 {
     HX_CHECK(count >= 1 && count < 65536, HX_EINVAL, "bad row count");

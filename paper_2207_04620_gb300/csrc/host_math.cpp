@@ -145,6 +145,96 @@ double round_half_away(double x)
     return x < 0 ? -a : a;
 }
 
+// ---- double-double arithmetic (host code is built with -ffp-contract=off: every operation
+// below is rounded once, as written)
+
+static inline DD two_sum(double a, double b)
+{
+    const double s = a + b, v = s - a;
+    return DD{s, (a - (s - v)) + (b - v)};
+}
+
+static inline DD fast_two_sum(double a, double b)  // |a| >= |b|
+{
+    const double s = a + b;
+    return DD{s, b - (s - a)};
+}
+
+static inline DD two_prod(double a, double b)
+{
+    const double p = a * b;
+    return DD{p, std::fma(a, b, -p)};  // the exact error of the product
+}
+
+DD dd_add(DD a, DD b)
+{
+    DD s = two_sum(a.hi, b.hi);
+    const DD t = two_sum(a.lo, b.lo);
+    s = fast_two_sum(s.hi, s.lo + t.hi);
+    return fast_two_sum(s.hi, s.lo + t.lo);
+}
+
+DD dd_mul(DD a, DD b)
+{
+    const DD p = two_prod(a.hi, b.hi);
+    return fast_two_sum(p.hi, p.lo + (a.hi * b.lo + a.lo * b.hi));
+}
+
+DD dd_mul_d(DD a, double b)
+{
+    const DD p = two_prod(a.hi, b);
+    return fast_two_sum(p.hi, p.lo + a.lo * b);
+}
+
+static DD dd_div_d(DD a, double b)
+{
+    const double q1 = a.hi / b;
+    const DD p = two_prod(q1, b);
+    const double r = ((a.hi - p.hi) - p.lo) + a.lo;
+    return fast_two_sum(q1, r / b);
+}
+
+int64_t dd_round_coeff(DD x)
+{
+    if (!(std::fabs(x.hi) < 4611686018427387904.0)) throw std::runtime_error("encoded coefficient exceeds 2^62");
+    // integer parts of both words (each exact), and what is left of each
+    const double i1 = std::nearbyint(x.hi), i2 = std::nearbyint(x.lo);
+    const double f = (x.hi - i1) + (x.lo - i2);  // |f| <= 1
+    const int64_t base = (int64_t)i1 + (int64_t)i2;
+    const double band = 0x1p-20;
+    int64_t c = base;
+    if (std::fabs(std::fabs(f) - 0.5) <= band) {
+        // the half-integer base +- 1/2, rounded away from zero
+        const bool positive = f > 0 ? base >= 0 : base > 0;
+        c = f > 0 ? (positive ? base + 1 : base) : (positive ? base : base - 1);
+    } else if (f > 0.5) {
+        c = base + 1;
+    } else if (f < -0.5) {
+        c = base - 1;
+    }
+    if (c >= ((int64_t)1 << 62) || c <= -((int64_t)1 << 62)) throw std::runtime_error("encoded coefficient exceeds 2^62");
+    return c;
+}
+
+// cos and sin of pi * a / b, 0 <= a/b <= 1/4, in double-double: Taylor series of the angle
+// pi*a/b (pi as the double-double 0x1.921fb54442d18p+1 + 0x1.1a62633145c07p-53)
+static void dd_cos_sin_pi(int64_t a, int64_t b, DD &c, DD &s)
+{
+    const DD pi{0x1.921fb54442d18p+1, 0x1.1a62633145c07p-53};
+    const DD phi = dd_div_d(dd_mul_d(pi, (double)a), (double)b);
+    const DD phi2 = dd_mul(phi, phi);
+    DD tc{1.0, 0.0}, ts = phi;
+    c = tc;
+    s = ts;
+    for (int k = 0; k < 40; k++) {
+        tc = dd_div_d(dd_mul(tc, phi2), -(double)((2 * k + 1) * (2 * k + 2)));
+        ts = dd_div_d(dd_mul(ts, phi2), -(double)((2 * k + 2) * (2 * k + 3)));
+        c = dd_add(c, tc);
+        s = dd_add(s, ts);
+        if (std::fabs(tc.hi) < 0x1p-112 && std::fabs(ts.hi) < 0x1p-112) break;
+    }
+}
+
 Encoder::Encoder(int ln) : log_n(ln), n(1 << ln)
 {
     const int s = n / 2;
@@ -154,10 +244,33 @@ Encoder::Encoder(int ln) : log_n(ln), n(1 << ln)
         e[j] = v;
         v = v * 5 % (2 * n);
     }
-    roots.resize(n);  // half of the 2N-th roots suffice for a 2N-point FFT
+    // e^(-2 pi i k / 2N) = cos(pi k/N) - i sin(pi k/N) for k < N, from the angles in [0, pi/4]
+    // (k = N/4 is pi/4) by the symmetries of cos and sin
+    const int m8 = n / 4;
+    std::vector<DD> tc(m8 + 1), ts(m8 + 1);
+    for (int j = 0; j <= m8; j++) dd_cos_sin_pi(j, n, tc[j], ts[j]);
+    auto neg = [](DD x) { return DD{-x.hi, -x.lo}; };
+    roots_re.resize(n);
+    roots_im.resize(n);
+    roots.resize(n);
     for (int k = 0; k < n; k++) {
-        const double ang = -2.0 * M_PI * (double)k / (double)(2 * n);
-        roots[k] = std::complex<double>(std::cos(ang), std::sin(ang));
+        DD c, si;
+        if (k <= m8) {
+            c = tc[k];
+            si = ts[k];
+        } else if (k <= 2 * m8) {  // pi/2 - angle
+            c = ts[2 * m8 - k];
+            si = tc[2 * m8 - k];
+        } else if (k <= 3 * m8) {  // pi/2 + angle
+            c = neg(ts[k - 2 * m8]);
+            si = tc[k - 2 * m8];
+        } else {  // pi - angle
+            c = neg(tc[4 * m8 - k]);
+            si = ts[4 * m8 - k];
+        }
+        roots_re[k] = c;
+        roots_im[k] = neg(si);
+        roots[k] = std::complex<double>(c.hi, -si.hi);
     }
 }
 
@@ -184,21 +297,48 @@ void Encoder::fft(std::vector<std::complex<double>> &a, bool inverse) const
     }
 }
 
-void Encoder::encode(const double *slots, size_t count, double scale, int64_t *coeffs) const
+void Encoder::encode_real(const double *slots, size_t count, std::vector<DD> &m) const
 {
-    const int m = 2 * n;
-    std::vector<std::complex<double>> big(m);
+    // radix-2 decimation in time over the slots scattered to exponents e_j and 2N - e_j (the
+    // conjugate of a real slot), in bit-reversed order; complex values as double-double pairs
+    const int len = 2 * n, bits = log_n + 1;
+    std::vector<DD> re(len, DD{0.0, 0.0}), im(len, DD{0.0, 0.0});
+    auto brv = [&](int x) {
+        int r = 0;
+        for (int b = 0; b < bits; b++) r |= ((x >> b) & 1) << (bits - 1 - b);
+        return r;
+    };
     for (size_t j = 0; j < (size_t)(n / 2); j++) {
         const double z = j < count ? slots[j] : 0.0;
-        big[e[j]] = z;
-        big[(m - e[j]) % m] = z;  // conjugate of a real slot
+        re[brv((int)e[j])] = DD{z, 0.0};
+        re[brv((int)((len - e[j]) % len))] = DD{z, 0.0};
     }
-    fft(big, false);
-    for (int i = 0; i < n; i++) {
-        const double v = round_half_away(big[i].real() / n * scale);
-        if (!(std::fabs(v) < 4611686018427387904.0)) throw std::runtime_error("encoded coefficient exceeds 2^62");
-        coeffs[i] = (int64_t)v;
+    for (int half = 1; half < len; half <<= 1) {
+        const int step = n / half;  // root index stride: e^(-2 pi i k / (2 half)) = roots[k * step]
+        for (int i = 0; i < len; i += 2 * half)
+            for (int k = 0; k < half; k++) {
+                const DD wr = roots_re[(size_t)k * step], wi = roots_im[(size_t)k * step];
+                const DD vr = re[i + k + half], vi = im[i + k + half];
+                const DD vw = dd_mul(vi, wi);
+                const DD tr = dd_add(dd_mul(vr, wr), DD{-vw.hi, -vw.lo});
+                const DD ti = dd_add(dd_mul(vr, wi), dd_mul(vi, wr));
+                const DD ur = re[i + k], ui = im[i + k];
+                re[i + k] = dd_add(ur, tr);
+                im[i + k] = dd_add(ui, ti);
+                re[i + k + half] = dd_add(ur, DD{-tr.hi, -tr.lo});
+                im[i + k + half] = dd_add(ui, DD{-ti.hi, -ti.lo});
+            }
     }
+    m.resize(n);
+    const double inv_n = 1.0 / n;  // a power of two: exact
+    for (int i = 0; i < n; i++) m[i] = DD{re[i].hi * inv_n, re[i].lo * inv_n};
+}
+
+void Encoder::encode(const double *slots, size_t count, double scale, int64_t *coeffs) const
+{
+    std::vector<DD> m;
+    encode_real(slots, count, m);
+    for (int i = 0; i < n; i++) coeffs[i] = dd_round_coeff(dd_mul_d(m[i], scale));
 }
 
 void Encoder::decode(const int64_t *coeffs, double scale, double *slots, size_t count) const

@@ -52,14 +52,31 @@ struct GaussianCdt {
 // round half away from zero, evaluated as sign(x) * floor(|x| + 0.5)
 double round_half_away(double x);
 
-// Canonical-embedding encoder/decoder (slot j at zeta^(5^j), zeta = e^(i pi/N))
-// built on a radix-2 complex FFT of length 2N.
+// Double-double numbers: the unevaluated sum hi + lo of two doubles, about 106 bits
+// (Dekker 1971 for the exact product through a fused multiply-add, Knuth's two-sum).
+struct DD {
+    double hi, lo;
+};
+DD dd_add(DD a, DD b);
+DD dd_mul(DD a, DD b);
+DD dd_mul_d(DD a, double b);
+// The encoder's rounding rule: hi + lo rounded half away from zero, a value within
+// 2^-20 of a half-integer taken as that half-integer.  Throws past 2^62.
+int64_t dd_round_coeff(DD x);
+
+// Canonical-embedding encoder/decoder (slot j at zeta^(5^j), zeta = e^(i pi/N)).
+// Encoding is exact: coefficient i is scale * (2/N) * sum_j z_j cos(pi (i e_j mod 2N)/N)
+// under dd_round_coeff, the sum taken by a double-double FFT of length 2N whose error
+// (about 2^-90 relative) lies far inside the rounding rule's band.
 struct Encoder {
     int log_n, n;
     std::vector<int64_t> e;  // 5^j mod 2N
-    std::vector<std::complex<double>> roots;  // e^(-2 pi i k / 2N)
+    std::vector<DD> roots_re, roots_im;  // e^(-2 pi i k / 2N), k < N, double-double
+    std::vector<std::complex<double>> roots;  // the same rounded to double (decoding)
     explicit Encoder(int log_n);
-    // m_i = (2/N) Re(sum_j z_j zeta^(-i e_j)),  coeffs = round(scale * m)
+    // m_i = (2/N) sum_j z_j cos(pi (i e_j mod 2N)/N) before the scale, double-double
+    void encode_real(const double *slots, size_t count, std::vector<DD> &m) const;
+    // coeffs = dd_round_coeff(scale * m)
     void encode(const double *slots, size_t count, double scale, int64_t *coeffs) const;
     // z_j = sum_i c_i zeta^(i e_j) / scale (real part)
     void decode(const int64_t *coeffs, double scale, double *slots, size_t count) const;

@@ -89,8 +89,9 @@ struct hx_context {
     size_t plan_limit = SIZE_MAX, plan_bytes = 0;
     uint64_t plan_tick = 0, plan_evictions = 0;
     cudaStream_t plan_stream = nullptr;  // builds cached plans; their masks are freed in its order
-    // the encoder's real coefficients of every mask of a plan shape (kind, h, Alg. 3 or not), in
-    // plan order: a plan at any level only scales and rounds them (guarded by mask_real_mu)
+    // the encoder's real coefficients (double-double) of every mask of a plan shape (kind, h,
+    // Alg. 3 or not), in plan order: a plan at any level only scales and rounds them (guarded by
+    // mask_real_mu)
     std::mutex mask_real_mu;
     std::map<std::tuple<int, int, bool>, hx::BufPtr> mask_real;
     std::vector<std::shared_ptr<const hx_matmul_plan>> plans_pinned;  // used inside a stream capture
@@ -266,9 +267,10 @@ Cts sign_batch(hx_context &ctx, const hx_keyset &ks, const Cts &x, int d, int k,
 struct DenseResult {
     Cts E, M, dW;
 };
-void encode_real_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int count, double *m_out,
+// the encodings' real coefficients before the scale, double-double (hi, lo) per coefficient
+void encode_real_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int count, double2 *m_out,
                        cudaStream_t s);
-void encode_rows_from_real(hx_context &ctx, const double *m, const int *idx_dev, int count, double scale,
+void encode_rows_from_real(hx_context &ctx, const double2 *m, const int *idx_dev, int count, double scale,
                            int64_t *out, cudaStream_t s);
 void encode_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int count, double scale, int64_t *out,
                   size_t out_stride, cudaStream_t s);

@@ -188,9 +188,9 @@ void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s)
         HX_CUDA(cudaMemcpyAsync(dbits.p, bits.data(), bits.size(), cudaMemcpyHostToDevice, s));
         launch_expand_masks(ev.lc(), reinterpret_cast<double *>(dslots.p), reinterpret_cast<const uint8_t *>(dbits.p),
                             M_all, hh, p->beta, S);
-        real = std::make_shared<DevBuf>((size_t)M_all * N, true);
+        real = std::make_shared<DevBuf>((size_t)2 * M_all * N, true);  // double-double per coefficient
         encode_real_batch(ctx, reinterpret_cast<const double *>(dslots.p), S, M_all,
-                          reinterpret_cast<double *>(real->p), s);
+                          reinterpret_cast<double2 *>(real->p), s);
         HX_CUDA(cudaStreamSynchronize(s));
         std::lock_guard<std::mutex> lk(ctx.mask_real_mu);
         auto ins = ctx.mask_real.emplace(shape, real);  // another call may have made it meanwhile
@@ -216,7 +216,7 @@ void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s)
         HX_CUDA(cudaMemcpyAsync(didx.p, idx.data(), sizeof(int) * idx.size(), cudaMemcpyHostToDevice, s));
         DevBuf dco((size_t)M * N, s);
         int64_t *co = reinterpret_cast<int64_t *>(dco.p);
-        encode_rows_from_real(ctx, reinterpret_cast<const double *>(real->p), reinterpret_cast<const int *>(didx.p), M,
+        encode_rows_from_real(ctx, reinterpret_cast<const double2 *>(real->p), reinterpret_cast<const int *>(didx.p), M,
                               std::get<0>(grp.first), co, s);
         BufPtr G = std::make_shared<DevBuf>((size_t)M * rows * N, s);
         const int *idp = reinterpret_cast<const int *>(dpr.p);
