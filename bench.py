@@ -196,13 +196,13 @@ def other_metrics(args):
     (64 ciphertexts, 3 timed steps) and a short serving stream (300 requests at 0.8x capacity)."""
     out = {}
     ns = argparse.Namespace(**vars(args))
-    ns.log_n, ns.rows, ns.steps, ns.warmup, ns.tiles = 14, 1600, 5, 3, None
+    ns.log_n, ns.rows, ns.steps, ns.warmup, ns.tiles, ns.reps = 14, 1600, 5, 3, None, 200
     m = run_micro(ns)
     out["ntt_micro"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in m.items()
                         if k in ("log_n", "rows", "tiles", "fwd_ms", "inv_ms", "fwd_gbs", "inv_gbs", "fwd_frac",
                                  "inv_frac", "fwd_alu_frac", "inv_alu_frac", "peak_gbs", "peak_kind", "clocks")}
     out["ntt_micro"]["what"] = "forward / inverse NTT of 1600 limbs of N=2^14 (210 MB, > L2) in place; " \
-                               "CUDA events, median of 5"
+                               "CUDA events around 200 transforms per direction, median of 5 steps"
     ns = argparse.Namespace(**vars(args))
     ns.steps, ns.warmup, ns.relu, ns.alpha = 3, 1, False, None
     sg = run_sign(ns)
@@ -843,17 +843,22 @@ def run_micro(args):
         hx.hx_ntt(ctx, x.data_ptr(), polys, idx, True, stream)
     torch.cuda.synchronize()
     fw, iv = [], []
+    # each timed step repeats each direction `reps` times between its events (inputs larger
+    # than L2), long enough for the clock sampler to see the GPU under load
+    reps = max(1, int(getattr(args, "reps", 1)))
     sampler = ClockSampler()
     for _ in range(args.steps):
         e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
         e[0].record(stream)
-        hx.hx_ntt(ctx, x.data_ptr(), polys, idx, False, stream)
+        for _ in range(reps):
+            hx.hx_ntt(ctx, x.data_ptr(), polys, idx, False, stream)
         e[1].record(stream)
-        hx.hx_ntt(ctx, x.data_ptr(), polys, idx, True, stream)
+        for _ in range(reps):
+            hx.hx_ntt(ctx, x.data_ptr(), polys, idx, True, stream)
         e[2].record(stream)
         torch.cuda.synchronize()
-        fw.append(e[0].elapsed_time(e[1]))
-        iv.append(e[1].elapsed_time(e[2]))
+        fw.append(e[0].elapsed_time(e[1]) / reps)
+        iv.append(e[1].elapsed_time(e[2]) / reps)
     clocks = sampler.stop()
     byt = 16.0 * polys * per * n
     peak, kind = peaks()
@@ -1147,6 +1152,7 @@ def main():
                     help="sign/dense: primes per key-switching digit (0: K; default 4 for sign, K for dense)")
     ap.add_argument("--log-n", type=int, default=14)
     ap.add_argument("--rows", type=int, default=1600)
+    ap.add_argument("--reps", type=int, default=1, help="NTT micro-benchmark: transforms per timed step")
     ap.add_argument("--tiles", default=None, help="NTT tile widths per phase, e.g. 16,16,16,16 (default: autotune)")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
