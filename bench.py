@@ -234,6 +234,7 @@ def run_hx(args, world, rank, local):
     stream = torch.cuda.current_stream()
     ctx = hx.hx_context_create(LOG_N, Q_BITS, P_BITS, LOG2_SCALE)
     tiles = hx.hx_autotune(ctx, stream=torch.cuda.current_stream())
+    ntt_tuning = hx.hx_ntt_tuning(ctx)  # variants per batch-size bucket and phase
     limbs = len(Q_BITS)
     steps = hx.hx_matmul_rotation_steps(ctx, H, limbs)
     ks = hx.hx_keygen(ctx, 2, 2024 + rank, steps)
@@ -408,6 +409,7 @@ def run_hx(args, world, rank, local):
                            "per_step_launch": "one hx_matmul_exec_run C-ABI call: the batched schedule "
                                               "(hx_matmul_batch) captured once into a CUDA graph",
                            "ntt_tiles_autotuned": tiles,
+                           "ntt_tuning": ntt_tuning,
                            "step2_premasked_key_bytes": premasked_bytes},
                 "e2e": {"value": round(PRODUCTS * world / e2e_s, 2), "unit": "matmul/s",
                         "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

@@ -478,15 +478,25 @@ int hx_counters(const hx_context *ctx, uint64_t *out, int cap);
 void hx_counters_reset(hx_context *ctx);
 
 /* ---- autotuning ------------------------------------------------------------- */
-/* Times each NTT tile width (8, 16 or 32 sub-transforms per block, for each of
- * the four phase kernels: forward column, forward row, inverse column, inverse
- * row) on this device with a scratch buffer of 256 limbs, and keeps the fastest
- * for the context.  Every choice computes identical residues.  choice[4]
- * (may be NULL) receives the chosen widths. */
+/* NTT autotuner.  Each of the four phase kernels (forward column, forward
+ * row, inverse column, inverse row) has variants: a tile width (4, 8, 16 or 32
+ * sub-transforms per block, i.e. columns or limb rows per block) and, for an
+ * odd number of stages in the phase, the order of its two register passes'
+ * radices (e.g. 16 then 8, or 8 then 16).  The best variant depends on the
+ * batch: launches are grouped into buckets by their number of limbs (up to 64,
+ * 256, 768, more), and each bucket is timed on its own batch (48, 176, 512 and
+ * 1024 limbs) on this device; the fastest per (bucket, phase) is kept for the
+ * context.  Every variant computes identical residues.  choice[4] (may be
+ * NULL) receives the variants of the 256-limb bucket as signed widths
+ * (negative: swapped radices). */
 hx_status hx_autotune(hx_context *ctx, int32_t *choice, void *stream);
-/* Sets (set != NULL: widths 8, 16 or 32 per phase, in the order above) and/or
- * reads (get != NULL) the NTT tile widths of the context. */
+/* Sets (set != NULL: signed widths per phase, in the order above, for every
+ * bucket) and/or reads (get != NULL: the 256-limb bucket) the NTT variants. */
 hx_status hx_ntt_tiles(hx_context *ctx, const int32_t *set, int32_t *get);
+/* The tuning table: per bucket six integers (largest limb count of the bucket,
+ * limbs it was timed on, then the four phases' signed widths).  Writes at most
+ * cap integers; returns the table's length. */
+int hx_ntt_tuning(const hx_context *ctx, int32_t *out, int cap);
 
 /* ---- profiling ------------------------------------------------------------- */
 /* While enabled, every kernel launch of the context is bracketed by CUDA events

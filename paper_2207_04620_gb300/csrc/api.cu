@@ -1151,22 +1151,27 @@ void hx_counters_reset(hx_context *ctx)
         for (int i = 0; i < C_NUM; i++) ctx->counters[i] = 0;
 }
 
+// a tuned NTT variant as the signed width of the public calls: negative = swapped radices
+static int variant_width(int v) { return v >= NTT_WIDTHS ? -kNttTileWidths[v % NTT_WIDTHS] : kNttTileWidths[v]; }
+
 hx_status hx_autotune(hx_context *ctx, int32_t *choice, void *stream)
 {
     HX_TRY
     need(ctx, "null argument");
-    const int rows = 256;
-    DevBuf buf((size_t)rows * ctx->N, S(stream));
-    HX_CUDA(cudaMemsetAsync(buf.p, 0, sizeof(uint64_t) * rows * ctx->N, S(stream)));
+    // one scratch buffer for the largest batch timed; every bucket of batch sizes is tuned on
+    // its own number of limbs (the widths that fill the SMs best depend on the batch)
+    const int rows_max = std::min(kNttBucketTune[NTT_BUCKETS - 1], MAX_NTT_ROWS);
+    DevBuf buf((size_t)rows_max * ctx->N, S(stream));
+    HX_CUDA(cudaMemsetAsync(buf.p, 0, sizeof(uint64_t) * rows_max * ctx->N, S(stream)));
     Eval ev(*ctx, S(stream));
-    int best[4] = {1, 1, 1, 1};
-    float ms[4];
-    autotune_ntt(ev.lc(), buf.p, rows, best, ms);
-    static const int widths[NTT_VARIANTS] = {8, 16, 32};
-    for (int i = 0; i < 4; i++) {
-        ctx->t.ntt_var[i] = best[i];
-        if (choice) choice[i] = widths[best[i]];
+    for (int b = 0; b < NTT_BUCKETS; b++) {
+        int best[4] = {2, 2, 2, 2};
+        float ms[4];
+        autotune_ntt(ev.lc(), buf.p, std::min(kNttBucketTune[b], rows_max), best, ms);
+        for (int i = 0; i < 4; i++) ctx->t.ntt_var[b][i] = best[i];
     }
+    if (choice)
+        for (int i = 0; i < 4; i++) choice[i] = variant_width(ctx->t.ntt_var[1][i]);
     return HX_OK;
     HX_END
 }
@@ -1175,21 +1180,37 @@ hx_status hx_ntt_tiles(hx_context *ctx, const int32_t *set, int32_t *get)
 {
     HX_TRY
     need(ctx, "null argument");
-    static const int widths[NTT_VARIANTS] = {8, 16, 32};
     if (set) {
         int v[4];
         for (int i = 0; i < 4; i++) {
             v[i] = -1;
-            for (int k = 0; k < NTT_VARIANTS; k++)
-                if (set[i] == widths[k]) v[i] = k;
-            need(v[i] >= 0, "tile width must be 8, 16 or 32");
+            for (int k = 0; k < NTT_WIDTHS; k++) {
+                if (set[i] == kNttTileWidths[k]) v[i] = k;
+                if (set[i] == -kNttTileWidths[k]) v[i] = k + NTT_WIDTHS;
+            }
+            need(v[i] >= 0, "tile width must be 4, 8, 16 or 32 (negative: swapped radices)");
         }
-        for (int i = 0; i < 4; i++) ctx->t.ntt_var[i] = v[i];
+        for (int b = 0; b < NTT_BUCKETS; b++)
+            for (int i = 0; i < 4; i++) ctx->t.ntt_var[b][i] = v[i];
     }
     if (get)
-        for (int i = 0; i < 4; i++) get[i] = widths[ctx->t.ntt_var[i]];
+        for (int i = 0; i < 4; i++) get[i] = variant_width(ctx->t.ntt_var[1][i]);
     return HX_OK;
     HX_END
+}
+
+int hx_ntt_tuning(const hx_context *ctx, int32_t *out, int cap)
+{
+    if (!ctx || (!out && cap > 0)) return HX_EINVAL;
+    int n = 0;
+    for (int b = 0; b < NTT_BUCKETS; b++) {
+        const int32_t row[6] = {kNttBucketMax[b], kNttBucketTune[b], variant_width(ctx->t.ntt_var[b][0]),
+                                variant_width(ctx->t.ntt_var[b][1]), variant_width(ctx->t.ntt_var[b][2]),
+                                variant_width(ctx->t.ntt_var[b][3])};
+        for (int k = 0; k < 6; k++, n++)
+            if (n < cap) out[n] = row[k];
+    }
+    return n;
 }
 
 hx_status hx_profile_enable(hx_context *ctx, int on)

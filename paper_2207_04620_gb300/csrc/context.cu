@@ -125,6 +125,8 @@ void build_context(hx_context &c, const hx_params &p)
             twf[(size_t)i * N + k] = make_ulonglong2(w, shoup_companion(w, q));
             twi[(size_t)i * N + k] = make_ulonglong2(wi, shoup_companion(wi, q));
         }
+        P.n_inv_w1 = hmul(P.n_inv, twi[(size_t)i * N + 1].x, q);
+        P.n_inv_w1_sh = shoup_companion(P.n_inv_w1, q);
     }
 
     // ModUp tables, by (limbs, digit)

@@ -17,7 +17,19 @@ namespace hx {
 constexpr int MAXP = HX_MAX_Q + HX_MAX_P;
 constexpr int MAXK = HX_MAX_P + 1;  // conversion sources: the special primes, plus q_top when RS joins ModDown
 constexpr int MAX_NTT_ROWS = 1024;
-constexpr int NTT_VARIANTS = 3;  // tile widths 8, 16, 32
+constexpr int NTT_WIDTHS = 4;    // tile widths 4, 8, 16, 32 (sub-transforms per block)
+constexpr int kNttTileWidths[NTT_WIDTHS] = {4, 8, 16, 32};
+constexpr int NTT_VARIANTS = 2 * NTT_WIDTHS;  // a width, with the register passes' radices as is or swapped
+// NTT batch sizes tuned separately: a launch of n limbs uses the first bucket with n <= its bound
+constexpr int NTT_BUCKETS = 4;
+constexpr int kNttBucketMax[NTT_BUCKETS] = {64, 256, 768, 1 << 30};
+constexpr int kNttBucketTune[NTT_BUCKETS] = {48, 176, 512, 1024};  // limbs timed for each bucket
+inline int ntt_bucket(long long limbs)
+{
+    int b = 0;
+    while (b < NTT_BUCKETS - 1 && limbs > kNttBucketMax[b]) b++;
+    return b;
+}
 
 // Fast basis conversion table (Han-Ki hybrid key switching, no correction):
 // out_t = sum_i [x_i * qhat_i^-1]_{q_i} * (qhat_i mod t)  (mod t)
@@ -102,7 +114,8 @@ struct DeviceTables {
     ModDownTable *moddown = nullptr;// [n_q+1] by limbs
     RescaleTable *rescale = nullptr;// [n_q+1] by limbs
     RelinRescaleTable *relin_rs = nullptr;  // [n_q+1] by limbs
-    int ntt_var[4] = {1, 1, 1, 1};  // tile width per phase: fwd cols, fwd rows, inv cols, inv rows
+    // NTT variant per batch-size bucket and phase (fwd cols, fwd rows, inv cols, inv rows)
+    int ntt_var[NTT_BUCKETS][4] = {{2, 2, 2, 2}, {2, 2, 2, 2}, {2, 2, 2, 2}, {2, 2, 2, 2}};
     int n_sm = 1;                   // multiprocessors of the device
 };
 
@@ -146,7 +159,8 @@ struct NttJob {
 void launch_ntt_multi(cudaStream_t s, const std::vector<NttJob> &jobs, bool inverse, int n_sm,
                       std::atomic<uint64_t> *launches);
 
-// times the NTT tile widths on `rows` limbs of buf and writes the fastest per phase
+// times every NTT variant (tile width, radix split) of each phase on `rows` limbs of buf and
+// writes the fastest per phase
 void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float *ms_out);
 void launch_add(const LaunchCtx &c, View out, View a, View b, int B, int comps, int limbs, bool sub);
 void launch_copy(const LaunchCtx &c, View out, View a, int B, int comps, int limbs);

@@ -20,7 +20,8 @@ struct PrimeConst {
     uint64_t r_mod_sh; // Shoup companion of r_mod
     uint64_t n_inv;    // N^-1 mod q
     uint64_t n_inv_sh;
-    uint64_t pad;
+    uint64_t n_inv_w1;     // N^-1 * psi^-brv(1) mod q: the last inverse stage's twiddle with N^-1 folded in
+    uint64_t n_inv_w1_sh;
 };
 
 __device__ __forceinline__ uint64_t shoup_lazy(uint64_t y, uint64_t w, uint64_t wsh, uint64_t q)

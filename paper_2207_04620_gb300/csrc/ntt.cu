@@ -93,9 +93,69 @@ __device__ __forceinline__ void ntt_pass(uint64_t *sh, int n_sub, int sk, int se
     }
 }
 
-template <int L> struct Split {
-    static constexpr int R1 = (L + 1) / 2;  // first pass (stages 0..R1-1)
-    static constexpr int R2 = L - R1;       // second pass
+// The column phase's last register pass, its results stored straight to global memory (word e
+// of column k at dst + e*N2 + k): consecutive threads hold consecutive columns, so each warp
+// store covers whole COLS-word row segments and the phase needs no shared-memory round trip
+// for its output.  Forward: outputs stay lazy (below 4q) for the row phase.  Inverse: the pass
+// ends with stage 0, whose butterfly also applies N^-1 -- x' = (x+y) N^-1 and
+// y' = (x-y) psi^-brv(1) N^-1, one product each instead of a butterfly product and two
+// scalings -- and the outputs are fully reduced.
+template <int LOGM, int R, int S0, int COLS, bool INV>
+__device__ __forceinline__ void ntt_pass_out(const uint64_t *sh, const ulonglong2 *__restrict__ tw, const PrimeConst &P,
+                                             uint64_t *dst, int N2, int nthr)
+{
+    constexpr int M = 1 << LOGM, RR = 1 << R, TL = M >> (S0 + R), ITEMS = M >> R;
+    const uint64_t q = P.q, two_q = 2 * q;
+    for (int w = threadIdx.x; w < ITEMS * COLS; w += nthr) {
+        const int k = w % COLS, u = w / COLS;
+        const int hi = u / TL, lo = u % TL;
+        const int base = hi * TL * RR + lo;
+        uint64_t v[RR];
+#pragma unroll
+        for (int m = 0; m < RR; m++) v[m] = sh[k + (base + m * TL) * COLS];
+        if (!INV) {
+#pragma unroll
+            for (int vv = 0; vv < R; vv++) {
+                const int s = S0 + vv, half = RR >> (vv + 1);
+                const int tbase = (1 << s) + (hi << vv);
+#pragma unroll
+                for (int gl = 0; gl < (1 << vv); gl++) {
+                    const ulonglong2 wv = tw[tbase + gl];
+#pragma unroll
+                    for (int j = 0; j < half; j++) bf_ct(v[gl * 2 * half + j], v[gl * 2 * half + j + half], wv, q, two_q);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int vv = R - 1; vv >= 1; vv--) {
+                const int s = S0 + vv, half = RR >> (vv + 1);
+                const int tbase = (1 << s) + (hi << vv);
+#pragma unroll
+                for (int gl = 0; gl < (1 << vv); gl++) {
+                    const ulonglong2 wv = tw[tbase + gl];
+#pragma unroll
+                    for (int j = 0; j < half; j++) bf_gs(v[gl * 2 * half + j], v[gl * 2 * half + j + half], wv, q, two_q);
+                }
+            }
+            static_assert(!INV || S0 == 0, "the inverse output pass must end with stage 0");
+#pragma unroll
+            for (int j = 0; j < RR / 2; j++) {
+                uint64_t x = v[j] + v[j + RR / 2];
+                if (x >= two_q) x -= two_q;
+                const uint64_t d = v[j] - v[j + RR / 2] + two_q;
+                v[j] = shoup(x, P.n_inv, P.n_inv_sh, q);
+                v[j + RR / 2] = shoup(d, P.n_inv_w1, P.n_inv_w1_sh, q);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < RR; m++) dst[(size_t)(base + m * TL) * N2 + k] = v[m];
+    }
+}
+
+template <int L, bool ALT = false> struct Split {
+    // first pass (stages 0..R1-1) and second pass; ALT swaps the two radices of an odd L
+    static constexpr int R1 = ALT ? L / 2 : (L + 1) / 2;
+    static constexpr int R2 = L - R1;
 };
 
 // Asynchronous global->shared copies (cp.async): the next tile streams in while
@@ -131,12 +191,12 @@ __device__ __forceinline__ TileId tile_of(int t, int nb, int n_rows)
 // column phase: the first LOGM stages on M rows of stride N2 (COLS adjacent columns
 // per tile); each block loops over tiles with the next tile (and its twiddles,
 // indices below M) prefetched into the other half of shared memory
-template <int LOGM, int COLS, bool INV>
-__global__ void __launch_bounds__((1 << (LOGM - Split<LOGM>::R1)) * COLS)
+template <int LOGM, int COLS, bool INV, bool ALT>
+__global__ void __launch_bounds__((1 << (LOGM - Split<LOGM, ALT>::R1)) * COLS)
 k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
            const ulonglong2 *__restrict__ tw_all, int log_n, int n_tiles)
 {
-    constexpr int M = 1 << LOGM, E = M * COLS, R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
+    constexpr int M = 1 << LOGM, E = M * COLS, R1 = Split<LOGM, ALT>::R1, R2 = Split<LOGM, ALT>::R2;
     constexpr int T = (M >> R1) * COLS;
     extern __shared__ uint64_t sh[];
     uint64_t *buf[2] = {sh, sh + E};
@@ -175,24 +235,11 @@ k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
         if (!INV) {
             ntt_pass<LOGM, R1, 0, false, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
             __syncthreads();
-            ntt_pass<LOGM, R2, R1, false, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
-            __syncthreads();
-            for (int i = threadIdx.x; i < E / 2; i += T) {  // 16-byte stores of column pairs
-                const int r = (2 * i) / COLS, c = (2 * i) % COLS;
-                *reinterpret_cast<ulonglong2 *>(dst + (size_t)r * N2 + c0 + c) =
-                    *reinterpret_cast<const ulonglong2 *>(b + 2 * i);
-            }
+            ntt_pass_out<LOGM, R2, R1, COLS, false>(b, stw[slot], P, dst + c0, N2, T);
         } else {
             ntt_pass<LOGM, R2, R1, true, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
             __syncthreads();
-            ntt_pass<LOGM, R1, 0, true, true, false>(b, COLS, 1, COLS, stw[slot], 0, 0, 0, P.q, T);
-            __syncthreads();
-            for (int i = threadIdx.x; i < E / 2; i += T) {
-                const int r = (2 * i) / COLS, c = (2 * i) % COLS;
-                const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(b + 2 * i);
-                *reinterpret_cast<ulonglong2 *>(dst + (size_t)r * N2 + c0 + c) =
-                    make_ulonglong2(shoup(x.x, P.n_inv, P.n_inv_sh, P.q), shoup(x.y, P.n_inv, P.n_inv_sh, P.q));
-            }
+            ntt_pass_out<LOGM, R1, 0, COLS, true>(b, stw[slot], P, dst + c0, N2, T);
         }
         __syncthreads();  // this half is refilled by the prefetch two tiles later
     }
@@ -200,12 +247,12 @@ k_ntt_cols(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
 
 // row phase: the remaining LOGM stages on ROWS contiguous blocks of M words per tile
 // (padded layout, one spare word per 16), next tile prefetched in 8-byte pieces
-template <int LOGM, int ROWS, bool INV>
-__global__ void __launch_bounds__((1 << (LOGM - Split<LOGM>::R1)) * ROWS)
+template <int LOGM, int ROWS, bool INV, bool ALT>
+__global__ void __launch_bounds__((1 << (LOGM - Split<LOGM, ALT>::R1)) * ROWS)
 k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ primes,
            const ulonglong2 *__restrict__ tw_all, int log_n, int n_tiles)
 {
-    constexpr int M = 1 << LOGM, E = M * ROWS, R1 = Split<LOGM>::R1, R2 = Split<LOGM>::R2;
+    constexpr int M = 1 << LOGM, E = M * ROWS, R1 = Split<LOGM, ALT>::R1, R2 = Split<LOGM, ALT>::R2;
     constexpr int T = (M >> R1) * ROWS;
     constexpr int SK = M + M / 8;  // padded block stride (two spare words per 16)
     extern __shared__ uint64_t sh[];
@@ -274,56 +321,68 @@ k_ntt_rows(const __grid_constant__ NttRows R, const PrimeConst *__restrict__ pri
     }
 }
 
-// tile widths the autotuner chooses from (sub-transforms per block)
-constexpr int kNttTiles[NTT_VARIANTS] = {8, 16, 32};
+// tile widths the autotuner chooses from (sub-transforms per block); a variant is a width index
+// plus NTT_WIDTHS if the phase's two register passes swap radices (odd phase sizes only)
+constexpr const int *kNttTiles = kNttTileWidths;
 
-template <int LOGM, int COLS, bool INV>
+template <int LOGM, int COLS, bool INV, bool ALT>
 void ntt_cols_w(const LaunchCtx &c, const NttRows &rows)
 {
     constexpr int M = 1 << LOGM;
     constexpr int E = M * COLS;
-    constexpr int T = (M >> Split<LOGM>::R1) * COLS;
+    constexpr int T = (M >> Split<LOGM, ALT>::R1) * COLS;
     const int N2 = c.N >> LOGM;
     HX_CHECK(N2 % COLS == 0, HX_EINVAL, "NTT tile wider than the ring");
     const long long n_tiles = (long long)(N2 / COLS) * rows.n_rows * rows.n_groups;
     HX_CHECK(n_tiles < (1ll << 31), HX_EINVAL, "NTT batch too large");
     const size_t smem = (size_t)E * 16 + (size_t)M * 32;  // two tiles + two twiddle sets
     static const bool attr =  // thread-safe one-time setup
-        cudaFuncSetAttribute(k_ntt_cols<LOGM, COLS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
-        cudaSuccess;
+        cudaFuncSetAttribute(k_ntt_cols<LOGM, COLS, INV, ALT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) == cudaSuccess;
     (void)attr;
     static const int per_sm = [&] {
         int v = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_ntt_cols<LOGM, COLS, INV>, T, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_ntt_cols<LOGM, COLS, INV, ALT>, T, smem);
         return v;
     }();
     const int grid = (int)std::min<long long>(n_tiles, (long long)std::max(1, per_sm) * c.t->n_sm);
-    k_ntt_cols<LOGM, COLS, INV><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
-                                                            c.log_n, (int)n_tiles);
+    k_ntt_cols<LOGM, COLS, INV, ALT><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
+                                                                 c.log_n, (int)n_tiles);
 }
 
-template <int LOGM, int ROWS, bool INV>
+template <int LOGM, int ROWS, bool INV, bool ALT>
 void ntt_rows_w(const LaunchCtx &c, const NttRows &rows)
 {
     constexpr int M = 1 << LOGM;
-    constexpr int T = (M >> Split<LOGM>::R1) * ROWS;
+    constexpr int T = (M >> Split<LOGM, ALT>::R1) * ROWS;
     const int N1 = c.N >> LOGM;
     HX_CHECK(N1 % ROWS == 0, HX_EINVAL, "NTT tile wider than the ring");
     const long long n_tiles = (long long)(N1 / ROWS) * rows.n_rows * rows.n_groups;
     HX_CHECK(n_tiles < (1ll << 31), HX_EINVAL, "NTT batch too large");
     const size_t smem = (size_t)ROWS * (M + M / 8) * 16;  // two tiles
     static const bool attr =  // thread-safe one-time setup
-        cudaFuncSetAttribute(k_ntt_rows<LOGM, ROWS, INV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
-        cudaSuccess;
+        cudaFuncSetAttribute(k_ntt_rows<LOGM, ROWS, INV, ALT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) == cudaSuccess;
     (void)attr;
     static const int per_sm = [&] {
         int v = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_ntt_rows<LOGM, ROWS, INV>, T, smem);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_ntt_rows<LOGM, ROWS, INV, ALT>, T, smem);
         return v;
     }();
     const int grid = (int)std::min<long long>(n_tiles, (long long)std::max(1, per_sm) * c.t->n_sm);
-    k_ntt_rows<LOGM, ROWS, INV><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
-                                                            c.log_n, (int)n_tiles);
+    k_ntt_rows<LOGM, ROWS, INV, ALT><<<grid, T, smem, c.stream>>>(rows, c.t->primes, INV ? c.t->tw_inv : c.t->tw_fwd,
+                                                                 c.log_n, (int)n_tiles);
+}
+
+template <bool INV, int LOGM, bool ALT>
+void ntt_phase_a(const LaunchCtx &c, const NttRows &r, bool cols, int wi)
+{
+    switch (wi) {
+    case 0: cols ? ntt_cols_w<LOGM, 4, INV, ALT>(c, r) : ntt_rows_w<LOGM, 4, INV, ALT>(c, r); break;
+    case 1: cols ? ntt_cols_w<LOGM, 8, INV, ALT>(c, r) : ntt_rows_w<LOGM, 8, INV, ALT>(c, r); break;
+    case 2: cols ? ntt_cols_w<LOGM, 16, INV, ALT>(c, r) : ntt_rows_w<LOGM, 16, INV, ALT>(c, r); break;
+    default: cols ? ntt_cols_w<LOGM, 32, INV, ALT>(c, r) : ntt_rows_w<LOGM, 32, INV, ALT>(c, r); break;
+    }
 }
 
 template <bool INV, int LOGM>
@@ -331,16 +390,10 @@ void ntt_phase_l(const LaunchCtx &c, const NttRows &r, bool cols, int var)
 {
     // the tile must not be wider than the other dimension of the ring
     const int other = c.N >> LOGM;
-    while (var > 0 && kNttTiles[var] > other) var--;
-    if (cols) {
-        if (var == 0) ntt_cols_w<LOGM, 8, INV>(c, r);
-        else if (var == 1) ntt_cols_w<LOGM, 16, INV>(c, r);
-        else ntt_cols_w<LOGM, 32, INV>(c, r);
-    } else {
-        if (var == 0) ntt_rows_w<LOGM, 8, INV>(c, r);
-        else if (var == 1) ntt_rows_w<LOGM, 16, INV>(c, r);
-        else ntt_rows_w<LOGM, 32, INV>(c, r);
-    }
+    int wi = var % NTT_WIDTHS;
+    while (wi > 0 && kNttTiles[wi] > other) wi--;
+    if ((LOGM & 1) && var >= NTT_WIDTHS) ntt_phase_a<INV, LOGM, (LOGM & 1) != 0>(c, r, cols, wi);
+    else ntt_phase_a<INV, LOGM, false>(c, r, cols, wi);
 }
 
 template <bool INV>
@@ -536,7 +589,7 @@ void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse)
     if (rows.n_rows <= 0 || rows.n_groups <= 0) return;
     HX_CHECK(rows.n_rows <= MAX_NTT_ROWS && rows.n_groups < 65536, HX_EINVAL, "NTT batch too large");
     const int logm1 = c.log_n / 2, logm2 = c.log_n - logm1;
-    const int *v = c.t->ntt_var;
+    const int *v = c.t->ntt_var[ntt_bucket((long long)rows.n_rows * rows.n_groups)];
     if (!inverse) {
         ntt_phase<false>(c, rows, true, logm1, v[0]);
         ntt_phase<false>(c, rows, false, logm2, v[1]);
@@ -567,8 +620,10 @@ void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float 
     for (int ph = 0; ph < 4; ph++) {
         const bool cols = ph == 0 || ph == 2, inv = ph >= 2;
         float best_ms = 1e30f;
+        const int logm = cols ? logm1 : logm2;
         for (int v = 0; v < NTT_VARIANTS; v++) {
-            if (kNttTiles[v] > (c.N >> (cols ? logm1 : logm2))) continue;
+            if (kNttTiles[v % NTT_WIDTHS] > (c.N >> logm)) continue;
+            if (v >= NTT_WIDTHS && !(logm & 1)) continue;  // even phase sizes have one radix split
             auto run = [&]() {
                 if (inv) ntt_phase<true>(c, *r, cols, cols ? logm1 : logm2, v);
                 else ntt_phase<false>(c, *r, cols, cols ? logm1 : logm2, v);

@@ -127,6 +127,7 @@ _SIGS = {
     "hx_counters_reset": (None, [c_vp]),
     "hx_autotune": (c_int, [c_vp, P_i32, c_vp]),
     "hx_ntt_tiles": (c_int, [c_vp, P_i32, P_i32]),
+    "hx_ntt_tuning": (c_int, [c_vp, P_i32, c_int]),
     "hx_profile_enable": (c_int, [c_vp, c_int]),
     "hx_profile_read": (c_int, [c_vp, c_int, ctypes.c_char_p, c_size_t, P_u64, P_dbl, P_dbl]),
 }
@@ -732,15 +733,25 @@ def hx_counters_reset(ctx: int) -> None:
 # ---- autotuning --------------------------------------------------------------------------
 
 def hx_autotune(ctx: int, stream=None) -> list:
-    """Picks the fastest NTT tile widths on this device; returns them per phase
-    (forward column, forward row, inverse column, inverse row)."""
+    """Picks the fastest NTT variants on this device for each bucket of batch sizes; returns
+    those of the 256-limb bucket per phase (forward column, forward row, inverse column,
+    inverse row) as signed tile widths (negative: swapped radices)."""
     arr = np.zeros(4, dtype=np.int32)
     _chk(lib().hx_autotune(ctx, arr.ctypes.data_as(P_i32), _stream(stream)))
     return [int(x) for x in arr]
 
 
+def hx_ntt_tuning(ctx: int) -> list:
+    """The autotuner's table: per bucket {max_limbs, tuned_limbs, widths[4]} (signed widths)."""
+    out = np.zeros(64, dtype=np.int32)
+    n = _chk(lib().hx_ntt_tuning(ctx, out.ctypes.data_as(P_i32), out.size))
+    return [{"max_limbs": int(out[i]), "tuned_limbs": int(out[i + 1]), "widths": [int(x) for x in out[i + 2:i + 6]]}
+            for i in range(0, n, 6)]
+
+
 def hx_ntt_tiles(ctx: int, widths=None) -> list:
-    """Sets the NTT tile widths per phase (if given) and returns the current ones."""
+    """Sets the NTT variants per phase for every batch bucket (if given; signed tile widths 4,
+    8, 16, 32, negative for swapped radices) and returns those of the 256-limb bucket."""
     get = np.zeros(4, dtype=np.int32)
     setp = None
     if widths is not None:

@@ -117,7 +117,7 @@ def test_ntt_every_tile_width_and_autotune(log_n):
         primes = octx.q + octx.p
         x = workloads.residues(3, primes, 2, octx.N)
         want = octx.ntt(x, primes * 2)
-        for w in ([8] * 4, [16] * 4, [32] * 4, [8, 32, 16, 8]):
+        for w in ([4] * 4, [8] * 4, [16] * 4, [32] * 4, [8, 32, 16, 8], [-4, -8, -16, -32], [-16, 4, 32, -8]):
             hx.hx_ntt_tiles(ctx, w)
             dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
             hx.hx_ntt(ctx, dev.data_ptr(), 2, [0, 1, 2])
@@ -127,7 +127,18 @@ def test_ntt_every_tile_width_and_autotune(log_n):
             torch.cuda.synchronize()
             assert np.array_equal(dev.cpu().numpy().view(np.uint64), x), w
         chosen = hx.hx_autotune(ctx)
-        assert all(c in (8, 16, 32) for c in chosen) and hx.hx_ntt_tiles(ctx) == chosen
+        assert all(abs(c) in (4, 8, 16, 32) for c in chosen) and hx.hx_ntt_tiles(ctx) == chosen
+        table = hx.hx_ntt_tuning(ctx)
+        assert len(table) == 4 and table[1]["widths"] == chosen
+        assert [t["max_limbs"] for t in table][:3] == [64, 256, 768]
+        # the tuned variants of every bucket give the same residues (a small and a large batch)
+        for polys in (2, 200):
+            y = workloads.residues(4, primes, polys, octx.N)
+            dev = torch.from_numpy(y.view(np.int64).copy()).cuda()
+            hx.hx_ntt(ctx, dev.data_ptr(), polys, [0, 1, 2])
+            torch.cuda.synchronize()
+            got = dev.cpu().numpy().view(np.uint64)
+            assert np.array_equal(got[:3], octx.ntt(y[:3], primes)) and np.array_equal(got[-3:], octx.ntt(y[-3:], primes))
     finally:
         hx.hx_context_destroy(ctx)
 
