@@ -282,21 +282,48 @@ void hx_matmul_plan_destroy(hx_matmul_plan *plan);
 /* Rotation steps (mod N/2, sorted, no 0) a product of this shape uses;
  * returns the count (writes at most cap) or a negative status. */
 int hx_matmul_rotation_steps(const hx_context *ctx, int h, int limbs, int32_t *out, int cap);
-/* One product: out = A x B for each of the beta packed pairs. */
+/* One product (Alg. 3, HE-MatMult, Sec. 3.3: A.B = sum_k phi^k(mu(A)) (.)
+ * pi^k(zeta(B)), Eq. (2), with the baby-step/giant-step linear transforms of
+ * App. B and the ι_β packing of App. E): out = A x B for each of the beta
+ * packed pairs.  A and B: ciphertexts of this context at one level (at least 4
+ * limbs for Alg. 3, exactly 3 for the depth-2 form) and scale; the plan is the
+ * context's cached one for (h, level).  HX_EKEY if a rotation key of
+ * hx_matmul_rotation_steps is missing. */
 hx_status hx_matmul(hx_context *ctx, const hx_keyset *ks, const hx_ct *A, const hx_ct *B, int h, hx_ct **out,
                     void *stream);
-/* `count` independent products through one batched schedule (every kernel
- * launch covers the whole batch; key reads are shared).  plan may be NULL
- * (library masks for the inputs' level). */
+/* `count` independent products (Alg. 3 with App. B and App. E, as hx_matmul)
+ * through one batched schedule: every kernel launch covers the whole batch
+ * and key reads are shared.  A[i], B[i]: ciphertexts of this context, all at
+ * one level and scale (HX_ESCALE otherwise).  plan may be NULL (the context's
+ * cached plan with library masks for the inputs' level).  out: `count` new
+ * handles, valid when `stream` completes; on error every out[i] is NULL. */
 hx_status hx_matmul_batch(hx_context *ctx, const hx_keyset *ks, const hx_matmul_plan *plan, const hx_ct *const *A,
                           const hx_ct *const *B, int h, size_t count, hx_ct **out, void *stream);
-/* A batch with a matrix size per entry: entries of one (h[i], level, scale) are
- * grouped and each group runs as one batched product (cached plans), the
- * groups one after another on the stream; out[i] is entry i's product.  A[i]
- * and B[i] must share level and scale (HX_ESCALE); on any error every out[i]
- * is NULL. */
+/* A batch with a matrix size per entry (Alg. 3 per entry, App. E packing per
+ * h): entries of one (h[i], level, scale) are grouped, each group runs as one
+ * batched product (cached plans), and the groups run side by side on streams
+ * of the context (forked from and joined back to `stream`); out[i] is entry
+ * i's product, identical to hx_matmul on that pair alone.  A[i] and B[i] must
+ * share level and scale (HX_ESCALE); on any error every out[i] is NULL. */
 hx_status hx_matmul_batch_mixed(hx_context *ctx, const hx_keyset *ks, const hx_ct *const *A, const hx_ct *const *B,
                                 const int *h, size_t count, hx_ct **out, void *stream);
+/* Products over several rings in one call (Alg. 3 per entry, App. E packing):
+ * job i multiplies A and B of its own context (any ring degree, prime chain
+ * and level) with that context's key set and matrix size h.  Jobs of one
+ * (context, key set, h, level, scale) form a batched group; the groups run
+ * side by side on streams forked from and joined back to `stream`, so
+ * products of different rings and levels overlap on the device.  out[i] is
+ * job i's product (a handle of job i's context), identical to hx_matmul on
+ * that pair alone.  Every handle must belong to its job's context (HX_EINVAL)
+ * and all contexts to one device; on any error every out[i] is NULL. */
+typedef struct hx_matmul_job {
+    hx_context *ctx;
+    const hx_keyset *ks;
+    const hx_ct *A;
+    const hx_ct *B;
+    int h;
+} hx_matmul_job;
+hx_status hx_matmul_jobs(const hx_matmul_job *jobs, size_t count, hx_ct **out, void *stream);
 
 /* ---- rectangular product (App. D) ------------------------------------------------ */
 /* Rectangular product (App. D, Alg. "41"): At[i] packs A~ = (A; ...; A), the

@@ -62,6 +62,78 @@ namespace hx {
 void set_error(const std::string &msg) { g_err = msg; }
 } // namespace hx
 
+namespace {
+
+// One group of a batched product call: entries of one context, key set, h, level and scale,
+// evaluated as one batched HE-MatMult.
+struct MatmulGroup {
+    hx_context *ctx;
+    const hx_keyset *ks;
+    int h;
+    std::vector<size_t> idx;  // positions in the call's entry list
+    std::vector<const hx_ct *> A, B;
+};
+
+// Runs the groups side by side: each on a stream of its context's pool, forked from s by an event,
+// so the schedules of different rings, levels and sizes overlap on the device.  After the join,
+// the products are copied into the outputs on s; each group's own buffers are released on its
+// stream only after s has made those copies.
+void run_matmul_groups(std::vector<MatmulGroup> &groups, cudaStream_t s, hx_ct **out, size_t count)
+{
+    struct Running {
+        hx_context *ctx = nullptr;
+        cudaStream_t gs = nullptr;
+        Cts r;
+    };
+    std::vector<Running> run(groups.size());
+    std::vector<hx_ct *> res(count, nullptr);
+    cudaEvent_t fork = nullptr, copied = nullptr;
+    std::vector<cudaEvent_t> done;
+    auto release = [&] {
+        if (fork) cudaEventDestroy(fork);
+        if (copied) cudaEventDestroy(copied);
+        for (cudaEvent_t e : done) cudaEventDestroy(e);
+    };
+    try {
+        HX_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        HX_CUDA(cudaEventCreateWithFlags(&copied, cudaEventDisableTiming));
+        HX_CUDA(cudaEventRecord(fork, s));
+        std::map<hx_context *, size_t> next;  // next pool stream of each context
+        for (size_t g = 0; g < groups.size(); g++) {
+            MatmulGroup &G = groups[g];
+            const cudaStream_t gs = group_stream(*G.ctx, s, next[G.ctx]++);
+            if (gs != s) HX_CUDA(cudaStreamWaitEvent(gs, fork, 0));
+            run[g].ctx = G.ctx;
+            run[g].gs = gs;
+            Cts a = gather(*G.ctx, G.A.data(), G.A.size(), gs);
+            Cts b = gather(*G.ctx, G.B.data(), G.B.size(), gs);
+            PlanUse plan(*G.ctx, gs, cached_plan(*G.ctx, G.h, a.limbs));
+            run[g].r = matmul_batch(*G.ctx, *G.ks, *plan.p, a, b, gs);
+            cudaEvent_t e = nullptr;
+            HX_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+            done.push_back(e);
+            HX_CUDA(cudaEventRecord(e, gs));
+        }
+        for (cudaEvent_t e : done) HX_CUDA(cudaStreamWaitEvent(s, e, 0));
+        for (size_t g = 0; g < groups.size(); g++) {
+            std::vector<hx_ct *> part(groups[g].idx.size(), nullptr);
+            scatter(*groups[g].ctx, run[g].r, part.data(), s);
+            for (size_t k = 0; k < part.size(); k++) res[groups[g].idx[k]] = part[k];
+        }
+        HX_CUDA(cudaEventRecord(copied, s));
+        for (auto &R : run)
+            if (R.gs && R.gs != s) HX_CUDA(cudaStreamWaitEvent(R.gs, copied, 0));
+    } catch (...) {
+        for (hx_ct *c : res) delete c;
+        release();
+        throw;
+    }
+    release();
+    std::copy(res.begin(), res.end(), out);
+}
+
+} // namespace
+
 extern "C" {
 
 const char *hx_last_error(void) { return g_err.c_str(); }
@@ -778,47 +850,46 @@ hx_status hx_matmul_batch_mixed(hx_context *ctx, const hx_keyset *ks, const hx_c
     need(ctx && ks && A && B && h && out && count >= 1 && count < 65536, "bad argument");
     for (size_t i = 0; i < count; i++) out[i] = nullptr;
     mine(ctx, ks);
-    // entries of one (h, level, scale) form a group, in order of first appearance
-    std::map<std::tuple<int, int, double>, size_t> gid;
-    std::vector<std::vector<size_t>> groups;
+    std::vector<hx_matmul_job> jobs(count);
+    for (size_t i = 0; i < count; i++) jobs[i] = hx_matmul_job{ctx, ks, A[i], B[i], h[i]};
+    return hx_matmul_jobs(jobs.data(), count, out, stream);
+    HX_END
+}
+
+hx_status hx_matmul_jobs(const hx_matmul_job *jobs, size_t count, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(jobs && out && count >= 1 && count < 65536, "bad argument");
+    for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    // entries of one (context, keys, h, level, scale) form a group, in order of first appearance
+    std::map<std::tuple<hx_context *, const hx_keyset *, int, int, double>, size_t> gid;
+    std::vector<MatmulGroup> groups;
+    int dev = -1;
     for (size_t i = 0; i < count; i++) {
-        need(A[i] && B[i], "null ciphertext");
-        mine(ctx, A[i]);
-        mine(ctx, B[i]);
-        need(h[i] >= 2 && (h[i] & (h[i] - 1)) == 0 && h[i] * h[i] <= ctx->N / 2, "h must be a power of two with h^2 <= N/2");
-        HX_CHECK(A[i]->c.comps == 2 && B[i]->c.comps == 2 && A[i]->c.limbs == B[i]->c.limbs &&
-                     A[i]->c.scale == B[i]->c.scale,
+        const hx_matmul_job &J = jobs[i];
+        need(J.ctx && J.ks && J.A && J.B, "null job field");
+        mine(J.ctx, J.ks);
+        mine(J.ctx, J.A);
+        mine(J.ctx, J.B);
+        need(dev < 0 || J.ctx->device == dev, "jobs on several devices");
+        dev = J.ctx->device;
+        need(J.h >= 2 && (J.h & (J.h - 1)) == 0 && J.h * J.h <= J.ctx->N / 2,
+             "h must be a power of two with h^2 <= N/2");
+        HX_CHECK(J.A->c.comps == 2 && J.B->c.comps == 2 && J.A->c.limbs == J.B->c.limbs &&
+                     J.A->c.scale == J.B->c.scale,
                  HX_ESCALE, "entry " + std::to_string(i) + ": A and B must be ciphertexts of one level and scale");
-        const auto key = std::make_tuple(h[i], A[i]->c.limbs, A[i]->c.scale);
+        const auto key = std::make_tuple(J.ctx, J.ks, J.h, J.A->c.limbs, J.A->c.scale);
         auto it = gid.find(key);
         if (it == gid.end()) {
             it = gid.emplace(key, groups.size()).first;
-            groups.emplace_back();
+            groups.push_back(MatmulGroup{J.ctx, J.ks, J.h, {}, {}, {}});
         }
-        groups[it->second].push_back(i);
+        MatmulGroup &G = groups[it->second];
+        G.idx.push_back(i);
+        G.A.push_back(J.A);
+        G.B.push_back(J.B);
     }
-    const cudaStream_t s = S(stream);
-    std::vector<hx_ct *> res(count, nullptr);
-    try {
-        for (const auto &g : groups) {  // each group one batched product (its own chains inside)
-            std::vector<const hx_ct *> ga, gb;
-            for (size_t i : g) {
-                ga.push_back(A[i]);
-                gb.push_back(B[i]);
-            }
-            Cts a = gather(*ctx, ga.data(), g.size(), s);
-            Cts b = gather(*ctx, gb.data(), g.size(), s);
-            PlanUse plan(*ctx, s, cached_plan(*ctx, h[g[0]], a.limbs));
-            Cts r = matmul_batch(*ctx, *ks, *plan.p, a, b, s);
-            std::vector<hx_ct *> part(g.size(), nullptr);
-            scatter(*ctx, r, part.data(), s);
-            for (size_t k = 0; k < g.size(); k++) res[g[k]] = part[k];
-        }
-    } catch (...) {
-        for (hx_ct *c : res) delete c;
-        throw;
-    }
-    std::copy(res.begin(), res.end(), out);
+    run_matmul_groups(groups, S(stream), out, count);
     return HX_OK;
     HX_END
 }

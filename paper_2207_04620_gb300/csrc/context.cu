@@ -310,6 +310,18 @@ SideStream &side_stream(hx_context &ctx, cudaStream_t main)
     return ss;
 }
 
+cudaStream_t group_stream(hx_context &ctx, cudaStream_t main, size_t i)
+{
+    if (ctx.profiling) return main;
+    std::lock_guard<std::mutex> lk(ctx.side_mu);
+    while (ctx.group_streams.size() <= i) {
+        cudaStream_t s = nullptr;
+        HX_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        ctx.group_streams.push_back(s);
+    }
+    return ctx.group_streams[i];
+}
+
 void destroy_context(hx_context &c)
 {
     cudaDeviceSynchronize();
@@ -331,6 +343,8 @@ void destroy_context(hx_context &c)
         for (auto &e : kv.second.e)
             if (e) cudaEventDestroy(e);
     c.side_serial.clear();
+    for (cudaStream_t s : c.group_streams) cudaStreamDestroy(s);
+    c.group_streams.clear();
     cudaFree(c.t.primes);
     cudaFree(c.t.tw_fwd);
     cudaFree(c.t.tw_inv);

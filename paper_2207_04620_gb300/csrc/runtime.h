@@ -103,6 +103,7 @@ struct hx_context {
     std::mutex side_mu;
     std::map<cudaStream_t, hx::SideStream> side;         // keyed by the caller's stream
     std::map<cudaStream_t, hx::SideStream> side_serial;  // profiling: the caller's stream itself
+    std::vector<cudaStream_t> group_streams;  // groups of one batched call run side by side (guarded by side_mu)
 };
 
 struct hx_keyset {
@@ -288,6 +289,9 @@ Cts aggregate(hx_context &ctx, const std::vector<const Cts *> &grads, int n_part
 // ---- context (context.cu) -------------------------------------------------------
 // the side stream paired with `main` (created on first use, destroyed with the context)
 SideStream &side_stream(hx_context &ctx, cudaStream_t main);
+// stream i of the context's pool for the independent groups of one batched call (created on first
+// use, destroyed with the context); while profiling, `main` itself, so the groups run in turn
+cudaStream_t group_stream(hx_context &ctx, cudaStream_t main, size_t i);
 void build_context(hx_context &ctx, const hx_params &p);
 void destroy_context(hx_context &ctx);
 Cts gather(hx_context &ctx, const hx_ct *const *cts, size_t count, cudaStream_t s);

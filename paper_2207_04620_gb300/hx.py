@@ -55,6 +55,7 @@ _SIGS = {
     "hx_decrypt_parties": (c_int, [c_vp, c_vp, c_vp, ctypes.POINTER(ctypes.c_uint8), c_size_t, P_dbl, c_size_t]),
     "hx_ct_save": (c_int, [c_vp, c_vp, ctypes.c_char_p]),
     "hx_matmul_batch_mixed": (c_int, [c_vp, c_vp, PP, PP, P_i32, c_size_t, PP, c_vp]),
+    "hx_matmul_jobs": (c_int, [c_vp, c_size_t, PP, c_vp]),
     "hx_keyset_save": (c_int, [c_vp, c_vp, ctypes.c_char_p]),
     "hx_keyset_load": (c_int, [c_vp, ctypes.c_char_p, PP]),
     "hx_ct_load": (c_int, [c_vp, ctypes.c_char_p, PP]),
@@ -513,6 +514,22 @@ def hx_matmul_batch_mixed(ctx: int, ks: int, A, B, h, stream=None) -> list:
     a, b, out = (c_vp * n)(*A), (c_vp * n)(*B), (c_vp * n)()
     hs = np.ascontiguousarray(np.asarray(h, dtype=np.int32))
     _chk(lib().hx_matmul_batch_mixed(ctx, ks, a, b, hs.ctypes.data_as(P_i32), n, out, _stream(stream)))
+    return [out[i] for i in range(n)]
+
+
+class _MatmulJob(ctypes.Structure):
+    _fields_ = [("ctx", c_vp), ("ks", c_vp), ("A", c_vp), ("B", c_vp), ("h", c_int)]
+
+
+def hx_matmul_jobs(jobs, stream=None) -> list:
+    """Products over several rings in one call: jobs = [(ctx, ks, A, B, h), ...]; returns one
+    product handle per job (of that job's context)."""
+    n = len(jobs)
+    if n == 0:
+        raise ValueError("no jobs")
+    arr = (_MatmulJob * n)(*[_MatmulJob(*j) for j in jobs])
+    out = (c_vp * n)()
+    _chk(lib().hx_matmul_jobs(arr, n, out, _stream(stream)))
     return [out[i] for i in range(n)]
 
 

@@ -13,6 +13,8 @@ PARAMS = {
     "cfg0": dict(log_n=12, q_bits=[60, 40, 40], p_bits=[60], log2_scale=40),
     # small chain with 4 levels (Alg. 3) and two special primes
     "alg3": dict(log_n=12, q_bits=[60, 45, 45, 45, 45], p_bits=[60, 60], log2_scale=45),
+    # the next ring with one more level (several-ring batches and serving)
+    "alg3_13": dict(log_n=13, q_bits=[60, 45, 45, 45, 45, 45], p_bits=[60, 60], log2_scale=45),
     # config 1 of the benchmark: N=2^14, 60 + 7*45, two 60-bit special primes, scale 2^45
     "cfg1": dict(log_n=14, q_bits=[60] + [45] * 7, p_bits=[60, 60], log2_scale=45),
     # the sign chain of config 2 on a smaller ring: 60 + 15*40, three special primes

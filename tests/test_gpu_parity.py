@@ -527,6 +527,45 @@ def test_rectangular_matmul_bit_exact(name, h, t):
         pr.close()
 
 
+def test_products_over_two_rings_in_one_call_bit_exact():
+    """hx_matmul_jobs: products of two rings (N = 2^12 and 2^13, chains of 5 and 6 limbs), two
+    levels and two matrix sizes in one call, the groups running side by side on the device;
+    every entry equals the oracle's HE-MatMult of its pair bit for bit and decrypts to A@B."""
+    specs = [("alg3", 8, 5), ("alg3", 16, 4), ("alg3_13", 8, 6), ("alg3_13", 8, 4), ("alg3", 8, 5)]
+    pairs = {}
+    for name in ("alg3", "alg3_13"):
+        S = (1 << PARAMS[name]["log_n"]) // 2
+        steps = set()
+        for n2, h, limbs in specs:
+            if n2 == name:
+                steps |= set(Hc.matmul_rotation_steps(h, S // (h * h), limbs))
+        pairs[name] = Pair(name, rot_steps=sorted(steps))
+    try:
+        jobs, want, mats = [], [], []
+        for i, (name, h, limbs) in enumerate(specs):
+            pr = pairs[name]
+            beta = pr.octx.S // (h * h)
+            ma, mb = workloads.matrices(90 + i, beta, h), workloads.matrices(95 + i, beta, h)
+            A = pr.encrypt(workloads.pack(ma, h, beta), 400 + i, limbs=limbs)
+            B = pr.encrypt(workloads.pack(mb, h, beta), 500 + i, limbs=limbs)
+            jobs.append((pr.ctx, pr.ks, pr.to_lib(A), pr.to_lib(B), h))
+            want.append(Hc.matmul(C.Evaluator(pr.octx, pr.oks), A, B, h, Hc.MaskProvider(pr.octx, h, limbs)))
+            mats.append((ma, mb, beta))
+        outs = hx.hx_matmul_jobs(jobs)
+        for (name, h, limbs), o, w, (ma, mb, beta) in zip(specs, outs, want, mats):
+            pr = pairs[name]
+            assert pr.same(o, w), (name, h, limbs)
+            got = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, o), h, beta)
+            assert max(np.abs(g - a @ b).max() for g, a, b in zip(got, ma, mb)) <= 2 ** -18
+            hx.hx_ct_destroy(o)
+        for j in jobs:
+            hx.hx_ct_destroy(j[2])
+            hx.hx_ct_destroy(j[3])
+    finally:
+        for pr in pairs.values():
+            pr.close()
+
+
 def test_matmul_library_masks_end_to_end():
     """The product path: library encryption, library masks, library decryption;
     config 0 (N=2^12, h=16, one product with the other packed slots zero)."""

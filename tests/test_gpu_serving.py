@@ -216,3 +216,75 @@ def test_mixed_size_batch_equals_products_alone(setup):
         hx.hx_matmul_batch_mixed(ctx, ks, A[:2], B[:2], [H[0], 12])   # not a power of two
     assert e.value.code == -1
     hx.hx_ct_destroy(low)
+
+
+def test_two_rings_in_one_server_equal_requests_alone(setup):
+    """One server over two contexts of different ring degree and chain length (N = 2^12 with
+    5 limbs, N = 2^13 with 6 limbs): a stream of matmuls and signs of both rings at several
+    levels, submitted together, batched per signature and run across lanes; every result equals
+    the same request computed alone, bit for bit."""
+    ctx, ks, s = setup
+    p = PARAMS["alg3_13"]
+    ctx2 = hx.hx_context_create(p["log_n"], p["q_bits"], p["p_bits"], p["log2_scale"])
+    s2 = (1 << p["log_n"]) // 2
+    steps2 = sorted(set(Hc.matmul_rotation_steps(8, s2 // 64, 6)) | set(Hc.matmul_rotation_steps(8, s2 // 64, 4))
+                    | set(Hc.matmul_rotation_steps(16, s2 // 256, 5)))
+    ks2 = hx.hx_keygen(ctx2, 2, 41, steps2)
+    try:
+        reqs = [(ctx, ks, kind, args) for kind, args in _requests(ctx, ks, s)[:6]]
+        for i, (h, limbs) in enumerate(((8, 6), (16, 5), (8, 4), (8, 6))):
+            beta = s2 // (h * h)
+            a = hx.hx_encrypt(ctx2, ks2, workloads.pack(workloads.matrices(700 + i, beta, h), h, beta), limbs, 70 + i)
+            b = hx.hx_encrypt(ctx2, ks2, workloads.pack(workloads.matrices(800 + i, beta, h), h, beta), limbs, 80 + i)
+            reqs.append((ctx2, ks2, "matmul", (a, b, h)))
+        for i, d in enumerate((2, 4)):
+            x = hx.hx_encrypt(ctx2, ks2, workloads.sign_inputs(60 + i, s2), 6, 90 + i)
+            reqs.append((ctx2, ks2, "sign", (x, d, 1, 2000 + i)))
+        order = np.random.default_rng(5).permutation(len(reqs))  # the rings interleaved
+        reqs = [reqs[i] for i in order]
+        sv = hx.hx_server_create(64 << 30, 3, 4)
+        hx.hx_server_register_keys(sv, ks)
+        hx.hx_server_register_keys(sv, ks2)
+        ids = [_submit(sv, c, k, kind, args) for c, k, kind, args in reqs]
+        got = _collect(sv, len(ids))
+        stats = hx.hx_server_stats(sv)
+        hx.hx_server_destroy(sv)
+        assert stats["completed"] == len(reqs)
+        for rid, (c, k, kind, args) in zip(ids, reqs):
+            res, st, lat = got[rid]
+            assert st == 0 and lat > 0
+            alone = _alone(c, k, kind, args)
+            assert np.array_equal(hx.hx_ct_export(c, res), hx.hx_ct_export(c, alone)), (kind, c == ctx2)
+            hx.hx_ct_destroy(res)
+            hx.hx_ct_destroy(alone)
+    finally:
+        hx.hx_keyset_destroy(ks2)
+        hx.hx_context_destroy(ctx2)
+
+
+def test_several_ring_call_equals_products_alone(setup):
+    """hx_matmul_jobs with both rings: the same results as hx_matmul on each pair alone."""
+    ctx, ks, s = setup
+    p = PARAMS["alg3_13"]
+    ctx2 = hx.hx_context_create(p["log_n"], p["q_bits"], p["p_bits"], p["log2_scale"])
+    s2 = (1 << p["log_n"]) // 2
+    ks2 = hx.hx_keygen(ctx2, 2, 43, sorted(set(Hc.matmul_rotation_steps(16, s2 // 256, 6))))
+    try:
+        jobs = [(ctx, ks, a, b, h) for _, (a, b, h) in [r for r in _requests(ctx, ks, s) if r[0] == "matmul"][:3]]
+        beta = s2 // 256
+        for i in range(2):
+            a = hx.hx_encrypt(ctx2, ks2, workloads.pack(workloads.matrices(30 + i, beta, 16), 16, beta), 6, 30 + i)
+            b = hx.hx_encrypt(ctx2, ks2, workloads.pack(workloads.matrices(40 + i, beta, 16), 16, beta), 6, 40 + i)
+            jobs.insert(1 + 2 * i, (ctx2, ks2, a, b, 16))
+        outs = hx.hx_matmul_jobs(jobs)
+        for (c, k, a, b, h), o in zip(jobs, outs):
+            alone = hx.hx_matmul(c, k, a, b, h)
+            assert np.array_equal(hx.hx_ct_export(c, o), hx.hx_ct_export(c, alone))
+            hx.hx_ct_destroy(alone)
+            hx.hx_ct_destroy(o)
+        with pytest.raises(hx.HxError) as e:  # a job whose keys belong to the other ring
+            hx.hx_matmul_jobs([jobs[0], (ctx, ks2, jobs[0][2], jobs[0][3], jobs[0][4])])
+        assert e.value.code == -1
+    finally:
+        hx.hx_keyset_destroy(ks2)
+        hx.hx_context_destroy(ctx2)
