@@ -334,7 +334,12 @@ def run_hx(args, world, rank, local):
     roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
                 "launches": n_launch, "avg_launch_us": round(dom_ms / n_launch * 1e3, 2),
-                "alg_bytes_per_launch": dom_bytes / n_launch}
+                "alg_bytes_per_launch": dom_bytes / n_launch,
+                "method": "one profiled step of the same batched schedule with its chains run one after another "
+                          "on the launching stream (CUDA events around every launch of a class); the timed graph "
+                          "overlaps the chains, so these are per-kernel speeds, not shares of the graph's time; "
+                          "traffic: ncu DRAM bytes per algorithmic byte of the NTT phase kernels "
+                          "(profiles/traffic.json) times this launch's algorithmic bytes"}
     if dom == "ntt":
         # the integer-issue ceiling beside it: one Shoup product per butterfly, log2(N)/32
         # butterflies per algorithmic byte (N/2 log2 N butterflies per 16 N bytes)
