@@ -163,7 +163,8 @@ void build_context(hx_context &c, const hx_params &p)
                     uint64_t qt = 1;
                     for (int k = lo; k < hi; k++)
                         if (k != lo + i) qt = hmul(qt, c.primes[k] % t, t);
-                    T.mont[i][d] = to_mont_host(qt, t);
+                    T.w[i][d] = qt;
+                    T.w_sh[i][d] = shoup_companion(qt, t);
                 }
             }
         }
@@ -196,7 +197,8 @@ void build_context(hx_context &c, const hx_params &p)
                 uint64_t pt = 1;
                 for (int m = 0; m < K; m++)
                     if (m != k) pt = hmul(pt, c.primes[n_q + m] % t, t);
-                T.mont[k][i] = to_mont_host(pt, t);
+                T.w[k][i] = pt;
+                T.w_sh[k][i] = shoup_companion(pt, t);
             }
         }
         for (int i = 0; i < l; i++) {
@@ -247,7 +249,10 @@ void build_context(hx_context &c, const hx_params &p)
             const uint64_t sk = c.primes[T.src_prime[k]];
             T.inv[k] = hinv(prod_mod(k, sk), sk);
             T.inv_sh[k] = shoup_companion(T.inv[k], sk);
-            for (int i = 0; i < l - 1; i++) T.mont[k][i] = to_mont_host(prod_mod(k, c.primes[i]), c.primes[i]);
+            for (int i = 0; i < l - 1; i++) {
+                T.w[k][i] = prod_mod(k, c.primes[i]);
+                T.w_sh[k][i] = shoup_companion(T.w[k][i], c.primes[i]);
+            }
         }
         // h = floor(P q_top / 2) = (P q_top - 1) / 2, the product being odd: h = (P q_top - 1) * 2^-1 mod t
         auto half_mod = [&](uint64_t t) {

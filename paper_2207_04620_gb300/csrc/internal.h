@@ -32,7 +32,7 @@ inline int ntt_bucket(long long limbs)
 }
 
 // Fast basis conversion table (Han-Ki hybrid key switching, no correction):
-// out_t = sum_i [x_i * qhat_i^-1]_{q_i} * (qhat_i mod t)  (mod t)
+// out_t = sum_i [x_i * qhat_i^-1]_{q_i} * (qhat_i mod t)  (mod t), every term a Shoup product
 struct ConvTable {
     int n_src, n_dst;
     int src_row[MAXK];        // rows of the source buffer
@@ -40,7 +40,7 @@ struct ConvTable {
     int dst_row[MAXP];        // rows of the destination buffer
     int dst_prime[MAXP];
     uint64_t inv[MAXK], inv_sh[MAXK];   // [qhat_i^-1]_{q_i} with Shoup companion
-    uint64_t mont[MAXK][MAXP];          // (qhat_i mod t) * 2^64 mod t (Montgomery form)
+    uint64_t w[MAXK][MAXP], w_sh[MAXK][MAXP];  // qhat_i mod t with its Shoup companion
     // shift != 0: the rounded division's remainder.  Convert x + h exactly (the overshoot
     // u = floor(sum_i y_i / q_i), summed in FP64, times the source product is removed),
     // then subtract h

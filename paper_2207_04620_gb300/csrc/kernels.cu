@@ -250,19 +250,21 @@ __global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2)
     // staged in shared memory once per block
     const int bz = blockIdx.z, bi = bz / groups, gi = bz % groups;
     const ConvTable &T = tabs[gi];
-    __shared__ uint64_t smont[MAXK * MAXP];
-    __shared__ uint64_t sq[MAXP], sbar[MAXP], smneg[MAXP];
+    __shared__ uint64_t sw[MAXK * MAXP], swsh[MAXK * MAXP];
+    __shared__ uint64_t sq[MAXP], sbar[MAXP];
     __shared__ uint64_t ssq[MAXK], sinv[MAXK], sinvsh[MAXK], sadd[MAXK], ssub[MAXP], spq[MAXP];
     __shared__ double sinvd[MAXK];
     __shared__ int sdrow[MAXP], ssrow[MAXK];
     const int ns = T.n_src, nd = T.n_dst;
     const bool shift = T.shift != 0;
-    for (int i = threadIdx.x; i < ns * nd; i += blockDim.x) smont[i] = T.mont[i / nd][i % nd];
+    for (int i = threadIdx.x; i < ns * nd; i += blockDim.x) {
+        sw[i] = T.w[i / nd][i % nd];
+        swsh[i] = T.w_sh[i / nd][i % nd];
+    }
     for (int d = threadIdx.x; d < nd; d += blockDim.x) {
         const PrimeConst P = primes[T.dst_prime[d]];
         sq[d] = P.q;
         sbar[d] = P.bar;
-        smneg[d] = P.mneg;
         sdrow[d] = T.dst_row[d];
         ssub[d] = T.sub_dst[d];
         spq[d] = T.prod_mod[d];
@@ -305,18 +307,21 @@ __global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2)
             u1 = __double2ull_rd(v1);
         }
         for (int d = 0; d < nd; d++) {
-            Acc128 a0, a1;
+            // each term a Shoup product below 2q, the running sum kept below 2q
+            const uint64_t q = sq[d], bar = sbar[d], two_q = 2 * q;
+            uint64_t s0 = 0, s1 = 0;
 #pragma unroll
             for (int i = 0; i < MK; i++)
                 if (i < ns) {
-                    const uint64_t m = smont[i * nd + d];
-                    a0.mac(y0[i], m);
-                    a1.mac(y1[i], m);
+                    const uint64_t w = sw[i * nd + d], wsh = swsh[i * nd + d];
+                    s0 += shoup_lazy(y0[i], w, wsh, q);
+                    s1 += shoup_lazy(y1[i], w, wsh, q);
+                    if (s0 >= two_q) s0 -= two_q;
+                    if (s1 >= two_q) s1 -= two_q;
                 }
-            const uint64_t q = sq[d], bar = sbar[d], mneg = smneg[d];
             ulonglong2 r;
-            r.x = csub(csub(a0.hi - __umul64hi(a0.hi, bar) * q, q) + mont64(a0.lo, q, mneg), q);
-            r.y = csub(csub(a1.hi - __umul64hi(a1.hi, bar) * q, q) + mont64(a1.lo, q, mneg), q);
+            r.x = csub(s0, q);
+            r.y = csub(s1, q);
             if (shift) {  // u <= sources - 1 <= 6, so u * (product mod q) < 2^64
                 r.x = submod(submod(r.x, reduce64(u0 * spq[d], q, bar), q), ssub[d], q);
                 r.y = submod(submod(r.y, reduce64(u1 * spq[d], q, bar), q), ssub[d], q);
