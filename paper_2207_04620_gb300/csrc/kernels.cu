@@ -126,9 +126,9 @@ __global__ void __launch_bounds__(128) k_lintrans_mac(const __grid_constant__ Ma
                 }
             }
             *reinterpret_cast<ulonglong2 *>(A.out + g * gstride + oo0 + j) =
-                make_ulonglong2(mont128(a0.hi, a0.lo, P), mont128(a1.hi, a1.lo, P));
+                make_ulonglong2(redc_few(a0.hi, a0.lo, P), redc_few(a1.hi, a1.lo, P));
             *reinterpret_cast<ulonglong2 *>(A.out + g * gstride + oo1 + j) =
-                make_ulonglong2(mont128(b0.hi, b0.lo, P), mont128(b1.hi, b1.lo, P));
+                make_ulonglong2(redc_few(b0.hi, b0.lo, P), redc_few(b1.hi, b1.lo, P));
         }
     }
 }
@@ -145,8 +145,8 @@ __global__ void k_mul_plain(View out, View a, const uint64_t *__restrict__ pt, c
         const ulonglong2 x = *reinterpret_cast<const ulonglong2 *>(a.p + oa + j);
         const ulonglong2 w = *reinterpret_cast<const ulonglong2 *>(pt + (size_t)l * n + j);
         ulonglong2 r;
-        r.x = mont128(__umul64hi(x.x, w.x), x.x * w.x, P);
-        r.y = mont128(__umul64hi(x.y, w.y), x.y * w.y, P);
+        r.x = redc_few(__umul64hi(x.x, w.x), x.x * w.x, P);
+        r.y = redc_few(__umul64hi(x.y, w.y), x.y * w.y, P);
         *reinterpret_cast<ulonglong2 *>(out.p + oo + j) = r;
     }
 }
@@ -190,9 +190,9 @@ __device__ __forceinline__ void tensor_one(uint64_t a0, uint64_t a1, uint64_t b0
     Acc128 d1;
     d1.mac(a0, b1);
     d1.mac(a1, b0);
-    r0 = shoup(mont128(__umul64hi(a0, b0), a0 * b0, P), P.r_mod, P.r_mod_sh, P.q);
-    r1 = shoup(mont128(d1.hi, d1.lo, P), P.r_mod, P.r_mod_sh, P.q);
-    r2 = shoup(mont128(__umul64hi(a1, b1), a1 * b1, P), P.r_mod, P.r_mod_sh, P.q);
+    r0 = shoup(redc_few(__umul64hi(a0, b0), a0 * b0, P), P.r_mod, P.r_mod_sh, P.q);
+    r1 = shoup(redc_few(d1.hi, d1.lo, P), P.r_mod, P.r_mod_sh, P.q);
+    r2 = shoup(redc_few(__umul64hi(a1, b1), a1 * b1, P), P.r_mod, P.r_mod_sh, P.q);
 }
 
 __global__ void k_tensor(View out, View a, View b, const PrimeConst *__restrict__ primes, int n, bool acc)
@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2)
 // elsewhere.  Keys are in Montgomery form, so one reduction gives the sum.
 __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt, size_t dnt_bstride,
                          const uint64_t *__restrict__ key, const PrimeConst *__restrict__ primes, int n_all, int n_q,
-                         int K, int alpha, int limbs, int ndig, uint64_t g, int log_n, bool accumulate)
+                         int K, int alpha, int limbs, int ndig, uint64_t g, int log_n, bool accumulate, bool few)
 {
     const int n = 1 << log_n;
     const int t = blockIdx.y, bi = blockIdx.z;
@@ -363,8 +363,14 @@ __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_
             a1.mac(x0, k1.x);
             b1.mac(x1, k1.y);
         }
-        ulonglong2 r0 = make_ulonglong2(mont128(a0.hi, a0.lo, P), mont128(b0.hi, b0.lo, P));
-        ulonglong2 r1 = make_ulonglong2(mont128(a1.hi, a1.lo, P), mont128(b1.hi, b1.lo, P));
+        ulonglong2 r0, r1;
+        if (few) {
+            r0 = make_ulonglong2(redc_few(a0.hi, a0.lo, P), redc_few(b0.hi, b0.lo, P));
+            r1 = make_ulonglong2(redc_few(a1.hi, a1.lo, P), redc_few(b1.hi, b1.lo, P));
+        } else {
+            r0 = make_ulonglong2(mont128(a0.hi, a0.lo, P), mont128(b0.hi, b0.lo, P));
+            r1 = make_ulonglong2(mont128(a1.hi, a1.lo, P), mont128(b1.hi, b1.lo, P));
+        }
         ulonglong2 *o0 = reinterpret_cast<ulonglong2 *>(acc.p + bi * acc.bstride + (size_t)t * n + j);
         ulonglong2 *o1 = reinterpret_cast<ulonglong2 *>(acc.p + bi * acc.bstride + acc.cstride + (size_t)t * n + j);
         if (accumulate) {
@@ -385,7 +391,7 @@ __global__ void k_key_ip_mux(View out, const uint64_t *__restrict__ D, const uin
                              size_t dnt_bstride, const uint64_t *__restrict__ key1, const uint64_t *__restrict__ key2,
                              const uint64_t *__restrict__ v, const __grid_constant__ Scalars cs,
                              const PrimeConst *__restrict__ primes, int n_all, int n_q, int K, int alpha, int limbs,
-                             int ndig, uint64_t g1, uint64_t g2, int log_n)
+                             int ndig, uint64_t g1, uint64_t g2, int log_n, bool few)
 {
     const int n = 1 << log_n;
     const int t = blockIdx.y, bi = blockIdx.z;
@@ -410,11 +416,13 @@ __global__ void k_key_ip_mux(View out, const uint64_t *__restrict__ D, const uin
             y1.mac(b, key2[ko + (size_t)n_all * n]);
         }
         const uint64_t vv = v[(size_t)t * n + j];
-        const uint64_t xr0 = mont128(x0.hi, x0.lo, P), yr0 = mont128(y0.hi, y0.lo, P);
-        const uint64_t xr1 = mont128(x1.hi, x1.lo, P), yr1 = mont128(y1.hi, y1.lo, P);
+        const uint64_t xr0 = few ? redc_few(x0.hi, x0.lo, P) : mont128(x0.hi, x0.lo, P);
+        const uint64_t yr0 = few ? redc_few(y0.hi, y0.lo, P) : mont128(y0.hi, y0.lo, P);
+        const uint64_t xr1 = few ? redc_few(x1.hi, x1.lo, P) : mont128(x1.hi, x1.lo, P);
+        const uint64_t yr1 = few ? redc_few(y1.hi, y1.lo, P) : mont128(y1.hi, y1.lo, P);
         const uint64_t d0 = submod(xr0, yr0, P.q), d1 = submod(xr1, yr1, P.q);
-        const uint64_t z0 = addmod(shoup(yr0, c, csh, P.q), mont128(__umul64hi(vv, d0), vv * d0, P), P.q);
-        const uint64_t z1 = addmod(shoup(yr1, c, csh, P.q), mont128(__umul64hi(vv, d1), vv * d1, P), P.q);
+        const uint64_t z0 = addmod(shoup(yr0, c, csh, P.q), redc_few(__umul64hi(vv, d0), vv * d0, P), P.q);
+        const uint64_t z1 = addmod(shoup(yr1, c, csh, P.q), redc_few(__umul64hi(vv, d1), vv * d1, P), P.q);
         out.p[bi * out.bstride + (size_t)t * n + j] = z0;
         out.p[bi * out.bstride + out.cstride + (size_t)t * n + j] = z1;
     }
@@ -437,15 +445,15 @@ __global__ void k_premask_keys(uint64_t *out, const uint64_t *__restrict__ key1,
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const uint64_t vv = v[(size_t)t * n + j], k1 = key1[ko + j], k2 = key2[ko + j];
         const uint64_t w = submod(cr, vv, P.q);  // (c - v) in Montgomery form
-        o1[j] = mont128(__umul64hi(vv, k1), vv * k1, P);
-        o2[j] = mont128(__umul64hi(w, k2), w * k2, P);
+        o1[j] = redc_few(__umul64hi(vv, k1), vv * k1, P);
+        o2[j] = redc_few(__umul64hi(w, k2), w * k2, P);
     }
 }
 
 __global__ void k_key_ip_mux_pm(View out, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt,
                                 size_t dnt_bstride, const uint64_t *__restrict__ pk,
                                 const PrimeConst *__restrict__ primes, int n_q, int K, int alpha, int limbs, int ndig,
-                                uint64_t g1, uint64_t g2, int log_n)
+                                uint64_t g1, uint64_t g2, int log_n, bool few)
 {
     const int n = 1 << log_n;
     const int t = blockIdx.y, bi = blockIdx.z;
@@ -479,10 +487,16 @@ __global__ void k_key_ip_mux_pm(View out, const uint64_t *__restrict__ D, const 
             z1b.mac(xb, p1.y);
             z1b.mac(yb, q1.y);
         }
-        *reinterpret_cast<ulonglong2 *>(out.p + bi * out.bstride + (size_t)t * n + j) =
-            make_ulonglong2(mont128(z0a.hi, z0a.lo, P), mont128(z0b.hi, z0b.lo, P));
-        *reinterpret_cast<ulonglong2 *>(out.p + bi * out.bstride + out.cstride + (size_t)t * n + j) =
-            make_ulonglong2(mont128(z1a.hi, z1a.lo, P), mont128(z1b.hi, z1b.lo, P));
+        ulonglong2 r0, r1;
+        if (few) {
+            r0 = make_ulonglong2(redc_few(z0a.hi, z0a.lo, P), redc_few(z0b.hi, z0b.lo, P));
+            r1 = make_ulonglong2(redc_few(z1a.hi, z1a.lo, P), redc_few(z1b.hi, z1b.lo, P));
+        } else {
+            r0 = make_ulonglong2(mont128(z0a.hi, z0a.lo, P), mont128(z0b.hi, z0b.lo, P));
+            r1 = make_ulonglong2(mont128(z1a.hi, z1a.lo, P), mont128(z1b.hi, z1b.lo, P));
+        }
+        *reinterpret_cast<ulonglong2 *>(out.p + bi * out.bstride + (size_t)t * n + j) = r0;
+        *reinterpret_cast<ulonglong2 *>(out.p + bi * out.bstride + out.cstride + (size_t)t * n + j) = r1;
     }
 }
 
@@ -552,7 +566,7 @@ __global__ void k_moddown_final_mux(View out, View acc, View conv, const ModDown
                 const uint64_t s1 = c0[galois_src(j + u, g1, log_n)], s2 = c0[galois_src(j + u, g2, log_n)];
                 const uint64_t d = submod(s1, s2, q);
                 const uint64_t sel =
-                    addmod(shoup(s2, cs.v[t], cs.sh[t], q), mont128(__umul64hi(vs[u], d), vs[u] * d, P), q);
+                    addmod(shoup(s2, cs.v[t], cs.sh[t], q), redc_few(__umul64hi(vs[u], d), vs[u] * d, P), q);
                 r[u] = addmod(r[u], sel, q);
             }
         }
@@ -882,7 +896,7 @@ void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64
     Timed tm_(c, K_KEYIP, 8.0 * c.N * ((double)B * ndig * (limbs + K) + 2.0 * ndig * (limbs + K) + 2.0 * B * (limbs + K)));
     dim3 grid(ew_blocks(c.N, 2), limbs + K, B);
     k_key_ip<<<grid, 256, 0, c.stream>>>(acc, D, dnt, dnt_bstride, key, c.t->primes, n_all, n_q, K, alpha, limbs, ndig, g,
-                                         c.log_n, accumulate);
+                                         c.log_n, accumulate, ndig <= kRedcFewTerms);
     post(c);
 }
 
@@ -904,7 +918,7 @@ void launch_key_ip_mux(const LaunchCtx &c, View out, const uint64_t *D, const ui
                                         2.0 * B * (limbs + K)));
     dim3 grid(ew_blocks(c.N, 1), limbs + K, B);
     k_key_ip_mux<<<grid, 256, 0, c.stream>>>(out, D, dnt, dnt_bstride, key1, key2, v, cs, c.t->primes, n_all, n_q, K,
-                                             alpha, limbs, ndig, g1, g2, c.log_n);
+                                             alpha, limbs, ndig, g1, g2, c.log_n, ndig <= kRedcFewTerms);
     post(c);
 }
 
@@ -924,7 +938,7 @@ void launch_key_ip_mux_pm(const LaunchCtx &c, View out, const uint64_t *D, const
                                         2.0 * B * (limbs + K)));
     dim3 grid(ew_blocks(c.N, 2), limbs + K, B);
     k_key_ip_mux_pm<<<grid, 256, 0, c.stream>>>(out, D, dnt, dnt_bstride, pk, c.t->primes, n_q, K, alpha, limbs, ndig, g1, g2,
-                                                c.log_n);
+                                                c.log_n, 2 * ndig <= kRedcFewTerms);
     post(c);
 }
 

@@ -56,6 +56,20 @@ __device__ __forceinline__ uint64_t mont128(uint64_t hi, uint64_t lo, const Prim
     return csub(reduce64(hi, p.q, p.bar) + mont64(lo, p.q, p.mneg), p.q);
 }
 
+// (hi*2^64 + lo) * 2^-64 mod q in one Montgomery step (REDC), valid for hi < 3q: a sum of fewer
+// than 24 products of residues, since q < 2^61 keeps each product's high word below q/8.  The
+// quotient step leaves t = hi + umulhi(m, q) + [lo != 0] < 4q, two conditional subtractions.
+__device__ __forceinline__ uint64_t redc_few(uint64_t hi, uint64_t lo, const PrimeConst &p)
+{
+    const uint64_t m = lo * p.mneg;
+    uint64_t t = hi + __umul64hi(m, p.q) + (lo != 0 ? 1u : 0u);
+    if (t >= 2 * p.q) t -= 2 * p.q;
+    return csub(t, p.q);
+}
+
+// products accumulated per output for which redc_few applies
+constexpr int kRedcFewTerms = 23;
+
 __device__ __forceinline__ uint64_t addmod(uint64_t a, uint64_t b, uint64_t q) { return csub(a + b, q); }
 __device__ __forceinline__ uint64_t submod(uint64_t a, uint64_t b, uint64_t q) { return a >= b ? a - b : a + q - b; }
 
@@ -75,7 +89,7 @@ struct Acc128 {
 // product with (2^64 mod q) restores the factor.
 __device__ __forceinline__ uint64_t mulmod(uint64_t a, uint64_t b, const PrimeConst &p)
 {
-    uint64_t t = mont128(__umul64hi(a, b), a * b, p);
+    uint64_t t = redc_few(__umul64hi(a, b), a * b, p);
     return shoup(t, p.r_mod, p.r_mod_sh, p.q);
 }
 
