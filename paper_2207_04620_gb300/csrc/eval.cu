@@ -86,22 +86,32 @@ Cts Eval::add_const(const Cts &a, double value)
     return o;
 }
 
-Cts Eval::tensor(const Cts &a, const Cts &b)
+Cts Eval::tensor(const Cts &a, const Cts &b, bool mont)
 {
     HX_CHECK(a.B == b.B && a.limbs == b.limbs && a.comps == 2 && b.comps == 2, HX_ESCALE, "tensor operands differ");
     Cts o = alloc(a.B, 3, a.limbs);
     o.scale = a.scale * b.scale;
-    launch_tensor(lc(), o.view(ctx.N), a.view(ctx.N), b.view(ctx.N), a.B, a.limbs, false);
+    launch_tensor(lc(), o.view(ctx.N), a.view(ctx.N), b.view(ctx.N), a.B, a.limbs, false, mont);
     ctx.counters[C_MULCT] += a.B;
     return o;
 }
 
-void Eval::tensor_acc(Cts &acc, const Cts &a, const Cts &b)
+void Eval::from_mont(Cts &a)
+{
+    Scalars sc;
+    for (int l = 0; l < a.limbs; l++) {
+        sc.v[l] = ctx.h_primes[l].r_mod;  // 2^64 mod q_l
+        sc.sh[l] = ctx.h_primes[l].r_mod_sh;
+    }
+    launch_mul_scalar(lc(), a.view(ctx.N), a.view(ctx.N), sc, a.B, a.comps, a.limbs);
+}
+
+void Eval::tensor_acc(Cts &acc, const Cts &a, const Cts &b, bool mont)
 {
     HX_CHECK(a.B == b.B && a.limbs == b.limbs && acc.limbs == a.limbs && acc.comps == 3, HX_ESCALE,
              "tensor operands differ");
     HX_CHECK(std::fabs(acc.scale / (a.scale * b.scale) - 1.0) <= std::ldexp(1.0, -20), HX_ESCALE, "scale mismatch");
-    launch_tensor(lc(), acc.view(ctx.N), a.view(ctx.N), b.view(ctx.N), a.B, a.limbs, true);
+    launch_tensor(lc(), acc.view(ctx.N), a.view(ctx.N), b.view(ctx.N), a.B, a.limbs, true, mont);
     ctx.counters[C_MULCT] += a.B;
     ctx.counters[C_ADD] += a.B;
 }

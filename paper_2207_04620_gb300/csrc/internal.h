@@ -175,7 +175,9 @@ void launch_aggregate(const LaunchCtx &c, View out, const AggSrc *src_dev, int n
 void launch_mul_plain(const LaunchCtx &c, View out, View a, const uint64_t *pt_mont, int B, int limbs);
 void launch_mul_scalar(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int comps, int limbs);
 void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &sc, int B, int limbs);
-void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate);
+// mont: the products left times 2^-64 (Montgomery reductions), to be scaled back once after summing
+void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate,
+                   bool mont = false);
 void launch_automorphism(const LaunchCtx &c, View out, View in, uint64_t g, int B, int comps, int limbs,
                          bool accumulate = false);
 // alg_bytes: one read of every source row and one write of every destination row (profiling)

@@ -182,20 +182,26 @@ __global__ void k_add_scalar_c0(View out, View a, const __grid_constant__ Scalar
     }
 }
 
-// (a0,a1) x (b0,b1) -> (a0b0, a0b1+a1b0, a1b1), optionally added to out
+// (a0,a1) x (b0,b1) -> (a0b0, a0b1+a1b0, a1b1), optionally added to out; mont: each product
+// left as its Montgomery reduction (times 2^-64), for sums that are brought back once at the end
 // two adjacent coefficients per thread, 16-byte loads and stores
 __device__ __forceinline__ void tensor_one(uint64_t a0, uint64_t a1, uint64_t b0, uint64_t b1, const PrimeConst &P,
-                                           uint64_t &r0, uint64_t &r1, uint64_t &r2)
+                                           bool mont, uint64_t &r0, uint64_t &r1, uint64_t &r2)
 {
     Acc128 d1;
     d1.mac(a0, b1);
     d1.mac(a1, b0);
-    r0 = shoup(redc_few(__umul64hi(a0, b0), a0 * b0, P), P.r_mod, P.r_mod_sh, P.q);
-    r1 = shoup(redc_few(d1.hi, d1.lo, P), P.r_mod, P.r_mod_sh, P.q);
-    r2 = shoup(redc_few(__umul64hi(a1, b1), a1 * b1, P), P.r_mod, P.r_mod_sh, P.q);
+    r0 = redc_few(__umul64hi(a0, b0), a0 * b0, P);
+    r1 = redc_few(d1.hi, d1.lo, P);
+    r2 = redc_few(__umul64hi(a1, b1), a1 * b1, P);
+    if (!mont) {
+        r0 = shoup(r0, P.r_mod, P.r_mod_sh, P.q);
+        r1 = shoup(r1, P.r_mod, P.r_mod_sh, P.q);
+        r2 = shoup(r2, P.r_mod, P.r_mod_sh, P.q);
+    }
 }
 
-__global__ void k_tensor(View out, View a, View b, const PrimeConst *__restrict__ primes, int n, bool acc)
+__global__ void k_tensor(View out, View a, View b, const PrimeConst *__restrict__ primes, int n, bool acc, bool mont)
 {
     const int l = blockIdx.y, bi = blockIdx.z;
     const PrimeConst P = primes[l];
@@ -207,8 +213,8 @@ __global__ void k_tensor(View out, View a, View b, const PrimeConst *__restrict_
         const ulonglong2 b0 = *reinterpret_cast<const ulonglong2 *>(b.p + lb + j);
         const ulonglong2 b1 = *reinterpret_cast<const ulonglong2 *>(b.p + lb + b.cstride + j);
         uint64_t x0, x1, x2, y0, y1, y2;
-        tensor_one(a0.x, a1.x, b0.x, b1.x, P, x0, x1, x2);
-        tensor_one(a0.y, a1.y, b0.y, b1.y, P, y0, y1, y2);
+        tensor_one(a0.x, a1.x, b0.x, b1.x, P, mont, x0, x1, x2);
+        tensor_one(a0.y, a1.y, b0.y, b1.y, P, mont, y0, y1, y2);
         ulonglong2 r0 = make_ulonglong2(x0, y0), r1 = make_ulonglong2(x1, y1), r2 = make_ulonglong2(x2, y2);
         ulonglong2 *o0 = reinterpret_cast<ulonglong2 *>(out.p + lo + j);
         ulonglong2 *o1 = reinterpret_cast<ulonglong2 *>(out.p + lo + out.cstride + j);
@@ -856,11 +862,11 @@ void launch_add_scalar_c0(const LaunchCtx &c, View out, View a, const Scalars &s
     post(c);
 }
 
-void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate)
+void launch_tensor(const LaunchCtx &c, View out3, View a, View b, int B, int limbs, bool accumulate, bool mont)
 {
     Timed tm_(c, K_TENSOR, 8.0 * B * limbs * c.N * (accumulate ? 10 : 7));
     dim3 grid(ew_blocks(c.N, 2), limbs, B);
-    k_tensor<<<grid, 256, 0, c.stream>>>(out3, a, b, c.t->primes, c.N, accumulate);
+    k_tensor<<<grid, 256, 0, c.stream>>>(out3, a, b, c.t->primes, c.N, accumulate, mont);
     post(c);
 }
 

@@ -177,8 +177,10 @@ struct Eval {
     Cts mul_plain(const Cts &a, const uint64_t *pt_mont, double pt_scale);
     Cts mul_int(const Cts &a, int64_t c, double new_scale = 0);
     Cts add_const(const Cts &a, double value);
-    Cts tensor(const Cts &a, const Cts &b);
-    void tensor_acc(Cts &acc, const Cts &a, const Cts &b);
+    // mont: the products times 2^-64 (Montgomery form), for a sum scaled back once by from_mont
+    Cts tensor(const Cts &a, const Cts &b, bool mont = false);
+    void tensor_acc(Cts &acc, const Cts &a, const Cts &b, bool mont = false);
+    void from_mont(Cts &a);  // a *= 2^64, in place
     Cts relinearize(const Cts &d, const SwitchKey &rk);
     Cts rescale(const Cts &a, int64_t c = 1);  // rescale(c * a), c an integer scalar
     Cts relin_rescale(const Cts &d, const SwitchKey &rk);  // rescale(relinearize(d)) as one division

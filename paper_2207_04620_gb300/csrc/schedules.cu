@@ -467,7 +467,8 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
     HX_CUDA(cudaEventRecord(e[2], ev.s));
     HX_CUDA(cudaStreamWaitEvent(ss.s2, e[2], 0));
     HX_CUDA(cudaStreamWaitEvent(ev.s, e[1], 0));
-    Cts acc = ev.tensor(ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt), B0);
+    // Step 3's products are summed in Montgomery form (each times 2^-64) and scaled back once
+    Cts acc = ev.tensor(ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt), B0, true);
     acc_odd.scale = acc.scale;
     HX_CUDA(cudaEventRecord(e[5], ev.s));
     HX_CUDA(cudaStreamWaitEvent(ss.s, e[5], 0));  // B0's read by the main stream comes before its release
@@ -486,7 +487,7 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
         const uint64_t *pm = (p.bound_uid && p.bound_uid == ks.uid) ? p.premasked[k]->p : nullptr;
         Cts Ak = ec.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, qt, ks, pm);
         HX_CUDA(cudaStreamWaitEvent(ec.s, e[3 + par], 0));
-        ec.tensor_acc(par ? acc_odd : acc, Ak, held[par]);
+        ec.tensor_acc(par ? acc_odd : acc, Ak, held[par], true);
         HX_CUDA(cudaEventRecord(e[5 + par], ec.s));
     }
     for (int par = 0; par < 2; par++)
@@ -501,6 +502,7 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
     HX_CUDA(cudaEventRecord(e[7], ss.s2));
     HX_CUDA(cudaStreamWaitEvent(ev.s, e[7], 0));
     ev.add_inplace(acc, acc_odd);
+    ev.from_mont(acc);
     // Step 3: one relinearisation, then the two rescales
     return ev.rescale(ev.rescale(ev.relinearize(acc, ks.relin)));
 }
@@ -526,13 +528,14 @@ Cts matmul_depth2(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const 
     for (int k = 1; k < t; k++) ast.push_back((int64_t)beta * k);
     for (int k = 1; k < t; k++) ast.push_back((int64_t)beta * (k - h));
     std::vector<Cts> RA = ev.rotate_hoisted(A0, ast, ks);
-    Cts acc = ev.tensor(A0, B0);
+    Cts acc = ev.tensor(A0, B0, true);  // summed in Montgomery form, scaled back once
     for (int k = 1; k < t; k++) {
         Cts X = ev.rescale(prefix[h - k]);
         Cts Y = ev.rescale(ev.add(Bfull, prefix[h - k], true));
-        ev.tensor_acc(acc, RA[k - 1], ev.rotate(X, (int64_t)beta * h * k, ks));
-        ev.tensor_acc(acc, RA[t - 1 + k - 1], ev.rotate(Y, (int64_t)beta * h * k, ks));
+        ev.tensor_acc(acc, RA[k - 1], ev.rotate(X, (int64_t)beta * h * k, ks), true);
+        ev.tensor_acc(acc, RA[t - 1 + k - 1], ev.rotate(Y, (int64_t)beta * h * k, ks), true);
     }
+    ev.from_mont(acc);
     return ev.rescale(ev.relinearize(acc, ks.relin));
 }
 
