@@ -98,12 +98,14 @@ template <int NB>
 __global__ void __launch_bounds__(128) k_lintrans_mac(const __grid_constant__ MacArgs A,
                                                       const PrimeConst *__restrict__ primes, int B, int limbs, int n)
 {
-    const int l = blockIdx.y, bi = blockIdx.z;
+    // batch entries vary fastest over the grid: the blocks reading one mask tile run together and
+    // share it through L2 (a plan's masks are larger than L2)
+    const int bi = blockIdx.x, l = blockIdx.z;
     const PrimeConst P = primes[l];
     const size_t ob0 = bi * A.baby_bstride + (size_t)l * n, ob1 = ob0 + A.baby_cstride;
     const size_t gstride = (size_t)B * 2 * limbs * n;
     const size_t oo0 = (size_t)bi * 2 * limbs * n + (size_t)l * n, oo1 = oo0 + (size_t)limbs * n;
-    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+    for (int j = (blockIdx.y * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.y * blockDim.x * 2) {
         ulonglong2 v0[NB], v1[NB];
 #pragma unroll
         for (int m = 0; m < NB; m++) {
@@ -245,7 +247,6 @@ __global__ void k_automorphism(View out, View in, uint64_t g, int comps, int log
         out.p[oo + j] = accumulate ? addmod(out.p[oo + j], v, q) : v;
     }
 }
-
 // Fast basis conversion; grid: x over coefficients, z = b * groups + grp
 template <int MK>  // at most MK sources (register arrays sized to it; four blocks per SM up to 4)
 __global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2)
@@ -909,7 +910,8 @@ void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64
 void launch_lintrans_mac(const LaunchCtx &c, const MacArgs &a, int B, int limbs, int n_terms)
 {
     Timed tm_(c, K_MULPT, 8.0 * limbs * c.N * ((double)B * 2 * (a.n_baby + a.n_group) + n_terms));
-    dim3 grid((c.N / 2 + 127) / 128, limbs, B);
+    HX_CHECK(B >= 1 && limbs < 65536, HX_EINVAL, "bad BSGS batch");
+    dim3 grid(B, (c.N / 2 + 127) / 128, limbs);
     if (a.n_baby <= 4) k_lintrans_mac<4><<<grid, 128, 0, c.stream>>>(a, c.t->primes, B, limbs, c.N);
     else if (a.n_baby <= 8) k_lintrans_mac<8><<<grid, 128, 0, c.stream>>>(a, c.t->primes, B, limbs, c.N);
     else k_lintrans_mac<16><<<grid, 128, 0, c.stream>>>(a, c.t->primes, B, limbs, c.N);
