@@ -213,8 +213,15 @@ def matmul_rotation_steps(h: int, beta: int, limbs: int, t: int | None = None) -
     return sorted({k % n_slots for k in s} - {0})
 
 
+def mask_scale(ctx: C.Context) -> int:
+    """Reading R7: every plan mask is encoded at one fixed integer scale, the power of two
+    nearest the context's scale, at every level (so a mask's coefficients do not depend on the
+    level); Mul_pt then RS by q_{l-1} leaves scale * 2^e / q_{l-1}, tracked exactly."""
+    return 1 << round(math.log2(ctx.scale))
+
+
 class MaskProvider:
-    """Encodes plan masks with the oracle encoder (scale q_{l-1} at l limbs);
+    """Encodes plan masks with the oracle encoder (at mask_scale(ctx), every level);
     `coeffs` exposes the signed integer coefficients so a test can hand the
     very same plaintexts to another implementation."""
 
@@ -228,7 +235,7 @@ class MaskProvider:
     def coeffs(self, i: int) -> np.ndarray:
         if i not in self._coeffs:
             kind, k, vec, lm = self.entries[i]
-            self._coeffs[i] = C.encode_real(self.ctx.N, expand(vec, self.beta), float(self.ctx.q[lm - 1]))
+            self._coeffs[i] = C.encode_real(self.ctx.N, expand(vec, self.beta), float(mask_scale(self.ctx)))
         return self._coeffs[i]
 
     def plaintext(self, kind: str, k: int, extended: bool = False):
@@ -237,7 +244,7 @@ class MaskProvider:
         lm = self.entries[i][3]
         prim = self.ctx.q[:lm] + (self.ctx.p if extended else [])
         pt = self.ctx.ntt(self.ctx.signed_to_rows(self.coeffs(i), prim), prim)
-        return pt, float(self.ctx.q[lm - 1])
+        return pt, float(mask_scale(self.ctx))
 
 
 # ----------------------------------------------------------------------------
@@ -307,9 +314,9 @@ def _matmul_alg3(ev, A, B, h, masks, t=None):
     # Step 2 (App. B multiplexer, applied after hoisting): A^(k) = v_k . R(A0, k)
     # + (1 - v_k) . R(A0, k-h); every rotation of A0 shares one ModUp and the
     # selection happens in the extended basis before a single ModDown per k.
-    # A^(k) stays at scale Delta*q_t (no rescale per k); B^(k) = R(B0, h*k)
-    # stays at the same level; A^(0) = q_t * A0.
-    qt = ev.ctx.q[A0.limbs - 1]
+    # A^(k) stays at scale Delta*c (c = the masks' scale as an integer; no rescale
+    # per k); B^(k) = R(B0, h*k) stays at the same level; A^(0) = c * A0.
+    qt = mask_scale(ev.ctx)
     DA = ev.hoist(A0)
     Bk = [B0] + ev.rotate_hoisted(B0, [beta * h * k for k in range(1, t)])
     # Step 3: sum_k A^(k) (x) B^(k), one relinearisation, then the two rescales
@@ -420,7 +427,7 @@ def transpose_rotation_steps(h: int, beta: int) -> list:
 
 
 class TransposeMasks(MaskProvider):
-    """Mask plaintexts of App. C's transpose (diagonals (h-1)s), encoded at scale q_{l-1}."""
+    """Mask plaintexts of App. C's transpose (diagonals (h-1)s), encoded at mask_scale(ctx)."""
 
     def __init__(self, ctx: C.Context, h: int, limbs: int):
         self.ctx, self.h, self.limbs = ctx, h, limbs

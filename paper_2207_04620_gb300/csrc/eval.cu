@@ -374,7 +374,7 @@ Cts Eval::hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, con
     ntt_inplace(conv.p, (size_t)limbs * N, 2 * B, iota_vec(0, limbs), iota_vec(0, limbs), false);
     Cts o = alloc(B, 2, limbs);
     launch_moddown_final_mux(lc(), o.view(N), zv, View{conv.p, (size_t)2 * limbs * N, (size_t)limbs * N},
-                             ctx.t.moddown + limbs, B, limbs, a.view(N), v_ext, cs, g1, g2);
+                             ctx.t.moddown + limbs, B, limbs, a.view(N), v_ext + (size_t)K * N, cs, g1, g2);
     o.scale = a.scale * v_scale;
     ctx.counters[C_ROT] += 2 * B;
     ctx.counters[C_ROT_HOIST] += 2 * B;
@@ -454,8 +454,8 @@ void upload_plaintext_ext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs
 {
     Eval ev(ctx, s);
     const int ext = limbs + ctx.K;
-    std::vector<int> pr(ext);
-    for (int t = 0; t < ext; t++) pr[t] = t < limbs ? t : ctx.n_q + (t - limbs);
+    std::vector<int> pr(ext);  // the special primes' rows first, then q_0 .. q_{limbs-1}
+    for (int t = 0; t < ext; t++) pr[t] = t < ctx.K ? ctx.n_q + t : t - ctx.K;
     DevBuf tmp((size_t)ctx.N, s);
     DevBuf ids((ext + 1) / 2, s);
     HX_CUDA(cudaMemcpyAsync(tmp.p, coeffs, sizeof(int64_t) * ctx.N, cudaMemcpyHostToDevice, s));

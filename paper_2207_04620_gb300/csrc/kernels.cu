@@ -422,7 +422,8 @@ __global__ void k_key_ip_mux(View out, const uint64_t *__restrict__ D, const uin
             y0.mac(b, key2[ko]);
             y1.mac(b, key2[ko + (size_t)n_all * n]);
         }
-        const uint64_t vv = v[(size_t)t * n + j];
+        // v holds the special primes' rows first, then the chain's (a mask of any level is a prefix)
+        const uint64_t vv = v[(size_t)(t < limbs ? K + t : t - limbs) * n + j];
         const uint64_t xr0 = few ? redc_few(x0.hi, x0.lo, P) : mont128(x0.hi, x0.lo, P);
         const uint64_t yr0 = few ? redc_few(y0.hi, y0.lo, P) : mont128(y0.hi, y0.lo, P);
         const uint64_t xr1 = few ? redc_few(x1.hi, x1.lo, P) : mont128(x1.hi, x1.lo, P);
@@ -450,7 +451,8 @@ __global__ void k_premask_keys(uint64_t *out, const uint64_t *__restrict__ key1,
     uint64_t *o2 = o1 + (size_t)ndig * 2 * ext * n;
     const uint64_t cr = cR.v[t];
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
-        const uint64_t vv = v[(size_t)t * n + j], k1 = key1[ko + j], k2 = key2[ko + j];
+        // v: the special primes' rows first, then the chain's
+        const uint64_t vv = v[(size_t)(t < limbs ? K + t : t - limbs) * n + j], k1 = key1[ko + j], k2 = key2[ko + j];
         const uint64_t w = submod(cr, vv, P.q);  // (c - v) in Montgomery form
         o1[j] = redc_few(__umul64hi(vv, k1), vv * k1, P);
         o2[j] = redc_few(__umul64hi(w, k2), w * k2, P);

@@ -145,7 +145,7 @@ struct hx_matmul_plan {
         int kind;  // 0 mu, 1 zeta, 2 v, 3 transpose diagonal
         int index;
         int limbs;
-        bool extended;  // stored over q_0..q_{limbs-1} and the special primes
+        bool extended;  // stored over the special primes, then q_0..q_{limbs-1}
         double scale;
         std::vector<int32_t> vec;  // logical 0/1 vector of length h^2
         hx::BufPtr pt;             // [limbs][N] Montgomery form, NTT
@@ -157,6 +157,9 @@ struct hx_matmul_plan {
     uint64_t bound_uid = 0;
     std::vector<hx::BufPtr> premasked;
     std::vector<hx::BufPtr> storage;  // batched mask buffers the masks' views point into
+    // a plan for a lower level is a view of the top-level plan of its shape: its masks are the
+    // first rows of the base plan's (mask coefficients do not depend on the level)
+    std::shared_ptr<const hx_matmul_plan> base;
 };
 
 namespace hx {
@@ -192,7 +195,7 @@ struct Eval {
     BufPtr hoist(const Cts &a);
     Cts rotate_hoisted_one(const Cts &a, const BufPtr &D, int64_t k, const hx_keyset &keys);
     // v . Rot(a, k1) + (1 - v) . Rot(a, k2) from the ModUp D of a; the selection is applied in
-    // the extended basis before one ModDown; v_ext: mask over Q_l then P (Montgomery), encoded
+    // the extended basis before one ModDown; v_ext: mask over P then Q_l (Montgomery), encoded
     // at scale v_scale whose integer value is c.  premasked (optional): the two rotation keys
     // already multiplied by v and c - v (premask_keys), so the inner product gives the selection
     Cts hoisted_mux(const Cts &a, const BufPtr &D, int64_t k1, int64_t k2, const uint64_t *v_ext, double v_scale,
@@ -217,7 +220,7 @@ struct Eval {
 
 Scalars scalars_for(const hx_context &ctx, int limbs, int64_t c);
 void upload_plaintext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst_mont);
-// the same over q_0..q_{limbs-1}, p_0..p_{K-1}
+// the same over p_0..p_{K-1} then q_0..q_{limbs-1} (an extended mask's row order)
 void upload_plaintext_ext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst_mont);
 // the same from N signed coefficients already on the device (extended: over the special primes too)
 void plaintext_from_device(hx_context &ctx, cudaStream_t s, const int64_t *dcoeffs, int limbs, bool extended,

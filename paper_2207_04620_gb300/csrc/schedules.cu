@@ -113,6 +113,13 @@ std::vector<int64_t> plan_rotation_steps(int h, int beta, int limbs, int t)
 
 void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s);
 
+// The masks' scale: the power of two nearest the context's scale, the same at every level (an
+// integer, so the multiplexer's constant and the Step-3 multiplier are exact); a product's scale
+// after the mask and the rescale by q_(l-1) is then tracked as scale * 2^e / q_(l-1)
+static int mask_scale_log2(const hx_context &ctx) { return (int)std::lround(std::log2(ctx.scale)); }
+static double mask_scale(const hx_context &ctx) { return std::ldexp(1.0, mask_scale_log2(ctx)); }
+static uint64_t mask_scale_int(const hx_context &ctx) { return (uint64_t)1 << mask_scale_log2(ctx); }
+
 // whether the masks' real coefficients of a plan shape are cached (then the 0/1 vectors are not needed)
 static bool mask_real_cached(hx_context &ctx, int kind, int h, bool alg3)
 {
@@ -139,7 +146,7 @@ hx_matmul_plan *make_plan(hx_context &ctx, int h, int limbs, cudaStream_t s)
         m.index = idx;
         m.limbs = lm;
         m.extended = extended;
-        m.scale = (double)ctx.primes[lm - 1];
+        m.scale = mask_scale(ctx);
         m.vec = std::move(vec);
         p->index[{kind, idx}] = (int)p->masks.size();
         p->masks.push_back(std::move(m));
@@ -209,7 +216,9 @@ void encode_plan_masks(hx_context &ctx, hx_matmul_plan &pl, cudaStream_t s)
         const bool ext = std::get<2>(grp.first);
         const int rows = ext ? limbs + ctx.K : limbs;
         std::vector<int> pr(rows), idx(ids.begin(), ids.end()), prM((size_t)M * rows);
-        for (int t = 0; t < rows; t++) pr[t] = t < limbs ? t : ctx.n_q + (t - limbs);
+        // an extended mask's rows: the special primes first, then q_0 .. q_(limbs-1), so the mask of a
+        // lower level is a prefix of the top level's
+        for (int t = 0; t < rows; t++) pr[t] = !ext ? t : t < ctx.K ? ctx.n_q + t : t - ctx.K;
         for (int r = 0; r < M; r++) std::copy(pr.begin(), pr.end(), prM.begin() + (size_t)r * rows);
         DevBuf dpr((prM.size() + 1) / 2, s), didx((idx.size() + 1) / 2, s);
         HX_CUDA(cudaMemcpyAsync(dpr.p, prM.data(), sizeof(int) * prM.size(), cudaMemcpyHostToDevice, s));
@@ -249,7 +258,7 @@ hx_matmul_plan *make_transpose_plan(hx_context &ctx, int h, int limbs, cudaStrea
         m.index = sh;
         m.limbs = limbs;
         m.extended = false;
-        m.scale = (double)ctx.primes[limbs - 1];
+        m.scale = mask_scale(ctx);
         if (vecs) m.vec = rot(diag_transpose(h, sh), -(h - 1) * p->b * floordiv(sh, p->b));
         p->index[{3, sh}] = (int)p->masks.size();
         p->masks.push_back(std::move(m));
@@ -269,9 +278,53 @@ size_t plan_device_bytes(const hx_matmul_plan &p)
     return b;
 }
 
-// the cached plan of (kind, h, limbs), built on first use (outside the lock, on the
-// context's plan stream); the cache may then drop least recently used plans no call holds
+std::shared_ptr<const hx_matmul_plan> cached_base(hx_context &ctx, int kind, int h, int limbs);
+
+// A plan for `limbs` limbs as a view of `base` (same kind, h and variant, base->limbs >= limbs).
+// The masks' coefficients do not depend on the level (one fixed scale), and a mask's NTT rows for
+// q_0 .. q_(l-1) are the first rows of the top level's (an extended mask keeps the special primes'
+// rows first), so the view's masks point into the base's buffers and the view keeps it alive.
+std::shared_ptr<const hx_matmul_plan> level_view(const std::shared_ptr<const hx_matmul_plan> &base, int limbs)
+{
+    if (base->limbs == limbs) return base;
+    const hx_context &ctx = *base->ctx;
+    std::shared_ptr<hx_matmul_plan> v(new hx_matmul_plan);
+    v->ctx = base->ctx;
+    v->kind = base->kind;
+    v->h = base->h;
+    v->limbs = limbs;
+    v->beta = base->beta;
+    v->b = base->b;
+    v->alg3 = base->alg3;
+    v->index = base->index;
+    for (const auto &bm : base->masks) {
+        hx_matmul_plan::Mask m;
+        m.kind = bm.kind;
+        m.index = bm.index;
+        m.extended = bm.extended;
+        m.scale = bm.scale;
+        m.limbs = bm.limbs - (base->limbs - limbs);  // limbs, or limbs - 1 for the Step-2 selections
+        const size_t rows = (size_t)(m.extended ? m.limbs + ctx.K : m.limbs);
+        m.pt = std::make_shared<DevBuf>(bm.pt->p, rows * ctx.N);
+        v->masks.push_back(std::move(m));
+    }
+    v->base = base;
+    return v;
+}
+
+// The plan of (kind, h, limbs): a view of the context's cached plan of its shape at the top of the
+// chain (the depth-2 product, which only runs at 3 limbs, has its own), built on first use
+// (outside the lock, on the context's plan stream); the cache may then drop least recently used
+// plans no call holds
 std::shared_ptr<const hx_matmul_plan> cached(hx_context &ctx, int kind, int h, int limbs)
+{
+    HX_CHECK(limbs >= 1 && limbs <= ctx.n_q, HX_EINVAL, "level above the chain");
+    HX_CHECK(kind == 0 || limbs >= 2, HX_ELEVEL, "the transpose needs a level to rescale");
+    const int base_limbs = (kind == 0 && limbs < 4) ? limbs : ctx.n_q;
+    return level_view(cached_base(ctx, kind, h, base_limbs), limbs);
+}
+
+std::shared_ptr<const hx_matmul_plan> cached_base(hx_context &ctx, int kind, int h, int limbs)
 {
     const auto key = std::make_tuple(kind, h, limbs);
     cudaStream_t ps;
@@ -461,14 +514,14 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
     // Step 2 (App. B multiplexer after hoisting): A^(k) = v_k . Rot(A0, k) + (1 - v_k) . Rot(A0, k-h),
     // all rotations of A0 from one ModUp, the selection before a single ModDown per k.  A^(k)
     // keeps the mask scale (no rescale per k); B^(k) = Rot(B0, h*k) stays at the same level.
-    const uint64_t qt = ctx.primes[A0.limbs - 1];
+    const uint64_t cm = mask_scale_int(ctx);  // the masks' scale as an integer: c of the multiplexer
     Cts acc_odd = ev.alloc(A0.B, 3, A0.limbs);  // the odd-k accumulator, zero, owned by the main stream
     HX_CUDA(cudaMemsetAsync(acc_odd.d, 0, sizeof(uint64_t) * acc_odd.bstride(ctx.N) * acc_odd.B, ev.s));
     HX_CUDA(cudaEventRecord(e[2], ev.s));
     HX_CUDA(cudaStreamWaitEvent(ss.s2, e[2], 0));
     HX_CUDA(cudaStreamWaitEvent(ev.s, e[1], 0));
     // Step 3's products are summed in Montgomery form (each times 2^-64) and scaled back once
-    Cts acc = ev.tensor(ev.mul_int(A0, (int64_t)qt, A0.scale * (double)qt), B0, true);
+    Cts acc = ev.tensor(ev.mul_int(A0, (int64_t)cm, A0.scale * (double)cm), B0, true);
     acc_odd.scale = acc.scale;
     HX_CUDA(cudaEventRecord(e[5], ev.s));
     HX_CUDA(cudaStreamWaitEvent(ss.s, e[5], 0));  // B0's read by the main stream comes before its release
@@ -485,7 +538,7 @@ Cts matmul_alg3(Eval &ev, const hx_keyset &ks, const hx_matmul_plan &p, const Ct
         double sc;
         const uint64_t *v = mask_pt(p, 2, k, &sc);
         const uint64_t *pm = (p.bound_uid && p.bound_uid == ks.uid) ? p.premasked[k]->p : nullptr;
-        Cts Ak = ec.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, qt, ks, pm);
+        Cts Ak = ec.hoisted_mux(A0, DA, (int64_t)beta * k, (int64_t)beta * (k - h), v, sc, cm, ks, pm);
         HX_CUDA(cudaStreamWaitEvent(ec.s, e[3 + par], 0));
         ec.tensor_acc(par ? acc_odd : acc, Ak, held[par], true);
         HX_CUDA(cudaEventRecord(e[5 + par], ec.s));
@@ -578,7 +631,7 @@ void bind_plan_keys(hx_context &ctx, hx_matmul_plan &plan, const hx_keyset &ks, 
         HX_CHECK(it1 != ks.rot.end() && it2 != ks.rot.end(), HX_EKEY, "missing Galois key for Step 2");
         double sc;
         const uint64_t *v = mask_pt(plan, 2, k, &sc);
-        const uint64_t c = ctx.primes[limbs - 1];
+        const uint64_t c = mask_scale_int(ctx);  // the integer value of the masks' scale
         Scalars cR;
         for (int t = 0; t < ext; t++) {
             const uint64_t q = ctx.primes[t < limbs ? t : ctx.n_q + (t - limbs)];
