@@ -261,10 +261,13 @@ int hx_context_plan_cache_info(hx_context *ctx, uint64_t *out, int cap);
 /* A plan fixes h (a power of two, h*h <= N/2, beta = (N/2)/h^2 products per
  * ciphertext pair) and the input level.  limbs >= 4 runs Alg. 3; limbs == 3
  * runs the depth-2 rearrangement; fewer returns HX_ELEVEL.  Its diagonal
- * masks are encoded by the library; hx_matmul_plan_set_mask replaces mask i
- * (in the plan's documented order: mu diagonals l = -h+1..h-1, zeta diagonals
- * l = 0..h-1, then for Alg. 3 the v_k masks k = 1..h-1) by N signed integer
- * coefficients. */
+ * masks are encoded by the library at one fixed scale, 2^round(log2 scale) of
+ * the context, at every level (a product's scale after a mask and a rescale by
+ * q_(l-1) is scale * 2^e / q_(l-1), carried in the ciphertext);
+ * hx_matmul_plan_set_mask replaces mask i (in the plan's documented order: mu
+ * diagonals l = -h+1..h-1, zeta diagonals l = 0..h-1, then for Alg. 3 the v_k
+ * masks k = 1..h-1) by N signed integer coefficients, to be encoded at that
+ * scale. */
 hx_status hx_matmul_plan_create(hx_context *ctx, int h, int limbs, hx_matmul_plan **out);
 int hx_matmul_plan_num_masks(const hx_matmul_plan *plan);
 hx_status hx_matmul_plan_set_mask(hx_context *ctx, hx_matmul_plan *plan, int i, const int64_t *coeffs);

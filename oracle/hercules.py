@@ -166,7 +166,7 @@ def plan_masks(h: int, limbs: int):
              u^zeta_{hl} unrotated for the depth-2 variant              at `limbs`
       v    : k = 1..h-1, v_k (Step 2 selects after rotating)              at `limbs`-1 (Alg. 3 only),
              used in the extended basis q_0..q_{l-1}, p_0..p_{K-1}
-    A mask multiplying a ciphertext of l limbs is encoded at scale q_{l-1}."""
+    Every mask is encoded at mask_scale(ctx), whatever the level (reading R7)."""
     variant = matmul_variant(limbs)
     b = baby_steps(h)
     out = []
