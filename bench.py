@@ -233,7 +233,10 @@ def run_hx(args, world, rank, local):
     barrier(world)
     stream = torch.cuda.current_stream()
     ctx = hx.hx_context_create(LOG_N, Q_BITS, P_BITS, LOG2_SCALE)
-    tiles = hx.hx_autotune(ctx, stream=torch.cuda.current_stream())
+    if args.tiles is None:
+        tiles = hx.hx_autotune(ctx, stream=torch.cuda.current_stream())
+    else:  # fixed NTT variants for every batch size (signed widths per phase)
+        tiles = hx.hx_ntt_tiles(ctx, [int(t) for t in args.tiles.split(",")])
     ntt_tuning = hx.hx_ntt_tuning(ctx)  # variants per batch-size bucket and phase
     limbs = len(Q_BITS)
     steps = hx.hx_matmul_rotation_steps(ctx, H, limbs)
