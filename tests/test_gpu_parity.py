@@ -836,6 +836,43 @@ def test_sign_config2_full_batch_sampled_bit_exact():
 
 
 @pytest.mark.slow
+def test_dense_config3_forward_products_full_size_sampled_bit_exact():
+    """The forward block products of config 3's dense layer at full size: N=2^15,
+    16 limbs (60 + 15 x 40 bit), three 60-bit special primes, h = 64 packed beta = 4
+    per ciphertext.  The four products W_{0,g} X_g of the layer's first output block
+    (784 inputs = 13 blocks in four groups, the last one ragged) run as one batch
+    through the library's own plan at the top level, as the layer's feedforward
+    runs them; group 0 equals the oracle's HE-MatMult bit for bit and every product
+    decrypts to its block products within 2^-16 (scale 2^40; the oracle's own
+    product is about 2^-18.7 off)."""
+    cfg = workloads.CONFIGS["cfg3_dense784x128_n15"]
+    pr, beta, limbs = _matmul_case("cfg2", cfg["h"], 0, 1)  # the same ring and prime chain
+    try:
+        h = cfg["h"]
+        assert (pr.N, limbs, beta) == (1 << cfg["log_n"], len(cfg["q_bits"]), 4)
+        W, X, G = workloads.dense_inputs(3, cfg["rows"], cfg["n_in"], cfg["batch"])
+        Wp, Xp, _ = workloads.dense_pack(W, X, G, h, beta)
+        groups = len(Xp)
+        Wc = [pr.encrypt(Wp[0][g], 1000 + g) for g in range(groups)]
+        Xc = [pr.encrypt(Xp[g], 2000 + g) for g in range(groups)]
+        plan = hx.hx_matmul_plan_create(pr.ctx, h, limbs)
+        outs = hx.hx_matmul_batch(pr.ctx, pr.ks, plan, [pr.to_lib(c) for c in Wc], [pr.to_lib(c) for c in Xc], h)
+        want = Hc.matmul(C.Evaluator(pr.octx, pr.oks), Wc[0], Xc[0], h, Hc.MaskProvider(pr.octx, h, limbs))
+        assert pr.same(outs[0], want)
+        Wb, Xb = workloads.blocks(W, h), [r[0] for r in workloads.blocks(X, h)]
+        for g in range(groups):
+            got = workloads.unpack(hx.hx_decrypt(pr.ctx, pr.ks, outs[g]), h, beta)
+            for p in range(beta):
+                j = beta * g + p
+                ref = Wb[0][j] @ Xb[j] if j < len(Xb) else np.zeros((h, h))
+                assert np.abs(got[p] - ref).max() <= 2 ** -16
+            hx.hx_ct_destroy(outs[g])
+        hx.hx_matmul_plan_destroy(plan)
+    finally:
+        pr.close()
+
+
+@pytest.mark.slow
 def test_dense_config3_full_size_against_fp64():
     """Config 3 at full size (784 -> 128, batch 64, h = 64, N = 2^15, 16 limbs) through
     hx_dense_layer with the library's plans: E, ReLU(E) and dW decrypt to the FP64
