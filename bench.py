@@ -34,6 +34,14 @@ N_SLOTS = (1 << LOG_N) // 2
 BETA = N_SLOTS // (H * H)
 PRODUCTS = PAIRS * BETA
 METRIC = "encrypted 64x64 matmuls/s (batched HE-MatMult, CKKS N=2^14)"
+# The 64-bit modular-multiply ceiling of the GB300 (the ALU roofline of the NTT): 152 SMs x 4
+# sub-partitions at the 2070 MHz maximum SM clock, each sub-partition's FMA-heavy pipe finishing
+# one lane's 64-bit Shoup product y*w - floor(y*w'/2^64)*q per cycle (a warp-wide product issues
+# 10 instructions on that pipe and holds it 32 cycles: ncu pipe counters on the calibration kernel)
+GPU_SMS, GPU_SUBPARTITIONS, GPU_MAX_SM_MHZ, SHOUP_PIPE_CYCLES_PER_WARP = 152, 4, 2070, 32
+ALU_PEAK_SHOUP = GPU_SMS * GPU_SUBPARTITIONS * GPU_MAX_SM_MHZ * 1e6 * 32 / SHOUP_PIPE_CYCLES_PER_WARP
+ALU_PEAK_KIND = ("derived: 152 SMs x 4 sub-partitions x 2070 MHz x 32 lanes / 32 FMA-heavy pipe cycles per "
+                 "warp-wide 64-bit Shoup product")
 WORKLOAD = ("cfg1: %d independent 64x64 products per step = %d ciphertext pairs x beta=%d packed products; "
             "CKKS N=2^14, Q=1x60+7x45 bit, P=2x60 bit, scale 2^45, entries U[-1,1] seeded" % (PRODUCTS, PAIRS, BETA))
 
@@ -200,7 +208,8 @@ def other_metrics(args):
     m = run_micro(ns)
     out["ntt_micro"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in m.items()
                         if k in ("log_n", "rows", "tiles", "fwd_ms", "inv_ms", "fwd_gbs", "inv_gbs", "fwd_frac",
-                                 "inv_frac", "fwd_alu_frac", "inv_alu_frac", "peak_gbs", "peak_kind", "clocks")}
+                                 "inv_frac", "fwd_alu_frac", "inv_alu_frac", "fwd_calibrated_frac",
+                                 "inv_calibrated_frac", "peak_gbs", "peak_kind", "clocks")}
     out["ntt_micro"]["what"] = "forward / inverse NTT of 1600 limbs of N=2^14 (210 MB, > L2) in place; " \
                                "CUDA events around 200 transforms per direction, median of 5 steps"
     ns = argparse.Namespace(**vars(args))
@@ -334,24 +343,34 @@ def run_hx(args, world, rank, local):
         if ent and ent.get("kernels_sha") == ntt_kernels_sha():
             # captured on a smaller launch of the same kernel; traffic grows with the residues processed
             traffic = round(ent["dram_bytes_per_alg_byte"] * dom_bytes / n_launch)
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
-                "launches": n_launch, "avg_launch_us": round(dom_ms / n_launch * 1e3, 2),
-                "alg_bytes_per_launch": dom_bytes / n_launch,
-                "method": "one profiled step of the same batched schedule with its chains run one after another "
-                          "on the launching stream (CUDA events around every launch of a class); the timed graph "
-                          "overlaps the chains, so these are per-kernel speeds, not shares of the graph's time; "
-                          "traffic: ncu DRAM bytes per algorithmic byte of the NTT phase kernels "
-                          "(profiles/traffic.json) times this launch's algorithmic bytes"}
+    method = ("one profiled step of the same batched schedule with its chains run one after another "
+              "on the launching stream (CUDA events around every launch of a class); the timed graph "
+              "overlaps the chains, so these are per-kernel speeds, not shares of the graph's time; "
+              "traffic: ncu DRAM bytes per algorithmic byte of the NTT phase kernels "
+              "(profiles/traffic.json) times this launch's algorithmic bytes")
+    hbm = {"achieved": round(achieved, 1), "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+           "peak_kind": peak_kind, "alg_bytes_per_launch": dom_bytes / n_launch}
     if dom == "ntt":
-        # the integer-issue ceiling beside it: one Shoup product per butterfly, log2(N)/32
-        # butterflies per algorithmic byte (N/2 log2 N butterflies per 16 N bytes)
+        # bound by its 64-bit integer multiplies, not by HBM: one Shoup product per butterfly,
+        # log2(N)/32 butterflies per algorithmic byte (N/2 log2 N butterflies per 16 N bytes)
         shoup_s, mac_s = hx.hx_alu_calibrate(ctx, stream=stream)
         bfly_s = achieved * 1e9 * LOG_N / 32.0
-        roofline["alu"] = {"butterflies_per_s": round(bfly_s / 1e9, 1), "shoup_products_per_s": round(shoup_s / 1e9, 1),
-                           "unit": "G/s", "frac": round(bfly_s / shoup_s, 4),
-                           "mac128_per_s": round(mac_s / 1e9, 1),
-                           "what": "measured on this GPU by hx_alu_calibrate (8 independent chains per thread)"}
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(bfly_s / 1e9, 1),
+                    "peak": round(ALU_PEAK_SHOUP / 1e9, 1), "unit": "G Shoup products/s (one per butterfly)",
+                    "frac": round(bfly_s / ALU_PEAK_SHOUP, 4), "traffic": traffic, "peak_kind": ALU_PEAK_KIND,
+                    "launches": n_launch, "avg_launch_us": round(dom_ms / n_launch * 1e3, 2),
+                    "alg_butterflies_per_launch": dom_bytes / n_launch * LOG_N / 32.0,
+                    "hbm": hbm,
+                    "calibrated": {"shoup_products_per_s": round(shoup_s / 1e9, 1), "unit": "G/s",
+                                   "frac": round(bfly_s / shoup_s, 4), "mac128_per_s": round(mac_s / 1e9, 1),
+                                   "what": "measured on this GPU by hx_alu_calibrate (8 independent chains "
+                                           "per thread)"},
+                    "method": method}
+    else:
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                    "frac": round(achieved / peak, 4), "traffic": traffic, "peak_kind": peak_kind,
+                    "launches": n_launch, "avg_launch_us": round(dom_ms / n_launch * 1e3, 2),
+                    "alg_bytes_per_launch": dom_bytes / n_launch, "method": method}
     # every kernel class of the step against the same HBM peak (algorithmic bytes of its
     # launches / their event-timed duration), the key-switching classes among them
     class_roofline = {c: {"launches": v[0], "ms": round(v[1], 3), "gbs": round(v[2] / (v[1] / 1e3) / 1e9, 1),
@@ -879,10 +898,14 @@ def run_micro(args):
            "peak_gbs": peak, "peak_kind": kind, "clocks": clocks}
     res["fwd_frac"] = res["fwd_gbs"] / peak
     res["inv_frac"] = res["inv_gbs"] / peak
-    # integer-issue ceiling: butterflies/s against measured Shoup products/s
+    # the ALU roofline: butterflies/s (one Shoup product each) against the derived ceiling, and
+    # against the Shoup products/s the calibration kernel reaches
     res["shoup_products_per_s"] = shoup_s
-    res["fwd_alu_frac"] = res["fwd_gbs"] * 1e9 * log_n / 32.0 / shoup_s
-    res["inv_alu_frac"] = res["inv_gbs"] * 1e9 * log_n / 32.0 / shoup_s
+    res["alu_peak_shoup_per_s"] = ALU_PEAK_SHOUP
+    res["fwd_alu_frac"] = res["fwd_gbs"] * 1e9 * log_n / 32.0 / ALU_PEAK_SHOUP
+    res["inv_alu_frac"] = res["inv_gbs"] * 1e9 * log_n / 32.0 / ALU_PEAK_SHOUP
+    res["fwd_calibrated_frac"] = res["fwd_gbs"] * 1e9 * log_n / 32.0 / shoup_s
+    res["inv_calibrated_frac"] = res["inv_gbs"] * 1e9 * log_n / 32.0 / shoup_s
     hx.hx_context_destroy(ctx)
     return res
 
