@@ -1097,6 +1097,89 @@ def run_micro_ntt_multi(args):
         hx.hx_context_destroy(c)
 
 
+def run_matmul_jobs(args):
+    """Products over several rings, levels and sizes in one hx_matmul_jobs call against the same
+    groups as one call each, one after another on the stream (same cached plans and keys).  Groups:
+    N = 2^12 (Q = 60 + 4x45 bit) h = 16, N = 2^13 (60 + 5x45) h = 32, N = 2^14 (60 + 7x45, config 1's
+    ring) h = 64 and h = 32, N = 2^14 at 6 limbs h = 64; 8 ciphertext pairs each, P = 2x60 bit,
+    scale 2^45, entries U[-1, 1] seeded; CUDA events on the stream, L2 flushed between steps."""
+    import torch
+
+    from paper_2207_04620_gb300 import hx, workloads
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    rings = {12: [60] + [45] * 4, 13: [60] + [45] * 5, 14: [60] + [45] * 7}
+    groups = [(12, 16, 5), (13, 32, 6), (14, 64, 8), (14, 32, 8), (14, 64, 6)]  # (log N, h, limbs)
+    pairs = 8
+    ctxs, kss = {}, {}
+    for ln, qb in rings.items():
+        ctx = hx.hx_context_create(ln, qb, [60, 60], 45)
+        hx.hx_autotune(ctx, stream=stream)
+        steps = sorted({s for g in groups if g[0] == ln for s in hx.hx_matmul_rotation_steps(ctx, g[1], g[2])})
+        ctxs[ln], kss[ln] = ctx, hx.hx_keygen(ctx, 2, 70 + ln, steps)
+    jobs_of, products = [], 0
+    for gi, (ln, h, limbs) in enumerate(groups):
+        beta = (1 << ln) // 2 // (h * h)
+        js = []
+        for i in range(pairs):
+            a = workloads.pack(workloads.matrices(1000 * gi + 2 * i, beta, h), h, beta)
+            b = workloads.pack(workloads.matrices(1000 * gi + 2 * i + 1, beta, h), h, beta)
+            A = hx.hx_encrypt(ctxs[ln], kss[ln], a, limbs, 10 + i)
+            B = hx.hx_encrypt(ctxs[ln], kss[ln], b, limbs, 50 + i)
+            js.append((ctxs[ln], kss[ln], A, B, h))
+        jobs_of.append(js)
+        products += pairs * beta
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_call():
+        return hx.hx_matmul_jobs([j for js in jobs_of for j in js], stream=stream)
+
+    def per_group():
+        return [o for js in jobs_of for o in hx.hx_matmul_jobs(js, stream=stream)]
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 1)):
+            for o in fn():
+                hx.hx_ct_destroy(o)
+        ts = []
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            for o in outs:
+                hx.hx_ct_destroy(o)
+        return statistics.median(ts)
+
+    sampler = ClockSampler()
+    ms_one = timed(one_call)
+    ms_seq = timed(per_group)
+    clocks = sampler.stop()
+    out = {"workload": "matmul_jobs", "unit": "products/s", "products_per_step": products,
+           "groups": [{"log_n": ln, "h": h, "limbs": limbs, "pairs": pairs,
+                       "products": pairs * ((1 << ln) // 2 // (h * h))} for ln, h, limbs in groups],
+           "one_call": {"ms": round(ms_one, 3), "value": round(products / (ms_one / 1e3), 1)},
+           "one_call_per_group": {"ms": round(ms_seq, 3), "value": round(products / (ms_seq / 1e3), 1)},
+           "speedup": round(ms_seq / ms_one, 3), "clocks": clocks,
+           "what": "hx_matmul_jobs over every group (groups side by side on per-context stream pools) "
+                   "against one hx_matmul_jobs call per group, one after another"}
+    print(json.dumps(out), flush=True)
+    for js in jobs_of:
+        for j in js:
+            hx.hx_ct_destroy(j[2])
+            hx.hx_ct_destroy(j[3])
+    for ln in rings:
+        hx.hx_keyset_destroy(kss[ln])
+        hx.hx_context_destroy(ctxs[ln])
+
+
 def run_micro_aggregate(args):
     """Alg. 6 Aggregation alone: the model update w - eta/(B N) * sum_i g_i for the 8
     gradient ciphertexts of one 784->128 layer (h=64, beta=4 packing) from 16 parties,
@@ -1173,7 +1256,7 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--micro", choices=["ntt", "aggregate", "encrypt", "ntt-multi"], default=None)
     ap.add_argument("--parties", type=int, default=16)
-    ap.add_argument("--workload", choices=["matmul", "sign", "dense", "serve", "rmatmul"], default="matmul")
+    ap.add_argument("--workload", choices=["matmul", "sign", "dense", "serve", "rmatmul", "jobs"], default="matmul")
     ap.add_argument("--t", type=int, default=16, help="rows of A in the rectangular product")
     ap.add_argument("--requests", type=int, default=1000)
     ap.add_argument("--load", type=float, default=0.8)
@@ -1212,6 +1295,8 @@ def main():
         return run_dense(args)
     if args.workload == "rmatmul":
         return run_rmatmul(args)
+    if args.workload == "jobs":
+        return run_matmul_jobs(args)
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
