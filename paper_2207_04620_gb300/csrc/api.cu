@@ -124,6 +124,14 @@ void run_matmul_groups(std::vector<MatmulGroup> &groups, cudaStream_t s, hx_ct *
         for (auto &R : run)
             if (R.gs && R.gs != s) HX_CUDA(cudaStreamWaitEvent(R.gs, copied, 0));
     } catch (...) {
+        // the caller's stream still waits for whatever the started groups launched, so inputs it
+        // frees after the error are not read afterwards (best effort: the error is rethrown)
+        cudaEvent_t j = nullptr;
+        if (cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess) {
+            for (auto &R : run)
+                if (R.gs && R.gs != s && cudaEventRecord(j, R.gs) == cudaSuccess) cudaStreamWaitEvent(s, j, 0);
+            cudaEventDestroy(j);
+        }
         for (hx_ct *c : res) delete c;
         release();
         throw;
