@@ -566,6 +566,34 @@ def test_products_over_two_rings_in_one_call_bit_exact():
             pr.close()
 
 
+def test_products_over_two_rings_error_in_one_group_leaves_the_library_usable():
+    """hx_matmul_jobs whose second group (N = 2^13, a key set without rotation keys) fails
+    after the first group (N = 2^12) has launched its schedule: the call returns the error,
+    hands back no outputs, and the first group's products, run again alone, still equal the
+    oracle bit for bit."""
+    h, limbs = 8, 5
+    good = Pair("alg3", rot_steps=Hc.matmul_rotation_steps(h, (1 << PARAMS["alg3"]["log_n"]) // 2 // (h * h), limbs))
+    bad = Pair("alg3_13", rot_steps=[])
+    try:
+        beta = good.octx.S // (h * h)
+        ma, mb = workloads.matrices(70, beta, h), workloads.matrices(71, beta, h)
+        A = good.encrypt(workloads.pack(ma, h, beta), 600, limbs=limbs)
+        B = good.encrypt(workloads.pack(mb, h, beta), 601, limbs=limbs)
+        beta13 = bad.octx.S // (h * h)
+        A13 = bad.encrypt(workloads.pack(workloads.matrices(72, beta13, h), h, beta13), 602)
+        B13 = bad.encrypt(workloads.pack(workloads.matrices(73, beta13, h), h, beta13), 603)
+        ga, gb, ba, bb = good.to_lib(A), good.to_lib(B), bad.to_lib(A13), bad.to_lib(B13)
+        with pytest.raises(hx.HxError):
+            hx.hx_matmul_jobs([(good.ctx, good.ks, ga, gb, h), (bad.ctx, bad.ks, ba, bb, h)])
+        out = hx.hx_matmul_jobs([(good.ctx, good.ks, ga, gb, h)])[0]
+        assert good.same(out, Hc.matmul(C.Evaluator(good.octx, good.oks), A, B, h, Hc.MaskProvider(good.octx, h, limbs)))
+        for c in (out, ga, gb, ba, bb):
+            hx.hx_ct_destroy(c)
+    finally:
+        good.close()
+        bad.close()
+
+
 def test_matmul_library_masks_end_to_end():
     """The product path: library encryption, library masks, library decryption;
     config 0 (N=2^12, h=16, one product with the other packed slots zero)."""
