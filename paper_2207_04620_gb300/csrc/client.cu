@@ -105,27 +105,34 @@ __device__ __forceinline__ int64_t round_coeff(ddv x, int *bad)
     return k;
 }
 
-// slot j of vector b goes to the bit-reversed positions of exponents e_j and 2N - e_j
+// The 2N-point transform's input holds slot j at the bit-reversed positions of the odd exponents
+// e_j and 2N - e_j, and zeros at every even exponent.  Bit reversal sends even exponents to the
+// first half, so the first half stays zero through every stage but the last, whose butterflies
+// then give A_i = w_i B_i (i < N, w_i = roots[i]) from the second half B alone.  The transform
+// therefore runs on the second half only (N points, compact: position p at p - N), and the last
+// stage is folded into the coefficients' read-out; every double-double value is the one the full
+// transform computes (adding a zero returns the other operand exactly).
 __global__ void k_enc_place(double4 *A, const double *slots, size_t n_slots, const int *e, int log_m, int half_n)
 {
     const int b = blockIdx.y;
-    const int m = 1 << log_m;
-    double4 *a = A + (size_t)b * m;
+    const int m = 1 << log_m, n = m >> 1;
+    double4 *a = A + (size_t)b * n;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < half_n; j += gridDim.x * blockDim.x) {
         const double z = (size_t)j < n_slots ? slots[(size_t)b * n_slots + j] : 0.0;
         const unsigned p1 = __brev((unsigned)e[j]) >> (32 - log_m);
         const unsigned p2 = __brev((unsigned)((m - e[j]) & (m - 1))) >> (32 - log_m);
-        a[p1] = make_double4(z, 0.0, 0.0, 0.0);
-        a[p2] = make_double4(z, 0.0, 0.0, 0.0);
+        a[p1 - n] = make_double4(z, 0.0, 0.0, 0.0);
+        a[p2 - n] = make_double4(z, 0.0, 0.0, 0.0);
     }
 }
 
-// stages len = 2 .. kFftTile (radix-2 decimation in time) on contiguous tiles in shared memory
+// stages len = 2 .. kFftTile (radix-2 decimation in time) on contiguous tiles of the compact
+// second half in shared memory
 __global__ void __launch_bounds__(kFftTile / 2) k_enc_fft_tile(double4 *A, const double4 *__restrict__ roots, int log_m)
 {
     __shared__ double4 s[kFftTile];
     const int m = 1 << log_m;
-    double4 *a = A + (size_t)blockIdx.y * m + (size_t)blockIdx.x * kFftTile;
+    double4 *a = A + (size_t)blockIdx.y * (m >> 1) + (size_t)blockIdx.x * kFftTile;
     for (int i = threadIdx.x; i < kFftTile; i += blockDim.x) s[i] = a[i];
     __syncthreads();
     for (int len = 2; len <= kFftTile; len <<= 1) {
@@ -142,12 +149,12 @@ __global__ void __launch_bounds__(kFftTile / 2) k_enc_fft_tile(double4 *A, const
     for (int i = threadIdx.x; i < kFftTile; i += blockDim.x) a[i] = s[i];
 }
 
-// one later stage (len > kFftTile) over global memory
+// one later stage (kFftTile < len <= N) over the compact second half in global memory
 __global__ void k_enc_fft_stage(double4 *A, const double4 *__restrict__ roots, int log_m, int len)
 {
     const int m = 1 << log_m, half = len >> 1, step = m / len;
-    double4 *a = A + (size_t)blockIdx.y * m;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m / 2; t += gridDim.x * blockDim.x) {
+    double4 *a = A + (size_t)blockIdx.y * (m >> 1);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m / 4; t += gridDim.x * blockDim.x) {
         const int g = t / half, k = t % half, i = g * len + k;
         double4 u = a[i], v = a[i + half];
         butterfly(u, v, roots[(size_t)k * step]);
@@ -156,16 +163,23 @@ __global__ void k_enc_fft_stage(double4 *A, const double4 *__restrict__ roots, i
     }
 }
 
+// Re A_i = Re(w_i B_i), the last stage's butterfly on a zero first-half entry
+__device__ __forceinline__ ddv enc_last_re(const double4 bi, const double4 w)
+{
+    return dd_minus(dd_times(ddv{bi.x, bi.y}, ddv{w.x, w.y}), dd_times(ddv{bi.z, bi.w}, ddv{w.z, w.w}));
+}
+
 // coefficient i = round(Re A_i / N * scale) under round_coeff; a coefficient past 2^62 sets *err
-__global__ void k_enc_round(int64_t *out, size_t out_stride, const double4 *A, int log_m, int n, double scale,
-                            int *err)
+__global__ void k_enc_round(int64_t *out, size_t out_stride, const double4 *A, const double4 *__restrict__ roots,
+                            int n, double scale, int *err)
 {
     const int b = blockIdx.y;
-    const double4 *a = A + ((size_t)b << log_m);
+    const double4 *a = A + (size_t)b * n;
     const double inv_n = 1.0 / n;  // a power of two: exact
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         int bad = 0;
-        const ddv m{__dmul_rn(a[i].x, inv_n), __dmul_rn(a[i].y, inv_n)};
+        const ddv re = enc_last_re(a[i], roots[i]);
+        const ddv m{__dmul_rn(re.hi, inv_n), __dmul_rn(re.lo, inv_n)};
         const int64_t v = round_coeff(dd_times_d(m, scale), &bad);
         if (bad) atomicExch(err, 1);
         out[b * out_stride + i] = bad ? 0 : v;
@@ -173,13 +187,15 @@ __global__ void k_enc_round(int64_t *out, size_t out_stride, const double4 *A, i
 }
 
 // the encoder's real coefficients m_i = Re(a_i) / n (double-double), before the scale
-__global__ void k_enc_real(double2 *m, size_t m_stride, const double4 *A, int log_m, int n)
+__global__ void k_enc_real(double2 *m, size_t m_stride, const double4 *A, const double4 *__restrict__ roots, int n)
 {
     const int b = blockIdx.y;
-    const double4 *a = A + ((size_t)b << log_m);
+    const double4 *a = A + (size_t)b * n;
     const double inv_n = 1.0 / n;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        m[b * m_stride + i] = make_double2(__dmul_rn(a[i].x, inv_n), __dmul_rn(a[i].y, inv_n));
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const ddv re = enc_last_re(a[i], roots[i]);
+        m[b * m_stride + i] = make_double2(__dmul_rn(re.hi, inv_n), __dmul_rn(re.lo, inv_n));
+    }
 }
 
 // out row r = round(m[idx[r]] * scale): k_enc_round's last steps on cached coefficients
@@ -249,20 +265,21 @@ const EncTables &enc_tables(hx_context &ctx)
     return ctx.enc_dev;
 }
 
-// the 2N-point transforms of `count` slot vectors, in place in A ([count][2N] complex double-double)
+// the 2N-point transforms of `count` slot vectors up to their last stage, in place in A
+// ([count][N] complex double-double: the second halves, see k_enc_place)
 void enc_transform(hx_context &ctx, const EncTables &t, double4 *a, const double *slots_dev, size_t n_slots,
                           int count, cudaStream_t s)
 {
-    const int N = ctx.N, log_m = ctx.log_n + 1, m = 2 * N;
+    const int N = ctx.N, log_m = ctx.log_n + 1;
     const double4 *roots = reinterpret_cast<const double4 *>(t.roots->p);
-    HX_CUDA(cudaMemsetAsync(a, 0, sizeof(double4) * (size_t)m * count, s));
+    HX_CUDA(cudaMemsetAsync(a, 0, sizeof(double4) * (size_t)N * count, s));
     k_enc_place<<<dim3(grid_for(N / 2), count), 256, 0, s>>>(a, slots_dev, n_slots,
                                                              reinterpret_cast<const int *>(t.e->p), log_m, N / 2);
-    k_enc_fft_tile<<<dim3(m / kFftTile, count), kFftTile / 2, 0, s>>>(a, roots, log_m);
-    for (int len = 2 * kFftTile; len <= m; len <<= 1)
-        k_enc_fft_stage<<<dim3(grid_for(m / 2), count), 256, 0, s>>>(a, roots, log_m, len);
+    k_enc_fft_tile<<<dim3(N / kFftTile, count), kFftTile / 2, 0, s>>>(a, roots, log_m);
+    for (int len = 2 * kFftTile; len <= N; len <<= 1)
+        k_enc_fft_stage<<<dim3(grid_for(N / 2), count), 256, 0, s>>>(a, roots, log_m, len);
     HX_CUDA(cudaGetLastError());
-    ctx.counters[C_LAUNCH] += 2 + (log_m - 10);
+    ctx.counters[C_LAUNCH] += 2 + (log_m - 11);
 }
 
 // vectors transformed per pass: bounds the complex double-double work buffer (32 B per point)
@@ -275,19 +292,20 @@ constexpr int kEncChunk = 64;
 void encode_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int count, double scale, int64_t *out,
                   size_t out_stride, cudaStream_t s)
 {
-    const int N = ctx.N, log_m = ctx.log_n + 1, m = 2 * N;
-    HX_CHECK(m % kFftTile == 0, HX_EINVAL, "the device encoder needs N >= 512");
+    const int N = ctx.N;
+    HX_CHECK(N % kFftTile == 0, HX_EINVAL, "the device encoder needs N >= 1024");
     HX_CHECK(n_slots <= (size_t)N / 2 && count >= 1 && count < 65536, HX_EINVAL, "bad slot batch");
     const EncTables &t = enc_tables(ctx);
+    const double4 *roots = reinterpret_cast<const double4 *>(t.roots->p);
     const int chunk = std::min(count, kEncChunk);
-    DevBuf A((size_t)4 * m * chunk, s);
+    DevBuf A((size_t)4 * N * chunk, s);
     DevBuf err(1, s);
     HX_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), s));
     double4 *a = reinterpret_cast<double4 *>(A.p);
     for (int b0 = 0; b0 < count; b0 += chunk) {
         const int c = std::min(chunk, count - b0);
         enc_transform(ctx, t, a, slots_dev + (size_t)b0 * n_slots, n_slots, c, s);
-        k_enc_round<<<dim3(grid_for(N), c), 256, 0, s>>>(out + (size_t)b0 * out_stride, out_stride, a, log_m, N, scale,
+        k_enc_round<<<dim3(grid_for(N), c), 256, 0, s>>>(out + (size_t)b0 * out_stride, out_stride, a, roots, N, scale,
                                                          reinterpret_cast<int *>(err.p));
         HX_CUDA(cudaGetLastError());
         ctx.counters[C_LAUNCH] += 1;
@@ -304,17 +322,18 @@ void encode_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int 
 void encode_real_batch(hx_context &ctx, const double *slots_dev, size_t n_slots, int count, double2 *m_out,
                        cudaStream_t s)
 {
-    const int N = ctx.N, log_m = ctx.log_n + 1, m = 2 * N;
-    HX_CHECK(m % kFftTile == 0, HX_EINVAL, "the device encoder needs N >= 512");
+    const int N = ctx.N;
+    HX_CHECK(N % kFftTile == 0, HX_EINVAL, "the device encoder needs N >= 1024");
     HX_CHECK(n_slots <= (size_t)N / 2 && count >= 1 && count < 65536, HX_EINVAL, "bad slot batch");
     const EncTables &t = enc_tables(ctx);
+    const double4 *roots = reinterpret_cast<const double4 *>(t.roots->p);
     const int chunk = std::min(count, kEncChunk);
-    DevBuf A((size_t)4 * m * chunk, s);
+    DevBuf A((size_t)4 * N * chunk, s);
     double4 *a = reinterpret_cast<double4 *>(A.p);
     for (int b0 = 0; b0 < count; b0 += chunk) {
         const int c = std::min(chunk, count - b0);
         enc_transform(ctx, t, a, slots_dev + (size_t)b0 * n_slots, n_slots, c, s);
-        k_enc_real<<<dim3(grid_for(N), c), 256, 0, s>>>(m_out + (size_t)b0 * N, (size_t)N, a, log_m, N);
+        k_enc_real<<<dim3(grid_for(N), c), 256, 0, s>>>(m_out + (size_t)b0 * N, (size_t)N, a, roots, N);
         HX_CUDA(cudaGetLastError());
         ctx.counters[C_LAUNCH] += 1;
     }

@@ -300,9 +300,14 @@ void Encoder::fft(std::vector<std::complex<double>> &a, bool inverse) const
 void Encoder::encode_real(const double *slots, size_t count, std::vector<DD> &m) const
 {
     // radix-2 decimation in time over the slots scattered to exponents e_j and 2N - e_j (the
-    // conjugate of a real slot), in bit-reversed order; complex values as double-double pairs
+    // conjugate of a real slot), in bit-reversed order; complex values as double-double pairs.
+    // Every exponent that holds a slot is odd, and bit reversal sends the even ones (zeros) to the
+    // first half, which stays zero until the last stage; that stage gives A_i = w_i B_i (i < N)
+    // from the second half B.  So only the second half is transformed, and the last stage is
+    // folded into the read-out (adding a zero returns the other operand exactly: the values are
+    // the full transform's).
     const int len = 2 * n, bits = log_n + 1;
-    std::vector<DD> re(len, DD{0.0, 0.0}), im(len, DD{0.0, 0.0});
+    std::vector<DD> re(n, DD{0.0, 0.0}), im(n, DD{0.0, 0.0});  // positions n .. 2n - 1
     auto brv = [&](int x) {
         int r = 0;
         for (int b = 0; b < bits; b++) r |= ((x >> b) & 1) << (bits - 1 - b);
@@ -310,12 +315,12 @@ void Encoder::encode_real(const double *slots, size_t count, std::vector<DD> &m)
     };
     for (size_t j = 0; j < (size_t)(n / 2); j++) {
         const double z = j < count ? slots[j] : 0.0;
-        re[brv((int)e[j])] = DD{z, 0.0};
-        re[brv((int)((len - e[j]) % len))] = DD{z, 0.0};
+        re[brv((int)e[j]) - n] = DD{z, 0.0};
+        re[brv((int)((len - e[j]) % len)) - n] = DD{z, 0.0};
     }
-    for (int half = 1; half < len; half <<= 1) {
+    for (int half = 1; half < n; half <<= 1) {
         const int step = n / half;  // root index stride: e^(-2 pi i k / (2 half)) = roots[k * step]
-        for (int i = 0; i < len; i += 2 * half)
+        for (int i = 0; i < n; i += 2 * half)
             for (int k = 0; k < half; k++) {
                 const DD wr = roots_re[(size_t)k * step], wi = roots_im[(size_t)k * step];
                 const DD vr = re[i + k + half], vi = im[i + k + half];
@@ -331,7 +336,11 @@ void Encoder::encode_real(const double *slots, size_t count, std::vector<DD> &m)
     }
     m.resize(n);
     const double inv_n = 1.0 / n;  // a power of two: exact
-    for (int i = 0; i < n; i++) m[i] = DD{re[i].hi * inv_n, re[i].lo * inv_n};
+    for (int i = 0; i < n; i++) {
+        const DD vw = dd_mul(im[i], roots_im[i]);
+        const DD r = dd_add(dd_mul(re[i], roots_re[i]), DD{-vw.hi, -vw.lo});  // Re(w_i B_i)
+        m[i] = DD{r.hi * inv_n, r.lo * inv_n};
+    }
 }
 
 void Encoder::encode(const double *slots, size_t count, double scale, int64_t *coeffs) const
