@@ -515,8 +515,13 @@ void hx_counters_reset(hx_context *ctx);
  * radices (e.g. 16 then 8, or 8 then 16).  The best variant depends on the
  * batch: launches are grouped into buckets by their number of limbs (up to 64,
  * 256, 768, more), and each bucket is timed on its own batch (48, 176, 512 and
- * 1024 limbs) on this device; the fastest per (bucket, phase) is kept for the
- * context.  Every variant computes identical residues.  choice[4] (may be
+ * 1024 limbs) on this device, each variant's time the best of three rounds.
+ * Per (bucket, phase) the default (width 16, swapped radices off) is kept
+ * unless another variant is more than 2 % faster, in which case the fastest is
+ * kept: alone the widths differ by about their timing noise, and blocks of the
+ * default size share the SMs best with concurrently running kernels.  The
+ * table belongs to the context.  Every variant computes identical residues.
+ * The call runs on `stream` and synchronizes it.  choice[4] (may be
  * NULL) receives the variants of the 256-limb bucket as signed widths
  * (negative: swapped radices). */
 hx_status hx_autotune(hx_context *ctx, int32_t *choice, void *stream);
