@@ -203,30 +203,45 @@ def run_reference(args, world, rank):
 def other_metrics(args):
     """The rest of the headline metric in compact, time-bounded form, each with its own clocks:
     the NTT alone (N=2^14, 1600 limbs, forward and inverse GB/s), the config-2 composite sign
-    (64 ciphertexts, 3 timed steps) and a short serving stream (300 requests at 0.8x capacity)."""
+    (64 ciphertexts, 3 timed steps) and a short serving stream (300 requests at 0.8x capacity).
+    A record that fails carries its error instead, so the headline line is still printed."""
     out = {}
-    ns = argparse.Namespace(**vars(args))
-    ns.log_n, ns.rows, ns.steps, ns.warmup, ns.tiles, ns.reps = 14, 1600, 5, 3, None, 200
-    m = run_micro(ns)
-    out["ntt_micro"] = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in m.items()
-                        if k in ("log_n", "rows", "tiles", "fwd_ms", "inv_ms", "fwd_gbs", "inv_gbs", "fwd_frac",
-                                 "inv_frac", "fwd_alu_frac", "inv_alu_frac", "fwd_calibrated_frac",
-                                 "inv_calibrated_frac", "peak_gbs", "peak_kind", "clocks")}
-    out["ntt_micro"]["what"] = "forward / inverse NTT of 1600 limbs of N=2^14 (210 MB, > L2) in place; " \
-                               "CUDA events around 200 transforms per direction, median of 5 steps"
-    ns = argparse.Namespace(**vars(args))
-    ns.steps, ns.warmup, ns.relu, ns.alpha = 3, 1, False, None
-    sg = run_sign(ns)
-    out["sign_cfg2"] = {k: sg[k] for k in ("value", "unit", "ms_per_step", "steps", "max_err_vs_exact",
-                                            "max_err_vs_fp64_composite", "clocks", "kernel_shares")}
-    out["sign_cfg2"]["what"] = sg["metric"] + "; " + sg["config"]["workload"]
-    ns = argparse.Namespace(**vars(args))
-    ns.requests, ns.load, ns.lanes, ns.max_batch, ns.full, ns.sweep = 300, 0.8, 4, 16, False, False
-    sv = run_serve(ns)
-    out["serve"] = {"p50_ms": sv["value"], "p99_ms": sv["p99_ms"], "throughput_req_s": sv["throughput_req_s"],
-                    "offered_req_s": sv["offered_req_s"], "capacity_req_s": sv["capacity_req_s"],
-                    "requests": sv["requests"], "clocks": sv["clocks"],
-                    "what": "serving stream, " + sv["config"]["workload"]}
+
+    def ntt_micro():
+        ns = argparse.Namespace(**vars(args))
+        ns.log_n, ns.rows, ns.steps, ns.warmup, ns.tiles, ns.reps = 14, 1600, 5, 3, None, 200
+        m = run_micro(ns)
+        r = {k: (round(v, 4) if isinstance(v, float) else v) for k, v in m.items()
+             if k in ("log_n", "rows", "tiles", "fwd_ms", "inv_ms", "fwd_gbs", "inv_gbs", "fwd_frac", "inv_frac",
+                      "fwd_alu_frac", "inv_alu_frac", "fwd_calibrated_frac", "inv_calibrated_frac", "peak_gbs",
+                      "peak_kind", "clocks")}
+        r["what"] = "forward / inverse NTT of 1600 limbs of N=2^14 (210 MB, > L2) in place; " \
+                    "CUDA events around 200 transforms per direction, median of 5 steps"
+        return r
+
+    def sign_cfg2():
+        ns = argparse.Namespace(**vars(args))
+        ns.steps, ns.warmup, ns.relu, ns.alpha = 3, 1, False, None
+        sg = run_sign(ns)
+        r = {k: sg[k] for k in ("value", "unit", "ms_per_step", "steps", "max_err_vs_exact",
+                                "max_err_vs_fp64_composite", "clocks", "kernel_shares")}
+        r["what"] = sg["metric"] + "; " + sg["config"]["workload"]
+        return r
+
+    def serve():
+        ns = argparse.Namespace(**vars(args))
+        ns.requests, ns.load, ns.lanes, ns.max_batch, ns.full, ns.sweep = 300, 0.8, 4, 16, False, False
+        sv = run_serve(ns)
+        return {"p50_ms": sv["value"], "p99_ms": sv["p99_ms"], "throughput_req_s": sv["throughput_req_s"],
+                "offered_req_s": sv["offered_req_s"], "capacity_req_s": sv["capacity_req_s"],
+                "requests": sv["requests"], "clocks": sv["clocks"], "what": "serving stream, " + sv["config"]["workload"]}
+
+    for name, fn in (("ntt_micro", ntt_micro), ("sign_cfg2", sign_cfg2), ("serve", serve)):
+        try:
+            out[name] = fn()
+        except Exception as e:  # noqa: BLE001 -- reported on the line, the headline stands
+            out[name] = {"error": "%s: %s" % (type(e).__name__, e)}
+            print("bench: %s failed: %s" % (name, e), file=sys.stderr, flush=True)
     return out
 
 
@@ -465,12 +480,17 @@ def run_hx(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_extras:
         line.update(other_metrics(args))
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        state = oracle_setup()
-        t = oracle_step(state)
-        line["cpu_baseline"] = {"value": round(BETA / t, 4), "unit": "matmul/s", "cores": cpu_cores(),
-                                "kind": "oracle",
-                                "sample": "one ciphertext pair (%d packed products) through the oracle's Alg. 3, "
-                                          "%.1f s" % (BETA, t)}
+        try:
+            state = oracle_setup()
+            t = oracle_step(state)
+            line["cpu_baseline"] = {"value": round(BETA / t, 4), "unit": "matmul/s", "cores": cpu_cores(),
+                                    "kind": "oracle",
+                                    "sample": "one ciphertext pair (%d packed products) through the oracle's Alg. 3, "
+                                              "%.1f s" % (BETA, t)}
+        except Exception as e:  # noqa: BLE001 -- reported on the line, the headline stands
+            line["cpu_baseline"] = {"value": None, "unit": "matmul/s", "kind": "oracle",
+                                    "error": "%s: %s" % (type(e).__name__, e)}
+            print("bench: cpu_baseline failed: %s" % e, file=sys.stderr, flush=True)
     if line is not None:
         print(json.dumps(line), flush=True)
 
