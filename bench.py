@@ -63,7 +63,7 @@ def sha_of(path):
 def ntt_kernels_sha():
     """Hash of the source of the per-ring NTT phase kernels: ntt.cu without its marked
     several-ring sections (kernels and launcher, which those phase kernels do not use) and without
-    its marked autotuner (host code that only times the kernels)."""
+    its marked host launcher and autotuner (which pick and time the kernels, changing none)."""
     with open(os.path.join(ROOT, "paper_2207_04620_gb300", "csrc", "ntt.cu")) as f:
         src = f.read()
     src = re.sub(r"// ---- several rings in one launch.*?// ---- end of the several-ring kernels\n\n", "", src,
@@ -71,6 +71,7 @@ def ntt_kernels_sha():
     src = re.sub(r"// ---- several rings: launcher\n.*?// ---- end of the several-ring launcher\n\n", "", src,
                  flags=re.S)
     src = re.sub(r"// ---- autotuner[^\n]*\n.*?// ---- end of the autotuner\n\n", "", src, flags=re.S)
+    src = re.sub(r"// ---- launcher[^\n]*\n.*?// ---- end of the launcher\n\n", "", src, flags=re.S)
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 

@@ -519,18 +519,28 @@ void hx_counters_reset(hx_context *ctx);
  * Per (bucket, phase) the default (width 16, swapped radices off) is kept
  * unless another variant is more than 2 % faster, in which case the fastest is
  * kept: alone the widths differ by about their timing noise, and blocks of the
- * default size share the SMs best with concurrently running kernels.  The
- * table belongs to the context.  Every variant computes identical residues.
+ * default size share the SMs best with concurrently running kernels.  For an
+ * odd log N both splits of the stages between the two phases are tuned this
+ * way, and the other split replaces the default (the column phase taking
+ * floor(log N / 2) stages) when the sum of its phases' times is more than 2 %
+ * lower.  The table belongs to the context.  Every variant computes identical residues.
  * The call runs on `stream` and synchronizes it.  choice[4] (may be
  * NULL) receives the variants of the 256-limb bucket as signed widths
  * (negative: swapped radices). */
 hx_status hx_autotune(hx_context *ctx, int32_t *choice, void *stream);
 /* Sets (set != NULL: signed widths per phase, in the order above, for every
- * bucket) and/or reads (get != NULL: the 256-limb bucket) the NTT variants. */
+ * bucket, with the default phase split) and/or reads (get != NULL: the
+ * 256-limb bucket) the NTT variants. */
 hx_status hx_ntt_tiles(hx_context *ctx, const int32_t *set, int32_t *get);
-/* The tuning table: per bucket six integers (largest limb count of the bucket,
- * limbs it was timed on, then the four phases' signed widths).  Writes at most
- * cap integers; returns the table's length. */
+/* Sets the split of an odd log N between the two NTT phases for every bucket
+ * (0: the column phase takes floor(log N / 2) stages, 1: the other half; no
+ * effect for an even log N).  HX_EINVAL for another value. */
+hx_status hx_ntt_split(hx_context *ctx, int split);
+/* The tuning table: per bucket seven integers (largest limb count of the
+ * bucket, limbs it was timed on, the four phases' signed widths, then the split
+ * of an odd log N: 0 when the column phase takes floor(log N / 2) stages, 1 when
+ * it takes the other half).  Writes at most cap integers; returns the table's
+ * length. */
 int hx_ntt_tuning(const hx_context *ctx, int32_t *out, int cap);
 
 /* ---- profiling ------------------------------------------------------------- */

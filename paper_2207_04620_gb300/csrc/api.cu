@@ -1244,10 +1244,10 @@ hx_status hx_autotune(hx_context *ctx, int32_t *choice, void *stream)
     HX_CUDA(cudaMemsetAsync(buf.p, 0, sizeof(uint64_t) * rows_max * ctx->N, S(stream)));
     Eval ev(*ctx, S(stream));
     for (int b = 0; b < NTT_BUCKETS; b++) {
-        int best[4] = {2, 2, 2, 2};
+        int best[5] = {2, 2, 2, 2, 0};
         float ms[4];
         autotune_ntt(ev.lc(), buf.p, std::min(kNttBucketTune[b], rows_max), best, ms);
-        for (int i = 0; i < 4; i++) ctx->t.ntt_var[b][i] = best[i];
+        for (int i = 0; i < 5; i++) ctx->t.ntt_var[b][i] = best[i];
     }
     if (choice)
         for (int i = 0; i < 4; i++) choice[i] = variant_width(ctx->t.ntt_var[1][i]);
@@ -1269,11 +1269,22 @@ hx_status hx_ntt_tiles(hx_context *ctx, const int32_t *set, int32_t *get)
             }
             need(v[i] >= 0, "tile width must be 4, 8, 16 or 32 (negative: swapped radices)");
         }
-        for (int b = 0; b < NTT_BUCKETS; b++)
+        for (int b = 0; b < NTT_BUCKETS; b++) {
             for (int i = 0; i < 4; i++) ctx->t.ntt_var[b][i] = v[i];
+            ctx->t.ntt_var[b][4] = 0;  // the default split of an odd log N
+        }
     }
     if (get)
         for (int i = 0; i < 4; i++) get[i] = variant_width(ctx->t.ntt_var[1][i]);
+    return HX_OK;
+    HX_END
+}
+
+hx_status hx_ntt_split(hx_context *ctx, int split)
+{
+    HX_TRY
+    need(ctx && (split == 0 || split == 1), "split must be 0 or 1");
+    for (int b = 0; b < NTT_BUCKETS; b++) ctx->t.ntt_var[b][4] = split;
     return HX_OK;
     HX_END
 }
@@ -1283,10 +1294,10 @@ int hx_ntt_tuning(const hx_context *ctx, int32_t *out, int cap)
     if (!ctx || (!out && cap > 0)) return HX_EINVAL;
     int n = 0;
     for (int b = 0; b < NTT_BUCKETS; b++) {
-        const int32_t row[6] = {kNttBucketMax[b], kNttBucketTune[b], variant_width(ctx->t.ntt_var[b][0]),
+        const int32_t row[7] = {kNttBucketMax[b], kNttBucketTune[b], variant_width(ctx->t.ntt_var[b][0]),
                                 variant_width(ctx->t.ntt_var[b][1]), variant_width(ctx->t.ntt_var[b][2]),
-                                variant_width(ctx->t.ntt_var[b][3])};
-        for (int k = 0; k < 6; k++, n++)
+                                variant_width(ctx->t.ntt_var[b][3]), ctx->t.ntt_var[b][4]};
+        for (int k = 0; k < 7; k++, n++)
             if (n < cap) out[n] = row[k];
     }
     return n;

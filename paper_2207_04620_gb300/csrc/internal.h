@@ -115,7 +115,9 @@ struct DeviceTables {
     RescaleTable *rescale = nullptr;// [n_q+1] by limbs
     RelinRescaleTable *relin_rs = nullptr;  // [n_q+1] by limbs
     // NTT variant per batch-size bucket and phase (fwd cols, fwd rows, inv cols, inv rows)
-    int ntt_var[NTT_BUCKETS][4] = {{2, 2, 2, 2}, {2, 2, 2, 2}, {2, 2, 2, 2}, {2, 2, 2, 2}};
+    // per bucket: the four phases' variants (forward column, forward row, inverse column, inverse
+    // row), then the split of an odd log N (0: the column phase takes floor(log N / 2) stages, 1: ceil)
+    int ntt_var[NTT_BUCKETS][5] = {{2, 2, 2, 2, 0}, {2, 2, 2, 2, 0}, {2, 2, 2, 2, 0}, {2, 2, 2, 2, 0}};
     int n_sm = 1;                   // multiprocessors of the device
 };
 

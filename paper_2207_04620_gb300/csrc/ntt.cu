@@ -583,13 +583,14 @@ __global__ void __launch_bounds__(kMultiT) k_ntt_multi(const NttJob *__restrict_
 
 } // namespace
 
+// ---- launcher (host code: it picks the tuned variants and the phase split of the kernels above)
 void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse)
 {
     Timed tm_(c, K_NTT, 16.0 * rows.n_rows * rows.n_groups * c.N);
     if (rows.n_rows <= 0 || rows.n_groups <= 0) return;
     HX_CHECK(rows.n_rows <= MAX_NTT_ROWS && rows.n_groups < 65536, HX_EINVAL, "NTT batch too large");
-    const int logm1 = c.log_n / 2, logm2 = c.log_n - logm1;
     const int *v = c.t->ntt_var[ntt_bucket((long long)rows.n_rows * rows.n_groups)];
+    const int logm1 = c.log_n / 2 + ((c.log_n & 1) && v[4] ? 1 : 0), logm2 = c.log_n - logm1;
     if (!inverse) {
         ntt_phase<false>(c, rows, true, logm1, v[0]);
         ntt_phase<false>(c, rows, false, logm2, v[1]);
@@ -599,11 +600,13 @@ void launch_ntt(const LaunchCtx &c, const NttRows &rows, bool inverse)
     }
     post(c, 2);
 }
+// ---- end of the launcher
 
 // ---- autotuner (host code: it times the phase kernels and changes none of them)
 void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float *ms_out)
 {
-    // times every tile width of each phase on `rows` limbs (one prime each) in place
+    // times every tile width of each phase on `rows` limbs (one prime each) in place, for each
+    // split of an odd log N between the phases
     NttRows *r = new NttRows();
     std::unique_ptr<NttRows> guard(r);
     r->src = r->dst = buf;
@@ -614,7 +617,6 @@ void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float 
         r->src_off[i] = r->dst_off[i] = (int16_t)i;
         r->prime[i] = 0;
     }
-    const int logm1 = c.log_n / 2, logm2 = c.log_n - logm1;
     cudaEvent_t e0, e1;
     HX_CUDA(cudaEventCreate(&e0));
     HX_CUDA(cudaEventCreate(&e1));
@@ -622,42 +624,58 @@ void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float 
     // over the variants so drift hits them alike.  A variant replaces the default (width 16: four
     // warps per block in the 128-point phases) only when it is clearly faster: the widths' isolated
     // times differ by about their noise (1-2 % at the batch sizes of a product's launches), and
-    // blocks of the default size share the SMs best with the kernels of concurrent chains.
+    // blocks of the default size share the SMs best with the kernels of concurrent chains.  The
+    // other split of an odd log N replaces the default one on the same rule, by the sum of its
+    // four phases' times.
     constexpr int kDefault = 2, kRounds = 3, kRuns = 5;
     constexpr float kClearWin = 0.98f;
-    for (int ph = 0; ph < 4; ph++) {
-        const bool cols = ph == 0 || ph == 2, inv = ph >= 2;
-        const int logm = cols ? logm1 : logm2;
-        float t[NTT_VARIANTS];
-        bool ok[NTT_VARIANTS];
-        for (int v = 0; v < NTT_VARIANTS; v++) {
-            t[v] = 1e30f;
-            ok[v] = kNttTiles[v % NTT_WIDTHS] <= (c.N >> logm) && (v < NTT_WIDTHS || (logm & 1));
-        }
-        for (int round = 0; round < kRounds; round++)
+    float split_ms[2] = {0.f, 0.f};
+    int split_best[2][4];
+    float split_phase_ms[2][4];
+    const int n_splits = (c.log_n & 1) ? 2 : 1;
+    for (int sp = 0; sp < n_splits; sp++) {
+        const int logm1 = c.log_n / 2 + sp, logm2 = c.log_n - logm1;
+        for (int ph = 0; ph < 4; ph++) {
+            const bool cols = ph == 0 || ph == 2, inv = ph >= 2;
+            const int logm = cols ? logm1 : logm2;
+            float t[NTT_VARIANTS];
+            bool ok[NTT_VARIANTS];
             for (int v = 0; v < NTT_VARIANTS; v++) {
-                if (!ok[v]) continue;
-                auto run = [&]() {
-                    if (inv) ntt_phase<true>(c, *r, cols, logm, v);
-                    else ntt_phase<false>(c, *r, cols, logm, v);
-                };
-                run();  // warm-up
-                HX_CUDA(cudaEventRecord(e0, c.stream));
-                for (int it = 0; it < kRuns; it++) run();
-                HX_CUDA(cudaEventRecord(e1, c.stream));
-                HX_CUDA(cudaEventSynchronize(e1));
-                float ms = 0;
-                HX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-                t[v] = std::min(t[v], ms / kRuns);
+                t[v] = 1e30f;
+                ok[v] = kNttTiles[v % NTT_WIDTHS] <= (c.N >> logm) && (v < NTT_WIDTHS || (logm & 1));
             }
-        int pick = ok[kDefault] ? kDefault : -1;
-        for (int v = 0; v < NTT_VARIANTS; v++) {
-            if (!ok[v] || v == pick) continue;
-            if (pick < 0 || t[v] < (pick == kDefault ? kClearWin : 1.0f) * t[pick]) pick = v;
+            for (int round = 0; round < kRounds; round++)
+                for (int v = 0; v < NTT_VARIANTS; v++) {
+                    if (!ok[v]) continue;
+                    auto run = [&]() {
+                        if (inv) ntt_phase<true>(c, *r, cols, logm, v);
+                        else ntt_phase<false>(c, *r, cols, logm, v);
+                    };
+                    run();  // warm-up
+                    HX_CUDA(cudaEventRecord(e0, c.stream));
+                    for (int it = 0; it < kRuns; it++) run();
+                    HX_CUDA(cudaEventRecord(e1, c.stream));
+                    HX_CUDA(cudaEventSynchronize(e1));
+                    float ms = 0;
+                    HX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                    t[v] = std::min(t[v], ms / kRuns);
+                }
+            int pick = ok[kDefault] ? kDefault : -1;
+            for (int v = 0; v < NTT_VARIANTS; v++) {
+                if (!ok[v] || v == pick) continue;
+                if (pick < 0 || t[v] < (pick == kDefault ? kClearWin : 1.0f) * t[pick]) pick = v;
+            }
+            split_best[sp][ph] = pick < 0 ? kDefault : pick;
+            split_phase_ms[sp][ph] = pick < 0 ? 0.f : t[pick];
+            split_ms[sp] += split_phase_ms[sp][ph];
         }
-        best[ph] = pick < 0 ? kDefault : pick;
-        if (ms_out) ms_out[ph] = pick < 0 ? 0.f : t[pick];
     }
+    const int sp = (n_splits == 2 && split_ms[1] < kClearWin * split_ms[0]) ? 1 : 0;
+    for (int ph = 0; ph < 4; ph++) {
+        best[ph] = split_best[sp][ph];
+        if (ms_out) ms_out[ph] = split_phase_ms[sp][ph];
+    }
+    best[4] = sp;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     HX_CUDA(cudaGetLastError());

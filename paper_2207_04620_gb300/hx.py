@@ -129,6 +129,7 @@ _SIGS = {
     "hx_autotune": (c_int, [c_vp, P_i32, c_vp]),
     "hx_ntt_tiles": (c_int, [c_vp, P_i32, P_i32]),
     "hx_ntt_tuning": (c_int, [c_vp, P_i32, c_int]),
+    "hx_ntt_split": (c_int, [c_vp, c_int]),
     "hx_profile_enable": (c_int, [c_vp, c_int]),
     "hx_profile_read": (c_int, [c_vp, c_int, ctypes.c_char_p, c_size_t, P_u64, P_dbl, P_dbl]),
 }
@@ -759,11 +760,18 @@ def hx_autotune(ctx: int, stream=None) -> list:
 
 
 def hx_ntt_tuning(ctx: int) -> list:
-    """The autotuner's table: per bucket {max_limbs, tuned_limbs, widths[4]} (signed widths)."""
+    """The autotuner's table: per bucket {max_limbs, tuned_limbs, widths[4] (signed widths),
+    split (of an odd log N: 1 when the column phase takes the larger half of the stages)}."""
     out = np.zeros(64, dtype=np.int32)
     n = _chk(lib().hx_ntt_tuning(ctx, out.ctypes.data_as(P_i32), out.size))
-    return [{"max_limbs": int(out[i]), "tuned_limbs": int(out[i + 1]), "widths": [int(x) for x in out[i + 2:i + 6]]}
-            for i in range(0, n, 6)]
+    return [{"max_limbs": int(out[i]), "tuned_limbs": int(out[i + 1]), "widths": [int(x) for x in out[i + 2:i + 6]],
+             "split": int(out[i + 6])} for i in range(0, n, 7)]
+
+
+def hx_ntt_split(ctx: int, split: int) -> None:
+    """Sets the split of an odd log N between the NTT phases for every bucket (0: the column phase
+    takes floor(log N / 2) stages, 1: the other half)."""
+    _chk(lib().hx_ntt_split(ctx, int(split)))
 
 
 def hx_ntt_tiles(ctx: int, widths=None) -> list:

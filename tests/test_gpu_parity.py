@@ -107,7 +107,7 @@ def test_ntt_multi_ring_one_launch_bit_exact():
             hx.hx_context_destroy(c)
 
 
-@pytest.mark.parametrize("log_n", [11, 14, 16])
+@pytest.mark.parametrize("log_n", [11, 14, 15, 16])
 def test_ntt_every_tile_width_and_autotune(log_n):
     import torch
 
@@ -117,19 +117,23 @@ def test_ntt_every_tile_width_and_autotune(log_n):
         primes = octx.q + octx.p
         x = workloads.residues(3, primes, 2, octx.N)
         want = octx.ntt(x, primes * 2)
-        for w in ([4] * 4, [8] * 4, [16] * 4, [32] * 4, [8, 32, 16, 8], [-4, -8, -16, -32], [-16, 4, 32, -8]):
+        widths = ([4] * 4, [8] * 4, [16] * 4, [32] * 4, [8, 32, 16, 8], [-4, -8, -16, -32], [-16, 4, 32, -8])
+        # an odd log N also runs with the column phase taking the larger half of the stages
+        for w, split in [(w, sp) for w in widths for sp in ((0, 1) if log_n & 1 else (0,))]:
             hx.hx_ntt_tiles(ctx, w)
+            hx.hx_ntt_split(ctx, split)
             dev = torch.from_numpy(x.view(np.int64).copy()).cuda()
             hx.hx_ntt(ctx, dev.data_ptr(), 2, [0, 1, 2])
             torch.cuda.synchronize()
-            assert np.array_equal(dev.cpu().numpy().view(np.uint64), want), w
+            assert np.array_equal(dev.cpu().numpy().view(np.uint64), want), (w, split)
             hx.hx_ntt(ctx, dev.data_ptr(), 2, [0, 1, 2], inverse=True)
             torch.cuda.synchronize()
-            assert np.array_equal(dev.cpu().numpy().view(np.uint64), x), w
+            assert np.array_equal(dev.cpu().numpy().view(np.uint64), x), (w, split)
         chosen = hx.hx_autotune(ctx)
         assert all(abs(c) in (4, 8, 16, 32) for c in chosen) and hx.hx_ntt_tiles(ctx) == chosen
         table = hx.hx_ntt_tuning(ctx)
         assert len(table) == 4 and table[1]["widths"] == chosen
+        assert all(t["split"] in ((0, 1) if log_n & 1 else (0,)) for t in table)
         assert [t["max_limbs"] for t in table][:3] == [64, 256, 768]
         # the tuned variants of every bucket give the same residues (a small and a large batch)
         for polys in (2, 200):
