@@ -198,6 +198,25 @@ hx_status hx_relin_rescale(hx_context *ctx, const hx_keyset *ks, const hx_ct *d,
 hx_status hx_drop(hx_context *ctx, const hx_ct *a, int limbs, hx_ct **out, void *stream);
 /* Rot(a, k): slots move left by k (R(m, k)); HX_EKEY without the Galois key. */
 hx_status hx_rotate(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, int32_t k, hx_ct **out, void *stream);
+/* One rotation of a several-ring call: ciphertext ct of context ctx rotated by
+ * `step` slots with ctx's key set ks. */
+typedef struct {
+    hx_context *ctx;
+    const hx_keyset *ks;
+    const hx_ct *ct;
+    int64_t step;
+} hx_rotate_job;
+/* Rot (Fig. 1 item 11) of ciphertexts of any contexts (ring degrees 2^11 ..
+ * 2^16, prime chains, levels) in one call.  Each stage of their hybrid key
+ * switches runs as one launch over every job: the automorphism, ModUp's
+ * inverse NTT, basis conversion and NTT, the key inner product, ModDown's
+ * inverse NTT, conversion and NTT, and the epilogue (13 launches in all).  The
+ * stage kernels run the bodies of the one-ring ones, so out[i] (a handle of
+ * jobs[i].ctx) equals hx_rotate of job i residue for residue.  A step of 0
+ * mod N/2 copies.  The contexts must share one device.  Every check (null
+ * fields, handles of another context, HX_EKEY for a missing Galois key) comes
+ * before any device work; on an error no output is set.  count <= 65535. */
+hx_status hx_rotate_jobs(const hx_rotate_job *jobs, size_t count, hx_ct **out, void *stream);
 /* n rotations of one ciphertext sharing a single ModUp of c1 (hoisting). */
 hx_status hx_rotate_hoisted(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, const int32_t *steps, int n,
                             hx_ct **outs, void *stream);

@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libhx.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["ntt.cu", "kernels.cu", "eval.cu", "keys.cu", "schedules.cu", "context.cu", "api.cu", "noalloc.cu", "server.cu", "client.cu", "host_math.cpp"]
+SOURCES = ["ntt.cu", "kernels.cu", "eval.cu", "keys.cu", "schedules.cu", "context.cu", "api.cu", "noalloc.cu", "server.cu",
+           "client.cu", "multi.cu", "host_math.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

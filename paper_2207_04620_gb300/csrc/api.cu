@@ -657,6 +657,27 @@ hx_status hx_rotate(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, int32_
     HX_END
 }
 
+hx_status hx_rotate_jobs(const hx_rotate_job *jobs, size_t count, hx_ct **out, void *stream)
+{
+    HX_TRY
+    need(jobs && out && count >= 1 && count < 65536, "bad argument");
+    for (size_t i = 0; i < count; i++) out[i] = nullptr;
+    std::vector<RotateJob> v(count);
+    for (size_t i = 0; i < count; i++) {
+        const hx_rotate_job &J = jobs[i];
+        need(J.ctx && J.ks && J.ct, "null job field");
+        mine(J.ctx, J.ks);
+        mine(J.ctx, J.ct);
+        v[i] = RotateJob{J.ctx, J.ks, J.ct->c, J.step};
+    }
+    std::vector<Cts> r = rotate_jobs(v, S(stream));
+    std::vector<std::unique_ptr<hx_ct>> h(count);
+    for (size_t i = 0; i < count; i++) h[i].reset(wrap(jobs[i].ctx, r[i]));
+    for (size_t i = 0; i < count; i++) out[i] = h[i].release();
+    return HX_OK;
+    HX_END
+}
+
 hx_status hx_rotate_hoisted(hx_context *ctx, const hx_keyset *ks, const hx_ct *a, const int32_t *steps, int n,
                             hx_ct **outs, void *stream)
 {

@@ -191,6 +191,71 @@ void launch_key_ip(const LaunchCtx &c, View acc, const uint64_t *D, const uint64
 // out_c = (acc_c - conv_c) * P^-1, plus add_c[galois(j)] for the components set in add_mask
 void launch_moddown_final(const LaunchCtx &c, View out, View acc, View conv, const ModDownTable *tab, int B,
                           int limbs, View add, int add_mask, uint64_t add_galois);
+
+// ---- several rings in one launch per key-switching stage (one job = one ring's batch) ----------
+// Each kernel runs the body of its one-ring counterpart over every job: a flat grid whose block
+// b belongs to the job with the largest block0 <= b, at the coordinates that job's own grid
+// (gx, gy, gz) would give it.
+struct AutomorphismJob {
+    View out, in;
+    uint64_t g;
+    int comps, log_n;
+    const PrimeConst *primes;
+    int gx, gy, gz;
+    long long block0;
+};
+struct ConvertJob {
+    const ConvTable *tabs;
+    View out, in;
+    const PrimeConst *primes;
+    int groups, n, max_src;
+    size_t gstride_out, gstride_in;
+    int gx, gy, gz;
+    long long block0;
+};
+struct KeyIpJob {
+    View acc;
+    const uint64_t *D, *dnt, *key;
+    size_t dnt_bstride;
+    const PrimeConst *primes;
+    int n_all, n_q, K, alpha, limbs, ndig, log_n, few;
+    uint64_t g;
+    int gx, gy, gz;
+    long long block0;
+};
+struct ModDownJob {
+    View out, acc, conv, add;
+    const ModDownTable *tab;
+    const PrimeConst *primes;
+    int add_mask, log_n;
+    uint64_t g;
+    int gx, gy, gz;
+    long long block0;
+};
+// Fills every job's block0; returns the blocks of the grid over all of them.
+template <class J> long long plan_job_blocks(std::vector<J> &jobs)
+{
+    long long total = 0;
+    for (auto &j : jobs) {
+        j.block0 = total;
+        total += (long long)j.gx * j.gy * j.gz;
+    }
+    return total;
+}
+// one grid over the jobs of a table already on the device (blocks from plan_job_blocks)
+void launch_automorphism_jobs(cudaStream_t s, const AutomorphismJob *jobs, int n_jobs, long long blocks,
+                              std::atomic<uint64_t> *launches);
+void launch_convert_jobs(cudaStream_t s, const ConvertJob *jobs, int n_jobs, long long blocks, int max_src,
+                         std::atomic<uint64_t> *launches);
+void launch_key_ip_jobs(cudaStream_t s, const KeyIpJob *jobs, int n_jobs, long long blocks,
+                        std::atomic<uint64_t> *launches);
+void launch_moddown_jobs(cudaStream_t s, const ModDownJob *jobs, int n_jobs, long long blocks,
+                         std::atomic<uint64_t> *launches);
+// the NTT over several rings in two steps: tile offsets of every job (host), then the two phase
+// launches over a job table already on the device
+void plan_ntt_jobs(std::vector<NttJob> &jobs, int *tiles_cols, int *tiles_rows);
+void launch_ntt_jobs(cudaStream_t s, const NttJob *jobs, int n_jobs, int tiles_cols, int tiles_rows, bool inverse,
+                     int n_sm, std::atomic<uint64_t> *launches);
 void launch_lintrans_mac(const LaunchCtx &c, const MacArgs &a, int B, int limbs, int n_terms);
 // two hoisted rotations selected by a mask in the extended basis (see kernels.cu)
 void launch_key_ip_mux(const LaunchCtx &c, View out, const uint64_t *D, const uint64_t *dnt, size_t dnt_bstride,

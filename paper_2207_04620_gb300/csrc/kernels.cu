@@ -22,6 +22,16 @@ __device__ __forceinline__ int galois_src(int j, uint64_t g, int log_n)
     return brv_bits((unsigned)((e - 1) >> 1), log_n);
 }
 
+// A block's coordinates and its grid's extent: the hardware's, or those of one job inside a launch
+// that runs the same kernel body over the jobs of several rings (see the several-ring key switch)
+struct Blk {
+    int x, y, z, gx, gy, gz;
+    __device__ __forceinline__ static Blk hw()
+    {
+        return Blk{(int)blockIdx.x, (int)blockIdx.y, (int)blockIdx.z, (int)gridDim.x, (int)gridDim.y, (int)gridDim.z};
+    }
+};
+
 // ---- elementwise ----------------------------------------------------------------
 // grid: x over pairs of coefficients, y = limb, z = b*comps + comp
 
@@ -234,28 +244,36 @@ __global__ void k_tensor(View out, View a, View b, const PrimeConst *__restrict_
 }
 
 // out = sigma_g(in) (accumulate: out += sigma_g(in), rows modulo prime index = row)
-__global__ void k_automorphism(View out, View in, uint64_t g, int comps, int log_n, bool accumulate,
-                               const PrimeConst *__restrict__ primes)
+__device__ __forceinline__ void automorphism_body(const Blk &b, View out, View in, uint64_t g, int comps, int log_n,
+                                                  bool accumulate, const PrimeConst *__restrict__ primes)
 {
     const int n = 1 << log_n;
-    const int l = blockIdx.y, bc = blockIdx.z, bi = bc / comps, ci = bc % comps;
+    const int l = b.y, bc = b.z, bi = bc / comps, ci = bc % comps;
     const size_t oo = bi * out.bstride + ci * out.cstride + (size_t)l * n;
     const size_t oi = bi * in.bstride + ci * in.cstride + (size_t)l * n;
     const uint64_t q = accumulate ? primes[l].q : 0;
-    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    for (int j = b.x * blockDim.x + threadIdx.x; j < n; j += b.gx * blockDim.x) {
         const uint64_t v = in.p[oi + galois_src(j, g, log_n)];
         out.p[oo + j] = accumulate ? addmod(out.p[oo + j], v, q) : v;
     }
 }
-// Fast basis conversion; grid: x over coefficients, z = b * groups + grp
-template <int MK>  // at most MK sources (register arrays sized to it; four blocks per SM up to 4)
-__global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2)
-    k_basis_convert(const ConvTable *__restrict__ tabs, View out, View in, const PrimeConst *__restrict__ primes,
-                    int groups, size_t gstride_out, size_t gstride_in, int n)
+
+__global__ void k_automorphism(View out, View in, uint64_t g, int comps, int log_n, bool accumulate,
+                               const PrimeConst *__restrict__ primes)
+{
+    automorphism_body(Blk::hw(), out, in, g, comps, log_n, accumulate, primes);
+}
+
+// Fast basis conversion; grid: x over coefficients, z = b * groups + grp (at most MK sources: register
+// arrays sized to it)
+template <int MK>
+__device__ __forceinline__ void basis_convert_body(const Blk &b, const ConvTable *__restrict__ tabs, View out, View in,
+                                                   const PrimeConst *__restrict__ primes, int groups, size_t gstride_out,
+                                                   size_t gstride_in, int n)
 {
     // two adjacent coefficients per thread (16-byte loads and stores); the table's constants
     // staged in shared memory once per block
-    const int bz = blockIdx.z, bi = bz / groups, gi = bz % groups;
+    const int bz = b.z, bi = bz / groups, gi = bz % groups;
     const ConvTable &T = tabs[gi];
     __shared__ uint64_t sw[MAXK * MAXP], swsh[MAXK * MAXP];
     __shared__ uint64_t sq[MAXP], sbar[MAXP];
@@ -287,7 +305,7 @@ __global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2)
     __syncthreads();
     const uint64_t *src = in.p + bi * in.bstride + gi * gstride_in;
     uint64_t *dst = out.p + bi * out.bstride + gi * gstride_out;
-    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+    for (int j = (b.x * blockDim.x + threadIdx.x) * 2; j < n; j += b.gx * blockDim.x * 2) {
         uint64_t y0[MK], y1[MK];
 #pragma unroll
         for (int i = 0; i < MK; i++) {
@@ -338,16 +356,26 @@ __global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2)
     }
 }
 
+template <int MK>  // at most MK sources (register arrays sized to it; four blocks per SM up to 4)
+__global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2)
+    k_basis_convert(const ConvTable *__restrict__ tabs, View out, View in, const PrimeConst *__restrict__ primes,
+                    int groups, size_t gstride_out, size_t gstride_in, int n)
+{
+    basis_convert_body<MK>(Blk::hw(), tabs, out, in, primes, groups, gstride_out, gstride_in, n);
+}
+
 // Key inner product of hybrid key switching: for ext row t (Q_l then P),
 // acc_h[t] = sum_j src_j[t][galois(n)] * key[j][h][row(t)][n], where src_j is
 // the NTT-form input itself on digit j's own rows and the ModUp output D_j
 // elsewhere.  Keys are in Montgomery form, so one reduction gives the sum.
-__global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt, size_t dnt_bstride,
-                         const uint64_t *__restrict__ key, const PrimeConst *__restrict__ primes, int n_all, int n_q,
-                         int K, int alpha, int limbs, int ndig, uint64_t g, int log_n, bool accumulate, bool few)
+__device__ __forceinline__ void key_ip_body(const Blk &b, View acc, const uint64_t *__restrict__ D,
+                                            const uint64_t *__restrict__ dnt, size_t dnt_bstride,
+                                            const uint64_t *__restrict__ key, const PrimeConst *__restrict__ primes,
+                                            int n_all, int n_q, int K, int alpha, int limbs, int ndig, uint64_t g,
+                                            int log_n, bool accumulate, bool few)
 {
     const int n = 1 << log_n;
-    const int t = blockIdx.y, bi = blockIdx.z;
+    const int t = b.y, bi = b.z;
     const int ext = limbs + K;
     const int pr = t < limbs ? t : n_q + (t - limbs);
     const PrimeConst P = primes[pr];
@@ -356,7 +384,7 @@ __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_
     const uint64_t *db = dnt + bi * dnt_bstride;
     const int own_digit = t < limbs ? t / alpha : -1;  // digit j holds Q rows j*alpha ..
     // two adjacent outputs per thread: 16-byte key loads and stores, the sources gathered
-    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+    for (int j = (b.x * blockDim.x + threadIdx.x) * 2; j < n; j += b.gx * blockDim.x * 2) {
         const int js0 = g == 1 ? j : galois_src(j, g, log_n), js1 = g == 1 ? j + 1 : galois_src(j + 1, g, log_n);
         Acc128 a0, a1, b0, b1;
         for (int d = 0; d < ndig; d++) {
@@ -388,6 +416,14 @@ __global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_
         *o0 = r0;
         *o1 = r1;
     }
+}
+
+__global__ void k_key_ip(View acc, const uint64_t *__restrict__ D, const uint64_t *__restrict__ dnt, size_t dnt_bstride,
+                         const uint64_t *__restrict__ key, const PrimeConst *__restrict__ primes, int n_all, int n_q,
+                         int K, int alpha, int limbs, int ndig, uint64_t g, int log_n, bool accumulate, bool few)
+{
+    key_ip_body(Blk::hw(), acc, D, dnt, dnt_bstride, key, primes, n_all, n_q, K, alpha, limbs, ndig, g, log_n, accumulate,
+                few);
 }
 
 // Two hoisted rotations of one ciphertext (Galois elements g1, g2) selected
@@ -584,18 +620,20 @@ __global__ void k_moddown_final_mux(View out, View acc, View conv, const ModDown
 }
 
 // out_c[t] = (acc_c[t] - conv_c[t]) * P^-1 (+ add_c[t][galois(j)] for the components in add_mask)
-__global__ void k_moddown_final(View out, View acc, View conv, const ModDownTable *__restrict__ tab,
-                                const PrimeConst *__restrict__ primes, View add, int add_mask, uint64_t g, int log_n)
+__device__ __forceinline__ void moddown_final_body(const Blk &b, View out, View acc, View conv,
+                                                   const ModDownTable *__restrict__ tab,
+                                                   const PrimeConst *__restrict__ primes, View add, int add_mask,
+                                                   uint64_t g, int log_n)
 {
     const int n = 1 << log_n;
-    const int t = blockIdx.y, bc = blockIdx.z, bi = bc / 2, ci = bc % 2;
+    const int t = b.y, bc = b.z, bi = bc / 2, ci = bc % 2;
     const uint64_t q = primes[t].q, w = tab->pinv[t], wsh = tab->pinv_sh[t];
     const uint64_t *a = acc.p + bi * acc.bstride + ci * acc.cstride + (size_t)t * n;
     const uint64_t *cv = conv.p + bi * conv.bstride + ci * conv.cstride + (size_t)t * n;
     uint64_t *o = out.p + bi * out.bstride + ci * out.cstride + (size_t)t * n;
     const bool has = (add_mask >> ci) & 1;
     const uint64_t *ap = has ? add.p + bi * add.bstride + ci * add.cstride + (size_t)t * n : nullptr;
-    for (int j = (blockIdx.x * blockDim.x + threadIdx.x) * 2; j < n; j += gridDim.x * blockDim.x * 2) {
+    for (int j = (b.x * blockDim.x + threadIdx.x) * 2; j < n; j += b.gx * blockDim.x * 2) {
         const ulonglong2 av = *reinterpret_cast<const ulonglong2 *>(a + j);
         const ulonglong2 cw = *reinterpret_cast<const ulonglong2 *>(cv + j);
         ulonglong2 r;
@@ -613,6 +651,12 @@ __global__ void k_moddown_final(View out, View acc, View conv, const ModDownTabl
         }
         *reinterpret_cast<ulonglong2 *>(o + j) = r;
     }
+}
+
+__global__ void k_moddown_final(View out, View acc, View conv, const ModDownTable *__restrict__ tab,
+                                const PrimeConst *__restrict__ primes, View add, int add_mask, uint64_t g, int log_n)
+{
+    moddown_final_body(Blk::hw(), out, acc, conv, tab, primes, add, add_mask, g, log_n);
 }
 
 // r_i = ([x + floor(q_t/2)]_{q_t} mod q_i - floor(q_t/2) mod q_i) for the lower limbs
@@ -786,6 +830,54 @@ __global__ void k_ddec_shares(uint64_t *out, View ct, const uint64_t *shares, co
     uint64_t *o = out + ((size_t)bi * (np + 1) + p) * n;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
         o[j] = p == 0 ? c0[j] : mulmod(c1[j], shares[(size_t)(p - 1) * n + j], P);
+}
+
+// ---- several rings in one launch per key-switching stage ----------------------------------------
+// The job of flat block bid: the last whose block0 <= bid (block0 ascending, the first 0); b gets
+// the coordinates that job's own grid gives the block.
+template <class J>
+__device__ __forceinline__ const J &job_of_block(const J *__restrict__ jobs, int n_jobs, long long bid, Blk &b)
+{
+    int lo = 0, hi = n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jobs[mid].block0 <= bid) lo = mid;
+        else hi = mid - 1;
+    }
+    const J &j = jobs[lo];
+    const long long local = bid - j.block0, plane = (long long)j.gx * j.gy;
+    b = Blk{(int)(local % j.gx), (int)((local / j.gx) % j.gy), (int)(local / plane), j.gx, j.gy, j.gz};
+    return j;
+}
+
+__global__ void k_automorphism_jobs(const AutomorphismJob *__restrict__ jobs, int n_jobs)
+{
+    Blk b;
+    const AutomorphismJob &J = job_of_block(jobs, n_jobs, blockIdx.x, b);
+    automorphism_body(b, J.out, J.in, J.g, J.comps, J.log_n, false, J.primes);
+}
+
+template <int MK>
+__global__ void __launch_bounds__(256, MK <= 4 ? 4 : 2) k_convert_jobs(const ConvertJob *__restrict__ jobs, int n_jobs)
+{
+    Blk b;
+    const ConvertJob &J = job_of_block(jobs, n_jobs, blockIdx.x, b);
+    basis_convert_body<MK>(b, J.tabs, J.out, J.in, J.primes, J.groups, J.gstride_out, J.gstride_in, J.n);
+}
+
+__global__ void k_key_ip_jobs(const KeyIpJob *__restrict__ jobs, int n_jobs)
+{
+    Blk b;
+    const KeyIpJob &J = job_of_block(jobs, n_jobs, blockIdx.x, b);
+    key_ip_body(b, J.acc, J.D, J.dnt, J.dnt_bstride, J.key, J.primes, J.n_all, J.n_q, J.K, J.alpha, J.limbs, J.ndig,
+                J.g, J.log_n, false, J.few != 0);
+}
+
+__global__ void k_moddown_jobs(const ModDownJob *__restrict__ jobs, int n_jobs)
+{
+    Blk b;
+    const ModDownJob &J = job_of_block(jobs, n_jobs, blockIdx.x, b);
+    moddown_final_body(b, J.out, J.acc, J.conv, J.tab, J.primes, J.add, J.add_mask, J.g, J.log_n);
 }
 
 } // namespace
@@ -1084,6 +1176,50 @@ void launch_ddec_shares(const LaunchCtx &c, uint64_t *out, View ct, const uint64
     dim3 grid(ew_blocks(c.N, 1), n_parties + 1, B);
     k_ddec_shares<<<grid, 256, 0, c.stream>>>(out, ct, shares, c.t->primes, n_parties, c.N);
     post(c);
+}
+
+// ---- several rings in one launch per key-switching stage: launchers ----------------------------
+static void check_job_grid(long long blocks, int n_jobs)
+{
+    HX_CHECK(n_jobs >= 1 && blocks >= 1 && blocks < (1ll << 31), HX_EINVAL, "bad several-ring job grid");
+}
+
+void launch_automorphism_jobs(cudaStream_t s, const AutomorphismJob *jobs, int n_jobs, long long blocks,
+                              std::atomic<uint64_t> *launches)
+{
+    check_job_grid(blocks, n_jobs);
+    k_automorphism_jobs<<<(unsigned)blocks, 256, 0, s>>>(jobs, n_jobs);
+    HX_CUDA(cudaGetLastError());
+    if (launches) *launches += 1;
+}
+
+void launch_convert_jobs(cudaStream_t s, const ConvertJob *jobs, int n_jobs, long long blocks, int max_src,
+                         std::atomic<uint64_t> *launches)
+{
+    check_job_grid(blocks, n_jobs);
+    HX_CHECK(max_src >= 1 && max_src <= MAXK, HX_EINVAL, "too many conversion sources");
+    if (max_src <= 4) k_convert_jobs<4><<<(unsigned)blocks, 256, 0, s>>>(jobs, n_jobs);
+    else k_convert_jobs<MAXK><<<(unsigned)blocks, 256, 0, s>>>(jobs, n_jobs);
+    HX_CUDA(cudaGetLastError());
+    if (launches) *launches += 1;
+}
+
+void launch_key_ip_jobs(cudaStream_t s, const KeyIpJob *jobs, int n_jobs, long long blocks,
+                        std::atomic<uint64_t> *launches)
+{
+    check_job_grid(blocks, n_jobs);
+    k_key_ip_jobs<<<(unsigned)blocks, 256, 0, s>>>(jobs, n_jobs);
+    HX_CUDA(cudaGetLastError());
+    if (launches) *launches += 1;
+}
+
+void launch_moddown_jobs(cudaStream_t s, const ModDownJob *jobs, int n_jobs, long long blocks,
+                         std::atomic<uint64_t> *launches)
+{
+    check_job_grid(blocks, n_jobs);
+    k_moddown_jobs<<<(unsigned)blocks, 256, 0, s>>>(jobs, n_jobs);
+    HX_CUDA(cudaGetLastError());
+    if (launches) *launches += 1;
 }
 
 } // namespace hx

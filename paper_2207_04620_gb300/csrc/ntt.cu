@@ -683,10 +683,8 @@ void autotune_ntt(const LaunchCtx &c, uint64_t *buf, int rows, int *best, float 
 // ---- end of the autotuner
 
 // ---- several rings: launcher
-void launch_ntt_multi(cudaStream_t s, const std::vector<NttJob> &jobs_in, bool inverse, int n_sm,
-                      std::atomic<uint64_t> *launches)
+void plan_ntt_jobs(std::vector<NttJob> &jobs, int *tiles_cols, int *tiles_rows)
 {
-    std::vector<NttJob> jobs = jobs_in;
     int tc = 0, tr = 0;
     for (auto &J : jobs) {
         HX_CHECK(J.log_n >= 11 && J.log_n <= 16, HX_EINVAL, "ring degree outside 2^11..2^16");
@@ -700,15 +698,17 @@ void launch_ntt_multi(cudaStream_t s, const std::vector<NttJob> &jobs_in, bool i
         tc += (int)c;
         tr += (int)r;
     }
+    *tiles_cols = tc;
+    *tiles_rows = tr;
+}
+
+void launch_ntt_jobs(cudaStream_t s, const NttJob *jp, int n_jobs, int tc, int tr, bool inverse, int n_sm,
+                     std::atomic<uint64_t> *launches)
+{
     if (tc == 0) return;
-    void *jd = nullptr;
-    HX_CUDA(cudaMallocAsync(&jd, jobs.size() * sizeof(NttJob), s));
-    HX_CUDA(cudaMemcpyAsync(jd, jobs.data(), jobs.size() * sizeof(NttJob), cudaMemcpyHostToDevice, s));
-    const NttJob *jp = reinterpret_cast<const NttJob *>(jd);
     // two halves of shared memory per block (current tile, next tile)
     const size_t smem_c = 2 * sizeof(uint64_t) * kMultiColsBuf, smem_r = 2 * sizeof(uint64_t) * kMultiRowsBuf;
     const int grid_c = std::min(tc, n_sm * 8), grid_r = std::min(tr, n_sm * 8);
-    const int n_jobs = (int)jobs.size();
     if (!inverse) {
         k_ntt_multi<false, true><<<grid_c, kMultiT, smem_c, s>>>(jp, n_jobs, tc);
         k_ntt_multi<false, false><<<grid_r, kMultiT, smem_r, s>>>(jp, n_jobs, tr);
@@ -716,10 +716,27 @@ void launch_ntt_multi(cudaStream_t s, const std::vector<NttJob> &jobs_in, bool i
         k_ntt_multi<true, false><<<grid_r, kMultiT, smem_r, s>>>(jp, n_jobs, tr);
         k_ntt_multi<true, true><<<grid_c, kMultiT, smem_c, s>>>(jp, n_jobs, tc);
     }
-    const cudaError_t le = cudaGetLastError();
-    HX_CUDA(cudaFreeAsync(jd, s));
-    HX_CUDA(le);
+    HX_CUDA(cudaGetLastError());
     if (launches) *launches += 2;
+}
+
+void launch_ntt_multi(cudaStream_t s, const std::vector<NttJob> &jobs_in, bool inverse, int n_sm,
+                      std::atomic<uint64_t> *launches)
+{
+    std::vector<NttJob> jobs = jobs_in;
+    int tc = 0, tr = 0;
+    plan_ntt_jobs(jobs, &tc, &tr);
+    if (tc == 0) return;
+    void *jd = nullptr;
+    HX_CUDA(cudaMallocAsync(&jd, jobs.size() * sizeof(NttJob), s));
+    HX_CUDA(cudaMemcpyAsync(jd, jobs.data(), jobs.size() * sizeof(NttJob), cudaMemcpyHostToDevice, s));
+    try {
+        launch_ntt_jobs(s, reinterpret_cast<const NttJob *>(jd), (int)jobs.size(), tc, tr, inverse, n_sm, launches);
+    } catch (...) {
+        cudaFreeAsync(jd, s);
+        throw;
+    }
+    HX_CUDA(cudaFreeAsync(jd, s));
     HX_CUDA(cudaStreamSynchronize(s));  // the host job vector is released at return
 }
 

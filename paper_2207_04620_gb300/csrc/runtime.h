@@ -218,6 +218,16 @@ struct Eval {
     const SwitchKey &rot_key(const hx_keyset &ks, uint64_t g);
 };
 
+// one rotation of a several-ring call: a ciphertext batch of its context, by `step` slots
+struct RotateJob {
+    hx_context *ctx;
+    const hx_keyset *ks;
+    Cts a;
+    int64_t step;
+};
+// the rotations, every stage of their key switches one launch over all jobs (multi.cu)
+std::vector<Cts> rotate_jobs(const std::vector<RotateJob> &jobs, cudaStream_t s);
+
 Scalars scalars_for(const hx_context &ctx, int limbs, int64_t c);
 void upload_plaintext(hx_context &ctx, cudaStream_t s, const int64_t *coeffs, int limbs, uint64_t *dst_mont);
 // the same over p_0..p_{K-1} then q_0..q_{limbs-1} (an extended mask's row order)

@@ -130,6 +130,7 @@ _SIGS = {
     "hx_ntt_tiles": (c_int, [c_vp, P_i32, P_i32]),
     "hx_ntt_tuning": (c_int, [c_vp, P_i32, c_int]),
     "hx_ntt_split": (c_int, [c_vp, c_int]),
+    "hx_rotate_jobs": (c_int, [c_vp, c_size_t, PP, c_vp]),
     "hx_profile_enable": (c_int, [c_vp, c_int]),
     "hx_profile_read": (c_int, [c_vp, c_int, ctypes.c_char_p, c_size_t, P_u64, P_dbl, P_dbl]),
 }
@@ -520,6 +521,22 @@ def hx_matmul_batch_mixed(ctx: int, ks: int, A, B, h, stream=None) -> list:
 
 class _MatmulJob(ctypes.Structure):
     _fields_ = [("ctx", c_vp), ("ks", c_vp), ("A", c_vp), ("B", c_vp), ("h", c_int)]
+
+
+class _RotateJob(ctypes.Structure):
+    _fields_ = [("ctx", c_vp), ("ks", c_vp), ("ct", c_vp), ("step", c_i64)]
+
+
+def hx_rotate_jobs(jobs, stream=None) -> list:
+    """Rotations over several rings in one call, each key-switching stage one launch over all of
+    them: jobs = [(ctx, ks, ct, step), ...]; returns one handle per job (of that job's context)."""
+    n = len(jobs)
+    if n == 0:
+        raise ValueError("no jobs")
+    arr = (_RotateJob * n)(*[_RotateJob(*j) for j in jobs])
+    out = (c_vp * n)()
+    _chk(lib().hx_rotate_jobs(arr, n, out, _stream(stream)))
+    return [out[i] for i in range(n)]
 
 
 def hx_matmul_jobs(jobs, stream=None) -> list:

@@ -531,6 +531,43 @@ def test_rectangular_matmul_bit_exact(name, h, t):
         pr.close()
 
 
+def test_rotations_over_three_rings_one_launch_per_stage_bit_exact():
+    """hx_rotate_jobs: rotations of ciphertexts of three rings (N = 2^12, 2^13, 2^14), at several
+    levels and steps (negative ones and the identity among them), every key-switching stage one
+    launch over all of them; each result equals hx_rotate of its job, and one per ring equals
+    the oracle's rotation.  A job whose keys lack the Galois key fails the whole call before any
+    device work."""
+    specs = {"alg3": [(1, 5), (-3, 4), (7, 2), (0, 5)], "alg3_13": [(5, 6), (-1, 3)], "cfg1": [(2, 8), (-6, 5)]}
+    pairs = {name: Pair(name, rot_steps=sorted({k for k, _ in js if k})) for name, js in specs.items()}
+    try:
+        jobs, plain, oracle_rot = [], [], []
+        for name, js in specs.items():
+            pr = pairs[name]
+            for i, (k, limbs) in enumerate(js):
+                x = np.random.default_rng(300 + i).uniform(-1, 1, pr.octx.S)
+                A = pr.encrypt(x, 310 + i, limbs=limbs)
+                h = pr.to_lib(A)
+                jobs.append((pr.ctx, pr.ks, h, k))
+                plain.append(hx.hx_rotate(pr.ctx, pr.ks, h, k))
+                oracle_rot.append(C.Evaluator(pr.octx, pr.oks).rotate(A, k) if i == 0 else None)
+        outs = hx.hx_rotate_jobs(jobs)
+        for (ctx, ks, h, k), o, p, want in zip(jobs, outs, plain, oracle_rot):
+            assert np.array_equal(hx.hx_ct_export(ctx, o), hx.hx_ct_export(ctx, p)), k
+            assert hx.hx_ct_info(o) == hx.hx_ct_info(p)
+            if want is not None:
+                assert np.array_equal(hx.hx_ct_export(ctx, o), want.c)
+        for o in outs + plain:
+            hx.hx_ct_destroy(o)
+        # the third ring's keys hold no key for step 3: the call fails and hands back nothing
+        with pytest.raises(hx.HxError):
+            hx.hx_rotate_jobs([jobs[0], (pairs["cfg1"].ctx, pairs["cfg1"].ks, jobs[-1][2], 3)])
+        for j in jobs:
+            hx.hx_ct_destroy(j[2])
+    finally:
+        for pr in pairs.values():
+            pr.close()
+
+
 def test_products_over_two_rings_in_one_call_bit_exact():
     """hx_matmul_jobs: products of two rings (N = 2^12 and 2^13, chains of 5 and 6 limbs), two
     levels and two matrix sizes in one call, the groups running side by side on the device;
