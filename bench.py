@@ -1203,6 +1203,69 @@ def run_matmul_jobs(args):
         hx.hx_context_destroy(ctxs[ln])
 
 
+def run_micro_rotate_jobs(args):
+    """Rotations of ciphertexts of several rings in one hx_rotate_jobs call (each key-switching
+    stage one launch over all of them) against one hx_rotate call per ciphertext, CUDA events on
+    the stream: 48 small jobs (N = 2^12 .. 2^14, 2 .. 5 limbs, the shape of a serving mix) and
+    16 jobs of the config-1 ring (N = 2^14, 8 limbs).  Chains of 60 + 7x45 bit, P = 2x60 bit."""
+    import torch
+
+    from paper_2207_04620_gb300 import hx
+
+    import __graft_entry__
+
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    steps_set = [1, 3, -2, 5]
+    ctxs, kss = {}, {}
+    for ln in (12, 13, 14):
+        ctxs[ln] = hx.hx_context_create(ln, [60] + [45] * 7, [60, 60], 45)
+        hx.hx_autotune(ctxs[ln], stream=stream)
+        kss[ln] = hx.hx_keygen(ctxs[ln], 2, 90 + ln, steps_set)
+    rng = np.random.default_rng(5)
+
+    def make(specs):
+        jobs = []
+        for i, (ln, limbs, k) in enumerate(specs):
+            z = rng.uniform(-1, 1, (1 << ln) // 2)
+            jobs.append((ctxs[ln], kss[ln], hx.hx_encrypt(ctxs[ln], kss[ln], z, limbs, 700 + i), k))
+        return jobs
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 1)):
+            for o in fn():
+                hx.hx_ct_destroy(o)
+        ts = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            outs = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            for o in outs:
+                hx.hx_ct_destroy(o)
+        return statistics.median(ts)
+
+    cases = {"many_small": [(12 + i % 3, 2 + i % 4, steps_set[i % 4]) for i in range(48)],
+             "config1_ring": [(14, 8, steps_set[i % 4]) for i in range(16)]}
+    out = {"micro": "rotate_jobs", "what": "one hx_rotate_jobs call (13 launches for all jobs) against one hx_rotate "
+                                          "call (13 launches) per ciphertext, median over the timed steps"}
+    for name, specs in cases.items():
+        jobs = make(specs)
+        ms_jobs = timed(lambda: hx.hx_rotate_jobs(jobs, stream=stream))
+        ms_each = timed(lambda: [hx.hx_rotate(c, k_, h, st, stream=stream) for c, k_, h, st in jobs])
+        out[name] = {"jobs": len(specs), "one_call_ms": round(ms_jobs, 4), "per_ciphertext_ms": round(ms_each, 4),
+                     "speedup": round(ms_each / ms_jobs, 2)}
+        for j in jobs:
+            hx.hx_ct_destroy(j[2])
+    print(json.dumps(out), flush=True)
+    for ln in ctxs:
+        hx.hx_keyset_destroy(kss[ln])
+        hx.hx_context_destroy(ctxs[ln])
+
+
 def run_micro_aggregate(args):
     """Alg. 6 Aggregation alone: the model update w - eta/(B N) * sum_i g_i for the 8
     gradient ciphertexts of one 784->128 layer (h=64, beta=4 packing) from 16 parties,
@@ -1277,7 +1340,7 @@ def run_micro_aggregate(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--micro", choices=["ntt", "aggregate", "encrypt", "ntt-multi"], default=None)
+    ap.add_argument("--micro", choices=["ntt", "aggregate", "encrypt", "ntt-multi", "rotate-jobs"], default=None)
     ap.add_argument("--parties", type=int, default=16)
     ap.add_argument("--workload", choices=["matmul", "sign", "dense", "serve", "rmatmul", "jobs"], default="matmul")
     ap.add_argument("--t", type=int, default=16, help="rows of A in the rectangular product")
@@ -1308,6 +1371,8 @@ def main():
         return run_micro_encrypt(args)
     if args.micro == "ntt-multi":
         return run_micro_ntt_multi(args)
+    if args.micro == "rotate-jobs":
+        return run_micro_rotate_jobs(args)
     if args.micro:
         return print(json.dumps(run_micro(args)), flush=True)
     if args.workload == "sign":
