@@ -475,10 +475,13 @@ hx_status hx_aggregate(hx_context *ctx, const hx_ct *const *grads, size_t n_part
  * pending requests of the same signature (context, keys, kind, level and h, or
  * d/k/relu) whenever one of n_lanes CUDA streams is idle and the batch's
  * estimated device memory fits in what hbm_budget_bytes leaves after the
- * registered keys; the lanes run concurrently.  Each result equals the same
- * request computed alone (hx_matmul, or hx_sign_approx with its
- * refresh_seed).  Submitted ciphertexts stay referenced until their request
- * completes, so the caller may destroy its handles at once. */
+ * registered keys; the lanes run concurrently.  Rotations are the exception to
+ * the signature: pending rotations of every context and level form one batch,
+ * run as one launch per key-switching stage over all of them (as
+ * hx_rotate_jobs).  Each result equals the same request computed alone
+ * (hx_matmul, hx_sign_approx with its refresh_seed, or hx_rotate).  Submitted
+ * ciphertexts stay referenced until their request completes, so the caller
+ * may destroy its handles at once. */
 typedef struct hx_server hx_server;
 hx_status hx_server_create(size_t hbm_budget_bytes, int n_lanes, int max_batch, hx_server **out);
 /* counts a keyset's device bytes against the budget (HX_ENOMEM if it does not fit) */
@@ -488,6 +491,9 @@ hx_status hx_server_submit_matmul(hx_server *sv, hx_context *ctx, const hx_keyse
                                   const hx_ct *B, int h, uint64_t *id);
 hx_status hx_server_submit_sign(hx_server *sv, hx_context *ctx, const hx_keyset *ks, const hx_ct *x, int d, int k,
                                 int relu, uint64_t refresh_seed, uint64_t *id);
+/* a rotation of x by `step` slots (Rot, Fig. 1 item 11) with ctx's keys ks */
+hx_status hx_server_submit_rotate(hx_server *sv, hx_context *ctx, const hx_keyset *ks, const hx_ct *x, int64_t step,
+                                  uint64_t *id);
 /* Moves up to cap completed requests out: ids, result handles (NULL on error),
  * statuses and latencies (submission to completion of its batch on the GPU,
  * ms).  wait != 0 blocks until at least one completes or nothing is pending.

@@ -1,5 +1,5 @@
-// Continuous-batching request server for encrypted matrix products and
-// composite sign/ReLU jobs.
+// Continuous-batching request server for encrypted matrix products,
+// composite sign/ReLU jobs and rotations.
 //
 // Requests queue on the host.  A dispatcher thread forms a batch from the
 // oldest pending request and every other pending request with the same
@@ -9,6 +9,8 @@
 // their batches concurrently, so requests that arrive while others are on the
 // GPU are admitted as lanes and memory free up.  A batch's results are views
 // into its output buffer, equal to what the same request computes alone.
+// Rotations batch across rings: pending rotations of any contexts and levels
+// form one batch, run as one launch per key-switching stage (rotate_jobs).
 // A request may carry a deadline: if it is still queued when its deadline
 // passes, it completes with HX_ETIMEOUT and no GPU work (a batch already on
 // the GPU always runs to the end).
@@ -26,12 +28,13 @@ namespace {
 
 struct Request {
     uint64_t id = 0;
-    int kind = 0;  // 0 matmul, 1 sign
+    int kind = 0;  // 0 matmul, 1 sign, 2 rotation (of any ring: batches span contexts)
     hx_context *ctx = nullptr;
     const hx_keyset *ks = nullptr;
     Cts a, b;
     int h = 0, d = 0, k = 0, relu = 0;
     uint64_t seed = 0;
+    int64_t step = 0;
     Clock::time_point t0, deadline = Clock::time_point::max();
     size_t est = 0;
 };
@@ -46,6 +49,7 @@ struct Done {
 
 bool same_batch(const Request &x, const Request &y)
 {
+    if (x.kind == 2 || y.kind == 2) return x.kind == y.kind;  // rotations of every ring batch together
     return x.ctx == y.ctx && x.ks == y.ks && x.kind == y.kind && x.a.limbs == y.a.limbs && x.a.scale == y.a.scale &&
            (x.kind == 0 ? (x.h == y.h && x.b.limbs == y.b.limbs && x.b.scale == y.b.scale)
                         : (x.d == y.d && x.k == y.k && x.relu == y.relu));
@@ -55,6 +59,10 @@ bool same_batch(const Request &x, const Request &y)
 size_t estimate(const Request &r)
 {
     const size_t ct = (size_t)2 * r.a.limbs * r.ctx->N * 8;
+    if (r.kind == 2) {  // sigma(c1) and its copy, ModUp's digits, the extended pair, the conversion, the output
+        const size_t ext = (size_t)r.a.limbs + r.ctx->K, nd = ((size_t)r.a.limbs + r.ctx->alpha - 1) / r.ctx->alpha;
+        return ((size_t)4 * r.a.limbs + (nd + 2) * ext + 2 * (size_t)r.a.limbs) * r.ctx->N * 8 + ct;
+    }
     return r.kind == 0 ? 48 * ct : 24 * ct + (size_t)2 * r.ctx->n_q * r.ctx->N * 8;
 }
 
@@ -184,32 +192,42 @@ void hx_server::run_lane(Lane &L)
         hx_context &ctx = *r0.ctx;
         int status = HX_OK;
         Cts out;
+        std::vector<Cts> rot_out;  // rotations: one result per request, of its own context
         std::shared_ptr<const hx_matmul_plan> plan;
         try {
-            Eval ev(ctx, L.s);
-            const int B = (int)batch.size();
-            Cts A = ev.alloc(B, 2, r0.a.limbs);
-            A.scale = r0.a.scale;
-            const size_t N = ctx.N;
-            auto pack = [&](Cts &dst, int i, const Cts &src) {
-                for (int c = 0; c < 2; c++)
-                    HX_CUDA(cudaMemcpyAsync(dst.d + i * dst.bstride(N) + c * dst.cstride(N), src.d + c * src.cstride(N),
-                                            sizeof(uint64_t) * dst.limbs * N, cudaMemcpyDeviceToDevice, L.s));
-            };
-            for (int i = 0; i < B; i++) pack(A, i, batch[i].a);
-            if (r0.kind == 0) {
-                Cts Bc = ev.alloc(B, 2, r0.b.limbs);
-                Bc.scale = r0.b.scale;
-                for (int i = 0; i < B; i++) pack(Bc, i, batch[i].b);
-                plan = cached_plan(ctx, r0.h, r0.a.limbs);  // held until the lane's stream is done
-                out = matmul_batch(ctx, *r0.ks, *plan, A, Bc, L.s);
+            if (r0.kind == 2) {
+                std::vector<RotateJob> jobs;
+                for (auto &r : batch) jobs.push_back(RotateJob{r.ctx, r.ks, r.a, r.step});
+                rot_out = rotate_jobs(jobs, L.s);
+                HX_CUDA(cudaStreamSynchronize(L.s));
+                for (auto &o : rot_out) o.buf->stream = nullptr;  // results outlive the lane's stream
             } else {
-                std::vector<uint64_t> seeds;
-                for (auto &r : batch) seeds.push_back(r.seed);
-                out = sign_batch(ctx, *r0.ks, A, r0.d, r0.k, r0.relu != 0, true, seeds, L.s);
+                Eval ev(ctx, L.s);
+                const int B = (int)batch.size();
+                Cts A = ev.alloc(B, 2, r0.a.limbs);
+                A.scale = r0.a.scale;
+                const size_t N = ctx.N;
+                auto pack = [&](Cts &dst, int i, const Cts &src) {
+                    for (int c = 0; c < 2; c++)
+                        HX_CUDA(cudaMemcpyAsync(dst.d + i * dst.bstride(N) + c * dst.cstride(N),
+                                                src.d + c * src.cstride(N), sizeof(uint64_t) * dst.limbs * N,
+                                                cudaMemcpyDeviceToDevice, L.s));
+                };
+                for (int i = 0; i < B; i++) pack(A, i, batch[i].a);
+                if (r0.kind == 0) {
+                    Cts Bc = ev.alloc(B, 2, r0.b.limbs);
+                    Bc.scale = r0.b.scale;
+                    for (int i = 0; i < B; i++) pack(Bc, i, batch[i].b);
+                    plan = cached_plan(ctx, r0.h, r0.a.limbs);  // held until the lane's stream is done
+                    out = matmul_batch(ctx, *r0.ks, *plan, A, Bc, L.s);
+                } else {
+                    std::vector<uint64_t> seeds;
+                    for (auto &r : batch) seeds.push_back(r.seed);
+                    out = sign_batch(ctx, *r0.ks, A, r0.d, r0.k, r0.relu != 0, true, seeds, L.s);
+                }
+                HX_CUDA(cudaStreamSynchronize(L.s));
+                out.buf->stream = nullptr;  // results outlive the lane's stream
             }
-            HX_CUDA(cudaStreamSynchronize(L.s));
-            out.buf->stream = nullptr;  // results outlive the lane's stream
         } catch (const hx::Error &e) {
             status = e.code;
             cudaStreamSynchronize(L.s);
@@ -221,8 +239,10 @@ void hx_server::run_lane(Lane &L)
             Done d;
             d.id = batch[i].id;
             d.status = status;
-            d.ctx = &ctx;
-            if (status == HX_OK) {
+            d.ctx = batch[i].ctx;
+            if (status == HX_OK && r0.kind == 2) {
+                d.out = rot_out[i];
+            } else if (status == HX_OK) {
                 d.out = out;
                 d.out.B = 1;
                 d.out.d = out.d + i * out.bstride(ctx.N);
@@ -343,6 +363,23 @@ hx_status hx_server_submit_sign(hx_server *sv, hx_context *ctx, const hx_keyset 
     r.k = k;
     r.relu = relu;
     r.seed = refresh_seed;
+    return submit(sv, std::move(r), id);
+}
+
+hx_status hx_server_submit_rotate(hx_server *sv, hx_context *ctx, const hx_keyset *ks, const hx_ct *x, int64_t step,
+                                  uint64_t *id)
+{
+    if (!ctx || !ks || !x || x->c.comps != 2) return HX_EINVAL;
+    if (ks->ctx != ctx || x->ctx != ctx) {
+        set_error("keys or ciphertext of another context");
+        return HX_EINVAL;
+    }
+    Request r;
+    r.kind = 2;
+    r.ctx = ctx;
+    r.ks = ks;
+    r.a = x->c;
+    r.step = step;
     return submit(sv, std::move(r), id);
 }
 

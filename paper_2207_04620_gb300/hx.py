@@ -119,6 +119,7 @@ _SIGS = {
     "hx_server_register_keys": (c_int, [c_vp, c_vp]),
     "hx_server_submit_matmul": (c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_int, P_u64]),
     "hx_server_submit_sign": (c_int, [c_vp, c_vp, c_vp, c_vp, c_int, c_int, c_int, c_u64, P_u64]),
+    "hx_server_submit_rotate": (c_int, [c_vp, c_vp, c_vp, c_vp, c_i64, P_u64]),
     "hx_server_poll": (c_int, [c_vp, c_int, P_u64, PP, P_i32, P_dbl, c_int]),
     "hx_server_stats": (c_int, [c_vp, P_u64, c_int]),
     "hx_server_destroy": (None, [c_vp]),
@@ -714,6 +715,12 @@ def hx_server_submit_matmul(sv, ctx, ks, A, B, h) -> int:
 def hx_server_submit_sign(sv, ctx, ks, x, d, k, relu=False, refresh_seed=0) -> int:
     rid = c_u64()
     _chk(lib().hx_server_submit_sign(sv, ctx, ks, x, d, k, int(relu), refresh_seed, ctypes.byref(rid)))
+    return rid.value
+
+
+def hx_server_submit_rotate(sv, ctx, ks, x, step) -> int:
+    rid = c_u64()
+    _chk(lib().hx_server_submit_rotate(sv, ctx, ks, x, int(step), ctypes.byref(rid)))
     return rid.value
 
 

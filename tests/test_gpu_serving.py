@@ -51,6 +51,8 @@ def _requests(ctx, ks, s):
 def _submit(sv, ctx, ks, kind, args):
     if kind == "matmul":
         return hx.hx_server_submit_matmul(sv, ctx, ks, *args)
+    if kind == "rotate":
+        return hx.hx_server_submit_rotate(sv, ctx, ks, *args)
     x, d, k, seed = args
     return hx.hx_server_submit_sign(sv, ctx, ks, x, d, k, relu=False, refresh_seed=seed)
 
@@ -58,6 +60,8 @@ def _submit(sv, ctx, ks, kind, args):
 def _alone(ctx, ks, kind, args):
     if kind == "matmul":
         return hx.hx_matmul(ctx, ks, *args)
+    if kind == "rotate":
+        return hx.hx_rotate(ctx, ks, *args)
     x, d, k, seed = args
     return hx.hx_sign_approx(ctx, ks, x, d, k, relu=False, allow_refresh=True, refresh_seed=seed)
 
@@ -224,9 +228,10 @@ def test_mixed_size_batch_equals_products_alone(setup):
 
 def test_two_rings_in_one_server_equal_requests_alone(setup):
     """One server over two contexts of different ring degree and chain length (N = 2^12 with
-    5 limbs, N = 2^13 with 6 limbs): a stream of matmuls and signs of both rings at several
-    levels, submitted together, batched per signature and run across lanes; every result equals
-    the same request computed alone, bit for bit."""
+    5 limbs, N = 2^13 with 6 limbs): a stream of matmuls, signs and rotations of both rings at
+    several levels, submitted together, batched (matmuls and signs per signature, rotations of
+    both rings together) and run across lanes; every result equals the same request computed
+    alone, bit for bit."""
     ctx, ks, s = setup
     p = PARAMS["alg3_13"]
     ctx2 = hx.hx_context_create(p["log_n"], p["q_bits"], p["p_bits"], p["log2_scale"])
@@ -244,6 +249,13 @@ def test_two_rings_in_one_server_equal_requests_alone(setup):
         for i, d in enumerate((2, 4)):
             x = hx.hx_encrypt(ctx2, ks2, workloads.sign_inputs(60 + i, s2), 6, 90 + i)
             reqs.append((ctx2, ks2, "sign", (x, d, 1, 2000 + i)))
+        st1 = Hc.matmul_rotation_steps(8, s // 64, 5)  # steps the first ring's keys hold
+        for i, (k, limbs) in enumerate(((st1[0], 5), (st1[-1], 3), (0, 4))):
+            x = hx.hx_encrypt(ctx, ks, np.random.default_rng(900 + i).uniform(-1, 1, s), limbs, 95 + i)
+            reqs.append((ctx, ks, "rotate", (x, k)))
+        for i, (k, limbs) in enumerate(((steps2[0], 6), (steps2[-1], 2))):
+            x = hx.hx_encrypt(ctx2, ks2, np.random.default_rng(950 + i).uniform(-1, 1, s2), limbs, 97 + i)
+            reqs.append((ctx2, ks2, "rotate", (x, k)))
         order = np.random.default_rng(5).permutation(len(reqs))  # the rings interleaved
         reqs = [reqs[i] for i in order]
         sv = hx.hx_server_create(64 << 30, 3, 4)
