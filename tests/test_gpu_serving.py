@@ -278,6 +278,45 @@ def test_two_rings_in_one_server_equal_requests_alone(setup):
         hx.hx_context_destroy(ctx2)
 
 
+def test_rotations_of_two_rings_form_one_batch(setup):
+    """Rotation requests of two rings (N = 2^12 and 2^13) queued while the server is paused go
+    out as one batch (one launch per key-switching stage over both rings) and each equals
+    hx_rotate alone."""
+    ctx, ks, s = setup
+    p = PARAMS["alg3_13"]
+    ctx2 = hx.hx_context_create(p["log_n"], p["q_bits"], p["p_bits"], p["log2_scale"])
+    s2 = (1 << p["log_n"]) // 2
+    ks2 = hx.hx_keygen(ctx2, 2, 47, [1, -5])
+    st1 = Hc.matmul_rotation_steps(8, s // 64, 5)
+    try:
+        reqs = []
+        for i, (c, k_, n, st, limbs) in enumerate([(ctx, ks, s, st1[0], 5), (ctx2, ks2, s2, 1, 6), (ctx, ks, s, st1[1], 2),
+                                                  (ctx2, ks2, s2, -5, 3), (ctx2, ks2, s2, 1, 4)]):
+            x = hx.hx_encrypt(c, k_, np.random.default_rng(400 + i).uniform(-1, 1, n), limbs, 40 + i)
+            reqs.append((c, k_, "rotate", (x, st)))
+        sv = hx.hx_server_create(64 << 30, 2, 16)
+        hx.hx_server_register_keys(sv, ks)
+        hx.hx_server_register_keys(sv, ks2)
+        hx.hx_server_pause(sv, True)
+        ids = [_submit(sv, c, k_, kind, args) for c, k_, kind, args in reqs]
+        hx.hx_server_pause(sv, False)
+        got = _collect(sv, len(ids))
+        stats = hx.hx_server_stats(sv)
+        hx.hx_server_destroy(sv)
+        assert stats["completed"] == len(reqs) and stats["batches"] == 1 and stats["largest_batch"] == len(reqs)
+        for rid, (c, k_, kind, args) in zip(ids, reqs):
+            res, st, lat = got[rid]
+            assert st == 0
+            alone = _alone(c, k_, kind, args)
+            assert np.array_equal(hx.hx_ct_export(c, res), hx.hx_ct_export(c, alone))
+            hx.hx_ct_destroy(res)
+            hx.hx_ct_destroy(alone)
+            hx.hx_ct_destroy(args[0])
+    finally:
+        hx.hx_keyset_destroy(ks2)
+        hx.hx_context_destroy(ctx2)
+
+
 def test_several_ring_call_equals_products_alone(setup):
     """hx_matmul_jobs with both rings: the same results as hx_matmul on each pair alone."""
     ctx, ks, s = setup
